@@ -1,0 +1,203 @@
+"""Python access to the CPU oracle (``qx_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the bench's
+CPU-baseline leg use this module; the CUDA library never imports it.
+
+``build()`` compiles the oracle with the host C++ compiler into
+``oracle/_build/liboracle.so`` (recompiled when the source is newer).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qx_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GATE_CODES = {
+    "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
+    "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
+}
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if needed; return the shared-library path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
+               "-pthread", _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_run.restype = ctypes.c_void_p
+            lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p, _c_int_p,
+                                       _c_dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _c_dbl_p,
+                                       ctypes.c_int]
+            lib.oracle_num_gens.argtypes = [ctypes.c_void_p]
+            lib.oracle_num_terms.restype = ctypes.c_long
+            lib.oracle_num_terms.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_terms.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p,
+                                         _c_dbl_p, _c_dbl_p]
+            lib.oracle_pruned_sumsq.restype = ctypes.c_double
+            lib.oracle_pruned_sumsq.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_free.argtypes = [ctypes.c_void_p]
+            lib.oracle_gate_table.argtypes = [ctypes.c_int, ctypes.c_double, _c_dbl_p]
+            lib.oracle_cx.restype = ctypes.c_int
+            lib.oracle_cx.argtypes = [ctypes.c_char, ctypes.c_char, ctypes.c_char_p]
+            lib.oracle_plan.restype = ctypes.c_void_p
+            lib.oracle_plan.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p, _c_int_p,
+                                        _c_dbl_p]
+            lib.oracle_plan_num_ops.restype = ctypes.c_long
+            lib.oracle_plan_num_ops.argtypes = [ctypes.c_void_p]
+            lib.oracle_plan_op_kind.argtypes = [ctypes.c_void_p, ctypes.c_long]
+            lib.oracle_plan_lut.argtypes = [ctypes.c_void_p, ctypes.c_long, _c_dbl_p]
+            lib.oracle_plan_free.argtypes = [ctypes.c_void_p]
+            lib.oracle_flatten.restype = ctypes.c_void_p
+            lib.oracle_flatten.argtypes = [ctypes.c_int, ctypes.c_int, _c_dbl_p, _c_dbl_p]
+            lib.oracle_expval.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p,
+                                          _c_int_p, _c_dbl_p, ctypes.c_char_p, _c_dbl_p]
+            _lib = lib
+    return _lib
+
+
+def _arrays(instrs):
+    m = len(instrs)
+    g = np.array([GATE_CODES[i[0]] for i in instrs], dtype=np.int32).reshape(m)
+    a = np.array([i[1] for i in instrs], dtype=np.int32).reshape(m)
+    b = np.array([i[2] for i in instrs], dtype=np.int32).reshape(m)
+    t = np.array([i[3] for i in instrs], dtype=np.float64).reshape(m)
+    return m, g, a, b, t
+
+
+def _ip(a):
+    return a.ctypes.data_as(_c_int_p)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_c_dbl_p)
+
+
+def _collect(lib, h, n):
+    out = []
+    try:
+        for g in range(lib.oracle_num_gens(h)):
+            k = lib.oracle_num_terms(h, g)
+            buf = ctypes.create_string_buffer(max(1, k * n))
+            re = np.empty(k, np.float64)
+            im = np.empty(k, np.float64)
+            lib.oracle_terms(h, g, buf, _dp(re), _dp(im))
+            raw = buf.raw[: k * n].decode("ascii")
+            strings = [raw[i * n:(i + 1) * n] for i in range(k)]
+            out.append({"strings": strings, "re": re, "im": im,
+                        "pruned_sumsq": lib.oracle_pruned_sumsq(h, g)})
+    finally:
+        lib.oracle_free(h)
+    return out
+
+
+def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
+    """Propagate generators through ``instrs``.
+
+    mode: "gate" or "plan".  gens: (begin, end) range of Z_j generators (default
+    all n).  init: optional list of (string, weight) initial generators.
+    Returns one dict per generator: strings (base-4 order), re, im, pruned_sumsq.
+    """
+    lib = _load()
+    m, g, a, b, t = _arrays(instrs)
+    gb, ge = (0, n) if gens is None else gens
+    if init:
+        s = "".join(p for p, _ in init).encode("ascii")
+        wts = np.array([w for _, w in init], np.float64)
+        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+                           float(eps), 0, 0, len(init), s, _dp(wts), int(threads))
+    else:
+        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+                           float(eps), int(gb), int(ge), 0, None, None, int(threads))
+    if not h:
+        raise ValueError("oracle rejected the circuit")
+    return _collect(lib, h, n)
+
+
+def as_dict(gen):
+    """{string: real weight} of one generator result (asserts im == 0)."""
+    assert np.all(gen["im"] == 0.0)
+    return dict(zip(gen["strings"], gen["re"].tolist()))
+
+
+def gate_table(name, theta=0.0):
+    lib = _load()
+    out = np.zeros(9, np.float64)
+    lib.oracle_gate_table(GATE_CODES[name], float(theta), _dp(out))
+    return out.reshape(3, 3)
+
+
+def cx(c, t):
+    """(control, target) letters -> (pair, sign) under CX."""
+    lib = _load()
+    buf = ctypes.create_string_buffer(2)
+    s = lib.oracle_cx(c.encode(), t.encode(), buf)
+    return buf.raw.decode(), s
+
+
+def plan(n, instrs):
+    """[(kind, lut)] per operator: kind 'U' with an n x 3 x 3 table, or 'V' with None."""
+    lib = _load()
+    m, g, a, b, t = _arrays(instrs)
+    h = lib.oracle_plan(n, m, _ip(g), _ip(a), _ip(b), _dp(t))
+    if not h:
+        raise ValueError("oracle rejected the circuit")
+    out = []
+    try:
+        for k in range(lib.oracle_plan_num_ops(h)):
+            if lib.oracle_plan_op_kind(h, k):
+                lut = np.zeros((n, 3, 3), np.float64)
+                lib.oracle_plan_lut(h, k, _dp(lut))
+                out.append(("U", lut))
+            else:
+                out.append(("V", None))
+    finally:
+        lib.oracle_plan_free(h)
+    return out
+
+
+def flatten(lambdas, w4):
+    """Eq. 3 on an explicit complex form: w4 has shape (parents, n, 4) over (I,X,Y,Z)."""
+    lib = _load()
+    w4 = np.ascontiguousarray(w4, np.float64)
+    lam = np.ascontiguousarray(lambdas, np.float64)
+    npar, n, _ = w4.shape
+    h = lib.oracle_flatten(n, npar, _dp(lam), _dp(w4))
+    return _collect(lib, h, n)[0]
+
+
+def expval(n, instrs, q):
+    """<0|U^dagger Q U|0> for one Pauli string q."""
+    lib = _load()
+    m, g, a, b, t = _arrays(instrs)
+    out = np.zeros(1, np.float64)
+    rc = lib.oracle_expval(n, m, _ip(g), _ip(a), _ip(b), _dp(t), q.encode("ascii"), _dp(out))
+    if rc:
+        raise ValueError("oracle rejected the circuit")
+    return float(out[0])

@@ -1,0 +1,312 @@
+"""Seeded synthetic circuits: the inputs shared by the oracle, the tests and the bench.
+
+This module only draws gate lists.  It holds none of the propagation
+arithmetic (no gate images, no tables, no Pauli algebra), so the CPU oracle
+and the CUDA library can both consume its output without sharing any code
+that computes a result.
+
+A circuit is ``(n, instrs)`` where ``instrs`` is a list of
+``(gate, q0, q1, theta)`` tuples: the instruction tuple ``{g, w, theta}`` of
+Section III.A of the Qimax paper (gate name, wire(s), parameter; theta = 0
+when the gate has none, q1 = -1 for single-qubit gates).
+
+Gate names: H S SDG X Y Z SX SXDG T TDG RX RY RZ (one qubit), CX CZ (two).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+ONE_QUBIT = ("H", "S", "SDG", "X", "Y", "Z", "SX", "SXDG", "T", "TDG", "RX", "RY", "RZ")
+TWO_QUBIT = ("CX", "CZ")
+ROTATIONS = ("RX", "RY", "RZ")
+ALL_GATES = ONE_QUBIT + TWO_QUBIT
+
+
+def _g1(name, q, theta=0.0):
+    return (name, int(q), -1, float(theta))
+
+
+def _g2(name, c, t):
+    return (name, int(c), int(t), 0.0)
+
+
+def _insert_at_random(rng, instrs, extra):
+    """Insert each gate of ``extra`` at a uniform position of the growing list."""
+    out = list(instrs)
+    for g in extra:
+        pos = int(rng.integers(0, len(out) + 1))
+        out.insert(pos, g)
+    return out
+
+
+def random_layers(seed: int, n: int = 8, layers: int = 20, n_t: int = 10):
+    """n-qubit random Clifford layers plus T gates (the n=8, 20-layer, 10-T workload).
+
+    Per layer the qubits are visited in a random order; each visited qubit
+    draws H, S or CNOT uniformly; a CNOT takes the visited qubit as control and
+    the next unvisited qubit as target (H when none is left).  Then ``n_t`` T
+    gates are inserted at uniform positions on uniform qubits.
+    """
+    rng = np.random.default_rng(seed)
+    instrs = []
+    for _ in range(layers):
+        order = list(rng.permutation(n))
+        while order:
+            q = order.pop(0)
+            kind = int(rng.integers(0, 3))
+            if kind == 0:
+                instrs.append(_g1("H", q))
+            elif kind == 1:
+                instrs.append(_g1("S", q))
+            elif order:
+                t = order.pop(0)
+                instrs.append(_g2("CX", q, t))
+            else:
+                instrs.append(_g1("H", q))
+    ts = [_g1("T", int(rng.integers(0, n))) for _ in range(n_t)]
+    return n, _insert_at_random(rng, instrs, ts)
+
+
+def brickwork(seed: int, n: int = 50, n_gates: int = 2000, n_t: int = 16, qubits=None):
+    """Random Clifford brickwork plus T gates (the n=50, 2000-gate, 16-T workload).
+
+    Layer L pairs (q, q+1) starting at offset L mod 2; each brick draws H, S or
+    CNOT uniformly; a CNOT gets a random orientation, a one-qubit gate a random
+    member of the pair.  Stops after ``n_gates`` Clifford gates, then inserts
+    ``n_t`` T gates at uniform positions on uniform qubits.
+    """
+    rng = np.random.default_rng(seed)
+    instrs = _brick_gates(rng, list(range(n)) if qubits is None else list(qubits), n_gates)
+    ts = [_g1("T", int(rng.integers(0, n))) for _ in range(n_t)]
+    return n, _insert_at_random(rng, instrs, ts)
+
+
+def _brick_gates(rng, wires, count):
+    """``count`` random H/S/CNOT bricks over the ordered wire list ``wires``."""
+    out = []
+    layer = 0
+    while len(out) < count:
+        for i in range(layer % 2, len(wires) - 1, 2):
+            if len(out) >= count:
+                break
+            a, b = wires[i], wires[i + 1]
+            kind = int(rng.integers(0, 3))
+            if kind == 2:
+                if rng.integers(0, 2):
+                    a, b = b, a
+                out.append(_g2("CX", a, b))
+            else:
+                q = a if rng.integers(0, 2) else b
+                out.append(_g1("H" if kind == 0 else "S", q))
+        layer += 1
+    return out
+
+
+def _random_pair_gates(rng, wires, count):
+    """``count`` random H/S/CX gates, CX on a uniform ordered pair of distinct wires."""
+    wires = list(wires)
+    out = []
+    for _ in range(count):
+        kind = int(rng.integers(0, 3))
+        if kind == 2:
+            a, b = rng.choice(len(wires), size=2, replace=False)
+            out.append(_g2("CX", wires[int(a)], wires[int(b)]))
+        else:
+            q = wires[int(rng.integers(0, len(wires)))]
+            out.append(_g1("H" if kind == 0 else "S", q))
+    return out
+
+
+def fan_in_heavy(seed: int, n: int = 50, n_s: int = 16, total: int = 2000, tail: int = 600):
+    """Heavy n=50 Clifford+T workload: 34 generators of 65,536 terms each.
+
+    Built so that the literal brickwork workload's quoted size (up to ~65k terms
+    per generator, millions in total) is actually reached:
+
+    * H on every qubit, then CX(i -> q) for every i outside S = {0..n_s-1} and
+      q in S: generator i becomes X on S plus a Pauli on i.
+    * A random Clifford prefix on the qubits outside S (keeps X on all of S).
+    * T on every q in S: each generator outside S fans out to 2^n_s terms.
+    * CX(n-2 -> n-1): a two-qubit operator that closes the one-qubit operator.
+    * RZ(theta_q) on every q in S, theta_q ~ U[0, 2 pi): every child now has two
+      parents per qubit, so the index-based accumulation is exercised.
+    * A random brickwork Clifford tail on all qubits (``tail`` gates).
+
+    The prefix length makes the gate count ``total``.
+    """
+    rng = np.random.default_rng(seed)
+    S = list(range(n_s))
+    rest = list(range(n_s, n))
+    head = [_g1("H", q) for q in range(n)]
+    head += [_g2("CX", i, q) for i in rest for q in S]
+    n_prefix = total - len(head) - 2 * n_s - 1 - tail
+    if n_prefix < 0:
+        raise ValueError("total too small for the fixed part of the workload")
+    prefix = _brick_gates(rng, rest, n_prefix)
+    ts = [_g1("T", q) for q in S]
+    sep = [_g2("CX", n - 2, n - 1)]
+    thetas = rng.uniform(0.0, 2.0 * math.pi, size=n_s)
+    rz = [_g1("RZ", q, thetas[q]) for q in S]
+    tail_g = _brick_gates(rng, list(range(n)), tail)
+    return n, head + prefix + ts + sep + rz + tail_g
+
+
+def hea(seed: int, n: int = 16, layers: int = 4):
+    """Hardware-efficient ansatz: per layer RY(t) RZ(t) on each qubit, then a CX ring.
+
+    theta = k pi / 4 with k ~ U{0..7} with probability 0.7, else U[0, 2 pi).
+    """
+    rng = np.random.default_rng(seed)
+    instrs = []
+
+    def draw():
+        if rng.random() < 0.7:
+            return int(rng.integers(0, 8)) * math.pi / 4.0
+        return float(rng.uniform(0.0, 2.0 * math.pi))
+
+    for _ in range(layers):
+        for q in range(n):
+            instrs.append(_g1("RY", q, draw()))
+            instrs.append(_g1("RZ", q, draw()))
+        for q in range(n):
+            instrs.append(_g2("CX", q, (q + 1) % n))
+    return n, instrs
+
+
+def random_pairs(seed: int, n: int = 100, n_cliff: int = 100_000, n_rz: int = 20):
+    """n=100 random-pair Clifford circuit with ``n_rz`` RZ(U[0,2pi)) at uniform positions."""
+    rng = np.random.default_rng(seed)
+    instrs = _random_pair_gates(rng, range(n), n_cliff)
+    rz = [_g1("RZ", int(rng.integers(0, n)), float(rng.uniform(0.0, 2.0 * math.pi)))
+          for _ in range(n_rz)]
+    return n, _insert_at_random(rng, instrs, rz)
+
+
+def fan_in_deep(seed: int, n: int = 100, n_s: int = 20, total: int = 100_000):
+    """Heavy n=100 workload: 80 generators of 2^20 terms (about 84M terms in all).
+
+    H on every qubit, CX(i -> q) for i outside S = {0..n_s-1} and q in S, then
+    n_s rounds of [random Clifford block on the qubits outside S; RZ(theta_r)
+    on qubit r], and a last Clifford block outside S.  The blocks never touch
+    S, so every coefficient is a product of per-qubit cos/sin factors.
+    """
+    rng = np.random.default_rng(seed)
+    S = list(range(n_s))
+    rest = list(range(n_s, n))
+    instrs = [_g1("H", q) for q in range(n)]
+    instrs += [_g2("CX", i, q) for i in rest for q in S]
+    n_cliff = total - len(instrs) - n_s
+    per = n_cliff // (n_s + 1)
+    sizes = [per] * (n_s + 1)
+    sizes[-1] += n_cliff - per * (n_s + 1)
+    thetas = rng.uniform(0.0, 2.0 * math.pi, size=n_s)
+    for r in range(n_s):
+        instrs += _random_pair_gates(rng, rest, sizes[r])
+        instrs.append(_g1("RZ", r, thetas[r]))
+    instrs += _random_pair_gates(rng, rest, sizes[-1])
+    return n, instrs
+
+
+def ghz(n: int):
+    """GHZ preparation: H(0) then a CX chain."""
+    return n, [_g1("H", 0)] + [_g2("CX", q, q + 1) for q in range(n - 1)]
+
+
+def graph_state(seed: int, n: int, p: float = 0.3):
+    """Graph state on a seeded Erdos-Renyi graph: H on all, CZ on each edge."""
+    rng = np.random.default_rng(seed)
+    instrs = [_g1("H", q) for q in range(n)]
+    for a in range(n):
+        for b in range(a + 1, n):
+            if rng.random() < p:
+                instrs.append(_g2("CZ", a, b))
+    return n, instrs
+
+
+def random_clifford(seed: int, n: int, m: int):
+    """Random circuit over every Clifford gate name of the gate set."""
+    rng = np.random.default_rng(seed)
+    names1 = ("H", "S", "SDG", "X", "Y", "Z", "SX", "SXDG")
+    out = []
+    for _ in range(m):
+        if n >= 2 and rng.random() < 0.4:
+            a, b = rng.choice(n, size=2, replace=False)
+            out.append(_g2(TWO_QUBIT[int(rng.integers(0, 2))], a, b))
+        else:
+            out.append(_g1(names1[int(rng.integers(0, len(names1)))], int(rng.integers(0, n))))
+    return n, out
+
+
+def random_small(seed: int, n: int, m: int, p2: float = 0.3, angles: str = "uniform"):
+    """Random circuit over the whole gate set, for brute-force checks at small n.
+
+    ``angles``: "uniform" draws rotation angles from U[0, 2 pi); "quarter" draws
+    multiples of pi/4 (exercises the exact-Clifford rounding of the tables).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(m):
+        if n >= 2 and rng.random() < p2:
+            a, b = rng.choice(n, size=2, replace=False)
+            out.append(_g2(TWO_QUBIT[int(rng.integers(0, 2))], a, b))
+        else:
+            g = ONE_QUBIT[int(rng.integers(0, len(ONE_QUBIT)))]
+            th = 0.0
+            if g in ROTATIONS:
+                if angles == "quarter":
+                    th = int(rng.integers(0, 8)) * math.pi / 4.0
+                else:
+                    th = float(rng.uniform(0.0, 2.0 * math.pi))
+            out.append(_g1(g, int(rng.integers(0, n)), th))
+    return n, out
+
+
+def random_paulis(seed: int, n: int, k: int, min_weight: int = 1):
+    """``k`` seeded random Pauli strings ("IXYZ" letters, character i = qubit i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < k:
+        s = "".join("IXYZ"[int(v)] for v in rng.integers(0, 4, size=n))
+        if sum(c != "I" for c in s) >= min_weight:
+            out.append(s)
+    return out
+
+
+def serving_stream(seed: int, count: int = 10_000, n_range=(10, 60), gate_range=(200, 5000),
+                   rot_range=(0, 14), rate_hz: float = 2000.0):
+    """Seeded request stream: (arrival time s, n, instrs) with Poisson arrivals.
+
+    n ~ U{10..60}, Clifford gate count ~ U{200..5000} (random pairs), T/RZ count
+    ~ U{0..14} at uniform positions (T or RZ(U[0,2pi)) with equal probability).
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += float(rng.exponential(1.0 / rate_hz))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        m = int(rng.integers(gate_range[0], gate_range[1] + 1))
+        k = int(rng.integers(rot_range[0], rot_range[1] + 1))
+        instrs = _random_pair_gates(rng, range(n), m)
+        rots = []
+        for _ in range(k):
+            q = int(rng.integers(0, n))
+            if rng.integers(0, 2):
+                rots.append(_g1("T", q))
+            else:
+                rots.append(_g1("RZ", q, float(rng.uniform(0.0, 2.0 * math.pi))))
+        out.append((t, n, _insert_at_random(rng, instrs, rots)))
+    return out
+
+
+#: Named workloads used by the tests and the bench.
+WORKLOADS = {
+    "random_layers_n8": lambda seed=1: random_layers(seed),
+    "brickwork_n50": lambda seed=1: brickwork(seed),
+    "fan_in_heavy_n50": lambda seed=1: fan_in_heavy(seed),
+    "hea_n16": lambda seed=1: hea(seed),
+    "random_pairs_n100": lambda seed=1: random_pairs(seed),
+    "fan_in_deep_n100": lambda seed=1: fan_in_deep(seed),
+}
