@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the extended-stabilizer propagation hot path (qx_propagate).
+
+Workload (the n=50 Clifford+T configuration at its quoted size): 50 qubits,
+2000 gates, 16 T and 16 RZ gates on 16 fan-out qubits, generators Z_0..Z_49;
+34 generators reach 65,536 terms each (2,228,256 terms in all).  A step is one
+qx_propagate of the whole circuit: initial generators (create_Z_j), fused
+Clifford passes, the 2^16 expansion, 16 index-accumulation passes and the
+Clifford tail, with inputs resident on the device.  L2 is flushed (a 512 MB
+write) between timed steps, outside the per-step CUDA events.
+
+Metric: Pauli-term updates per second = sum over the K + K' grouped operators
+of the terms each was applied to, divided by the step time.
+
+--gpus N under torchrun: every rank propagates its own seeded instance
+(independent problems, no data-path collective): weak scaling.
+--impl reference: the CPU oracle (std::map per generator, gate by gate) on
+the host cores, each step advancing one heavy generator through a bounded
+slice of the same circuit.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fan_in_heavy_n50"
+CONFIG = {
+    "workload": WORKLOAD,
+    "description": "n=50, 2000 gates (H/S/CNOT + 16 T + 16 RZ on 16 fan-out qubits), "
+                   "generators Z_0..Z_49, 34 x 65536 + 16 x 2 = 2,228,256 final terms, "
+                   "FP64 weights, eps=0",
+    "n_qubits": 50,
+    "gates": 2000,
+    "final_terms": 2228256,
+    "l2": "flushed between timed steps (512 MB write)",
+}
+METRIC = "Pauli-term updates/sec"
+UNIT = "term-updates/s"
+FLUSH_BYTES = 512 << 20
+NON_CLIFFORD = ("T", "TDG", "RX", "RY", "RZ")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (sha256 recorded there)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2505_03307_gb300", "csrc", "qx_kernels.cuh")
+    summ = os.path.join(ROOT, "profiles", "ncu_traffic_fan_in_heavy_n50.txt")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        rows = {}
+        kernel_sha = None
+        for ln in open(summ):
+            ln = ln.strip()
+            if ln.startswith("source_sha256:"):
+                kernel_sha = ln.split(":", 1)[1].strip()
+            elif ln.startswith("traffic_per_launch"):
+                _, name, val = ln.split()
+                rows[name] = float(val)
+        if kernel_sha == sha and kernel in rows:
+            return rows[kernel]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "out", "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2505_03307_gb300 import qx
+    from paper_2505_03307_gb300 import workloads as W
+
+    qx.load_library()
+    n, instrs = W.fan_in_heavy(1 + rank)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        r = qx.propagate(plan, kernel_timing=True)
+        r.free()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, stats = [], []
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = qx.propagate(plan, kernel_timing=True)
+            e1.record(stream)
+            stats.append(r.stats())
+            r.free()
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    updates = sum(s["term_updates"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI: host circuit in, host result out
+    e2e_ms = []
+    h2d = d2h = 0
+    e2e_updates = 0
+    pinned = None
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = qx.group_ops(qx.load_circuit(n, instrs))
+        r = qx.propagate(p2)
+        x, z, w, g = r.raw_device()
+        if pinned is None or pinned[0].numel() != x.numel():
+            pinned = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (x, z, w, g)]
+        for hst, dev in zip(pinned, (x, z, w, g)):
+            hst.copy_(dev, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+            e2e_updates += r.stats()["term_updates"]
+            h2d = len(instrs) * 24
+            d2h = sum(t.numel() * t.element_size() for t in (x, z, w, g))
+        del x, z, w, g
+        r.free()
+        del p2
+
+    # ---- max over ranks
+    tot = torch.tensor([total_ms, sum(e2e_ms), float(updates), float(e2e_updates)],
+                       dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms_max, e2e_ms_max = float(mx[0]), float(mx[1])
+        updates_all, e2e_updates_all = float(sm[2]), float(sm[3])
+    else:
+        total_ms_max, e2e_ms_max = total_ms, sum(e2e_ms)
+        updates_all, e2e_updates_all = float(updates), float(e2e_updates)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    value = updates_all / (total_ms_max / 1e3)
+    # ---- roofline of the dominant kernel class
+    kc = {}
+    for s in stats:
+        for name, d in s["kernels"].items():
+            a = kc.setdefault(name, {"launches": 0, "alg_bytes": 0, "ms": 0.0})
+            a["launches"] += d["launches"]
+            a["alg_bytes"] += d["alg_bytes"]
+            a["ms"] += d["ms"]
+    dom = max(kc, key=lambda k: kc[k]["ms"])
+    d = kc[dom]
+    peak, peak_kind = peaks()
+    achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic = ncu_traffic(dom)
+    share = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kc.values())), 4)
+             for k, v in kc.items() if v["launches"]}
+    s0 = stats[0]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded circuits; no dataset)",
+        "config": dict(CONFIG, parallelism=f"independent circuits x{world}" if world > 1 else "single"),
+        "e2e": {"value": e2e_updates_all / (e2e_ms_max / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms_max / args.steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "alg_bytes_per_launch": d["alg_bytes"] / max(1, d["launches"]),
+                     "avg_launch_ms": d["ms"] / max(1, d["launches"])},
+        "kernel_share": share,
+        "per_step": {"term_updates": s0["term_updates"], "children": s0["children"],
+                     "alg_bytes": s0["alg_bytes"], "kernel_launches": s0["kernel_launches"],
+                     "host_syncs": s0["host_syncs"], "K": s0["K"], "Kp": s0["Kp"],
+                     "final_terms": s0["final_terms"], "merge_passes": s0["merge_passes"],
+                     "alg_gbs": s0["alg_bytes"] / (statistics.median(step_ms) / 1e3) / 1e9},
+        "clocks": clocks,
+        "wall_s": t_wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(plan_updates_per_gen(qx, plan, n), budget_s=20.0)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def plan_updates_per_gen(qx, plan, n):
+    """Term updates of one heavy generator (Z_16) in the library's own accounting."""
+    r = qx.propagate(plan, gens=(16, 17))
+    u = r.stats()["term_updates"]
+    r.free()
+    return u
+
+
+# --------------------------------------------------------------------------- oracle
+
+def operator_bounds(instrs):
+    """[begin, end) of every maximal run of one- or two-qubit gates (Sec. III.A)."""
+    out = []
+    for i, g in enumerate(instrs):
+        two = g[0] in ("CX", "CZ")
+        if not out or out[-1][2] != two:
+            out.append([i, i, two])
+        out[-1][1] = i + 1
+    return [(b, e) for b, e, _ in out]
+
+
+class OracleStepper:
+    """Advances the oracle (gate mode) through the workload circuit for one
+    heavy generator, operator by operator, counting term updates per operator
+    like the library does (terms present when the operator starts)."""
+
+    def __init__(self, n, instrs, gen):
+        from oracle import oracle as O
+        self.O = O
+        self.n, self.instrs = n, instrs
+        self.ops = operator_bounds(instrs)
+        self.gen = gen
+        self.reset()
+
+    def reset(self):
+        self.k = 0
+        z = "".join("Z" if q == self.gen else "I" for q in range(self.n))
+        self.strings, self.weights = [z], [1.0]
+
+    def step(self, budget_updates):
+        """Apply whole operators until budget_updates term updates; returns
+        (updates, seconds)."""
+        done = 0
+        t0 = time.perf_counter()
+        while done < budget_updates:
+            if self.k == len(self.ops):
+                self.reset()
+            b = self.ops[self.k][0]
+            e = b
+            upd = 0
+            while self.k < len(self.ops) and done + upd < budget_updates:
+                upd += len(self.strings)
+                ob, oe = self.ops[self.k]
+                e = oe
+                self.k += 1
+                # the term count changes only after an operator with a
+                # non-Clifford gate: end the slice there so that every
+                # operator is counted with the terms present at its start
+                if any(g[0] in NON_CLIFFORD for g in self.instrs[ob:oe]):
+                    break
+            r = self.O.propagate_sum(self.n, self.instrs[b:e], self.strings, self.weights,
+                                     mode="gate")
+            self.strings, self.weights = r["strings"], r["re"]
+            done += upd
+        return done, time.perf_counter() - t0
+
+
+def cpu_baseline(lib_updates_per_gen, budget_s):
+    from paper_2505_03307_gb300 import workloads as W
+    n, instrs = W.fan_in_heavy(1)
+    st = OracleStepper(n, instrs, 16)
+    done, secs = 0, 0.0
+    while secs < budget_s:
+        u, s = st.step(2_000_000)
+        done += u
+        secs += s
+    return {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"generator Z_16 (a 65,536-term generator) of the same circuit, gate by gate "
+                      f"through whole operators for {secs:.1f} s ({done} term updates); "
+                      f"single thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2505_03307_gb300 import workloads as W
+
+    O.build()
+    n, instrs = W.fan_in_heavy(1)
+    st = OracleStepper(n, instrs, 16)
+    budget = 3_000_000
+    for _ in range(args.warmup):
+        st.step(budget)
+    times, done = [], 0
+    for _ in range(args.steps):
+        u, s = st.step(budget)
+        done += u
+        times.append(s)
+    value = done / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded circuits; no dataset)", "config": dict(CONFIG),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: about 3M term updates of generator Z_16 "
+                                   "(65,536 terms at the heavy end), gate by gate through whole "
+                                   "operators of the same circuit; single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * qx.h - C interface of libqx, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of extended-stabilizer Pauli propagation (Qimax,
+ * arXiv 2505.03307).
+ *
+ * What it computes.  For a circuit U = g_{m-1} ... g_0 on n qubits, every
+ * generator Z_j of |0...0> evolves as U Z_j U^dagger = sum_P c_j(P) P, a sum of
+ * real-weighted Hermitian Pauli strings (Eq. 1 and Sec. II.A; gates act by
+ * conjugation g P g^dagger, Sec. II.C).  The library follows the paper's
+ * operator-level method: the instruction list is grouped into one-qubit
+ * operators U_k and two-qubit operators V_k (Sec. III.A, Algorithm 2), every
+ * U_k gets a table of 3x3 Pauli images per qubit (Algorithm 1), and each term
+ * is expanded through those tables (sub + flatten, Eq. 3) with identical
+ * strings merged by index-based accumulation (abstract).
+ *
+ * Pauli strings cross this interface as bit masks.  A string on n qubits uses
+ * W = ceil(n / 64) words of x bits and W words of z bits; qubit q is bit
+ * (q mod 64) of word q / 64.  (x, z) = (0,0) I, (1,0) X, (1,1) Y, (0,1) Z, and
+ * Y is the Hermitian Y (any sign lives in the real weight).  Arrays of strings
+ * are row-major: string i occupies words [i*W, i*W + W).
+ *
+ * Conventions (not fixed by the paper): RX/RY/RZ(theta) = exp(-i theta s / 2),
+ * T = diag(1, e^{i pi/4}), S = diag(1, i), SX = sqrt(X); CZ = H(t) CX H(t).
+ * Composed table entries within 2^-50 of 0 or of +-1 are set to 0 or +-1.
+ * eps = 0 keeps every string that the tables reach, even when its weight sums
+ * to exactly 0; eps > 0 drops |w| < eps after every U_k.
+ *
+ * Errors.  Every call returns a qx_status.  On error the out-parameters are
+ * left untouched and qx_last_error() returns a message for the calling thread.
+ * The library never aborts the process.
+ *
+ * Threads and streams.  Handles are not thread-safe; distinct handles may be
+ * used from distinct threads on distinct streams.  Device work is issued on
+ * the stream of qx_prop_opts; calls that return host values synchronise that
+ * stream.
+ */
+#ifndef QX_H_INCLUDED_
+#define QX_H_INCLUDED_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QX_OK = 0,
+  QX_EINVAL = 1,       /* invalid argument or circuit */
+  QX_ENOMEM = 2,       /* device or host allocation failed */
+  QX_EBUDGET = 3,      /* the counted term storage exceeds qx_prop_opts.hbm_budget */
+  QX_ECAP = 4,         /* the term count exceeds qx_prop_opts.max_terms, or a table filled up */
+  QX_ECUDA = 5,        /* a CUDA runtime call failed (message in qx_last_error) */
+  QX_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+  QX_EUNSUPPORTED = 7  /* valid but not supported (e.g. n > 128, no usable GPU) */
+} qx_status;
+
+/* Gate codes of qx_instr.gate. */
+typedef enum {
+  QX_H = 0, QX_S = 1, QX_SDG = 2, QX_X = 3, QX_Y = 4, QX_Z = 5, QX_SX = 6, QX_SXDG = 7,
+  QX_T = 8, QX_TDG = 9, QX_RX = 10, QX_RY = 11, QX_RZ = 12, QX_CX = 13, QX_CZ = 14
+} qx_gate;
+
+/* One instruction {g, w, theta} (Sec. III.A): gate, wire(s), parameter.
+ * q1 is the target of CX / second wire of CZ and is ignored (use -1) for
+ * one-qubit gates; theta is ignored by gates without a parameter. */
+typedef struct {
+  uint32_t gate;
+  int32_t q0;
+  int32_t q1;
+  double theta;
+} qx_instr;
+
+typedef struct qx_circuit qx_circuit;
+typedef struct qx_plan qx_plan;
+typedef struct qx_result qx_result;
+
+/* Optional device allocator: returns device memory of at least `bytes` bytes
+ * usable on `stream` (NULL on failure); free releases it, stream-ordered. */
+typedef void* (*qx_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*qx_free_fn)(void* ptr, void* ctx, void* stream);
+
+typedef struct {
+  int precision;        /* 64: FP64 weights (the only value accepted at present) */
+  double eps;           /* pruning threshold, >= 0 (see above) */
+  int gen_begin;        /* generators Z_j with gen_begin <= j < gen_end; */
+  int gen_end;          /*   gen_end <= 0 means n (all generators) */
+  size_t hbm_budget;    /* max bytes of term storage at any step; 0 = unlimited */
+  size_t max_terms;     /* max number of terms at any step; 0 = unlimited */
+  void* stream;         /* cudaStream_t to issue work on; NULL = default stream */
+  qx_alloc_fn alloc;    /* NULL: cudaMallocAsync / cudaFreeAsync on `stream` */
+  qx_free_fn free;
+  void* alloc_ctx;
+  uint32_t timeout_ms;  /* bound on device-side waits; 0 = 2000 ms */
+  uint32_t flags;       /* QX_FLAG_* bits */
+} qx_prop_opts;
+
+/* qx_prop_opts.flags: record CUDA events around every kernel launch (on the
+ * launch stream) and report per-kernel-class device time in qx_prop_stats. */
+#define QX_FLAG_KERNEL_TIMING 1u
+
+/* Kernel classes of qx_prop_stats.kc_* (names from qx_kernel_class_name). */
+#define QX_KC_COUNT 10
+
+/* Counters of one propagation (metrics and launch accounting). */
+typedef struct {
+  uint64_t K, Kp;              /* number of U_k and V_k operators of the plan (Sec. III.A) */
+  uint64_t term_updates;       /* sum over the K + K' operators of the terms they were applied to */
+  uint64_t children;           /* terms written by expansion and merge steps */
+  uint64_t alg_bytes;          /* algorithmic bytes: (in + out) terms of each device step x 16W+8 */
+  uint64_t kernel_launches;    /* kernels launched by this call */
+  uint64_t host_syncs;         /* stream synchronisations inside this call */
+  uint64_t final_terms;        /* terms of all generators at the end */
+  uint64_t peak_terms;         /* largest term count of any step */
+  uint64_t fan_steps;          /* device expansion steps (one-qubit operators with fan-out) */
+  uint64_t merge_passes;       /* index-accumulation (merge) passes */
+  uint64_t clifford_passes;    /* fused Clifford passes */
+  /* per kernel class: launches, algorithmic bytes (terms each launch must
+   * read and write, 16W+8 bytes per term), and device milliseconds (only with
+   * QX_FLAG_KERNEL_TIMING; 0 otherwise) */
+  uint64_t kc_launches[16];
+  uint64_t kc_bytes[16];
+  double kc_ms[16];
+} qx_prop_stats;
+
+/* Name of kernel class k (0 <= k < QX_KC_COUNT), "" otherwise. */
+const char* qx_kernel_class_name(int k);
+
+/* Fills *o with defaults: precision 64, eps 0, all generators, no limits,
+ * default stream, cudaMallocAsync, timeout 2000 ms. */
+void qx_default_opts(qx_prop_opts* o);
+
+/* Validates and copies an instruction list (Sec. III.A).  1 <= n <= 128,
+ * 0 <= q0 < n, for CX/CZ 0 <= q1 < n and q1 != q0, theta finite.
+ * m may be 0.  *out is owned by the caller (qx_free_circuit). */
+qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out);
+
+/* divide_instruction + create_chain + create_LUT_1q (Algorithm 2 header lines,
+ * Algorithm 1): maximal runs of one-qubit gates become U_k, maximal runs of
+ * two-qubit gates V_k; for each U_k and wire j the gates of U_{k,j} are
+ * composed in list order into a 3x3 table.  Host only; deterministic.
+ * *out is owned by the caller (qx_free_plan); it does not refer to `c`. */
+qx_status qx_group_ops(const qx_circuit* c, qx_plan** out);
+
+/* Number of U_k (*K) and V_k (*Kp) operators; either pointer may be NULL. */
+qx_status qx_plan_info(const qx_plan* p, size_t* K, size_t* Kp);
+
+/* Kind of operator `op` of the chain (in circuit order): 1 = U, 0 = V. */
+qx_status qx_plan_op(const qx_plan* p, size_t op, int* kind);
+
+/* LUT_1q of operator `op` (which must be a U): n x 3 x 3 doubles, row-major,
+ * entry [j][a][c] = coefficient of Pauli c in the image of Pauli a under
+ * U_{k,j}, with a, c in (X, Y, Z) order.  out holds n*9 doubles. */
+qx_status qx_plan_lut(const qx_plan* p, size_t op, double* out);
+
+/* Host-side inspection of the fused Clifford passes built from the plan:
+ * *count = number of passes; pass s maps a Pauli string (x, z: W words each,
+ * host memory) and *sign to its image under that pass (in place). */
+qx_status qx_plan_clifford_passes(const qx_plan* p, size_t* count);
+qx_status qx_plan_clifford_apply(const qx_plan* p, size_t pass, uint64_t* x, uint64_t* z,
+                                 int* sign);
+
+/* Algorithm 2 on the GPU: generators Z_j (gen_begin <= j < gen_end) start as
+ * one term of weight 1 (create_Z_j) and pass through the operator chain.
+ * The result owns its device arrays (freed by qx_free_result with the same
+ * allocator).  Returns QX_EBUDGET / QX_ECAP before allocating a step whose
+ * counted size exceeds the limits; the plan stays valid either way.
+ * Result generator g (0 <= g < gen_end - gen_begin) is Z_{gen_begin + g}. */
+qx_status qx_propagate(const qx_plan* p, const qx_prop_opts* o, qx_result** out);
+
+/* As qx_propagate, but the initial generators are `ngen` single terms given
+ * in host memory: x, z (ngen x W words) and weights w (ngen doubles, or NULL
+ * for all 1).  gen_begin / gen_end of *o are ignored. */
+qx_status qx_propagate_from(const qx_plan* p, int ngen, const uint64_t* x, const uint64_t* z,
+                            const double* w, const qx_prop_opts* o, qx_result** out);
+
+/* Number of generators, words per string and terms of the whole result. */
+qx_status qx_result_shape(const qx_result* r, int* ngen, int* nwords, size_t* nterms);
+
+/* Per generator: number of terms, sum of squared weights and the squared
+ * weight removed by pruning.  Any out pointer may be NULL. */
+qx_status qx_result_info(const qx_result* r, int gen, size_t* nterms, double* sumsq,
+                         double* pruned_sumsq);
+
+/* Counters of the propagation that made r. */
+qx_status qx_result_stats(const qx_result* r, qx_prop_stats* s);
+
+/* Terms of generator `gen` in base-4 index order (I=0, X=1, Y=2, Z=3, qubit 0
+ * the most significant digit; the order of Example 1).  x, z: cap x W words;
+ * w: cap doubles.  on_device != 0: the three pointers are device memory.
+ * QX_EINVAL if cap is smaller than the generator's term count. */
+qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
+                           size_t cap, int on_device);
+
+/* All terms of the result in device order (unsorted), into caller device
+ * buffers: x, z (cap x W words), w (cap doubles), gen (cap int32). */
+qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w, int32_t* gen,
+                        size_t cap);
+
+/* Coefficient c_gen(P) of one string (x, z: W words, host memory): the
+ * weight of P in generator gen, 0 when absent.  *im is always 0 (weights are
+ * real, Sec. II.A).  im may be NULL. */
+qx_status qx_coeff(const qx_result* r, int gen, const uint64_t* x, const uint64_t* z, double* re,
+                   double* im);
+
+/* nq lookups at once: gen (nq int32), x, z (nq x W words), out (nq doubles).
+ * on_device != 0: all four pointers are device memory. */
+qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, const uint64_t* x,
+                         const uint64_t* z, double* out, int on_device);
+
+/* <0| U^dagger Q U |0> for nobs Pauli strings Q (x, z: nobs x W words, host
+ * memory; out: nobs doubles, host).  Each Q is propagated through the inverse
+ * circuit with the same kernels (Heisenberg picture) and the weights of its
+ * Z-type strings (x = 0) are summed.  This is the single-qubit measurement of
+ * Sec. II.B in exact form: p_{k,0} = (1 + <Z_k>) / 2. */
+qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint64_t* z,
+                    const qx_prop_opts* o, double* out);
+
+void qx_free_circuit(qx_circuit* c);
+void qx_free_plan(qx_plan* p);
+void qx_free_result(qx_result* r);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* qx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QX_H_INCLUDED_ */

@@ -55,6 +55,10 @@ def _load():
                                        _c_dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _c_dbl_p,
                                        ctypes.c_int]
+            lib.oracle_run_sum.restype = ctypes.c_void_p
+            lib.oracle_run_sum.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p,
+                                           _c_int_p, _c_dbl_p, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_long, ctypes.c_char_p, _c_dbl_p]
             lib.oracle_num_gens.argtypes = [ctypes.c_void_p]
             lib.oracle_num_terms.restype = ctypes.c_long
             lib.oracle_num_terms.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -138,6 +142,19 @@ def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
     if not h:
         raise ValueError("oracle rejected the circuit")
     return _collect(lib, h, n)
+
+
+def propagate_sum(n, instrs, strings, weights, mode="gate", eps=0.0):
+    """One generator starting as sum_i weights[i] strings[i]; returns its result dict."""
+    lib = _load()
+    m, g, a, b, t = _arrays(instrs)
+    s = "".join(strings).encode("ascii")
+    w = np.ascontiguousarray(weights, np.float64)
+    h = lib.oracle_run_sum(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+                           float(eps), len(strings), s, _dp(w))
+    if not h:
+        raise ValueError("oracle rejected the input")
+    return _collect(lib, h, n)[0]
 
 
 def as_dict(gen):

@@ -420,6 +420,33 @@ void* oracle_run(int n, long m, const int* gate, const int* q0, const int* q1,
   return res;
 }
 
+// One generator that starts as the weighted sum of n_terms strings (n letters
+// each, concatenated) and passes through the circuit.  Returns NULL on invalid
+// input.
+void* oracle_run_sum(int n, long m, const int* gate, const int* q0, const int* q1,
+                     const double* theta, int mode, double eps, long n_terms, const char* strings,
+                     const double* weights) {
+  std::vector<Instr> ins = read_instrs(m, gate, q0, q1, theta);
+  if (!valid(n, ins) || n_terms < 0) return nullptr;
+  PauliSum s;
+  for (long i = 0; i < n_terms; ++i) s[std::string(strings + size_t(i) * n, n)] += weights[i];
+  auto* res = new Result;
+  res->n = n;
+  res->gens.resize(1);
+  res->pruned.assign(1, 0.0);
+  PauliSum out;
+  if (mode == 1) {
+    std::vector<Op> ops = divide_instructions(n, ins);
+    for (auto& op : ops)
+      if (op.one_qubit) create_lut(n, op);
+    out = run_plan_mode(s, n, ops, eps, &res->pruned[0]);
+  } else {
+    out = run_gate_mode(s, ins, eps, &res->pruned[0]);
+  }
+  res->gens[0].assign(out.begin(), out.end());
+  return res;
+}
+
 int oracle_num_gens(void* h) { return int(static_cast<Result*>(h)->gens.size()); }
 
 long oracle_num_terms(void* h, int g) { return long(static_cast<Result*>(h)->gens[g].size()); }

@@ -1,0 +1,105 @@
+// Internal declarations of libqx shared by the host planner and the device driver.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qx.h"
+
+namespace qx {
+
+constexpr int kMaxQubits = 128;
+constexpr int kMaxWords = 2;
+
+// Error reporting: thread-local message behind qx_last_error().
+qx_status fail(qx_status s, const std::string& msg);
+void clear_error();
+
+// 3x3 Pauli image table, rows and columns in (X, Y, Z) order.
+struct Table3 {
+  double r[3][3];
+};
+
+// Encoded op of a fused Clifford pass (gate-list form).
+//   bits 0-1  : kind (0 = one-qubit signed permutation, 1 = CX, 2 = CZ)
+//   bits 2-8  : q0, bits 9-15: q1
+//   bits 16-24: signed permutation, 3 bits per source letter p in (X, Y, Z):
+//               bits 0-1 target letter index, bit 2 sign (1 = negative)
+enum : uint32_t { kOpPerm = 0, kOpCX = 1, kOpCZ = 2 };
+inline uint32_t encode_op(uint32_t kind, int q0, int q1, uint32_t perm) {
+  return kind | (uint32_t(q0) << 2) | (uint32_t(q1 < 0 ? 0 : q1) << 9) | (perm << 16);
+}
+
+// One fused Clifford pass: every Clifford gate between two expansion steps.
+struct CliffPass {
+  std::vector<uint32_t> ops;        // gate-list form, in application order
+  bool identity = true;             // the composed map is the identity
+  // Tableau form: images of X_q (q < n) and Z_q in XZ form
+  // (phase exponent e: the Pauli is i^e X^x Z^z).
+  std::vector<uint64_t> img_x, img_z;  // [2n][W]
+  std::vector<uint8_t> img_e;          // [2n]
+  // Chunk tables for the device: chunk c covers qubits [c*cb, c*cb + cb);
+  // entry (c, idx) with idx = xbits | zbits << cb is the XZ-form image of
+  // X^xbits Z^zbits on that chunk.
+  int chunk_bits = 0;
+  int chunks = 0;
+  std::vector<uint64_t> tab_xz;  // [chunks][1 << 2cb][2W]: x words then z words
+  std::vector<uint8_t> tab_e;    // [chunks][1 << 2cb]
+  bool use_table = false;        // device applies tab_* (else the gate list)
+};
+
+// A fan-out qubit of a one-qubit operator: a 3x3 table that is not a signed
+// permutation.
+struct FanQubit {
+  int q;
+  Table3 t;
+  uint8_t nnz[3];      // non-zero entries per row
+  uint8_t col[3][3];   // their columns, in increasing order
+  bool iso[3];         // row p maps to one letter that no other row reaches
+};
+
+struct FanStep {
+  std::vector<FanQubit> qs;  // increasing qubit order
+  size_t op_index;           // position of the U operator in the chain
+};
+
+enum StepKind { kStepCliff = 0, kStepFan = 1 };
+struct Step {
+  int kind;
+  int index;              // into passes or fans
+  uint64_t ops_before;    // chain operators (paper's U_k, V_k) since the previous fan step
+};
+
+}  // namespace qx
+
+struct qx_circuit {
+  int n;
+  std::vector<qx_instr> ins;
+};
+
+struct qx_plan_device;  // device-side copy of the plan (built on first use)
+
+struct qx_plan {
+  int n = 0;
+  int W = 1;
+  std::vector<qx_instr> ins;                       // the circuit (for the inverse plan of qx_expval)
+  size_t K = 0, Kp = 0;
+  std::vector<int> op_kind;                        // chain: 1 = U, 0 = V
+  std::vector<std::vector<qx::Table3>> luts;       // per chain op (empty for V)
+  std::vector<qx::CliffPass> passes;
+  std::vector<qx::FanStep> fans;
+  std::vector<qx::Step> program;
+  uint64_t ops_after_last_fan = 0;
+  qx_plan_device* dev = nullptr;
+};
+
+namespace qx {
+// Host planner entry points used by the device driver.
+qx_status build_plan(const qx_circuit* c, qx_plan** out);
+qx_status inverse_circuit(const qx_circuit* c, qx_circuit** out);
+void free_plan_device(qx_plan* p);
+// Applies pass `pc` to one string on the host with the same tables the device uses.
+void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z, int* sign);
+}  // namespace qx

@@ -1,0 +1,1068 @@
+// Device driver and C-ABI entry points of libqx that run on the GPU.
+//
+// qx_propagate walks the device program built by the planner: fused Clifford
+// passes (in place) and fan-out steps (expansion with index-based
+// accumulation), Algorithm 2.  Term buffers come from the caller's allocator
+// or from cudaMallocAsync on the caller's stream; nothing is allocated with a
+// blocking call on the hot path.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "qx_common.h"
+#include "qx_kernels.cuh"
+
+using namespace qx;
+using namespace qx::dev;
+
+#define QX_TRY_CUDA(call)                                                             \
+  do {                                                                                \
+    const cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(QX_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define QX_TRY(call)                  \
+  do {                                \
+    const qx_status s_ = (call);      \
+    if (s_ != QX_OK) return s_;       \
+  } while (0)
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Alloc {
+  qx_alloc_fn a = nullptr;
+  qx_free_fn f = nullptr;
+  void* ctx = nullptr;
+  cudaStream_t s = nullptr;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (a) return a(bytes, ctx, s);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    if (f)
+      f(p, ctx, s);
+    else
+      cudaFreeAsync(p, s);
+  }
+};
+
+struct TermBuf {
+  Terms t{};
+  void* base = nullptr;
+};
+
+size_t term_bytes(int W) { return size_t(16 * W + 12); }
+
+qx_status alloc_terms(Alloc& al, int W, size_t cap, TermBuf* out) {
+  cap = std::max<size_t>(cap, 1);
+  const size_t bytes = cap * term_bytes(W) + 64;
+  void* base = al.get(bytes);
+  if (!base) return fail(QX_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  auto* x = static_cast<uint64_t*>(base);
+  out->base = base;
+  out->t.x = x;
+  out->t.z = x + size_t(W) * cap;
+  out->t.w = reinterpret_cast<double*>(x + 2 * size_t(W) * cap);
+  out->t.g = reinterpret_cast<uint32_t*>(out->t.w + cap);
+  out->t.cap = cap;
+  return QX_OK;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+unsigned grid_for(size_t n, int per_block, int sms, int blocks_per_sm) {
+  const size_t need = (n + per_block - 1) / per_block;
+  return unsigned(std::max<size_t>(1, std::min<size_t>(need, size_t(sms) * blocks_per_sm)));
+}
+
+void set_pool_threshold() {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (done_dev == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done_dev = dev;
+}
+
+}  // namespace
+
+// Device copy of the plan: Clifford passes (gate lists or chunk tables) and
+// the fan-out tables, uploaded once per plan and device.
+struct qx_plan_device {
+  int device = -1;
+  void* base = nullptr;
+  struct Pass {
+    const uint32_t* ops = nullptr;
+    int nops = 0;
+    const uint64_t* tab_xz = nullptr;
+    const uint8_t* tab_e = nullptr;
+    int chunks = 0, cb = 0;
+    bool use_table = false, identity = true;
+    size_t smem = 0;
+  };
+  std::vector<Pass> passes;
+  size_t max_smem = 0;
+};
+
+namespace qx {
+
+void free_plan_device(qx_plan* p) {
+  if (!p || !p->dev) return;
+  if (p->dev->base) cudaFree(p->dev->base);
+  delete p->dev;
+  p->dev = nullptr;
+}
+
+}  // namespace qx
+
+namespace {
+
+qx_status ensure_plan_device(const qx_plan* cp, int device) {
+  auto* p = const_cast<qx_plan*>(cp);
+  if (p->dev && p->dev->device == device) return QX_OK;
+  free_plan_device(p);
+  auto* d = new (std::nothrow) qx_plan_device;
+  if (!d) return fail(QX_ENOMEM, "host allocation failed");
+  d->device = device;
+  // one contiguous upload: [ops of every pass][tables of every pass]
+  std::vector<size_t> off_ops(p->passes.size()), off_tab(p->passes.size()),
+      off_e(p->passes.size());
+  size_t bytes = 0;
+  auto align = [](size_t v) { return (v + 255) & ~size_t(255); };
+  for (size_t i = 0; i < p->passes.size(); ++i) {
+    const CliffPass& pc = p->passes[i];
+    off_ops[i] = bytes;
+    bytes = align(bytes + pc.ops.size() * 4);
+    off_tab[i] = bytes;
+    bytes = align(bytes + pc.tab_xz.size() * 8);
+    off_e[i] = bytes;
+    bytes = align(bytes + pc.tab_e.size());
+  }
+  std::vector<unsigned char> host(std::max<size_t>(bytes, 1));
+  for (size_t i = 0; i < p->passes.size(); ++i) {
+    const CliffPass& pc = p->passes[i];
+    if (!pc.ops.empty()) std::memcpy(&host[off_ops[i]], pc.ops.data(), pc.ops.size() * 4);
+    if (!pc.tab_xz.empty()) std::memcpy(&host[off_tab[i]], pc.tab_xz.data(), pc.tab_xz.size() * 8);
+    if (!pc.tab_e.empty()) std::memcpy(&host[off_e[i]], pc.tab_e.data(), pc.tab_e.size());
+  }
+  void* base = nullptr;
+  if (cudaMalloc(&base, host.size()) != cudaSuccess) {
+    cudaGetLastError();
+    delete d;
+    return fail(QX_ENOMEM, "device allocation for the plan tables failed");
+  }
+  if (cudaMemcpy(base, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(base);
+    delete d;
+    return fail(QX_ECUDA, "upload of the plan tables failed");
+  }
+  d->base = base;
+  auto* b = static_cast<unsigned char*>(base);
+  for (size_t i = 0; i < p->passes.size(); ++i) {
+    const CliffPass& pc = p->passes[i];
+    qx_plan_device::Pass dp;
+    dp.ops = reinterpret_cast<const uint32_t*>(b + off_ops[i]);
+    dp.nops = int(pc.ops.size());
+    dp.tab_xz = reinterpret_cast<const uint64_t*>(b + off_tab[i]);
+    dp.tab_e = b + off_e[i];
+    dp.chunks = pc.chunks;
+    dp.cb = pc.chunk_bits;
+    dp.use_table = pc.use_table;
+    dp.identity = pc.identity;
+    dp.smem = pc.use_table ? pc.tab_xz.size() * 8 + pc.tab_e.size() : pc.ops.size() * 4;
+    d->max_smem = std::max(d->max_smem, dp.smem);
+    d->passes.push_back(dp);
+  }
+  p->dev = d;
+  return QX_OK;
+}
+
+FanQ to_dev(const FanQubit& f) {
+  FanQ d{};
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) d.t[a][c] = f.t.r[a][c];
+  d.q = f.q;
+  for (int a = 0; a < 3; ++a) {
+    d.nnz[a] = f.nnz[a];
+    for (int c = 0; c < 3; ++c) d.col[a][c] = f.col[a][c];
+    d.iso[a] = f.iso[a] ? 1 : 0;
+  }
+  return d;
+}
+
+// Scratch of one propagation (freed at the end, stream-ordered).
+struct Scratch {
+  unsigned long long* ncnt = nullptr;  // [0], [1]: term counts; [2]: scan total
+  unsigned* err = nullptr;
+  unsigned long long* gmask = nullptr;  // [G][3][W]
+  uint64_t* mixed = nullptr;            // [G][W]
+  double* pruned = nullptr;             // [G]
+  FanQ* fanq = nullptr;                 // [n]
+  void* base = nullptr;
+  // hash table and leader payload (grow on demand)
+  Slot* table = nullptr;
+  unsigned long long tcap = 0;
+  unsigned epoch = 0;
+  void* payload = nullptr;
+  uint32_t* lead = nullptr;
+  double* pv = nullptr;
+  uint32_t* pmask = nullptr;
+  size_t pcap = 0;
+};
+
+}  // namespace
+
+// Kernel classes of qx_prop_stats.kc_*.
+enum KernelClass {
+  KC_INIT = 0, KC_CLIFF, KC_MASK, KC_INSERT, KC_EMIT, KC_COUNT, KC_SCAN, KC_EXPAND, KC_COMPACT,
+  KC_STATS
+};
+const char* const kKernelClassNames[QX_KC_COUNT] = {
+    "init", "clifford_pass", "fan_mask", "merge_insert", "merge_emit", "expand_count",
+    "expand_scan", "expand_emit", "prune_compact", "gen_stats"};
+
+// Optional CUDA-event timing of every launch, resolved after the final sync.
+struct Timer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t>* pool = nullptr;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> rec;  // class, index of the start event
+  cudaEvent_t get() {
+    if (used == pool->size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool->push_back(e);
+    }
+    return (*pool)[used++];
+  }
+  void begin(int k) {
+    if (!on) return;
+    const size_t i = used;
+    cudaEvent_t e = get();
+    if (!e) return;
+    cudaEventRecord(e, s);
+    rec.push_back({k, i});
+  }
+  void end() {
+    if (!on) return;
+    cudaEvent_t e = get();
+    if (e) cudaEventRecord(e, s);
+  }
+  void resolve(qx_prop_stats* st) {
+    for (const auto& [k, i] : rec) {
+      float ms = 0.f;
+      if (i + 1 < used && cudaEventElapsedTime(&ms, (*pool)[i], (*pool)[i + 1]) == cudaSuccess)
+        st->kc_ms[k] += ms;
+    }
+  }
+};
+
+thread_local std::vector<cudaEvent_t> t_event_pool;
+
+struct qx_result {
+  int n = 0, W = 1, G = 0;
+  size_t N = 0;
+  TermBuf buf;
+  Alloc al;
+  int device = 0;
+  std::vector<unsigned long long> count;
+  std::vector<double> sumsq, pruned;
+  qx_prop_stats st{};
+  IndexSlot* index = nullptr;
+  unsigned long long icap = 0;
+};
+
+namespace {
+
+struct Ctx {
+  const qx_plan* p = nullptr;
+  int n = 0, W = 1, G = 0;
+  int sms = 1;
+  double eps = 0.0;
+  size_t budget = 0, max_terms = 0;
+  unsigned spin_limit = 1u << 22;
+  Alloc al;
+  Scratch sc;
+  qx_prop_stats st{};
+  TermBuf cur;
+  size_t N = 0;
+  int cslot = 0;  // which of ncnt[0], ncnt[1] holds cur's count
+  Timer tm;
+  void begin(int k) { tm.begin(k); }
+  // after a launch: class, launches it made, algorithmic bytes
+  void end(int k, int launches, uint64_t bytes) {
+    tm.end();
+    end_bytes_only(k, launches, bytes);
+  }
+  void end_bytes_only(int k, int launches, uint64_t bytes) {
+    st.kernel_launches += launches;
+    st.kc_launches[k] += launches;
+    st.kc_bytes[k] += bytes;
+  }
+};
+
+qx_status sync_read(Ctx& c, void* host, const void* dev, size_t bytes) {
+  QX_TRY_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
+  c.st.host_syncs++;
+  return QX_OK;
+}
+
+qx_status check_err(Ctx& c) {
+  unsigned e = 0;
+  QX_TRY(sync_read(c, &e, c.sc.err, sizeof e));
+  if (e & kErrSpin) return fail(QX_ETIMEOUT, "a device-side wait for a group leader gave up");
+  if (e & kErrProbe) return fail(QX_ECAP, "a hash table ran out of probe slots");
+  if (e & kErrCap) return fail(QX_ECUDA, "internal error: an output buffer was too small");
+  return QX_OK;
+}
+
+qx_status check_limits(Ctx& c, size_t terms) {
+  if (c.max_terms && terms > c.max_terms)
+    return fail(QX_ECAP, "term count " + std::to_string(terms) + " exceeds max_terms");
+  if (c.budget && terms * term_bytes(c.W) > c.budget)
+    return fail(QX_EBUDGET, "term storage of " + std::to_string(terms * term_bytes(c.W)) +
+                                " bytes exceeds hbm_budget");
+  return QX_OK;
+}
+
+void replace_cur(Ctx& c, TermBuf nb, size_t n, int slot) {
+  c.al.put(c.cur.base);
+  c.cur = nb;
+  c.N = n;
+  c.cslot = slot;
+  c.st.peak_terms = std::max<uint64_t>(c.st.peak_terms, n);
+}
+
+template <int W>
+qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
+  if (dp.identity || c.N == 0) return QX_OK;
+  const unsigned long long* n_in = c.sc.ncnt + c.cslot;
+  c.begin(KC_CLIFF);
+  if (dp.use_table) {
+    const unsigned grid = grid_for(c.N, kThreads, c.sms, 2);
+    if (dp.cb == 4)
+      k_clifford_table<W, 4><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.tab_xz,
+                                                                   dp.tab_e, dp.chunks);
+    else
+      k_clifford_table<W, 3><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.tab_xz,
+                                                                   dp.tab_e, dp.chunks);
+  } else {
+    const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
+    k_clifford_ops<W><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.ops, dp.nops);
+  }
+  c.end(KC_CLIFF, 1, 2ull * c.N * (16 * W + 8));
+  QX_TRY_CUDA(cudaGetLastError());
+  c.st.clifford_passes++;
+  c.st.alg_bytes += 2ull * c.N * (16 * W + 8);
+  return QX_OK;
+}
+
+template <int W>
+qx_status ensure_hash(Ctx& c, size_t n) {
+  Scratch& s = c.sc;
+  const unsigned long long want = std::max<unsigned long long>(64, 2ull * n);
+  if (s.tcap < want) {
+    c.al.put(s.table);
+    s.table = static_cast<Slot*>(c.al.get(want * sizeof(Slot)));
+    if (!s.table) return fail(QX_ENOMEM, "device allocation of the merge table failed");
+    QX_TRY_CUDA(cudaMemsetAsync(s.table, 0, want * sizeof(Slot), c.al.s));
+    s.tcap = want;
+    s.epoch = 0;
+  }
+  if (++s.epoch >= 0xffffu) {
+    QX_TRY_CUDA(cudaMemsetAsync(s.table, 0, s.tcap * sizeof(Slot), c.al.s));
+    s.epoch = 1;
+  }
+  if (s.pcap < n) {
+    c.al.put(s.payload);
+    const size_t cap = std::max<size_t>(n, 64);
+    s.payload = c.al.get(cap * (4 + 24 + 4));
+    if (!s.payload) return fail(QX_ENOMEM, "device allocation of the merge payload failed");
+    s.pv = static_cast<double*>(s.payload);
+    s.lead = reinterpret_cast<uint32_t*>(s.pv + 3 * cap);
+    s.pmask = s.lead + cap;
+    s.pcap = cap;
+  }
+  return QX_OK;
+}
+
+template <int W>
+qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
+  c.st.term_updates += (ops_before + 1) * c.N;
+  c.st.fan_steps++;
+  if (c.N == 0) return QX_OK;
+  Scratch& s = c.sc;
+  const size_t G = size_t(c.G);
+  // 1. which fan-out qubits need a merge, per generator
+  uint64_t niso[3][kMaxWords] = {};
+  for (const FanQubit& f : fs.qs)
+    for (int a = 0; a < 3; ++a)
+      if (!f.iso[a]) niso[a][f.q / 64] |= 1ull << (f.q % 64);
+  uint64_t* d_niso = reinterpret_cast<uint64_t*>(s.fanq + c.n);  // staging after the FanQ array
+  QX_TRY_CUDA(cudaMemcpyAsync(d_niso, niso, sizeof niso, cudaMemcpyHostToDevice, c.al.s));
+  QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
+  c.begin(KC_MASK);
+  k_fan_mask<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+      c.cur.t, s.ncnt + c.cslot, d_niso, d_niso + kMaxWords, d_niso + 2 * kMaxWords, s.gmask);
+  c.end(KC_MASK, 1, uint64_t(c.N) * 16 * W);
+  QX_TRY_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> gm(G * 3 * W);
+  QX_TRY(sync_read(c, gm.data(), s.gmask, gm.size() * 8));
+  std::vector<uint64_t> mixed(G * W, 0);
+  uint64_t any[kMaxWords] = {0, 0};
+  for (size_t g = 0; g < G; ++g)
+    for (int k = 0; k < W; ++k) {
+      const uint64_t a = gm[(g * 3 + 0) * W + k], b = gm[(g * 3 + 1) * W + k],
+                     d = gm[(g * 3 + 2) * W + k];
+      const uint64_t m = (a & b) | (a & d) | (b & d);
+      mixed[g * W + k] = m;
+      any[k] |= m;
+    }
+  std::vector<const FanQubit*> mq, fq;
+  for (const FanQubit& f : fs.qs)
+    ((any[f.q / 64] >> (f.q % 64)) & 1 ? mq : fq).push_back(&f);
+  if (!mq.empty())
+    QX_TRY_CUDA(cudaMemcpyAsync(s.mixed, mixed.data(), G * W * 8, cudaMemcpyHostToDevice, c.al.s));
+  // 2. one merge pass per qubit that needs it in some generator
+  for (size_t j = 0; j < mq.size(); ++j) {
+    const bool last = fq.empty() && j + 1 == mq.size();
+    const FanQ f = to_dev(*mq[j]);
+    QX_TRY(ensure_hash<W>(c, c.N));
+    const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
+    c.begin(KC_INSERT);
+    k_merge_insert<W><<<grid, kThreads, 0, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed,
+                                                     s.table, s.tcap, s.epoch, s.lead, s.pv,
+                                                     s.pmask, s.pcap, c.spin_limit, s.err);
+    c.end(KC_INSERT, 1, uint64_t(c.N) * (16 * W + 8));
+    QX_TRY_CUDA(cudaGetLastError());
+    TermBuf out;
+    QX_TRY(alloc_terms(c.al, W, 3 * c.N, &out));
+    const int oslot = 1 - c.cslot;
+    QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + oslot, 0, 8, c.al.s));
+    c.begin(KC_EMIT);
+    k_merge_emit<W, kThreads><<<grid, kThreads, 0, c.al.s>>>(
+        c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed, s.lead, s.pv, s.pmask, s.pcap,
+        last ? c.eps : 0.0, s.pruned, out.t, s.ncnt + oslot, s.err);
+    c.tm.end();
+    QX_TRY_CUDA(cudaGetLastError());
+    c.st.merge_passes++;
+    unsigned long long nout = 0;
+    QX_TRY(sync_read(c, &nout, s.ncnt + oslot, 8));
+    c.end_bytes_only(KC_EMIT, 1, (c.N + nout) * (16 * W + 8));
+    if (const qx_status e = check_err(c)) {
+      c.al.put(out.base);
+      return e;
+    }
+    if (const qx_status e = check_limits(c, nout)) {
+      c.al.put(out.base);
+      return e;
+    }
+    c.st.alg_bytes += (c.N + nout) * (16 * W + 8);
+    c.st.children += nout;
+    replace_cur(c, out, nout, oslot);
+  }
+  if (fq.empty()) return QX_OK;
+  // 3. one-shot expansion over the qubits that need no merge anywhere
+  std::vector<FanQ> hq;
+  for (const FanQubit* f : fq) hq.push_back(to_dev(*f));
+  QX_TRY_CUDA(cudaMemcpyAsync(s.fanq, hq.data(), hq.size() * sizeof(FanQ), cudaMemcpyHostToDevice,
+                              c.al.s));
+  const int nq = int(hq.size());
+  const size_t ntiles = (c.N + kScanTile - 1) / kScanTile;
+  auto* offs = static_cast<unsigned long long*>(c.al.get((c.N + ntiles + 1) * 8));
+  if (!offs) return fail(QX_ENOMEM, "device allocation of the expansion offsets failed");
+  unsigned long long* tsum = offs + c.N;
+  c.begin(KC_COUNT);
+  k_expand_count<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, nq * sizeof(FanQ), c.al.s>>>(
+      c.cur.t, s.ncnt + c.cslot, s.fanq, nq, offs);
+  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + 8));
+  c.begin(KC_SCAN);
+  k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, s.ncnt + c.cslot, tsum);
+  k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, s.ncnt + 2);
+  k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, s.ncnt + c.cslot, tsum);
+  c.end(KC_SCAN, 3, uint64_t(c.N) * 8 * 3);
+  QX_TRY_CUDA(cudaGetLastError());
+  unsigned long long total = 0;
+  QX_TRY(sync_read(c, &total, s.ncnt + 2, 8));
+  if (const qx_status e = check_limits(c, total)) {
+    c.al.put(offs);
+    return e;
+  }
+  TermBuf out;
+  if (const qx_status e = alloc_terms(c.al, W, total, &out)) {
+    c.al.put(offs);
+    return e;
+  }
+  const unsigned egrid = unsigned(std::max<unsigned long long>(
+      1, std::min<unsigned long long>((total + kExpTile - 1) / kExpTile,
+                                      (unsigned long long)c.sms * 8)));
+  const size_t esmem = nq * sizeof(FanQ) + size_t(kExpTile) * 8;
+  c.begin(KC_EXPAND);
+  k_expand_emit<W><<<egrid, kExpThreads, esmem, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, offs, total,
+                                                         s.fanq, nq, out.t);
+  c.end(KC_EXPAND, 1, (c.N + total) * (16 * W + 8));
+  QX_TRY_CUDA(cudaGetLastError());
+  c.al.put(offs);
+  const int oslot = 1 - c.cslot;
+  c.st.alg_bytes += (c.N + total) * (16 * W + 8);
+  c.st.children += total;
+  QX_TRY_CUDA(cudaMemcpyAsync(s.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
+  replace_cur(c, out, total, oslot);
+  if (c.eps > 0.0) {
+    TermBuf kept;
+    QX_TRY(alloc_terms(c.al, W, c.N, &kept));
+    const int kslot = 1 - c.cslot;
+    QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + kslot, 0, 8, c.al.s));
+    c.begin(KC_COMPACT);
+    k_compact_pruned<W, kThreads><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.t, s.ncnt + c.cslot, c.eps, s.pruned, kept.t, s.ncnt + kslot);
+    c.tm.end();
+    QX_TRY_CUDA(cudaGetLastError());
+    unsigned long long nk = 0;
+    QX_TRY(sync_read(c, &nk, s.ncnt + kslot, 8));
+    c.end_bytes_only(KC_COMPACT, 1, (c.N + nk) * (16 * W + 8));
+    replace_cur(c, kept, nk, kslot);
+  }
+  return QX_OK;
+}
+
+void free_scratch(Ctx& c) {
+  c.al.put(c.sc.table);
+  c.al.put(c.sc.payload);
+  c.al.put(c.sc.base);
+  c.sc = Scratch();
+}
+
+template <int W>
+qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
+                         const double* init_w, int gen_begin, qx_result** out) {
+  const qx_plan* p = c.p;
+  // scratch: counters, masks, pruned mass, fan-out tables
+  const size_t G = size_t(c.G);
+  const size_t sz_cnt = 64, sz_gm = G * 3 * W * 8, sz_mx = G * W * 8, sz_pr = G * 8,
+               sz_fq = size_t(c.n) * sizeof(FanQ) + 3 * kMaxWords * 8;
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t total = al(sz_cnt) + al(sz_gm) + al(sz_mx) + al(sz_pr) + al(sz_fq);
+  c.sc.base = c.al.get(total);
+  if (!c.sc.base) return fail(QX_ENOMEM, "device allocation of scratch failed");
+  auto* b = static_cast<unsigned char*>(c.sc.base);
+  c.sc.ncnt = reinterpret_cast<unsigned long long*>(b);
+  c.sc.err = reinterpret_cast<unsigned*>(b + 32);
+  b += al(sz_cnt);
+  c.sc.gmask = reinterpret_cast<unsigned long long*>(b);
+  b += al(sz_gm);
+  c.sc.mixed = reinterpret_cast<uint64_t*>(b);
+  b += al(sz_mx);
+  c.sc.pruned = reinterpret_cast<double*>(b);
+  b += al(sz_pr);
+  c.sc.fanq = reinterpret_cast<FanQ*>(b);
+  QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
+  QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
+  // A3: initial generators
+  QX_TRY(alloc_terms(c.al, W, G, &c.cur));
+  c.N = G;
+  c.cslot = 0;
+  c.st.peak_terms = G;
+  c.begin(KC_INIT);
+  if (!init_x) {
+    k_init_z<W><<<1, 128, 0, c.al.s>>>(c.cur.t, gen_begin, c.G, c.sc.ncnt);
+  } else {
+    void* tmp = c.al.get(G * (16 * W + 8));
+    if (!tmp) return fail(QX_ENOMEM, "device allocation failed");
+    auto* tx = static_cast<uint64_t*>(tmp);
+    auto* tz = tx + G * W;
+    auto* tw = reinterpret_cast<double*>(tz + G * W);
+    QX_TRY_CUDA(cudaMemcpyAsync(tx, init_x, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(tz, init_z, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
+    if (init_w) QX_TRY_CUDA(cudaMemcpyAsync(tw, init_w, G * 8, cudaMemcpyHostToDevice, c.al.s));
+    k_init_rows<W><<<unsigned((G + 127) / 128), 128, 0, c.al.s>>>(c.cur.t, tx, tz,
+                                                                  init_w ? tw : nullptr, c.G,
+                                                                  c.sc.ncnt);
+    c.al.put(tmp);
+  }
+  c.end(KC_INIT, 1, G * (16 * W + 8));
+  QX_TRY_CUDA(cudaGetLastError());
+  // the program: Clifford passes and fan-out steps in circuit order
+  for (const Step& stp : p->program) {
+    if (stp.kind == kStepCliff) {
+      QX_TRY(run_pass<W>(c, p->dev->passes[stp.index]));
+    } else {
+      QX_TRY(run_fan<W>(c, p->fans[stp.index], stp.ops_before));
+    }
+  }
+  c.st.term_updates += p->ops_after_last_fan * c.N;
+  // per-generator statistics
+  auto* r = new (std::nothrow) qx_result;
+  if (!r) return fail(QX_ENOMEM, "host allocation failed");
+  r->n = c.n;
+  r->W = W;
+  r->G = c.G;
+  r->count.assign(G, 0);
+  r->sumsq.assign(G, 0.0);
+  r->pruned.assign(G, 0.0);
+  void* st = c.al.get(G * 16 + 16);
+  if (!st) {
+    delete r;
+    return fail(QX_ENOMEM, "device allocation failed");
+  }
+  auto* d_count = static_cast<unsigned long long*>(st);
+  auto* d_sumsq = reinterpret_cast<double*>(d_count + G);
+  QX_TRY_CUDA(cudaMemsetAsync(st, 0, G * 16, c.al.s));
+  c.begin(KC_STATS);
+  if (c.N)
+    k_gen_stats<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.t, c.sc.ncnt + c.cslot, d_count, d_sumsq);
+  c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
+  QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(r->sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(r->pruned.data(), c.sc.pruned, G * 8, cudaMemcpyDeviceToHost,
+                              c.al.s));
+  const cudaError_t se = cudaStreamSynchronize(c.al.s);
+  c.st.host_syncs++;
+  c.al.put(st);
+  if (se != cudaSuccess) {
+    delete r;
+    return fail(QX_ECUDA, std::string("propagation failed: ") + cudaGetErrorString(se));
+  }
+  c.tm.resolve(&c.st);
+  c.st.final_terms = c.N;
+  c.st.K = p->K;
+  c.st.Kp = p->Kp;
+  r->N = c.N;
+  r->buf = c.cur;
+  c.cur = TermBuf();
+  r->al = c.al;
+  cudaGetDevice(&r->device);
+  r->st = c.st;
+  *out = r;
+  return QX_OK;
+}
+
+qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, int gen_begin,
+                           const uint64_t* ix, const uint64_t* iz, const double* iw,
+                           qx_result** out) {
+  clear_error();
+  if (!p || !out) return fail(QX_EINVAL, "NULL argument");
+  qx_prop_opts opts;
+  qx_default_opts(&opts);
+  if (o) opts = *o;
+  if (opts.precision != 64) return fail(QX_EUNSUPPORTED, "only precision 64 is supported");
+  if (!(opts.eps >= 0.0)) return fail(QX_EINVAL, "eps must be >= 0");
+  if ((opts.alloc == nullptr) != (opts.free == nullptr))
+    return fail(QX_EINVAL, "alloc and free must both be set or both be NULL");
+  int dev = 0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(QX_EUNSUPPORTED, "no CUDA device is available");
+  }
+  QX_TRY_CUDA(cudaGetDevice(&dev));
+  set_pool_threshold();
+  QX_TRY(ensure_plan_device(p, dev));
+  Ctx c;
+  c.p = p;
+  c.n = p->n;
+  c.W = p->W;
+  c.G = ngen;
+  c.sms = device_sms();
+  c.eps = opts.eps;
+  c.budget = opts.hbm_budget;
+  c.max_terms = opts.max_terms;
+  const unsigned ms = opts.timeout_ms ? opts.timeout_ms : 2000;
+  // one spin iteration sleeps about 32 ns or more: bound the wait by the timeout
+  c.spin_limit = std::max(1024u, std::min(ms, 60000u) * 16000u);
+  c.al.a = opts.alloc;
+  c.al.f = opts.free;
+  c.al.ctx = opts.alloc_ctx;
+  c.al.s = static_cast<cudaStream_t>(opts.stream);
+  c.tm.on = (opts.flags & QX_FLAG_KERNEL_TIMING) != 0;
+  c.tm.s = c.al.s;
+  c.tm.pool = &t_event_pool;
+  if (p->dev->max_smem > 48 * 1024) {
+    static thread_local int attr_dev = -1;
+    if (attr_dev != dev) {
+      const int mx = 200 * 1024;
+      cudaFuncSetAttribute(k_clifford_table<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(k_clifford_table<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      attr_dev = dev;
+    }
+  }
+  qx_status s;
+  if (p->W == 1)
+    s = propagate_impl<1>(c, ix, iz, iw, gen_begin, out);
+  else
+    s = propagate_impl<2>(c, ix, iz, iw, gen_begin, out);
+  if (s != QX_OK) {
+    const std::string msg = qx_last_error();
+    c.al.put(c.cur.base);
+    free_scratch(c);
+    cudaStreamSynchronize(c.al.s);
+    cudaGetLastError();
+    fail(s, msg);
+    return s;
+  }
+  free_scratch(c);
+  return QX_OK;
+}
+
+// Canonical base-4 order: digit(q) = (x xor z) | z << 1 gives I=0, X=1, Y=2,
+// Z=3; qubit 0 is the most significant digit (Example 1).
+void sort_canonical(int n, int W, size_t cnt, const uint64_t* px, const uint64_t* pz,
+                    std::vector<size_t>* order) {
+  const int KW = (2 * n + 63) / 64;
+  std::vector<uint64_t> keys(cnt * KW, 0);
+  for (size_t i = 0; i < cnt; ++i) {
+    uint64_t* k = &keys[i * KW];
+    for (int q = 0; q < n; ++q) {
+      const int xb = int((px[i * W + q / 64] >> (q % 64)) & 1);
+      const int zb = int((pz[i * W + q / 64] >> (q % 64)) & 1);
+      const uint64_t d = uint64_t((xb ^ zb) | (zb << 1));
+      const int pos = 2 * (n - 1 - q);  // bit position from the least significant end
+      const int word = KW - 1 - pos / 64;
+      k[word] |= d << (pos % 64);
+    }
+  }
+  order->resize(cnt);
+  for (size_t i = 0; i < cnt; ++i) (*order)[i] = i;
+  std::sort(order->begin(), order->end(), [&](size_t a, size_t b) {
+    const uint64_t* ka = &keys[a * KW];
+    const uint64_t* kb = &keys[b * KW];
+    for (int w = 0; w < KW; ++w)
+      if (ka[w] != kb[w]) return ka[w] < kb[w];
+    return false;
+  });
+}
+
+template <int W>
+qx_status export_impl(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
+                      size_t cap, int on_device) {
+  Alloc al = r->al;
+  const size_t cnt = r->count[gen];
+  if (cap < cnt) return fail(QX_EINVAL, "cap is smaller than the generator's term count");
+  if (cnt == 0) return QX_OK;
+  TermBuf sel;
+  QX_TRY(alloc_terms(al, W, cnt, &sel));
+  auto* nsel = static_cast<unsigned long long*>(al.get(8));
+  if (!nsel) {
+    al.put(sel.base);
+    return fail(QX_ENOMEM, "device allocation failed");
+  }
+  cudaMemsetAsync(nsel, 0, 8, al.s);
+  auto* nall = static_cast<unsigned long long*>(al.get(8));
+  if (!nall) {
+    al.put(sel.base);
+    al.put(nsel);
+    return fail(QX_ENOMEM, "device allocation failed");
+  }
+  const unsigned long long nn = r->N;
+  cudaMemcpyAsync(nall, &nn, 8, cudaMemcpyHostToDevice, al.s);
+  const int sms = device_sms();
+  k_select<W, kThreads><<<grid_for(r->N, kThreads, sms, 8), kThreads, 0, al.s>>>(
+      r->buf.t, nall, uint32_t(gen), sel.t, nsel);
+  std::vector<uint64_t> hx(cnt * W), hz(cnt * W), px(cnt * W), pz(cnt * W);
+  std::vector<double> hw(cnt), pw(cnt);
+  for (int k = 0; k < W; ++k) {
+    cudaMemcpyAsync(px.data() + k * cnt, sel.t.x + k * sel.t.cap, cnt * 8, cudaMemcpyDeviceToHost,
+                    al.s);
+    cudaMemcpyAsync(pz.data() + k * cnt, sel.t.z + k * sel.t.cap, cnt * 8, cudaMemcpyDeviceToHost,
+                    al.s);
+  }
+  cudaMemcpyAsync(pw.data(), sel.t.w, cnt * 8, cudaMemcpyDeviceToHost, al.s);
+  const cudaError_t e = cudaStreamSynchronize(al.s);
+  al.put(sel.base);
+  al.put(nsel);
+  al.put(nall);
+  if (e != cudaSuccess) return fail(QX_ECUDA, std::string("export failed: ") + cudaGetErrorString(e));
+  // planar -> row-major, then canonical order
+  std::vector<uint64_t> rx(cnt * W), rz(cnt * W);
+  for (size_t i = 0; i < cnt; ++i)
+    for (int k = 0; k < W; ++k) {
+      rx[i * W + k] = px[k * cnt + i];
+      rz[i * W + k] = pz[k * cnt + i];
+    }
+  std::vector<size_t> order;
+  sort_canonical(r->n, W, cnt, rx.data(), rz.data(), &order);
+  for (size_t i = 0; i < cnt; ++i) {
+    const size_t j = order[i];
+    for (int k = 0; k < W; ++k) {
+      hx[i * W + k] = rx[j * W + k];
+      hz[i * W + k] = rz[j * W + k];
+    }
+    hw[i] = pw[j];
+  }
+  if (on_device) {
+    QX_TRY_CUDA(cudaMemcpyAsync(x, hx.data(), cnt * W * 8, cudaMemcpyHostToDevice, al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(z, hz.data(), cnt * W * 8, cudaMemcpyHostToDevice, al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(w, hw.data(), cnt * 8, cudaMemcpyHostToDevice, al.s));
+    QX_TRY_CUDA(cudaStreamSynchronize(al.s));
+  } else {
+    std::memcpy(x, hx.data(), cnt * W * 8);
+    std::memcpy(z, hz.data(), cnt * W * 8);
+    std::memcpy(w, hw.data(), cnt * 8);
+  }
+  return QX_OK;
+}
+
+template <int W>
+qx_status ensure_index(qx_result* r) {
+  if (r->index || r->N == 0) return QX_OK;
+  Alloc al = r->al;
+  const unsigned long long cap = std::max<unsigned long long>(64, 2ull * r->N);
+  auto* tab = static_cast<IndexSlot*>(al.get(cap * sizeof(IndexSlot) + 16));
+  if (!tab) return fail(QX_ENOMEM, "device allocation of the lookup index failed");
+  unsigned* err = reinterpret_cast<unsigned*>(tab + cap);
+  QX_TRY_CUDA(cudaMemsetAsync(tab, 0, cap * sizeof(IndexSlot) + 16, al.s));
+  k_index_build<W><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+      r->buf.t, r->N, tab, cap, err);
+  unsigned e = 0;
+  QX_TRY_CUDA(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, al.s));
+  QX_TRY_CUDA(cudaStreamSynchronize(al.s));
+  if (e) {
+    al.put(tab);
+    return fail(QX_ECAP, "lookup index ran out of probe slots");
+  }
+  r->index = tab;
+  r->icap = cap;
+  return QX_OK;
+}
+
+template <int W>
+qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t* x,
+                     const uint64_t* z, double* out, int on_device) {
+  for (size_t i = 0; !on_device && i < nq; ++i)
+    if (gen[i] < 0 || gen[i] >= r->G) return fail(QX_EINVAL, "generator index out of range");
+  if (r->N == 0) {
+    if (on_device)
+      QX_TRY_CUDA(cudaMemsetAsync(out, 0, nq * 8, r->al.s));
+    else
+      std::fill(out, out + nq, 0.0);
+    return QX_OK;
+  }
+  QX_TRY(ensure_index<W>(r));
+  Alloc al = r->al;
+  const int32_t* dg = gen;
+  const uint64_t *dx = x, *dz = z;
+  double* dout = out;
+  void* tmp = nullptr;
+  if (!on_device) {
+    tmp = al.get(nq * (4 + 16 * W + 8) + 64);
+    if (!tmp) return fail(QX_ENOMEM, "device allocation failed");
+    auto* bx = static_cast<uint64_t*>(tmp);
+    auto* bz = bx + nq * W;
+    auto* bo = reinterpret_cast<double*>(bz + nq * W);
+    auto* bg = reinterpret_cast<int32_t*>(bo + nq);
+    QX_TRY_CUDA(cudaMemcpyAsync(bx, x, nq * W * 8, cudaMemcpyHostToDevice, al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(bz, z, nq * W * 8, cudaMemcpyHostToDevice, al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(bg, gen, nq * 4, cudaMemcpyHostToDevice, al.s));
+    dg = bg;
+    dx = bx;
+    dz = bz;
+    dout = bo;
+  }
+  if (nq)
+    k_lookup<W><<<grid_for(nq, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+        r->buf.t, r->index, r->icap, nq, dg, dx, dz, dout);
+  QX_TRY_CUDA(cudaGetLastError());
+  if (!on_device) {
+    QX_TRY_CUDA(cudaMemcpyAsync(out, dout, nq * 8, cudaMemcpyDeviceToHost, al.s));
+    QX_TRY_CUDA(cudaStreamSynchronize(al.s));
+    al.put(tmp);
+  }
+  return QX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qx_status qx_propagate(const qx_plan* p, const qx_prop_opts* o, qx_result** out) {
+  if (!p) return fail(QX_EINVAL, "plan is NULL");
+  qx_prop_opts opts;
+  qx_default_opts(&opts);
+  if (o) opts = *o;
+  const int gb = opts.gen_begin, ge = opts.gen_end <= 0 ? p->n : opts.gen_end;
+  if (gb < 0 || ge > p->n || gb >= ge) return fail(QX_EINVAL, "bad generator range");
+  return propagate_common(p, &opts, ge - gb, gb, nullptr, nullptr, nullptr, out);
+}
+
+qx_status qx_propagate_from(const qx_plan* p, int ngen, const uint64_t* x, const uint64_t* z,
+                            const double* w, const qx_prop_opts* o, qx_result** out) {
+  if (!p) return fail(QX_EINVAL, "plan is NULL");
+  if (ngen < 1 || !x || !z) return fail(QX_EINVAL, "need at least one initial generator");
+  for (int i = 0; i < ngen; ++i)
+    for (int k = 0; k < p->W; ++k) {
+      const int hi = p->n - 64 * k;  // valid bits in word k
+      const uint64_t mask = hi >= 64 ? ~0ull : ((1ull << hi) - 1);
+      if ((x[size_t(i) * p->W + k] | z[size_t(i) * p->W + k]) & ~mask)
+        return fail(QX_EINVAL, "initial string has bits beyond qubit n-1");
+    }
+  return propagate_common(p, o, ngen, 0, x, z, w, out);
+}
+
+qx_status qx_result_shape(const qx_result* r, int* ngen, int* nwords, size_t* nterms) {
+  clear_error();
+  if (!r) return fail(QX_EINVAL, "result is NULL");
+  if (ngen) *ngen = r->G;
+  if (nwords) *nwords = r->W;
+  if (nterms) *nterms = r->N;
+  return QX_OK;
+}
+
+qx_status qx_result_info(const qx_result* r, int gen, size_t* nterms, double* sumsq,
+                         double* pruned_sumsq) {
+  clear_error();
+  if (!r) return fail(QX_EINVAL, "result is NULL");
+  if (gen < 0 || gen >= r->G) return fail(QX_EINVAL, "generator index out of range");
+  if (nterms) *nterms = r->count[gen];
+  if (sumsq) *sumsq = r->sumsq[gen];
+  if (pruned_sumsq) *pruned_sumsq = r->pruned[gen];
+  return QX_OK;
+}
+
+qx_status qx_result_stats(const qx_result* r, qx_prop_stats* s) {
+  clear_error();
+  if (!r || !s) return fail(QX_EINVAL, "NULL argument");
+  *s = r->st;
+  return QX_OK;
+}
+
+qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
+                           size_t cap, int on_device) {
+  clear_error();
+  if (!r) return fail(QX_EINVAL, "result is NULL");
+  if (gen < 0 || gen >= r->G) return fail(QX_EINVAL, "generator index out of range");
+  if (r->count[gen] && (!x || !z || !w)) return fail(QX_EINVAL, "NULL output buffer");
+  return r->W == 1 ? export_impl<1>(r, gen, x, z, w, cap, on_device)
+                   : export_impl<2>(r, gen, x, z, w, cap, on_device);
+}
+
+qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w, int32_t* gen,
+                        size_t cap) {
+  clear_error();
+  if (!r) return fail(QX_EINVAL, "result is NULL");
+  if (cap < r->N) return fail(QX_EINVAL, "cap is smaller than the result's term count");
+  if (r->N == 0) return QX_OK;
+  if (!x || !z || !w || !gen) return fail(QX_EINVAL, "NULL output buffer");
+  const unsigned grid = grid_for(r->N, kThreads, device_sms(), 8);
+  if (r->W == 1)
+    k_raw<1><<<grid, kThreads, 0, r->al.s>>>(r->buf.t, r->N, x, z, w, gen);
+  else
+    k_raw<2><<<grid, kThreads, 0, r->al.s>>>(r->buf.t, r->N, x, z, w, gen);
+  QX_TRY_CUDA(cudaGetLastError());
+  QX_TRY_CUDA(cudaStreamSynchronize(r->al.s));
+  return QX_OK;
+}
+
+qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, const uint64_t* x,
+                         const uint64_t* z, double* out, int on_device) {
+  clear_error();
+  if (!r) return fail(QX_EINVAL, "result is NULL");
+  if (nq && (!gen || !x || !z || !out)) return fail(QX_EINVAL, "NULL argument");
+  auto* rr = const_cast<qx_result*>(r);
+  return r->W == 1 ? coeff_impl<1>(rr, nq, gen, x, z, out, on_device)
+                   : coeff_impl<2>(rr, nq, gen, x, z, out, on_device);
+}
+
+qx_status qx_coeff(const qx_result* r, int gen, const uint64_t* x, const uint64_t* z, double* re,
+                   double* im) {
+  clear_error();
+  if (!r || !x || !z || !re) return fail(QX_EINVAL, "NULL argument");
+  const int32_t g = gen;
+  double v = 0.0;
+  QX_TRY(qx_coeff_batch(r, 1, &g, x, z, &v, 0));
+  *re = v;
+  if (im) *im = 0.0;
+  return QX_OK;
+}
+
+qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint64_t* z,
+                    const qx_prop_opts* o, double* out) {
+  clear_error();
+  if (!p || !x || !z || !out) return fail(QX_EINVAL, "NULL argument");
+  if (nobs == 0) return QX_OK;
+  qx_circuit fwd;
+  fwd.n = p->n;
+  fwd.ins = p->ins;
+  qx_circuit* inv = nullptr;
+  QX_TRY(inverse_circuit(&fwd, &inv));
+  qx_plan* ip = nullptr;
+  const qx_status ps = build_plan(inv, &ip);
+  qx_free_circuit(inv);
+  if (ps != QX_OK) return ps;
+  qx_prop_opts opts;
+  qx_default_opts(&opts);
+  if (o) opts = *o;
+  qx_result* r = nullptr;
+  qx_status s = qx_propagate_from(ip, int(nobs), x, z, nullptr, &opts, &r);
+  if (s == QX_OK) {
+    Alloc al = r->al;
+    auto* d = static_cast<double*>(al.get(nobs * 8 + 8));
+    auto* nd = reinterpret_cast<unsigned long long*>(d + nobs);
+    if (!d) {
+      s = fail(QX_ENOMEM, "device allocation failed");
+    } else {
+      const unsigned long long nn = r->N;
+      cudaMemsetAsync(d, 0, nobs * 8, al.s);
+      cudaMemcpyAsync(nd, &nn, 8, cudaMemcpyHostToDevice, al.s);
+      if (r->N) {
+        if (r->W == 1)
+          k_ztype_sum<1><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+              r->buf.t, nd, d);
+        else
+          k_ztype_sum<2><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+              r->buf.t, nd, d);
+      }
+      std::vector<double> h(nobs);
+      cudaMemcpyAsync(h.data(), d, nobs * 8, cudaMemcpyDeviceToHost, al.s);
+      const cudaError_t e = cudaStreamSynchronize(al.s);
+      al.put(d);
+      if (e != cudaSuccess)
+        s = fail(QX_ECUDA, std::string("expval failed: ") + cudaGetErrorString(e));
+      else
+        std::memcpy(out, h.data(), nobs * 8);
+    }
+    qx_free_result(r);
+  }
+  qx_free_plan(ip);
+  return s;
+}
+
+const char* qx_kernel_class_name(int k) {
+  return (k >= 0 && k < QX_KC_COUNT) ? kKernelClassNames[k] : "";
+}
+
+void qx_free_result(qx_result* r) {
+  if (!r) return;
+  r->al.put(r->index);
+  r->al.put(r->buf.base);
+  delete r;
+}
+
+}  // extern "C"

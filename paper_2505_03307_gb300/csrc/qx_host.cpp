@@ -1,0 +1,550 @@
+// Host planner of libqx: circuit validation, operator grouping (Sec. III.A),
+// per-qubit Pauli image tables (Algorithm 1), and the device program of fused
+// Clifford passes and fan-out steps.
+//
+// Built with -ffp-contract=off: the composed tables must be bit-reproducible,
+// because their zero pattern decides which strings exist.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "qx_common.h"
+
+namespace qx {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+qx_status fail(qx_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+bool two_qubit(uint32_t g) { return g == QX_CX || g == QX_CZ; }
+
+// Values within 2^-50 of 0 or +-1 are those values: the composition of gates
+// that is exactly Clifford (k pi/2 rotations, T T = S) then stays exact.
+double settle(double v) {
+  const double tol = 0x1p-50;
+  if (std::fabs(v) <= tol) return 0.0;
+  if (std::fabs(std::fabs(v) - 1.0) <= tol) return v > 0 ? 1.0 : -1.0;
+  return v;
+}
+
+// Signed permutations of (X, Y, Z) under P -> g P g^dagger for the Clifford
+// one-qubit gates: image letter index and sign for each source letter.
+struct SignedPerm {
+  int to[3];
+  int sign[3];
+};
+
+bool clifford_image(uint32_t g, SignedPerm* sp) {
+  switch (g) {
+    case QX_H: *sp = {{2, 1, 0}, {1, -1, 1}}; return true;
+    case QX_S: *sp = {{1, 0, 2}, {1, -1, 1}}; return true;
+    case QX_SDG: *sp = {{1, 0, 2}, {-1, 1, 1}}; return true;
+    case QX_X: *sp = {{0, 1, 2}, {1, -1, -1}}; return true;
+    case QX_Y: *sp = {{0, 1, 2}, {-1, 1, -1}}; return true;
+    case QX_Z: *sp = {{0, 1, 2}, {-1, -1, 1}}; return true;
+    case QX_SX: *sp = {{0, 2, 1}, {1, 1, -1}}; return true;
+    case QX_SXDG: *sp = {{0, 2, 1}, {1, -1, 1}}; return true;
+    default: return false;
+  }
+}
+
+// Rotation about Pauli axis a by angle t (cosine c, sine s): the axis letter is
+// fixed, and with (b, d) the two letters that follow a cyclically,
+// b -> c b + s d and d -> c d - s b.
+Table3 axis_rotation(int a, double c, double s) {
+  Table3 t{};
+  const int b = (a + 1) % 3, d = (a + 2) % 3;
+  t.r[a][a] = 1.0;
+  t.r[b][b] = c;
+  t.r[b][d] = s;
+  t.r[d][d] = c;
+  t.r[d][b] = -s;
+  return t;
+}
+
+Table3 gate_image(const qx_instr& g) {
+  Table3 t{};
+  SignedPerm sp;
+  if (clifford_image(g.gate, &sp)) {
+    for (int p = 0; p < 3; ++p) t.r[p][sp.to[p]] = double(sp.sign[p]);
+    return t;
+  }
+  const double h = std::sqrt(0.5);
+  switch (g.gate) {
+    case QX_T: t = axis_rotation(2, h, h); break;
+    case QX_TDG: t = axis_rotation(2, h, -h); break;
+    case QX_RX: t = axis_rotation(0, std::cos(g.theta), std::sin(g.theta)); break;
+    case QX_RY: t = axis_rotation(1, std::cos(g.theta), std::sin(g.theta)); break;
+    case QX_RZ: t = axis_rotation(2, std::cos(g.theta), std::sin(g.theta)); break;
+    default: break;
+  }
+  for (auto& row : t.r)
+    for (double& v : row) v = settle(v);
+  return t;
+}
+
+// Algorithm 1 for one wire: each of X, Y, Z is mapped through the gates of
+// U_{k,j} in list order; the weight vector after the last gate is the row.
+Table3 compose(const std::vector<const qx_instr*>& gates) {
+  Table3 out{};
+  for (int p = 0; p < 3; ++p) {
+    double w[3] = {0.0, 0.0, 0.0};
+    w[p] = 1.0;
+    for (const qx_instr* g : gates) {
+      const Table3 t = gate_image(*g);
+      double nw[3];
+      for (int c = 0; c < 3; ++c) {
+        double acc = w[0] * t.r[0][c];
+        acc += w[1] * t.r[1][c];
+        acc += w[2] * t.r[2][c];
+        nw[c] = acc;
+      }
+      std::memcpy(w, nw, sizeof w);
+    }
+    for (int c = 0; c < 3; ++c) out.r[p][c] = settle(w[c]);
+  }
+  return out;
+}
+
+enum TableKind { kIdentity, kSignedPerm, kFanOut };
+
+TableKind classify(const Table3& t, uint32_t* perm_code) {
+  bool ident = true, perm = true;
+  uint32_t code = 0;
+  for (int p = 0; p < 3; ++p) {
+    int nz = 0, at = -1;
+    for (int c = 0; c < 3; ++c) {
+      if (t.r[p][c] != 0.0) {
+        ++nz;
+        at = c;
+      }
+      if (t.r[p][c] != (p == c ? 1.0 : 0.0)) ident = false;
+    }
+    if (nz != 1 || std::fabs(t.r[p][at]) != 1.0) {
+      perm = false;
+    } else {
+      code |= (uint32_t(at) | (t.r[p][at] < 0 ? 4u : 0u)) << (3 * p);
+    }
+  }
+  if (ident) return kIdentity;
+  if (perm) {
+    *perm_code = code;
+    return kSignedPerm;
+  }
+  return kFanOut;
+}
+
+FanQubit make_fan_qubit(int q, const Table3& t) {
+  FanQubit f{};
+  f.q = q;
+  f.t = t;
+  int colcount[3] = {0, 0, 0};
+  for (int p = 0; p < 3; ++p)
+    for (int c = 0; c < 3; ++c)
+      if (t.r[p][c] != 0.0) colcount[c]++;
+  for (int p = 0; p < 3; ++p) {
+    f.nnz[p] = 0;
+    for (int c = 0; c < 3; ++c)
+      if (t.r[p][c] != 0.0) f.col[p][f.nnz[p]++] = uint8_t(c);
+    f.iso[p] = f.nnz[p] == 1 && colcount[f.col[p][0]] == 1;
+  }
+  return f;
+}
+
+// --- Pauli helpers in XZ form: i^e X^x Z^z -----------------------------------
+
+[[maybe_unused]] int popcount_words(const uint64_t* a, int W) {
+  int s = 0;
+  for (int k = 0; k < W; ++k) s += __builtin_popcountll(a[k]);
+  return s;
+}
+
+// (e1, x1, z1) <- (e1, x1, z1) * (e2, x2, z2)
+void xz_mul(int W, uint8_t* e1, uint64_t* x1, uint64_t* z1, uint8_t e2, const uint64_t* x2,
+            const uint64_t* z2) {
+  int anti = 0;
+  for (int k = 0; k < W; ++k) anti += __builtin_popcountll(z1[k] & x2[k]);
+  *e1 = uint8_t((*e1 + e2 + 2 * anti) & 3);
+  for (int k = 0; k < W; ++k) {
+    x1[k] ^= x2[k];
+    z1[k] ^= z2[k];
+  }
+}
+
+// Column-wise tableau: for each qubit column, the x and z bits of the 2n image
+// rows (rows q < n: image of X_q; rows n + q: image of Z_q) plus a sign row.
+struct ColumnTableau {
+  int n, RW;
+  std::vector<uint64_t> X, Z, S;  // X[q * RW + k]
+  explicit ColumnTableau(int n_) : n(n_), RW((2 * n_ + 63) / 64) {
+    X.assign(size_t(n) * RW, 0);
+    Z.assign(size_t(n) * RW, 0);
+    S.assign(RW, 0);
+    for (int q = 0; q < n; ++q) {
+      X[size_t(q) * RW + q / 64] |= 1ull << (q % 64);
+      Z[size_t(q) * RW + (n + q) / 64] |= 1ull << ((n + q) % 64);
+    }
+  }
+  uint64_t* xc(int q) { return &X[size_t(q) * RW]; }
+  uint64_t* zc(int q) { return &Z[size_t(q) * RW]; }
+
+  void apply(uint32_t op) {
+    const uint32_t kind = op & 3, a = (op >> 2) & 127, b = (op >> 9) & 127, perm = op >> 16;
+    if (kind == kOpCX) {
+      uint64_t *xa = xc(a), *za = zc(a), *xb = xc(b), *zb = zc(b);
+      for (int k = 0; k < RW; ++k) {
+        S[k] ^= xa[k] & zb[k] & ~(xb[k] ^ za[k]);
+        xb[k] ^= xa[k];
+        za[k] ^= zb[k];
+      }
+    } else if (kind == kOpCZ) {
+      uint64_t *xa = xc(a), *za = zc(a), *xb = xc(b), *zb = zc(b);
+      for (int k = 0; k < RW; ++k) {
+        S[k] ^= xa[k] & xb[k] & (za[k] ^ zb[k]);
+        zb[k] ^= xa[k];
+        za[k] ^= xb[k];
+      }
+    } else {
+      uint64_t *xq = xc(a), *zq = zc(a);
+      for (int k = 0; k < RW; ++k) {
+        const uint64_t m[3] = {xq[k] & ~zq[k], xq[k] & zq[k], ~xq[k] & zq[k]};
+        uint64_t nx = 0, nz = 0;
+        for (int p = 0; p < 3; ++p) {
+          const uint32_t f = (perm >> (3 * p)) & 7, to = f & 3;
+          if (to <= 1) nx |= m[p];
+          if (to >= 1) nz |= m[p];
+          if (f & 4) S[k] ^= m[p];
+        }
+        xq[k] = nx;
+        zq[k] = nz;
+      }
+    }
+  }
+};
+
+void build_pass_tables(CliffPass& pc, int n, int W) {
+  ColumnTableau tab(n);
+  for (uint32_t op : pc.ops) tab.apply(op);
+  pc.img_x.assign(size_t(2 * n) * W, 0);
+  pc.img_z.assign(size_t(2 * n) * W, 0);
+  pc.img_e.assign(2 * n, 0);
+  bool ident = true;
+  for (int r = 0; r < 2 * n; ++r) {
+    uint64_t* xr = &pc.img_x[size_t(r) * W];
+    uint64_t* zr = &pc.img_z[size_t(r) * W];
+    for (int q = 0; q < n; ++q) {
+      const uint64_t bit = 1ull << (r % 64);
+      if (tab.X[size_t(q) * tab.RW + r / 64] & bit) xr[q / 64] |= 1ull << (q % 64);
+      if (tab.Z[size_t(q) * tab.RW + r / 64] & bit) zr[q / 64] |= 1ull << (q % 64);
+    }
+    // Hermitian image (-1)^s H(x, z) = (-1)^s i^{|x & z|} X^x Z^z in XZ form
+    const int s = int((tab.S[r / 64] >> (r % 64)) & 1);
+    int xz = 0;
+    for (int k = 0; k < W; ++k) xz += __builtin_popcountll(xr[k] & zr[k]);
+    pc.img_e[r] = uint8_t((2 * s + xz) & 3);
+    // identity check: row q is X_q, row n + q is Z_q, no sign
+    const int q = r < n ? r : r - n;
+    for (int k = 0; k < W; ++k) {
+      const uint64_t want = (k == q / 64) ? (1ull << (q % 64)) : 0;
+      if (xr[k] != (r < n ? want : 0) || zr[k] != (r < n ? 0 : want)) ident = false;
+    }
+    if (s) ident = false;
+  }
+  pc.identity = ident;
+  pc.chunk_bits = (W == 1) ? 4 : 3;
+  pc.chunks = (n + pc.chunk_bits - 1) / pc.chunk_bits;
+  pc.use_table = !ident && pc.ops.size() > size_t(pc.chunks);
+  if (!pc.use_table) return;
+  const int cb = pc.chunk_bits, E = 1 << (2 * cb);
+  pc.tab_xz.assign(size_t(pc.chunks) * E * 2 * W, 0);
+  pc.tab_e.assign(size_t(pc.chunks) * E, 0);
+  for (int c = 0; c < pc.chunks; ++c) {
+    for (int idx = 1; idx < E; ++idx) {
+      // last factor in the order X (ascending qubit) then Z (ascending qubit)
+      const int xb = idx & ((1 << cb) - 1), zb = idx >> cb;
+      int bit, row;
+      if (zb) {
+        bit = 31 - __builtin_clz(unsigned(zb));
+        row = n + c * cb + bit;
+      } else {
+        bit = 31 - __builtin_clz(unsigned(xb));
+        row = c * cb + bit;
+      }
+      const int prev = zb ? (idx & ~(1 << (cb + bit))) : (idx & ~(1 << bit));
+      const int q = c * cb + bit;
+      uint64_t* dst = &pc.tab_xz[(size_t(c) * E + idx) * 2 * W];
+      const uint64_t* src = &pc.tab_xz[(size_t(c) * E + prev) * 2 * W];
+      uint8_t e = pc.tab_e[size_t(c) * E + prev];
+      std::memcpy(dst, src, sizeof(uint64_t) * 2 * W);
+      if (q < n) xz_mul(W, &e, dst, dst + W, pc.img_e[row], &pc.img_x[size_t(row) * W],
+                        &pc.img_z[size_t(row) * W]);
+      pc.tab_e[size_t(c) * E + idx] = e;
+    }
+  }
+}
+
+}  // namespace
+
+void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z, int* sign) {
+  if (pc.identity) return;
+  if (pc.use_table) {
+    const int cb = pc.chunk_bits, E = 1 << (2 * cb);
+    int xzc = 0;
+    for (int k = 0; k < W; ++k) xzc += __builtin_popcountll(x[k] & z[k]);
+    uint8_t e = uint8_t(xzc & 3);
+    uint64_t ax[kMaxWords] = {0, 0}, az[kMaxWords] = {0, 0};
+    for (int c = 0; c < pc.chunks; ++c) {
+      const int lo = c * cb, k = lo / 64, off = lo % 64;
+      const uint32_t m = (1u << cb) - 1;
+      uint64_t xs = x[k] >> off, zs = z[k] >> off;
+      if (off + cb > 64 && k + 1 < W) {  // chunk straddles two words
+        xs |= x[k + 1] << (64 - off);
+        zs |= z[k + 1] << (64 - off);
+      }
+      const uint32_t xb = uint32_t(xs) & m, zb = uint32_t(zs) & m;
+      const int idx = int(xb | (zb << cb));
+      if (!idx) continue;
+      const uint64_t* t = &pc.tab_xz[(size_t(c) * E + idx) * 2 * W];
+      xz_mul(W, &e, ax, az, pc.tab_e[size_t(c) * E + idx], t, t + W);
+    }
+    int c2 = 0;
+    for (int k = 0; k < W; ++k) c2 += __builtin_popcountll(ax[k] & az[k]);
+    const int d = (e - c2) & 3;
+    if (d == 2) *sign = -*sign;
+    for (int k = 0; k < W; ++k) {
+      x[k] = ax[k];
+      z[k] = az[k];
+    }
+    return;
+  }
+  auto bit = [](const uint64_t* v, int q) { return int((v[q / 64] >> (q % 64)) & 1); };
+  auto put = [](uint64_t* v, int q, int b) {
+    v[q / 64] = (v[q / 64] & ~(1ull << (q % 64))) | (uint64_t(b) << (q % 64));
+  };
+  for (uint32_t op : pc.ops) {
+    const uint32_t kind = op & 3;
+    const int a = (op >> 2) & 127, b = (op >> 9) & 127;
+    const uint32_t perm = op >> 16;
+    if (kind == kOpCX) {
+      const int xa = bit(x, a), za = bit(z, a), xb = bit(x, b), zb = bit(z, b);
+      if (xa & zb & (1 ^ xb ^ za)) *sign = -*sign;
+      put(x, b, xb ^ xa);
+      put(z, a, za ^ zb);
+    } else if (kind == kOpCZ) {
+      const int xa = bit(x, a), za = bit(z, a), xb = bit(x, b), zb = bit(z, b);
+      if (xa & xb & (za ^ zb)) *sign = -*sign;
+      put(z, b, zb ^ xa);
+      put(z, a, za ^ xb);
+    } else {
+      const int xq = bit(x, a), zq = bit(z, a);
+      if (!xq && !zq) continue;
+      const int p = xq ? (zq ? 1 : 0) : 2;
+      const uint32_t f = (perm >> (3 * p)) & 7, to = f & 3;
+      put(x, a, to <= 1);
+      put(z, a, to >= 1);
+      if (f & 4) *sign = -*sign;
+    }
+  }
+  (void)n;
+}
+
+qx_status build_plan(const qx_circuit* c, qx_plan** out) {
+  auto* p = new (std::nothrow) qx_plan;
+  if (!p) return fail(QX_ENOMEM, "host allocation failed");
+  const int n = c->n;
+  p->n = n;
+  p->W = (n + 63) / 64;
+  p->ins = c->ins;
+  // divide_instruction: maximal runs of one-qubit / two-qubit instructions.
+  std::vector<std::pair<size_t, size_t>> runs;  // [begin, end) per operator
+  for (size_t i = 0; i < c->ins.size(); ++i) {
+    const bool one = !two_qubit(c->ins[i].gate);
+    if (runs.empty() || (p->op_kind.back() == 1) != one) {
+      runs.push_back({i, i});
+      p->op_kind.push_back(one ? 1 : 0);
+    }
+    runs.back().second = i + 1;
+  }
+  p->luts.resize(runs.size());
+  CliffPass cur;
+  uint64_t ops_since_fan = 0;
+  for (size_t k = 0; k < runs.size(); ++k) {
+    const auto [b, e] = runs[k];
+    if (p->op_kind[k] == 0) {
+      ++p->Kp;
+      for (size_t i = b; i < e; ++i) {
+        const qx_instr& g = c->ins[i];
+        cur.ops.push_back(encode_op(g.gate == QX_CX ? kOpCX : kOpCZ, g.q0, g.q1, 0));
+      }
+      ++ops_since_fan;
+      continue;
+    }
+    ++p->K;
+    std::vector<std::vector<const qx_instr*>> per(n);
+    for (size_t i = b; i < e; ++i) per[c->ins[i].q0].push_back(&c->ins[i]);
+    std::vector<Table3>& lut = p->luts[k];
+    lut.resize(n);
+    FanStep fs;
+    fs.op_index = k;
+    for (int j = 0; j < n; ++j) {
+      lut[j] = compose(per[j]);
+      uint32_t code = 0;
+      const TableKind kind = classify(lut[j], &code);
+      if (kind == kSignedPerm)
+        cur.ops.push_back(encode_op(kOpPerm, j, -1, code));
+      else if (kind == kFanOut)
+        fs.qs.push_back(make_fan_qubit(j, lut[j]));
+    }
+    if (fs.qs.empty()) {
+      ++ops_since_fan;
+      continue;
+    }
+    // The Clifford wires of this U_k act on other qubits than its fan-out
+    // wires, so they commute and run in the pass before the expansion.
+    p->passes.push_back(std::move(cur));
+    cur = CliffPass();
+    p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
+    p->fans.push_back(std::move(fs));
+    p->program.push_back({kStepFan, int(p->fans.size() - 1), ops_since_fan});
+    ops_since_fan = 0;
+  }
+  p->passes.push_back(std::move(cur));
+  p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
+  p->ops_after_last_fan = ops_since_fan;
+  for (auto& pc : p->passes) build_pass_tables(pc, n, p->W);
+  *out = p;
+  return QX_OK;
+}
+
+qx_status inverse_circuit(const qx_circuit* c, qx_circuit** out) {
+  auto* r = new (std::nothrow) qx_circuit;
+  if (!r) return fail(QX_ENOMEM, "host allocation failed");
+  r->n = c->n;
+  r->ins.assign(c->ins.rbegin(), c->ins.rend());
+  for (auto& g : r->ins) {
+    switch (g.gate) {
+      case QX_S: g.gate = QX_SDG; break;
+      case QX_SDG: g.gate = QX_S; break;
+      case QX_SX: g.gate = QX_SXDG; break;
+      case QX_SXDG: g.gate = QX_SX; break;
+      case QX_T: g.gate = QX_TDG; break;
+      case QX_TDG: g.gate = QX_T; break;
+      case QX_RX:
+      case QX_RY:
+      case QX_RZ: g.theta = -g.theta; break;
+      default: break;
+    }
+  }
+  *out = r;
+  return QX_OK;
+}
+
+}  // namespace qx
+
+using namespace qx;
+
+extern "C" {
+
+void qx_default_opts(qx_prop_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = 64;
+  o->eps = 0.0;
+  o->gen_begin = 0;
+  o->gen_end = 0;
+  o->timeout_ms = 2000;
+}
+
+qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out) {
+  clear_error();
+  if (!out) return fail(QX_EINVAL, "out is NULL");
+  if (n < 1) return fail(QX_EINVAL, "n must be >= 1");
+  if (n > kMaxQubits) return fail(QX_EUNSUPPORTED, "n > 128 is not supported");
+  if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
+  for (size_t i = 0; i < m; ++i) {
+    const qx_instr& g = ins[i];
+    if (g.gate > QX_CZ) return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad gate");
+    if (g.q0 < 0 || g.q0 >= n)
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": wire out of range");
+    if (two_qubit(g.gate) && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0))
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad second wire");
+    if (!std::isfinite(g.theta))
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": theta not finite");
+  }
+  auto* c = new (std::nothrow) qx_circuit;
+  if (!c) return fail(QX_ENOMEM, "host allocation failed");
+  c->n = n;
+  c->ins.assign(ins, ins + m);
+  *out = c;
+  return QX_OK;
+}
+
+qx_status qx_group_ops(const qx_circuit* c, qx_plan** out) {
+  clear_error();
+  if (!c || !out) return fail(QX_EINVAL, "NULL argument");
+  return build_plan(c, out);
+}
+
+qx_status qx_plan_info(const qx_plan* p, size_t* K, size_t* Kp) {
+  clear_error();
+  if (!p) return fail(QX_EINVAL, "plan is NULL");
+  if (K) *K = p->K;
+  if (Kp) *Kp = p->Kp;
+  return QX_OK;
+}
+
+qx_status qx_plan_op(const qx_plan* p, size_t op, int* kind) {
+  clear_error();
+  if (!p || !kind) return fail(QX_EINVAL, "NULL argument");
+  if (op >= p->op_kind.size()) return fail(QX_EINVAL, "operator index out of range");
+  *kind = p->op_kind[op];
+  return QX_OK;
+}
+
+qx_status qx_plan_lut(const qx_plan* p, size_t op, double* out) {
+  clear_error();
+  if (!p || !out) return fail(QX_EINVAL, "NULL argument");
+  if (op >= p->op_kind.size() || p->op_kind[op] != 1)
+    return fail(QX_EINVAL, "operator is not a one-qubit operator");
+  for (int j = 0; j < p->n; ++j)
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = p->luts[op][j].r[a][c];
+  return QX_OK;
+}
+
+qx_status qx_plan_clifford_passes(const qx_plan* p, size_t* count) {
+  clear_error();
+  if (!p || !count) return fail(QX_EINVAL, "NULL argument");
+  *count = p->passes.size();
+  return QX_OK;
+}
+
+qx_status qx_plan_clifford_apply(const qx_plan* p, size_t pass, uint64_t* x, uint64_t* z,
+                                 int* sign) {
+  clear_error();
+  if (!p || !x || !z || !sign) return fail(QX_EINVAL, "NULL argument");
+  if (pass >= p->passes.size()) return fail(QX_EINVAL, "pass index out of range");
+  host_apply_pass(p->passes[pass], p->n, p->W, x, z, sign);
+  return QX_OK;
+}
+
+void qx_free_circuit(qx_circuit* c) { delete c; }
+
+void qx_free_plan(qx_plan* p) {
+  if (!p) return;
+  free_plan_device(p);
+  delete p;
+}
+
+const char* qx_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,981 @@
+// Device kernels of libqx (sm_103a).
+//
+// Terms live in HBM as structure-of-arrays: x and z bit planes (W words per
+// string, plane k at x + k * cap), an FP64 weight and a 32-bit generator id per
+// term.  Every kernel is a grid-stride loop whose bound is read from device
+// memory, so a launch does not need the host to know the current count.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace qx {
+namespace dev {
+
+constexpr unsigned kErrProbe = 1u;    // a hash table ran out of probes
+constexpr unsigned kErrSpin = 2u;     // a bounded wait gave up
+constexpr unsigned kErrCap = 4u;      // an output buffer was too small
+
+struct Terms {
+  uint64_t* x;
+  uint64_t* z;
+  double* w;
+  uint32_t* g;
+  size_t cap;
+};
+
+// A fan-out qubit as the kernels see it.
+struct FanQ {
+  double t[3][3];
+  int q;
+  uint8_t nnz[3];
+  uint8_t col[3][3];
+  uint8_t iso[3];
+  uint8_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t key_hash(uint32_t g, const uint64_t* kx, const uint64_t* kz) {
+  uint64_t h = fmix64(0x9e3779b97f4a7c15ull * (uint64_t(g) + 1));
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    h = fmix64(h ^ kx[k]);
+    h = fmix64(h + 0x632be59bd9b4e019ull + kz[k]);
+  }
+  return h;
+}
+
+// Pauli letter of qubit q: 0 = I, 1 = X, 2 = Y, 3 = Z (as (x, z) bits).
+template <int W>
+__device__ __forceinline__ int letter_at(const uint64_t* x, const uint64_t* z, int q) {
+  const int k = q >> 6, b = q & 63;
+  const int xb = int((x[k] >> b) & 1), zb = int((z[k] >> b) & 1);
+  return xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+}
+
+// Sets qubit q to table letter c (0 = X, 1 = Y, 2 = Z).
+template <int W>
+__device__ __forceinline__ void set_letter(uint64_t* x, uint64_t* z, int q, int c) {
+  const int k = q >> 6;
+  const uint64_t m = 1ull << (q & 63);
+  x[k] = (c <= 1) ? (x[k] | m) : (x[k] & ~m);
+  z[k] = (c >= 1) ? (z[k] | m) : (z[k] & ~m);
+}
+
+template <int W>
+__device__ __forceinline__ void load_term(const Terms& t, size_t i, uint64_t* x, uint64_t* z) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    x[k] = t.x[k * t.cap + i];
+    z[k] = t.z[k * t.cap + i];
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void store_term(const Terms& t, size_t i, const uint64_t* x,
+                                           const uint64_t* z, double w, uint32_t g) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    t.x[k * t.cap + i] = x[k];
+    t.z[k * t.cap + i] = z[k];
+  }
+  t.w[i] = w;
+  t.g[i] = g;
+}
+
+// Block-wide exclusive scan of one unsigned value per thread; returns the
+// thread's offset and writes the block total to *total (all threads).
+template <int THREADS>
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total,
+                                                    unsigned* smem /* THREADS/32 + 1 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) smem[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    constexpr int NW = THREADS / 32;
+    unsigned s = lane < NW ? smem[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= d) s += o;
+    }
+    if (lane < NW) smem[lane] = s;  // inclusive warp prefix
+    if (lane == NW - 1) smem[NW] = s;
+  }
+  __syncthreads();
+  const unsigned warp_base = wid ? smem[wid - 1] : 0;
+  *total = smem[THREADS / 32];
+  const unsigned r = warp_base + inc - v;
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// A3: create_Z_j
+
+template <int W>
+__global__ void k_init_z(Terms t, int g0, int G, unsigned long long* n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < G) {
+    uint64_t x[W], z[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[k] = 0;
+      z[k] = 0;
+    }
+    const int j = g0 + i;
+    z[j >> 6] = 1ull << (j & 63);
+    store_term<W>(t, i, x, z, 1.0, uint32_t(i));
+  }
+  if (i == 0) *n_out = (unsigned long long)G;
+}
+
+// ---------------------------------------------------------------------------
+// A4: fused Clifford pass, in place (bijection on strings: no merge).
+//
+// Gate-list form: the ops of the pass are applied one after another with the
+// CHP bit rules.  Table form: the string is split into chunks of CB qubits;
+// the XZ-form image of each chunk's X^a Z^b is read from a shared-memory table
+// and the images are multiplied, tracking the phase with popcounts.
+
+template <int W>
+__device__ __forceinline__ void apply_ops(const uint32_t* ops, int nops, uint64_t* x, uint64_t* z,
+                                          int* neg) {
+  for (int i = 0; i < nops; ++i) {
+    const uint32_t op = ops[i];
+    const uint32_t kind = op & 3;
+    const int a = (op >> 2) & 127, b = (op >> 9) & 127;
+    const int ka = a >> 6, sa = a & 63, kb = b >> 6, sb = b & 63;
+    if (kind == 1u) {  // CX(a -> b)
+      const uint64_t xa = (x[ka] >> sa) & 1, za = (z[ka] >> sa) & 1;
+      const uint64_t xb = (x[kb] >> sb) & 1, zb = (z[kb] >> sb) & 1;
+      *neg ^= int(xa & zb & (1 ^ xb ^ za));
+      x[kb] ^= xa << sb;
+      z[ka] ^= zb << sa;
+    } else if (kind == 2u) {  // CZ(a, b)
+      const uint64_t xa = (x[ka] >> sa) & 1, za = (z[ka] >> sa) & 1;
+      const uint64_t xb = (x[kb] >> sb) & 1, zb = (z[kb] >> sb) & 1;
+      *neg ^= int(xa & xb & (za ^ zb));
+      z[kb] ^= xa << sb;
+      z[ka] ^= xb << sa;
+    } else {  // signed permutation of (X, Y, Z) on qubit a
+      const uint64_t xa = (x[ka] >> sa) & 1, za = (z[ka] >> sa) & 1;
+      if (xa | za) {
+        const int p = xa ? (za ? 1 : 0) : 2;
+        const uint32_t f = (op >> (16 + 3 * p)) & 7, to = f & 3;
+        const uint64_t m = 1ull << sa;
+        x[ka] = (to <= 1) ? (x[ka] | m) : (x[ka] & ~m);
+        z[ka] = (to >= 1) ? (z[ka] | m) : (z[ka] & ~m);
+        *neg ^= int(f >> 2);
+      }
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_clifford_ops(Terms t, const unsigned long long* n_in,
+                                                      const uint32_t* ops, int nops) {
+  extern __shared__ uint32_t s_ops[];
+  for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops[i];
+  __syncthreads();
+  const size_t N = *n_in;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(t, i, x, z);
+    int neg = 0;
+    apply_ops<W>(s_ops, nops, x, z, &neg);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      t.x[k * t.cap + i] = x[k];
+      t.z[k * t.cap + i] = z[k];
+    }
+    if (neg) t.w[i] = -t.w[i];
+  }
+}
+
+template <int W, int CB>
+__global__ void __launch_bounds__(256) k_clifford_table(Terms t, const unsigned long long* n_in,
+                                                        const uint64_t* tab_xz,
+                                                        const uint8_t* tab_e, int chunks) {
+  constexpr int E = 1 << (2 * CB);
+  extern __shared__ uint64_t s_tab[];
+  uint8_t* s_e = reinterpret_cast<uint8_t*>(s_tab + size_t(chunks) * E * 2 * W);
+  {
+    const int nw = chunks * E * 2 * W;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) s_tab[i] = tab_xz[i];
+    const int ne = chunks * E;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) s_e[i] = tab_e[i];
+  }
+  __syncthreads();
+  const size_t N = *n_in;
+  constexpr uint32_t M = (1u << CB) - 1;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(t, i, x, z);
+    int e = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
+    uint64_t ax[W], az[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      ax[k] = 0;
+      az[k] = 0;
+    }
+    for (int c = 0; c < chunks; ++c) {
+      const int lo = c * CB, k = lo >> 6, off = lo & 63;
+      // chunks never straddle a word: 64 is a multiple of CB = 4, and for
+      // CB = 3 the straddling chunk is assembled from both words
+      uint32_t xb, zb;
+      if (CB == 4 || off + CB <= 64) {
+        xb = uint32_t(x[k] >> off) & M;
+        zb = uint32_t(z[k] >> off) & M;
+      } else {
+        xb = uint32_t((x[k] >> off) | (k + 1 < W ? (x[k + 1] << (64 - off)) : 0)) & M;
+        zb = uint32_t((z[k] >> off) | (k + 1 < W ? (z[k + 1] << (64 - off)) : 0)) & M;
+      }
+      const uint32_t idx = xb | (zb << CB);
+      if (!idx) continue;
+      const uint64_t* ent = s_tab + (size_t(c) * E + idx) * 2 * W;
+      int anti = 0;
+#pragma unroll
+      for (int kk = 0; kk < W; ++kk) anti += __popcll(az[kk] & ent[kk]);
+      e += int(s_e[c * E + idx]) + 2 * anti;
+#pragma unroll
+      for (int kk = 0; kk < W; ++kk) {
+        ax[kk] ^= ent[kk];
+        az[kk] ^= ent[W + kk];
+      }
+    }
+    int c2 = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) c2 += __popcll(ax[k] & az[k]);
+    const bool neg = ((e - c2) & 3) == 2;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      t.x[k * t.cap + i] = ax[k];
+      t.z[k * t.cap + i] = az[k];
+    }
+    if (neg) t.w[i] = -t.w[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A5/A6 preparation: which fan-out qubits need index accumulation.
+//
+// For every generator, OR over its terms of the qubits carrying X (resp. Y, Z)
+// where that row of the qubit's table is not isolated.  A qubit whose
+// non-isolated letters are all the same in a generator cannot make two of that
+// generator's strings collide, so it is expanded without a merge.
+
+template <int W>
+__global__ void k_fan_mask(Terms t, const unsigned long long* n_in, const uint64_t* nisoX,
+                           const uint64_t* nisoY, const uint64_t* nisoZ,
+                           unsigned long long* gmask /* [G][3][W] */) {
+  const size_t N = *n_in;
+  const unsigned lane = threadIdx.x & 31;
+  for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
+       base += size_t(gridDim.x) * blockDim.x) {
+    const size_t i = base + threadIdx.x;
+    const bool valid = i < N;
+    uint32_t g = valid ? t.g[i] : 0xffffffffu;
+    uint64_t m[3][W];
+    if (valid) {
+      uint64_t x[W], z[W];
+      load_term<W>(t, i, x, z);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        m[0][k] = x[k] & ~z[k] & nisoX[k];
+        m[1][k] = x[k] & z[k] & nisoY[k];
+        m[2][k] = ~x[k] & z[k] & nisoZ[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) m[0][k] = m[1][k] = m[2][k] = 0;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, g);
+    const unsigned leader = __ffs(peers) - 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        uint64_t v = m[a][k];
+        // OR within the peer group through shuffles over its members
+        unsigned rest = peers;
+        uint64_t acc = 0;
+        while (rest) {
+          const int src = __ffs(rest) - 1;
+          rest &= rest - 1;
+          acc |= __shfl_sync(peers, v, src);
+        }
+        m[a][k] = acc;
+      }
+    if (valid && lane == leader) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          if (m[a][k]) atomicOr(&gmask[(size_t(g) * 3 + a) * W + k], m[a][k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A6: index-based accumulation for one fan-out qubit q.
+//
+// Strings of one generator that differ only at q form a group of at most
+// three members (X, Y, Z at q, non-isolated rows).  The group key is the
+// string with q cleared.  Insertion: the first member to claim the group's
+// slot becomes its leader and publishes its term index; later members find it
+// (bounded wait on the publish flag), compare the full key and store their
+// weight in the leader's payload.  Emission: each leader writes one child per
+// letter c reached by a member, with weight sum_p t[p][c] * v[p] in the fixed
+// order p = X, Y, Z, so results do not depend on arrival order.
+
+struct Slot {
+  unsigned long long tag;  // epoch << 48 | 48-bit fingerprint; 0 = never used
+  unsigned leader;
+  unsigned ready;          // epoch of the last publish
+};
+
+template <int W>
+__global__ void __launch_bounds__(256) k_merge_insert(
+    Terms t, const unsigned long long* n_in, int q, FanQ fq, const uint64_t* mixed /* [G][W] */,
+    Slot* table, unsigned long long tcap, unsigned epoch, uint32_t* lead, double* pv /* [3][cap] */,
+    uint32_t* pmask, size_t pcap, unsigned spin_limit, unsigned* err) {
+  const size_t N = *n_in;
+  const int qk = q >> 6;
+  const uint64_t qm = 1ull << (q & 63);
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(t, i, x, z);
+    const int L = letter_at<W>(x, z, q);
+    if (L == 0) continue;
+    const int p = L - 1;
+    if (fq.iso[p]) continue;
+    const uint32_t g = t.g[i];
+    if (!(mixed[size_t(g) * W + qk] & qm)) continue;
+    const double w = t.w[i];
+    x[qk] &= ~qm;
+    z[qk] &= ~qm;
+    const uint64_t h = key_hash<W>(g, x, z);
+    const unsigned long long tag =
+        (static_cast<unsigned long long>(epoch) << 48) | (h & 0xffffffffffffull);
+    unsigned long long pos = __umul64hi(h, tcap);
+    bool done = false;
+    for (unsigned long long probe = 0; probe < tcap && !done; ++probe) {
+      Slot* s = &table[pos];
+      unsigned long long cur = ld_relaxed64(&s->tag);
+      while (true) {
+        if ((cur >> 48) != epoch) {
+          const unsigned long long old = atomicCAS(&s->tag, cur, tag);
+          if (old == cur) {  // claimed: this term leads the group
+            s->leader = unsigned(i);
+            lead[i] = unsigned(i);
+            pv[size_t(p) * pcap + i] = w;
+            pmask[i] = 1u << p;
+            st_release(&s->ready, epoch);
+            done = true;
+            break;
+          }
+          cur = old;
+          continue;
+        }
+        if (cur == tag) {
+          unsigned it = 0;
+          while (ld_acquire(&s->ready) != epoch) {
+            if (++it > spin_limit) {
+              atomicOr(err, kErrSpin);
+              return;
+            }
+            __nanosleep(32);
+          }
+          const unsigned ld = ld_relaxed(&s->leader);
+          bool same = t.g[ld] == g;
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            uint64_t lx = t.x[k * t.cap + ld], lz = t.z[k * t.cap + ld];
+            if (k == qk) {
+              lx &= ~qm;
+              lz &= ~qm;
+            }
+            same = same && lx == x[k] && lz == z[k];
+          }
+          if (same) {
+            lead[i] = ld;
+            pv[size_t(p) * pcap + ld] = w;
+            atomicOr(&pmask[ld], 1u << p);
+            done = true;
+          }
+        }
+        break;  // occupied by another key (or matched)
+      }
+      if (++pos == tcap) pos = 0;
+    }
+    if (!done) atomicOr(err, kErrProbe);
+  }
+}
+
+// Children of one input term at qubit q: letter (-1 = keep the input's) and
+// weight of each, at most three.  Modes per term:
+//   direct: I at q, an isolated row, or a generator where q needs no merge:
+//           one child per non-zero entry of the row;
+//   leader: one child per letter reached by any member of the group, weight
+//           sum_p t[p][c] v[p] over the members in the order X, Y, Z;
+//   member: nothing (its weight went to the leader).
+// Children below eps are dropped here and their squared weight is added to
+// pruned[g]; the returned count is what the caller writes.
+template <int W>
+__device__ __forceinline__ unsigned merge_children(const uint64_t* x, const uint64_t* z, double w,
+                                                   uint32_t g, size_t i, int q, const FanQ& fq,
+                                                   const uint64_t* mixed, const uint32_t* lead,
+                                                   const double* pv, const uint32_t* pmask,
+                                                   size_t pcap, double eps, double* pruned,
+                                                   int* cl, double* cw) {
+  const int L = letter_at<W>(x, z, q);
+  unsigned n = 0;
+  auto keep = [&](int c, double v) {
+    if (eps > 0.0 && fabs(v) < eps) {
+      atomicAdd(&pruned[g], v * v);
+      return;
+    }
+    cl[n] = c;
+    cw[n] = v;
+    ++n;
+  };
+  if (L == 0) {
+    keep(-1, w);
+    return n;
+  }
+  const int p = L - 1;
+  const bool merged = !fq.iso[p] && (mixed[size_t(g) * W + (q >> 6)] & (1ull << (q & 63)));
+  if (!merged) {
+    for (int j = 0; j < fq.nnz[p]; ++j) {
+      const int c = fq.col[p][j];
+      keep(c, w * fq.t[p][c]);
+    }
+    return n;
+  }
+  if (lead[i] != unsigned(i)) return 0;
+  const uint32_t msk = pmask[i];
+  double v[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[a] = (msk >> a) & 1 ? pv[size_t(a) * pcap + i] : 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    bool reached = false;
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (((msk >> a) & 1) && fq.t[a][c] != 0.0) {
+        acc = reached ? acc + fq.t[a][c] * v[a] : fq.t[a][c] * v[a];
+        reached = true;
+      }
+    }
+    if (reached) keep(c, acc);
+  }
+  return n;
+}
+
+template <int W, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_merge_emit(
+    Terms in, const unsigned long long* n_in, int q, FanQ fq, const uint64_t* mixed,
+    const uint32_t* lead, const double* pv, const uint32_t* pmask, size_t pcap, double eps,
+    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+  __shared__ unsigned s_scan[THREADS / 32 + 1];
+  __shared__ unsigned long long s_base;
+  const size_t N = *n_in;
+  for (size_t tile = size_t(blockIdx.x) * THREADS; tile < N; tile += size_t(gridDim.x) * THREADS) {
+    const size_t i = tile + threadIdx.x;
+    uint64_t x[W], z[W];
+    double w = 0.0;
+    uint32_t g = 0;
+    int cl[3];
+    double cw[3];
+    unsigned c = 0;
+    if (i < N) {
+      load_term<W>(in, i, x, z);
+      w = in.w[i];
+      g = in.g[i];
+      c = merge_children<W>(x, z, w, g, i, q, fq, mixed, lead, pv, pmask, pcap, eps, pruned, cl,
+                            cw);
+    }
+    unsigned total;
+    const unsigned off = block_excl_scan<THREADS>(c, &total, s_scan);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(n_out, (unsigned long long)total) : 0;
+    __syncthreads();
+    const size_t base = size_t(s_base) + off;
+    if (c) {
+      if (base + c > out.cap) {
+        atomicOr(err, kErrCap);
+      } else {
+        for (unsigned j = 0; j < c; ++j) {
+          uint64_t cx[W], cz[W];
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            cx[k] = x[k];
+            cz[k] = z[k];
+          }
+          if (cl[j] >= 0) set_letter<W>(cx, cz, q, cl[j]);
+          store_term<W>(out, base + j, cx, cz, cw[j], g);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A5: one-shot expansion over the fan-out qubits that need no merge in any
+// generator (flatten, Eq. 3): each parent has prod_q nnz(row) children, laid
+// out contiguously after an exclusive scan of the counts.
+
+template <int W>
+__device__ __forceinline__ unsigned long long child_count(const uint64_t* x, const uint64_t* z,
+                                                          const FanQ* fq, int nq) {
+  unsigned long long c = 1;
+  for (int j = 0; j < nq; ++j) {
+    const int L = letter_at<W>(x, z, fq[j].q);
+    if (L) {
+      c *= fq[j].nnz[L - 1];
+      if (c > (1ull << 40)) c = 1ull << 40;  // saturate: far beyond any budget
+    }
+  }
+  return c;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_expand_count(Terms t, const unsigned long long* n_in,
+                                                      const FanQ* fq_g, int nq,
+                                                      unsigned long long* cnt_out) {
+  extern __shared__ FanQ s_fq[];
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  __syncthreads();
+  const size_t N = *n_in;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(t, i, x, z);
+    cnt_out[i] = child_count<W>(x, z, s_fq, nq);
+  }
+}
+
+// Exclusive scan, three phases: per-tile scan, scan of tile sums, add.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(unsigned long long* a,
+                                                             const unsigned long long* n_in,
+                                                             unsigned long long* tile_sums) {
+  __shared__ unsigned long long s[kScanThreads / 32 + 1];
+  const size_t N = *n_in;
+  const size_t tile = size_t(blockIdx.x) * kScanTile;
+  if (tile >= N) return;
+  unsigned long long v[kScanItems];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const size_t i = tile + size_t(threadIdx.x) * kScanItems + k;
+    v[k] = i < N ? a[i] : 0;
+    sum += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) s[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    constexpr int NW = kScanThreads / 32;
+    unsigned long long w = lane < NW ? s[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += o;
+    }
+    if (lane < NW) s[lane] = w;
+  }
+  __syncthreads();
+  unsigned long long run = (wid ? s[wid - 1] : 0) + inc - sum;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const size_t i = tile + size_t(threadIdx.x) * kScanItems + k;
+    if (i < N) a[i] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* sums, size_t ntiles,
+                                                    unsigned long long* total) {
+  __shared__ unsigned long long s[33];
+  unsigned long long carry = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (size_t base = 0; base < ntiles; base += blockDim.x) {
+    const size_t i = base + threadIdx.x;
+    const unsigned long long v = i < ntiles ? sums[i] : 0;
+    unsigned long long inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += o;
+    }
+    if (lane == 31) s[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const int NW = blockDim.x / 32;
+      unsigned long long w = lane < NW ? s[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += o;
+      }
+      if (lane < NW) s[lane] = w;
+      if (lane == NW - 1) s[32] = w;
+    }
+    __syncthreads();
+    if (i < ntiles) sums[i] = carry + (wid ? s[wid - 1] : 0) + inc - v;
+    carry += s[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long long* a,
+                                                           const unsigned long long* n_in,
+                                                           const unsigned long long* tile_offs) {
+  const size_t N = *n_in;
+  const size_t tile = size_t(blockIdx.x) * kScanTile;
+  const unsigned long long add = tile_offs[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    const size_t i = tile + k;
+    if (i < N) a[i] += add;
+  }
+}
+
+constexpr int kExpThreads = 256;
+constexpr int kExpItems = 4;
+constexpr int kExpTile = kExpThreads * kExpItems;
+
+// Children [c0, c0 + kExpTile) per block iteration.  The parents of the tile
+// are located once (binary search on the offsets), their offsets staged in
+// shared memory, and each child finds its parent there; the child index within
+// the parent is decoded in mixed radix over the parent's fan-out letters.
+template <int W>
+__global__ void __launch_bounds__(kExpThreads) k_expand_emit(
+    Terms in, const unsigned long long* n_in, const unsigned long long* offs,
+    unsigned long long total, const FanQ* fq_g, int nq, Terms out) {
+  extern __shared__ unsigned char s_raw[];
+  FanQ* s_fq = reinterpret_cast<FanQ*>(s_raw);
+  unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_fq + nq);
+  __shared__ size_t s_p0, s_p1;
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  const size_t N = *n_in;
+  for (unsigned long long c0 = (unsigned long long)blockIdx.x * kExpTile; c0 < total;
+       c0 += (unsigned long long)gridDim.x * kExpTile) {
+    const unsigned long long c1 = min(total, c0 + kExpTile);
+    if (threadIdx.x == 0) {
+      // last parent with offs[p] <= c0, and last parent with offs[p] <= c1 - 1
+      size_t lo = 0, hi = N;
+      while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (offs[mid] <= c0) lo = mid; else hi = mid;
+      }
+      s_p0 = lo;
+      size_t lo2 = lo, hi2 = N;
+      while (hi2 - lo2 > 1) {
+        const size_t mid = (lo2 + hi2) / 2;
+        if (offs[mid] <= c1 - 1) lo2 = mid; else hi2 = mid;
+      }
+      s_p1 = lo2;
+    }
+    __syncthreads();
+    const size_t p0 = s_p0, np = s_p1 - p0 + 1;
+    for (size_t j = threadIdx.x; j < np; j += blockDim.x) s_off[j] = offs[p0 + j];
+    __syncthreads();
+    for (int k = 0; k < kExpItems; ++k) {
+      const unsigned long long c = c0 + (unsigned long long)k * kExpThreads + threadIdx.x;
+      if (c >= c1) break;
+      size_t lo = 0, hi = np;
+      while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (s_off[mid] <= c) lo = mid; else hi = mid;
+      }
+      const size_t p = p0 + lo;
+      unsigned long long r = c - s_off[lo];
+      uint64_t x[W], z[W];
+      load_term<W>(in, p, x, z);
+      double w = in.w[p];
+      const uint32_t g = in.g[p];
+      for (int j = 0; j < nq; ++j) {
+        const FanQ& f = s_fq[j];
+        const int L = letter_at<W>(x, z, f.q);
+        if (!L) continue;
+        const int a = L - 1;
+        const int nn = f.nnz[a];
+        int d = 0;
+        if (nn == 2) {
+          d = int(r & 1);
+          r >>= 1;
+        } else if (nn == 3) {
+          d = int(r % 3);
+          r /= 3;
+        }
+        const int col = f.col[a][d];
+        w *= f.t[a][col];
+        set_letter<W>(x, z, f.q, col);
+      }
+      store_term<W>(out, size_t(c), x, z, w, g);
+    }
+    __syncthreads();
+  }
+}
+
+// Compaction after pruning inside k_expand_emit: pruned children leave holes;
+// when eps > 0 the expansion writes into a staging buffer and this kernel
+// keeps the terms whose weight passes the threshold.
+template <int W, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_compact_pruned(Terms in, const unsigned long long* n_in,
+                                                            double eps, double* pruned, Terms out,
+                                                            unsigned long long* n_out) {
+  const size_t n = *n_in;
+  __shared__ unsigned s_scan[THREADS / 32 + 1];
+  __shared__ unsigned long long s_base;
+  for (size_t tile = size_t(blockIdx.x) * THREADS; tile < n; tile += size_t(gridDim.x) * THREADS) {
+    const size_t i = tile + threadIdx.x;
+    const double w = i < n ? in.w[i] : 0.0;
+    const unsigned keep = (i < n && !(fabs(w) < eps)) ? 1u : 0u;
+    if (i < n && !keep) atomicAdd(&pruned[in.g[i]], w * w);
+    unsigned total;
+    const unsigned off = block_excl_scan<THREADS>(keep, &total, s_scan);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(n_out, (unsigned long long)total) : 0;
+    __syncthreads();
+    if (keep) {
+      uint64_t x[W], z[W];
+      load_term<W>(in, i, x, z);
+      store_term<W>(out, size_t(s_base) + off, x, z, in.w[i], in.g[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-generator statistics: term count and sum of squared weights.
+
+template <int W>
+__global__ void k_gen_stats(Terms t, const unsigned long long* n_in, unsigned long long* count,
+                            double* sumsq) {
+  const size_t N = *n_in;
+  for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
+       base += size_t(gridDim.x) * blockDim.x) {
+    const size_t i = base + threadIdx.x;
+    const bool valid = i < N;
+    const uint32_t g = valid ? t.g[i] : 0xffffffffu;
+    const double w = valid ? t.w[i] : 0.0;
+    const unsigned peers = __match_any_sync(0xffffffffu, g);
+    const int leader = __ffs(peers) - 1;
+    double s = 0.0;
+    unsigned rest = peers;
+    while (rest) {
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const double o = __shfl_sync(peers, w, src);
+      s += o * o;
+    }
+    if (valid && int(threadIdx.x & 31) == leader) {
+      atomicAdd(&count[g], (unsigned long long)__popc(peers));
+      atomicAdd(&sumsq[g], s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A7: readout.
+
+// Initial generators given as row-major strings (x, z: [G][W]) and weights.
+template <int W>
+__global__ void k_init_rows(Terms t, const uint64_t* rx, const uint64_t* rz, const double* w,
+                            int G, unsigned long long* n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < G) {
+    uint64_t x[W], z[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[k] = rx[size_t(i) * W + k];
+      z[k] = rz[size_t(i) * W + k];
+    }
+    store_term<W>(t, i, x, z, w ? w[i] : 1.0, uint32_t(i));
+  }
+  if (i == 0) *n_out = (unsigned long long)G;
+}
+
+// Terms of one generator, compacted into out (planar, cap = its count).
+template <int W, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_select(Terms in, const unsigned long long* n_in,
+                                                    uint32_t gen, Terms out,
+                                                    unsigned long long* n_out) {
+  __shared__ unsigned s_scan[THREADS / 32 + 1];
+  __shared__ unsigned long long s_base;
+  const size_t n = *n_in;
+  for (size_t tile = size_t(blockIdx.x) * THREADS; tile < n; tile += size_t(gridDim.x) * THREADS) {
+    const size_t i = tile + threadIdx.x;
+    const unsigned keep = (i < n && in.g[i] == gen) ? 1u : 0u;
+    unsigned total;
+    const unsigned off = block_excl_scan<THREADS>(keep, &total, s_scan);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(n_out, (unsigned long long)total) : 0;
+    __syncthreads();
+    if (keep && size_t(s_base) + off < out.cap) {
+      uint64_t x[W], z[W];
+      load_term<W>(in, i, x, z);
+      store_term<W>(out, size_t(s_base) + off, x, z, in.w[i], in.g[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// All terms in device order, row-major strings.
+template <int W>
+__global__ void k_raw(Terms in, size_t n, uint64_t* x, uint64_t* z, double* w, int32_t* g) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[i * W + k] = in.x[k * in.cap + i];
+      z[i * W + k] = in.z[k * in.cap + i];
+    }
+    w[i] = in.w[i];
+    g[i] = int32_t(in.g[i]);
+  }
+}
+
+// Lookup index over a result: open addressing on (generator, x, z).  Result
+// strings are unique, so building needs no key comparison: each term claims
+// the first empty slot of its probe sequence.
+struct IndexSlot {
+  unsigned long long tag;  // 0 = empty, else fingerprint | 1
+  unsigned idx;
+  unsigned pad;
+};
+
+template <int W>
+__global__ void k_index_build(Terms t, size_t n, IndexSlot* tab, unsigned long long cap,
+                              unsigned* err) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(t, i, x, z);
+    const uint64_t h = key_hash<W>(t.g[i], x, z);
+    const unsigned long long tag = h | 1ull;
+    unsigned long long pos = __umul64hi(h, cap);
+    bool done = false;
+    for (unsigned long long probe = 0; probe < cap; ++probe) {
+      if (atomicCAS(&tab[pos].tag, 0ull, tag) == 0ull) {
+        tab[pos].idx = unsigned(i);
+        done = true;
+        break;
+      }
+      if (++pos == cap) pos = 0;
+    }
+    if (!done) atomicOr(err, kErrProbe);
+  }
+}
+
+template <int W>
+__global__ void k_lookup(Terms t, const IndexSlot* tab, unsigned long long cap, size_t nq,
+                         const int32_t* qg, const uint64_t* qx, const uint64_t* qz, double* out) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nq;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[k] = qx[i * W + k];
+      z[k] = qz[i * W + k];
+    }
+    const uint32_t g = uint32_t(qg[i]);
+    const uint64_t h = key_hash<W>(g, x, z);
+    const unsigned long long tag = h | 1ull;
+    unsigned long long pos = __umul64hi(h, cap);
+    double v = 0.0;
+    for (unsigned long long probe = 0; probe < cap; ++probe) {
+      const unsigned long long s = tab[pos].tag;
+      if (s == 0ull) break;
+      if (s == tag) {
+        const unsigned j = tab[pos].idx;
+        bool same = t.g[j] == g;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          same = same && t.x[k * t.cap + j] == x[k] && t.z[k * t.cap + j] == z[k];
+        if (same) {
+          v = t.w[j];
+          break;
+        }
+      }
+      if (++pos == cap) pos = 0;
+    }
+    out[i] = v;
+  }
+}
+
+// sum of weights of the Z-type strings (x = 0) per generator: <0|P|0> = 1 for
+// those and 0 for every string with an X or Y.
+template <int W>
+__global__ void k_ztype_sum(Terms t, const unsigned long long* n_in, double* out) {
+  const size_t n = *n_in;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    bool ztype = true;
+#pragma unroll
+    for (int k = 0; k < W; ++k) ztype = ztype && t.x[k * t.cap + i] == 0;
+    if (ztype) atomicAdd(&out[t.g[i]], t.w[i]);
+  }
+}
+
+}  // namespace dev
+}  // namespace qx

@@ -1,0 +1,432 @@
+"""Python binding of libqx (ctypes): argument marshalling only.
+
+Every step of the propagation runs in libqx's CUDA kernels; this module
+converts circuits and Pauli strings to the C structures, passes PyTorch's
+current CUDA stream, and raises on any non-OK status.  There is no CPU
+fallback: without the built library or a GPU the calls raise.
+
+Pauli strings are given either as "IXYZ" letter strings (character i =
+qubit i) or as (x, z) integer bit masks (bit q = qubit q).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GATE_CODES = {
+    "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
+    "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
+}
+STATUS = {0: "QX_OK", 1: "QX_EINVAL", 2: "QX_ENOMEM", 3: "QX_EBUDGET", 4: "QX_ECAP",
+          5: "QX_ECUDA", 6: "QX_ETIMEOUT", 7: "QX_EUNSUPPORTED"}
+
+#: Every symbol that include/qx.h declares.
+EXPORTED = (
+    "qx_default_opts", "qx_load_circuit", "qx_group_ops", "qx_plan_info", "qx_plan_op",
+    "qx_plan_lut", "qx_plan_clifford_passes", "qx_plan_clifford_apply", "qx_propagate",
+    "qx_propagate_from", "qx_result_shape", "qx_result_info", "qx_result_stats",
+    "qx_result_export", "qx_result_raw", "qx_coeff", "qx_coeff_batch", "qx_expval",
+    "qx_free_circuit", "qx_free_plan", "qx_free_result", "qx_last_error",
+    "qx_kernel_class_name",
+)
+
+
+class QxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Instr(ctypes.Structure):
+    _fields_ = [("gate", ctypes.c_uint32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("theta", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PropOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
+                ("gen_begin", ctypes.c_int), ("gen_end", ctypes.c_int),
+                ("hbm_budget", ctypes.c_size_t), ("max_terms", ctypes.c_size_t),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p), ("timeout_ms", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+FLAG_KERNEL_TIMING = 1
+KC_COUNT = 10
+
+
+_SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
+            "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes")
+
+
+class PropStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in _SCALARS] + [
+        ("kc_launches", ctypes.c_uint64 * 16), ("kc_bytes", ctypes.c_uint64 * 16),
+        ("kc_ms", ctypes.c_double * 16)]
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k in _SCALARS}
+        lib = load_library()
+        d["kernels"] = {
+            lib.qx_kernel_class_name(k).decode(): {
+                "launches": int(self.kc_launches[k]), "alg_bytes": int(self.kc_bytes[k]),
+                "ms": float(self.kc_ms[k])}
+            for k in range(KC_COUNT)}
+        return d
+
+
+_lib = None
+_P = ctypes.c_void_p
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_DP = ctypes.POINTER(ctypes.c_double)
+_SZ = ctypes.c_size_t
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load libqx.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqx is not built ({path} missing): run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "qx_default_opts": (None, [ctypes.POINTER(PropOpts)]),
+        "qx_load_circuit": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Instr), _SZ,
+                                           ctypes.POINTER(_P)]),
+        "qx_group_ops": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "qx_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+        "qx_plan_op": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
+        "qx_plan_lut": (ctypes.c_int, [_P, _SZ, _DP]),
+        "qx_plan_clifford_passes": (ctypes.c_int, [_P, ctypes.POINTER(_SZ)]),
+        "qx_plan_clifford_apply": (ctypes.c_int, [_P, _SZ, _U64P, _U64P,
+                                                  ctypes.POINTER(ctypes.c_int)]),
+        "qx_propagate": (ctypes.c_int, [_P, ctypes.POINTER(PropOpts), ctypes.POINTER(_P)]),
+        "qx_propagate_from": (ctypes.c_int, [_P, ctypes.c_int, _U64P, _U64P, _DP,
+                                             ctypes.POINTER(PropOpts), ctypes.POINTER(_P)]),
+        "qx_result_shape": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ)]),
+        "qx_result_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_SZ), _DP, _DP]),
+        "qx_result_stats": (ctypes.c_int, [_P, ctypes.POINTER(PropStats)]),
+        "qx_result_export": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _SZ, ctypes.c_int]),
+        "qx_result_raw": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ]),
+        "qx_coeff": (ctypes.c_int, [_P, ctypes.c_int, _U64P, _U64P, _DP, _DP]),
+        "qx_coeff_batch": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P, ctypes.c_int]),
+        "qx_expval": (ctypes.c_int, [_P, _SZ, _U64P, _U64P, ctypes.POINTER(PropOpts), _DP]),
+        "qx_free_circuit": (None, [_P]),
+        "qx_free_plan": (None, [_P]),
+        "qx_free_result": (None, [_P]),
+        "qx_last_error": (ctypes.c_char_p, []),
+        "qx_kernel_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise QxError(status, load_library().qx_last_error().decode(errors="replace"))
+
+
+def words(n: int) -> int:
+    return (n + 63) // 64
+
+
+def pauli_to_words(p, n):
+    """'IXYZ...' string or (x, z) ints -> (x words, z words) as uint64 arrays."""
+    W = words(n)
+    if isinstance(p, str):
+        if len(p) != n:
+            raise ValueError("Pauli string length must equal n")
+        x = sum(1 << q for q, c in enumerate(p) if c in "XY")
+        z = sum(1 << q for q, c in enumerate(p) if c in "YZ")
+    else:
+        x, z = int(p[0]), int(p[1])
+    mask = (1 << 64) - 1
+    xw = np.array([(x >> (64 * k)) & mask for k in range(W)], dtype=np.uint64)
+    zw = np.array([(z >> (64 * k)) & mask for k in range(W)], dtype=np.uint64)
+    return xw, zw
+
+
+def words_to_pauli(xw, zw, n):
+    x = sum(int(v) << (64 * k) for k, v in enumerate(xw))
+    z = sum(int(v) << (64 * k) for k, v in enumerate(zw))
+    return "".join("IXZY"[((x >> q) & 1) + 2 * ((z >> q) & 1)] for q in range(n))
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+class _TorchAllocator:
+    """Routes libqx device allocations to PyTorch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx, stream):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:  # noqa: BLE001 - report as NULL to the library
+            return None
+
+    def _free(self, ptr, ctx, stream):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+_torch_alloc = None
+
+
+def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeout_ms=0,
+              torch_allocator=False, kernel_timing=False):
+    o = PropOpts()
+    load_library().qx_default_opts(ctypes.byref(o))
+    o.eps = float(eps)
+    if gens is not None:
+        o.gen_begin, o.gen_end = int(gens[0]), int(gens[1])
+    o.hbm_budget = int(hbm_budget)
+    o.max_terms = int(max_terms)
+    o.stream = _stream_ptr(stream)
+    o.timeout_ms = int(timeout_ms)
+    o.flags = FLAG_KERNEL_TIMING if kernel_timing else 0
+    if torch_allocator:
+        global _torch_alloc
+        if _torch_alloc is None:
+            _torch_alloc = _TorchAllocator()
+        o.alloc = _torch_alloc.alloc
+        o.free = _torch_alloc.free
+    return o
+
+
+class Circuit:
+    def __init__(self, n, instrs):
+        lib = load_library()
+        arr = (Instr * max(1, len(instrs)))()
+        for i, (g, a, b, th) in enumerate(instrs):
+            arr[i] = Instr(GATE_CODES[g], int(a), int(b), float(th))
+        h = _P()
+        _check(lib.qx_load_circuit(int(n), arr, len(instrs), ctypes.byref(h)))
+        self.n = n
+        self.instrs = list(instrs)
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qx_free_circuit(self._h)
+            self._h = None
+
+
+class Plan:
+    def __init__(self, circuit: Circuit):
+        lib = load_library()
+        h = _P()
+        _check(lib.qx_group_ops(circuit._h, ctypes.byref(h)))
+        self._h = h
+        self.n = circuit.n
+        self.W = words(circuit.n)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qx_free_plan(self._h)
+            self._h = None
+
+    def info(self):
+        K, Kp = _SZ(), _SZ()
+        _check(load_library().qx_plan_info(self._h, ctypes.byref(K), ctypes.byref(Kp)))
+        return int(K.value), int(Kp.value)
+
+    def ops(self):
+        K, Kp = self.info()
+        out = []
+        for k in range(K + Kp):
+            kind = ctypes.c_int()
+            _check(load_library().qx_plan_op(self._h, k, ctypes.byref(kind)))
+            out.append("U" if kind.value else "V")
+        return out
+
+    def lut(self, op):
+        out = np.zeros((self.n, 3, 3), np.float64)
+        _check(load_library().qx_plan_lut(self._h, op, out.ctypes.data_as(_DP)))
+        return out
+
+    def clifford_passes(self):
+        c = _SZ()
+        _check(load_library().qx_plan_clifford_passes(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def clifford_apply(self, k, pauli):
+        """Image (string, sign) of a Pauli string under fused Clifford pass k (host)."""
+        xw, zw = pauli_to_words(pauli, self.n)
+        sign = ctypes.c_int(1)
+        _check(load_library().qx_plan_clifford_apply(
+            self._h, k, xw.ctypes.data_as(_U64P), zw.ctypes.data_as(_U64P), ctypes.byref(sign)))
+        return words_to_pauli(xw, zw, self.n), int(sign.value)
+
+
+class Result:
+    def __init__(self, h, n):
+        self._h = h
+        self.n = n
+        g, w, t = ctypes.c_int(), ctypes.c_int(), _SZ()
+        _check(load_library().qx_result_shape(h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(t)))
+        self.ngen, self.W, self.nterms = int(g.value), int(w.value), int(t.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qx_free_result(self._h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
+
+    def info(self, g):
+        n, s, p = _SZ(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().qx_result_info(self._h, int(g), ctypes.byref(n), ctypes.byref(s),
+                                              ctypes.byref(p)))
+        return {"nterms": int(n.value), "sumsq": s.value, "pruned_sumsq": p.value}
+
+    def stats(self):
+        s = PropStats()
+        _check(load_library().qx_result_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def export(self, g):
+        """(x words [k, W] uint64, z words, weights) of generator g in base-4 order (host)."""
+        k = self.info(g)["nterms"]
+        x = np.zeros((max(k, 1), self.W), np.uint64)
+        z = np.zeros((max(k, 1), self.W), np.uint64)
+        w = np.zeros(max(k, 1), np.float64)
+        _check(load_library().qx_result_export(self._h, int(g), x.ctypes.data, z.ctypes.data,
+                                                w.ctypes.data, k, 0))
+        return x[:k], z[:k], w[:k]
+
+    def export_dict(self, g):
+        x, z, w = self.export(g)
+        return {words_to_pauli(x[i], z[i], self.n): float(w[i]) for i in range(len(w))}
+
+    def export_strings(self, g):
+        x, z, w = self.export(g)
+        return [words_to_pauli(x[i], z[i], self.n) for i in range(len(w))], w
+
+    def export_device(self, g):
+        """Generator g in base-4 order into new torch CUDA tensors (x, z, w)."""
+        import torch
+        k = self.info(g)["nterms"]
+        x = torch.zeros((max(k, 1), self.W), dtype=torch.int64, device="cuda")
+        z = torch.zeros_like(x)
+        w = torch.zeros(max(k, 1), dtype=torch.float64, device="cuda")
+        _check(load_library().qx_result_export(self._h, int(g), x.data_ptr(), z.data_ptr(),
+                                                w.data_ptr(), k, 1))
+        return x[:k], z[:k], w[:k]
+
+    def raw_device(self):
+        """All terms in device order as torch CUDA tensors (x, z, w, generator)."""
+        import torch
+        k = self.nterms
+        x = torch.zeros((max(k, 1), self.W), dtype=torch.int64, device="cuda")
+        z = torch.zeros_like(x)
+        w = torch.zeros(max(k, 1), dtype=torch.float64, device="cuda")
+        g = torch.zeros(max(k, 1), dtype=torch.int32, device="cuda")
+        _check(load_library().qx_result_raw(self._h, x.data_ptr(), z.data_ptr(), w.data_ptr(),
+                                             g.data_ptr(), k))
+        return x[:k], z[:k], w[:k], g[:k]
+
+    def coeff(self, g, pauli):
+        xw, zw = pauli_to_words(pauli, self.n)
+        re, im = ctypes.c_double(), ctypes.c_double()
+        _check(load_library().qx_coeff(self._h, int(g), xw.ctypes.data_as(_U64P),
+                                        zw.ctypes.data_as(_U64P), ctypes.byref(re),
+                                        ctypes.byref(im)))
+        return re.value
+
+    def coeff_batch(self, gens, paulis):
+        nq = len(paulis)
+        g = np.ascontiguousarray(gens, dtype=np.int32)
+        x = np.zeros((max(nq, 1), self.W), np.uint64)
+        z = np.zeros((max(nq, 1), self.W), np.uint64)
+        for i, p in enumerate(paulis):
+            x[i], z[i] = pauli_to_words(p, self.n)
+        out = np.zeros(max(nq, 1), np.float64)
+        _check(load_library().qx_coeff_batch(self._h, nq, g.ctypes.data, x.ctypes.data,
+                                              z.ctypes.data, out.ctypes.data, 0))
+        return out[:nq]
+
+
+def load_circuit(n, instrs) -> Circuit:
+    return Circuit(n, instrs)
+
+
+def group_ops(circuit: Circuit) -> Plan:
+    return Plan(circuit)
+
+
+def propagate(plan: Plan, **kw) -> Result:
+    o = make_opts(**kw)
+    h = _P()
+    _check(load_library().qx_propagate(plan._h, ctypes.byref(o), ctypes.byref(h)))
+    return Result(h, plan.n)
+
+
+def propagate_from(plan: Plan, paulis, weights=None, **kw) -> Result:
+    W = plan.W
+    G = len(paulis)
+    x = np.zeros((max(G, 1), W), np.uint64)
+    z = np.zeros((max(G, 1), W), np.uint64)
+    for i, p in enumerate(paulis):
+        x[i], z[i] = pauli_to_words(p, plan.n)
+    wp = None
+    if weights is not None:
+        warr = np.ascontiguousarray(weights, np.float64)
+        wp = warr.ctypes.data_as(_DP)
+    o = make_opts(**kw)
+    h = _P()
+    _check(load_library().qx_propagate_from(plan._h, G, x.ctypes.data_as(_U64P),
+                                             z.ctypes.data_as(_U64P), wp, ctypes.byref(o),
+                                             ctypes.byref(h)))
+    return Result(h, plan.n)
+
+
+def expval(plan: Plan, paulis, **kw):
+    W = plan.W
+    G = len(paulis)
+    x = np.zeros((max(G, 1), W), np.uint64)
+    z = np.zeros((max(G, 1), W), np.uint64)
+    for i, p in enumerate(paulis):
+        x[i], z[i] = pauli_to_words(p, plan.n)
+    out = np.zeros(max(G, 1), np.float64)
+    o = make_opts(**kw)
+    _check(load_library().qx_expval(plan._h, G, x.ctypes.data_as(_U64P), z.ctypes.data_as(_U64P),
+                                     ctypes.byref(o), out.ctypes.data_as(_DP)))
+    return out[:G]
+
+
+def coeff(result: Result, g, pauli):
+    return result.coeff(g, pauli)

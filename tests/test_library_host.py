@@ -1,0 +1,106 @@
+"""CPU checks of libqx: exported symbols, validation, and the host planner.
+
+The host planner's tables must be bit-equal to the oracle's (their zero
+pattern decides which strings exist), and the fused Clifford passes must map
+Pauli strings exactly as the oracle's gate-by-gate propagation does.
+"""
+import math
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2505_03307_gb300 import qx
+from paper_2505_03307_gb300 import workloads as W
+
+HEADER = __import__("os").path.join(__import__("os").path.dirname(__file__), "..", "include", "qx.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_exports_every_declared_symbol():
+    text = open(HEADER).read()
+    declared = set(re.findall(r"\b(qx_[a-z_]+)\s*\(", text))
+    assert declared == set(qx.EXPORTED)
+    lib = qx.load_library()
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_validation():
+    with pytest.raises(qx.QxError) as e:
+        qx.load_circuit(4, [("H", 4, -1, 0.0)])
+    assert e.value.name == "QX_EINVAL"
+    with pytest.raises(qx.QxError) as e:
+        qx.load_circuit(4, [("CX", 1, 1, 0.0)])
+    assert e.value.name == "QX_EINVAL"
+    with pytest.raises(qx.QxError) as e:
+        qx.load_circuit(129, [])
+    assert e.value.name == "QX_EUNSUPPORTED"
+    with pytest.raises(qx.QxError) as e:
+        qx.load_circuit(2, [("RZ", 0, -1, float("nan"))])
+    assert e.value.name == "QX_EINVAL"
+    qx.load_circuit(3, [])  # empty circuit is valid
+
+
+def _circuits():
+    yield W.random_layers(1)
+    yield W.hea(2, n=8, layers=2)
+    yield W.fan_in_heavy(1, n=12, n_s=4, total=200, tail=40)
+    for seed in range(12):
+        yield W.random_small(seed, 1 + seed % 6, 40, angles="quarter" if seed % 2 else "uniform")
+    yield W.random_small(99, 70, 300, angles="quarter")
+
+
+@pytest.mark.parametrize("idx", range(16))
+def test_plan_matches_oracle_bit_for_bit(idx):
+    n, instrs = list(_circuits())[idx]
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    ref = O.plan(n, instrs)
+    assert plan.ops() == [k for k, _ in ref]
+    K, Kp = plan.info()
+    assert K == sum(k == "U" for k, _ in ref) and Kp == sum(k == "V" for k, _ in ref)
+    assert abs(K - Kp) <= 1
+    for op, (kind, lut) in enumerate(ref):
+        if kind == "U":
+            assert np.array_equal(plan.lut(op), lut), op
+
+
+def _check_passes(n, instrs, seed):
+    """A Clifford-only circuit gives one fused pass equal to the whole circuit."""
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    assert plan.clifford_passes() == 1
+    starts = W.random_paulis(seed, n, 6) + ["".join("Z" if q == j else "I" for q in range(n))
+                                            for j in (0, n - 1)]
+    ref = O.propagate(n, instrs, mode="gate", init=[(s, 1.0) for s in starts])
+    for s, r in zip(starts, ref):
+        (want_s, want_w), = O.as_dict(r).items()
+        assert plan.clifford_apply(0, s) == (want_s, int(want_w))
+
+
+@pytest.mark.parametrize("n,m", [(5, 3), (5, 400), (40, 10), (64, 900), (65, 30), (100, 3000),
+                                 (128, 2000)])
+def test_clifford_pass_matches_oracle(n, m):
+    _, instrs = W.random_clifford(n * 7 + m, n, m)
+    _check_passes(n, instrs, n + m)
+
+
+def test_clifford_pass_forms():
+    """Short passes use the gate list, long passes the chunk tables; both exact."""
+    _check_passes(*W.ghz(60), 3)
+    _check_passes(*W.graph_state(4, 90, 0.2), 4)
+
+
+def test_propagate_without_gpu_fails_loudly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    plan = qx.group_ops(qx.load_circuit(2, [("H", 0, -1, 0.0)]))
+    with pytest.raises(qx.QxError) as e:
+        qx.propagate(plan)
+    assert e.value.name in ("QX_EUNSUPPORTED", "QX_ECUDA")
