@@ -216,6 +216,39 @@ qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, cons
 qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint64_t* z,
                     const qx_prop_opts* o, double* out);
 
+/* One-qubit expansion with index-based accumulation that allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, for example a process whose GPU memory is
+ * entirely owned by another allocator (a framework pool that reserved the
+ * device), or a latency-critical loop where cudaMalloc, which may synchronise
+ * the device, is not acceptable.  The scratch (hash table and group payload,
+ * about 16 MiB) is a fixed array inside the library that every GPU which
+ * loads the library holds until the process exits.
+ *
+ * Applies the 3x3 image table `table` (9 doubles, host memory, rows and
+ * columns in (X, Y, Z) order, as qx_plan_lut) to wire q of every input term,
+ * and merges the children that land on the same (generator, string).  Inputs
+ * and outputs are device memory in planar layout: word k of string i is at
+ * x[k * n_in + i] (input) and out_x[k * out_cap + i] (output), W = ceil(n/64)
+ * words; weights and generator ids one per term.  Input strings must be
+ * unique within their generator and generator ids must be < ngen.  Output
+ * order is unspecified; *n_out (host) receives the number of output terms.
+ *
+ * Limits: n_in <= 262144 terms, ngen <= 4096, otherwise QX_EINVAL before any
+ * device work; QX_ECAP when out_cap is too small (at most 3 * n_in outputs).
+ * The first call on a device (with that device current) looks up and clears
+ * the scratch and synchronises the device; make that first call before any
+ * other work that must not be synchronised.  Every call on a device shares
+ * the same scratch and leaves its contents behind (later calls ignore them);
+ * calls whose device work overlaps (different streams or threads) race on
+ * the scratch and must be serialised by the caller.  The call synchronises
+ * `stream` (a cudaStream_t, NULL for the default stream) before returning. */
+qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const uint64_t* x,
+                                const uint64_t* z, const double* w, const uint32_t* gen, int q,
+                                const double* table, uint64_t* out_x, uint64_t* out_z,
+                                double* out_w, uint32_t* out_gen, size_t out_cap, size_t* n_out,
+                                void* stream);
+
 void qx_free_circuit(qx_circuit* c);
 void qx_free_plan(qx_plan* p);
 void qx_free_result(qx_result* r);

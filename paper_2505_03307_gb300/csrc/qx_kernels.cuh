@@ -608,7 +608,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(unsigned long long* a,
+static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(unsigned long long* a,
                                                              const unsigned long long* n_in,
                                                              unsigned long long* tile_sums) {
   __shared__ unsigned long long s[kScanThreads / 32 + 1];
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(unsigned long long*
   if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = run;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* sums, size_t ntiles,
+static __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* sums, size_t ntiles,
                                                     unsigned long long* total) {
   __shared__ unsigned long long s[33];
   unsigned long long carry = 0;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* sums, si
   if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long long* a,
+static __global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long long* a,
                                                            const unsigned long long* n_in,
                                                            const unsigned long long* tile_offs) {
   const size_t N = *n_in;

@@ -31,7 +31,7 @@ EXPORTED = (
     "qx_propagate_from", "qx_result_shape", "qx_result_info", "qx_result_stats",
     "qx_result_export", "qx_result_raw", "qx_coeff", "qx_coeff_batch", "qx_expval",
     "qx_free_circuit", "qx_free_plan", "qx_free_result", "qx_last_error",
-    "qx_kernel_class_name",
+    "qx_kernel_class_name", "qx_merge_qubit_static",
 )
 
 
@@ -131,6 +131,9 @@ def load_library():
         "qx_free_result": (None, [_P]),
         "qx_last_error": (ctypes.c_char_p, []),
         "qx_kernel_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "qx_merge_qubit_static": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.c_int, _P, _P, _P, _P,
+                                                 ctypes.c_int, _DP, _P, _P, _P, _P, _SZ,
+                                                 ctypes.POINTER(_SZ), _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -426,6 +429,22 @@ def expval(plan: Plan, paulis, **kw):
     _check(load_library().qx_expval(plan._h, G, x.ctypes.data_as(_U64P), z.ctypes.data_as(_U64P),
                                      ctypes.byref(o), out.ctypes.data_as(_DP)))
     return out[:G]
+
+
+def merge_qubit_static(n, ngen, x, z, w, gen, q, table, out_x, out_z, out_w, out_gen,
+                       stream=None):
+    """qx_merge_qubit_static on torch CUDA tensors (planar layout, see include/qx.h).
+
+    x, z: int64 [W, N]; w: float64 [N]; gen: int32 [N]; outputs likewise with
+    capacity out_w.numel().  Returns the number of output terms."""
+    t = np.ascontiguousarray(table, np.float64).reshape(9)
+    nout = _SZ()
+    _check(load_library().qx_merge_qubit_static(
+        int(n), int(w.numel()), int(ngen), x.data_ptr(), z.data_ptr(), w.data_ptr(),
+        gen.data_ptr(), int(q), t.ctypes.data_as(_DP), out_x.data_ptr(), out_z.data_ptr(),
+        out_w.data_ptr(), out_gen.data_ptr(), int(out_w.numel()), ctypes.byref(nout),
+        _stream_ptr(stream)))
+    return int(nout.value)
 
 
 def coeff(result: Result, g, pauli):
