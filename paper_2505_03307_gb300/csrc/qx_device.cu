@@ -125,6 +125,12 @@ struct qx_plan_device {
   };
   std::vector<Pass> passes;
   size_t max_smem = 0;
+  // Merge table of the one-word fast path, kept between propagations: every
+  // pass leaves it empty, so it is cleared only when allocated or after an
+  // aborted pass.
+  FastSlot* ftab = nullptr;
+  unsigned long long fcap = 0;
+  bool fdirty = false;
 };
 
 namespace qx {
@@ -132,6 +138,7 @@ namespace qx {
 void free_plan_device(qx_plan* p) {
   if (!p || !p->dev) return;
   if (p->dev->base) cudaFree(p->dev->base);
+  if (p->dev->ftab) cudaFree(p->dev->ftab);
   delete p->dev;
   p->dev = nullptr;
 }
@@ -231,6 +238,7 @@ struct Scratch {
   double* pv = nullptr;
   uint32_t* pmask = nullptr;
   size_t pcap = 0;
+  bool payload_fast = false;
 };
 
 }  // namespace
@@ -411,6 +419,230 @@ qx_status ensure_hash(Ctx& c, size_t n) {
   return QX_OK;
 }
 
+// The one-word fast path needs the generator id to fit in the free high bits
+// of the two key words.
+bool fast_eligible(int n, int W, int G) {
+  if (W != 1 || n >= 64) return false;
+  int bits = 0;
+  while ((1ll << bits) < G) ++bits;
+  return bits <= 2 * (64 - n);
+}
+
+qx_status ensure_fast_table(Ctx& c, unsigned long long want) {
+  qx_plan_device* d = const_cast<qx_plan*>(c.p)->dev;
+  if (d->fcap < want) {
+    if (d->ftab) {
+      cudaStreamSynchronize(c.al.s);
+      cudaFree(d->ftab);
+      d->ftab = nullptr;
+      d->fcap = 0;
+    }
+    void* t = nullptr;
+    if (cudaMalloc(&t, want * sizeof(FastSlot)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QX_ENOMEM, "device allocation of the merge table failed");
+    }
+    d->ftab = static_cast<FastSlot*>(t);
+    d->fcap = want;
+    d->fdirty = true;
+  }
+  if (d->fdirty) {
+    k_fast_table_init<<<grid_for(d->fcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(d->ftab,
+                                                                                     d->fcap);
+    QX_TRY_CUDA(cudaGetLastError());
+    d->fdirty = false;
+  }
+  return QX_OK;
+}
+
+// Insert + emit of one merge pass at fan-out qubit f.q: reads cur (count in
+// ncnt[cslot]), writes `out` (count in ncnt[oslot], reset here).  No sync.
+template <int W>
+qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const TermBuf& out,
+                       int oslot, double eps) {
+  Scratch& s = c.sc;
+  QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + oslot, 0, 8, c.al.s));
+  if (fast) {
+    // insert + children of unmerged terms, then one thread per active slot;
+    // the table counts as dirty until a sync has shown the pass completed
+    qx_plan_device* d = const_cast<qx_plan*>(c.p)->dev;
+    d->fdirty = true;
+    c.begin(KC_INSERT);
+    k_merge_insert_fast<kThreads><<<grid, kThreads, 0, c.al.s>>>(
+        c.cur.t, s.ncnt + c.cslot, c.n, f.q, f, s.mixed, d->ftab, d->fcap, eps, s.pruned, out.t,
+        s.ncnt + oslot, s.err);
+    c.tm.end();
+    c.begin(KC_EMIT);
+    const unsigned ggrid = grid_for(2 * std::max<size_t>(c.cur.t.cap, 512), kThreads, c.sms, 8);
+    k_merge_groups_fast<kThreads><<<ggrid, kThreads, 0, c.al.s>>>(
+        s.ncnt + c.cslot, c.cur.t.cap, c.n, f.q, f, d->ftab, d->fcap, eps, s.pruned, out.t,
+        s.ncnt + oslot, s.err);
+    c.tm.end();
+  } else {
+    c.begin(KC_INSERT);
+    k_merge_insert<W><<<grid, kThreads, 0, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed,
+                                                     s.table, s.tcap, s.epoch, s.lead, s.pv,
+                                                     s.pmask, s.pcap, c.spin_limit, s.err);
+    c.tm.end();
+    c.begin(KC_EMIT);
+    k_merge_emit<W, kThreads><<<grid, kThreads, 0, c.al.s>>>(
+        c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed, s.lead, s.pv, s.pmask, s.pcap, eps,
+        s.pruned, out.t, s.ncnt + oslot, s.err);
+    c.tm.end();
+  }
+  QX_TRY_CUDA(cudaGetLastError());
+  c.st.merge_passes++;
+  return QX_OK;
+}
+
+// Makes the slow path's table and the leader array hold `n` terms.
+template <int W>
+qx_status ensure_merge_scratch(Ctx& c, bool fast, size_t n) {
+  if (fast) {
+    QX_TRY(ensure_fast_table(c, std::max<unsigned long long>(1024, 2ull * n)));
+    Scratch& s = c.sc;
+    if (s.pcap < n) {
+      c.al.put(s.payload);
+      const size_t cap = std::max<size_t>(n, 64);
+      s.payload = c.al.get(cap * 4);
+      if (!s.payload) return fail(QX_ENOMEM, "device allocation of the merge payload failed");
+      s.lead = static_cast<uint32_t*>(s.payload);
+      s.pv = nullptr;
+      s.pmask = nullptr;
+      s.pcap = cap;
+      s.payload_fast = true;
+    }
+    return QX_OK;
+  }
+  if (c.sc.payload_fast) {  // switch layouts
+    c.al.put(c.sc.payload);
+    c.sc.payload = nullptr;
+    c.sc.pcap = 0;
+    c.sc.payload_fast = false;
+  }
+  return ensure_hash<W>(c, n);
+}
+
+// Merge passes over the mixed qubits.  First without host syncs inside a
+// capacity arena (counts stay on the device); if an output or the table
+// overflows, the passes are redone one by one with exact counts.
+template <int W>
+qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after) {
+  const bool fast = fast_eligible(c.n, W, c.G);
+  const size_t N0 = c.N;
+  const int slot0 = c.cslot;
+  // arena: the growth bound of the passes (product of the largest row
+  // fan-out of each qubit), clamped to [3, 8] x the input, at least 64K terms
+  double growth = 1.0;
+  for (const FanQubit* f : mq) growth *= std::max({f->nnz[0], f->nnz[1], f->nnz[2]});
+  size_t cap = size_t(std::min(8.0, std::max(3.0, growth)) * double(N0));
+  cap = std::max<size_t>(cap, 65536);
+  if (c.budget) cap = std::min(cap, std::max(N0, c.budget / term_bytes(W)));
+  if (c.max_terms) cap = std::min(cap, std::max(N0, c.max_terms));
+  bool ok = false;
+  // pruning inside these passes accumulates pruned mass that a redo would
+  // count twice: with eps > 0 the passes run in exact mode directly
+  const bool optimistic = !(c.eps > 0.0 && !more_after);
+  if (optimistic) {
+    TermBuf buf[2];
+    qx_status st = alloc_terms(c.al, W, cap, &buf[0]);
+    if (st == QX_OK) st = alloc_terms(c.al, W, cap, &buf[1]);
+    if (st == QX_OK) st = ensure_merge_scratch<W>(c, fast, cap);
+    if (st != QX_OK) {
+      c.al.put(buf[0].base);
+      c.al.put(buf[1].base);
+      return st;
+    }
+    const unsigned grid = grid_for(cap, kThreads, c.sms, 8);
+    TermBuf input = c.cur;
+    int b = 0;
+    for (size_t j = 0; j < mq.size(); ++j) {
+      const bool last = !more_after && j + 1 == mq.size();
+      const FanQ f = to_dev(*mq[j]);
+      if (!fast) {
+        if (++c.sc.epoch >= 0xffffu) {
+          QX_TRY_CUDA(cudaMemsetAsync(c.sc.table, 0, c.sc.tcap * sizeof(Slot), c.al.s));
+          c.sc.epoch = 1;
+        }
+      }
+      const int oslot = 1 - c.cslot;
+      QX_TRY(launch_merge<W>(c, f, fast, grid, buf[b], oslot, last ? c.eps : 0.0));
+      c.cur = buf[b];
+      c.cslot = oslot;
+      b ^= 1;
+    }
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    QX_TRY(sync_read(c, h, c.sc.ncnt, 40));
+    const unsigned long long nout = h[c.cslot];
+    const unsigned err = unsigned(h[4]);
+    if (err & kErrSpin) return fail(QX_ETIMEOUT, "a device-side wait for a group leader gave up");
+    ok = !(err & (kErrProbe | kErrCap));
+    if (ok) {
+      if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = false;
+      // counts of every pass are not kept on the host in this mode: account
+      // the passes with the final count
+      c.st.alg_bytes += mq.size() * (N0 + nout) * (16 * W + 8);
+      c.st.children += mq.size() * nout;
+      c.st.kc_bytes[KC_INSERT] += mq.size() * N0 * (16 * W + 8);
+      c.st.kc_bytes[KC_EMIT] += mq.size() * (N0 + nout) * (16 * W + 8);
+      c.st.kc_launches[KC_INSERT] += mq.size();
+      c.st.kc_launches[KC_EMIT] += mq.size();
+      c.st.kernel_launches += 2 * mq.size();
+      const TermBuf keep = c.cur;
+      c.al.put(buf[b].base);  // the unused buffer of the pair
+      c.cur = input;
+      replace_cur(c, keep, nout, c.cslot);
+      if (const qx_status e = check_limits(c, nout)) return e;
+      return QX_OK;
+    }
+    // overflow: start over from the step's input
+    if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = true;
+    c.al.put(buf[0].base);
+    c.al.put(buf[1].base);
+    c.cur = input;
+    c.cslot = slot0;
+    c.N = N0;
+    // the passes above overwrote both count slots: restore the input's count
+    const unsigned long long n0 = N0;
+    QX_TRY_CUDA(cudaMemcpyAsync(c.sc.ncnt + slot0, &n0, 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+    QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
+    c.st.host_syncs++;
+  }
+  // exact mode: one pass at a time, counts read after each
+  for (size_t j = 0; j < mq.size(); ++j) {
+    const bool last = !more_after && j + 1 == mq.size();
+    const FanQ f = to_dev(*mq[j]);
+    QX_TRY(ensure_merge_scratch<W>(c, fast, c.N));
+    if (!fast && ++c.sc.epoch >= 0xffffu) {
+      QX_TRY_CUDA(cudaMemsetAsync(c.sc.table, 0, c.sc.tcap * sizeof(Slot), c.al.s));
+      c.sc.epoch = 1;
+    }
+    TermBuf out;
+    QX_TRY(alloc_terms(c.al, W, 3 * c.N, &out));
+    const int oslot = 1 - c.cslot;
+    QX_TRY(launch_merge<W>(c, f, fast, grid_for(c.N, kThreads, c.sms, 8), out, oslot,
+                           last ? c.eps : 0.0));
+    unsigned long long nout = 0;
+    QX_TRY(sync_read(c, &nout, c.sc.ncnt + oslot, 8));
+    if (const qx_status e = check_err(c)) {
+      c.al.put(out.base);
+      return e;
+    }
+    if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = false;
+    if (const qx_status e = check_limits(c, nout)) {
+      c.al.put(out.base);
+      return e;
+    }
+    c.end_bytes_only(KC_INSERT, 1, uint64_t(c.N) * (16 * W + 8));
+    c.end_bytes_only(KC_EMIT, 1, (c.N + nout) * (16 * W + 8));
+    c.st.alg_bytes += (c.N + nout) * (16 * W + 8);
+    c.st.children += nout;
+    replace_cur(c, out, nout, oslot);
+  }
+  return QX_OK;
+}
+
 template <int W>
 qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   c.st.term_updates += (ops_before + 1) * c.N;
@@ -449,43 +681,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   if (!mq.empty())
     QX_TRY_CUDA(cudaMemcpyAsync(s.mixed, mixed.data(), G * W * 8, cudaMemcpyHostToDevice, c.al.s));
   // 2. one merge pass per qubit that needs it in some generator
-  for (size_t j = 0; j < mq.size(); ++j) {
-    const bool last = fq.empty() && j + 1 == mq.size();
-    const FanQ f = to_dev(*mq[j]);
-    QX_TRY(ensure_hash<W>(c, c.N));
-    const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
-    c.begin(KC_INSERT);
-    k_merge_insert<W><<<grid, kThreads, 0, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed,
-                                                     s.table, s.tcap, s.epoch, s.lead, s.pv,
-                                                     s.pmask, s.pcap, c.spin_limit, s.err);
-    c.end(KC_INSERT, 1, uint64_t(c.N) * (16 * W + 8));
-    QX_TRY_CUDA(cudaGetLastError());
-    TermBuf out;
-    QX_TRY(alloc_terms(c.al, W, 3 * c.N, &out));
-    const int oslot = 1 - c.cslot;
-    QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + oslot, 0, 8, c.al.s));
-    c.begin(KC_EMIT);
-    k_merge_emit<W, kThreads><<<grid, kThreads, 0, c.al.s>>>(
-        c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed, s.lead, s.pv, s.pmask, s.pcap,
-        last ? c.eps : 0.0, s.pruned, out.t, s.ncnt + oslot, s.err);
-    c.tm.end();
-    QX_TRY_CUDA(cudaGetLastError());
-    c.st.merge_passes++;
-    unsigned long long nout = 0;
-    QX_TRY(sync_read(c, &nout, s.ncnt + oslot, 8));
-    c.end_bytes_only(KC_EMIT, 1, (c.N + nout) * (16 * W + 8));
-    if (const qx_status e = check_err(c)) {
-      c.al.put(out.base);
-      return e;
-    }
-    if (const qx_status e = check_limits(c, nout)) {
-      c.al.put(out.base);
-      return e;
-    }
-    c.st.alg_bytes += (c.N + nout) * (16 * W + 8);
-    c.st.children += nout;
-    replace_cur(c, out, nout, oslot);
-  }
+  if (!mq.empty()) QX_TRY(run_merges<W>(c, mq, !fq.empty()));
   if (fq.empty()) return QX_OK;
   // 3. one-shot expansion over the qubits that need no merge anywhere
   std::vector<FanQ> hq;
@@ -635,8 +831,8 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   QX_TRY_CUDA(cudaMemsetAsync(st, 0, G * 16, c.al.s));
   c.begin(KC_STATS);
   if (c.N)
-    k_gen_stats<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-        c.cur.t, c.sc.ncnt + c.cslot, d_count, d_sumsq);
+    k_gen_stats<W><<<grid_for(c.N, kThreads * 16, c.sms, 2), kThreads, 0, c.al.s>>>(
+        c.cur.t, c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
   c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
   QX_TRY_CUDA(cudaMemcpyAsync(r->sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));

@@ -382,10 +382,19 @@ struct Slot {
 
 template <int W>
 __global__ void __launch_bounds__(256) k_merge_insert(
-    Terms t, const unsigned long long* n_in, int q, FanQ fq, const uint64_t* mixed /* [G][W] */,
+    Terms t, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p,
+    const uint64_t* mixed /* [G][W] */,
     Slot* table, unsigned long long tcap, unsigned epoch, uint32_t* lead, double* pv /* [3][cap] */,
     uint32_t* pmask, size_t pcap, unsigned spin_limit, unsigned* err) {
-  const size_t N = *n_in;
+  // the table is read with per-thread letter indices: a shared copy keeps
+  // those reads parallel (divergent reads of kernel parameters serialise)
+  __shared__ FanQ fq;
+  if (threadIdx.x == 0) fq = fq_p;
+  __syncthreads();
+  // after an overflow (flagged in *err) the chain of passes stops: the
+  // buffer may hold unwritten entries, and the host redoes the step
+  if (*(volatile const unsigned*)err) return;
+  const size_t N = min(size_t(*n_in), t.cap);
   const int qk = q >> 6;
   const uint64_t qm = 1ull << (q & 63);
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
@@ -428,6 +437,7 @@ __global__ void __launch_bounds__(256) k_merge_insert(
           unsigned it = 0;
           while (ld_acquire(&s->ready) != epoch) {
             if (++it > spin_limit) {
+              lead[i] = 0xffffffffu;  // not a leader: emits nothing
               atomicOr(err, kErrSpin);
               return;
             }
@@ -455,7 +465,10 @@ __global__ void __launch_bounds__(256) k_merge_insert(
       }
       if (++pos == tcap) pos = 0;
     }
-    if (!done) atomicOr(err, kErrProbe);
+    if (!done) {
+      lead[i] = 0xffffffffu;  // not a leader: emits nothing
+      atomicOr(err, kErrProbe);
+    }
   }
 }
 
@@ -522,12 +535,24 @@ __device__ __forceinline__ unsigned merge_children(const uint64_t* x, const uint
 
 template <int W, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_merge_emit(
-    Terms in, const unsigned long long* n_in, int q, FanQ fq, const uint64_t* mixed,
+    Terms in, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p, const uint64_t* mixed,
     const uint32_t* lead, const double* pv, const uint32_t* pmask, size_t pcap, double eps,
     double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+  // the table is read with per-thread letter indices: a shared copy keeps
+  // those reads parallel (divergent reads of kernel parameters serialise)
+  __shared__ FanQ fq;
+  if (threadIdx.x == 0) fq = fq_p;
+  __syncthreads();
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
-  const size_t N = *n_in;
+  // after an overflow (flagged in *err) the chain of passes stops: the
+  // buffer may hold unwritten entries, and the host redoes the step
+  // (read once per block: the emit has block barriers)
+  __shared__ unsigned s_err;
+  if (threadIdx.x == 0) s_err = *(volatile const unsigned*)err;
+  __syncthreads();
+  if (s_err) return;
+  const size_t N = min(size_t(*n_in), in.cap);
   for (size_t tile = size_t(blockIdx.x) * THREADS; tile < N; tile += size_t(gridDim.x) * THREADS) {
     const size_t i = tile + threadIdx.x;
     uint64_t x[W], z[W];
@@ -563,6 +588,358 @@ __global__ void __launch_bounds__(THREADS) k_merge_emit(
           store_term<W>(out, base + j, cx, cz, cw[j], g);
         }
       }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A6, one-word strings (n < 64): the group key fits in 128 bits.
+//
+// The generator id is packed into the free high bits of the two key words
+// (bits n..63 of x, then of z) and bit q of the x word is set as a marker, so
+// the all-zero pair never occurs as a key and marks an empty slot.
+//
+// Insert pass (one thread per term, coalesced): terms that need no merge write
+// their children at once; the others claim or find their group's slot with
+// one 128-bit compare-and-swap and store their weight in the slot, in the
+// position of their letter among the qubit's non-isolated rows.  A weight slot
+// holding the sentinel bit pattern is absent (no counters, no atomics, no
+// leader: nothing waits on anything).
+//
+// Group pass (one thread per slot of the active region, coalesced): every
+// occupied slot is a group; its strings and generator are unpacked from the
+// key, its children written with weights sum_p t[p][c] v_p in the fixed order
+// p = X, Y, Z, and the slot reset.  The table is empty again after every pass.
+
+struct FastSlot {
+  unsigned long long klo, khi;  // packed key; 0, 0 = empty
+  double v[3];                  // member weights by rank among non-isolated rows
+  unsigned long long pad[3];    // 64-byte slots: v[0], v[1] share the key's sector
+};
+
+constexpr unsigned long long kAbsent = 0x7ff4dead7ff4deadull;  // a NaN never computed
+
+__device__ __forceinline__ void cas128(unsigned long long* p, unsigned long long cmp_lo,
+                                       unsigned long long cmp_hi, unsigned long long new_lo,
+                                       unsigned long long new_hi, unsigned long long* old_lo,
+                                       unsigned long long* old_hi) {
+  asm volatile(
+      "{\n\t.reg .b128 d, b, c;\n\t"
+      "mov.b128 b, {%2, %3};\n\t"
+      "mov.b128 c, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], b, c;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(*old_lo), "=l"(*old_hi)
+      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(p)
+      : "memory");
+}
+
+__device__ __forceinline__ void pack_key(uint64_t x, uint64_t z, uint32_t g, int n, int q,
+                                         unsigned long long* lo, unsigned long long* hi) {
+  const uint64_t qm = 1ull << q;
+  const int fb = 64 - n;  // free high bits per word, >= 1
+  *lo = (x & ~qm) | qm | (uint64_t(g) << n);
+  *hi = (z & ~qm) | (fb < 32 ? (uint64_t(g) >> fb) << n : 0ull);
+}
+
+__device__ __forceinline__ void unpack_key(unsigned long long lo, unsigned long long hi, int n,
+                                           int q, uint64_t* x, uint64_t* z, uint32_t* g) {
+  const uint64_t low = (1ull << n) - 1;  // n < 64
+  const int fb = 64 - n;
+  *x = lo & low & ~(1ull << q);
+  *z = hi & low;
+  *g = uint32_t((lo >> n) | (fb < 32 ? (hi >> n) << fb : 0ull));
+}
+
+// Active slots of a pass: 1.5 times its input count (load <= 2/3 even if no
+// two terms merge), at least 1024.
+__device__ __forceinline__ unsigned long long active_slots(size_t N, unsigned long long tcap) {
+  return min(tcap, max(1024ull, (unsigned long long)N + ((unsigned long long)N >> 1)));
+}
+
+static __global__ void k_fast_table_init(FastSlot* tab, unsigned long long cap) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    tab[i].klo = 0ull;
+    tab[i].khi = 0ull;
+    tab[i].v[0] = __longlong_as_double(kAbsent);
+    tab[i].v[1] = __longlong_as_double(kAbsent);
+    tab[i].v[2] = __longlong_as_double(kAbsent);
+  }
+}
+
+// Block-wide output allocation: returns this thread's first output index.
+template <int THREADS>
+__device__ __forceinline__ size_t alloc_out(unsigned c, unsigned* s_scan,
+                                            unsigned long long* s_base,
+                                            unsigned long long* n_out) {
+  unsigned total;
+  const unsigned off = block_excl_scan<THREADS>(c, &total, s_scan);
+  if (threadIdx.x == 0) *s_base = total ? atomicAdd(n_out, (unsigned long long)total) : 0;
+  __syncthreads();
+  const size_t base = size_t(*s_base) + off;
+  __syncthreads();
+  return base;
+}
+
+
+// One-word children of a block, staged in shared memory and written out with
+// consecutive threads on consecutive terms.  Each thread contributes up to 3
+// children (x, z, w, g) at block-local offsets from the block scan.
+template <int THREADS>
+struct StageOut {
+  uint64_t x[3 * THREADS];
+  uint64_t z[3 * THREADS];
+  double w[3 * THREADS];
+  uint32_t g[3 * THREADS];
+};
+
+template <int THREADS>
+__device__ __forceinline__ void flush_stage(StageOut<THREADS>& st, unsigned total, size_t base,
+                                            const Terms& out) {
+  for (unsigned k = threadIdx.x; k < total; k += THREADS) {
+    out.x[base + k] = st.x[k];
+    out.z[base + k] = st.z[k];
+    out.w[base + k] = st.w[k];
+    out.g[base + k] = st.g[k];
+  }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
+    Terms t, const unsigned long long* n_in, int n, int q, const __grid_constant__ FanQ fq_p,
+    const uint64_t* mixed, FastSlot* tab, unsigned long long tcap, double eps, double* pruned,
+    Terms out, unsigned long long* n_out, unsigned* err) {
+  // the table is read with per-thread letter indices: a shared copy keeps
+  // those reads parallel (divergent reads of kernel parameters serialise)
+  __shared__ FanQ fq;
+  __shared__ unsigned s_scan[THREADS / 32 + 1];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned s_err;
+  __shared__ StageOut<THREADS> st;
+  if (threadIdx.x == 0) {
+    fq = fq_p;
+    s_err = *(volatile const unsigned*)err;
+  }
+  __syncthreads();
+  // after an overflow (flagged in *err) the chain of passes stops: the
+  // buffer may hold unwritten entries, and the host redoes the step
+  if (s_err) return;
+  const size_t N = min(size_t(*n_in), t.cap);
+  const unsigned long long teff = active_slots(N, tcap);
+  const uint64_t qm = 1ull << q;
+  constexpr int ITEMS = 2;  // terms per thread per tile: two CAS chains in flight
+  for (size_t tile = size_t(blockIdx.x) * THREADS * ITEMS; tile < N;
+       tile += size_t(gridDim.x) * THREADS * ITEMS) {
+    uint64_t x[ITEMS], z[ITEMS];
+    uint32_t g[ITEMS];
+    double w[ITEMS];
+    int p[ITEMS];
+    bool hashed[ITEMS];
+    unsigned long long pos[ITEMS], klo[ITEMS], khi[ITEMS];
+    int cl[3];
+    double cw[3];
+    uint64_t cx0 = 0, cz0 = 0;
+    uint32_t cg0 = 0;
+    unsigned c = 0;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const size_t i = tile + size_t(it) * THREADS + threadIdx.x;
+      hashed[it] = false;
+      p[it] = -1;
+      if (i >= N) continue;
+      x[it] = t.x[i];
+      z[it] = t.z[i];
+      g[it] = t.g[i];
+      w[it] = t.w[i];
+      const int xb = int((x[it] >> q) & 1), zb = int((z[it] >> q) & 1);
+      if (xb | zb) {
+        p[it] = xb ? (zb ? 1 : 0) : 2;
+        hashed[it] = !fq.iso[p[it]] && (mixed[g[it]] & qm);
+      }
+      if (hashed[it]) {
+        pack_key(x[it], z[it], g[it], n, q, &klo[it], &khi[it]);
+        const uint64_t h = fmix64(klo[it] ^ fmix64(khi[it] + 0x632be59bd9b4e019ull));
+        pos[it] = __umul64hi(h, teff);
+      }
+    }
+    // claim or find the group slots (independent chains per item)
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      if (!hashed[it]) continue;
+      bool done = false;
+      for (unsigned long long probe = 0; probe < teff; ++probe) {
+        unsigned long long olo, ohi;
+        cas128(&tab[pos[it]].klo, 0ull, 0ull, klo[it], khi[it], &olo, &ohi);
+        if ((olo | ohi) == 0ull || (olo == klo[it] && ohi == khi[it])) {
+          done = true;
+          break;
+        }
+        if (++pos[it] == teff) pos[it] = 0;
+      }
+      if (done) {
+        const int rank = (p[it] > 0 && !fq.iso[0]) + (p[it] > 1 && !fq.iso[1]);
+        tab[pos[it]].v[rank] = w[it];
+      } else {
+        atomicOr(err, kErrProbe);
+      }
+    }
+    // children of the terms that need no merge (at most 3 per item)
+    unsigned cn[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      cn[it] = 0;
+      const size_t i = tile + size_t(it) * THREADS + threadIdx.x;
+      if (i >= N || hashed[it]) continue;
+      cn[it] = p[it] < 0 ? 1u : unsigned(fq.nnz[p[it]]);
+    }
+    const bool any = __syncthreads_or(int(cn[0] | cn[1]));
+    if (!any) continue;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      c = 0;
+      if (cn[it]) {
+        auto keep = [&](int letter, double v) {
+          if (eps > 0.0 && fabs(v) < eps) {
+            atomicAdd(&pruned[g[it]], v * v);
+            return;
+          }
+          cl[c] = letter;
+          cw[c] = v;
+          ++c;
+        };
+        if (p[it] < 0) {
+          keep(-1, w[it]);
+        } else {
+          for (int j = 0; j < fq.nnz[p[it]]; ++j) {
+            const int col = fq.col[p[it]][j];
+            keep(col, w[it] * fq.t[p[it]][col]);
+          }
+        }
+        cx0 = x[it];
+        cz0 = z[it];
+        cg0 = g[it];
+      }
+      unsigned total;
+      const unsigned off = block_excl_scan<THREADS>(c, &total, s_scan);
+      for (unsigned j = 0; j < c; ++j) {
+        uint64_t cx = cx0, cz = cz0;
+        if (cl[j] >= 0) {
+          cx = (cl[j] <= 1) ? (cx | qm) : (cx & ~qm);
+          cz = (cl[j] >= 1) ? (cz | qm) : (cz & ~qm);
+        }
+        st.x[off + j] = cx;
+        st.z[off + j] = cz;
+        st.w[off + j] = cw[j];
+        st.g[off + j] = cg0;
+      }
+      if (threadIdx.x == 0) s_base = total ? atomicAdd(n_out, (unsigned long long)total) : 0;
+      __syncthreads();
+      const size_t base = size_t(s_base);
+      if (base + total > out.cap) {
+        if (threadIdx.x == 0 && total) atomicOr(err, kErrCap);
+      } else {
+        flush_stage<THREADS>(st, total, base, out);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
+    const unsigned long long* n_in, size_t in_cap, int n, int q,
+    const __grid_constant__ FanQ fq_p, FastSlot* tab, unsigned long long tcap, double eps,
+    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+  __shared__ FanQ fq;
+  __shared__ unsigned s_scan[THREADS / 32 + 1];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned s_err;
+  __shared__ StageOut<THREADS> st;
+  if (threadIdx.x == 0) {
+    fq = fq_p;
+    s_err = *(volatile const unsigned*)err;
+  }
+  __syncthreads();
+  if (s_err) return;
+  const size_t N = min(size_t(*n_in), in_cap);
+  const unsigned long long teff = active_slots(N, tcap);
+  const uint64_t qm = 1ull << q;
+  // rank of each letter among the non-isolated rows (-1: isolated)
+  int rank_of[3];
+  {
+    int r = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rank_of[a] = fq.iso[a] ? -1 : r++;
+  }
+  const bool three = rank_of[0] >= 0 && rank_of[1] >= 0 && rank_of[2] >= 0;
+  for (unsigned long long tile = (unsigned long long)blockIdx.x * THREADS; tile < teff;
+       tile += (unsigned long long)gridDim.x * THREADS) {
+    const unsigned long long sidx = tile + threadIdx.x;
+    uint64_t x = 0, z = 0;
+    uint32_t g = 0;
+    int cl[3];
+    double cw[3];
+    unsigned c = 0;
+    if (sidx < teff) {
+      // the key and the first two weights share one 32-byte sector
+      ulonglong2* s0 = reinterpret_cast<ulonglong2*>(&tab[sidx]);
+      const ulonglong2 key = s0[0];
+      if (key.x | key.y) {
+        const ulonglong2 vv = s0[1];
+        const unsigned long long vb[3] = {vv.x, vv.y,
+                                          three ? __double_as_longlong(tab[sidx].v[2]) : kAbsent};
+        double v[3];
+        bool has[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          has[a] = rank_of[a] >= 0 && vb[rank_of[a]] != kAbsent;
+          v[a] = has[a] ? __longlong_as_double(vb[rank_of[a]]) : 0.0;
+        }
+        s0[0] = make_ulonglong2(0ull, 0ull);
+        s0[1] = make_ulonglong2(kAbsent, kAbsent);
+        if (three) tab[sidx].v[2] = __longlong_as_double(kAbsent);
+        unpack_key(key.x, key.y, n, q, &x, &z, &g);
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+          bool reached = false;
+          double acc = 0.0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (has[a] && fq.t[a][col] != 0.0) {
+              acc = reached ? acc + fq.t[a][col] * v[a] : fq.t[a][col] * v[a];
+              reached = true;
+            }
+          }
+          if (reached) {
+            if (eps > 0.0 && fabs(acc) < eps) {
+              atomicAdd(&pruned[g], acc * acc);
+            } else {
+              cl[c] = col;
+              cw[c] = acc;
+              ++c;
+            }
+          }
+        }
+      }
+    }
+    if (!__syncthreads_or(int(c))) continue;
+    unsigned total;
+    const unsigned off = block_excl_scan<THREADS>(c, &total, s_scan);
+    for (unsigned j = 0; j < c; ++j) {
+      st.x[off + j] = (cl[j] <= 1) ? (x | qm) : x;
+      st.z[off + j] = (cl[j] >= 1) ? (z | qm) : z;
+      st.w[off + j] = cw[j];
+      st.g[off + j] = g;
+    }
+    if (threadIdx.x == 0) s_base = atomicAdd(n_out, (unsigned long long)total);
+    __syncthreads();
+    const size_t base = size_t(s_base);
+    if (base + total > out.cap) {
+      if (threadIdx.x == 0) atomicOr(err, kErrCap);
+    } else {
+      flush_stage<THREADS>(st, total, base, out);
     }
     __syncthreads();
   }
@@ -809,10 +1186,39 @@ __global__ void __launch_bounds__(THREADS) k_compact_pruned(Terms in, const unsi
 // ---------------------------------------------------------------------------
 // Per-generator statistics: term count and sum of squared weights.
 
+constexpr int kStatsSmemGens = 2048;
+
+// Per-generator term count and sum of squared weights.  With at most
+// kStatsSmemGens generators each block accumulates in shared memory and adds
+// its totals once per generator; otherwise warps aggregate runs of equal ids.
 template <int W>
-__global__ void k_gen_stats(Terms t, const unsigned long long* n_in, unsigned long long* count,
-                            double* sumsq) {
+__global__ void k_gen_stats(Terms t, const unsigned long long* n_in, int G,
+                            unsigned long long* count, double* sumsq) {
+  __shared__ unsigned s_cnt[kStatsSmemGens];
+  __shared__ double s_sq[kStatsSmemGens];
   const size_t N = *n_in;
+  if (G <= kStatsSmemGens) {
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+      s_cnt[k] = 0;
+      s_sq[k] = 0.0;
+    }
+    __syncthreads();
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+         i += size_t(gridDim.x) * blockDim.x) {
+      const uint32_t g = t.g[i];
+      const double w = t.w[i];
+      atomicAdd(&s_cnt[g], 1u);
+      atomicAdd(&s_sq[g], w * w);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+      if (s_cnt[k]) {
+        atomicAdd(&count[k], (unsigned long long)s_cnt[k]);
+        atomicAdd(&sumsq[k], s_sq[k]);
+      }
+    }
+    return;
+  }
   for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
        base += size_t(gridDim.x) * blockDim.x) {
     const size_t i = base + threadIdx.x;
@@ -821,17 +1227,17 @@ __global__ void k_gen_stats(Terms t, const unsigned long long* n_in, unsigned lo
     const double w = valid ? t.w[i] : 0.0;
     const unsigned peers = __match_any_sync(0xffffffffu, g);
     const int leader = __ffs(peers) - 1;
-    double s = 0.0;
+    double sq = 0.0;
     unsigned rest = peers;
     while (rest) {
       const int src = __ffs(rest) - 1;
       rest &= rest - 1;
       const double o = __shfl_sync(peers, w, src);
-      s += o * o;
+      sq += o * o;
     }
     if (valid && int(threadIdx.x & 31) == leader) {
       atomicAdd(&count[g], (unsigned long long)__popc(peers));
-      atomicAdd(&sumsq[g], s);
+      atomicAdd(&sumsq[g], sq);
     }
   }
 }
