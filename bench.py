@@ -102,7 +102,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -222,19 +222,11 @@ def run_ours(args):
         r.free()
         del p2
 
-    # ---- max over ranks
-    tot = torch.tensor([total_ms, sum(e2e_ms), float(updates), float(e2e_updates)],
-                       dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms_max, e2e_ms_max = float(mx[0]), float(mx[1])
-        updates_all, e2e_updates_all = float(sm[2]), float(sm[3])
-    else:
-        total_ms_max, e2e_ms_max = total_ms, sum(e2e_ms)
-        updates_all, e2e_updates_all = float(updates), float(e2e_updates)
+    # ---- max of the time over ranks, sum of the work
+    from paper_2505_03307_gb300 import dist as qdist
+    total_ms_max, updates_all = qdist.reduce_step_times(total_ms, updates, device="cuda")
+    e2e_ms_max, e2e_updates_all = qdist.reduce_step_times(sum(e2e_ms), e2e_updates,
+                                                          device="cuda")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

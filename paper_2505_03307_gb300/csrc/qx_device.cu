@@ -7,6 +7,7 @@
 // blocking call on the hot path.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -125,20 +126,54 @@ struct qx_plan_device {
   };
   std::vector<Pass> passes;
   size_t max_smem = 0;
-  // Merge table of the one-word fast path, kept between propagations: every
-  // pass leaves it empty, so it is cleared only when allocated or after an
-  // aborted pass.
-  FastSlot* ftab = nullptr;
-  unsigned long long fcap = 0;
-  bool fdirty = false;
 };
+
+namespace {
+
+// Merge tables of the one-word fast path, kept for the life of the process
+// and shared by all plans: every pass leaves its table empty, so a table is
+// initialised only when it is created, grown, or after an aborted pass.  A
+// propagation holds one table exclusively (concurrent propagations on other
+// streams get other tables).
+struct FastTable {
+  int device = -1;
+  FastSlot* tab = nullptr;
+  double* v2 = nullptr;  // rank-2 weights, indexed like tab
+  unsigned long long cap = 0;
+  bool dirty = true;
+  bool busy = false;
+};
+std::mutex g_table_mutex;
+std::vector<FastTable*> g_tables;
+
+FastTable* acquire_table(int device) {
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  for (FastTable* t : g_tables)
+    if (!t->busy && t->device == device) {
+      t->busy = true;
+      return t;
+    }
+  auto* t = new (std::nothrow) FastTable;
+  if (!t) return nullptr;
+  t->device = device;
+  t->busy = true;
+  g_tables.push_back(t);
+  return t;
+}
+
+void release_table(FastTable* t) {
+  if (!t) return;
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  t->busy = false;
+}
+
+}  // namespace
 
 namespace qx {
 
 void free_plan_device(qx_plan* p) {
   if (!p || !p->dev) return;
   if (p->dev->base) cudaFree(p->dev->base);
-  if (p->dev->ftab) cudaFree(p->dev->ftab);
   delete p->dev;
   p->dev = nullptr;
 }
@@ -320,6 +355,7 @@ struct Ctx {
   size_t N = 0;
   int cslot = 0;  // which of ncnt[0], ncnt[1] holds cur's count
   Timer tm;
+  FastTable* ftab = nullptr;  // pooled merge table of the fast path (held for the call)
   void begin(int k) { tm.begin(k); }
   // after a launch: class, launches it made, algorithmic bytes
   void end(int k, int launches, uint64_t bytes) {
@@ -429,28 +465,35 @@ bool fast_eligible(int n, int W, int G) {
 }
 
 qx_status ensure_fast_table(Ctx& c, unsigned long long want) {
-  qx_plan_device* d = const_cast<qx_plan*>(c.p)->dev;
-  if (d->fcap < want) {
-    if (d->ftab) {
+  if (!c.ftab) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    c.ftab = acquire_table(dev);
+    if (!c.ftab) return fail(QX_ENOMEM, "host allocation failed");
+  }
+  FastTable* d = c.ftab;
+  if (d->cap < want) {
+    if (d->tab) {
       cudaStreamSynchronize(c.al.s);
-      cudaFree(d->ftab);
-      d->ftab = nullptr;
-      d->fcap = 0;
+      cudaFree(d->tab);
+      d->tab = nullptr;
+      d->cap = 0;
     }
     void* t = nullptr;
-    if (cudaMalloc(&t, want * sizeof(FastSlot)) != cudaSuccess) {
+    if (cudaMalloc(&t, want * (sizeof(FastSlot) + sizeof(double))) != cudaSuccess) {
       cudaGetLastError();
       return fail(QX_ENOMEM, "device allocation of the merge table failed");
     }
-    d->ftab = static_cast<FastSlot*>(t);
-    d->fcap = want;
-    d->fdirty = true;
+    d->tab = static_cast<FastSlot*>(t);
+    d->v2 = reinterpret_cast<double*>(d->tab + want);
+    d->cap = want;
+    d->dirty = true;
   }
-  if (d->fdirty) {
-    k_fast_table_init<<<grid_for(d->fcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(d->ftab,
-                                                                                     d->fcap);
+  if (d->dirty) {
+    k_fast_table_init<<<grid_for(d->cap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(d->tab, d->v2,
+                                                                                   d->cap);
     QX_TRY_CUDA(cudaGetLastError());
-    d->fdirty = false;
+    d->dirty = false;
   }
   return QX_OK;
 }
@@ -465,18 +508,18 @@ qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const Te
   if (fast) {
     // insert + children of unmerged terms, then one thread per active slot;
     // the table counts as dirty until a sync has shown the pass completed
-    qx_plan_device* d = const_cast<qx_plan*>(c.p)->dev;
-    d->fdirty = true;
+    FastTable* d = c.ftab;
+    d->dirty = true;
     c.begin(KC_INSERT);
     k_merge_insert_fast<kThreads><<<grid, kThreads, 0, c.al.s>>>(
-        c.cur.t, s.ncnt + c.cslot, c.n, f.q, f, s.mixed, d->ftab, d->fcap, eps, s.pruned, out.t,
-        s.ncnt + oslot, s.err);
+        c.cur.t, s.ncnt + c.cslot, c.n, f.q, f, s.mixed, d->tab, d->v2, d->cap, eps, s.pruned,
+        out.t, s.ncnt + oslot, s.err);
     c.tm.end();
     c.begin(KC_EMIT);
     const unsigned ggrid = grid_for(2 * std::max<size_t>(c.cur.t.cap, 512), kThreads, c.sms, 8);
     k_merge_groups_fast<kThreads><<<ggrid, kThreads, 0, c.al.s>>>(
-        s.ncnt + c.cslot, c.cur.t.cap, c.n, f.q, f, d->ftab, d->fcap, eps, s.pruned, out.t,
-        s.ncnt + oslot, s.err);
+        s.ncnt + c.cslot, c.cur.t.cap, c.n, f.q, f, d->tab, d->v2, d->cap, eps, s.pruned,
+        out.t, s.ncnt + oslot, s.err);
     c.tm.end();
   } else {
     c.begin(KC_INSERT);
@@ -499,7 +542,7 @@ qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const Te
 template <int W>
 qx_status ensure_merge_scratch(Ctx& c, bool fast, size_t n) {
   if (fast) {
-    QX_TRY(ensure_fast_table(c, std::max<unsigned long long>(1024, 2ull * n)));
+    QX_TRY(ensure_fast_table(c, std::max<unsigned long long>(1024, n + n / 4 + 1)));
     Scratch& s = c.sc;
     if (s.pcap < n) {
       c.al.put(s.payload);
@@ -547,7 +590,9 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
     TermBuf buf[2];
     qx_status st = alloc_terms(c.al, W, cap, &buf[0]);
     if (st == QX_OK) st = alloc_terms(c.al, W, cap, &buf[1]);
-    if (st == QX_OK) st = ensure_merge_scratch<W>(c, fast, cap);
+    // the fast table is sized for 3x growth: a larger pass fills it, fails its
+    // probes and is redone exactly
+    if (st == QX_OK) st = ensure_merge_scratch<W>(c, fast, fast ? std::min(cap, 3 * N0) : cap);
     if (st != QX_OK) {
       c.al.put(buf[0].base);
       c.al.put(buf[1].base);
@@ -578,7 +623,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
     if (err & kErrSpin) return fail(QX_ETIMEOUT, "a device-side wait for a group leader gave up");
     ok = !(err & (kErrProbe | kErrCap));
     if (ok) {
-      if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = false;
+      if (fast) c.ftab->dirty = false;
       // counts of every pass are not kept on the host in this mode: account
       // the passes with the final count
       c.st.alg_bytes += mq.size() * (N0 + nout) * (16 * W + 8);
@@ -596,7 +641,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
       return QX_OK;
     }
     // overflow: start over from the step's input
-    if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = true;
+    if (fast) c.ftab->dirty = true;
     c.al.put(buf[0].base);
     c.al.put(buf[1].base);
     c.cur = input;
@@ -629,7 +674,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
       c.al.put(out.base);
       return e;
     }
-    if (fast) const_cast<qx_plan*>(c.p)->dev->fdirty = false;
+    if (fast) c.ftab->dirty = false;
     if (const qx_status e = check_limits(c, nout)) {
       c.al.put(out.base);
       return e;
@@ -921,10 +966,12 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
     free_scratch(c);
     cudaStreamSynchronize(c.al.s);
     cudaGetLastError();
+    release_table(c.ftab);
     fail(s, msg);
     return s;
   }
   free_scratch(c);
+  release_table(c.ftab);
   return QX_OK;
 }
 

@@ -612,10 +612,12 @@ __global__ void __launch_bounds__(THREADS) k_merge_emit(
 // key, its children written with weights sum_p t[p][c] v_p in the fixed order
 // p = X, Y, Z, and the slot reset.  The table is empty again after every pass.
 
+// One 32-byte sector per slot: the key and the weights of ranks 0 and 1.  A
+// qubit with three non-isolated rows keeps its rank-2 weights in a side array
+// indexed like the slots.
 struct FastSlot {
   unsigned long long klo, khi;  // packed key; 0, 0 = empty
-  double v[3];                  // member weights by rank among non-isolated rows
-  unsigned long long pad[3];    // 64-byte slots: v[0], v[1] share the key's sector
+  double v[2];                  // member weights by rank among non-isolated rows
 };
 
 constexpr unsigned long long kAbsent = 0x7ff4dead7ff4deadull;  // a NaN never computed
@@ -643,6 +645,12 @@ __device__ __forceinline__ void pack_key(uint64_t x, uint64_t z, uint32_t g, int
   *hi = (z & ~qm) | (fb < 32 ? (uint64_t(g) >> fb) << n : 0ull);
 }
 
+// Slot hash of a packed key: one 64-bit multiply after folding the words.
+__device__ __forceinline__ uint64_t slot_hash(unsigned long long lo, unsigned long long hi) {
+  uint64_t h = (lo ^ (hi * 0x9e3779b97f4a7c15ull)) * 0xd6e8feb86659fd93ull;
+  return h ^ (h >> 32);
+}
+
 __device__ __forceinline__ void unpack_key(unsigned long long lo, unsigned long long hi, int n,
                                            int q, uint64_t* x, uint64_t* z, uint32_t* g) {
   const uint64_t low = (1ull << n) - 1;  // n < 64
@@ -652,20 +660,20 @@ __device__ __forceinline__ void unpack_key(unsigned long long lo, unsigned long 
   *g = uint32_t((lo >> n) | (fb < 32 ? (hi >> n) << fb : 0ull));
 }
 
-// Active slots of a pass: 1.5 times its input count (load <= 2/3 even if no
-// two terms merge), at least 1024.
+// Active slots of a pass: 1.25 times its input count (load <= 0.8 even if
+// no two terms merge), at least 1024.
 __device__ __forceinline__ unsigned long long active_slots(size_t N, unsigned long long tcap) {
-  return min(tcap, max(1024ull, (unsigned long long)N + ((unsigned long long)N >> 1)));
+  return min(tcap, max(1024ull, (unsigned long long)N + ((unsigned long long)N >> 2)));
 }
 
-static __global__ void k_fast_table_init(FastSlot* tab, unsigned long long cap) {
+static __global__ void k_fast_table_init(FastSlot* tab, double* v2, unsigned long long cap) {
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     tab[i].klo = 0ull;
     tab[i].khi = 0ull;
     tab[i].v[0] = __longlong_as_double(kAbsent);
     tab[i].v[1] = __longlong_as_double(kAbsent);
-    tab[i].v[2] = __longlong_as_double(kAbsent);
+    v2[i] = __longlong_as_double(kAbsent);
   }
 }
 
@@ -699,18 +707,18 @@ template <int THREADS>
 __device__ __forceinline__ void flush_stage(StageOut<THREADS>& st, unsigned total, size_t base,
                                             const Terms& out) {
   for (unsigned k = threadIdx.x; k < total; k += THREADS) {
-    out.x[base + k] = st.x[k];
-    out.z[base + k] = st.z[k];
-    out.w[base + k] = st.w[k];
-    out.g[base + k] = st.g[k];
+    __stcs(&out.x[base + k], st.x[k]);
+    __stcs(&out.z[base + k], st.z[k]);
+    __stcs(&out.w[base + k], st.w[k]);
+    __stcs(&out.g[base + k], st.g[k]);
   }
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
+__global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
     Terms t, const unsigned long long* n_in, int n, int q, const __grid_constant__ FanQ fq_p,
-    const uint64_t* mixed, FastSlot* tab, unsigned long long tcap, double eps, double* pruned,
-    Terms out, unsigned long long* n_out, unsigned* err) {
+    const uint64_t* mixed, FastSlot* tab, double* tab_v2, unsigned long long tcap, double eps,
+    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
   // the table is read with per-thread letter indices: a shared copy keeps
   // those reads parallel (divergent reads of kernel parameters serialise)
   __shared__ FanQ fq;
@@ -749,10 +757,11 @@ __global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
       hashed[it] = false;
       p[it] = -1;
       if (i >= N) continue;
-      x[it] = t.x[i];
-      z[it] = t.z[i];
-      g[it] = t.g[i];
-      w[it] = t.w[i];
+      // the term streams are read once: evict-first keeps the table in L2
+      x[it] = __ldcs(&t.x[i]);
+      z[it] = __ldcs(&t.z[i]);
+      g[it] = __ldcs(&t.g[i]);
+      w[it] = __ldcs(&t.w[i]);
       const int xb = int((x[it] >> q) & 1), zb = int((z[it] >> q) & 1);
       if (xb | zb) {
         p[it] = xb ? (zb ? 1 : 0) : 2;
@@ -760,8 +769,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
       }
       if (hashed[it]) {
         pack_key(x[it], z[it], g[it], n, q, &klo[it], &khi[it]);
-        const uint64_t h = fmix64(klo[it] ^ fmix64(khi[it] + 0x632be59bd9b4e019ull));
-        pos[it] = __umul64hi(h, teff);
+        pos[it] = __umul64hi(slot_hash(klo[it], khi[it]), teff);
       }
     }
     // claim or find the group slots (independent chains per item)
@@ -780,7 +788,10 @@ __global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
       }
       if (done) {
         const int rank = (p[it] > 0 && !fq.iso[0]) + (p[it] > 1 && !fq.iso[1]);
-        tab[pos[it]].v[rank] = w[it];
+        if (rank < 2)
+          tab[pos[it]].v[rank] = w[it];
+        else
+          tab_v2[pos[it]] = w[it];
       } else {
         atomicOr(err, kErrProbe);
       }
@@ -850,8 +861,8 @@ __global__ void __launch_bounds__(THREADS) k_merge_insert_fast(
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
     const unsigned long long* n_in, size_t in_cap, int n, int q,
-    const __grid_constant__ FanQ fq_p, FastSlot* tab, unsigned long long tcap, double eps,
-    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+    const __grid_constant__ FanQ fq_p, FastSlot* tab, double* tab_v2, unsigned long long tcap,
+    double eps, double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
   __shared__ FanQ fq;
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
@@ -863,8 +874,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
   }
   __syncthreads();
   if (s_err) return;
-  const size_t N = min(size_t(*n_in), in_cap);
-  const unsigned long long teff = active_slots(N, tcap);
+  const unsigned long long teff = active_slots(min(size_t(*n_in), in_cap), tcap);
   const uint64_t qm = 1ull << q;
   // rank of each letter among the non-isolated rows (-1: isolated)
   int rank_of[3];
@@ -889,7 +899,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
       if (key.x | key.y) {
         const ulonglong2 vv = s0[1];
         const unsigned long long vb[3] = {vv.x, vv.y,
-                                          three ? __double_as_longlong(tab[sidx].v[2]) : kAbsent};
+                                          three ? __double_as_longlong(tab_v2[sidx]) : kAbsent};
         double v[3];
         bool has[3];
 #pragma unroll
@@ -899,7 +909,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
         }
         s0[0] = make_ulonglong2(0ull, 0ull);
         s0[1] = make_ulonglong2(kAbsent, kAbsent);
-        if (three) tab[sidx].v[2] = __longlong_as_double(kAbsent);
+        if (three) tab_v2[sidx] = __longlong_as_double(kAbsent);
         unpack_key(key.x, key.y, n, q, &x, &z, &g);
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
