@@ -81,7 +81,9 @@ typedef void* (*qx_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*qx_free_fn)(void* ptr, void* ctx, void* stream);
 
 typedef struct {
-  int precision;        /* 64: FP64 weights (the only value accepted at present) */
+  int precision;        /* 64: FP64 weights; 32: FP32 weights with compensated products
+                           and sums (TwoProduct / TwoSum, about one float rounding per
+                           operator); strings, signs and phases stay exact either way */
   double eps;           /* pruning threshold, >= 0 (see above) */
   int gen_begin;        /* generators Z_j with gen_begin <= j < gen_end; */
   int gen_end;          /*   gen_end <= 0 means n (all generators) */

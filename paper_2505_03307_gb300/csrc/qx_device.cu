@@ -27,10 +27,10 @@ using namespace qx::dev;
       return fail(QX_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
   } while (0)
 
-#define QX_TRY(call)                  \
-  do {                                \
-    const qx_status s_ = (call);      \
-    if (s_ != QX_OK) return s_;       \
+#define QX_TRY(...)                       \
+  do {                                    \
+    const qx_status s_ = (__VA_ARGS__);   \
+    if (s_ != QX_OK) return s_;           \
   } while (0)
 
 namespace {
@@ -61,25 +61,36 @@ struct Alloc {
   }
 };
 
+// Term buffer of either weight type: x, z planes, weights, generator ids.
 struct TermBuf {
-  Terms t{};
+  uint64_t* x = nullptr;
+  uint64_t* z = nullptr;
+  void* w = nullptr;
+  uint32_t* g = nullptr;
+  size_t cap = 0;
   void* base = nullptr;
+  template <typename WT>
+  TermsT<WT> view() const {
+    return TermsT<WT>{x, z, static_cast<WT*>(w), g, cap};
+  }
 };
 
-size_t term_bytes(int W) { return size_t(16 * W + 12); }
+// bytes per term: x and z words, the weight (wtb = 8 or 4), the generator id
+size_t term_bytes(int W, int wtb) { return size_t(16 * W + wtb + 4); }
 
-qx_status alloc_terms(Alloc& al, int W, size_t cap, TermBuf* out) {
+qx_status alloc_terms(Alloc& al, int W, int wtb, size_t cap, TermBuf* out) {
   cap = std::max<size_t>(cap, 1);
-  const size_t bytes = cap * term_bytes(W) + 64;
+  const size_t bytes = cap * term_bytes(W, wtb) + 64;
   void* base = al.get(bytes);
   if (!base) return fail(QX_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   auto* x = static_cast<uint64_t*>(base);
   out->base = base;
-  out->t.x = x;
-  out->t.z = x + size_t(W) * cap;
-  out->t.w = reinterpret_cast<double*>(x + 2 * size_t(W) * cap);
-  out->t.g = reinterpret_cast<uint32_t*>(out->t.w + cap);
-  out->t.cap = cap;
+  out->x = x;
+  out->z = x + size_t(W) * cap;
+  auto* wp = reinterpret_cast<unsigned char*>(x + 2 * size_t(W) * cap);
+  out->w = wp;
+  out->g = reinterpret_cast<uint32_t*>(wp + size_t(wtb) * cap);
+  out->cap = cap;
   return QX_OK;
 }
 
@@ -245,7 +256,11 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
 FanQ to_dev(const FanQubit& f) {
   FanQ d{};
   for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) d.t[a][c] = f.t.r[a][c];
+    for (int c = 0; c < 3; ++c) {
+      d.t[a][c] = f.t.r[a][c];
+      d.th[a][c] = float(d.t[a][c]);
+      d.tl[a][c] = float(d.t[a][c] - double(d.th[a][c]));
+    }
   d.q = f.q;
   for (int a = 0; a < 3; ++a) {
     d.nnz[a] = f.nnz[a];
@@ -328,6 +343,7 @@ thread_local std::vector<cudaEvent_t> t_event_pool;
 
 struct qx_result {
   int n = 0, W = 1, G = 0;
+  int wtb = 8;  // bytes per weight: 8 (FP64) or 4 (FP32)
   size_t N = 0;
   TermBuf buf;
   Alloc al;
@@ -344,6 +360,7 @@ namespace {
 struct Ctx {
   const qx_plan* p = nullptr;
   int n = 0, W = 1, G = 0;
+  int wtb = 8;  // bytes per weight: 8 (FP64) or 4 (FP32)
   int sms = 1;
   double eps = 0.0;
   size_t budget = 0, max_terms = 0;
@@ -388,8 +405,8 @@ qx_status check_err(Ctx& c) {
 qx_status check_limits(Ctx& c, size_t terms) {
   if (c.max_terms && terms > c.max_terms)
     return fail(QX_ECAP, "term count " + std::to_string(terms) + " exceeds max_terms");
-  if (c.budget && terms * term_bytes(c.W) > c.budget)
-    return fail(QX_EBUDGET, "term storage of " + std::to_string(terms * term_bytes(c.W)) +
+  if (c.budget && terms * term_bytes(c.W, c.wtb) > c.budget)
+    return fail(QX_EBUDGET, "term storage of " + std::to_string(terms * term_bytes(c.W, c.wtb)) +
                                 " bytes exceeds hbm_budget");
   return QX_OK;
 }
@@ -402,7 +419,7 @@ void replace_cur(Ctx& c, TermBuf nb, size_t n, int slot) {
   c.st.peak_terms = std::max<uint64_t>(c.st.peak_terms, n);
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   if (dp.identity || c.N == 0) return QX_OK;
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
@@ -410,23 +427,23 @@ qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   if (dp.use_table) {
     const unsigned grid = grid_for(c.N, kThreads, c.sms, 2);
     if (dp.cb == 4)
-      k_clifford_table<W, 4><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.tab_xz,
+      k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.tab_xz,
                                                                    dp.tab_e, dp.chunks);
     else
-      k_clifford_table<W, 3><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.tab_xz,
+      k_clifford_table<W, 3, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.tab_xz,
                                                                    dp.tab_e, dp.chunks);
   } else {
     const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
-    k_clifford_ops<W><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.t, n_in, dp.ops, dp.nops);
+    k_clifford_ops<W, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.ops, dp.nops);
   }
-  c.end(KC_CLIFF, 1, 2ull * c.N * (16 * W + 8));
+  c.end(KC_CLIFF, 1, 2ull * c.N * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
   c.st.clifford_passes++;
-  c.st.alg_bytes += 2ull * c.N * (16 * W + 8);
+  c.st.alg_bytes += 2ull * c.N * (16 * W + sizeof(WT));
   return QX_OK;
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status ensure_hash(Ctx& c, size_t n) {
   Scratch& s = c.sc;
   const unsigned long long want = std::max<unsigned long long>(64, 2ull * n);
@@ -500,7 +517,7 @@ qx_status ensure_fast_table(Ctx& c, unsigned long long want) {
 
 // Insert + emit of one merge pass at fan-out qubit f.q: reads cur (count in
 // ncnt[cslot]), writes `out` (count in ncnt[oslot], reset here).  No sync.
-template <int W>
+template <int W, typename WT>
 qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const TermBuf& out,
                        int oslot, double eps) {
   Scratch& s = c.sc;
@@ -511,26 +528,26 @@ qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const Te
     FastTable* d = c.ftab;
     d->dirty = true;
     c.begin(KC_INSERT);
-    k_merge_insert_fast<kThreads><<<grid, kThreads, 0, c.al.s>>>(
-        c.cur.t, s.ncnt + c.cslot, c.n, f.q, f, s.mixed, d->tab, d->v2, d->cap, eps, s.pruned,
-        out.t, s.ncnt + oslot, s.err);
+    k_merge_insert_fast<kThreads, WT><<<grid, kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), s.ncnt + c.cslot, c.n, f.q, f, s.mixed, d->tab, d->v2, d->cap, eps, s.pruned,
+        out.view<WT>(), s.ncnt + oslot, s.err);
     c.tm.end();
     c.begin(KC_EMIT);
-    const unsigned ggrid = grid_for(2 * std::max<size_t>(c.cur.t.cap, 512), kThreads, c.sms, 8);
-    k_merge_groups_fast<kThreads><<<ggrid, kThreads, 0, c.al.s>>>(
-        s.ncnt + c.cslot, c.cur.t.cap, c.n, f.q, f, d->tab, d->v2, d->cap, eps, s.pruned,
-        out.t, s.ncnt + oslot, s.err);
+    const unsigned ggrid = grid_for(2 * std::max<size_t>(c.cur.cap, 512), kThreads, c.sms, 8);
+    k_merge_groups_fast<kThreads, WT><<<ggrid, kThreads, 0, c.al.s>>>(
+        s.ncnt + c.cslot, c.cur.cap, c.n, f.q, f, d->tab, d->v2, d->cap, eps, s.pruned,
+        out.view<WT>(), s.ncnt + oslot, s.err);
     c.tm.end();
   } else {
     c.begin(KC_INSERT);
-    k_merge_insert<W><<<grid, kThreads, 0, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed,
+    k_merge_insert<W, WT><<<grid, kThreads, 0, c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, f.q, f, s.mixed,
                                                      s.table, s.tcap, s.epoch, s.lead, s.pv,
                                                      s.pmask, s.pcap, c.spin_limit, s.err);
     c.tm.end();
     c.begin(KC_EMIT);
-    k_merge_emit<W, kThreads><<<grid, kThreads, 0, c.al.s>>>(
-        c.cur.t, s.ncnt + c.cslot, f.q, f, s.mixed, s.lead, s.pv, s.pmask, s.pcap, eps,
-        s.pruned, out.t, s.ncnt + oslot, s.err);
+    k_merge_emit<W, kThreads, WT><<<grid, kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), s.ncnt + c.cslot, f.q, f, s.mixed, s.lead, s.pv, s.pmask, s.pcap, eps,
+        s.pruned, out.view<WT>(), s.ncnt + oslot, s.err);
     c.tm.end();
   }
   QX_TRY_CUDA(cudaGetLastError());
@@ -539,7 +556,7 @@ qx_status launch_merge(Ctx& c, const FanQ& f, bool fast, unsigned grid, const Te
 }
 
 // Makes the slow path's table and the leader array hold `n` terms.
-template <int W>
+template <int W, typename WT>
 qx_status ensure_merge_scratch(Ctx& c, bool fast, size_t n) {
   if (fast) {
     QX_TRY(ensure_fast_table(c, std::max<unsigned long long>(1024, n + n / 4 + 1)));
@@ -563,13 +580,13 @@ qx_status ensure_merge_scratch(Ctx& c, bool fast, size_t n) {
     c.sc.pcap = 0;
     c.sc.payload_fast = false;
   }
-  return ensure_hash<W>(c, n);
+  return ensure_hash<W, WT>(c, n);
 }
 
 // Merge passes over the mixed qubits.  First without host syncs inside a
 // capacity arena (counts stay on the device); if an output or the table
 // overflows, the passes are redone one by one with exact counts.
-template <int W>
+template <int W, typename WT>
 qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after) {
   const bool fast = fast_eligible(c.n, W, c.G);
   const size_t N0 = c.N;
@@ -580,7 +597,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
   for (const FanQubit* f : mq) growth *= std::max({f->nnz[0], f->nnz[1], f->nnz[2]});
   size_t cap = size_t(std::min(8.0, std::max(3.0, growth)) * double(N0));
   cap = std::max<size_t>(cap, 65536);
-  if (c.budget) cap = std::min(cap, std::max(N0, c.budget / term_bytes(W)));
+  if (c.budget) cap = std::min(cap, std::max(N0, c.budget / term_bytes(W, c.wtb)));
   if (c.max_terms) cap = std::min(cap, std::max(N0, c.max_terms));
   bool ok = false;
   // pruning inside these passes accumulates pruned mass that a redo would
@@ -588,11 +605,11 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
   const bool optimistic = !(c.eps > 0.0 && !more_after);
   if (optimistic) {
     TermBuf buf[2];
-    qx_status st = alloc_terms(c.al, W, cap, &buf[0]);
-    if (st == QX_OK) st = alloc_terms(c.al, W, cap, &buf[1]);
+    qx_status st = alloc_terms(c.al, W, c.wtb, cap, &buf[0]);
+    if (st == QX_OK) st = alloc_terms(c.al, W, c.wtb, cap, &buf[1]);
     // the fast table is sized for 3x growth: a larger pass fills it, fails its
     // probes and is redone exactly
-    if (st == QX_OK) st = ensure_merge_scratch<W>(c, fast, fast ? std::min(cap, 3 * N0) : cap);
+    if (st == QX_OK) st = ensure_merge_scratch<W, WT>(c, fast, fast ? std::min(cap, 3 * N0) : cap);
     if (st != QX_OK) {
       c.al.put(buf[0].base);
       c.al.put(buf[1].base);
@@ -611,7 +628,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
         }
       }
       const int oslot = 1 - c.cslot;
-      QX_TRY(launch_merge<W>(c, f, fast, grid, buf[b], oslot, last ? c.eps : 0.0));
+      QX_TRY(launch_merge<W, WT>(c, f, fast, grid, buf[b], oslot, last ? c.eps : 0.0));
       c.cur = buf[b];
       c.cslot = oslot;
       b ^= 1;
@@ -626,10 +643,10 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
       if (fast) c.ftab->dirty = false;
       // counts of every pass are not kept on the host in this mode: account
       // the passes with the final count
-      c.st.alg_bytes += mq.size() * (N0 + nout) * (16 * W + 8);
+      c.st.alg_bytes += mq.size() * (N0 + nout) * (16 * W + sizeof(WT));
       c.st.children += mq.size() * nout;
-      c.st.kc_bytes[KC_INSERT] += mq.size() * N0 * (16 * W + 8);
-      c.st.kc_bytes[KC_EMIT] += mq.size() * (N0 + nout) * (16 * W + 8);
+      c.st.kc_bytes[KC_INSERT] += mq.size() * N0 * (16 * W + sizeof(WT));
+      c.st.kc_bytes[KC_EMIT] += mq.size() * (N0 + nout) * (16 * W + sizeof(WT));
       c.st.kc_launches[KC_INSERT] += mq.size();
       c.st.kc_launches[KC_EMIT] += mq.size();
       c.st.kernel_launches += 2 * mq.size();
@@ -658,18 +675,28 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
   for (size_t j = 0; j < mq.size(); ++j) {
     const bool last = !more_after && j + 1 == mq.size();
     const FanQ f = to_dev(*mq[j]);
-    QX_TRY(ensure_merge_scratch<W>(c, fast, c.N));
+    QX_TRY(ensure_merge_scratch<W, WT>(c, fast, c.N));
     if (!fast && ++c.sc.epoch >= 0xffffu) {
       QX_TRY_CUDA(cudaMemsetAsync(c.sc.table, 0, c.sc.tcap * sizeof(Slot), c.al.s));
       c.sc.epoch = 1;
     }
+    // at most 3 children per term; with a budget, no more than it allows (a
+    // pass that needs more stops with QX_EBUDGET)
+    size_t ocap = 3 * c.N;
+    const bool capped = c.budget && ocap * term_bytes(W, c.wtb) > c.budget;
+    if (capped) ocap = std::max<size_t>(1, c.budget / term_bytes(W, c.wtb));
     TermBuf out;
-    QX_TRY(alloc_terms(c.al, W, 3 * c.N, &out));
+    QX_TRY(alloc_terms(c.al, W, c.wtb, ocap, &out));
     const int oslot = 1 - c.cslot;
-    QX_TRY(launch_merge<W>(c, f, fast, grid_for(c.N, kThreads, c.sms, 8), out, oslot,
+    QX_TRY(launch_merge<W, WT>(c, f, fast, grid_for(c.N, kThreads, c.sms, 8), out, oslot,
                            last ? c.eps : 0.0));
     unsigned long long nout = 0;
     QX_TRY(sync_read(c, &nout, c.sc.ncnt + oslot, 8));
+    if (capped && nout > ocap) {
+      if (fast) c.ftab->dirty = true;
+      c.al.put(out.base);
+      return fail(QX_EBUDGET, "term storage of a merge pass exceeds hbm_budget");
+    }
     if (const qx_status e = check_err(c)) {
       c.al.put(out.base);
       return e;
@@ -679,16 +706,16 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
       c.al.put(out.base);
       return e;
     }
-    c.end_bytes_only(KC_INSERT, 1, uint64_t(c.N) * (16 * W + 8));
-    c.end_bytes_only(KC_EMIT, 1, (c.N + nout) * (16 * W + 8));
-    c.st.alg_bytes += (c.N + nout) * (16 * W + 8);
+    c.end_bytes_only(KC_INSERT, 1, uint64_t(c.N) * (16 * W + sizeof(WT)));
+    c.end_bytes_only(KC_EMIT, 1, (c.N + nout) * (16 * W + sizeof(WT)));
+    c.st.alg_bytes += (c.N + nout) * (16 * W + sizeof(WT));
     c.st.children += nout;
     replace_cur(c, out, nout, oslot);
   }
   return QX_OK;
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   c.st.term_updates += (ops_before + 1) * c.N;
   c.st.fan_steps++;
@@ -704,8 +731,8 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   QX_TRY_CUDA(cudaMemcpyAsync(d_niso, niso, sizeof niso, cudaMemcpyHostToDevice, c.al.s));
   QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
   c.begin(KC_MASK);
-  k_fan_mask<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-      c.cur.t, s.ncnt + c.cslot, d_niso, d_niso + kMaxWords, d_niso + 2 * kMaxWords, s.gmask);
+  k_fan_mask<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, d_niso, d_niso + kMaxWords, d_niso + 2 * kMaxWords, s.gmask);
   c.end(KC_MASK, 1, uint64_t(c.N) * 16 * W);
   QX_TRY_CUDA(cudaGetLastError());
   std::vector<unsigned long long> gm(G * 3 * W);
@@ -726,7 +753,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   if (!mq.empty())
     QX_TRY_CUDA(cudaMemcpyAsync(s.mixed, mixed.data(), G * W * 8, cudaMemcpyHostToDevice, c.al.s));
   // 2. one merge pass per qubit that needs it in some generator
-  if (!mq.empty()) QX_TRY(run_merges<W>(c, mq, !fq.empty()));
+  if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty()));
   if (fq.empty()) return QX_OK;
   // 3. one-shot expansion over the qubits that need no merge anywhere
   std::vector<FanQ> hq;
@@ -739,9 +766,9 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   if (!offs) return fail(QX_ENOMEM, "device allocation of the expansion offsets failed");
   unsigned long long* tsum = offs + c.N;
   c.begin(KC_COUNT);
-  k_expand_count<W><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, nq * sizeof(FanQ), c.al.s>>>(
-      c.cur.t, s.ncnt + c.cslot, s.fanq, nq, offs);
-  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + 8));
+  k_expand_count<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, nq * sizeof(FanQ), c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, nq, offs);
+  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + sizeof(WT)));
   c.begin(KC_SCAN);
   k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, s.ncnt + c.cslot, tsum);
   k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, s.ncnt + 2);
@@ -755,7 +782,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
     return e;
   }
   TermBuf out;
-  if (const qx_status e = alloc_terms(c.al, W, total, &out)) {
+  if (const qx_status e = alloc_terms(c.al, W, c.wtb, total, &out)) {
     c.al.put(offs);
     return e;
   }
@@ -764,29 +791,29 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
                                       (unsigned long long)c.sms * 8)));
   const size_t esmem = nq * sizeof(FanQ) + size_t(kExpTile) * 8;
   c.begin(KC_EXPAND);
-  k_expand_emit<W><<<egrid, kExpThreads, esmem, c.al.s>>>(c.cur.t, s.ncnt + c.cslot, offs, total,
-                                                         s.fanq, nq, out.t);
-  c.end(KC_EXPAND, 1, (c.N + total) * (16 * W + 8));
+  k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, offs, total,
+                                                         s.fanq, nq, out.view<WT>());
+  c.end(KC_EXPAND, 1, (c.N + total) * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
   c.al.put(offs);
   const int oslot = 1 - c.cslot;
-  c.st.alg_bytes += (c.N + total) * (16 * W + 8);
+  c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
   c.st.children += total;
   QX_TRY_CUDA(cudaMemcpyAsync(s.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
   replace_cur(c, out, total, oslot);
   if (c.eps > 0.0) {
     TermBuf kept;
-    QX_TRY(alloc_terms(c.al, W, c.N, &kept));
+    QX_TRY(alloc_terms(c.al, W, c.wtb, c.N, &kept));
     const int kslot = 1 - c.cslot;
     QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + kslot, 0, 8, c.al.s));
     c.begin(KC_COMPACT);
-    k_compact_pruned<W, kThreads><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-        c.cur.t, s.ncnt + c.cslot, c.eps, s.pruned, kept.t, s.ncnt + kslot);
+    k_compact_pruned<W, kThreads, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), s.ncnt + c.cslot, c.eps, s.pruned, kept.view<WT>(), s.ncnt + kslot);
     c.tm.end();
     QX_TRY_CUDA(cudaGetLastError());
     unsigned long long nk = 0;
     QX_TRY(sync_read(c, &nk, s.ncnt + kslot, 8));
-    c.end_bytes_only(KC_COMPACT, 1, (c.N + nk) * (16 * W + 8));
+    c.end_bytes_only(KC_COMPACT, 1, (c.N + nk) * (16 * W + sizeof(WT)));
     replace_cur(c, kept, nk, kslot);
   }
   return QX_OK;
@@ -799,7 +826,7 @@ void free_scratch(Ctx& c) {
   c.sc = Scratch();
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
                          const double* init_w, int gen_begin, qx_result** out) {
   const qx_plan* p = c.p;
@@ -825,15 +852,15 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
   // A3: initial generators
-  QX_TRY(alloc_terms(c.al, W, G, &c.cur));
+  QX_TRY(alloc_terms(c.al, W, c.wtb, G, &c.cur));
   c.N = G;
   c.cslot = 0;
   c.st.peak_terms = G;
   c.begin(KC_INIT);
   if (!init_x) {
-    k_init_z<W><<<1, 128, 0, c.al.s>>>(c.cur.t, gen_begin, c.G, c.sc.ncnt);
+    k_init_z<W, WT><<<1, 128, 0, c.al.s>>>(c.cur.view<WT>(), gen_begin, c.G, c.sc.ncnt);
   } else {
-    void* tmp = c.al.get(G * (16 * W + 8));
+    void* tmp = c.al.get(G * (16 * W + sizeof(WT)));
     if (!tmp) return fail(QX_ENOMEM, "device allocation failed");
     auto* tx = static_cast<uint64_t*>(tmp);
     auto* tz = tx + G * W;
@@ -841,19 +868,19 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     QX_TRY_CUDA(cudaMemcpyAsync(tx, init_x, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
     QX_TRY_CUDA(cudaMemcpyAsync(tz, init_z, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
     if (init_w) QX_TRY_CUDA(cudaMemcpyAsync(tw, init_w, G * 8, cudaMemcpyHostToDevice, c.al.s));
-    k_init_rows<W><<<unsigned((G + 127) / 128), 128, 0, c.al.s>>>(c.cur.t, tx, tz,
+    k_init_rows<W, WT><<<unsigned((G + 127) / 128), 128, 0, c.al.s>>>(c.cur.view<WT>(), tx, tz,
                                                                   init_w ? tw : nullptr, c.G,
                                                                   c.sc.ncnt);
     c.al.put(tmp);
   }
-  c.end(KC_INIT, 1, G * (16 * W + 8));
+  c.end(KC_INIT, 1, G * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
   // the program: Clifford passes and fan-out steps in circuit order
   for (const Step& stp : p->program) {
     if (stp.kind == kStepCliff) {
-      QX_TRY(run_pass<W>(c, p->dev->passes[stp.index]));
+      QX_TRY(run_pass<W, WT>(c, p->dev->passes[stp.index]));
     } else {
-      QX_TRY(run_fan<W>(c, p->fans[stp.index], stp.ops_before));
+      QX_TRY(run_fan<W, WT>(c, p->fans[stp.index], stp.ops_before));
     }
   }
   c.st.term_updates += p->ops_after_last_fan * c.N;
@@ -862,6 +889,7 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   if (!r) return fail(QX_ENOMEM, "host allocation failed");
   r->n = c.n;
   r->W = W;
+  r->wtb = int(sizeof(WT));
   r->G = c.G;
   r->count.assign(G, 0);
   r->sumsq.assign(G, 0.0);
@@ -876,8 +904,8 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   QX_TRY_CUDA(cudaMemsetAsync(st, 0, G * 16, c.al.s));
   c.begin(KC_STATS);
   if (c.N)
-    k_gen_stats<W><<<grid_for(c.N, kThreads * 16, c.sms, 2), kThreads, 0, c.al.s>>>(
-        c.cur.t, c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
+    k_gen_stats<W, WT><<<grid_for(c.N, kThreads * 16, c.sms, 2), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
   c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
   QX_TRY_CUDA(cudaMemcpyAsync(r->sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));
@@ -912,7 +940,8 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   qx_prop_opts opts;
   qx_default_opts(&opts);
   if (o) opts = *o;
-  if (opts.precision != 64) return fail(QX_EUNSUPPORTED, "only precision 64 is supported");
+  if (opts.precision != 64 && opts.precision != 32)
+    return fail(QX_EINVAL, "precision must be 64 or 32");
   if (!(opts.eps >= 0.0)) return fail(QX_EINVAL, "eps must be >= 0");
   if ((opts.alloc == nullptr) != (opts.free == nullptr))
     return fail(QX_EINVAL, "alloc and free must both be set or both be NULL");
@@ -948,18 +977,25 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
     static thread_local int attr_dev = -1;
     if (attr_dev != dev) {
       const int mx = 200 * 1024;
-      cudaFuncSetAttribute(k_clifford_table<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      cudaFuncSetAttribute(k_clifford_table<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      cudaFuncSetAttribute(k_clifford_table<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      cudaFuncSetAttribute(k_clifford_table<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+      cudaFuncSetAttribute(k_clifford_table<1, 4, double>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<1, 3, double>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 4, double>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 3, double>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<1, 4, float>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<1, 3, float>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 4, float>, attr, mx);
+      cudaFuncSetAttribute(k_clifford_table<2, 3, float>, attr, mx);
       attr_dev = dev;
     }
   }
   qx_status s;
   if (p->W == 1)
-    s = propagate_impl<1>(c, ix, iz, iw, gen_begin, out);
+    s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, out)
+                             : propagate_impl<1, double>(c, ix, iz, iw, gen_begin, out);
   else
-    s = propagate_impl<2>(c, ix, iz, iw, gen_begin, out);
+    s = opts.precision == 32 ? propagate_impl<2, float>(c, ix, iz, iw, gen_begin, out)
+                             : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, out);
   if (s != QX_OK) {
     const std::string msg = qx_last_error();
     c.al.put(c.cur.base);
@@ -1003,7 +1039,7 @@ void sort_canonical(int n, int W, size_t cnt, const uint64_t* px, const uint64_t
   });
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status export_impl(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
                       size_t cap, int on_device) {
   Alloc al = r->al;
@@ -1011,7 +1047,7 @@ qx_status export_impl(const qx_result* r, int gen, uint64_t* x, uint64_t* z, dou
   if (cap < cnt) return fail(QX_EINVAL, "cap is smaller than the generator's term count");
   if (cnt == 0) return QX_OK;
   TermBuf sel;
-  QX_TRY(alloc_terms(al, W, cnt, &sel));
+  QX_TRY(alloc_terms(al, W, int(sizeof(WT)), cnt, &sel));
   auto* nsel = static_cast<unsigned long long*>(al.get(8));
   if (!nsel) {
     al.put(sel.base);
@@ -1027,18 +1063,20 @@ qx_status export_impl(const qx_result* r, int gen, uint64_t* x, uint64_t* z, dou
   const unsigned long long nn = r->N;
   cudaMemcpyAsync(nall, &nn, 8, cudaMemcpyHostToDevice, al.s);
   const int sms = device_sms();
-  k_select<W, kThreads><<<grid_for(r->N, kThreads, sms, 8), kThreads, 0, al.s>>>(
-      r->buf.t, nall, uint32_t(gen), sel.t, nsel);
+  k_select<W, kThreads, WT><<<grid_for(r->N, kThreads, sms, 8), kThreads, 0, al.s>>>(
+      r->buf.view<WT>(), nall, uint32_t(gen), sel.view<WT>(), nsel);
   std::vector<uint64_t> hx(cnt * W), hz(cnt * W), px(cnt * W), pz(cnt * W);
   std::vector<double> hw(cnt), pw(cnt);
+  std::vector<WT> pwt(cnt);
   for (int k = 0; k < W; ++k) {
-    cudaMemcpyAsync(px.data() + k * cnt, sel.t.x + k * sel.t.cap, cnt * 8, cudaMemcpyDeviceToHost,
+    cudaMemcpyAsync(px.data() + k * cnt, sel.x + k * sel.cap, cnt * 8, cudaMemcpyDeviceToHost,
                     al.s);
-    cudaMemcpyAsync(pz.data() + k * cnt, sel.t.z + k * sel.t.cap, cnt * 8, cudaMemcpyDeviceToHost,
+    cudaMemcpyAsync(pz.data() + k * cnt, sel.z + k * sel.cap, cnt * 8, cudaMemcpyDeviceToHost,
                     al.s);
   }
-  cudaMemcpyAsync(pw.data(), sel.t.w, cnt * 8, cudaMemcpyDeviceToHost, al.s);
+  cudaMemcpyAsync(pwt.data(), sel.w, cnt * sizeof(WT), cudaMemcpyDeviceToHost, al.s);
   const cudaError_t e = cudaStreamSynchronize(al.s);
+  for (size_t i = 0; i < cnt; ++i) pw[i] = double(pwt[i]);
   al.put(sel.base);
   al.put(nsel);
   al.put(nall);
@@ -1073,7 +1111,7 @@ qx_status export_impl(const qx_result* r, int gen, uint64_t* x, uint64_t* z, dou
   return QX_OK;
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status ensure_index(qx_result* r) {
   if (r->index || r->N == 0) return QX_OK;
   Alloc al = r->al;
@@ -1082,8 +1120,8 @@ qx_status ensure_index(qx_result* r) {
   if (!tab) return fail(QX_ENOMEM, "device allocation of the lookup index failed");
   unsigned* err = reinterpret_cast<unsigned*>(tab + cap);
   QX_TRY_CUDA(cudaMemsetAsync(tab, 0, cap * sizeof(IndexSlot) + 16, al.s));
-  k_index_build<W><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
-      r->buf.t, r->N, tab, cap, err);
+  k_index_build<W, WT><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+      r->buf.view<WT>(), r->N, tab, cap, err);
   unsigned e = 0;
   QX_TRY_CUDA(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, al.s));
   QX_TRY_CUDA(cudaStreamSynchronize(al.s));
@@ -1096,7 +1134,7 @@ qx_status ensure_index(qx_result* r) {
   return QX_OK;
 }
 
-template <int W>
+template <int W, typename WT>
 qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t* x,
                      const uint64_t* z, double* out, int on_device) {
   for (size_t i = 0; !on_device && i < nq; ++i)
@@ -1108,7 +1146,7 @@ qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t
       std::fill(out, out + nq, 0.0);
     return QX_OK;
   }
-  QX_TRY(ensure_index<W>(r));
+  QX_TRY(ensure_index<W, WT>(r));
   Alloc al = r->al;
   const int32_t* dg = gen;
   const uint64_t *dx = x, *dz = z;
@@ -1130,8 +1168,8 @@ qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t
     dout = bo;
   }
   if (nq)
-    k_lookup<W><<<grid_for(nq, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
-        r->buf.t, r->index, r->icap, nq, dg, dx, dz, dout);
+    k_lookup<W, WT><<<grid_for(nq, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
+        r->buf.view<WT>(), r->index, r->icap, nq, dg, dx, dz, dout);
   QX_TRY_CUDA(cudaGetLastError());
   if (!on_device) {
     QX_TRY_CUDA(cudaMemcpyAsync(out, dout, nq * 8, cudaMemcpyDeviceToHost, al.s));
@@ -1202,8 +1240,11 @@ qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z
   if (!r) return fail(QX_EINVAL, "result is NULL");
   if (gen < 0 || gen >= r->G) return fail(QX_EINVAL, "generator index out of range");
   if (r->count[gen] && (!x || !z || !w)) return fail(QX_EINVAL, "NULL output buffer");
-  return r->W == 1 ? export_impl<1>(r, gen, x, z, w, cap, on_device)
-                   : export_impl<2>(r, gen, x, z, w, cap, on_device);
+  if (r->wtb == 4)
+    return r->W == 1 ? export_impl<1, float>(r, gen, x, z, w, cap, on_device)
+                     : export_impl<2, float>(r, gen, x, z, w, cap, on_device);
+  return r->W == 1 ? export_impl<1, double>(r, gen, x, z, w, cap, on_device)
+                   : export_impl<2, double>(r, gen, x, z, w, cap, on_device);
 }
 
 qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w, int32_t* gen,
@@ -1214,10 +1255,15 @@ qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w,
   if (r->N == 0) return QX_OK;
   if (!x || !z || !w || !gen) return fail(QX_EINVAL, "NULL output buffer");
   const unsigned grid = grid_for(r->N, kThreads, device_sms(), 8);
-  if (r->W == 1)
-    k_raw<1><<<grid, kThreads, 0, r->al.s>>>(r->buf.t, r->N, x, z, w, gen);
+  const auto s = r->al.s;
+  if (r->W == 1 && r->wtb == 8)
+    k_raw<1, double><<<grid, kThreads, 0, s>>>(r->buf.view<double>(), r->N, x, z, w, gen);
+  else if (r->W == 1)
+    k_raw<1, float><<<grid, kThreads, 0, s>>>(r->buf.view<float>(), r->N, x, z, w, gen);
+  else if (r->wtb == 8)
+    k_raw<2, double><<<grid, kThreads, 0, s>>>(r->buf.view<double>(), r->N, x, z, w, gen);
   else
-    k_raw<2><<<grid, kThreads, 0, r->al.s>>>(r->buf.t, r->N, x, z, w, gen);
+    k_raw<2, float><<<grid, kThreads, 0, s>>>(r->buf.view<float>(), r->N, x, z, w, gen);
   QX_TRY_CUDA(cudaGetLastError());
   QX_TRY_CUDA(cudaStreamSynchronize(r->al.s));
   return QX_OK;
@@ -1229,8 +1275,11 @@ qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, cons
   if (!r) return fail(QX_EINVAL, "result is NULL");
   if (nq && (!gen || !x || !z || !out)) return fail(QX_EINVAL, "NULL argument");
   auto* rr = const_cast<qx_result*>(r);
-  return r->W == 1 ? coeff_impl<1>(rr, nq, gen, x, z, out, on_device)
-                   : coeff_impl<2>(rr, nq, gen, x, z, out, on_device);
+  if (r->wtb == 4)
+    return r->W == 1 ? coeff_impl<1, float>(rr, nq, gen, x, z, out, on_device)
+                     : coeff_impl<2, float>(rr, nq, gen, x, z, out, on_device);
+  return r->W == 1 ? coeff_impl<1, double>(rr, nq, gen, x, z, out, on_device)
+                   : coeff_impl<2, double>(rr, nq, gen, x, z, out, on_device);
 }
 
 qx_status qx_coeff(const qx_result* r, int gen, const uint64_t* x, const uint64_t* z, double* re,
@@ -1275,12 +1324,15 @@ qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint
       cudaMemsetAsync(d, 0, nobs * 8, al.s);
       cudaMemcpyAsync(nd, &nn, 8, cudaMemcpyHostToDevice, al.s);
       if (r->N) {
-        if (r->W == 1)
-          k_ztype_sum<1><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
-              r->buf.t, nd, d);
+        const unsigned zg = grid_for(r->N, kThreads, device_sms(), 8);
+        if (r->W == 1 && r->wtb == 8)
+          k_ztype_sum<1, double><<<zg, kThreads, 0, al.s>>>(r->buf.view<double>(), nd, d);
+        else if (r->W == 1)
+          k_ztype_sum<1, float><<<zg, kThreads, 0, al.s>>>(r->buf.view<float>(), nd, d);
+        else if (r->wtb == 8)
+          k_ztype_sum<2, double><<<zg, kThreads, 0, al.s>>>(r->buf.view<double>(), nd, d);
         else
-          k_ztype_sum<2><<<grid_for(r->N, kThreads, device_sms(), 8), kThreads, 0, al.s>>>(
-              r->buf.t, nd, d);
+          k_ztype_sum<2, float><<<zg, kThreads, 0, al.s>>>(r->buf.view<float>(), nd, d);
       }
       std::vector<double> h(nobs);
       cudaMemcpyAsync(h.data(), d, nobs * 8, cudaMemcpyDeviceToHost, al.s);

@@ -17,22 +17,119 @@ constexpr unsigned kErrProbe = 1u;    // a hash table ran out of probes
 constexpr unsigned kErrSpin = 2u;     // a bounded wait gave up
 constexpr unsigned kErrCap = 4u;      // an output buffer was too small
 
-struct Terms {
+// WT: weight type, double (FP64 path) or float (FP32 path with compensated
+// arithmetic).  Strings, generator ids and signs are exact in both.
+template <typename WT>
+struct TermsT {
   uint64_t* x;
   uint64_t* z;
-  double* w;
+  WT* w;
   uint32_t* g;
   size_t cap;
+};
+using Terms = TermsT<double>;
+
+// Keeps a parameter out of template deduction (the weight converts to WT).
+template <typename T>
+struct NoDeduce {
+  using type = T;
 };
 
 // A fan-out qubit as the kernels see it.
 struct FanQ {
   double t[3][3];
+  float th[3][3], tl[3][3];  // t = th + tl to about 2^-48 (FP32 path)
   int q;
   uint8_t nnz[3];
   uint8_t col[3][3];
   uint8_t iso[3];
   uint8_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// Weight arithmetic.  FP64 weights multiply and add plainly.  FP32 weights use
+// each table entry split into float hi + lo and recover the rounding error of
+// the leading product with an FMA (TwoProduct); group sums add those pairs
+// with TwoSum (the Dot2 scheme of Ogita, Rump and Oishi), so every child or
+// merged weight carries about one float rounding whatever the cancellation.
+
+__device__ __forceinline__ double wmul(double w, const FanQ& f, int a, int c) {
+  return w * f.t[a][c];
+}
+
+__device__ __forceinline__ float wmul(float w, const FanQ& f, int a, int c) {
+  const float th = f.th[a][c];
+  const float p = w * th;
+  return p + fmaf(w, f.tl[a][c], fmaf(w, th, -p));
+}
+
+// sum over the present letters a (in the order X, Y, Z) of t[a][col] v[a];
+// *reached: some present letter reaches col
+__device__ __forceinline__ double group_sum(const FanQ& f, int col, const bool* has,
+                                            const double* v, bool* reached) {
+  bool any = false;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (has[a] && f.t[a][col] != 0.0) {
+      acc = any ? acc + f.t[a][col] * v[a] : f.t[a][col] * v[a];
+      any = true;
+    }
+  }
+  *reached = any;
+  return acc;
+}
+
+__device__ __forceinline__ float group_sum(const FanQ& f, int col, const bool* has,
+                                           const float* v, bool* reached) {
+  bool any = false;
+  float sum = 0.f, comp = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (has[a] && f.t[a][col] != 0.0) {
+      const float th = f.th[a][col];
+      const float p = v[a] * th;
+      const float pe = fmaf(v[a], th, -p) + v[a] * f.tl[a][col];
+      if (!any) {
+        sum = p;
+        comp = pe;
+        any = true;
+      } else {
+        const float t = sum + p;  // TwoSum
+        const float bp = t - sum;
+        comp += ((sum - (t - bp)) + (p - bp)) + pe;
+        sum = t;
+      }
+    }
+  }
+  *reached = any;
+  return sum + comp;
+}
+
+// Running product of a weight with table entries (the Cartesian expansion).
+template <typename WT>
+struct WProd;
+
+template <>
+struct WProd<double> {
+  double v;
+  __device__ __forceinline__ explicit WProd(double w) : v(w) {}
+  __device__ __forceinline__ void mul(const FanQ& f, int a, int c) { v *= f.t[a][c]; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+
+template <>
+struct WProd<float> {  // float-float (hi, lo) product
+  float hi, lo;
+  __device__ __forceinline__ explicit WProd(float w) : hi(w), lo(0.f) {}
+  __device__ __forceinline__ void mul(const FanQ& f, int a, int c) {
+    const float th = f.th[a][c];
+    const float p = hi * th;
+    const float e = fmaf(hi, th, -p) + fmaf(hi, f.tl[a][c], lo * th);
+    hi = p + e;  // renormalise (FastTwoSum: |p| >= |e|)
+    lo = e - (hi - p);
+  }
+  __device__ __forceinline__ float get() const { return hi + lo; }
 };
 
 // ---------------------------------------------------------------------------
@@ -97,8 +194,8 @@ __device__ __forceinline__ void set_letter(uint64_t* x, uint64_t* z, int q, int 
   z[k] = (c >= 1) ? (z[k] | m) : (z[k] & ~m);
 }
 
-template <int W>
-__device__ __forceinline__ void load_term(const Terms& t, size_t i, uint64_t* x, uint64_t* z) {
+template <int W, typename WT = double>
+__device__ __forceinline__ void load_term(const TermsT<WT>& t, size_t i, uint64_t* x, uint64_t* z) {
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     x[k] = t.x[k * t.cap + i];
@@ -106,9 +203,10 @@ __device__ __forceinline__ void load_term(const Terms& t, size_t i, uint64_t* x,
   }
 }
 
-template <int W>
-__device__ __forceinline__ void store_term(const Terms& t, size_t i, const uint64_t* x,
-                                           const uint64_t* z, double w, uint32_t g) {
+template <int W, typename WT = double>
+__device__ __forceinline__ void store_term(const TermsT<WT>& t, size_t i, const uint64_t* x,
+                                           const uint64_t* z, typename NoDeduce<WT>::type w,
+                                           uint32_t g) {
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     t.x[k * t.cap + i] = x[k];
@@ -154,8 +252,8 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total,
 // ---------------------------------------------------------------------------
 // A3: create_Z_j
 
-template <int W>
-__global__ void k_init_z(Terms t, int g0, int G, unsigned long long* n_out) {
+template <int W, typename WT = double>
+__global__ void k_init_z(TermsT<WT> t, int g0, int G, unsigned long long* n_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < G) {
     uint64_t x[W], z[W];
@@ -213,8 +311,8 @@ __device__ __forceinline__ void apply_ops(const uint32_t* ops, int nops, uint64_
   }
 }
 
-template <int W>
-__global__ void __launch_bounds__(256) k_clifford_ops(Terms t, const unsigned long long* n_in,
+template <int W, typename WT = double>
+__global__ void __launch_bounds__(256) k_clifford_ops(TermsT<WT> t, const unsigned long long* n_in,
                                                       const uint32_t* ops, int nops) {
   extern __shared__ uint32_t s_ops[];
   for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops[i];
@@ -235,8 +333,8 @@ __global__ void __launch_bounds__(256) k_clifford_ops(Terms t, const unsigned lo
   }
 }
 
-template <int W, int CB>
-__global__ void __launch_bounds__(256) k_clifford_table(Terms t, const unsigned long long* n_in,
+template <int W, int CB, typename WT = double>
+__global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsigned long long* n_in,
                                                         const uint64_t* tab_xz,
                                                         const uint8_t* tab_e, int chunks) {
   constexpr int E = 1 << (2 * CB);
@@ -310,8 +408,8 @@ __global__ void __launch_bounds__(256) k_clifford_table(Terms t, const unsigned 
 // non-isolated letters are all the same in a generator cannot make two of that
 // generator's strings collide, so it is expanded without a merge.
 
-template <int W>
-__global__ void k_fan_mask(Terms t, const unsigned long long* n_in, const uint64_t* nisoX,
+template <int W, typename WT = double>
+__global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const uint64_t* nisoX,
                            const uint64_t* nisoY, const uint64_t* nisoZ,
                            unsigned long long* gmask /* [G][3][W] */) {
   const size_t N = *n_in;
@@ -380,9 +478,9 @@ struct Slot {
   unsigned ready;          // epoch of the last publish
 };
 
-template <int W>
+template <int W, typename WT = double>
 __global__ void __launch_bounds__(256) k_merge_insert(
-    Terms t, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p,
+    TermsT<WT> t, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p,
     const uint64_t* mixed /* [G][W] */,
     Slot* table, unsigned long long tcap, unsigned epoch, uint32_t* lead, double* pv /* [3][cap] */,
     uint32_t* pmask, size_t pcap, unsigned spin_limit, unsigned* err) {
@@ -533,11 +631,11 @@ __device__ __forceinline__ unsigned merge_children(const uint64_t* x, const uint
   return n;
 }
 
-template <int W, int THREADS>
+template <int W, int THREADS, typename WT = double>
 __global__ void __launch_bounds__(THREADS) k_merge_emit(
-    Terms in, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p, const uint64_t* mixed,
+    TermsT<WT> in, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p, const uint64_t* mixed,
     const uint32_t* lead, const double* pv, const uint32_t* pmask, size_t pcap, double eps,
-    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+    double* pruned, TermsT<WT> out, unsigned long long* n_out, unsigned* err) {
   // the table is read with per-thread letter indices: a shared copy keeps
   // those reads parallel (divergent reads of kernel parameters serialise)
   __shared__ FanQ fq;
@@ -695,17 +793,17 @@ __device__ __forceinline__ size_t alloc_out(unsigned c, unsigned* s_scan,
 // One-word children of a block, staged in shared memory and written out with
 // consecutive threads on consecutive terms.  Each thread contributes up to 3
 // children (x, z, w, g) at block-local offsets from the block scan.
-template <int THREADS>
+template <int THREADS, typename WT = double>
 struct StageOut {
   uint64_t x[3 * THREADS];
   uint64_t z[3 * THREADS];
-  double w[3 * THREADS];
+  WT w[3 * THREADS];
   uint32_t g[3 * THREADS];
 };
 
-template <int THREADS>
-__device__ __forceinline__ void flush_stage(StageOut<THREADS>& st, unsigned total, size_t base,
-                                            const Terms& out) {
+template <int THREADS, typename WT = double>
+__device__ __forceinline__ void flush_stage(StageOut<THREADS, WT>& st, unsigned total, size_t base,
+                                            const TermsT<WT>& out) {
   for (unsigned k = threadIdx.x; k < total; k += THREADS) {
     __stcs(&out.x[base + k], st.x[k]);
     __stcs(&out.z[base + k], st.z[k]);
@@ -714,18 +812,18 @@ __device__ __forceinline__ void flush_stage(StageOut<THREADS>& st, unsigned tota
   }
 }
 
-template <int THREADS>
+template <int THREADS, typename WT = double>
 __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
-    Terms t, const unsigned long long* n_in, int n, int q, const __grid_constant__ FanQ fq_p,
+    TermsT<WT> t, const unsigned long long* n_in, int n, int q, const __grid_constant__ FanQ fq_p,
     const uint64_t* mixed, FastSlot* tab, double* tab_v2, unsigned long long tcap, double eps,
-    double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+    double* pruned, TermsT<WT> out, unsigned long long* n_out, unsigned* err) {
   // the table is read with per-thread letter indices: a shared copy keeps
   // those reads parallel (divergent reads of kernel parameters serialise)
   __shared__ FanQ fq;
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
   __shared__ unsigned s_err;
-  __shared__ StageOut<THREADS> st;
+  __shared__ StageOut<THREADS, WT> st;
   if (threadIdx.x == 0) {
     fq = fq_p;
     s_err = *(volatile const unsigned*)err;
@@ -742,12 +840,12 @@ __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
        tile += size_t(gridDim.x) * THREADS * ITEMS) {
     uint64_t x[ITEMS], z[ITEMS];
     uint32_t g[ITEMS];
-    double w[ITEMS];
+    WT w[ITEMS];
     int p[ITEMS];
     bool hashed[ITEMS];
     unsigned long long pos[ITEMS], klo[ITEMS], khi[ITEMS];
     int cl[3];
-    double cw[3];
+    WT cw[3];
     uint64_t cx0 = 0, cz0 = 0;
     uint32_t cg0 = 0;
     unsigned c = 0;
@@ -789,9 +887,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
       if (done) {
         const int rank = (p[it] > 0 && !fq.iso[0]) + (p[it] > 1 && !fq.iso[1]);
         if (rank < 2)
-          tab[pos[it]].v[rank] = w[it];
+          tab[pos[it]].v[rank] = double(w[it]);
         else
-          tab_v2[pos[it]] = w[it];
+          tab_v2[pos[it]] = double(w[it]);
       } else {
         atomicOr(err, kErrProbe);
       }
@@ -811,9 +909,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
     for (int it = 0; it < ITEMS; ++it) {
       c = 0;
       if (cn[it]) {
-        auto keep = [&](int letter, double v) {
-          if (eps > 0.0 && fabs(v) < eps) {
-            atomicAdd(&pruned[g[it]], v * v);
+        auto keep = [&](int letter, WT v) {
+          if (eps > 0.0 && fabs(double(v)) < eps) {
+            atomicAdd(&pruned[g[it]], double(v) * double(v));
             return;
           }
           cl[c] = letter;
@@ -825,7 +923,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
         } else {
           for (int j = 0; j < fq.nnz[p[it]]; ++j) {
             const int col = fq.col[p[it]][j];
-            keep(col, w[it] * fq.t[p[it]][col]);
+            keep(col, wmul(w[it], fq, p[it], col));
           }
         }
         cx0 = x[it];
@@ -858,16 +956,16 @@ __global__ void __launch_bounds__(THREADS, 4) k_merge_insert_fast(
   }
 }
 
-template <int THREADS>
+template <int THREADS, typename WT = double>
 __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
     const unsigned long long* n_in, size_t in_cap, int n, int q,
     const __grid_constant__ FanQ fq_p, FastSlot* tab, double* tab_v2, unsigned long long tcap,
-    double eps, double* pruned, Terms out, unsigned long long* n_out, unsigned* err) {
+    double eps, double* pruned, TermsT<WT> out, unsigned long long* n_out, unsigned* err) {
   __shared__ FanQ fq;
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
   __shared__ unsigned s_err;
-  __shared__ StageOut<THREADS> st;
+  __shared__ StageOut<THREADS, WT> st;
   if (threadIdx.x == 0) {
     fq = fq_p;
     s_err = *(volatile const unsigned*)err;
@@ -890,7 +988,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
     uint64_t x = 0, z = 0;
     uint32_t g = 0;
     int cl[3];
-    double cw[3];
+    WT cw[3];
     unsigned c = 0;
     if (sidx < teff) {
       // the key and the first two weights share one 32-byte sector
@@ -900,12 +998,12 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
         const ulonglong2 vv = s0[1];
         const unsigned long long vb[3] = {vv.x, vv.y,
                                           three ? __double_as_longlong(tab_v2[sidx]) : kAbsent};
-        double v[3];
+        WT v[3];
         bool has[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           has[a] = rank_of[a] >= 0 && vb[rank_of[a]] != kAbsent;
-          v[a] = has[a] ? __longlong_as_double(vb[rank_of[a]]) : 0.0;
+          v[a] = has[a] ? WT(__longlong_as_double(vb[rank_of[a]])) : WT(0);
         }
         s0[0] = make_ulonglong2(0ull, 0ull);
         s0[1] = make_ulonglong2(kAbsent, kAbsent);
@@ -914,17 +1012,10 @@ __global__ void __launch_bounds__(THREADS) k_merge_groups_fast(
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
           bool reached = false;
-          double acc = 0.0;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            if (has[a] && fq.t[a][col] != 0.0) {
-              acc = reached ? acc + fq.t[a][col] * v[a] : fq.t[a][col] * v[a];
-              reached = true;
-            }
-          }
+          const WT acc = group_sum(fq, col, has, v, &reached);
           if (reached) {
-            if (eps > 0.0 && fabs(acc) < eps) {
-              atomicAdd(&pruned[g], acc * acc);
+            if (eps > 0.0 && fabs(double(acc)) < eps) {
+              atomicAdd(&pruned[g], double(acc) * double(acc));
             } else {
               cl[c] = col;
               cw[c] = acc;
@@ -974,8 +1065,8 @@ __device__ __forceinline__ unsigned long long child_count(const uint64_t* x, con
   return c;
 }
 
-template <int W>
-__global__ void __launch_bounds__(256) k_expand_count(Terms t, const unsigned long long* n_in,
+template <int W, typename WT = double>
+__global__ void __launch_bounds__(256) k_expand_count(TermsT<WT> t, const unsigned long long* n_in,
                                                       const FanQ* fq_g, int nq,
                                                       unsigned long long* cnt_out) {
   extern __shared__ FanQ s_fq[];
@@ -1095,10 +1186,10 @@ constexpr int kExpTile = kExpThreads * kExpItems;
 // are located once (binary search on the offsets), their offsets staged in
 // shared memory, and each child finds its parent there; the child index within
 // the parent is decoded in mixed radix over the parent's fan-out letters.
-template <int W>
+template <int W, typename WT = double>
 __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
-    Terms in, const unsigned long long* n_in, const unsigned long long* offs,
-    unsigned long long total, const FanQ* fq_g, int nq, Terms out) {
+    TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* offs,
+    unsigned long long total, const FanQ* fq_g, int nq, TermsT<WT> out) {
   extern __shared__ unsigned char s_raw[];
   FanQ* s_fq = reinterpret_cast<FanQ*>(s_raw);
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_fq + nq);
@@ -1139,7 +1230,7 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
       unsigned long long r = c - s_off[lo];
       uint64_t x[W], z[W];
       load_term<W>(in, p, x, z);
-      double w = in.w[p];
+      WProd<WT> w(in.w[p]);
       const uint32_t g = in.g[p];
       for (int j = 0; j < nq; ++j) {
         const FanQ& f = s_fq[j];
@@ -1156,10 +1247,10 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
           r /= 3;
         }
         const int col = f.col[a][d];
-        w *= f.t[a][col];
+        w.mul(f, a, col);
         set_letter<W>(x, z, f.q, col);
       }
-      store_term<W>(out, size_t(c), x, z, w, g);
+      store_term<W>(out, size_t(c), x, z, w.get(), g);
     }
     __syncthreads();
   }
@@ -1168,16 +1259,16 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
 // Compaction after pruning inside k_expand_emit: pruned children leave holes;
 // when eps > 0 the expansion writes into a staging buffer and this kernel
 // keeps the terms whose weight passes the threshold.
-template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_compact_pruned(Terms in, const unsigned long long* n_in,
-                                                            double eps, double* pruned, Terms out,
+template <int W, int THREADS, typename WT = double>
+__global__ void __launch_bounds__(THREADS) k_compact_pruned(TermsT<WT> in, const unsigned long long* n_in,
+                                                            double eps, double* pruned, TermsT<WT> out,
                                                             unsigned long long* n_out) {
   const size_t n = *n_in;
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
   for (size_t tile = size_t(blockIdx.x) * THREADS; tile < n; tile += size_t(gridDim.x) * THREADS) {
     const size_t i = tile + threadIdx.x;
-    const double w = i < n ? in.w[i] : 0.0;
+    const double w = i < n ? double(in.w[i]) : 0.0;
     const unsigned keep = (i < n && !(fabs(w) < eps)) ? 1u : 0u;
     if (i < n && !keep) atomicAdd(&pruned[in.g[i]], w * w);
     unsigned total;
@@ -1201,8 +1292,8 @@ constexpr int kStatsSmemGens = 2048;
 // Per-generator term count and sum of squared weights.  With at most
 // kStatsSmemGens generators each block accumulates in shared memory and adds
 // its totals once per generator; otherwise warps aggregate runs of equal ids.
-template <int W>
-__global__ void k_gen_stats(Terms t, const unsigned long long* n_in, int G,
+template <int W, typename WT = double>
+__global__ void k_gen_stats(TermsT<WT> t, const unsigned long long* n_in, int G,
                             unsigned long long* count, double* sumsq) {
   __shared__ unsigned s_cnt[kStatsSmemGens];
   __shared__ double s_sq[kStatsSmemGens];
@@ -1216,7 +1307,7 @@ __global__ void k_gen_stats(Terms t, const unsigned long long* n_in, int G,
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
          i += size_t(gridDim.x) * blockDim.x) {
       const uint32_t g = t.g[i];
-      const double w = t.w[i];
+      const double w = double(t.w[i]);
       atomicAdd(&s_cnt[g], 1u);
       atomicAdd(&s_sq[g], w * w);
     }
@@ -1234,7 +1325,7 @@ __global__ void k_gen_stats(Terms t, const unsigned long long* n_in, int G,
     const size_t i = base + threadIdx.x;
     const bool valid = i < N;
     const uint32_t g = valid ? t.g[i] : 0xffffffffu;
-    const double w = valid ? t.w[i] : 0.0;
+    const double w = valid ? double(t.w[i]) : 0.0;
     const unsigned peers = __match_any_sync(0xffffffffu, g);
     const int leader = __ffs(peers) - 1;
     double sq = 0.0;
@@ -1256,8 +1347,8 @@ __global__ void k_gen_stats(Terms t, const unsigned long long* n_in, int G,
 // A7: readout.
 
 // Initial generators given as row-major strings (x, z: [G][W]) and weights.
-template <int W>
-__global__ void k_init_rows(Terms t, const uint64_t* rx, const uint64_t* rz, const double* w,
+template <int W, typename WT = double>
+__global__ void k_init_rows(TermsT<WT> t, const uint64_t* rx, const uint64_t* rz, const double* w,
                             int G, unsigned long long* n_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < G) {
@@ -1273,9 +1364,9 @@ __global__ void k_init_rows(Terms t, const uint64_t* rx, const uint64_t* rz, con
 }
 
 // Terms of one generator, compacted into out (planar, cap = its count).
-template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_select(Terms in, const unsigned long long* n_in,
-                                                    uint32_t gen, Terms out,
+template <int W, int THREADS, typename WT = double>
+__global__ void __launch_bounds__(THREADS) k_select(TermsT<WT> in, const unsigned long long* n_in,
+                                                    uint32_t gen, TermsT<WT> out,
                                                     unsigned long long* n_out) {
   __shared__ unsigned s_scan[THREADS / 32 + 1];
   __shared__ unsigned long long s_base;
@@ -1297,8 +1388,8 @@ __global__ void __launch_bounds__(THREADS) k_select(Terms in, const unsigned lon
 }
 
 // All terms in device order, row-major strings.
-template <int W>
-__global__ void k_raw(Terms in, size_t n, uint64_t* x, uint64_t* z, double* w, int32_t* g) {
+template <int W, typename WT = double>
+__global__ void k_raw(TermsT<WT> in, size_t n, uint64_t* x, uint64_t* z, double* w, int32_t* g) {
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
 #pragma unroll
@@ -1320,8 +1411,8 @@ struct IndexSlot {
   unsigned pad;
 };
 
-template <int W>
-__global__ void k_index_build(Terms t, size_t n, IndexSlot* tab, unsigned long long cap,
+template <int W, typename WT = double>
+__global__ void k_index_build(TermsT<WT> t, size_t n, IndexSlot* tab, unsigned long long cap,
                               unsigned* err) {
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
@@ -1343,8 +1434,8 @@ __global__ void k_index_build(Terms t, size_t n, IndexSlot* tab, unsigned long l
   }
 }
 
-template <int W>
-__global__ void k_lookup(Terms t, const IndexSlot* tab, unsigned long long cap, size_t nq,
+template <int W, typename WT = double>
+__global__ void k_lookup(TermsT<WT> t, const IndexSlot* tab, unsigned long long cap, size_t nq,
                          const int32_t* qg, const uint64_t* qx, const uint64_t* qz, double* out) {
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nq;
        i += size_t(gridDim.x) * blockDim.x) {
@@ -1381,15 +1472,15 @@ __global__ void k_lookup(Terms t, const IndexSlot* tab, unsigned long long cap, 
 
 // sum of weights of the Z-type strings (x = 0) per generator: <0|P|0> = 1 for
 // those and 0 for every string with an X or Y.
-template <int W>
-__global__ void k_ztype_sum(Terms t, const unsigned long long* n_in, double* out) {
+template <int W, typename WT = double>
+__global__ void k_ztype_sum(TermsT<WT> t, const unsigned long long* n_in, double* out) {
   const size_t n = *n_in;
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
     bool ztype = true;
 #pragma unroll
     for (int k = 0; k < W; ++k) ztype = ztype && t.x[k * t.cap + i] == 0;
-    if (ztype) atomicAdd(&out[t.g[i]], t.w[i]);
+    if (ztype) atomicAdd(&out[t.g[i]], double(t.w[i]));
   }
 }
 

@@ -82,6 +82,8 @@ bool fan_qubit_from_table(int q, const double* t9, FanQ* f) {
       const double v = t9[3 * a + c];
       if (!std::isfinite(v)) return false;
       f->t[a][c] = v;
+      f->th[a][c] = float(v);
+      f->tl[a][c] = float(v - double(f->th[a][c]));
       if (v != 0.0) colcount[c]++;
     }
   for (int a = 0; a < 3; ++a) {

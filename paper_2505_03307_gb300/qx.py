@@ -209,9 +209,10 @@ _torch_alloc = None
 
 
 def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeout_ms=0,
-              torch_allocator=False, kernel_timing=False):
+              torch_allocator=False, kernel_timing=False, precision=64):
     o = PropOpts()
     load_library().qx_default_opts(ctypes.byref(o))
+    o.precision = int(precision)
     o.eps = float(eps)
     if gens is not None:
         o.gen_begin, o.gen_end = int(gens[0]), int(gens[1])

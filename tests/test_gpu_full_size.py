@@ -1,0 +1,137 @@
+"""Full-size parity of the n=100 and n=16 workloads through the C ABI.
+
+* random_pairs_n100 (100,000 random H/S/CNOT + 20 RZ, eps = 1e-14): every
+  generator's string set (SHA-256 of the sorted list), term count, norm and
+  pruned mass against a digest written by the oracle
+  (tests/golden/make_random_pairs_digest.py), plus sampled exact weights; and
+  exact agreement with the oracle on a 70,000-gate prefix.
+* fan_in_deep_n100 (84M terms, 3.7 GB on the device): every coefficient is
+  sigma_i * prod_q (cos t_q or sin t_q) over the 20 fan-out qubits with a fixed
+  rest of the string, which the oracle supplies from the Clifford-only circuit;
+  sampled strings are checked one by one, all counts and norms exactly.
+* hea_n16 (4 layers of RY RZ + CX ring on 16 qubits): 2 layers against the
+  oracle; the 4-layer run exceeds the device and must stop cleanly at the
+  budget.
+"""
+import hashlib
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import compare_gen, compare_result
+from oracle import oracle as O
+from paper_2505_03307_gb300 import qx
+from paper_2505_03307_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+
+
+def test_random_pairs_n100_prefix_exact():
+    n, instrs = W.random_pairs(1)
+    pre = instrs[:70000]
+    plan = qx.group_ops(qx.load_circuit(n, pre))
+    res = qx.propagate(plan, eps=1e-14)
+    ref = O.propagate(n, pre, mode="plan", eps=1e-14, threads=os.cpu_count() or 1)
+    compare_result(res, ref)
+
+
+def test_random_pairs_n100_full_digest():
+    path = os.path.join(GOLDEN, "random_pairs_n100_digest.json")
+    dg = json.load(open(path))
+    n, instrs = W.random_pairs(1)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    res = qx.propagate(plan, eps=dg["eps"])
+    assert res.ngen == n
+    for g, d in enumerate(dg["generators"]):
+        info = res.info(g)
+        strings, w = res.export_strings(g)
+        kept = float(np.sum(w * w))
+        assert abs(kept + info["pruned_sumsq"] - 1.0) < 1e-11
+        assert abs(kept - d["sumsq"]) < 1e-11
+        if d["near_eps"] == 0:  # no rounding tie can decide pruning: exact sets
+            assert info["nterms"] == d["nterms"], g
+            h = hashlib.sha256("\n".join(strings).encode()).hexdigest()
+            assert h == d["sha256"], f"generator {g}: string set differs"
+        got = dict(zip(strings, w.tolist()))
+        for s, hx in d["sample"]:
+            want = float.fromhex(hx)
+            assert s in got, (g, s)
+            assert abs(got[s] - want) <= 1e-12 * abs(want) + 1e-13, (g, s, got[s], want)
+
+
+def test_fan_in_deep_n100_closed_form():
+    n, instrs = W.fan_in_deep(1)
+    S = 20
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    res = qx.propagate(plan)
+    assert res.nterms == 80 * 2 ** 20 + 2 * S
+    for g in range(n):
+        info = res.info(g)
+        assert info["nterms"] == (2 ** 20 if g >= S else 2)
+        assert abs(info["sumsq"] - 1.0) < 1e-10
+    # the Clifford-only circuit gives the rest of each string and its sign
+    cliff = [ins for ins in instrs if ins[0] != "RZ"]
+    base = [O.as_dict(gen) for gen in O.propagate(n, cliff, mode="gate", threads=8)]
+    thetas = {ins[1]: ins[3] for ins in instrs if ins[0] == "RZ"}
+    rng = np.random.default_rng(5)
+    for g in (20, 57, 99):
+        (bs, bw), = base[g].items()
+        assert all(bs[q] == "X" for q in range(S))
+        patterns = rng.integers(0, 2, size=(512, S))
+        strings, want = [], []
+        for pat in patterns:
+            s = "".join("XY"[b] for b in pat) + bs[S:]
+            v = bw
+            for q in range(S):
+                v *= math.cos(thetas[q]) if pat[q] == 0 else math.sin(thetas[q])
+            strings.append(s)
+            want.append(v)
+        # strings that are not in the generator: a Z on a fan-out qubit, another rest
+        absent = ["Z" + s[1:] for s in strings[:16]] + [s[:S] + ("Z" if s[S] != "Z" else "X") + s[S + 1:]
+                                                        for s in strings[:16]]
+        got = res.coeff_batch([g] * (len(strings) + len(absent)), strings + absent)
+        for s, v, x in zip(strings, want, got):
+            assert abs(x - v) <= 1e-12 * abs(v) + 1e-15, (g, s, x, v)
+        assert np.all(got[len(strings):] == 0.0)
+    for g in (0, 7, 19):
+        d = res.export_dict(g)
+        x = "".join("X" if q == g else "I" for q in range(n))
+        y = "".join("Y" if q == g else "I" for q in range(n))
+        assert d.keys() == {x, y}
+        assert abs(d[x] - math.cos(thetas[g])) < 1e-15 and abs(d[y] - math.sin(thetas[g])) < 1e-15
+
+
+def test_hea_n16_two_layers():
+    n, instrs = W.hea(1, n=16, layers=2)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    res = qx.propagate(plan, gens=(0, 4))
+    ref = O.propagate(n, instrs, mode="plan", gens=(0, 4), threads=4)
+    compare_result(res, ref)
+    assert res.info(0)["nterms"] == 349920
+
+
+def test_hea_n16_four_layers_stops_at_budget():
+    """The full 4-layer ansatz approaches 4^16 terms per generator; with a
+    8 GB budget the propagation must stop with QX_EBUDGET or QX_ECAP and
+    leave the plan usable."""
+    n, instrs = W.hea(1, n=16, layers=4)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    with pytest.raises(qx.QxError) as e:
+        qx.propagate(plan, gens=(0, 1), hbm_budget=8 << 30)
+    assert e.value.name in ("QX_EBUDGET", "QX_ECAP")
+    n2, two = W.hea(1, n=16, layers=2)
+    res = qx.propagate(qx.group_ops(qx.load_circuit(n2, two)), gens=(0, 1))
+    assert res.info(0)["nterms"] == 349920
