@@ -274,11 +274,71 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": t_wall,
     }
+    if world == 1 and args.serve_requests > 0:
+        line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(plan_updates_per_gen(qx, plan, n), budget_s=20.0)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
+    """Serving stream (n in [10, 60], 200-5000 Clifford gates, 0-14 T/RZ,
+    Poisson arrivals at rate_hz): circuits/s and p50/p99 latency of the
+    request loop (FP32 weights, admission by HBM budget), next to the same
+    circuits propagated one at a time in FP64 on the same GPU."""
+    import threading
+    import torch
+
+    reqs = W.serving_stream(7, count=count, rate_hz=rate_hz)
+    # the client's marshalling is done before the clock starts
+    arrays = [qx.instr_array(instrs) for _, _, instrs in reqs]
+    srv = qx.Server(slots=slots, hbm_budget=64 << 30, precision=32)
+    # warm-up: a few requests through every slot
+    for _, n, instrs in reqs[:2 * slots]:
+        res, _ = srv.wait(srv.submit(n, instrs))
+        res.free()
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, (at, n, _) in enumerate(reqs):
+            delay = at - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(n, arrays[k])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    for k in range(len(reqs)):
+        while tickets[k] is None:
+            time.sleep(0.0005)
+        res, ms = srv.wait(tickets[k])
+        lat.append(ms)
+        res.free()
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # one at a time, FP64, no overlap: the first baseline_count circuits
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    for _, n, instrs in reqs[:baseline_count]:
+        plan = qx.group_ops(qx.load_circuit(n, instrs))
+        r = qx.propagate(plan)
+        r.free()
+    torch.cuda.synchronize()
+    base = baseline_count / (time.perf_counter() - b0)
+    lat.sort()
+    return {"requests": count, "rate_hz": rate_hz, "slots": slots, "precision": 32,
+            "hbm_budget_bytes": 64 << 30,
+            "served_circuits_per_s": count / wall, "wall_s": wall,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "retried_exclusive": st["retried_exclusive"], "failed": st["failed"],
+            "one_at_a_time_fp64_circuits_per_s": base,
+            "one_at_a_time_sample": f"first {baseline_count} requests of the same stream"}
 
 
 def plan_updates_per_gen(qx, plan, n):
@@ -403,6 +463,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving stream (0: skip; the full stream has 10000)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

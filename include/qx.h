@@ -218,6 +218,47 @@ qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, cons
 qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint64_t* z,
                     const qx_prop_opts* o, double* out);
 
+/* ---- Serving: a request loop with continuous batching ---------------------
+ * Circuits are submitted as they arrive and propagated by `slots` host
+ * workers, each with its own CUDA stream, so the device work of several
+ * circuits overlaps; a request starts as soon as a slot is free, in arrival
+ * order.  Admission by memory follows the feasibility region of Sec. IV
+ * (term storage bounded by M_max): each slot may use hbm_budget / slots bytes
+ * of term storage; a request that needs more is run again alone with the
+ * whole budget once the other slots have drained (0 = no limit).
+ * Results are the same as qx_propagate of the circuit alone. */
+typedef struct qx_server qx_server;
+
+typedef struct {
+  int slots;          /* concurrent requests (host workers / CUDA streams), 1..256 */
+  size_t hbm_budget;  /* bytes of term storage for all slots together; 0 = unlimited */
+  int precision;      /* 64 or 32, as qx_prop_opts.precision */
+  double eps;         /* as qx_prop_opts.eps */
+  size_t max_queue;   /* waiting requests accepted; 0 = unlimited (else QX_ECAP) */
+} qx_server_opts;
+
+typedef struct {
+  uint64_t completed, failed, retried_exclusive, queued, running;
+  double p50_ms, p99_ms, max_ms;  /* latency from submission to completion */
+} qx_serve_stats;
+
+/* Defaults: 4 slots, no budget, precision 64, eps 0, unbounded queue. */
+void qx_server_default_opts(qx_server_opts* o);
+/* Starts the workers on the current device. */
+qx_status qx_server_create(const qx_server_opts* o, qx_server** out);
+/* Queues a circuit (copied; validated when it runs); *ticket identifies it. */
+qx_status qx_server_submit(qx_server* s, int n, const qx_instr* ins, size_t m, uint64_t* ticket);
+/* *done = 1 once the request has finished (with or without error). */
+qx_status qx_server_poll(qx_server* s, uint64_t ticket, int* done);
+/* Blocks until the request finishes; returns its status.  On success *out
+ * is a result owned by the caller (qx_free_result).  A ticket can be waited
+ * for once. */
+qx_status qx_server_wait(qx_server* s, uint64_t ticket, qx_result** out, double* latency_ms);
+qx_status qx_server_stats(qx_server* s, qx_serve_stats* st);
+/* Finishes running requests, fails queued ones, stops the workers and frees
+ * results that were never waited for. */
+void qx_server_destroy(qx_server* s);
+
 /* One-qubit expansion with index-based accumulation that allocates nothing.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory, for example a process whose GPU memory is

@@ -100,6 +100,9 @@ namespace qx {
 qx_status build_plan(const qx_circuit* c, qx_plan** out);
 qx_status inverse_circuit(const qx_circuit* c, qx_circuit** out);
 void free_plan_device(qx_plan* p);
+// Makes later device work on r (readout, free) use `stream` (e.g. when the
+// stream it was computed on is about to be destroyed).  r must be idle.
+void result_set_stream(qx_result* r, void* stream);
 // Applies pass `pc` to one string on the host with the same tables the device uses.
 void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z, int* sign);
 }  // namespace qx

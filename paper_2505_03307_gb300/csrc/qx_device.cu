@@ -351,9 +351,16 @@ struct qx_result {
   std::vector<unsigned long long> count;
   std::vector<double> sumsq, pruned;
   qx_prop_stats st{};
+
   IndexSlot* index = nullptr;
   unsigned long long icap = 0;
 };
+namespace qx {
+void result_set_stream(qx_result* r, void* stream) {
+  if (r) r->al.s = static_cast<cudaStream_t>(stream);
+}
+}  // namespace qx
+
 
 namespace {
 
@@ -936,6 +943,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
                            const uint64_t* ix, const uint64_t* iz, const double* iw,
                            qx_result** out) {
   clear_error();
+  cudaGetLastError();  // a stale error of an unrelated earlier call is not ours
   if (!p || !out) return fail(QX_EINVAL, "NULL argument");
   qx_prop_opts opts;
   qx_default_opts(&opts);
@@ -1237,6 +1245,7 @@ qx_status qx_result_stats(const qx_result* r, qx_prop_stats* s) {
 qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
                            size_t cap, int on_device) {
   clear_error();
+  cudaGetLastError();
   if (!r) return fail(QX_EINVAL, "result is NULL");
   if (gen < 0 || gen >= r->G) return fail(QX_EINVAL, "generator index out of range");
   if (r->count[gen] && (!x || !z || !w)) return fail(QX_EINVAL, "NULL output buffer");
@@ -1250,6 +1259,7 @@ qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z
 qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w, int32_t* gen,
                         size_t cap) {
   clear_error();
+  cudaGetLastError();
   if (!r) return fail(QX_EINVAL, "result is NULL");
   if (cap < r->N) return fail(QX_EINVAL, "cap is smaller than the result's term count");
   if (r->N == 0) return QX_OK;
@@ -1272,6 +1282,7 @@ qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w,
 qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, const uint64_t* x,
                          const uint64_t* z, double* out, int on_device) {
   clear_error();
+  cudaGetLastError();
   if (!r) return fail(QX_EINVAL, "result is NULL");
   if (nq && (!gen || !x || !z || !out)) return fail(QX_EINVAL, "NULL argument");
   auto* rr = const_cast<qx_result*>(r);

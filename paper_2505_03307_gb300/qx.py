@@ -31,7 +31,8 @@ EXPORTED = (
     "qx_propagate_from", "qx_result_shape", "qx_result_info", "qx_result_stats",
     "qx_result_export", "qx_result_raw", "qx_coeff", "qx_coeff_batch", "qx_expval",
     "qx_free_circuit", "qx_free_plan", "qx_free_result", "qx_last_error",
-    "qx_kernel_class_name", "qx_merge_qubit_static",
+    "qx_kernel_class_name", "qx_merge_qubit_static", "qx_server_default_opts", "qx_server_create",
+    "qx_server_submit", "qx_server_poll", "qx_server_wait", "qx_server_stats", "qx_server_destroy",
 )
 
 
@@ -65,6 +66,22 @@ KC_COUNT = 10
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
             "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes")
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("precision", ctypes.c_int), ("eps", ctypes.c_double),
+                ("max_queue", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("retried_exclusive", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("running", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PropStats(ctypes.Structure):
@@ -131,6 +148,15 @@ def load_library():
         "qx_free_result": (None, [_P]),
         "qx_last_error": (ctypes.c_char_p, []),
         "qx_kernel_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "qx_server_default_opts": (None, [ctypes.POINTER(ServerOpts)]),
+        "qx_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)]),
+        "qx_server_submit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Instr), _SZ,
+                                            ctypes.POINTER(ctypes.c_uint64)]),
+        "qx_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+        "qx_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P),
+                                          ctypes.POINTER(ctypes.c_double)]),
+        "qx_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+        "qx_server_destroy": (None, [_P]),
         "qx_merge_qubit_static": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.c_int, _P, _P, _P, _P,
                                                  ctypes.c_int, _DP, _P, _P, _P, _P, _SZ,
                                                  ctypes.POINTER(_SZ), _P]),
@@ -446,6 +472,71 @@ def merge_qubit_static(n, ngen, x, z, w, gen, q, table, out_x, out_z, out_w, out
         out_w.data_ptr(), out_gen.data_ptr(), int(out_w.numel()), ctypes.byref(nout),
         _stream_ptr(stream)))
     return int(nout.value)
+
+
+def _instr_array(instrs):
+    arr = (Instr * max(1, len(instrs)))()
+    for i, (g, a, b, th) in enumerate(instrs):
+        arr[i] = Instr(GATE_CODES[g], int(a), int(b), float(th))
+    arr.count = len(instrs)
+    return arr
+
+
+def instr_array(instrs):
+    """C instruction array of a circuit, for Server.submit."""
+    return _instr_array(instrs)
+
+
+class Server:
+    """Request loop with continuous batching (qx_server_*): submit circuits as
+    they arrive, wait for their results; slots propagate concurrently."""
+
+    def __init__(self, slots=4, hbm_budget=0, precision=64, eps=0.0, max_queue=0):
+        lib = load_library()
+        o = ServerOpts()
+        lib.qx_server_default_opts(ctypes.byref(o))
+        o.slots, o.hbm_budget, o.precision = int(slots), int(hbm_budget), int(precision)
+        o.eps, o.max_queue = float(eps), int(max_queue)
+        h = _P()
+        _check(lib.qx_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def submit(self, n, instrs):
+        """Queue a circuit: a list of (gate, q0, q1, theta), or an array made
+        beforehand with instr_array (no marshalling at submission time)."""
+        t = ctypes.c_uint64()
+        arr = instrs if isinstance(instrs, ctypes.Array) else _instr_array(instrs)
+        m = getattr(instrs, "count", None) if isinstance(instrs, ctypes.Array) else len(instrs)
+        _check(load_library().qx_server_submit(self._h, int(n), arr, int(m), ctypes.byref(t)))
+        self._n[t.value] = n
+        return int(t.value)
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        _check(load_library().qx_server_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket):
+        """(Result, latency in ms); raises QxError if the request failed."""
+        h = _P()
+        lat = ctypes.c_double()
+        n = self._n.pop(ticket, 0)
+        _check(load_library().qx_server_wait(self._h, ticket, ctypes.byref(h), ctypes.byref(lat)))
+        return Result(h, n), lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(load_library().qx_server_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def coeff(result: Result, g, pauli):
