@@ -218,6 +218,80 @@ qx_status qx_coeff_batch(const qx_result* r, size_t nq, const int32_t* gen, cons
 qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint64_t* z,
                     const qx_prop_opts* o, double* out);
 
+/* ---- Continuation and gradients ------------------------------------------
+ * The map that a circuit applies to the real weights of one generator is
+ * linear and orthogonal: conjugation by a unitary permutes the orthonormal
+ * basis {P / sqrt(2^n)} of Hermitian operators into another orthonormal basis
+ * (Sec. II.A, II.C).  Its transpose is therefore the map of the inverse
+ * circuit, which is what the reverse (adjoint) pass below propagates.  The
+ * gradient of a linear functional L = sum_k a_k c_{g_k}(P_k) of output weights
+ * with respect to the angle theta of a rotation (RX, RY, RZ) inside the
+ * one-qubit operator U_k (Sec. III.A) is
+ *     dL/dtheta = < M_k D, Lambda_k >,
+ * where M_k is the forward state after U_k, Lambda_k the functional pulled
+ * back to the same point through the inverse of the rest of the circuit, and
+ * D = T^T dT/dtheta acts on the rotation's wire only, T being that wire's
+ * 3x3 table of U_k (Algorithm 1).  The paper does not treat gradients; this
+ * is the adjoint of its forward map.  With eps > 0 both passes prune, and the
+ * result is the gradient of the pruned computation only approximately. */
+
+/* A result holding the given terms: nterms strings (x, z: nterms x W words),
+ * weights w and generator ids gen (0 <= gen < ngen), all in host memory.
+ * Repeated (gen, string) pairs are summed; pairs whose weight sums to
+ * exactly 0 are dropped.  precision 64 or 32 selects the weight type, as in
+ * qx_prop_opts.  Device memory comes from cudaMallocAsync on the default
+ * stream. */
+qx_status qx_result_from_terms(int n, int ngen, size_t nterms, const uint64_t* x,
+                               const uint64_t* z, const double* w, const int32_t* gen,
+                               int precision, qx_result** out);
+
+/* Propagation through plan p starting from every term of `from` (which is
+ * left unchanged); the result has from's generators.  from must have p's
+ * qubit count and the precision of *o.  gen_begin / gen_end of *o are
+ * ignored. */
+qx_status qx_propagate_result(const qx_plan* p, const qx_result* from, const qx_prop_opts* o,
+                              qx_result** out);
+
+/* For instruction `instr` of the plan's circuit, which must be RX, RY or RZ:
+ * d9 (9 doubles, row-major, (X, Y, Z) order) receives D = T^T dT/dtheta of its
+ * wire in the one-qubit operator U_k that holds it, *qubit its wire and
+ * *op_end the index one past the last instruction of U_k (the point where
+ * M_k and Lambda_k are taken).  qubit and op_end may be NULL. */
+qx_status qx_plan_derivative(const qx_plan* p, size_t instr, double* d9, int* qubit,
+                             size_t* op_end);
+
+/* out[r] = sum_g sum_P m_g(P) * sum_l D_r[p][l] * lam_{lam_gen[g]}(P with letter
+ * l on wire qubit[r]), for nrot rotations r, where p is P's letter on that
+ * wire (strings with I there contribute nothing).  lam_gen (m's generator
+ * count entries, host) pairs each generator of m with one of lam, -1 for
+ * none; d9: nrot x 9 doubles; qubit, out: nrot entries; all host memory.
+ * m and lam must have the same qubit count and precision.  Sums are taken
+ * in a fixed order: the same inputs on the same GPU give the same bits. */
+qx_status qx_adjoint_dot(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
+                         size_t nrot, const int32_t* qubit, const double* d9, double* out);
+
+/* Tape: a forward pass that keeps the term arrays at the end of every U_k
+ * that holds a rotation (per-operator checkpoints), and reverse passes over
+ * it.  ckpt_stride s >= 1 keeps every s-th of those states and recomputes
+ * the others one block at a time during the reverse pass (s = 1 keeps all;
+ * 0 picks s = ceil(sqrt(number of such operators))).
+ * qx_tape_forward propagates the generators of *o (as qx_propagate) and
+ * writes values[k] = c_{gen[k]}(P_k) for nq query strings (x, z: nq x W
+ * words; gen relative to gen_begin), all host memory. */
+typedef struct qx_tape qx_tape;
+qx_status qx_tape_forward(const qx_plan* p, const qx_prop_opts* o, int ckpt_stride, size_t nq,
+                          const int32_t* gen, const uint64_t* x, const uint64_t* z,
+                          double* values, qx_tape** out);
+/* grad[i] = dL/dtheta_i for L = sum_k a[k] values[k] and every instruction i
+ * of the circuit (0 for instructions other than RX, RY, RZ); a: nq doubles,
+ * grad: number-of-instructions doubles, host memory.  May be called any
+ * number of times with different a. */
+qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad);
+/* Number of rotations, of checkpointed operators, of states held now, and
+ * the bytes of term storage they use.  Any out pointer may be NULL. */
+qx_status qx_tape_info(const qx_tape* t, size_t* nrot, size_t* nops, size_t* held,
+                       size_t* held_bytes);
+
 /* ---- Serving: a request loop with continuous batching ---------------------
  * Circuits are submitted as they arrive and propagated by `slots` host
  * workers, each with its own CUDA stream, so the device work of several
@@ -295,6 +369,7 @@ qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const uint64_t* x,
 void qx_free_circuit(qx_circuit* c);
 void qx_free_plan(qx_plan* p);
 void qx_free_result(qx_result* r);
+void qx_free_tape(qx_tape* t);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* qx_last_error(void);

@@ -218,3 +218,63 @@ def expval(n, instrs, q):
     if rc:
         raise ValueError("oracle rejected the circuit")
     return float(out[0])
+
+
+# ---- gradients of output weights (parameter-shift rule) ----------------------
+#
+# Conjugation by a rotation exp(-i theta s / 2) maps each Pauli letter to a
+# combination whose coefficients are 1, cos(theta) or sin(theta) (the images of
+# Sec. II.C).  Every output weight c_g(P) is therefore a + b cos(theta) +
+# c sin(theta) as a function of one rotation angle, and for such a function
+# f'(theta) = (f(theta + pi/2) - f(theta - pi/2)) / 2 holds exactly.  The
+# oracle's gradient is that identity applied to two oracle propagations per
+# rotation; the paper has no gradient, so this is parity by definition of the
+# derivative.
+
+ROTATIONS = ("RX", "RY", "RZ")
+
+
+def rotation_positions(instrs):
+    """Indices of the RX / RY / RZ instructions."""
+    return [i for i, ins in enumerate(instrs) if ins[0] in ROTATIONS]
+
+
+def coeffs(n, instrs, queries, mode="plan", threads=1):
+    """c_g(P) after the circuit for queries [(g, P)] (g: generator Z_g)."""
+    gs = sorted({g for g, _ in queries})
+    if not gs:
+        return np.zeros(0)
+    lo, hi = gs[0], gs[-1] + 1
+    res = propagate(n, instrs, mode=mode, gens=(lo, hi), threads=threads)
+    maps = {g: as_dict(res[g - lo]) for g in gs}
+    return np.array([maps[g].get(p, 0.0) for g, p in queries], np.float64)
+
+
+def functional(n, instrs, queries, a, mode="plan", threads=1):
+    """L = sum_k a[k] c_{g_k}(P_k)."""
+    return float(np.dot(np.asarray(a, np.float64), coeffs(n, instrs, queries, mode, threads)))
+
+
+def grad_shift(n, instrs, queries, a, positions=None, mode="plan", threads=1, workers=1):
+    """dL/dtheta_i by the parameter-shift rule for each rotation position i
+    (default: every RX / RY / RZ).  workers > 1 runs the shifted propagations
+    in threads (the C oracle releases the interpreter lock)."""
+    if positions is None:
+        positions = rotation_positions(instrs)
+
+    def shifted(i, s):
+        g, a_, b, th = instrs[i]
+        if g not in ROTATIONS:
+            raise ValueError(f"instruction {i} is not a rotation")
+        ins = list(instrs)
+        ins[i] = (g, a_, b, th + s * np.pi / 2)
+        return functional(n, ins, queries, a, mode, threads)
+
+    jobs = [(i, s) for i in positions for s in (1, -1)]
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            vals = list(ex.map(lambda js: shifted(*js), jobs))
+    else:
+        vals = [shifted(i, s) for i, s in jobs]
+    return np.array([(vals[2 * k] - vals[2 * k + 1]) / 2 for k in range(len(positions))])

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libqx.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["qx_host.cpp", "qx_device.cu", "qx_noalloc.cu", "qx_server.cpp"]
+SOURCES = ["qx_host.cpp", "qx_device.cu", "qx_noalloc.cu", "qx_server.cpp", "qx_adjoint.cpp"]
 HEADERS = ["qx_common.h", "qx_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -835,7 +835,8 @@ void free_scratch(Ctx& c) {
 
 template <int W, typename WT>
 qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
-                         const double* init_w, int gen_begin, qx_result** out) {
+                         const double* init_w, int gen_begin, const qx_result* from,
+                         qx_result** out) {
   const qx_plan* p = c.p;
   // scratch: counters, masks, pruned mass, fan-out tables
   const size_t G = size_t(c.G);
@@ -858,13 +859,19 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   c.sc.fanq = reinterpret_cast<FanQ*>(b);
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
-  // A3: initial generators
-  QX_TRY(alloc_terms(c.al, W, c.wtb, G, &c.cur));
-  c.N = G;
+  // A3: initial generators (or every term of a given state)
+  const size_t N0 = from ? from->N : G;
+  QX_TRY(check_limits(c, N0));
+  QX_TRY(alloc_terms(c.al, W, c.wtb, N0, &c.cur));
+  c.N = N0;
   c.cslot = 0;
-  c.st.peak_terms = G;
+  c.st.peak_terms = N0;
   c.begin(KC_INIT);
-  if (!init_x) {
+  if (from) {
+    if (N0)
+      k_copy_terms<W, WT><<<grid_for(N0, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+          from->buf.view<WT>(), N0, c.cur.view<WT>(), c.sc.ncnt);
+  } else if (!init_x) {
     k_init_z<W, WT><<<1, 128, 0, c.al.s>>>(c.cur.view<WT>(), gen_begin, c.G, c.sc.ncnt);
   } else {
     void* tmp = c.al.get(G * (16 * W + sizeof(WT)));
@@ -880,7 +887,7 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
                                                                   c.sc.ncnt);
     c.al.put(tmp);
   }
-  c.end(KC_INIT, 1, G * (16 * W + sizeof(WT)));
+  c.end(KC_INIT, 1, N0 * (16 * W + sizeof(WT) + 4) * (from ? 2 : 1));
   QX_TRY_CUDA(cudaGetLastError());
   // the program: Clifford passes and fan-out steps in circuit order
   for (const Step& stp : p->program) {
@@ -941,7 +948,7 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
 
 qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, int gen_begin,
                            const uint64_t* ix, const uint64_t* iz, const double* iw,
-                           qx_result** out) {
+                           qx_result** out, const qx_result* from = nullptr) {
   clear_error();
   cudaGetLastError();  // a stale error of an unrelated earlier call is not ours
   if (!p || !out) return fail(QX_EINVAL, "NULL argument");
@@ -968,6 +975,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   c.W = p->W;
   c.G = ngen;
   c.sms = device_sms();
+  c.wtb = opts.precision == 32 ? 4 : 8;
   c.eps = opts.eps;
   c.budget = opts.hbm_budget;
   c.max_terms = opts.max_terms;
@@ -998,12 +1006,14 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
     }
   }
   qx_status s;
+  if (from && (from->n != p->n || from->wtb != (opts.precision == 32 ? 4 : 8)))
+    return fail(QX_EINVAL, "the initial state must have the plan's qubit count and precision");
   if (p->W == 1)
-    s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, out)
-                             : propagate_impl<1, double>(c, ix, iz, iw, gen_begin, out);
+    s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, from, out)
+                             : propagate_impl<1, double>(c, ix, iz, iw, gen_begin, from, out);
   else
-    s = opts.precision == 32 ? propagate_impl<2, float>(c, ix, iz, iw, gen_begin, out)
-                             : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, out);
+    s = opts.precision == 32 ? propagate_impl<2, float>(c, ix, iz, iw, gen_begin, from, out)
+                             : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, from, out);
   if (s != QX_OK) {
     const std::string msg = qx_last_error();
     c.al.put(c.cur.base);
@@ -1187,6 +1197,74 @@ qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t
   return QX_OK;
 }
 
+// <M D, Lambda> for a batch of rotations (the adjoint of one U_k's wire): the
+// smaller of the two states is iterated and the other is looked up through
+// its hash index.
+template <int W, typename WT>
+qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
+                           size_t nrot, const int32_t* qubit, const double* d9, double* out) {
+  if (m->N == 0 || lam->N == 0) {
+    std::fill(out, out + nrot, 0.0);
+    return QX_OK;
+  }
+  bool iter_m = m->N <= lam->N;
+  std::vector<int32_t> gmap;
+  if (!iter_m) {  // pairing seen from lam; needs at most one m generator per lam generator
+    gmap.assign(size_t(lam->G), -1);
+    for (int g = 0; g < m->G && !iter_m; ++g) {
+      const int32_t h = lam_gen[g];
+      if (h < 0) continue;
+      if (gmap[h] >= 0) iter_m = true;
+      gmap[h] = g;
+    }
+  }
+  if (iter_m) gmap.assign(lam_gen, lam_gen + m->G);
+  const qx_result* A = iter_m ? m : lam;
+  qx_result* B = const_cast<qx_result*>(iter_m ? lam : m);
+  QX_TRY(ensure_index<W, WT>(B));  // built and synchronised on B's stream
+  Alloc al = A->al;
+  const int sms = device_sms();
+  const unsigned grid = grid_for(A->N, kThreads, sms, 4);
+  const size_t chunk = std::min<size_t>(nrot, kAdjMaxRot);
+  const size_t bytes = size_t(A->G) * 4 + chunk * sizeof(AdjRot) + size_t(grid) * chunk * 8 +
+                       nrot * 8 + 256;
+  void* tmp = al.get(bytes);
+  if (!tmp) return fail(QX_ENOMEM, "device allocation for the adjoint product failed");
+  auto* d_rot = static_cast<AdjRot*>(tmp);
+  auto* d_part = reinterpret_cast<double*>(d_rot + chunk);
+  auto* d_out = d_part + size_t(grid) * chunk;
+  auto* d_gmap = reinterpret_cast<int32_t*>(d_out + nrot);
+  qx_status st = QX_OK;
+  auto body = [&]() -> qx_status {
+    QX_TRY_CUDA(cudaMemcpyAsync(d_gmap, gmap.data(), size_t(A->G) * 4, cudaMemcpyHostToDevice, al.s));
+    std::vector<AdjRot> hr(chunk);
+    for (size_t r0 = 0; r0 < nrot; r0 += chunk) {
+      const size_t cnt = std::min(chunk, nrot - r0);
+      for (size_t r = 0; r < cnt; ++r) {
+        hr[r] = AdjRot{};
+        hr[r].q = qubit[r0 + r];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)  // iterating lam applies D^T
+            hr[r].d[i][j] = iter_m ? d9[(r0 + r) * 9 + 3 * i + j] : d9[(r0 + r) * 9 + 3 * j + i];
+      }
+      QX_TRY_CUDA(cudaMemcpyAsync(d_rot, hr.data(), cnt * sizeof(AdjRot), cudaMemcpyHostToDevice, al.s));
+      const size_t smem = cnt * (sizeof(AdjRot) + (kThreads / 32) * 8);
+      k_adjoint_dot<W, WT><<<grid, kThreads, smem, al.s>>>(A->buf.view<WT>(), A->N, d_gmap,
+                                                           B->buf.view<WT>(), B->index, B->icap,
+                                                           d_rot, int(cnt), d_part);
+      k_adjoint_reduce<<<unsigned((cnt + 127) / 128), 128, 0, al.s>>>(d_part, int(grid), int(cnt),
+                                                                     d_out + r0);
+      QX_TRY_CUDA(cudaGetLastError());
+    }
+    QX_TRY_CUDA(cudaMemcpyAsync(out, d_out, nrot * 8, cudaMemcpyDeviceToHost, al.s));
+    QX_TRY_CUDA(cudaStreamSynchronize(al.s));
+    return QX_OK;
+  };
+  st = body();
+  al.put(tmp);
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1213,6 +1291,143 @@ qx_status qx_propagate_from(const qx_plan* p, int ngen, const uint64_t* x, const
         return fail(QX_EINVAL, "initial string has bits beyond qubit n-1");
     }
   return propagate_common(p, o, ngen, 0, x, z, w, out);
+}
+
+qx_status qx_propagate_result(const qx_plan* p, const qx_result* from, const qx_prop_opts* o,
+                              qx_result** out) {
+  clear_error();
+  if (!p || !from || !out) return fail(QX_EINVAL, "NULL argument");
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev != from->device)
+    return fail(QX_EINVAL, "the initial state lives on another device");
+  cudaGetLastError();
+  return propagate_common(p, o, from->G, 0, nullptr, nullptr, nullptr, out, from);
+}
+
+qx_status qx_result_from_terms(int n, int ngen, size_t nterms, const uint64_t* x,
+                               const uint64_t* z, const double* w, const int32_t* gen,
+                               int precision, qx_result** out) {
+  clear_error();
+  cudaGetLastError();
+  if (!out) return fail(QX_EINVAL, "out is NULL");
+  if (n < 1) return fail(QX_EINVAL, "n must be >= 1");
+  if (n > kMaxQubits) return fail(QX_EUNSUPPORTED, "n > 128 is not supported");
+  if (ngen < 1) return fail(QX_EINVAL, "ngen must be >= 1");
+  if (precision != 64 && precision != 32) return fail(QX_EINVAL, "precision must be 64 or 32");
+  if (nterms && (!x || !z || !w || !gen)) return fail(QX_EINVAL, "NULL term array");
+  if (nterms >= (size_t(1) << 32)) return fail(QX_EUNSUPPORTED, "too many terms");
+  const int W = (n + 63) / 64;
+  for (size_t i = 0; i < nterms; ++i) {
+    if (gen[i] < 0 || gen[i] >= ngen) return fail(QX_EINVAL, "generator id out of range");
+    for (int k = 0; k < W; ++k) {
+      const int hi = n - 64 * k;
+      const uint64_t mask = hi >= 64 ? ~0ull : ((1ull << hi) - 1);
+      if ((x[i * W + k] | z[i * W + k]) & ~mask)
+        return fail(QX_EINVAL, "string has bits beyond qubit n-1");
+    }
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(QX_EUNSUPPORTED, "no CUDA device is available");
+  }
+  // sum repeated (generator, string) pairs
+  std::vector<size_t> ord(nterms);
+  for (size_t i = 0; i < nterms; ++i) ord[i] = i;
+  auto key_less = [&](size_t a, size_t b) {
+    if (gen[a] != gen[b]) return gen[a] < gen[b];
+    for (int k = 0; k < W; ++k) {
+      if (x[a * W + k] != x[b * W + k]) return x[a * W + k] < x[b * W + k];
+      if (z[a * W + k] != z[b * W + k]) return z[a * W + k] < z[b * W + k];
+    }
+    return false;
+  };
+  std::stable_sort(ord.begin(), ord.end(), key_less);
+  std::vector<size_t> keep;
+  std::vector<double> sum;
+  for (size_t a = 0; a < nterms;) {
+    size_t b = a + 1;
+    double v = w[ord[a]];
+    while (b < nterms && !key_less(ord[a], ord[b])) v += w[ord[b++]];
+    if (v != 0.0) {
+      keep.push_back(ord[a]);
+      sum.push_back(v);
+    }
+    a = b;
+  }
+  const size_t N = keep.size(), cap = std::max<size_t>(N, 1);
+  const int wtb = precision == 32 ? 4 : 8;
+  std::vector<uint64_t> px(size_t(W) * cap, 0), pz(size_t(W) * cap, 0);
+  std::vector<uint32_t> pg(cap, 0);
+  std::vector<double> pw(cap, 0.0);
+  std::vector<float> pf(cap, 0.0f);
+  auto* r = new (std::nothrow) qx_result;
+  if (!r) return fail(QX_ENOMEM, "host allocation failed");
+  r->n = n;
+  r->W = W;
+  r->G = ngen;
+  r->wtb = wtb;
+  r->count.assign(size_t(ngen), 0);
+  r->sumsq.assign(size_t(ngen), 0.0);
+  r->pruned.assign(size_t(ngen), 0.0);
+  for (size_t i = 0; i < N; ++i) {
+    for (int k = 0; k < W; ++k) {
+      px[size_t(k) * cap + i] = x[keep[i] * W + k];
+      pz[size_t(k) * cap + i] = z[keep[i] * W + k];
+    }
+    pg[i] = uint32_t(gen[keep[i]]);
+    pw[i] = sum[i];
+    pf[i] = float(sum[i]);
+    const double stored = wtb == 4 ? double(pf[i]) : pw[i];
+    r->count[pg[i]]++;
+    r->sumsq[pg[i]] += stored * stored;
+  }
+  if (const qx_status e = alloc_terms(r->al, W, wtb, cap, &r->buf)) {
+    delete r;
+    return e;
+  }
+  auto upload = [&]() -> qx_status {
+    QX_TRY_CUDA(cudaMemcpyAsync(r->buf.x, px.data(), px.size() * 8, cudaMemcpyHostToDevice, r->al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(r->buf.z, pz.data(), pz.size() * 8, cudaMemcpyHostToDevice, r->al.s));
+    if (wtb == 4)
+      QX_TRY_CUDA(cudaMemcpyAsync(r->buf.w, pf.data(), cap * 4, cudaMemcpyHostToDevice, r->al.s));
+    else
+      QX_TRY_CUDA(cudaMemcpyAsync(r->buf.w, pw.data(), cap * 8, cudaMemcpyHostToDevice, r->al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(r->buf.g, pg.data(), cap * 4, cudaMemcpyHostToDevice, r->al.s));
+    QX_TRY_CUDA(cudaStreamSynchronize(r->al.s));
+    return QX_OK;
+  };
+  if (const qx_status e = upload()) {
+    r->al.put(r->buf.base);
+    delete r;
+    return e;
+  }
+  r->N = N;
+  cudaGetDevice(&r->device);
+  r->st.final_terms = N;
+  r->st.peak_terms = N;
+  *out = r;
+  return QX_OK;
+}
+
+qx_status qx_adjoint_dot(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
+                         size_t nrot, const int32_t* qubit, const double* d9, double* out) {
+  clear_error();
+  cudaGetLastError();
+  if (!m || !lam || !lam_gen) return fail(QX_EINVAL, "NULL argument");
+  if (nrot && (!qubit || !d9 || !out)) return fail(QX_EINVAL, "NULL argument");
+  if (m->n != lam->n || m->wtb != lam->wtb)
+    return fail(QX_EINVAL, "the two states differ in qubit count or precision");
+  for (int g = 0; g < m->G; ++g)
+    if (lam_gen[g] < -1 || lam_gen[g] >= lam->G) return fail(QX_EINVAL, "lam_gen out of range");
+  for (size_t r = 0; r < nrot; ++r)
+    if (qubit[r] < 0 || qubit[r] >= m->n) return fail(QX_EINVAL, "qubit out of range");
+  if (nrot == 0) return QX_OK;
+  if (m->wtb == 4)
+    return m->W == 1 ? adjoint_dot_impl<1, float>(m, lam, lam_gen, nrot, qubit, d9, out)
+                     : adjoint_dot_impl<2, float>(m, lam, lam_gen, nrot, qubit, d9, out);
+  return m->W == 1 ? adjoint_dot_impl<1, double>(m, lam, lam_gen, nrot, qubit, d9, out)
+                   : adjoint_dot_impl<2, double>(m, lam, lam_gen, nrot, qubit, d9, out);
 }
 
 qx_status qx_result_shape(const qx_result* r, int* ngen, int* nwords, size_t* nterms) {

@@ -115,6 +115,31 @@ Table3 compose(const std::vector<const qx_instr*>& gates) {
   return out;
 }
 
+// d/dtheta of a rotation table (RX, RY, RZ): (c, s) -> (-s, c).
+bool rotation_derivative(const qx_instr& g, Table3* out) {
+  int a;
+  switch (g.gate) {
+    case QX_RX: a = 0; break;
+    case QX_RY: a = 1; break;
+    case QX_RZ: a = 2; break;
+    default: return false;
+  }
+  *out = axis_rotation(a, -std::sin(g.theta), std::cos(g.theta));
+  out->r[a][a] = 0.0;  // the axis letter is fixed: its row does not depend on theta
+  return true;
+}
+
+Table3 mat_mul(const Table3& A, const Table3& B) {
+  Table3 C{};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += A.r[i][k] * B.r[k][j];
+      C.r[i][j] = acc;
+    }
+  return C;
+}
+
 enum TableKind { kIdentity, kSignedPerm, kFanOut };
 
 TableKind classify(const Table3& t, uint32_t* perm_code) {
@@ -534,6 +559,44 @@ qx_status qx_plan_clifford_apply(const qx_plan* p, size_t pass, uint64_t* x, uin
   if (!p || !x || !z || !sign) return fail(QX_EINVAL, "NULL argument");
   if (pass >= p->passes.size()) return fail(QX_EINVAL, "pass index out of range");
   host_apply_pass(p->passes[pass], p->n, p->W, x, z, sign);
+  return QX_OK;
+}
+
+qx_status qx_plan_derivative(const qx_plan* p, size_t instr, double* d9, int* qubit,
+                             size_t* op_end) {
+  clear_error();
+  if (!p || !d9) return fail(QX_EINVAL, "NULL argument");
+  if (instr >= p->ins.size()) return fail(QX_EINVAL, "instruction index out of range");
+  const qx_instr& gi = p->ins[instr];
+  Table3 dgi;
+  if (!rotation_derivative(gi, &dgi)) return fail(QX_EINVAL, "instruction is not RX, RY or RZ");
+  // the one-qubit operator (maximal run of one-qubit gates) holding it
+  size_t b = instr, e = instr + 1;
+  while (b > 0 && !two_qubit(p->ins[b - 1].gate)) --b;
+  while (e < p->ins.size() && !two_qubit(p->ins[e].gate)) ++e;
+  // T = G_1 ... G_m on this wire (row-vector composition, Algorithm 1) and
+  // its derivative with G_i replaced by dG_i/dtheta
+  Table3 T{}, dT{};
+  for (int a = 0; a < 3; ++a) T.r[a][a] = dT.r[a][a] = 1.0;
+  bool seen = false;
+  for (size_t k = b; k < e; ++k) {
+    const qx_instr& g = p->ins[k];
+    if (g.q0 != gi.q0) continue;
+    const Table3 G = gate_image(g);
+    T = mat_mul(T, G);
+    dT = mat_mul(dT, k == instr ? dgi : G);
+    seen |= k == instr;
+  }
+  if (!seen) return fail(QX_EINVAL, "internal error: gate not found in its operator");
+  // D = T^T dT acts on the operator's output: v dT = (v T)(T^T dT)
+  Table3 Tt{};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Tt.r[i][j] = T.r[j][i];
+  const Table3 D = mat_mul(Tt, dT);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) d9[3 * i + j] = D.r[i][j];
+  if (qubit) *qubit = gi.q0;
+  if (op_end) *op_end = e;
   return QX_OK;
 }
 

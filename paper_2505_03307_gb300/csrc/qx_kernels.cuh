@@ -1434,6 +1434,30 @@ __global__ void k_index_build(TermsT<WT> t, size_t n, IndexSlot* tab, unsigned l
   }
 }
 
+// Weight of (g, x, z) in the terms behind index tab, 0 when absent.
+template <int W, typename WT>
+__device__ __forceinline__ double index_find(const TermsT<WT>& t, const IndexSlot* tab,
+                                             unsigned long long cap, uint32_t g, const uint64_t* x,
+                                             const uint64_t* z) {
+  const uint64_t h = key_hash<W>(g, x, z);
+  const unsigned long long tag = h | 1ull;
+  unsigned long long pos = __umul64hi(h, cap);
+  for (unsigned long long probe = 0; probe < cap; ++probe) {
+    const unsigned long long s = tab[pos].tag;
+    if (s == 0ull) break;
+    if (s == tag) {
+      const unsigned j = tab[pos].idx;
+      bool same = t.g[j] == g;
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        same = same && t.x[k * t.cap + j] == x[k] && t.z[k * t.cap + j] == z[k];
+      if (same) return double(t.w[j]);
+    }
+    if (++pos == cap) pos = 0;
+  }
+  return 0.0;
+}
+
 template <int W, typename WT = double>
 __global__ void k_lookup(TermsT<WT> t, const IndexSlot* tab, unsigned long long cap, size_t nq,
                          const int32_t* qg, const uint64_t* qx, const uint64_t* qz, double* out) {
@@ -1445,28 +1469,7 @@ __global__ void k_lookup(TermsT<WT> t, const IndexSlot* tab, unsigned long long 
       x[k] = qx[i * W + k];
       z[k] = qz[i * W + k];
     }
-    const uint32_t g = uint32_t(qg[i]);
-    const uint64_t h = key_hash<W>(g, x, z);
-    const unsigned long long tag = h | 1ull;
-    unsigned long long pos = __umul64hi(h, cap);
-    double v = 0.0;
-    for (unsigned long long probe = 0; probe < cap; ++probe) {
-      const unsigned long long s = tab[pos].tag;
-      if (s == 0ull) break;
-      if (s == tag) {
-        const unsigned j = tab[pos].idx;
-        bool same = t.g[j] == g;
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-          same = same && t.x[k * t.cap + j] == x[k] && t.z[k * t.cap + j] == z[k];
-        if (same) {
-          v = t.w[j];
-          break;
-        }
-      }
-      if (++pos == cap) pos = 0;
-    }
-    out[i] = v;
+    out[i] = index_find<W>(t, tab, cap, uint32_t(qg[i]), x, z);
   }
 }
 
@@ -1482,6 +1485,104 @@ __global__ void k_ztype_sum(TermsT<WT> t, const unsigned long long* n_in, double
     for (int k = 0; k < W; ++k) ztype = ztype && t.x[k * t.cap + i] == 0;
     if (ztype) atomicAdd(&out[t.g[i]], double(t.w[i]));
   }
+}
+
+// ---- adjoint (reverse-mode) kernels ----------------------------------------
+
+// Derivative of one rotation, in shared memory: its wire and the 3x3 matrix D
+// applied to the letter the iterated side has there.
+struct AdjRot {
+  int q;
+  int pad;
+  double d[3][3];
+};
+
+constexpr int kAdjMaxRot = 256;  // rotations per launch
+
+// partial[block][r] = sum over this block's terms i of the iterated side a:
+//   w_i * sum_l D_r[p][l] * b_{gmap[g_i]}(string_i with letter l on wire q_r),
+// p the letter of string_i on q_r (I contributes nothing).  Terms are taken in
+// a grid-stride order that depends only on the grid; each warp reduces with
+// shuffles in a fixed tree and each block sums its warps in order, so the
+// partials are reproducible bit for bit.
+template <int W, typename WT>
+__global__ void __launch_bounds__(256) k_adjoint_dot(TermsT<WT> a, size_t na, const int32_t* gmap,
+                                                     TermsT<WT> b, const IndexSlot* tab,
+                                                     unsigned long long cap, const AdjRot* rots,
+                                                     int nrot, double* partial) {
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  AdjRot* s_rot = reinterpret_cast<AdjRot*>(adj_smem);
+  double* s_part = reinterpret_cast<double*>(s_rot + nrot);  // [warps][nrot]
+  const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < nrot; i += blockDim.x) s_rot[i] = rots[i];
+  for (int i = threadIdx.x; i < warps * nrot; i += blockDim.x) s_part[i] = 0.0;
+  __syncthreads();
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (size_t base = size_t(blockIdx.x) * blockDim.x; base < na; base += stride) {
+    const size_t i = base + threadIdx.x;
+    uint64_t x[W], z[W];
+    double w = 0.0;
+    int gb = -1;
+    if (i < na) {
+      load_term<W>(a, i, x, z);
+      gb = gmap[a.g[i]];
+      w = double(a.w[i]);
+    }
+    for (int r = 0; r < nrot; ++r) {
+      double c = 0.0;
+      if (gb >= 0) {
+        const int q = s_rot[r].q;
+        const int L = letter_at<W>(x, z, q);
+        if (L) {
+          double acc = 0.0;
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const double d = s_rot[r].d[L - 1][l];
+            if (d == 0.0) continue;
+            uint64_t xx[W], zz[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              xx[k] = x[k];
+              zz[k] = z[k];
+            }
+            set_letter<W>(xx, zz, q, l);
+            acc += d * index_find<W>(b, tab, cap, uint32_t(gb), xx, zz);
+          }
+          c = w * acc;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+      if (lane == 0) s_part[wid * nrot + r] += c;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrot; r += blockDim.x) {
+    double v = 0.0;
+    for (int k = 0; k < warps; ++k) v += s_part[k * nrot + r];
+    partial[size_t(blockIdx.x) * nrot + r] = v;
+  }
+}
+
+// out[r] = sum over blocks of partial[block][r], blocks in order.
+static __global__ void k_adjoint_reduce(const double* partial, int nblocks, int nrot, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrot) return;
+  double v = 0.0;
+  for (int k = 0; k < nblocks; ++k) v += partial[size_t(k) * nrot + r];
+  out[r] = v;
+}
+
+// Copies n terms between buffers of different capacity.
+template <int W, typename WT>
+__global__ void k_copy_terms(TermsT<WT> src, size_t n, TermsT<WT> dst, unsigned long long* n_out) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t x[W], z[W];
+    load_term<W>(src, i, x, z);
+    store_term<W>(dst, i, x, z, src.w[i], src.g[i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = (unsigned long long)n;
 }
 
 }  // namespace dev

@@ -33,6 +33,8 @@ EXPORTED = (
     "qx_free_circuit", "qx_free_plan", "qx_free_result", "qx_last_error",
     "qx_kernel_class_name", "qx_merge_qubit_static", "qx_server_default_opts", "qx_server_create",
     "qx_server_submit", "qx_server_poll", "qx_server_wait", "qx_server_stats", "qx_server_destroy",
+    "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
+    "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
 )
 
 
@@ -157,6 +159,18 @@ def load_library():
                                           ctypes.POINTER(ctypes.c_double)]),
         "qx_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
         "qx_server_destroy": (None, [_P]),
+        "qx_result_from_terms": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _SZ, _P, _P, _P, _P,
+                                                ctypes.c_int, ctypes.POINTER(_P)]),
+        "qx_propagate_result": (ctypes.c_int, [_P, _P, ctypes.POINTER(PropOpts), ctypes.POINTER(_P)]),
+        "qx_plan_derivative": (ctypes.c_int, [_P, _SZ, _DP, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(_SZ)]),
+        "qx_adjoint_dot": (ctypes.c_int, [_P, _P, _P, _SZ, _P, _P, _P]),
+        "qx_tape_forward": (ctypes.c_int, [_P, ctypes.POINTER(PropOpts), ctypes.c_int, _SZ, _P, _P,
+                                           _P, _P, ctypes.POINTER(_P)]),
+        "qx_tape_backward": (ctypes.c_int, [_P, _P, _P]),
+        "qx_tape_info": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ),
+                                        ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+        "qx_free_tape": (None, [_P]),
         "qx_merge_qubit_static": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.c_int, _P, _P, _P, _P,
                                                  ctypes.c_int, _DP, _P, _P, _P, _P, _SZ,
                                                  ctypes.POINTER(_SZ), _P]),
@@ -282,6 +296,7 @@ class Plan:
         self._h = h
         self.n = circuit.n
         self.W = words(circuit.n)
+        self.ninstr = len(circuit.instrs)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -456,6 +471,114 @@ def expval(plan: Plan, paulis, **kw):
     _check(load_library().qx_expval(plan._h, G, x.ctypes.data_as(_U64P), z.ctypes.data_as(_U64P),
                                      ctypes.byref(o), out.ctypes.data_as(_DP)))
     return out[:G]
+
+
+def paulis_to_arrays(paulis, n):
+    """Pauli strings -> (x, z) uint64 arrays of shape [len, W] (at least one row)."""
+    W = words(n)
+    x = np.zeros((max(len(paulis), 1), W), np.uint64)
+    z = np.zeros((max(len(paulis), 1), W), np.uint64)
+    for i, p in enumerate(paulis):
+        x[i], z[i] = pauli_to_words(p, n)
+    return x, z
+
+
+def result_from_terms(n, ngen, gens, paulis, weights, precision=64) -> Result:
+    """A state of `ngen` generators holding the given terms (summed where
+    repeated); see qx_result_from_terms."""
+    g = np.ascontiguousarray(gens, np.int32)
+    w = np.ascontiguousarray(weights, np.float64)
+    if not (len(g) == len(w) == len(paulis)):
+        raise ValueError("gens, paulis and weights must have the same length")
+    x, z = paulis_to_arrays(paulis, n)
+    h = _P()
+    _check(load_library().qx_result_from_terms(int(n), int(ngen), len(paulis), x.ctypes.data,
+                                                z.ctypes.data, w.ctypes.data, g.ctypes.data,
+                                                int(precision), ctypes.byref(h)))
+    return Result(h, n)
+
+
+def propagate_result(plan: Plan, start: Result, **kw) -> Result:
+    """Propagation of every term of `start` through `plan` (start is unchanged)."""
+    o = make_opts(**kw)
+    h = _P()
+    _check(load_library().qx_propagate_result(plan._h, start._h, ctypes.byref(o), ctypes.byref(h)))
+    return Result(h, plan.n)
+
+
+def plan_derivative(plan: Plan, instr):
+    """(D [3, 3], wire, op_end) of rotation instruction `instr` (qx_plan_derivative)."""
+    d = np.zeros(9, np.float64)
+    q, e = ctypes.c_int(), _SZ()
+    _check(load_library().qx_plan_derivative(plan._h, int(instr), d.ctypes.data_as(_DP),
+                                              ctypes.byref(q), ctypes.byref(e)))
+    return d.reshape(3, 3), int(q.value), int(e.value)
+
+
+def adjoint_dot(m: Result, lam: Result, lam_gen, qubits, dmats):
+    """<M D_r, Lambda> for each rotation r (qx_adjoint_dot)."""
+    lg = np.ascontiguousarray(lam_gen, np.int32)
+    if len(lg) != m.ngen:
+        raise ValueError("lam_gen needs one entry per generator of m")
+    q = np.ascontiguousarray(qubits, np.int32)
+    d = np.ascontiguousarray(dmats, np.float64).reshape(-1)
+    if d.size != 9 * len(q):
+        raise ValueError("need one 3x3 matrix per rotation")
+    out = np.zeros(max(len(q), 1), np.float64)
+    _check(load_library().qx_adjoint_dot(m._h, lam._h, lg.ctypes.data, len(q), q.ctypes.data,
+                                          d.ctypes.data, out.ctypes.data))
+    return out[:len(q)]
+
+
+class Tape:
+    """Forward pass with per-operator checkpoints and reverse passes
+    (qx_tape_forward / qx_tape_backward).
+
+    ``values`` holds c_{query_gens[k]}(paulis[k]) after the circuit (generator
+    indices relative to the ``gens`` range of the options);
+    ``backward(a)`` returns dL/dtheta_i for L = sum_k a[k] values[k] and every
+    instruction i (0 where the instruction is not a rotation)."""
+
+    def __init__(self, plan: Plan, query_gens, paulis, ckpt_stride=1, **kw):
+        self.plan = plan
+        self.m = plan.ninstr
+        g = np.ascontiguousarray(query_gens, np.int32)
+        if len(g) != len(paulis):
+            raise ValueError("query_gens and paulis must have the same length")
+        x, z = paulis_to_arrays(paulis, plan.n)
+        self.nq = len(paulis)
+        vals = np.zeros(max(self.nq, 1), np.float64)
+        o = make_opts(**kw)
+        self._h = None
+        h = _P()
+        _check(load_library().qx_tape_forward(plan._h, ctypes.byref(o), int(ckpt_stride), self.nq,
+                                               g.ctypes.data, x.ctypes.data, z.ctypes.data,
+                                               vals.ctypes.data, ctypes.byref(h)))
+        self._h = h
+        self.values = vals[:self.nq]
+
+    def backward(self, a):
+        a = np.ascontiguousarray(a, np.float64).reshape(-1)
+        if a.size != self.nq:
+            raise ValueError("need one cotangent per query")
+        grad = np.zeros(max(self.m, 1), np.float64)
+        _check(load_library().qx_tape_backward(self._h, a.ctypes.data, grad.ctypes.data))
+        return grad[:self.m]
+
+    def info(self):
+        r, k, h, b = _SZ(), _SZ(), _SZ(), _SZ()
+        _check(load_library().qx_tape_info(self._h, ctypes.byref(r), ctypes.byref(k),
+                                            ctypes.byref(h), ctypes.byref(b)))
+        return {"rotations": int(r.value), "ops": int(k.value), "held": int(h.value),
+                "held_bytes": int(b.value)}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qx_free_tape(self._h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
 
 
 def merge_qubit_static(n, ngen, x, z, w, gen, q, table, out_x, out_z, out_w, out_gen,

@@ -69,6 +69,17 @@ def random_layers(seed: int, n: int = 8, layers: int = 20, n_t: int = 10):
     return n, _insert_at_random(rng, instrs, ts)
 
 
+def rotation_layers(seed: int, n: int = 8, layers: int = 20, n_rot: int = 10):
+    """The random Clifford layers of ``random_layers`` with ``n_rot`` parametric
+    rotations in place of the T gates: RX, RY or RZ (uniform) with angle
+    U[0, 2 pi) on a uniform qubit, at uniform positions."""
+    rng = np.random.default_rng(seed + 7919)
+    _, base = random_layers(seed, n=n, layers=layers, n_t=0)
+    rots = [_g1(("RX", "RY", "RZ")[int(rng.integers(0, 3))], int(rng.integers(0, n)),
+                float(rng.uniform(0.0, 2.0 * math.pi))) for _ in range(n_rot)]
+    return n, _insert_at_random(rng, base, rots)
+
+
 def brickwork(seed: int, n: int = 50, n_gates: int = 2000, n_t: int = 16, qubits=None):
     """Random Clifford brickwork plus T gates (the n=50, 2000-gate, 16-T workload).
 
