@@ -26,6 +26,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -276,6 +278,8 @@ def run_ours(args):
     }
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
+    if world == 1 and args.adjoint_steps > 0:
+        line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(plan_updates_per_gen(qx, plan, n), budget_s=20.0)
     print(json.dumps(line), flush=True)
@@ -339,6 +343,62 @@ def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
             "retried_exclusive": st["retried_exclusive"], "failed": st["failed"],
             "one_at_a_time_fp64_circuits_per_s": base,
             "one_at_a_time_sample": f"first {baseline_count} requests of the same stream"}
+
+
+def adjoint_bench(qx, W, steps, warmup=3):
+    """Full gradient of a linear functional of output weights with respect to
+    all 64 rotation angles of the n = 16, two-layer hardware-efficient ansatz
+    (all 16 generators, 5.6M output terms; 4 queried strings per generator,
+    a ~ N(0, 1)): forward pass with checkpoints plus reverse pass, next to one
+    plain forward propagation of the same circuit."""
+    import torch
+
+    n, instrs = W.hea(1, n=16, layers=2)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    r = qx.propagate(plan)
+    qg, qp = [], []
+    for g in range(n):  # the four heaviest strings of each generator
+        strings, w = r.export_strings(g)
+        for k in np.argsort(-np.abs(w), kind="stable")[:4]:
+            qg.append(g)
+            qp.append(strings[int(k)])
+    nterms = r.nterms
+    r.free()
+    a = np.random.default_rng(12).normal(size=len(qg))
+
+    def timed(fn):
+        out = []
+        for k in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            if k >= warmup:
+                out.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(out)
+
+    fwd_ms = timed(lambda: qx.propagate(plan).free())
+    tapes = []
+
+    def make_tape():
+        if tapes:
+            tapes.pop().free()
+        tapes.append(qx.Tape(plan, qg, qp))
+
+    tape_ms = timed(make_tape)
+    tape = tapes[-1]
+    bwd_ms = timed(lambda: tape.backward(a))
+    info = tape.info()
+    tape.free()
+    grad_ms = tape_ms + bwd_ms
+    return {"workload": "hea_n16_2layers_all_generators", "rotations": info["rotations"],
+            "checkpointed_ops": info["ops"], "checkpoint_bytes": info["held_bytes"],
+            "output_terms": nterms, "queries": len(qg), "steps": steps, "warmup": warmup,
+            "forward_ms": fwd_ms, "tape_forward_ms": tape_ms, "backward_ms": bwd_ms,
+            "gradient_ms": grad_ms, "gradient_over_forward": grad_ms / fwd_ms,
+            "angle_gradients_per_s": info["rotations"] / (grad_ms / 1e3),
+            "parameter_shift_equivalent_ms": 2 * info["rotations"] * fwd_ms,
+            "timing": "host clock around synchronised calls, median of steps"}
 
 
 def plan_updates_per_gen(qx, plan, n):
@@ -466,6 +526,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream (0: skip; the full stream has 10000)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
+    ap.add_argument("--adjoint-steps", type=int, default=5,
+                    help="timed steps of the gradient leg (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -1224,8 +1224,11 @@ qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32
   QX_TRY(ensure_index<W, WT>(B));  // built and synchronised on B's stream
   Alloc al = A->al;
   const int sms = device_sms();
-  const unsigned grid = grid_for(A->N, kThreads, sms, 4);
+  const unsigned grid = grid_for(A->N, kThreads, sms, 4);  // term tiles (grid x)
   const size_t chunk = std::min<size_t>(nrot, kAdjMaxRot);
+  // rotation groups (grid y): enough blocks for 4 per SM when the iterated
+  // side has few tiles, one group (every term read once) when it has many
+  const size_t want_groups = (size_t(4) * sms + grid - 1) / grid;
   const size_t bytes = size_t(A->G) * 4 + chunk * sizeof(AdjRot) + size_t(grid) * chunk * 8 +
                        nrot * 8 + 256;
   void* tmp = al.get(bytes);
@@ -1248,10 +1251,13 @@ qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32
             hr[r].d[i][j] = iter_m ? d9[(r0 + r) * 9 + 3 * i + j] : d9[(r0 + r) * 9 + 3 * j + i];
       }
       QX_TRY_CUDA(cudaMemcpyAsync(d_rot, hr.data(), cnt * sizeof(AdjRot), cudaMemcpyHostToDevice, al.s));
-      const size_t smem = cnt * (sizeof(AdjRot) + (kThreads / 32) * 8);
-      k_adjoint_dot<W, WT><<<grid, kThreads, smem, al.s>>>(A->buf.view<WT>(), A->N, d_gmap,
-                                                           B->buf.view<WT>(), B->index, B->icap,
-                                                           d_rot, int(cnt), d_part);
+      const size_t groups = std::max<size_t>(1, std::min(cnt, want_groups));
+      const size_t rb = (cnt + groups - 1) / groups;
+      const dim3 g2(grid, unsigned((cnt + rb - 1) / rb));
+      const size_t smem = rb * (sizeof(AdjRot) + (kThreads / 32) * 8);
+      k_adjoint_dot<W, WT><<<g2, kThreads, smem, al.s>>>(A->buf.view<WT>(), A->N, d_gmap,
+                                                         B->buf.view<WT>(), B->index, B->icap,
+                                                         d_rot, int(cnt), int(rb), d_part);
       k_adjoint_reduce<<<unsigned((cnt + 127) / 128), 128, 0, al.s>>>(d_part, int(grid), int(cnt),
                                                                      d_out + r0);
       QX_TRY_CUDA(cudaGetLastError());

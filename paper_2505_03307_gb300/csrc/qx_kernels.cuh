@@ -1289,36 +1289,25 @@ __global__ void __launch_bounds__(THREADS) k_compact_pruned(TermsT<WT> in, const
 
 constexpr int kStatsSmemGens = 2048;
 
-// Per-generator term count and sum of squared weights.  With at most
-// kStatsSmemGens generators each block accumulates in shared memory and adds
-// its totals once per generator; otherwise warps aggregate runs of equal ids.
+// Per-generator term count and sum of squared weights.  Each warp first
+// combines the lanes that hold the same generator id (one atomic per distinct
+// id and warp instead of one per term, which matters when few generators
+// share all terms).  With at most kStatsSmemGens generators the warp leaders
+// add into shared memory and each block adds its totals once per generator;
+// otherwise they add into global memory directly.
 template <int W, typename WT = double>
 __global__ void k_gen_stats(TermsT<WT> t, const unsigned long long* n_in, int G,
                             unsigned long long* count, double* sumsq) {
   __shared__ unsigned s_cnt[kStatsSmemGens];
   __shared__ double s_sq[kStatsSmemGens];
   const size_t N = *n_in;
-  if (G <= kStatsSmemGens) {
+  const bool shared = G <= kStatsSmemGens;
+  if (shared) {
     for (int k = threadIdx.x; k < G; k += blockDim.x) {
       s_cnt[k] = 0;
       s_sq[k] = 0.0;
     }
     __syncthreads();
-    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
-         i += size_t(gridDim.x) * blockDim.x) {
-      const uint32_t g = t.g[i];
-      const double w = double(t.w[i]);
-      atomicAdd(&s_cnt[g], 1u);
-      atomicAdd(&s_sq[g], w * w);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < G; k += blockDim.x) {
-      if (s_cnt[k]) {
-        atomicAdd(&count[k], (unsigned long long)s_cnt[k]);
-        atomicAdd(&sumsq[k], s_sq[k]);
-      }
-    }
-    return;
   }
   for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
        base += size_t(gridDim.x) * blockDim.x) {
@@ -1327,18 +1316,37 @@ __global__ void k_gen_stats(TermsT<WT> t, const unsigned long long* n_in, int G,
     const uint32_t g = valid ? t.g[i] : 0xffffffffu;
     const double w = valid ? double(t.w[i]) : 0.0;
     const unsigned peers = __match_any_sync(0xffffffffu, g);
-    const int leader = __ffs(peers) - 1;
-    double sq = 0.0;
-    unsigned rest = peers;
-    while (rest) {
-      const int src = __ffs(rest) - 1;
-      rest &= rest - 1;
-      const double o = __shfl_sync(peers, w, src);
-      sq += o * o;
+    double sq;
+    if (peers == 0xffffffffu) {  // one id in the whole warp: butterfly sum
+      sq = w * w;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    } else {
+      sq = 0.0;
+      unsigned rest = peers;
+      while (rest) {
+        const int src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const double o = __shfl_sync(peers, w, src);
+        sq += o * o;
+      }
     }
-    if (valid && int(threadIdx.x & 31) == leader) {
-      atomicAdd(&count[g], (unsigned long long)__popc(peers));
-      atomicAdd(&sumsq[g], sq);
+    if (valid && int(threadIdx.x & 31) == __ffs(peers) - 1) {
+      if (shared) {
+        atomicAdd(&s_cnt[g], unsigned(__popc(peers)));
+        atomicAdd(&s_sq[g], sq);
+      } else {
+        atomicAdd(&count[g], (unsigned long long)__popc(peers));
+        atomicAdd(&sumsq[g], sq);
+      }
+    }
+  }
+  if (!shared) return;
+  __syncthreads();
+  for (int k = threadIdx.x; k < G; k += blockDim.x) {
+    if (s_cnt[k]) {
+      atomicAdd(&count[k], (unsigned long long)s_cnt[k]);
+      atomicAdd(&sumsq[k], s_sq[k]);
     }
   }
 }
@@ -1499,7 +1507,7 @@ struct AdjRot {
 
 constexpr int kAdjMaxRot = 256;  // rotations per launch
 
-// partial[block][r] = sum over this block's terms i of the iterated side a:
+// partial[x][r] = sum over the terms i of tile column x of the iterated side a:
 //   w_i * sum_l D_r[p][l] * b_{gmap[g_i]}(string_i with letter l on wire q_r),
 // p the letter of string_i on q_r (I contributes nothing).  Terms are taken in
 // a grid-stride order that depends only on the grid; each warp reduces with
@@ -1509,12 +1517,16 @@ template <int W, typename WT>
 __global__ void __launch_bounds__(256) k_adjoint_dot(TermsT<WT> a, size_t na, const int32_t* gmap,
                                                      TermsT<WT> b, const IndexSlot* tab,
                                                      unsigned long long cap, const AdjRot* rots,
-                                                     int nrot, double* partial) {
+                                                     int nrot_all, int rb, double* partial) {
   extern __shared__ __align__(16) unsigned char adj_smem[];
+  // blockIdx.y selects rotations [r0, r0 + nrot): several blocks share a term
+  // tile when the iterated side is too small to fill the GPU on its own
+  const int r0 = blockIdx.y * rb;
+  const int nrot = min(rb, nrot_all - r0);
   AdjRot* s_rot = reinterpret_cast<AdjRot*>(adj_smem);
-  double* s_part = reinterpret_cast<double*>(s_rot + nrot);  // [warps][nrot]
+  double* s_part = reinterpret_cast<double*>(s_rot + rb);  // [warps][nrot]
   const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < nrot; i += blockDim.x) s_rot[i] = rots[i];
+  for (int i = threadIdx.x; i < nrot; i += blockDim.x) s_rot[i] = rots[r0 + i];
   for (int i = threadIdx.x; i < warps * nrot; i += blockDim.x) s_part[i] = 0.0;
   __syncthreads();
   const size_t stride = size_t(gridDim.x) * blockDim.x;
@@ -1560,7 +1572,7 @@ __global__ void __launch_bounds__(256) k_adjoint_dot(TermsT<WT> a, size_t na, co
   for (int r = threadIdx.x; r < nrot; r += blockDim.x) {
     double v = 0.0;
     for (int k = 0; k < warps; ++k) v += s_part[k * nrot + r];
-    partial[size_t(blockIdx.x) * nrot + r] = v;
+    partial[size_t(blockIdx.x) * nrot_all + r0 + r] = v;
   }
 }
 

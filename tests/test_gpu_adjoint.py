@@ -197,6 +197,23 @@ def test_tape_hea16_two_layers_matches_oracle():
         assert abs(grad[i] - shift) <= _tol(a), (i, grad[i], shift)
 
 
+def test_tape_hea_n8_four_layers_matches_oracle():
+    """The four-layer ansatz at n = 8 (the n = 16 one exceeds the device);
+    generators Z_0..Z_3 with output strings of each queried."""
+    n, ins = W.hea(1, n=8, layers=4)
+    gens = [0, 1, 2, 3]
+    queries, a = _queries(n, ins, gens, 4, 21)
+    tape = _tape(n, ins, queries, gens, ckpt_stride=0)
+    assert tape.info()["ops"] == 4
+    grad = tape.backward(a)
+    pos = O.rotation_positions(ins)
+    rng = np.random.default_rng(5)
+    sample = sorted(int(i) for i in rng.choice(pos, size=16, replace=False))
+    want = O.grad_shift(n, ins, queries, a, positions=sample, workers=8)
+    assert np.all(np.abs(grad[sample] - want) <= _tol(a))
+    assert np.max(np.abs(want)) > 1e-3
+
+
 @pytest.mark.parametrize("case", ["layers", "hea"])
 def test_checkpoint_stride_gives_identical_gradients(case):
     if case == "layers":
