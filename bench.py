@@ -67,9 +67,10 @@ def peaks():
 
 def ncu_traffic(kernel):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    summary was taken on the current kernel source (sha256 recorded there)."""
+    summary was taken on the current source of the fast merge kernels (the
+    sha256 of qx_merge_fast.cuh is recorded there)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2505_03307_gb300", "csrc", "qx_kernels.cuh")
+    src = os.path.join(ROOT, "paper_2505_03307_gb300", "csrc", "qx_merge_fast.cuh")
     summ = os.path.join(ROOT, "profiles", "ncu_traffic_fan_in_heavy_n50.txt")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
