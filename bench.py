@@ -281,6 +281,9 @@ def run_ours(args):
         line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
     if world == 1 and args.adjoint_steps > 0:
         line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
+    if world == 1 and args.xyz_repeats:
+        line["xyz_chain"] = xyz_chain_bench(qx, W, [int(r) for r in args.xyz_repeats.split(",")],
+                                            flush.zero_, oracle_sample=not args.no_cpu_baseline)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(plan_updates_per_gen(qx, plan, n), budget_s=20.0)
     print(json.dumps(line), flush=True)
@@ -400,6 +403,58 @@ def adjoint_bench(qx, W, steps, warmup=3):
             "angle_gradients_per_s": info["rotations"] / (grad_ms / 1e3),
             "parameter_shift_equivalent_ms": 2 * info["rotations"] * fwd_ms,
             "timing": "host clock around synchronised calls, median of steps"}
+
+
+def xyz_chain_bench(qx, W, repeats_list, flush, steps=5, warmup=3, n=12, layers=2,
+                    oracle_sample=True):
+    """The |XYZ + chain> sweep of the paper's scalability experiment: n = 12,
+    2 layers, #Repeats of the RX RY RZ block per layer from 100 up.  Device
+    time (generator initialisation to final generators, CUDA events, L2
+    flushed between steps) and host planning time per #Repeats; the oracle's
+    time at the smallest #Repeats on the host cores."""
+    import torch
+
+    out = []
+    for reps in repeats_list:
+        _, cols = W.xyz_chain_columns(1, n=n, layers=layers, repeats=reps)
+        rec = qx.instr_records(*cols)
+        t0 = time.perf_counter()
+        plan = qx.group_ops(qx.load_circuit_records(n, rec))
+        plan_ms = (time.perf_counter() - t0) * 1e3
+        times = []
+        for k in range(warmup + steps):
+            flush()
+            s = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            r = qx.propagate(plan)
+            e1.record(s)
+            torch.cuda.synchronize()
+            if k >= warmup:
+                times.append(e0.elapsed_time(e1))
+            st = r.stats()
+            nterms = r.nterms
+            r.free()
+        ms = statistics.median(times)
+        out.append({"repeats": reps, "gates": len(rec), "K": st["K"], "Kp": st["Kp"],
+                    "final_terms": nterms, "propagate_ms": ms, "plan_ms": plan_ms,
+                    "term_updates_per_s": st["term_updates"] / (ms / 1e3)})
+        del plan
+    res = {"workload": f"xyz_chain_n{n}_{layers}layers (reconstructed topology)",
+           "steps": steps, "warmup": warmup, "l2": "flushed between timed steps",
+           "sweep": out}
+    if oracle_sample:
+        sys.path.insert(0, ROOT)
+        from oracle import oracle as O
+        _, instrs = W.xyz_chain(1, n=n, layers=layers, repeats=repeats_list[0])
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        O.propagate(n, instrs, mode="plan", threads=cores)
+        res["oracle"] = {"repeats": repeats_list[0], "ms": (time.perf_counter() - t0) * 1e3,
+                         "cores": cores, "kind": "oracle",
+                         "sample": "the whole circuit, one thread per generator"}
+    return res
 
 
 def plan_updates_per_gen(qx, plan, n):
@@ -529,6 +584,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
     ap.add_argument("--adjoint-steps", type=int, default=5,
                     help="timed steps of the gradient leg (0: skip)")
+    ap.add_argument("--xyz-repeats", default="100,1000,10000,100000",
+                    help="#Repeats of the XYZ + chain sweep, comma-separated ('' skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -270,16 +270,46 @@ def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeou
     return o
 
 
+#: numpy layout of qx_instr (uint32 gate, int32 q0, int32 q1, double theta).
+INSTR_DTYPE = np.dtype({"names": ["gate", "q0", "q1", "theta"],
+                        "formats": [np.uint32, np.int32, np.int32, np.float64],
+                        "offsets": [0, 4, 8, 16], "itemsize": 24})
+assert INSTR_DTYPE.itemsize == ctypes.sizeof(Instr)
+
+
+def instr_records(names, q0, q1, theta):
+    """qx_instr records from column arrays (gate names, wires, angles), without
+    a Python loop over instructions."""
+    names = np.asarray(names)
+    rec = np.zeros(len(names), INSTR_DTYPE)
+    uniq, inv = np.unique(names, return_inverse=True)
+    rec["gate"] = np.array([GATE_CODES[str(u)] for u in uniq], np.uint32)[inv]
+    rec["q0"] = q0
+    rec["q1"] = q1
+    rec["theta"] = theta
+    return rec
+
+
 class Circuit:
-    def __init__(self, n, instrs):
+    def __init__(self, n, instrs, records=None):
+        """instrs: (gate, q0, q1, theta) tuples; or records: an INSTR_DTYPE
+        array (then instrs is None)."""
         lib = load_library()
-        arr = (Instr * max(1, len(instrs)))()
-        for i, (g, a, b, th) in enumerate(instrs):
-            arr[i] = Instr(GATE_CODES[g], int(a), int(b), float(th))
         h = _P()
-        _check(lib.qx_load_circuit(int(n), arr, len(instrs), ctypes.byref(h)))
+        if records is not None:
+            rec = np.ascontiguousarray(records, INSTR_DTYPE)
+            _check(lib.qx_load_circuit(int(n), ctypes.cast(rec.ctypes.data, ctypes.POINTER(Instr)),
+                                       len(rec), ctypes.byref(h)))
+            self.instrs = None
+            self.ninstr = len(rec)
+        else:
+            arr = (Instr * max(1, len(instrs)))()
+            for i, (g, a, b, th) in enumerate(instrs):
+                arr[i] = Instr(GATE_CODES[g], int(a), int(b), float(th))
+            _check(lib.qx_load_circuit(int(n), arr, len(instrs), ctypes.byref(h)))
+            self.instrs = list(instrs)
+            self.ninstr = len(instrs)
         self.n = n
-        self.instrs = list(instrs)
         self._h = h
 
     def __del__(self):
@@ -296,7 +326,7 @@ class Plan:
         self._h = h
         self.n = circuit.n
         self.W = words(circuit.n)
-        self.ninstr = len(circuit.instrs)
+        self.ninstr = circuit.ninstr
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -427,6 +457,11 @@ class Result:
 
 def load_circuit(n, instrs) -> Circuit:
     return Circuit(n, instrs)
+
+
+def load_circuit_records(n, records) -> Circuit:
+    """Circuit from an INSTR_DTYPE array (see instr_records)."""
+    return Circuit(n, None, records=records)
 
 
 def group_ops(circuit: Circuit) -> Plan:

@@ -80,6 +80,46 @@ def rotation_layers(seed: int, n: int = 8, layers: int = 20, n_rot: int = 10):
     return n, _insert_at_random(rng, base, rots)
 
 
+def xyz_chain(seed: int, n: int = 12, layers: int = 2, repeats: int = 100):
+    """The |XYZ + chain> benchmark circuit, reconstructed (its topology figure
+    is not available): ``layers`` layers, each the XYZ block RX RY RZ (angles
+    U[0, 2 pi)) on every qubit repeated ``repeats`` times, then a CX chain
+    CX(q, q+1) for q = 0..n-2.  The gate count grows linearly with ``repeats``
+    and n; with the paper's grouping each layer's rotations form one U_k."""
+    rng = np.random.default_rng(seed)
+    instrs = []
+    for _ in range(layers):
+        th = rng.uniform(0.0, 2.0 * math.pi, size=(repeats, n, 3))
+        for r in range(repeats):
+            for q in range(n):
+                instrs.append(_g1("RX", q, float(th[r, q, 0])))
+                instrs.append(_g1("RY", q, float(th[r, q, 1])))
+                instrs.append(_g1("RZ", q, float(th[r, q, 2])))
+        for q in range(n - 1):
+            instrs.append(_g2("CX", q, q + 1))
+    return n, instrs
+
+
+def xyz_chain_columns(seed: int, n: int = 12, layers: int = 2, repeats: int = 100):
+    """``xyz_chain`` as column arrays (names, q0, q1, theta), built without a
+    Python loop per gate; the same gates in the same order."""
+    rng = np.random.default_rng(seed)
+    names, q0, q1, theta = [], [], [], []
+    rot = np.array(["RX", "RY", "RZ"])
+    for _ in range(layers):
+        th = rng.uniform(0.0, 2.0 * math.pi, size=(repeats, n, 3))
+        names.append(np.tile(rot, repeats * n))
+        q0.append(np.tile(np.repeat(np.arange(n, dtype=np.int32), 3), repeats))
+        q1.append(np.full(repeats * n * 3, -1, np.int32))
+        theta.append(th.reshape(-1))
+        names.append(np.full(n - 1, "CX"))
+        q0.append(np.arange(n - 1, dtype=np.int32))
+        q1.append(np.arange(1, n, dtype=np.int32))
+        theta.append(np.zeros(n - 1))
+    return n, (np.concatenate(names), np.concatenate(q0), np.concatenate(q1),
+               np.concatenate(theta))
+
+
 def brickwork(seed: int, n: int = 50, n_gates: int = 2000, n_t: int = 16, qubits=None):
     """Random Clifford brickwork plus T gates (the n=50, 2000-gate, 16-T workload).
 

@@ -56,6 +56,19 @@ def test_hea_merge_heavy(n, layers, seed):
         assert abs(res.info(g)["sumsq"] - 1.0) < 1e-11
 
 
+@pytest.mark.parametrize("n,layers,repeats,seed", [(6, 3, 100, 1), (8, 3, 10, 2), (10, 2, 1000, 3)])
+def test_xyz_chain(n, layers, repeats, seed):
+    """Reconstructed XYZ + chain circuit: every layer's repeated rotation
+    blocks compose into one table per wire (Algorithm 1), so the device sees
+    one fan-out step per layer whatever the repeat count."""
+    _, instrs = W.xyz_chain(seed, n=n, layers=layers, repeats=repeats)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    assert plan.info() == (layers, layers)
+    res = qx.propagate(plan)
+    ref = O.propagate(n, instrs, mode="plan", threads=8)
+    compare_result(res, ref)
+
+
 def test_fan_in_reduced_full_compare():
     """fan_in_heavy at n=20 with 8 fan-out qubits: 12 generators x 256 terms,
     one-shot expansion then 8 merge passes and a Clifford tail."""

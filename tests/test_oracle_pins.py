@@ -137,6 +137,16 @@ def test_dense_hea_small():
     _check_dense(n, instrs, "plan")
 
 
+@pytest.mark.parametrize("mode", ["gate", "plan"])
+def test_dense_xyz_chain_small(mode):
+    """The reconstructed XYZ + chain circuit: 2 layers of 5 repeated RX RY RZ
+    blocks and a CX chain on 5 qubits (each layer's 75 rotations are one U_k
+    in plan mode)."""
+    n, instrs = W.xyz_chain(2, n=5, layers=2, repeats=5)
+    res = _check_dense(n, instrs, mode)
+    assert max(len(g["strings"]) for g in res) > 100
+
+
 def test_gate_and_plan_agree_semantically():
     """Gate and plan mode may differ only in keys of weight ~0 (T;T = S)."""
     for seed in range(10):
