@@ -281,6 +281,8 @@ def run_ours(args):
         line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
     if world == 1 and args.adjoint_steps > 0:
         line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
+    if world == 1 and args.grouping_steps > 0:
+        line["grouping"] = grouping_bench(qx, W, flush.zero_, args.grouping_steps)
     if world == 1 and args.xyz_repeats:
         line["xyz_chain"] = xyz_chain_bench(qx, W, [int(r) for r in args.xyz_repeats.split(",")],
                                             flush.zero_, oracle_sample=not args.no_cpu_baseline)
@@ -403,6 +405,47 @@ def adjoint_bench(qx, W, steps, warmup=3):
             "angle_gradients_per_s": info["rotations"] / (grad_ms / 1e3),
             "parameter_shift_equivalent_ms": 2 * info["rotations"] * fwd_ms,
             "timing": "host clock around synchronised calls, median of steps"}
+
+
+def grouping_bench(qx, W, flush, steps, warmup=3):
+    """List-order grouping (Sec. III.A) against qubit-wise grouping
+    (qx_group_ops_dag) on the paper-sized workloads: operator counts, host
+    planning time and device propagation time (CUDA events, L2 flushed)."""
+    import torch
+
+    cases = [("random_layers_n8", W.random_layers(1), 0.0),
+             ("brickwork_n50", W.brickwork(1), 0.0),
+             ("fan_in_heavy_n50", W.fan_in_heavy(1), 0.0),
+             ("random_pairs_n100", W.random_pairs(1), 1e-14)]
+    out = []
+    for name, (n, instrs), eps in cases:
+        row = {"workload": name, "gates": len(instrs), "eps": eps}
+        circ = qx.load_circuit(n, instrs)
+        for mode in ("list", "dag"):
+            t0 = time.perf_counter()
+            plan = qx.group_ops(circ, dag=(mode == "dag"))
+            plan_ms = (time.perf_counter() - t0) * 1e3
+            times = []
+            for k in range(warmup + steps):
+                flush()
+                s = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(s)
+                r = qx.propagate(plan, eps=eps)
+                e1.record(s)
+                torch.cuda.synchronize()
+                if k >= warmup:
+                    times.append(e0.elapsed_time(e1))
+                st = r.stats()
+                nterms = r.nterms
+                r.free()
+            K, Kp = plan.info()
+            row[mode] = {"K": K, "Kp": Kp, "plan_ms": plan_ms,
+                         "propagate_ms": statistics.median(times), "final_terms": nterms,
+                         "fan_steps": st["fan_steps"], "merge_passes": st["merge_passes"]}
+        out.append(row)
+    return {"steps": steps, "warmup": warmup, "l2": "flushed between timed steps", "cases": out}
 
 
 def xyz_chain_bench(qx, W, repeats_list, flush, steps=5, warmup=3, n=12, layers=2,
@@ -584,6 +627,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
     ap.add_argument("--adjoint-steps", type=int, default=5,
                     help="timed steps of the gradient leg (0: skip)")
+    ap.add_argument("--grouping-steps", type=int, default=5,
+                    help="timed steps per case of the grouping comparison (0: skip)")
     ap.add_argument("--xyz-repeats", default="100,1000,10000,100000",
                     help="#Repeats of the XYZ + chain sweep, comma-separated ('' skips it)")
     args = ap.parse_args()

@@ -144,6 +144,26 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
  * *out is owned by the caller (qx_free_plan); it does not refer to `c`. */
 qx_status qx_group_ops(const qx_circuit* c, qx_plan** out);
 
+/* Qubit-wise (dependency-graph) grouping.  One-qubit gates commute with
+ * gates on other wires, so each wire's one-qubit gates between two of its
+ * two-qubit gates can join one operator: the gates are reordered by their
+ * level in the circuit's dependency graph (counted in two-qubit gates on the
+ * same wires) and grouped as by qx_group_ops.  The circuit is unchanged; the
+ * operator count K + K' is at most that of list-order grouping (Sec. III.A's
+ * chain, built over the reordered list), and tables of gates that meet on a
+ * wire compose (e.g. T ... T becomes S even with two-qubit gates on other
+ * wires in between).  Weights agree with list-order grouping up to rounding;
+ * string sets may differ in strings of weight exactly 0.  The plan applies
+ * its instructions in its own order (qx_plan_order). */
+qx_status qx_group_ops_dag(const qx_circuit* c, qx_plan** out);
+
+/* *m = instruction count; order (m entries, may be NULL) receives, for each
+ * position k of the plan's application order, the index of that instruction
+ * in the circuit given to qx_group_ops / qx_group_ops_dag (identity for the
+ * former).  qx_plan_derivative and its op_end use the plan's order;
+ * qx_tape_backward reports gradients in the circuit's order. */
+qx_status qx_plan_order(const qx_plan* p, size_t* m, size_t* order);
+
 /* Number of U_k (*K) and V_k (*Kp) operators; either pointer may be NULL. */
 qx_status qx_plan_info(const qx_plan* p, size_t* K, size_t* Kp);
 
@@ -252,7 +272,8 @@ qx_status qx_result_from_terms(int n, int ngen, size_t nterms, const uint64_t* x
 qx_status qx_propagate_result(const qx_plan* p, const qx_result* from, const qx_prop_opts* o,
                               qx_result** out);
 
-/* For instruction `instr` of the plan's circuit, which must be RX, RY or RZ:
+/* For instruction `instr` of the plan (position in the plan's application
+ * order, see qx_plan_order), which must be RX, RY or RZ:
  * d9 (9 doubles, row-major, (X, Y, Z) order) receives D = T^T dT/dtheta of its
  * wire in the one-qubit operator U_k that holds it, *qubit its wire and
  * *op_end the index one past the last instruction of U_k (the point where
@@ -283,7 +304,8 @@ qx_status qx_tape_forward(const qx_plan* p, const qx_prop_opts* o, int ckpt_stri
                           const int32_t* gen, const uint64_t* x, const uint64_t* z,
                           double* values, qx_tape** out);
 /* grad[i] = dL/dtheta_i for L = sum_k a[k] values[k] and every instruction i
- * of the circuit (0 for instructions other than RX, RY, RZ); a: nq doubles,
+ * of the circuit, in the order the circuit was given to qx_group_ops or
+ * qx_group_ops_dag (0 for instructions other than RX, RY, RZ); a: nq doubles,
  * grad: number-of-instructions doubles, host memory.  May be called any
  * number of times with different a. */
 qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad);

@@ -27,6 +27,7 @@ GATE_CODES = {
     "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
 }
 
+_MODES = {"gate": 0, "plan": 1, "dag": 2}
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
 
@@ -72,7 +73,7 @@ def _load():
             lib.oracle_cx.argtypes = [ctypes.c_char, ctypes.c_char, ctypes.c_char_p]
             lib.oracle_plan.restype = ctypes.c_void_p
             lib.oracle_plan.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p, _c_int_p,
-                                        _c_dbl_p]
+                                        _c_dbl_p, ctypes.c_int]
             lib.oracle_plan_num_ops.restype = ctypes.c_long
             lib.oracle_plan_num_ops.argtypes = [ctypes.c_void_p]
             lib.oracle_plan_op_kind.argtypes = [ctypes.c_void_p, ctypes.c_long]
@@ -124,7 +125,8 @@ def _collect(lib, h, n):
 def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
     """Propagate generators through ``instrs``.
 
-    mode: "gate" or "plan".  gens: (begin, end) range of Z_j generators (default
+    mode: "gate", "plan" or "dag" (plan mode with qubit-wise grouping).
+    gens: (begin, end) range of Z_j generators (default
     all n).  init: optional list of (string, weight) initial generators.
     Returns one dict per generator: strings (base-4 order), re, im, pruned_sumsq.
     """
@@ -134,10 +136,10 @@ def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
     if init:
         s = "".join(p for p, _ in init).encode("ascii")
         wts = np.array([w for _, w in init], np.float64)
-        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
                            float(eps), 0, 0, len(init), s, _dp(wts), int(threads))
     else:
-        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
                            float(eps), int(gb), int(ge), 0, None, None, int(threads))
     if not h:
         raise ValueError("oracle rejected the circuit")
@@ -150,7 +152,7 @@ def propagate_sum(n, instrs, strings, weights, mode="gate", eps=0.0):
     m, g, a, b, t = _arrays(instrs)
     s = "".join(strings).encode("ascii")
     w = np.ascontiguousarray(weights, np.float64)
-    h = lib.oracle_run_sum(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if mode == "plan" else 0,
+    h = lib.oracle_run_sum(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
                            float(eps), len(strings), s, _dp(w))
     if not h:
         raise ValueError("oracle rejected the input")
@@ -178,11 +180,12 @@ def cx(c, t):
     return buf.raw.decode(), s
 
 
-def plan(n, instrs):
-    """[(kind, lut)] per operator: kind 'U' with an n x 3 x 3 table, or 'V' with None."""
+def plan(n, instrs, dag=False):
+    """[(kind, lut)] per operator: kind 'U' with an n x 3 x 3 table, or 'V' with None.
+    dag=True: qubit-wise grouping (one-qubit gates move past gates on other wires)."""
     lib = _load()
     m, g, a, b, t = _arrays(instrs)
-    h = lib.oracle_plan(n, m, _ip(g), _ip(a), _ip(b), _dp(t))
+    h = lib.oracle_plan(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if dag else 0)
     if not h:
         raise ValueError("oracle rejected the circuit")
     out = []

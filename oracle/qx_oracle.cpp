@@ -43,6 +43,7 @@
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC -pthread
 #include <algorithm>
 #include <array>
+#include <deque>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -243,6 +244,61 @@ std::vector<Op> divide_instructions(int n, const std::vector<Instr>& ins) {
   return ops;
 }
 
+// Qubit-wise grouping: a one-qubit gate commutes with every gate on other
+// wires, so it may join the operator of the other one-qubit gates on its wire
+// up to the next two-qubit gate there.  Built in rounds over per-wire queues:
+// a U round takes, on every wire, the one-qubit gates at the head of its queue
+// until a two-qubit gate or the end; a V round takes, again and again until
+// none is left, every two-qubit gate that heads the queues of both its wires.
+std::vector<Op> divide_instructions_dag(int n, const std::vector<Instr>& ins) {
+  std::vector<std::deque<size_t>> queue(n);
+  for (size_t i = 0; i < ins.size(); ++i) {
+    queue[ins[i].q0].push_back(i);
+    if (is_two_qubit(ins[i].g)) queue[ins[i].q1].push_back(i);
+  }
+  std::vector<Op> ops;
+  size_t left = ins.size();
+  while (left > 0) {
+    Op u;
+    u.one_qubit = true;
+    u.per_qubit.assign(n, {});
+    bool any = false;
+    for (int w = 0; w < n; ++w)
+      while (!queue[w].empty() && !is_two_qubit(ins[queue[w].front()].g)) {
+        u.per_qubit[w].push_back(ins[queue[w].front()]);
+        queue[w].pop_front();
+        --left;
+        any = true;
+      }
+    if (any) ops.push_back(std::move(u));
+    // V round: repeatedly take the two-qubit gates that head both their
+    // queues (a gate freed by another one in this round joins the round)
+    while (true) {
+      std::vector<size_t> ready;
+      for (int w = 0; w < n; ++w) {
+        if (queue[w].empty()) continue;
+        const size_t i = queue[w].front();
+        const Instr& g = ins[i];
+        if (is_two_qubit(g.g) && g.q0 == w && queue[g.q1].front() == i) ready.push_back(i);
+      }
+      if (ready.empty()) break;
+      std::sort(ready.begin(), ready.end());
+      if (ops.empty() || ops.back().one_qubit) {
+        Op v;
+        v.one_qubit = false;
+        ops.push_back(std::move(v));
+      }
+      for (size_t i : ready) {
+        ops.back().two.push_back(ins[i]);
+        queue[ins[i].q0].pop_front();
+        queue[ins[i].q1].pop_front();
+        --left;
+      }
+    }
+  }
+  return ops;
+}
+
 // create_LUT_1q (Algorithm 1): for each wire j and p in (X, Y, Z), start from
 // the weight vector of p and map it through the gates of U_{k,j} in order.
 void create_lut(int n, Op& op) {
@@ -362,7 +418,7 @@ int inverse_gate(int g) {
 extern "C" {
 
 // Propagate generators through a circuit.
-//   mode 0 = gate mode, 1 = plan mode.
+//   mode 0 = gate mode, 1 = plan mode, 2 = plan mode with qubit-wise grouping.
 //   Generators: if n_init == 0, Z_j for j in [gen_begin, gen_end); otherwise the
 //   n_init strings in init (n letters each, concatenated) with weights init_w.
 //   nthreads: generators are independent, so they are split across threads.
@@ -391,8 +447,8 @@ void* oracle_run(int n, long m, const int* gate, const int* q0, const int* q1,
   }
   Plan plan;
   plan.n = n;
-  if (mode == 1) {
-    plan.ops = divide_instructions(n, ins);
+  if (mode == 1 || mode == 2) {
+    plan.ops = mode == 2 ? divide_instructions_dag(n, ins) : divide_instructions(n, ins);
     for (auto& op : plan.ops)
       if (op.one_qubit) create_lut(n, op);
   }
@@ -402,7 +458,7 @@ void* oracle_run(int n, long m, const int* gate, const int* q0, const int* q1,
   res->gens.resize(G);
   res->pruned.assign(G, 0.0);
   auto work = [&](int g) {
-    PauliSum out = mode == 1 ? run_plan_mode(start[g], n, plan.ops, eps, &res->pruned[g])
+    PauliSum out = mode >= 1 ? run_plan_mode(start[g], n, plan.ops, eps, &res->pruned[g])
                              : run_gate_mode(start[g], ins, eps, &res->pruned[g]);
     res->gens[g].assign(out.begin(), out.end());
   };
@@ -435,8 +491,8 @@ void* oracle_run_sum(int n, long m, const int* gate, const int* q0, const int* q
   res->gens.resize(1);
   res->pruned.assign(1, 0.0);
   PauliSum out;
-  if (mode == 1) {
-    std::vector<Op> ops = divide_instructions(n, ins);
+  if (mode == 1 || mode == 2) {
+    std::vector<Op> ops = mode == 2 ? divide_instructions_dag(n, ins) : divide_instructions(n, ins);
     for (auto& op : ops)
       if (op.one_qubit) create_lut(n, op);
     out = run_plan_mode(s, n, ops, eps, &res->pruned[0]);
@@ -485,12 +541,12 @@ int oracle_cx(char c, char t, char* out2) {
 // Plan introspection: number of operators, and for operator k its kind
 // (1 = U, 0 = V) and, for U operators, LUT_1q[k] as n x 3 x 3 doubles.
 void* oracle_plan(int n, long m, const int* gate, const int* q0, const int* q1,
-                  const double* theta) {
+                  const double* theta, int dag) {
   std::vector<Instr> ins = read_instrs(m, gate, q0, q1, theta);
   if (!valid(n, ins)) return nullptr;
   auto* p = new Plan;
   p->n = n;
-  p->ops = divide_instructions(n, ins);
+  p->ops = dag ? divide_instructions_dag(n, ins) : divide_instructions(n, ins);
   for (auto& op : p->ops)
     if (op.one_qubit) create_lut(n, op);
   return p;

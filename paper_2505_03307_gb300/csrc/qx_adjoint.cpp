@@ -45,6 +45,7 @@ struct qx_tape {
   int stride = 1;
   std::vector<int32_t> qgen;
   std::vector<uint64_t> qx, qz;
+  std::vector<size_t> order;     // plan position -> circuit index (empty: identity)
 };
 
 namespace {
@@ -105,6 +106,7 @@ qx_status qx_tape_forward(const qx_plan* p, const qx_prop_opts* o, int ckpt_stri
   t->G = G;
   t->opts = opts;
   t->m = p->ins.size();
+  t->order = p->order;
   t->qgen.assign(gen, gen + nq);
   t->qx.assign(x, x + nq * size_t(p->W));
   t->qz.assign(z, z + nq * size_t(p->W));
@@ -217,7 +219,8 @@ qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad) {
       outv.assign(qs.size(), 0.0);
       QX_TRY_STATUS(qx_adjoint_dot(M, lam, lam_of.data(), qs.size(), qs.data(), ds.data(),
                                    outv.data()));
-      for (size_t r = 0; r < who.size(); ++r) grad[who[r]] = outv[r];
+      for (size_t r = 0; r < who.size(); ++r)
+        grad[t->order.empty() ? who[r] : t->order[who[r]]] = outv[r];
       qx_free_result(tmp[j]);
       tmp[j] = nullptr;
       if (j > 0) QX_TRY_STATUS(advance(t, t->inv[j], &lam));

@@ -84,7 +84,8 @@ struct qx_plan_device;  // device-side copy of the plan (built on first use)
 struct qx_plan {
   int n = 0;
   int W = 1;
-  std::vector<qx_instr> ins;                       // the circuit (for the inverse plan of qx_expval)
+  std::vector<qx_instr> ins;                       // the circuit in the plan's application order
+  std::vector<size_t> order;                       // order[k]: input index of ins[k] (empty: identity)
   size_t K = 0, Kp = 0;
   std::vector<int> op_kind;                        // chain: 1 = U, 0 = V
   std::vector<std::vector<qx::Table3>> luts;       // per chain op (empty for V)

@@ -4,6 +4,7 @@
 //
 // Built with -ffp-contract=off: the composed tables must be bit-reproducible,
 // because their zero pattern decides which strings exist.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -517,6 +518,64 @@ qx_status qx_group_ops(const qx_circuit* c, qx_plan** out) {
   clear_error();
   if (!c || !out) return fail(QX_EINVAL, "NULL argument");
   return build_plan(c, out);
+}
+
+qx_status qx_group_ops_dag(const qx_circuit* c, qx_plan** out) {
+  clear_error();
+  if (!c || !out) return fail(QX_EINVAL, "NULL argument");
+  // Operators U_0 V_1 U_1 V_2 ...: every gate gets the earliest operator that
+  // keeps the order of the gates on each of its wires.  A one-qubit gate may
+  // share U_u with earlier one-qubit gates of its wire and follows its wire's
+  // last V; a two-qubit gate may share V_v with earlier two-qubit gates of its
+  // wires (applied in input order) and follows their last U.  These are the
+  // least indices satisfying the per-wire order, so the operator count is at
+  // most that of list-order grouping.
+  const size_t m = c->ins.size();
+  std::vector<long> last_u(size_t(c->n), -1), last_v(size_t(c->n), 0);
+  std::vector<size_t> slot(m);  // U_u -> 2u, V_v -> 2v - 1
+  size_t top = 0;
+  for (size_t i = 0; i < m; ++i) {
+    const qx_instr& g = c->ins[i];
+    if (two_qubit(g.gate)) {
+      const long v = std::max({1L, last_v[g.q0], last_v[g.q1], last_u[g.q0] + 1, last_u[g.q1] + 1});
+      last_v[g.q0] = last_v[g.q1] = v;
+      slot[i] = size_t(2 * v - 1);
+    } else {
+      const long u = std::max({0L, last_u[g.q0], last_v[g.q0]});
+      last_u[g.q0] = u;
+      slot[i] = size_t(2 * u);
+    }
+    top = std::max(top, slot[i]);
+  }
+  // Emission slot by slot, input order within a slot.  A gate moves only past
+  // gates on other wires, so the circuit is unchanged.
+  std::vector<size_t> start(top + 2, 0);
+  for (size_t i = 0; i < m; ++i) start[slot[i] + 1]++;
+  for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+  qx_circuit rc;
+  rc.n = c->n;
+  rc.ins.resize(m);
+  std::vector<size_t> order(m);
+  for (size_t i = 0; i < m; ++i) {
+    const size_t k = start[slot[i]]++;
+    rc.ins[k] = c->ins[i];
+    order[k] = i;
+  }
+  qx_plan* p = nullptr;
+  const qx_status s = build_plan(&rc, &p);
+  if (s != QX_OK) return s;
+  p->order = std::move(order);
+  *out = p;
+  return QX_OK;
+}
+
+qx_status qx_plan_order(const qx_plan* p, size_t* m, size_t* order) {
+  clear_error();
+  if (!p || !m) return fail(QX_EINVAL, "NULL argument");
+  *m = p->ins.size();
+  if (order)
+    for (size_t k = 0; k < p->ins.size(); ++k) order[k] = p->order.empty() ? k : p->order[k];
+  return QX_OK;
 }
 
 qx_status qx_plan_info(const qx_plan* p, size_t* K, size_t* Kp) {

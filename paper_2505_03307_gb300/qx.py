@@ -35,6 +35,7 @@ EXPORTED = (
     "qx_server_submit", "qx_server_poll", "qx_server_wait", "qx_server_stats", "qx_server_destroy",
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
+    "qx_group_ops_dag", "qx_plan_order",
 )
 
 
@@ -127,6 +128,8 @@ def load_library():
         "qx_load_circuit": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Instr), _SZ,
                                            ctypes.POINTER(_P)]),
         "qx_group_ops": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "qx_group_ops_dag": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "qx_plan_order": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), _P]),
         "qx_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
         "qx_plan_op": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
         "qx_plan_lut": (ctypes.c_int, [_P, _SZ, _DP]),
@@ -319,10 +322,11 @@ class Circuit:
 
 
 class Plan:
-    def __init__(self, circuit: Circuit):
+    def __init__(self, circuit: Circuit, dag=False):
         lib = load_library()
         h = _P()
-        _check(lib.qx_group_ops(circuit._h, ctypes.byref(h)))
+        fn = lib.qx_group_ops_dag if dag else lib.qx_group_ops
+        _check(fn(circuit._h, ctypes.byref(h)))
         self._h = h
         self.n = circuit.n
         self.W = words(circuit.n)
@@ -332,6 +336,14 @@ class Plan:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.qx_free_plan(self._h)
             self._h = None
+
+    def order(self):
+        """order[k] = circuit index of the plan's k-th applied instruction."""
+        m = _SZ()
+        _check(load_library().qx_plan_order(self._h, ctypes.byref(m), None))
+        out = np.zeros(max(int(m.value), 1), np.uint64)
+        _check(load_library().qx_plan_order(self._h, ctypes.byref(m), out.ctypes.data))
+        return out[:int(m.value)].astype(np.int64)
 
     def info(self):
         K, Kp = _SZ(), _SZ()
@@ -464,8 +476,10 @@ def load_circuit_records(n, records) -> Circuit:
     return Circuit(n, None, records=records)
 
 
-def group_ops(circuit: Circuit) -> Plan:
-    return Plan(circuit)
+def group_ops(circuit: Circuit, dag=False) -> Plan:
+    """List-order grouping (Sec. III.A), or qubit-wise dependency-graph
+    grouping with dag=True (qx_group_ops_dag)."""
+    return Plan(circuit, dag=dag)
 
 
 def propagate(plan: Plan, **kw) -> Result:

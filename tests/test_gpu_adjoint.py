@@ -214,6 +214,23 @@ def test_tape_hea_n8_four_layers_matches_oracle():
     assert np.max(np.abs(want)) > 1e-3
 
 
+def test_tape_on_dag_plan_reports_circuit_order():
+    """A tape on a qubit-wise plan (gates reordered) returns gradients in the
+    circuit's own instruction order, equal to those of list-order grouping."""
+    n, ins = W.rotation_layers(8, n_rot=12)
+    gens = [0, 2]
+    queries, a = _queries(n, ins, gens, 6, 8)
+    qg = [g for g, _ in queries]
+    qp = [p for _, p in queries]
+    lst = qx.Tape(qx.group_ops(qx.load_circuit(n, ins)), qg, qp, gens=(0, 3)).backward(a)
+    dplan = qx.group_ops(qx.load_circuit(n, ins), dag=True)
+    assert not np.array_equal(dplan.order(), np.arange(len(ins)))
+    dag = qx.Tape(dplan, qg, qp, gens=(0, 3)).backward(a)
+    assert np.all(np.abs(dag - lst) <= _tol(a))
+    pos = O.rotation_positions(ins)
+    assert np.max(np.abs(dag[pos])) > 1e-3
+
+
 @pytest.mark.parametrize("case", ["layers", "hea"])
 def test_checkpoint_stride_gives_identical_gradients(case):
     if case == "layers":

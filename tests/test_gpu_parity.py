@@ -69,6 +69,37 @@ def test_xyz_chain(n, layers, repeats, seed):
     compare_result(res, ref)
 
 
+def _dag_cases():
+    for seed in range(1, 4):
+        yield f"layers{seed}", W.random_layers(seed)
+    for seed in range(12):
+        yield f"small{seed}", W.random_small(seed, 1 + seed % 7, 60,
+                                             angles="uniform" if seed % 2 else "quarter")
+    yield "hea10", W.hea(2, n=10, layers=3)
+    yield "brickwork50", W.brickwork(1)
+    yield "xyz8", W.xyz_chain(4, n=8, layers=3, repeats=5)
+    yield "pairs100", W.random_pairs(2, n_cliff=20000, n_rz=12)
+
+
+@pytest.mark.parametrize("case", [c for c, _ in _dag_cases()])
+def test_dag_grouping_matches_oracle(case):
+    """Qubit-wise grouping (qx_group_ops_dag) against the oracle's own
+    qubit-wise plan mode: exact string sets, weights within tolerance; and
+    against list-order grouping up to strings of weight 0."""
+    n, instrs = dict(_dag_cases())[case]
+    plan = qx.group_ops(qx.load_circuit(n, instrs), dag=True)
+    res = qx.propagate(plan)
+    ref = O.propagate(n, instrs, mode="dag", threads=8)
+    compare_result(res, ref)
+    lst = qx.propagate(qx.group_ops(qx.load_circuit(n, instrs)))
+    for g in range(0, n, max(1, n // 8)):
+        a = {s: w for s, w in res.export_dict(g).items() if abs(w) > 1e-13}
+        b = {s: w for s, w in lst.export_dict(g).items() if abs(w) > 1e-13}
+        assert a.keys() == b.keys(), g
+        for s, w in a.items():
+            assert abs(b[s] - w) <= 1e-12 * abs(w) + 1e-13
+
+
 def test_fan_in_reduced_full_compare():
     """fan_in_heavy at n=20 with 8 fan-out qubits: 12 generators x 256 terms,
     one-shot expansion then 8 merge passes and a Clifford tail."""

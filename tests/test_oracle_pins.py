@@ -147,6 +147,29 @@ def test_dense_xyz_chain_small(mode):
     assert max(len(g["strings"]) for g in res) > 100
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_dense_dag_grouping(seed):
+    """Plan mode with qubit-wise grouping against dense brute force."""
+    n = 2 + seed % 5
+    _, instrs = W.random_small(seed, n, 10 + 3 * n, angles="uniform" if seed % 2 else "quarter")
+    _check_dense(n, instrs, "dag")
+
+
+def test_dag_grouping_composes_across_other_wires():
+    """T on wire 0, a CNOT on wires 1-2, T on wire 0: list-order grouping
+    makes two fan-outs (a zero-weight X stays behind), the qubit-wise one
+    composes T T = S (no fan-out at all)."""
+    ins = [("H", 0, -1, 0.0), ("T", 0, -1, 0.0), ("CX", 1, 2, 0.0), ("T", 0, -1, 0.0)]
+    kinds = [k for k, _ in O.plan(3, ins, dag=True)]
+    assert kinds == ["U", "V"]
+    lut = O.plan(3, ins, dag=True)[0][1]
+    assert np.array_equal(lut[0], O.plan(1, [("H", 0, -1, 0.0), ("S", 0, -1, 0.0)])[0][1][0])
+    d = O.as_dict(O.propagate(3, ins, mode="dag", gens=(0, 1))[0])
+    p = O.as_dict(O.propagate(3, ins, mode="plan", gens=(0, 1))[0])
+    assert d == {"YII": 1.0}
+    assert p.keys() == {"XII", "YII"} and abs(p["XII"]) < 1e-15
+
+
 def test_gate_and_plan_agree_semantically():
     """Gate and plan mode may differ only in keys of weight ~0 (T;T = S)."""
     for seed in range(10):
