@@ -100,9 +100,14 @@ typedef struct {
 /* qx_prop_opts.flags: record CUDA events around every kernel launch (on the
  * launch stream) and report per-kernel-class device time in qx_prop_stats. */
 #define QX_FLAG_KERNEL_TIMING 1u
+/* qx_prop_opts.flags: never run merge wires in place.  By default a fan-out
+ * step whose merge groups all hold every letter their tables produce (no
+ * string created or removed) updates the weights in place through a full-key
+ * index instead of rebuilding the terms; the results are the same. */
+#define QX_FLAG_NO_INPLACE 2u
 
 /* Kernel classes of qx_prop_stats.kc_* (names from qx_kernel_class_name). */
-#define QX_KC_COUNT 10
+#define QX_KC_COUNT 12
 
 /* Counters of one propagation (metrics and launch accounting). */
 typedef struct {
@@ -117,6 +122,8 @@ typedef struct {
   uint64_t fan_steps;          /* device expansion steps (one-qubit operators with fan-out) */
   uint64_t merge_passes;       /* index-accumulation (merge) passes */
   uint64_t clifford_passes;    /* fused Clifford passes */
+  uint64_t inplace_steps;      /* fan-out steps whose merges ran in place */
+  uint64_t inplace_fallbacks;  /* in-place attempts that found an open group */
   /* per kernel class: launches, algorithmic bytes (terms each launch must
    * read and write, 16W+8 bytes per term), and device milliseconds (only with
    * QX_FLAG_KERNEL_TIMING; 0 otherwise) */

@@ -296,11 +296,12 @@ struct Scratch {
 // Kernel classes of qx_prop_stats.kc_*.
 enum KernelClass {
   KC_INIT = 0, KC_CLIFF, KC_MASK, KC_INSERT, KC_EMIT, KC_COUNT, KC_SCAN, KC_EXPAND, KC_COMPACT,
-  KC_STATS
+  KC_STATS, KC_INDEX, KC_INPLACE
 };
 const char* const kKernelClassNames[QX_KC_COUNT] = {
     "init", "clifford_pass", "fan_mask", "merge_insert", "merge_emit", "expand_count",
-    "expand_scan", "expand_emit", "prune_compact", "gen_stats"};
+    "expand_scan", "expand_emit", "prune_compact", "gen_stats", "inplace_index",
+    "merge_inplace"};
 
 // Optional CUDA-event timing of every launch, resolved after the final sync.
 struct Timer {
@@ -380,6 +381,7 @@ struct Ctx {
   int cslot = 0;  // which of ncnt[0], ncnt[1] holds cur's count
   Timer tm;
   FastTable* ftab = nullptr;  // pooled merge table of the fast path (held for the call)
+  bool inplace = true;        // merge wires may run in place (QX_FLAG_NO_INPLACE clears it)
   void begin(int k) { tm.begin(k); }
   // after a launch: class, launches it made, algorithmic bytes
   void end(int k, int launches, uint64_t bytes) {
@@ -593,8 +595,165 @@ qx_status ensure_merge_scratch(Ctx& c, bool fast, size_t n) {
 // Merge passes over the mixed qubits.  First without host syncs inside a
 // capacity arena (counts stay on the device); if an output or the table
 // overflows, the passes are redone one by one with exact counts.
+// Drops |w| < eps from the current terms (the last kernel of a U_k).
 template <int W, typename WT>
-qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after) {
+qx_status prune_cur(Ctx& c) {
+  Scratch& s = c.sc;
+  TermBuf kept;
+  QX_TRY(alloc_terms(c.al, W, c.wtb, c.N, &kept));
+  const int kslot = 1 - c.cslot;
+  QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + kslot, 0, 8, c.al.s));
+  c.begin(KC_COMPACT);
+  k_compact_pruned<W, kThreads, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, c.eps, s.pruned, kept.view<WT>(), s.ncnt + kslot);
+  c.tm.end();
+  QX_TRY_CUDA(cudaGetLastError());
+  unsigned long long nk = 0;
+  QX_TRY(sync_read(c, &nk, s.ncnt + kslot, 8));
+  c.end_bytes_only(KC_COMPACT, 1, (c.N + nk) * (16 * W + sizeof(WT)));
+  replace_cur(c, kept, nk, kslot);
+  return QX_OK;
+}
+
+// Letter permutation of an in-place merge wire: each isolated row keeps its
+// only column, the other letters take the remaining columns (themselves where
+// possible).  Packed 2 bits per source letter (X, Y, Z).
+int inplace_pi(const FanQubit& f) {
+  int pi[3] = {-1, -1, -1};
+  bool used[3] = {false, false, false};
+  for (int p = 0; p < 3; ++p)
+    if (f.iso[p]) {
+      pi[p] = f.col[p][0];
+      used[pi[p]] = true;
+    }
+  for (int p = 0; p < 3; ++p)
+    if (pi[p] < 0 && !used[p]) {
+      pi[p] = p;
+      used[p] = true;
+    }
+  for (int p = 0; p < 3; ++p)
+    if (pi[p] < 0)
+      for (int c = 0; c < 3; ++c)
+        if (!used[c]) {
+          pi[p] = c;
+          used[c] = true;
+          break;
+        }
+  return pi[0] | (pi[1] << 2) | (pi[2] << 4);
+}
+
+// Whether the merge wires of a step may run in place: one-word keys with a
+// free empty pattern and, per generator, letter sets that are closed under
+// each wire's table up to its letter permutation (a necessary condition for
+// closed groups; the kernel checks every group).
+bool inplace_candidate(const Ctx& c, const std::vector<const FanQubit*>& mq,
+                       const std::vector<unsigned long long>& gm) {
+  if (c.W != 1 || c.n >= 64) return false;
+  const int fb = 64 - c.n;
+  if (2 * fb < 40 && (unsigned long long)c.G >= (1ull << (2 * fb))) return false;
+  for (const FanQubit* f : mq) {
+    const int pi = inplace_pi(*f);
+    int inv[3];
+    for (int p = 0; p < 3; ++p) inv[(pi >> (2 * p)) & 3] = p;
+    const uint64_t qb = 1ull << f->q;
+    for (int g = 0; g < c.G; ++g) {
+      bool has[3];
+      for (int a = 0; a < 3; ++a) has[a] = (gm[size_t(g) * 3 + a] & qb) != 0;
+      for (int a = 0; a < 3; ++a) {
+        if (!has[a]) continue;
+        const int ca = (pi >> (2 * a)) & 3;
+        bool reached = false;
+        for (int col = 0; col < 3; ++col)
+          if (f->t.r[a][col] != 0.0 && !has[inv[col]]) return false;
+        for (int b = 0; b < 3; ++b)
+          if (has[b] && f->t.r[b][ca] != 0.0) reached = true;
+        if (!reached) return false;
+      }
+    }
+  }
+  return true;
+}
+
+// The merge wires of a step in place (see qx_merge_inplace.cuh).  *done is
+// false when some group turned out not to be closed; the terms are then
+// unchanged and the caller runs the general merge.
+template <int W, typename WT>
+qx_status run_merges_inplace(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
+                             bool* done) {
+  *done = false;
+  const size_t N = c.N;
+  const unsigned long long cap = std::max<unsigned long long>(1024, 2ull * N);
+  const size_t tab_bytes = size_t(cap) * sizeof(KeySlot);
+  void* mem = c.al.get(tab_bytes + 2 * N * sizeof(WT) + 512);
+  if (!mem) return QX_OK;  // no room for the index: the general merge needs none
+  auto* tab = static_cast<KeySlot*>(mem);
+  WT* wb[2] = {reinterpret_cast<WT*>(static_cast<unsigned char*>(mem) + tab_bytes),
+               reinterpret_cast<WT*>(static_cast<unsigned char*>(mem) + tab_bytes + 256) + N};
+  auto body = [&]() -> qx_status {
+    QX_TRY_CUDA(cudaMemsetAsync(tab, 0xff, tab_bytes, c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+    const unsigned grid = grid_for(N, kThreads, c.sms, 8);
+    const auto view = c.cur.view<WT>();
+    c.begin(KC_INDEX);
+    k_keyindex_build<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, tab, cap, c.sc.err);
+    c.end(KC_INDEX, 1, uint64_t(N) * 20);
+    const WT* src = view.w;
+    std::vector<uint32_t> relabel;  // letter permutations, applied after every wire
+    for (size_t j = 0; j < mq.size(); ++j) {
+      WT* dst = wb[j & 1];
+      const int pi = inplace_pi(*mq[j]);
+      if (pi != (0 | (1 << 2) | (2 << 4))) {
+        uint32_t code = 0;
+        for (int p = 0; p < 3; ++p) code |= uint32_t((pi >> (2 * p)) & 3) << (3 * p);
+        relabel.push_back(encode_op(kOpPerm, mq[j]->q, -1, code));
+      }
+      c.begin(KC_INPLACE);
+      k_merge_inplace<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, to_dev(*mq[j]), pi, src,
+                                                          dst, tab, cap, c.sc.err);
+      c.end(KC_INPLACE, 1, 2ull * N * (16 * W + sizeof(WT)));
+      src = dst;
+    }
+    QX_TRY_CUDA(cudaGetLastError());
+    unsigned err = 0;
+    QX_TRY(sync_read(c, &err, c.sc.err, 4));
+    if (err) {
+      QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+      return QX_OK;
+    }
+    QX_TRY_CUDA(cudaMemcpyAsync(view.w, src, N * sizeof(WT), cudaMemcpyDeviceToDevice, c.al.s));
+    if (!relabel.empty()) {  // the letters the in-place weights belong to
+      auto* d_ops = reinterpret_cast<uint32_t*>(tab);  // the index is no longer needed
+      QX_TRY_CUDA(cudaMemcpyAsync(d_ops, relabel.data(), relabel.size() * 4,
+                                  cudaMemcpyHostToDevice, c.al.s));
+      c.begin(KC_CLIFF);
+      k_clifford_ops<W, WT><<<grid, kThreads, relabel.size() * 4, c.al.s>>>(
+          view, c.sc.ncnt + c.cslot, d_ops, int(relabel.size()));
+      c.end(KC_CLIFF, 1, 2ull * N * 16 * W);
+      QX_TRY_CUDA(cudaGetLastError());
+    }
+    *done = true;
+    return QX_OK;
+  };
+  const qx_status st = body();
+  c.al.put(mem);
+  if (st != QX_OK || !*done) return st;
+  c.st.merge_passes += mq.size();
+  c.st.inplace_steps++;
+  c.st.alg_bytes += mq.size() * 2ull * N * (16 * W + sizeof(WT));
+  c.st.children += mq.size() * N;
+  if (!more_after && c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
+                     const std::vector<unsigned long long>& gm) {
+  if (c.inplace && inplace_candidate(c, mq, gm)) {
+    bool done = false;
+    QX_TRY(run_merges_inplace<W, WT>(c, mq, more_after, &done));
+    if (done) return QX_OK;
+    c.st.inplace_fallbacks++;
+  }
   const bool fast = fast_eligible(c.n, W, c.G);
   const size_t N0 = c.N;
   const int slot0 = c.cslot;
@@ -760,7 +919,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   if (!mq.empty())
     QX_TRY_CUDA(cudaMemcpyAsync(s.mixed, mixed.data(), G * W * 8, cudaMemcpyHostToDevice, c.al.s));
   // 2. one merge pass per qubit that needs it in some generator
-  if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty()));
+  if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm));
   if (fq.empty()) return QX_OK;
   // 3. one-shot expansion over the qubits that need no merge anywhere
   std::vector<FanQ> hq;
@@ -808,21 +967,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   c.st.children += total;
   QX_TRY_CUDA(cudaMemcpyAsync(s.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
   replace_cur(c, out, total, oslot);
-  if (c.eps > 0.0) {
-    TermBuf kept;
-    QX_TRY(alloc_terms(c.al, W, c.wtb, c.N, &kept));
-    const int kslot = 1 - c.cslot;
-    QX_TRY_CUDA(cudaMemsetAsync(s.ncnt + kslot, 0, 8, c.al.s));
-    c.begin(KC_COMPACT);
-    k_compact_pruned<W, kThreads, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-        c.cur.view<WT>(), s.ncnt + c.cslot, c.eps, s.pruned, kept.view<WT>(), s.ncnt + kslot);
-    c.tm.end();
-    QX_TRY_CUDA(cudaGetLastError());
-    unsigned long long nk = 0;
-    QX_TRY(sync_read(c, &nk, s.ncnt + kslot, 8));
-    c.end_bytes_only(KC_COMPACT, 1, (c.N + nk) * (16 * W + sizeof(WT)));
-    replace_cur(c, kept, nk, kslot);
-  }
+  if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
   return QX_OK;
 }
 
@@ -987,6 +1132,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   c.al.ctx = opts.alloc_ctx;
   c.al.s = static_cast<cudaStream_t>(opts.stream);
   c.tm.on = (opts.flags & QX_FLAG_KERNEL_TIMING) != 0;
+  c.inplace = (opts.flags & QX_FLAG_NO_INPLACE) == 0;
   c.tm.s = c.al.s;
   c.tm.pool = &t_event_pool;
   if (p->dev->max_smem > 48 * 1024) {

@@ -695,6 +695,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_emit(
 }  // namespace qx
 
 #include "qx_merge_fast.cuh"
+#include "qx_merge_inplace.cuh"
 
 namespace qx {
 namespace dev {

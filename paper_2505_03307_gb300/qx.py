@@ -64,11 +64,13 @@ class PropOpts(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 FLAG_KERNEL_TIMING = 1
-KC_COUNT = 10
+FLAG_NO_INPLACE = 2
+KC_COUNT = 12
 
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
-            "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes")
+            "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes",
+            "inplace_steps", "inplace_fallbacks")
 
 
 class ServerOpts(ctypes.Structure):
@@ -252,7 +254,7 @@ _torch_alloc = None
 
 
 def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeout_ms=0,
-              torch_allocator=False, kernel_timing=False, precision=64):
+              torch_allocator=False, kernel_timing=False, precision=64, inplace=True):
     o = PropOpts()
     load_library().qx_default_opts(ctypes.byref(o))
     o.precision = int(precision)
@@ -263,7 +265,7 @@ def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeou
     o.max_terms = int(max_terms)
     o.stream = _stream_ptr(stream)
     o.timeout_ms = int(timeout_ms)
-    o.flags = FLAG_KERNEL_TIMING if kernel_timing else 0
+    o.flags = (FLAG_KERNEL_TIMING if kernel_timing else 0) | (0 if inplace else FLAG_NO_INPLACE)
     if torch_allocator:
         global _torch_alloc
         if _torch_alloc is None:
