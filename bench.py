@@ -66,25 +66,18 @@ def peaks():
 
 
 def ncu_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    summary was taken on the current source of the fast merge kernels (the
-    sha256 of qx_merge_fast.cuh is recorded there)."""
+    """Per-launch DRAM bytes of kernel class `kernel` from the committed ncu
+    summary, if the capture was taken on the current source of that kernel
+    (the file and its sha256 are recorded on the kernel's line)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2505_03307_gb300", "csrc", "qx_merge_fast.cuh")
     summ = os.path.join(ROOT, "profiles", "ncu_traffic_fan_in_heavy_n50.txt")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        rows = {}
-        kernel_sha = None
         for ln in open(summ):
-            ln = ln.strip()
-            if ln.startswith("source_sha256:"):
-                kernel_sha = ln.split(":", 1)[1].strip()
-            elif ln.startswith("traffic_per_launch"):
-                _, name, val = ln.split()
-                rows[name] = float(val)
-        if kernel_sha == sha and kernel in rows:
-            return rows[kernel]
+            parts = ln.split()
+            if len(parts) == 5 and parts[0] == "traffic_per_launch" and parts[1] == kernel:
+                src = os.path.join(ROOT, "paper_2505_03307_gb300", "csrc", parts[3])
+                sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+                return float(parts[2]) if sha == parts[4] else None
     except (OSError, ValueError):
         pass
     return None
