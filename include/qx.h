@@ -21,6 +21,9 @@
  *
  * Conventions (not fixed by the paper): RX/RY/RZ(theta) = exp(-i theta s / 2),
  * T = diag(1, e^{i pi/4}), S = diag(1, i), SX = sqrt(X); CZ = H(t) CX H(t).
+ * Two-qubit rotations (RXX ... CP) enter the device program as Pauli rotation
+ * steps inside their V_k (each string Q that anticommutes with the rotation's
+ * Pauli P gains the partner Q xor P; the two are merged).
  * Composed table entries within 2^-50 of 0 or of +-1 are set to 0 or +-1.
  * eps = 0 keeps every string that the tables reach, even when its weight sums
  * to exactly 0; eps > 0 drops |w| < eps after every U_k.
@@ -58,7 +61,14 @@ typedef enum {
 /* Gate codes of qx_instr.gate. */
 typedef enum {
   QX_H = 0, QX_S = 1, QX_SDG = 2, QX_X = 3, QX_Y = 4, QX_Z = 5, QX_SX = 6, QX_SXDG = 7,
-  QX_T = 8, QX_TDG = 9, QX_RX = 10, QX_RY = 11, QX_RZ = 12, QX_CX = 13, QX_CZ = 14
+  QX_T = 8, QX_TDG = 9, QX_RX = 10, QX_RY = 11, QX_RZ = 12, QX_CX = 13, QX_CZ = 14,
+  /* Two-qubit gates beyond CX / CZ (the paper leaves them to future work,
+   * Sec. III.C).  SWAP is Clifford.  The others are Pauli rotations on the
+   * two wires (q0, q1): RXX/RYY/RZZ(theta) = exp(-i theta P0 P1 / 2), and the
+   * controlled rotations with q0 the control: CRX/CRY/CRZ(theta) apply
+   * RX/RY/RZ(theta) to q1 when q0 is |1>, CP(theta) = diag(1, 1, 1, e^{i theta}). */
+  QX_SWAP = 15, QX_RXX = 16, QX_RYY = 17, QX_RZZ = 18, QX_CRX = 19, QX_CRY = 20,
+  QX_CRZ = 21, QX_CP = 22
 } qx_gate;
 
 /* One instruction {g, w, theta} (Sec. III.A): gate, wire(s), parameter.
@@ -107,7 +117,7 @@ typedef struct {
 #define QX_FLAG_NO_INPLACE 2u
 
 /* Kernel classes of qx_prop_stats.kc_* (names from qx_kernel_class_name). */
-#define QX_KC_COUNT 12
+#define QX_KC_COUNT 13
 
 /* Counters of one propagation (metrics and launch accounting). */
 typedef struct {
@@ -170,6 +180,20 @@ qx_status qx_group_ops_dag(const qx_circuit* c, qx_plan** out);
  * former).  qx_plan_derivative and its op_end use the plan's order;
  * qx_tape_backward reports gradients in the circuit's order. */
 qx_status qx_plan_order(const qx_plan* p, size_t* m, size_t* order);
+
+/* Clifford push-through (not in the paper).  Every Clifford gate is moved to
+ * the end of the circuit: with D the product of the Clifford gates before a
+ * non-Clifford gate, that gate's rotation exp(-i phi s / 2) about a Pauli s
+ * equals exp(-i phi P / 2) after the whole Clifford part, P = D^dagger s D.
+ * The plan applies these Pauli rotations in circuit order (T and TDG as
+ * rotations by +-pi/4 about Z, the two-qubit rotations as one to three
+ * commuting Pauli rotations) and then the whole Clifford part as one pass.
+ * Each rotation maps a string Q that anticommutes with P to cos phi Q +
+ * sin phi (i Q P) and leaves the others; strings Q and Q xor P are merged.
+ * Weights agree with qx_group_ops up to rounding; string sets may differ in
+ * strings of weight exactly 0.  The plan has no U_k / V_k chain (K = K' = 0,
+ * qx_plan_lut is not available). */
+qx_status qx_group_ops_pushthrough(const qx_circuit* c, qx_plan** out);
 
 /* Number of U_k (*K) and V_k (*Kp) operators; either pointer may be NULL. */
 qx_status qx_plan_info(const qx_plan* p, size_t* K, size_t* Kp);

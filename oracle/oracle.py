@@ -25,9 +25,10 @@ _lib = None
 GATE_CODES = {
     "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
     "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
+    "SWAP": 15, "RXX": 16, "RYY": 17, "RZZ": 18, "CRX": 19, "CRY": 20, "CRZ": 21, "CP": 22,
 }
 
-_MODES = {"gate": 0, "plan": 1, "dag": 2}
+_MODES = {"gate": 0, "plan": 1, "dag": 2, "push": 3}
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
 
@@ -125,7 +126,9 @@ def _collect(lib, h, n):
 def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
     """Propagate generators through ``instrs``.
 
-    mode: "gate", "plan" or "dag" (plan mode with qubit-wise grouping).
+    mode: "gate", "plan", "dag" (plan mode with qubit-wise grouping) or "push"
+    (non-Clifford gates conjugated by their Clifford prefix, then all Clifford
+    gates).
     gens: (begin, end) range of Z_j generators (default
     all n).  init: optional list of (string, weight) initial generators.
     Returns one dict per generator: strings (base-4 order), re, im, pruned_sumsq.

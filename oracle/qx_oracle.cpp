@@ -62,7 +62,7 @@ using Table = std::array<std::array<double, 3>, 3>;  // T[p][c]: coefficient of 
 // Gate codes of this file (the Python wrapper maps names onto them).
 enum Gate {
   G_H = 0, G_S, G_SDG, G_X, G_Y, G_Z, G_SX, G_SXDG, G_T, G_TDG, G_RX, G_RY, G_RZ, G_CX, G_CZ,
-  G_COUNT
+  G_SWAP, G_RXX, G_RYY, G_RZZ, G_CRX, G_CRY, G_CRZ, G_CP, G_COUNT
 };
 
 struct Instr {
@@ -81,7 +81,11 @@ int letter_index(char c) {
   }
 }
 
-bool is_two_qubit(int g) { return g == G_CX || g == G_CZ; }
+bool is_two_qubit(int g) { return g == G_CX || g == G_CZ || (g >= G_SWAP && g <= G_CP); }
+
+bool is_clifford(int g) {
+  return g != G_T && g != G_TDG && g != G_RX && g != G_RY && g != G_RZ && (g < G_RXX || g > G_CP);
+}
 
 double snap(double v) {
   const double tol = std::ldexp(1.0, -50);
@@ -186,11 +190,140 @@ PauliSum apply_cx(const PauliSum& in, int c, int t) {
   return out;
 }
 
+// --- two-qubit gates beyond CX and CZ ----------------------------------------
+// Their transfer tables come from the 4 x 4 unitaries: with wire q0 the left
+// tensor factor (basis index 2 b0 + b1),
+//   T[(p0, p1)][(c0, c1)] = Tr((C0 x C1) U (P0 x P1) U^dagger) / 4,
+// letters 0 = I, 1 = X, 2 = Y, 3 = Z.
+using Mat4 = std::array<std::array<cplx, 4>, 4>;
+using Table16 = std::array<std::array<double, 16>, 16>;
+
+Mat4 gate_unitary_2q(int g, double th) {
+  Mat4 u{};
+  const cplx I(0.0, 1.0);
+  const double c = std::cos(th / 2), s = std::sin(th / 2);
+  auto diag = [&](cplx a, cplx b, cplx d, cplx e) {
+    u[0][0] = a; u[1][1] = b; u[2][2] = d; u[3][3] = e;
+  };
+  switch (g) {
+    case G_SWAP:
+      u[0][0] = u[3][3] = 1.0;
+      u[1][2] = u[2][1] = 1.0;
+      break;
+    case G_RXX:  // cos I - i sin X x X
+      diag(c, c, c, c);
+      u[0][3] = u[3][0] = u[1][2] = u[2][1] = -I * s;
+      break;
+    case G_RYY:  // Y x Y = [[0,0,0,-1],[0,0,1,0],[0,1,0,0],[-1,0,0,0]]
+      diag(c, c, c, c);
+      u[0][3] = u[3][0] = I * s;
+      u[1][2] = u[2][1] = -I * s;
+      break;
+    case G_RZZ:
+      diag(std::exp(-I * (th / 2)), std::exp(I * (th / 2)), std::exp(I * (th / 2)),
+           std::exp(-I * (th / 2)));
+      break;
+    case G_CRX:
+      diag(1.0, 1.0, c, c);
+      u[2][3] = u[3][2] = -I * s;
+      break;
+    case G_CRY:
+      diag(1.0, 1.0, c, c);
+      u[2][3] = -s;
+      u[3][2] = s;
+      break;
+    case G_CRZ:
+      diag(1.0, 1.0, std::exp(-I * (th / 2)), std::exp(I * (th / 2)));
+      break;
+    case G_CP:
+      diag(1.0, 1.0, 1.0, std::exp(I * th));
+      break;
+    default: break;
+  }
+  return u;
+}
+
+Mat4 pauli_pair(int a, int b) {
+  std::array<std::array<std::array<cplx, 2>, 2>, 4> P{};
+  const cplx I(0.0, 1.0);
+  P[0][0][0] = P[0][1][1] = 1.0;
+  P[1][0][1] = P[1][1][0] = 1.0;
+  P[2][0][1] = -I;
+  P[2][1][0] = I;
+  P[3][0][0] = 1.0;
+  P[3][1][1] = -1.0;
+  Mat4 m{};
+  for (int i0 = 0; i0 < 2; ++i0)
+    for (int i1 = 0; i1 < 2; ++i1)
+      for (int j0 = 0; j0 < 2; ++j0)
+        for (int j1 = 0; j1 < 2; ++j1) m[2 * i0 + i1][2 * j0 + j1] = P[a][i0][j0] * P[b][i1][j1];
+  return m;
+}
+
+Mat4 mul4(const Mat4& a, const Mat4& b) {
+  Mat4 r{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 4; ++k) r[i][j] += a[i][k] * b[k][j];
+  return r;
+}
+
+Table16 gate_table_2q(int g, double th) {
+  const Mat4 u = gate_unitary_2q(g, th);
+  Mat4 ud{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) ud[i][j] = std::conj(u[j][i]);
+  Table16 t{};
+  for (int p = 0; p < 16; ++p) {
+    const Mat4 img = mul4(mul4(u, pauli_pair(p / 4, p % 4)), ud);
+    for (int c = 0; c < 16; ++c) {
+      const Mat4 prod = mul4(pauli_pair(c / 4, c % 4), img);
+      cplx tr = 0.0;
+      for (int i = 0; i < 4; ++i) tr += prod[i][i];
+      t[p][c] = snap(tr.real() / 4.0);
+    }
+  }
+  return t;
+}
+
+int letter16(char c) {
+  switch (c) {
+    case 'X': return 1;
+    case 'Y': return 2;
+    case 'Z': return 3;
+    default: return 0;
+  }
+}
+
+PauliSum apply_2q_table(const PauliSum& in, int a, int b, const Table16& t) {
+  static const char kL[4] = {'I', 'X', 'Y', 'Z'};
+  PauliSum out;
+  for (const auto& [key, w] : in) {
+    const int p = 4 * letter16(key[a]) + letter16(key[b]);
+    for (int c = 0; c < 16; ++c) {
+      if (t[p][c] == 0.0) continue;
+      std::string k2 = key;
+      k2[a] = kL[c / 4];
+      k2[b] = kL[c % 4];
+      out[k2] += w * t[p][c];
+    }
+  }
+  return out;
+}
+
 PauliSum apply_2q(const PauliSum& in, int g, int c, int t) {
   if (g == G_CX) return apply_cx(in, c, t);
-  // CZ = H(t) CX(c, t) H(t)
-  const Table h = gate_table(G_H, 0.0);
-  return apply_1q(apply_cx(apply_1q(in, t, h), c, t), t, h);
+  if (g == G_CZ) {  // CZ = H(t) CX(c, t) H(t)
+    const Table h = gate_table(G_H, 0.0);
+    return apply_1q(apply_cx(apply_1q(in, t, h), c, t), t, h);
+  }
+  return apply_2q_table(in, c, t, gate_table_2q(g, 0.0));
+}
+
+PauliSum apply_gate(const PauliSum& in, const Instr& g) {
+  if (g.g >= G_RXX && g.g <= G_CP) return apply_2q_table(in, g.q0, g.q1, gate_table_2q(g.g, g.theta));
+  if (is_two_qubit(g.g)) return apply_2q(in, g.g, g.q0, g.q1);
+  return apply_1q(in, g.q0, gate_table(g.g, g.theta));
 }
 
 void prune(PauliSum& s, double eps, double* pruned) {
@@ -207,10 +340,7 @@ void prune(PauliSum& s, double eps, double* pruned) {
 
 PauliSum run_gate_mode(PauliSum s, const std::vector<Instr>& ins, double eps, double* pruned) {
   for (const auto& g : ins) {
-    if (is_two_qubit(g.g))
-      s = apply_2q(s, g.g, g.q0, g.q1);
-    else
-      s = apply_1q(s, g.q0, gate_table(g.g, g.theta));
+    s = apply_gate(s, g);
     prune(s, eps, pruned);
   }
   return s;
@@ -367,9 +497,38 @@ PauliSum run_plan_mode(PauliSum s, int n, const std::vector<Op>& ops, double eps
       s = apply_u(s, n, op);
       prune(s, eps, pruned);
     } else {
-      for (const auto& g : op.two) s = apply_2q(s, g.g, g.q0, g.q1);
+      for (const auto& g : op.two) s = apply_gate(s, g);
     }
   }
+  return s;
+}
+
+// --- push-through mode -------------------------------------------------------
+// With D the product of the Clifford gates before a non-Clifford gate G, the
+// circuit equals (all its Clifford gates) x ... x (D^dagger G D) x ..., the
+// non-Clifford factors in circuit order.  Conjugation by D^dagger G D is done
+// literally: forward through the Clifford gates before G, through G, and back
+// through their inverses in reverse order; the Clifford gates are applied once
+// more, all of them, at the end.  eps > 0 prunes after every non-Clifford gate.
+int inverse_gate(int g);
+
+PauliSum run_push_mode(PauliSum s, const std::vector<Instr>& ins, double eps, double* pruned) {
+  std::vector<Instr> prefix;
+  for (const auto& g : ins) {
+    if (is_clifford(g.g)) {
+      prefix.push_back(g);
+      continue;
+    }
+    for (const auto& c : prefix) s = apply_gate(s, c);
+    s = apply_gate(s, g);
+    for (auto it = prefix.rbegin(); it != prefix.rend(); ++it) {
+      Instr inv = *it;
+      inv.g = inverse_gate(inv.g);
+      s = apply_gate(s, inv);
+    }
+    prune(s, eps, pruned);
+  }
+  for (const auto& c : prefix) s = apply_gate(s, c);
   return s;
 }
 
@@ -418,7 +577,8 @@ int inverse_gate(int g) {
 extern "C" {
 
 // Propagate generators through a circuit.
-//   mode 0 = gate mode, 1 = plan mode, 2 = plan mode with qubit-wise grouping.
+//   mode 0 = gate mode, 1 = plan mode, 2 = plan mode with qubit-wise grouping,
+//   3 = push-through mode.
 //   Generators: if n_init == 0, Z_j for j in [gen_begin, gen_end); otherwise the
 //   n_init strings in init (n letters each, concatenated) with weights init_w.
 //   nthreads: generators are independent, so they are split across threads.
@@ -458,8 +618,9 @@ void* oracle_run(int n, long m, const int* gate, const int* q0, const int* q1,
   res->gens.resize(G);
   res->pruned.assign(G, 0.0);
   auto work = [&](int g) {
-    PauliSum out = mode >= 1 ? run_plan_mode(start[g], n, plan.ops, eps, &res->pruned[g])
-                             : run_gate_mode(start[g], ins, eps, &res->pruned[g]);
+    PauliSum out = mode == 3   ? run_push_mode(start[g], ins, eps, &res->pruned[g])
+                   : mode >= 1 ? run_plan_mode(start[g], n, plan.ops, eps, &res->pruned[g])
+                               : run_gate_mode(start[g], ins, eps, &res->pruned[g]);
     res->gens[g].assign(out.begin(), out.end());
   };
   if (nthreads <= 1 || G <= 1) {
@@ -496,6 +657,8 @@ void* oracle_run_sum(int n, long m, const int* gate, const int* q0, const int* q
     for (auto& op : ops)
       if (op.one_qubit) create_lut(n, op);
     out = run_plan_mode(s, n, ops, eps, &res->pruned[0]);
+  } else if (mode == 3) {
+    out = run_push_mode(s, ins, eps, &res->pruned[0]);
   } else {
     out = run_gate_mode(s, ins, eps, &res->pruned[0]);
   }

@@ -65,7 +65,14 @@ struct FanStep {
   size_t op_index;           // position of the U operator in the chain
 };
 
-enum StepKind { kStepCliff = 0, kStepFan = 1 };
+// A Pauli rotation exp(-i phi P / 2) as a device step: a string Q that
+// anticommutes with P becomes cos phi Q + sin phi (i Q P), and i Q P = +-(Q xor P).
+struct RotStep {
+  uint64_t px[kMaxWords], pz[kMaxWords];  // the Hermitian string P (bits beyond n clear)
+  double c, s;                            // cos phi, sin phi (within 2^-50 of 0, +-1: exact)
+};
+
+enum StepKind { kStepCliff = 0, kStepFan = 1, kStepRot = 2 };
 struct Step {
   int kind;
   int index;              // into passes or fans
@@ -91,6 +98,7 @@ struct qx_plan {
   std::vector<std::vector<qx::Table3>> luts;       // per chain op (empty for V)
   std::vector<qx::CliffPass> passes;
   std::vector<qx::FanStep> fans;
+  std::vector<qx::RotStep> rots;
   std::vector<qx::Step> program;
   uint64_t ops_after_last_fan = 0;
   qx_plan_device* dev = nullptr;

@@ -6,6 +6,7 @@
 // or from cudaMallocAsync on the caller's stream; nothing is allocated with a
 // blocking call on the hot path.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -270,6 +271,31 @@ FanQ to_dev(const FanQubit& f) {
   return d;
 }
 
+RotQ to_dev(const RotStep& r) {
+  RotQ d{};
+  for (int k = 0; k < kMaxWords; ++k) {
+    d.px[k] = r.px[k];
+    d.pz[k] = r.pz[k];
+  }
+  // rank bit: the lowest bit of P's support (x plane if P has X or Y there)
+  for (int k = 0; k < kMaxWords; ++k) {
+    const uint64_t sup = r.px[k] | r.pz[k];
+    if (!sup) continue;
+    d.rword = k;
+    d.rbit = __builtin_ctzll(sup);
+    d.rx = ((r.px[k] >> d.rbit) & 1) ? 1 : 0;
+    break;
+  }
+  const double t[3][3] = {{r.c, r.s, 0.0}, {r.s, r.c, 0.0}, {0.0, 0.0, 0.0}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      d.tab.t[a][b] = t[a][b];
+      d.tab.th[a][b] = float(t[a][b]);
+      d.tab.tl[a][b] = float(t[a][b] - double(d.tab.th[a][b]));
+    }
+  return d;
+}
+
 // Scratch of one propagation (freed at the end, stream-ordered).
 struct Scratch {
   unsigned long long* ncnt = nullptr;  // [0], [1]: term counts; [2]: scan total
@@ -296,12 +322,12 @@ struct Scratch {
 // Kernel classes of qx_prop_stats.kc_*.
 enum KernelClass {
   KC_INIT = 0, KC_CLIFF, KC_MASK, KC_INSERT, KC_EMIT, KC_COUNT, KC_SCAN, KC_EXPAND, KC_COMPACT,
-  KC_STATS, KC_INDEX, KC_INPLACE
+  KC_STATS, KC_INDEX, KC_INPLACE, KC_ROT
 };
 const char* const kKernelClassNames[QX_KC_COUNT] = {
     "init", "clifford_pass", "fan_mask", "merge_insert", "merge_emit", "expand_count",
     "expand_scan", "expand_emit", "prune_compact", "gen_stats", "inplace_index",
-    "merge_inplace"};
+    "merge_inplace", "pauli_rot"};
 
 // Optional CUDA-event timing of every launch, resolved after the final sync.
 struct Timer {
@@ -971,6 +997,66 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   return QX_OK;
 }
 
+// One Pauli rotation step (qx_pauli_rot.cuh): index the terms, count each
+// term's outputs and find its partner, scan, emit.
+template <int W, typename WT>
+qx_status run_rot(Ctx& c, const RotStep& rs, uint64_t ops_before) {
+  c.st.term_updates += (ops_before + 1) * c.N;
+  c.st.fan_steps++;
+  if (c.N == 0) return QX_OK;
+  const size_t N = c.N;
+  const unsigned long long cap = std::max<unsigned long long>(64, 2ull * N);
+  const size_t ntiles = (N + kScanTile - 1) / kScanTile;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t tab_bytes = up(cap * sizeof(IndexSlot) + 16);
+  void* mem = c.al.get(tab_bytes + up((N + ntiles + 1) * 8) + up(N * 8));
+  if (!mem) return fail(QX_ENOMEM, "device allocation for a rotation step failed");
+  auto* b8 = static_cast<unsigned char*>(mem);
+  auto* tab = reinterpret_cast<IndexSlot*>(b8);
+  auto* offs = reinterpret_cast<unsigned long long*>(b8 + tab_bytes);
+  unsigned long long* tsum = offs + N;
+  auto* pidx = reinterpret_cast<long long*>(b8 + tab_bytes + up((N + ntiles + 1) * 8));
+  const RotQ rq = to_dev(rs);
+  TermBuf out;
+  auto body = [&]() -> qx_status {
+    QX_TRY_CUDA(cudaMemsetAsync(tab, 0, cap * sizeof(IndexSlot), c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+    const unsigned grid = grid_for(N, kThreads, c.sms, 8);
+    const auto view = c.cur.view<WT>();
+    c.begin(KC_ROT);
+    k_index_build<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, tab, cap, c.sc.err);
+    k_rot_count<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, rq, tab, cap, offs, pidx);
+    k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, c.sc.ncnt + c.cslot, tsum);
+    k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, c.sc.ncnt + 2);
+    k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, c.sc.ncnt + c.cslot, tsum);
+    QX_TRY_CUDA(cudaGetLastError());
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    QX_TRY(sync_read(c, h, c.sc.ncnt, 40));
+    if (unsigned(h[4]) & kErrProbe) return fail(QX_ECAP, "a hash table ran out of probe slots");
+    const unsigned long long total = h[2];
+    QX_TRY(check_limits(c, total));
+    QX_TRY(alloc_terms(c.al, W, c.wtb, total, &out));
+    k_rot_emit<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, rq, offs, pidx, out.view<WT>());
+    c.end(KC_ROT, 6, (N + total) * (16 * W + sizeof(WT)));
+    QX_TRY_CUDA(cudaGetLastError());
+    const int oslot = 1 - c.cslot;
+    QX_TRY_CUDA(cudaMemcpyAsync(c.sc.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
+    c.st.alg_bytes += (N + total) * (16 * W + sizeof(WT));
+    c.st.children += total;
+    replace_cur(c, out, total, oslot);
+    out = TermBuf();
+    return QX_OK;
+  };
+  const qx_status st = body();
+  c.al.put(mem);
+  if (st != QX_OK) {
+    c.al.put(out.base);
+    return st;
+  }
+  if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
+  return QX_OK;
+}
+
 void free_scratch(Ctx& c) {
   c.al.put(c.sc.table);
   c.al.put(c.sc.payload);
@@ -1038,6 +1124,8 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   for (const Step& stp : p->program) {
     if (stp.kind == kStepCliff) {
       QX_TRY(run_pass<W, WT>(c, p->dev->passes[stp.index]));
+    } else if (stp.kind == kStepRot) {
+      QX_TRY(run_rot<W, WT>(c, p->rots[stp.index], stp.ops_before));
     } else {
       QX_TRY(run_fan<W, WT>(c, p->fans[stp.index], stp.ops_before));
     }

@@ -26,7 +26,31 @@ void clear_error() { g_last_error.clear(); }
 
 namespace {
 
-bool two_qubit(uint32_t g) { return g == QX_CX || g == QX_CZ; }
+bool two_qubit(uint32_t g) { return g == QX_CX || g == QX_CZ || (g >= QX_SWAP && g <= QX_CP); }
+
+bool rotation_2q(uint32_t g) { return g >= QX_RXX && g <= QX_CP; }
+
+// The two-qubit rotation gates as commuting Pauli rotations exp(-i phi P / 2),
+// P given by its letters on (q0, q1) (0 = I, 1 = X, 2 = Y, 3 = Z).  With c the
+// control: CR_s(t) = R_{s_t}(t/2) R_{Z_c s_t}(-t/2), and
+// CP(t) = R_{Z_c}(t/2) R_{Z_t}(t/2) R_{Z_c Z_t}(-t/2) up to a global phase.
+struct PauliRot2 {
+  int l0, l1;
+  double phi;
+};
+std::vector<PauliRot2> gate_rotations(const qx_instr& g) {
+  const double t = g.theta;
+  switch (g.gate) {
+    case QX_RXX: return {{1, 1, t}};
+    case QX_RYY: return {{2, 2, t}};
+    case QX_RZZ: return {{3, 3, t}};
+    case QX_CRX: return {{0, 1, t / 2}, {3, 1, -t / 2}};
+    case QX_CRY: return {{0, 2, t / 2}, {3, 2, -t / 2}};
+    case QX_CRZ: return {{0, 3, t / 2}, {3, 3, -t / 2}};
+    case QX_CP: return {{3, 0, t / 2}, {0, 3, t / 2}, {3, 3, -t / 2}};
+    default: return {};
+  }
+}
 
 // Values within 2^-50 of 0 or +-1 are those values: the composition of gates
 // that is exactly Clifford (k pi/2 rotations, T T = S) then stays exact.
@@ -383,6 +407,145 @@ void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z
   (void)n;
 }
 
+// Rotation step of exp(-i phi P / 2) for P given by letters l0 on wire q0 and
+// l1 on wire q1 (0 = I), with sign +1.
+RotStep make_rot(int n, int q0, int l0, int q1, int l1, double phi) {
+  (void)n;
+  RotStep r{};
+  auto put = [&](int q, int l) {
+    if (l == 0) return;
+    const uint64_t m = 1ull << (q % 64);
+    if (l == 1 || l == 2) r.px[q / 64] |= m;
+    if (l == 2 || l == 3) r.pz[q / 64] |= m;
+  };
+  put(q0, l0);
+  put(q1, l1);
+  r.c = settle(std::cos(phi));
+  r.s = settle(std::sin(phi));
+  return r;
+}
+
+// Pauli in XZ form i^e X^x Z^z (W words).
+struct PauliXZ {
+  uint8_t e = 0;
+  uint64_t x[kMaxWords] = {0, 0}, z[kMaxWords] = {0, 0};
+};
+
+PauliXZ xz_product(int W, const PauliXZ& a, const PauliXZ& b) {
+  PauliXZ r = a;
+  xz_mul(W, &r.e, r.x, r.z, b.e, b.x, b.z);
+  return r;
+}
+
+// Rotation step for exp(-i phi P / 2) with P given in XZ form: the Hermitian
+// string with P's bits and the sign i^(e - |x & z|) (folded into phi).
+RotStep rot_from_xz(int W, const PauliXZ& P, double phi) {
+  RotStep r{};
+  int overlap = 0;
+  for (int k = 0; k < W; ++k) {
+    r.px[k] = P.x[k];
+    r.pz[k] = P.z[k];
+    overlap += __builtin_popcountll(P.x[k] & P.z[k]);
+  }
+  const int ph = ((int(P.e) - overlap) % 4 + 4) % 4;  // 0: +P, 2: -P
+  const double sphi = ph == 0 ? phi : -phi;
+  r.c = settle(std::cos(sphi));
+  r.s = settle(std::sin(sphi));
+  return r;
+}
+
+qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
+  auto* p = new (std::nothrow) qx_plan;
+  if (!p) return fail(QX_ENOMEM, "host allocation failed");
+  const int n = c->n, W = (n + 63) / 64;
+  p->n = n;
+  p->W = W;
+  p->ins = c->ins;
+  // M(s) = D^dagger s D for the Clifford prefix D, kept as the images of X_q
+  // and Z_q; after a Clifford gate g, M'(s) = M(g^dagger s g).
+  std::vector<PauliXZ> MX(n), MZ(n);
+  for (int q = 0; q < n; ++q) {
+    MX[q].x[q / 64] = 1ull << (q % 64);
+    MZ[q].z[q / 64] = 1ull << (q % 64);
+  }
+  auto image = [&](int q, int l) {  // M of the letter l (1 X, 2 Y, 3 Z) on wire q
+    if (l == 1) return MX[q];
+    if (l == 3) return MZ[q];
+    PauliXZ y = xz_product(W, MX[q], MZ[q]);  // Y = i X Z
+    y.e = uint8_t((y.e + 1) & 3);
+    return y;
+  };
+  auto add_rot = [&](const PauliXZ& P, double phi) {
+    p->rots.push_back(rot_from_xz(W, P, phi));
+    p->program.push_back({kStepRot, int(p->rots.size() - 1), 0});
+  };
+  CliffPass all;  // every Clifford gate, in circuit order
+  for (const qx_instr& g : c->ins) {
+    SignedPerm sp;
+    switch (g.gate) {
+      case QX_RX:
+      case QX_RY:
+      case QX_RZ:
+        add_rot(image(g.q0, int(g.gate - QX_RX) + 1), g.theta);
+        continue;
+      case QX_T:
+      case QX_TDG:
+        add_rot(image(g.q0, 3), g.gate == QX_T ? std::atan(1.0) : -std::atan(1.0));
+        continue;
+      case QX_CX: {
+        all.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
+        MX[g.q0] = xz_product(W, MX[g.q0], MX[g.q1]);
+        MZ[g.q1] = xz_product(W, MZ[g.q0], MZ[g.q1]);
+        continue;
+      }
+      case QX_CZ: {
+        all.ops.push_back(encode_op(kOpCZ, g.q0, g.q1, 0));
+        const PauliXZ xa = MX[g.q0], xb = MX[g.q1];
+        MX[g.q0] = xz_product(W, xa, MZ[g.q1]);
+        MX[g.q1] = xz_product(W, MZ[g.q0], xb);
+        continue;
+      }
+      case QX_SWAP:
+        all.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
+        all.ops.push_back(encode_op(kOpCX, g.q1, g.q0, 0));
+        all.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
+        std::swap(MX[g.q0], MX[g.q1]);
+        std::swap(MZ[g.q0], MZ[g.q1]);
+        continue;
+      default:
+        break;
+    }
+    if (rotation_2q(g.gate)) {
+      for (const PauliRot2& r : gate_rotations(g)) {
+        PauliXZ P;
+        if (r.l0) P = image(g.q0, r.l0);
+        if (r.l1) P = r.l0 ? xz_product(W, P, image(g.q1, r.l1)) : image(g.q1, r.l1);
+        add_rot(P, r.phi);
+      }
+      continue;
+    }
+    if (!clifford_image(g.gate, &sp)) return fail(QX_EINVAL, "internal error: unknown gate");
+    uint32_t code = 0;
+    for (int a = 0; a < 3; ++a) code |= (uint32_t(sp.to[a]) | (sp.sign[a] < 0 ? 4u : 0u)) << (3 * a);
+    all.ops.push_back(encode_op(kOpPerm, g.q0, -1, code));
+    // images under the inverse gate (g^dagger s g)
+    SignedPerm inv;
+    const uint32_t ig = g.gate == QX_S ? QX_SDG : g.gate == QX_SDG ? QX_S
+                      : g.gate == QX_SX ? QX_SXDG : g.gate == QX_SXDG ? QX_SX : g.gate;
+    clifford_image(ig, &inv);
+    const PauliXZ nx = image(g.q0, inv.to[0] + 1), nz = image(g.q0, inv.to[2] + 1);
+    MX[g.q0] = nx;
+    MZ[g.q0] = nz;
+    if (inv.sign[0] < 0) MX[g.q0].e = uint8_t((MX[g.q0].e + 2) & 3);
+    if (inv.sign[2] < 0) MZ[g.q0].e = uint8_t((MZ[g.q0].e + 2) & 3);
+  }
+  p->passes.push_back(std::move(all));
+  p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
+  for (auto& pc : p->passes) build_pass_tables(pc, n, W);
+  *out = p;
+  return QX_OK;
+}
+
 qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   auto* p = new (std::nothrow) qx_plan;
   if (!p) return fail(QX_ENOMEM, "host allocation failed");
@@ -409,7 +572,24 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
       ++p->Kp;
       for (size_t i = b; i < e; ++i) {
         const qx_instr& g = c->ins[i];
-        cur.ops.push_back(encode_op(g.gate == QX_CX ? kOpCX : kOpCZ, g.q0, g.q1, 0));
+        if (g.gate == QX_CX || g.gate == QX_CZ) {
+          cur.ops.push_back(encode_op(g.gate == QX_CX ? kOpCX : kOpCZ, g.q0, g.q1, 0));
+        } else if (g.gate == QX_SWAP) {
+          cur.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
+          cur.ops.push_back(encode_op(kOpCX, g.q1, g.q0, 0));
+          cur.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
+        } else {
+          // a two-qubit rotation: the Clifford gates so far run first, then
+          // its Pauli rotations as their own steps
+          p->passes.push_back(std::move(cur));
+          cur = CliffPass();
+          p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
+          for (const PauliRot2& r : gate_rotations(g)) {
+            p->rots.push_back(make_rot(n, g.q0, r.l0, g.q1, r.l1, r.phi));
+            p->program.push_back({kStepRot, int(p->rots.size() - 1), ops_since_fan});
+            ops_since_fan = 0;
+          }
+        }
       }
       ++ops_since_fan;
       continue;
@@ -466,7 +646,14 @@ qx_status inverse_circuit(const qx_circuit* c, qx_circuit** out) {
       case QX_TDG: g.gate = QX_T; break;
       case QX_RX:
       case QX_RY:
-      case QX_RZ: g.theta = -g.theta; break;
+      case QX_RZ:
+      case QX_RXX:
+      case QX_RYY:
+      case QX_RZZ:
+      case QX_CRX:
+      case QX_CRY:
+      case QX_CRZ:
+      case QX_CP: g.theta = -g.theta; break;
       default: break;
     }
   }
@@ -498,7 +685,7 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
   if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
   for (size_t i = 0; i < m; ++i) {
     const qx_instr& g = ins[i];
-    if (g.gate > QX_CZ) return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad gate");
+    if (g.gate > QX_CP) return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad gate");
     if (g.q0 < 0 || g.q0 >= n)
       return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": wire out of range");
     if (two_qubit(g.gate) && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0))
@@ -567,6 +754,12 @@ qx_status qx_group_ops_dag(const qx_circuit* c, qx_plan** out) {
   p->order = std::move(order);
   *out = p;
   return QX_OK;
+}
+
+qx_status qx_group_ops_pushthrough(const qx_circuit* c, qx_plan** out) {
+  clear_error();
+  if (!c || !out) return fail(QX_EINVAL, "NULL argument");
+  return build_plan_pushthrough(c, out);
 }
 
 qx_status qx_plan_order(const qx_plan* p, size_t* m, size_t* order) {

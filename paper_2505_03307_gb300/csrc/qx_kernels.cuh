@@ -1253,3 +1253,5 @@ __global__ void k_copy_terms(TermsT<WT> src, size_t n, TermsT<WT> dst, unsigned 
 
 }  // namespace dev
 }  // namespace qx
+
+#include "qx_pauli_rot.cuh"

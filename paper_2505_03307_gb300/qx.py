@@ -20,6 +20,7 @@ from . import build as _build
 GATE_CODES = {
     "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
     "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
+    "SWAP": 15, "RXX": 16, "RYY": 17, "RZZ": 18, "CRX": 19, "CRY": 20, "CRZ": 21, "CP": 22,
 }
 STATUS = {0: "QX_OK", 1: "QX_EINVAL", 2: "QX_ENOMEM", 3: "QX_EBUDGET", 4: "QX_ECAP",
           5: "QX_ECUDA", 6: "QX_ETIMEOUT", 7: "QX_EUNSUPPORTED"}
@@ -35,7 +36,7 @@ EXPORTED = (
     "qx_server_submit", "qx_server_poll", "qx_server_wait", "qx_server_stats", "qx_server_destroy",
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
-    "qx_group_ops_dag", "qx_plan_order",
+    "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough",
 )
 
 
@@ -65,7 +66,7 @@ class PropOpts(ctypes.Structure):
 
 FLAG_KERNEL_TIMING = 1
 FLAG_NO_INPLACE = 2
-KC_COUNT = 12
+KC_COUNT = 13
 
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
@@ -131,6 +132,7 @@ def load_library():
                                            ctypes.POINTER(_P)]),
         "qx_group_ops": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "qx_group_ops_dag": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "qx_group_ops_pushthrough": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "qx_plan_order": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), _P]),
         "qx_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
         "qx_plan_op": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
@@ -324,10 +326,13 @@ class Circuit:
 
 
 class Plan:
-    def __init__(self, circuit: Circuit, dag=False):
+    def __init__(self, circuit: Circuit, dag=False, pushthrough=False):
         lib = load_library()
         h = _P()
-        fn = lib.qx_group_ops_dag if dag else lib.qx_group_ops
+        if dag and pushthrough:
+            raise ValueError("choose one of dag and pushthrough")
+        fn = (lib.qx_group_ops_dag if dag else
+              lib.qx_group_ops_pushthrough if pushthrough else lib.qx_group_ops)
         _check(fn(circuit._h, ctypes.byref(h)))
         self._h = h
         self.n = circuit.n
@@ -478,10 +483,11 @@ def load_circuit_records(n, records) -> Circuit:
     return Circuit(n, None, records=records)
 
 
-def group_ops(circuit: Circuit, dag=False) -> Plan:
-    """List-order grouping (Sec. III.A), or qubit-wise dependency-graph
-    grouping with dag=True (qx_group_ops_dag)."""
-    return Plan(circuit, dag=dag)
+def group_ops(circuit: Circuit, dag=False, pushthrough=False) -> Plan:
+    """List-order grouping (Sec. III.A); qubit-wise dependency-graph grouping
+    with dag=True (qx_group_ops_dag); Clifford push-through with
+    pushthrough=True (qx_group_ops_pushthrough)."""
+    return Plan(circuit, dag=dag, pushthrough=pushthrough)
 
 
 def propagate(plan: Plan, **kw) -> Result:

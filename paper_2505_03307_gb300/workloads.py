@@ -314,6 +314,59 @@ def random_small(seed: int, n: int, m: int, p2: float = 0.3, angles: str = "unif
     return n, out
 
 
+TWO_QUBIT_ROT = ("RXX", "RYY", "RZZ", "CRX", "CRY", "CRZ", "CP")
+
+
+def random_small_2q(seed: int, n: int, m: int, p2: float = 0.35, angles: str = "uniform"):
+    """``random_small`` with the two-qubit gates beyond CX / CZ mixed in: half
+    of the two-qubit draws are SWAP or a two-qubit rotation (RXX ... CP)."""
+    rng = np.random.default_rng(seed + 104729)
+    _, base = random_small(seed, n, m, p2=p2, angles=angles)
+    out = []
+    for g in base:
+        if g[0] in TWO_QUBIT and rng.random() < 0.5:
+            name = ("SWAP",) + TWO_QUBIT_ROT
+            k = int(rng.integers(0, len(name)))
+            if angles == "quarter":
+                th = int(rng.integers(0, 8)) * math.pi / 4.0
+            else:
+                th = float(rng.uniform(0.0, 2.0 * math.pi))
+            out.append((name[k], g[1], g[2], th if k > 0 else 0.0))
+        else:
+            out.append(g)
+    # at least one of the new gates whenever there is a two-qubit gate
+    if not any(g[0] in ("SWAP",) + TWO_QUBIT_ROT for g in out):
+        for i, g in enumerate(out):
+            if g[0] in TWO_QUBIT:
+                out[i] = ("RZZ", g[1], g[2], float(rng.uniform(0.0, 2.0 * math.pi)))
+                break
+    return n, out
+
+
+def qaoa(seed: int, n: int = 16, layers: int = 2, degree: int = 3):
+    """QAOA-style circuit on a random ``degree``-regular graph: H on every
+    qubit, then per layer RZZ(gamma) on every edge and RX(beta) on every
+    qubit (gamma, beta ~ U[0, pi))."""
+    rng = np.random.default_rng(seed)
+    # random regular graph by repeated perfect matchings on a shuffled ring
+    edges = set()
+    while len(edges) < n * degree // 2:
+        perm = rng.permutation(n)
+        for k in range(0, n - 1, 2):
+            a, b = int(perm[k]), int(perm[k + 1])
+            if a != b and len(edges) < n * degree // 2:
+                edges.add((min(a, b), max(a, b)))
+    edges = sorted(edges)
+    instrs = [_g1("H", q) for q in range(n)]
+    for _ in range(layers):
+        gamma, beta = float(rng.uniform(0, math.pi)), float(rng.uniform(0, math.pi))
+        for a, b in edges:
+            instrs.append(("RZZ", a, b, gamma))
+        for q in range(n):
+            instrs.append(_g1("RX", q, beta))
+    return n, instrs
+
+
 def random_paulis(seed: int, n: int, k: int, min_weight: int = 1):
     """``k`` seeded random Pauli strings ("IXYZ" letters, character i = qubit i)."""
     rng = np.random.default_rng(seed)

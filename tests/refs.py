@@ -75,6 +75,39 @@ def _apply_1q(M, n, q, G):
     return T.reshape(2 ** n, K)
 
 
+def gate_matrix_2q(name, theta=0.0):
+    """4 x 4 matrix on (q0, q1), basis index 2 b(q0) + b(q1) (q0 is the control
+    of the controlled gates)."""
+    c, s = math.cos(theta / 2), math.sin(theta / 2)
+    I4 = np.eye(4, dtype=complex)
+    if name == "SWAP":
+        return np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=complex)
+    if name in ("RXX", "RYY", "RZZ"):
+        P = PAULI[name[1]]
+        return c * I4 - 1j * s * np.kron(P, P)
+    if name in ("CRX", "CRY", "CRZ"):
+        m = np.eye(4, dtype=complex)
+        m[2:, 2:] = gate_matrix("R" + name[2], theta)
+        return m
+    if name == "CP":
+        return np.diag([1, 1, 1, cmath.exp(1j * theta)])
+    raise KeyError(name)
+
+
+def _apply_2q(M, n, a, b, G):
+    """G (4 x 4 on qubits a, b; local index 2 b_a + b_b) applied to the rows of M."""
+    idx = np.arange(2 ** n)
+    base = idx[(((idx >> a) & 1) == 0) & (((idx >> b) & 1) == 0)]
+    out = np.zeros_like(M)
+    for lo in range(4):
+        tgt = base | (((lo >> 1) & 1) << a) | ((lo & 1) << b)
+        for li in range(4):
+            if G[lo, li] != 0:
+                src = base | (((li >> 1) & 1) << a) | ((li & 1) << b)
+                out[tgt] += G[lo, li] * M[src]
+    return out
+
+
 def dense_unitary(n, instrs):
     """2^n x 2^n unitary of the circuit (first instruction applied first)."""
     D = 2 ** n
@@ -87,6 +120,8 @@ def dense_unitary(n, instrs):
         elif g == "CZ":
             sign = np.where(((idx >> a) & 1) & ((idx >> b) & 1), -1.0, 1.0)
             U = U * sign[:, None]
+        elif b >= 0:
+            U = _apply_2q(U, n, a, b, gate_matrix_2q(g, th))
         else:
             U = _apply_1q(U, n, a, gate_matrix(g, th))
     return U

@@ -108,6 +108,23 @@ def _check_passes(n, instrs, seed):
         assert plan.clifford_apply(0, s) == (want_s, int(want_w))
 
 
+@pytest.mark.parametrize("n,seed", [(6, 1), (40, 2), (70, 3), (100, 4)])
+def test_pushthrough_plan_ends_with_the_clifford_part(n, seed):
+    """A push-through plan has no operator chain and one Clifford pass: the
+    circuit's Clifford gates, SWAP as three CX, in order."""
+    _, instrs = W.random_small_2q(seed, n, 4 * n, angles="uniform")
+    plan = qx.group_ops(qx.load_circuit(n, instrs), pushthrough=True)
+    assert plan.info() == (0, 0)
+    assert plan.clifford_passes() == 1
+    cliff = [g for g in instrs if g[0] in ("H", "S", "SDG", "X", "Y", "Z", "SX", "SXDG", "CX", "CZ",
+                                          "SWAP")]
+    starts = W.random_paulis(seed, n, 6)
+    ref = O.propagate(n, cliff, mode="gate", init=[(s, 1.0) for s in starts])
+    for st, r in zip(starts, ref):
+        (want_s, want_w), = O.as_dict(r).items()
+        assert plan.clifford_apply(0, st) == (want_s, int(want_w))
+
+
 @pytest.mark.parametrize("n,m", [(5, 3), (5, 400), (40, 10), (64, 900), (65, 30), (100, 3000),
                                  (128, 2000)])
 def test_clifford_pass_matches_oracle(n, m):

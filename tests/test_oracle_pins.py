@@ -170,6 +170,25 @@ def test_dag_grouping_composes_across_other_wires():
     assert p.keys() == {"XII", "YII"} and abs(p["XII"]) < 1e-15
 
 
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("mode", ["gate", "plan", "dag", "push"])
+def test_dense_two_qubit_rotations_and_push(seed, mode):
+    """SWAP and the two-qubit rotations (16 x 16 tables from 4 x 4 unitaries
+    in the oracle; Kronecker products of textbook matrices here) in every
+    oracle mode, including push-through."""
+    n = 2 + seed % 5
+    _, instrs = W.random_small_2q(seed, n, 12 + 3 * n,
+                                  angles="quarter" if seed % 3 == 0 else "uniform")
+    assert any(g[0] not in ("CX", "CZ") and g[2] >= 0 for g in instrs) or n < 2
+    _check_dense(n, instrs, mode)
+
+
+def test_dense_qaoa_small():
+    n, instrs = W.qaoa(1, n=6, layers=2)
+    for mode in ("gate", "plan", "push"):
+        _check_dense(n, instrs, mode)
+
+
 def test_gate_and_plan_agree_semantically():
     """Gate and plan mode may differ only in keys of weight ~0 (T;T = S)."""
     for seed in range(10):
