@@ -402,21 +402,24 @@ def adjoint_bench(qx, W, steps, warmup=3):
 
 def grouping_bench(qx, W, flush, steps, warmup=3):
     """List-order grouping (Sec. III.A) against qubit-wise grouping
-    (qx_group_ops_dag) on the paper-sized workloads: operator counts, host
-    planning time and device propagation time (CUDA events, L2 flushed)."""
+    (qx_group_ops_dag) and Clifford push-through (qx_group_ops_pushthrough) on
+    the paper-sized workloads and a QAOA circuit of RZZ gates: operator
+    counts, host planning time and device propagation time (CUDA events, L2
+    flushed)."""
     import torch
 
     cases = [("random_layers_n8", W.random_layers(1), 0.0),
              ("brickwork_n50", W.brickwork(1), 0.0),
              ("fan_in_heavy_n50", W.fan_in_heavy(1), 0.0),
-             ("random_pairs_n100", W.random_pairs(1), 1e-14)]
+             ("random_pairs_n100", W.random_pairs(1), 1e-14),
+             ("qaoa_n20_2layers_rzz", W.qaoa(1, n=20, layers=2), 0.0)]
     out = []
     for name, (n, instrs), eps in cases:
         row = {"workload": name, "gates": len(instrs), "eps": eps}
         circ = qx.load_circuit(n, instrs)
-        for mode in ("list", "dag"):
+        for mode in ("list", "dag", "push"):
             t0 = time.perf_counter()
-            plan = qx.group_ops(circ, dag=(mode == "dag"))
+            plan = qx.group_ops(circ, dag=(mode == "dag"), pushthrough=(mode == "push"))
             plan_ms = (time.perf_counter() - t0) * 1e3
             times = []
             for k in range(warmup + steps):
@@ -436,7 +439,8 @@ def grouping_bench(qx, W, flush, steps, warmup=3):
             K, Kp = plan.info()
             row[mode] = {"K": K, "Kp": Kp, "plan_ms": plan_ms,
                          "propagate_ms": statistics.median(times), "final_terms": nterms,
-                         "fan_steps": st["fan_steps"], "merge_passes": st["merge_passes"]}
+                         "fan_steps": st["fan_steps"], "merge_passes": st["merge_passes"],
+                         "clifford_passes": st["clifford_passes"]}
         out.append(row)
     return {"steps": steps, "warmup": warmup, "l2": "flushed between timed steps", "cases": out}
 
