@@ -322,9 +322,17 @@ qx_status qx_plan_derivative(const qx_plan* p, size_t instr, double* d9, int* qu
 qx_status qx_adjoint_dot(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
                          size_t nrot, const int32_t* qubit, const double* d9, double* out);
 
+/* As qx_adjoint_dot for Pauli rotations exp(-i phi P / 2) (the two-qubit
+ * rotation gates): out[r] = sum_g sum_Q m_g(Q) sigma(Q) lam_{lam_gen[g]}(Q xor P_r)
+ * over the strings Q of m that anticommute with P_r, where i Q P_r =
+ * sigma(Q) (Q xor P_r); this is dL/dphi when m and lam are taken right after
+ * the rotation.  px, pz: nrot x W words (host). */
+qx_status qx_adjoint_dot_pauli(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
+                               size_t nrot, const uint64_t* px, const uint64_t* pz, double* out);
+
 /* Tape: a forward pass that keeps the term arrays at the end of every U_k
- * that holds a rotation (per-operator checkpoints), and reverse passes over
- * it.  ckpt_stride s >= 1 keeps every s-th of those states and recomputes
+ * that holds a rotation and after every two-qubit rotation gate (per-operator
+ * checkpoints), and reverse passes over it.  ckpt_stride s >= 1 keeps every s-th of those states and recomputes
  * the others one block at a time during the reverse pass (s = 1 keeps all;
  * 0 picks s = ceil(sqrt(number of such operators))).
  * qx_tape_forward propagates the generators of *o (as qx_propagate) and
@@ -336,7 +344,8 @@ qx_status qx_tape_forward(const qx_plan* p, const qx_prop_opts* o, int ckpt_stri
                           double* values, qx_tape** out);
 /* grad[i] = dL/dtheta_i for L = sum_k a[k] values[k] and every instruction i
  * of the circuit, in the order the circuit was given to qx_group_ops or
- * qx_group_ops_dag (0 for instructions other than RX, RY, RZ); a: nq doubles,
+ * qx_group_ops_dag (0 for instructions without an angle: RX, RY, RZ and
+ * RXX ... CP have one); a: nq doubles,
  * grad: number-of-instructions doubles, host memory.  May be called any
  * number of times with different a. */
 qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad);

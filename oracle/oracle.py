@@ -238,11 +238,22 @@ def expval(n, instrs, q):
 # derivative.
 
 ROTATIONS = ("RX", "RY", "RZ")
+# one Pauli rotation each: the shift rule is exact for these too
+PAULI_ROTATIONS_2Q = ("RXX", "RYY", "RZZ")
+# two or three commuting rotations by theta/2: the weights hold frequencies
+# 1/2 and 1 in theta, so the two-point shift rule does not apply to these
+SPLIT_ROTATIONS_2Q = ("CRX", "CRY", "CRZ", "CP")
 
 
 def rotation_positions(instrs):
     """Indices of the RX / RY / RZ instructions."""
     return [i for i, ins in enumerate(instrs) if ins[0] in ROTATIONS]
+
+
+def angle_positions(instrs):
+    """Indices of every instruction with an angle (one- and two-qubit rotations)."""
+    names = ROTATIONS + PAULI_ROTATIONS_2Q + SPLIT_ROTATIONS_2Q
+    return [i for i, ins in enumerate(instrs) if ins[0] in names]
 
 
 def coeffs(n, instrs, queries, mode="plan", threads=1):
@@ -270,8 +281,8 @@ def grad_shift(n, instrs, queries, a, positions=None, mode="plan", threads=1, wo
 
     def shifted(i, s):
         g, a_, b, th = instrs[i]
-        if g not in ROTATIONS:
-            raise ValueError(f"instruction {i} is not a rotation")
+        if g not in ROTATIONS + PAULI_ROTATIONS_2Q:
+            raise ValueError(f"instruction {i} is not a single Pauli rotation")
         ins = list(instrs)
         ins[i] = (g, a_, b, th + s * np.pi / 2)
         return functional(n, ins, queries, a, mode, threads)
@@ -284,3 +295,22 @@ def grad_shift(n, instrs, queries, a, positions=None, mode="plan", threads=1, wo
     else:
         vals = [shifted(i, s) for i, s in jobs]
     return np.array([(vals[2 * k] - vals[2 * k + 1]) / 2 for k in range(len(positions))])
+
+
+def grad_fd(n, instrs, queries, a, positions, h=1e-5, mode="plan", threads=1, workers=1):
+    """dL/dtheta_i by central differences of oracle propagations (any angle;
+    error about h^2 times the third derivative plus rounding / h)."""
+    def shifted(i, s):
+        g, a_, b, th = instrs[i]
+        ins = list(instrs)
+        ins[i] = (g, a_, b, th + s * h)
+        return functional(n, ins, queries, a, mode, threads)
+
+    jobs = [(i, s) for i in positions for s in (1, -1)]
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            vals = list(ex.map(lambda js: shifted(*js), jobs))
+    else:
+        vals = [shifted(i, s) for i, s in jobs]
+    return np.array([(vals[2 * k] - vals[2 * k + 1]) / (2 * h) for k in range(len(positions))])

@@ -16,7 +16,7 @@ import torch
 
 from . import qx
 
-ROTATIONS = ("RX", "RY", "RZ")
+ROTATIONS = ("RX", "RY", "RZ", "RXX", "RYY", "RZZ", "CRX", "CRY", "CRZ", "CP")
 
 
 class _Coeffs(torch.autograd.Function):
@@ -44,8 +44,9 @@ class RotationCircuit:
     """A circuit whose rotation angles are free parameters.
 
     instrs: (gate, q0, q1, theta) tuples as in ``qx.load_circuit``; the angles
-    of the RX / RY / RZ instructions are taken from ``theta`` in order
-    (``positions`` lists their instruction indices)."""
+    of the rotation instructions (RX / RY / RZ and the two-qubit RXX ... CP)
+    are taken from ``theta`` in order (``positions`` lists their instruction
+    indices)."""
 
     def __init__(self, n, instrs):
         self.n = int(n)

@@ -38,7 +38,8 @@ struct qx_tape {
     size_t instr;
     int q;
     double d[9];
-    size_t j;  // cut point after its U_k
+    size_t j;  // cut point after its U_k (or after the gate, for two-qubit rotations)
+    std::vector<RotTerm> terms;  // two-qubit rotation gates: their Pauli rotations
   };
   std::vector<Rot> rots;
   std::vector<qx_result*> ckpt;  // M_j at cut point j, or nullptr where not kept
@@ -114,15 +115,20 @@ qx_status qx_tape_forward(const qx_plan* p, const qx_prop_opts* o, int ckpt_stri
     // rotations and the cut point after the U_k of each
     for (size_t i = 0; i < t->m; ++i) {
       const uint32_t g = p->ins[i].gate;
-      if (g != QX_RX && g != QX_RY && g != QX_RZ) continue;
       qx_tape::Rot r{};
       r.instr = i;
-      size_t end = 0;
-      const qx_status s = qx_plan_derivative(p, i, r.d, &r.q, &end);
-      if (s != QX_OK) return s;
-      r.j = end;  // replaced by the cut index below
-      t->rots.push_back(r);
-      t->bounds.push_back(end);
+      if (g == QX_RX || g == QX_RY || g == QX_RZ) {
+        size_t end = 0;
+        const qx_status s = qx_plan_derivative(p, i, r.d, &r.q, &end);
+        if (s != QX_OK) return s;
+        r.j = end;  // replaced by the cut index below
+      } else {
+        r.terms = gate_rotation_terms(p->ins[i]);
+        if (r.terms.empty()) continue;
+        r.j = i + 1;  // right after the gate: its rotations commute with each other
+      }
+      t->bounds.push_back(r.j);
+      t->rots.push_back(std::move(r));
     }
     std::sort(t->bounds.begin(), t->bounds.end());
     t->bounds.erase(std::unique(t->bounds.begin(), t->bounds.end()), t->bounds.end());
@@ -192,9 +198,11 @@ qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad) {
   std::vector<qx_result*> tmp(B, nullptr);
   auto body = [&]() -> qx_status {
     QX_TRY_STATUS(advance(t, t->inv[B], &lam));  // Lambda at the last cut point
+    const int W = (t->n + 63) / 64;
     std::vector<int32_t> qs;
-    std::vector<double> ds, outv;
-    std::vector<size_t> who;
+    std::vector<double> ds, outv, pfac;
+    std::vector<size_t> who, pwho;
+    std::vector<uint64_t> pxs, pzs;
     for (size_t j = B; j-- > 0;) {
       const qx_result* M = t->ckpt[j];
       if (!M && !tmp[j]) {  // recompute the block from its kept state
@@ -210,17 +218,40 @@ qx_status qx_tape_backward(qx_tape* t, const double* a, double* grad) {
       qs.clear();
       ds.clear();
       who.clear();
-      for (const auto& r : t->rots)
-        if (r.j == j) {
+      pxs.clear();
+      pzs.clear();
+      pwho.clear();
+      pfac.clear();
+      for (const auto& r : t->rots) {
+        if (r.j != j) continue;
+        if (r.terms.empty()) {
           qs.push_back(r.q);
           ds.insert(ds.end(), r.d, r.d + 9);
           who.push_back(r.instr);
+          continue;
         }
-      outv.assign(qs.size(), 0.0);
-      QX_TRY_STATUS(qx_adjoint_dot(M, lam, lam_of.data(), qs.size(), qs.data(), ds.data(),
-                                   outv.data()));
-      for (size_t r = 0; r < who.size(); ++r)
-        grad[t->order.empty() ? who[r] : t->order[who[r]]] = outv[r];
+        for (const RotTerm& rt : r.terms) {
+          pxs.insert(pxs.end(), rt.px, rt.px + W);
+          pzs.insert(pzs.end(), rt.pz, rt.pz + W);
+          pwho.push_back(r.instr);
+          pfac.push_back(rt.a);
+        }
+      }
+      auto slot = [&](size_t instr) -> double& {
+        return grad[t->order.empty() ? instr : t->order[instr]];
+      };
+      if (!qs.empty()) {
+        outv.assign(qs.size(), 0.0);
+        QX_TRY_STATUS(qx_adjoint_dot(M, lam, lam_of.data(), qs.size(), qs.data(), ds.data(),
+                                     outv.data()));
+        for (size_t r = 0; r < who.size(); ++r) slot(who[r]) = outv[r];
+      }
+      if (!pwho.empty()) {  // dL/dtheta = sum over the gate's rotations of a dL/dphi
+        outv.assign(pwho.size(), 0.0);
+        QX_TRY_STATUS(qx_adjoint_dot_pauli(M, lam, lam_of.data(), pwho.size(), pxs.data(),
+                                           pzs.data(), outv.data()));
+        for (size_t r = 0; r < pwho.size(); ++r) slot(pwho[r]) += pfac[r] * outv[r];
+      }
       qx_free_result(tmp[j]);
       tmp[j] = nullptr;
       if (j > 0) QX_TRY_STATUS(advance(t, t->inv[j], &lam));

@@ -73,6 +73,15 @@ struct RotStep {
 };
 
 enum StepKind { kStepCliff = 0, kStepFan = 1, kStepRot = 2 };
+
+// The Pauli rotations exp(-i a theta P / 2) that make up a two-qubit
+// rotation gate (RXX ... CP), with P's bits and the factor a = dphi/dtheta;
+// empty for other gates.
+struct RotTerm {
+  uint64_t px[kMaxWords], pz[kMaxWords];
+  double a;
+};
+std::vector<RotTerm> gate_rotation_terms(const qx_instr& g);
 struct Step {
   int kind;
   int index;              // into passes or fans

@@ -1436,7 +1436,8 @@ qx_status coeff_impl(qx_result* r, size_t nq, const int32_t* gen, const uint64_t
 // its hash index.
 template <int W, typename WT>
 qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
-                           size_t nrot, const int32_t* qubit, const double* d9, double* out) {
+                           size_t nrot, const int32_t* qubit, const double* d9,
+                           const uint64_t* px, const uint64_t* pz, double* out) {
   if (m->N == 0 || lam->N == 0) {
     std::fill(out, out + nrot, 0.0);
     return QX_OK;
@@ -1479,6 +1480,15 @@ qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32
       const size_t cnt = std::min(chunk, nrot - r0);
       for (size_t r = 0; r < cnt; ++r) {
         hr[r] = AdjRot{};
+        if (px) {  // Pauli rotations: Q -> sigma(Q) (Q xor P); its transpose
+          hr[r].kind = 1;  // maps R to sigma(R xor P) (R xor P) = -sigma(R) (R xor P)
+          for (int k = 0; k < W; ++k) {
+            hr[r].px[k] = px[(r0 + r) * W + k];
+            hr[r].pz[k] = pz[(r0 + r) * W + k];
+          }
+          hr[r].d[0][0] = iter_m ? 1.0 : -1.0;
+          continue;
+        }
         hr[r].q = qubit[r0 + r];
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j)  // iterating lam applies D^T
@@ -1664,10 +1674,35 @@ qx_status qx_adjoint_dot(const qx_result* m, const qx_result* lam, const int32_t
     if (qubit[r] < 0 || qubit[r] >= m->n) return fail(QX_EINVAL, "qubit out of range");
   if (nrot == 0) return QX_OK;
   if (m->wtb == 4)
-    return m->W == 1 ? adjoint_dot_impl<1, float>(m, lam, lam_gen, nrot, qubit, d9, out)
-                     : adjoint_dot_impl<2, float>(m, lam, lam_gen, nrot, qubit, d9, out);
-  return m->W == 1 ? adjoint_dot_impl<1, double>(m, lam, lam_gen, nrot, qubit, d9, out)
-                   : adjoint_dot_impl<2, double>(m, lam, lam_gen, nrot, qubit, d9, out);
+    return m->W == 1 ? adjoint_dot_impl<1, float>(m, lam, lam_gen, nrot, qubit, d9, nullptr, nullptr, out)
+                     : adjoint_dot_impl<2, float>(m, lam, lam_gen, nrot, qubit, d9, nullptr, nullptr, out);
+  return m->W == 1 ? adjoint_dot_impl<1, double>(m, lam, lam_gen, nrot, qubit, d9, nullptr, nullptr, out)
+                   : adjoint_dot_impl<2, double>(m, lam, lam_gen, nrot, qubit, d9, nullptr, nullptr, out);
+}
+
+qx_status qx_adjoint_dot_pauli(const qx_result* m, const qx_result* lam, const int32_t* lam_gen,
+                               size_t nrot, const uint64_t* px, const uint64_t* pz, double* out) {
+  clear_error();
+  cudaGetLastError();
+  if (!m || !lam || !lam_gen) return fail(QX_EINVAL, "NULL argument");
+  if (nrot && (!px || !pz || !out)) return fail(QX_EINVAL, "NULL argument");
+  if (m->n != lam->n || m->wtb != lam->wtb)
+    return fail(QX_EINVAL, "the two states differ in qubit count or precision");
+  for (int g = 0; g < m->G; ++g)
+    if (lam_gen[g] < -1 || lam_gen[g] >= lam->G) return fail(QX_EINVAL, "lam_gen out of range");
+  for (size_t r = 0; r < nrot; ++r)
+    for (int k = 0; k < m->W; ++k) {
+      const int hi = m->n - 64 * k;
+      const uint64_t mask = hi >= 64 ? ~0ull : ((1ull << hi) - 1);
+      if ((px[r * m->W + k] | pz[r * m->W + k]) & ~mask)
+        return fail(QX_EINVAL, "Pauli string has bits beyond qubit n-1");
+    }
+  if (nrot == 0) return QX_OK;
+  if (m->wtb == 4)
+    return m->W == 1 ? adjoint_dot_impl<1, float>(m, lam, lam_gen, nrot, nullptr, nullptr, px, pz, out)
+                     : adjoint_dot_impl<2, float>(m, lam, lam_gen, nrot, nullptr, nullptr, px, pz, out);
+  return m->W == 1 ? adjoint_dot_impl<1, double>(m, lam, lam_gen, nrot, nullptr, nullptr, px, pz, out)
+                   : adjoint_dot_impl<2, double>(m, lam, lam_gen, nrot, nullptr, nullptr, px, pz, out);
 }
 
 qx_status qx_result_shape(const qx_result* r, int* ngen, int* nwords, size_t* nterms) {

@@ -546,6 +546,24 @@ qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
   return QX_OK;
 }
 
+std::vector<RotTerm> gate_rotation_terms(const qx_instr& g) {
+  // the factors do not depend on theta: read them off theta = 1
+  qx_instr one = g;
+  one.theta = 1.0;
+  std::vector<RotTerm> out;
+  for (const PauliRot2& r : gate_rotations(one)) {
+    const RotStep s = make_rot(0, g.q0, r.l0, g.q1, r.l1, 0.0);
+    RotTerm t{};
+    for (int k = 0; k < kMaxWords; ++k) {
+      t.px[k] = s.px[k];
+      t.pz[k] = s.pz[k];
+    }
+    t.a = r.phi;
+    out.push_back(t);
+  }
+  return out;
+}
+
 qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   auto* p = new (std::nothrow) qx_plan;
   if (!p) return fail(QX_ENOMEM, "host allocation failed");

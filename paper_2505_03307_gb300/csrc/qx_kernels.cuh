@@ -1153,10 +1153,14 @@ __global__ void k_ztype_sum(TermsT<WT> t, const unsigned long long* n_in, double
 
 // Derivative of one rotation, in shared memory: its wire and the 3x3 matrix D
 // applied to the letter the iterated side has there.
+// kind 0: the letter on wire q goes through D (a rotation in a one-qubit
+// operator); kind 1: a Pauli rotation about (px, pz), whose derivative map
+// sends an anticommuting string Q to sigma(Q) (Q xor P), scaled by d[0][0].
 struct AdjRot {
   int q;
-  int pad;
+  int kind;
   double d[3][3];
+  uint64_t px[2], pz[2];
 };
 
 constexpr int kAdjMaxRot = 256;  // rotations per launch
@@ -1196,7 +1200,25 @@ __global__ void __launch_bounds__(256) k_adjoint_dot(TermsT<WT> a, size_t na, co
     }
     for (int r = 0; r < nrot; ++r) {
       double c = 0.0;
-      if (gb >= 0) {
+      if (gb >= 0 && s_rot[r].kind == 1) {
+        const AdjRot& pr = s_rot[r];
+        int par = 0, aq = 0, ap = 0, ar = 0, zx = 0;
+        uint64_t xx[W], zz[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          par += __popcll((x[k] & pr.pz[k]) ^ (z[k] & pr.px[k]));
+          xx[k] = x[k] ^ pr.px[k];
+          zz[k] = z[k] ^ pr.pz[k];
+          aq += __popcll(x[k] & z[k]);
+          ap += __popcll(pr.px[k] & pr.pz[k]);
+          ar += __popcll(xx[k] & zz[k]);
+          zx += __popcll(z[k] & pr.px[k]);
+        }
+        if (par & 1) {  // i Q P = sigma (Q xor P)
+          const double sigma = ((1 + aq + ap - ar + 2 * zx) & 3) == 0 ? 1.0 : -1.0;
+          c = w * pr.d[0][0] * sigma * index_find<W>(b, tab, cap, uint32_t(gb), xx, zz);
+        }
+      } else if (gb >= 0) {
         const int q = s_rot[r].q;
         const int L = letter_at<W>(x, z, q);
         if (L) {

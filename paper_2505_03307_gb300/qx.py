@@ -36,7 +36,7 @@ EXPORTED = (
     "qx_server_submit", "qx_server_poll", "qx_server_wait", "qx_server_stats", "qx_server_destroy",
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
-    "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough",
+    "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough", "qx_adjoint_dot_pauli",
 )
 
 
@@ -172,6 +172,7 @@ def load_library():
         "qx_plan_derivative": (ctypes.c_int, [_P, _SZ, _DP, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(_SZ)]),
         "qx_adjoint_dot": (ctypes.c_int, [_P, _P, _P, _SZ, _P, _P, _P]),
+        "qx_adjoint_dot_pauli": (ctypes.c_int, [_P, _P, _P, _SZ, _P, _P, _P]),
         "qx_tape_forward": (ctypes.c_int, [_P, ctypes.POINTER(PropOpts), ctypes.c_int, _SZ, _P, _P,
                                            _P, _P, ctypes.POINTER(_P)]),
         "qx_tape_backward": (ctypes.c_int, [_P, _P, _P]),

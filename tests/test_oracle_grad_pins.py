@@ -152,3 +152,24 @@ def test_shift_sign_mutation_is_caught():
     flipped = (minus - plus) / 2
     assert abs(good[0] + math.sin(0.37)) < 1e-14
     assert abs(flipped + math.sin(0.37)) > 0.5
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_two_qubit_gradients_match_dense_finite_differences(seed):
+    """RXX / RYY / RZZ by the shift rule (one Pauli rotation each), the
+    controlled rotations and CP by central differences of the oracle, both
+    against central differences of the dense unitaries."""
+    n = 3
+    _, ins = W.random_small_2q(seed, n, 16, p2=0.5)
+    rng = np.random.default_rng(200 + seed)
+    strings = ["".join(p) for p in np.array(list("IXYZ"))[rng.integers(0, 4, size=(12, n))]]
+    queries = [(int(rng.integers(0, n)), s) for s in strings]
+    a = rng.normal(size=len(queries))
+    single = [i for i, g in enumerate(ins) if g[0] in O.ROTATIONS + O.PAULI_ROTATIONS_2Q]
+    split = [i for i, g in enumerate(ins) if g[0] in O.SPLIT_ROTATIONS_2Q]
+    assert single
+    assert np.allclose(O.grad_shift(n, ins, queries, a, positions=single),
+                       _dense_fd(n, ins, queries, a, single), atol=1e-8)
+    if split:
+        assert np.allclose(O.grad_fd(n, ins, queries, a, split),
+                           _dense_fd(n, ins, queries, a, split), atol=1e-7)
