@@ -274,6 +274,8 @@ def run_ours(args):
         line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
     if world == 1 and args.adjoint_steps > 0:
         line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
+    if world == 1 and args.large_steps > 0:
+        line["large"] = large_bench(qx, W, flush.zero_, args.large_steps, peak)
     if world == 1 and args.grouping_steps > 0:
         line["grouping"] = grouping_bench(qx, W, flush.zero_, args.grouping_steps)
     if world == 1 and args.xyz_repeats:
@@ -398,6 +400,65 @@ def adjoint_bench(qx, W, steps, warmup=3):
             "angle_gradients_per_s": info["rotations"] / (grad_ms / 1e3),
             "parameter_shift_equivalent_ms": 2 * info["rotations"] * fwd_ms,
             "timing": "host clock around synchronised calls, median of steps"}
+
+
+def large_bench(qx, W, flush, steps, peak, warmup=2):
+    """The HBM-scale configuration: fan_in_deep_n100 (n = 100, 20 RZ on 20
+    fan-out qubits spread over 100,000 gates, 80 x 2^20 + 40 = 83,886,120
+    final terms, 3.4 GB of FP64 terms).  Device time per propagation (CUDA
+    events) and the dominant kernel class's achieved bandwidth (algorithmic
+    bytes over its CUDA-event time, QX_FLAG_KERNEL_TIMING)."""
+    import torch
+
+    n, instrs = W.fan_in_deep(1)
+    circ = qx.load_circuit(n, instrs)
+    plan = qx.group_ops(circ)
+    dag_ms = []
+    dplan = qx.group_ops(circ, dag=True)
+    for k in range(warmup + steps):  # the same circuit with qubit-wise grouping
+        flush()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r = qx.propagate(dplan)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            dag_ms.append(e0.elapsed_time(e1))
+        dag_terms = r.nterms
+        r.free()
+    del dplan
+    times, st = [], None
+    for k in range(warmup + steps):
+        flush()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r = qx.propagate(plan, kernel_timing=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(e0.elapsed_time(e1))
+            st = r.stats()
+        nterms = r.nterms
+        r.free()
+    ms = statistics.median(times)
+    kern = st["kernels"]
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    return {"workload": "fan_in_deep_n100", "final_terms": nterms,
+            "term_bytes": nterms * 44, "steps": steps, "warmup": warmup,
+            "propagate_ms": ms, "term_updates_per_s": st["term_updates"] / (ms / 1e3),
+            "children_per_s": st["children"] / (ms / 1e3),
+            "dominant_kernel": dom, "dominant_share": d["ms"] / sum(v["ms"] for v in kern.values()),
+            "dominant_achieved_gbs": achieved, "dominant_frac_of_peak": achieved / peak,
+            "kernel_ms": {k: round(v["ms"], 3) for k, v in kern.items() if v["ms"] > 0},
+            "qubit_wise_grouping": {"propagate_ms": statistics.median(dag_ms),
+                                    "final_terms": dag_terms},
+            "l2": "flushed between timed steps"}
 
 
 def grouping_bench(qx, W, flush, steps, warmup=3):
@@ -624,6 +685,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
     ap.add_argument("--adjoint-steps", type=int, default=5,
                     help="timed steps of the gradient leg (0: skip)")
+    ap.add_argument("--large-steps", type=int, default=3,
+                    help="timed steps of the 84M-term fan_in_deep_n100 leg (0: skip)")
     ap.add_argument("--grouping-steps", type=int, default=5,
                     help="timed steps per case of the grouping comparison (0: skip)")
     ap.add_argument("--xyz-repeats", default="100,1000,10000,100000",

@@ -460,7 +460,9 @@ qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   c.begin(KC_CLIFF);
   if (dp.use_table) {
-    const unsigned grid = grid_for(c.N, kThreads, c.sms, 2);
+    // as many blocks per SM as their tables fit in shared memory
+    const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (dp.smem + 1024))));
+    const unsigned grid = grid_for(c.N, kThreads, c.sms, per_sm);
     if (dp.cb == 4)
       k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.tab_xz,
                                                                    dp.tab_e, dp.chunks);

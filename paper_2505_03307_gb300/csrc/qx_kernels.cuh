@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
                                                         const uint64_t* tab_xz,
                                                         const uint8_t* tab_e, int chunks) {
   constexpr int E = 1 << (2 * CB);
-  extern __shared__ uint64_t s_tab[];
+  extern __shared__ __align__(16) uint64_t s_tab[];
   uint8_t* s_e = reinterpret_cast<uint8_t*>(s_tab + size_t(chunks) * E * 2 * W);
   {
     const int nw = chunks * E * 2 * W;
@@ -376,15 +376,28 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
       }
       const uint32_t idx = xb | (zb << CB);
       if (!idx) continue;
-      const uint64_t* ent = s_tab + (size_t(c) * E + idx) * 2 * W;
+      // the entry (x words, then z words) in 16-byte loads
+      const ulonglong2* ent = reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
+      uint64_t ex[W], ez[W];
+      if (W == 1) {
+        const ulonglong2 v = ent[0];
+        ex[0] = v.x;
+        ez[0] = v.y;
+      } else {
+        const ulonglong2 v0 = ent[0], v1 = ent[1];
+        ex[0] = v0.x;
+        ex[W - 1] = v0.y;
+        ez[0] = v1.x;
+        ez[W - 1] = v1.y;
+      }
       int anti = 0;
 #pragma unroll
-      for (int kk = 0; kk < W; ++kk) anti += __popcll(az[kk] & ent[kk]);
+      for (int kk = 0; kk < W; ++kk) anti += __popcll(az[kk] & ex[kk]);
       e += int(s_e[c * E + idx]) + 2 * anti;
 #pragma unroll
       for (int kk = 0; kk < W; ++kk) {
-        ax[kk] ^= ent[kk];
-        az[kk] ^= ent[W + kk];
+        ax[kk] ^= ex[kk];
+        az[kk] ^= ez[kk];
       }
     }
     int c2 = 0;
@@ -438,24 +451,21 @@ __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const u
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        uint64_t v = m[a][k];
-        // OR within the peer group through shuffles over its members
-        unsigned rest = peers;
-        uint64_t acc = 0;
-        while (rest) {
-          const int src = __ffs(rest) - 1;
-          rest &= rest - 1;
-          acc |= __shfl_sync(peers, v, src);
-        }
-        m[a][k] = acc;
+      for (int k = 0; k < W; ++k) {  // OR over the lanes of the same generator
+        const unsigned lo = __reduce_or_sync(peers, unsigned(m[a][k]));
+        const unsigned hi = __reduce_or_sync(peers, unsigned(m[a][k] >> 32));
+        m[a][k] = (uint64_t(hi) << 32) | lo;
       }
     if (valid && lane == leader) {
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < W; ++k)
-          if (m[a][k]) atomicOr(&gmask[(size_t(g) * 3 + a) * W + k], m[a][k]);
+        for (int k = 0; k < W; ++k) {
+          unsigned long long* dst = &gmask[(size_t(g) * 3 + a) * W + k];
+          // bits are only ever set: skip the atomic when they are all there
+          // already (a stale read costs at most a redundant atomic)
+          if (m[a][k] && (__ldcg(dst) & m[a][k]) != m[a][k]) atomicOr(dst, m[a][k]);
+        }
     }
   }
 }
