@@ -117,7 +117,7 @@ typedef struct {
 #define QX_FLAG_NO_INPLACE 2u
 
 /* Kernel classes of qx_prop_stats.kc_* (names from qx_kernel_class_name). */
-#define QX_KC_COUNT 13
+#define QX_KC_COUNT 15
 
 /* Counters of one propagation (metrics and launch accounting). */
 typedef struct {

@@ -12,7 +12,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libqx.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["qx_host.cpp", "qx_device.cu", "qx_noalloc.cu", "qx_server.cpp", "qx_adjoint.cpp"]
-HEADERS = ["qx_common.h", "qx_kernels.cuh", "qx_merge_fast.cuh", "qx_merge_inplace.cuh", "qx_pauli_rot.cuh"]
+HEADERS = ["qx_common.h", "qx_kernels.cuh", "qx_merge_fast.cuh", "qx_merge_inplace.cuh", "qx_merge_blocks.cuh", "qx_pauli_rot.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

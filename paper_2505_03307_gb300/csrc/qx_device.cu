@@ -268,6 +268,7 @@ FanQ to_dev(const FanQubit& f) {
     for (int c = 0; c < 3; ++c) d.col[a][c] = f.col[a][c];
     d.iso[a] = f.iso[a] ? 1 : 0;
   }
+  fanq_set_nz(&d);
   return d;
 }
 
@@ -293,6 +294,7 @@ RotQ to_dev(const RotStep& r) {
       d.tab.th[a][b] = float(t[a][b]);
       d.tab.tl[a][b] = float(t[a][b] - double(d.tab.th[a][b]));
     }
+  fanq_set_nz(&d.tab);
   return d;
 }
 
@@ -322,12 +324,12 @@ struct Scratch {
 // Kernel classes of qx_prop_stats.kc_*.
 enum KernelClass {
   KC_INIT = 0, KC_CLIFF, KC_MASK, KC_INSERT, KC_EMIT, KC_COUNT, KC_SCAN, KC_EXPAND, KC_COMPACT,
-  KC_STATS, KC_INDEX, KC_INPLACE, KC_ROT
+  KC_STATS, KC_INDEX, KC_INPLACE, KC_ROT, KC_BLOCK_SETUP, KC_BLOCK
 };
 const char* const kKernelClassNames[QX_KC_COUNT] = {
     "init", "clifford_pass", "fan_mask", "merge_insert", "merge_emit", "expand_count",
     "expand_scan", "expand_emit", "prune_compact", "gen_stats", "inplace_index",
-    "merge_inplace", "pauli_rot"};
+    "merge_inplace", "pauli_rot", "block_setup", "merge_blocks"};
 
 // Optional CUDA-event timing of every launch, resolved after the final sync.
 struct Timer {
@@ -773,11 +775,148 @@ qx_status run_merges_inplace(Ctx& c, const std::vector<const FanQubit*>& mq, boo
   return QX_OK;
 }
 
+// The merge wires of a step in place, with the terms in block order (see
+// qx_merge_blocks.cuh).  *done is false when some block is incomplete (or the
+// step does not fit the block code); the terms are then unchanged.
+template <int W, typename WT>
+qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
+                            bool* done) {
+  *done = false;
+  const int m = int(mq.size());
+  if (m > kMaxBlockWires) return QX_OK;
+  BlockWires hb{};
+  hb.m = m;
+  for (int j = 0; j < m; ++j) {
+    hb.q[j] = mq[j]->q;
+    int r = 0;
+    hb.canon[j] = 255;
+    for (int a = 0; a < 3; ++a) {
+      if (mq[j]->iso[a]) {
+        hb.rank[j][a] = 255;
+        continue;
+      }
+      if (hb.canon[j] == 255) hb.canon[j] = uint8_t(a);
+      hb.rank[j][a] = uint8_t(r++);
+    }
+    hb.radix[j] = uint8_t(r);
+    if (r < 2) return QX_OK;
+  }
+  const size_t N = c.N;
+  const unsigned long long bcap = std::max<unsigned long long>(1024, 2ull * N);
+  const size_t ntiles = (bcap + kScanTile - 1) / kScanTile;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += up(bytes);
+    return o;
+  };
+  const size_t o_tab = take(bcap * 16), o_cnt = take(bcap * 4), o_exp = take(bcap * 4),
+               o_off = take((bcap + ntiles + 1) * 8), o_n = take(32), o_slot = take(N * 4),
+               o_pib = take(N * 4), o_code = take(N * 8), o_code2 = take(N * 8),
+               o_w = take(N * sizeof(WT)), o_bw = take(sizeof(BlockWires)), o_ops = take(256);
+  void* mem = c.al.get(off);
+  if (!mem) return QX_OK;
+  auto* b8 = static_cast<unsigned char*>(mem);
+  auto* btab = reinterpret_cast<ulonglong2*>(b8 + o_tab);
+  auto* bcnt = reinterpret_cast<unsigned*>(b8 + o_cnt);
+  auto* bexp = reinterpret_cast<unsigned*>(b8 + o_exp);
+  auto* boff = reinterpret_cast<unsigned long long*>(b8 + o_off);
+  auto* dn = reinterpret_cast<unsigned long long*>(b8 + o_n);  // [0] bcap, [1] scan total
+  auto* bslot = reinterpret_cast<unsigned*>(b8 + o_slot);
+  auto* pib = reinterpret_cast<unsigned*>(b8 + o_pib);
+  auto* lcode = reinterpret_cast<unsigned long long*>(b8 + o_code);
+  auto* lcode2 = reinterpret_cast<unsigned long long*>(b8 + o_code2);
+  auto* wtmp = reinterpret_cast<WT*>(b8 + o_w);
+  auto* d_bw = reinterpret_cast<BlockWires*>(b8 + o_bw);
+  auto* d_ops = reinterpret_cast<uint32_t*>(b8 + o_ops);
+  TermBuf out;
+  auto body = [&]() -> qx_status {
+    const unsigned grid = grid_for(N, kThreads, c.sms, 8);
+    const auto view = c.cur.view<WT>();
+    QX_TRY_CUDA(cudaMemsetAsync(btab, 0xff, bcap * 16, c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(bcnt, 0, bcap * 4, c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(d_bw, &hb, sizeof hb, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY_CUDA(cudaMemcpyAsync(dn, &bcap, 8, cudaMemcpyHostToDevice, c.al.s));
+    c.begin(KC_BLOCK_SETUP);
+    k_block_claim<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, d_bw, btab, bcap, bcnt, bexp,
+                                                      bslot, pib, lcode, c.sc.err);
+    k_block_sizes<<<grid_for(bcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(btab, bcap, bcnt,
+                                                                             bexp, boff, c.sc.err);
+    k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
+    k_scan_sums<<<1, 1024, 0, c.al.s>>>(boff + bcap, ntiles, dn + 1);
+    k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
+    QX_TRY_CUDA(cudaGetLastError());
+    // complete blocks only: their sizes must add up to the term count
+    unsigned long long chk[2] = {0, 0};
+    unsigned err = 0;
+    QX_TRY_CUDA(cudaMemcpyAsync(&err, c.sc.err, 4, cudaMemcpyDeviceToHost, c.al.s));
+    QX_TRY(sync_read(c, chk, dn, 16));
+    if (err || chk[1] != N) {
+      QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+      c.tm.end();
+      return QX_OK;
+    }
+    QX_TRY(alloc_terms(c.al, W, c.wtb, N, &out));
+    const auto ov = out.view<WT>();
+    k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, bslot, pib, boff, lcode, ov, lcode2,
+                                                        ov.w);
+    c.end(KC_BLOCK_SETUP, 6, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
+    const WT* src = ov.w;
+    std::vector<uint32_t> relabel;  // letter permutations, applied after every wire
+    for (int j = 0; j < m; ++j) {
+      WT* dst = (j & 1) ? ov.w : wtmp;
+      const int pi = inplace_pi(*mq[j]);
+      if (pi != (0 | (1 << 2) | (2 << 4))) {
+        uint32_t code = 0;
+        for (int p = 0; p < 3; ++p) code |= uint32_t((pi >> (2 * p)) & 3) << (3 * p);
+        relabel.push_back(encode_op(kOpPerm, mq[j]->q, -1, code));
+      }
+      c.begin(KC_BLOCK);
+      k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), pi, lcode2, src,
+                                                       dst);
+      c.end(KC_BLOCK, 1, 2ull * N * (16 * W + sizeof(WT)));
+      src = dst;
+    }
+    if (src != ov.w)
+      QX_TRY_CUDA(cudaMemcpyAsync(ov.w, src, N * sizeof(WT), cudaMemcpyDeviceToDevice, c.al.s));
+    if (!relabel.empty()) {
+      QX_TRY_CUDA(cudaMemcpyAsync(d_ops, relabel.data(), relabel.size() * 4,
+                                  cudaMemcpyHostToDevice, c.al.s));
+      c.begin(KC_CLIFF);
+      k_clifford_ops<W, WT><<<grid, kThreads, relabel.size() * 4, c.al.s>>>(
+          ov, c.sc.ncnt + c.cslot, d_ops, int(relabel.size()));
+      c.end(KC_CLIFF, 1, 2ull * N * 16 * W);
+    }
+    QX_TRY_CUDA(cudaGetLastError());
+    replace_cur(c, out, N, c.cslot);
+    out = TermBuf();
+    *done = true;
+    return QX_OK;
+  };
+  const qx_status st = body();
+  c.al.put(mem);
+  if (st != QX_OK) {
+    c.al.put(out.base);
+    return st;
+  }
+  if (!*done) return QX_OK;
+  c.st.merge_passes += mq.size();
+  c.st.inplace_steps++;
+  c.st.alg_bytes += mq.size() * 2ull * N * (16 * W + sizeof(WT));
+  c.st.children += mq.size() * N;
+  if (!more_after && c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
+  return QX_OK;
+}
+
 template <int W, typename WT>
 qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
                      const std::vector<unsigned long long>& gm) {
   if (c.inplace && inplace_candidate(c, mq, gm)) {
     bool done = false;
+    QX_TRY(run_merges_blocks<W, WT>(c, mq, more_after, &done));
+    if (done) return QX_OK;
     QX_TRY(run_merges_inplace<W, WT>(c, mq, more_after, &done));
     if (done) return QX_OK;
     c.st.inplace_fallbacks++;

@@ -44,7 +44,17 @@ struct FanQ {
   uint8_t col[3][3];
   uint8_t iso[3];
   uint8_t pad;
+  uint16_t nz;   // bit 3a + c: t[a][c] != 0 (integer tests keep the FP64 pipe free)
+  uint16_t pad2;
 };
+
+// Sets FanQ::nz from the table (every builder of a FanQ calls this last).
+inline void fanq_set_nz(FanQ* f) {
+  f->nz = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c)
+      if (f->t[a][c] != 0.0) f->nz = uint16_t(f->nz | (1u << (3 * a + c)));
+}
 
 // ---------------------------------------------------------------------------
 // Weight arithmetic.  FP64 weights multiply and add plainly.  FP32 weights use
@@ -71,7 +81,7 @@ __device__ __forceinline__ double group_sum(const FanQ& f, int col, const bool* 
   double acc = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (has[a] && f.t[a][col] != 0.0) {
+    if (has[a] && ((f.nz >> (3 * a + col)) & 1)) {
       acc = any ? acc + f.t[a][col] * v[a] : f.t[a][col] * v[a];
       any = true;
     }
@@ -86,7 +96,7 @@ __device__ __forceinline__ float group_sum(const FanQ& f, int col, const bool* h
   float sum = 0.f, comp = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (has[a] && f.t[a][col] != 0.0) {
+    if (has[a] && ((f.nz >> (3 * a + col)) & 1)) {
       const float th = f.th[a][col];
       const float p = v[a] * th;
       const float pe = fmaf(v[a], th, -p) + v[a] * f.tl[a][col];
@@ -631,7 +641,7 @@ __device__ __forceinline__ unsigned merge_children(const uint64_t* x, const uint
     double acc = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (((msk >> a) & 1) && fq.t[a][c] != 0.0) {
+      if (((msk >> a) & 1) && ((fq.nz >> (3 * a + c)) & 1)) {
         acc = reached ? acc + fq.t[a][c] * v[a] : fq.t[a][c] * v[a];
         reached = true;
       }
@@ -706,6 +716,7 @@ __global__ void __launch_bounds__(THREADS) k_merge_emit(
 
 #include "qx_merge_fast.cuh"
 #include "qx_merge_inplace.cuh"
+#include "qx_merge_blocks.cuh"
 
 namespace qx {
 namespace dev {

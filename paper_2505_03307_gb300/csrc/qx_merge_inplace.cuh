@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_merge_inplace(TermsT<WT> t, size_t N, i
     for (int a = 0; a < 3; ++a) {
       if (a == p || f.iso[a]) continue;
       const int ca = (pi >> (2 * a)) & 3;
-      const bool need_in = f.t[a][cp] != 0.0, need_out = f.t[p][ca] != 0.0;
+      const bool need_in = (f.nz >> (3 * a + cp)) & 1, need_out = (f.nz >> (3 * p + ca)) & 1;
       if (!need_in && !need_out) continue;
       const uint64_t xa = a <= 1 ? (x | qm) : (x & ~qm);
       const uint64_t za = a >= 1 ? (z | qm) : (z & ~qm);

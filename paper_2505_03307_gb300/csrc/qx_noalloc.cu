@@ -92,6 +92,7 @@ bool fan_qubit_from_table(int q, const double* t9, FanQ* f) {
     if (f->nnz[a] == 0) return false;  // a row of an image table is never zero
     f->iso[a] = (f->nnz[a] == 1 && colcount[f->col[a][0]] == 1) ? 1 : 0;
   }
+  fanq_set_nz(f);
   return true;
 }
 

@@ -66,7 +66,7 @@ class PropOpts(ctypes.Structure):
 
 FLAG_KERNEL_TIMING = 1
 FLAG_NO_INPLACE = 2
-KC_COUNT = 13
+KC_COUNT = 15
 
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
