@@ -73,8 +73,9 @@ __device__ __forceinline__ float wmul(float w, const FanQ& f, int a, int c) {
   return p + fmaf(w, f.tl[a][c], fmaf(w, th, -p));
 }
 
-// sum over the present letters a (in the order X, Y, Z) of t[a][col] v[a];
-// *reached: some present letter reaches col
+// sum over the present letters a (in the order X, Y, Z) of t[a][col] v[a],
+// one fused multiply-add per member starting from 0 (the FP64 pipe is the
+// scarce unit on this GPU); *reached: some present letter reaches col
 __device__ __forceinline__ double group_sum(const FanQ& f, int col, const bool* has,
                                             const double* v, bool* reached) {
   bool any = false;
@@ -82,7 +83,7 @@ __device__ __forceinline__ double group_sum(const FanQ& f, int col, const bool* 
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (has[a] && ((f.nz >> (3 * a + col)) & 1)) {
-      acc = any ? acc + f.t[a][col] * v[a] : f.t[a][col] * v[a];
+      acc = fma(f.t[a][col], v[a], acc);
       any = true;
     }
   }
@@ -642,7 +643,7 @@ __device__ __forceinline__ unsigned merge_children(const uint64_t* x, const uint
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (((msk >> a) & 1) && ((fq.nz >> (3 * a + c)) & 1)) {
-        acc = reached ? acc + fq.t[a][c] * v[a] : fq.t[a][c] * v[a];
+        acc = fma(fq.t[a][c], v[a], acc);
         reached = true;
       }
     }

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
           k.y = ohi;
           if (olo == ~0ull && ohi == ~0ull) {
             slot = unsigned(p);
+            bexp[slot] = stride;  // the claimant records the block's size
             break;
           }
         }
@@ -105,7 +106,6 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
         bslot[i] = slot;
         pib[i] = pos;
         lcode[i] = code;
-        bexp[slot] = stride;  // every member writes the same size
       }
     }
     // member counts, one atomic per block and warp
