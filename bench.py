@@ -274,6 +274,8 @@ def run_ours(args):
         line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
     if world == 1 and args.adjoint_steps > 0:
         line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
+    if world == 1 and args.fp32_steps > 0:
+        line["fp32"] = fp32_bench(qx, plan, flush.zero_, args.fp32_steps, step_ms)
     if world == 1 and args.large_steps > 0:
         line["large"] = large_bench(qx, W, flush.zero_, args.large_steps, peak)
     if world == 1 and args.grouping_steps > 0:
@@ -400,6 +402,42 @@ def adjoint_bench(qx, W, steps, warmup=3):
             "angle_gradients_per_s": info["rotations"] / (grad_ms / 1e3),
             "parameter_shift_equivalent_ms": 2 * info["rotations"] * fwd_ms,
             "timing": "host clock around synchronised calls, median of steps"}
+
+
+def fp32_bench(qx, plan, flush, steps, fp64_step_ms, warmup=3):
+    """The main workload with FP32 weights and compensated arithmetic: time
+    per step (CUDA events, L2 flushed) and the largest relative error against
+    the FP64 result over three heavy generators (|w| > 1e-6)."""
+    import torch
+
+    times = []
+    for k in range(warmup + steps):
+        flush()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r = qx.propagate(plan, precision=32)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(e0.elapsed_time(e1))
+        if k < warmup + steps - 1:
+            r.free()
+    st = r.stats()
+    ref = qx.propagate(plan)
+    worst = 0.0
+    for g in (16, 33, 49):
+        a, b = r.export_dict(g), ref.export_dict(g)
+        assert a.keys() == b.keys()
+        for key, w in b.items():
+            if abs(w) > 1e-6:
+                worst = max(worst, abs(a[key] - w) / abs(w))
+    ms = statistics.median(times)
+    return {"precision": 32, "ms_per_step": ms, "term_updates_per_s": st["term_updates"] / (ms / 1e3),
+            "speedup_vs_fp64": statistics.median(fp64_step_ms) / ms,
+            "max_rel_error_vs_fp64": worst, "error_sample": "generators 16, 33, 49, |w| > 1e-6",
+            "l2": "flushed between timed steps"}
 
 
 def large_bench(qx, W, flush, steps, peak, warmup=2):
@@ -685,6 +723,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
     ap.add_argument("--adjoint-steps", type=int, default=5,
                     help="timed steps of the gradient leg (0: skip)")
+    ap.add_argument("--fp32-steps", type=int, default=5,
+                    help="timed steps of the FP32 leg (0: skip)")
     ap.add_argument("--large-steps", type=int, default=3,
                     help="timed steps of the 84M-term fan_in_deep_n100 leg (0: skip)")
     ap.add_argument("--grouping-steps", type=int, default=5,
