@@ -134,6 +134,7 @@ typedef struct {
   uint64_t clifford_passes;    /* fused Clifford passes */
   uint64_t inplace_steps;      /* fan-out steps whose merges ran in place */
   uint64_t inplace_fallbacks;  /* in-place attempts that found an open group */
+  uint64_t block_steps;        /* in-place steps that ran in block order */
   /* per kernel class: launches, algorithmic bytes (terms each launch must
    * read and write, 16W+8 bytes per term), and device milliseconds (only with
    * QX_FLAG_KERNEL_TIMING; 0 otherwise) */

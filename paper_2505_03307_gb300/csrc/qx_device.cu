@@ -904,6 +904,7 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
   if (!*done) return QX_OK;
   c.st.merge_passes += mq.size();
   c.st.inplace_steps++;
+  c.st.block_steps++;
   c.st.alg_bytes += mq.size() * 2ull * N * (16 * W + sizeof(WT));
   c.st.children += mq.size() * N;
   if (!more_after && c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));

@@ -80,9 +80,11 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       pack_full_key(x, z, t.g[i], n, &lo, &hi);
       unsigned long long p = __umul64hi(slot_hash(lo, hi), bcap);
       for (unsigned long long probe = 0; probe < bcap; ++probe) {
-        // a block has many members: read first and compare-and-swap only an
-        // empty slot, so that the members of a claimed block do not contend
-        ulonglong2 k = __ldcg(&btab[p]);
+        // a block has many members: read first (a cached read may be stale
+        // only as "empty", which the compare-and-swap corrects; keys never
+        // change once written) and compare-and-swap only an empty slot, so
+        // that the members of a claimed block do not contend
+        ulonglong2 k = btab[p];
         if (k.x == ~0ull && k.y == ~0ull) {
           unsigned long long olo, ohi;
           cas128(&btab[p].x, ~0ull, ~0ull, lo, hi, &olo, &ohi);

@@ -71,7 +71,7 @@ KC_COUNT = 15
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
             "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes",
-            "inplace_steps", "inplace_fallbacks")
+            "inplace_steps", "inplace_fallbacks", "block_steps")
 
 
 class ServerOpts(ctypes.Structure):

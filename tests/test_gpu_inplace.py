@@ -49,6 +49,7 @@ def test_bench_workload_in_place_equals_general(precision):
     b = qx.propagate(plan, precision=precision, inplace=False)
     sa, sb = a.stats(), b.stats()
     assert sa["inplace_steps"] == 1 and sa["inplace_fallbacks"] == 0
+    assert sa["block_steps"] == 1
     assert sb["inplace_steps"] == 0
     assert sa["merge_passes"] == sb["merge_passes"] == 16
     assert a.nterms == b.nterms == 2228256
@@ -95,3 +96,28 @@ def test_open_groups_fall_back_with_equal_results(case):
     _same(a, b)
     st = a.stats()
     assert st["inplace_steps"] + st["inplace_fallbacks"] <= st["fan_steps"]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_radix_three_blocks_equal_general(seed):
+    """Every generator gets all three letters on the wires 0..4 (a full
+    rotation after a CX chain spreads X), then, after a CZ on wires 5 and 6
+    only, a second rotation on wires 0..4 whose table has a full X and Y row:
+    closed groups of three, so the blocks have radix 3 on every merge wire."""
+    n = 7
+    rng = np.random.default_rng(seed)
+    ins = [("H", q, -1, 0.0) for q in range(n)]
+    ins += [("CX", q, q + 1, 0.0) for q in range(4)]
+    wires = list(range(5))
+    for q in wires:  # X -> all three letters
+        ins += [("RZ", q, -1, float(rng.uniform(0.2, 1.3))), ("RY", q, -1, float(rng.uniform(0.2, 1.3)))]
+    ins.append(("CZ", 5, 6, 0.0))  # ends the operator without touching a merge wire
+    for q in wires:
+        ins += [("RZ", q, -1, float(rng.uniform(0.2, 1.3))), ("RX", q, -1, float(rng.uniform(0.2, 1.3)))]
+    plan = qx.group_ops(qx.load_circuit(n, ins))
+    a = qx.propagate(plan)
+    b = qx.propagate(plan, inplace=False)
+    _same(a, b)
+    compare_result(a, O.propagate(n, ins, mode="plan"))
+    st = a.stats()
+    assert st["block_steps"] == 1 and st["inplace_fallbacks"] == 0
