@@ -429,6 +429,13 @@ qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const uint64_t* x,
                                 double* out_w, uint32_t* out_gen, size_t out_cap, size_t* n_out,
                                 void* stream);
 
+/* Self-test of the device-side bounded wait that every wait of the library
+ * uses: one warp waits for a flag that another warp of the same block
+ * publishes only when publish != 0.  Returns QX_OK when the wait ended, or
+ * QX_ETIMEOUT when it gave up after about timeout_ms (0: 2000 ms); the
+ * device stays usable either way.  QX_EUNSUPPORTED without a GPU. */
+qx_status qx_wait_selftest(uint32_t timeout_ms, int publish);
+
 void qx_free_circuit(qx_circuit* c);
 void qx_free_plan(qx_plan* p);
 void qx_free_result(qx_result* r);

@@ -1992,6 +1992,31 @@ qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint
   return s;
 }
 
+qx_status qx_wait_selftest(uint32_t timeout_ms, int publish) {
+  clear_error();
+  cudaGetLastError();
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(QX_EUNSUPPORTED, "no CUDA device is available");
+  }
+  const unsigned ms = timeout_ms ? timeout_ms : 2000;
+  const unsigned limit = std::max(1024u, std::min(ms, 60000u) * 16000u);
+  unsigned* d = nullptr;
+  QX_TRY_CUDA(cudaMalloc(&d, 8));
+  unsigned h[2] = {0, 0};
+  cudaError_t e = cudaMemset(d, 0, 8);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 64>>>(d, publish, limit, d + 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, 8, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(QX_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  if (h[1]) return fail(QX_ETIMEOUT, "a device-side wait gave up (no publish)");
+  return QX_OK;
+}
+
 const char* qx_kernel_class_name(int k) {
   return (k >= 0 && k < QX_KC_COUNT) ? kKernelClassNames[k] : "";
 }

@@ -499,6 +499,29 @@ struct Slot {
   unsigned ready;          // epoch of the last publish
 };
 
+// Waits until *flag == want (acquire), at most `limit` rounds of a short
+// sleep; false when it gave up.  Every device-side wait of the library is one
+// of these, so a missing publish ends in an error status, never a hang.
+__device__ __forceinline__ bool bounded_wait_eq(const unsigned* flag, unsigned want,
+                                                unsigned limit) {
+  unsigned it = 0;
+  while (ld_acquire(flag) != want) {
+    if (++it > limit) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Self-test of the bounded wait: warp 1 of the single block waits for a flag
+// that warp 0 publishes only when `publish` is set.  err[0] = 1 when the wait
+// gave up.
+static __global__ void k_wait_selftest(unsigned* flag, int publish, unsigned limit,
+                                       unsigned* err) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0 && lane == 0 && publish) st_release(flag, 1u);
+  if (warp == 1 && lane == 0 && !bounded_wait_eq(flag, 1u, limit)) *err = 1u;
+}
+
 template <int W, typename WT = double>
 __global__ void __launch_bounds__(256) k_merge_insert(
     TermsT<WT> t, const unsigned long long* n_in, int q, const __grid_constant__ FanQ fq_p,
@@ -553,14 +576,10 @@ __global__ void __launch_bounds__(256) k_merge_insert(
           continue;
         }
         if (cur == tag) {
-          unsigned it = 0;
-          while (ld_acquire(&s->ready) != epoch) {
-            if (++it > spin_limit) {
-              lead[i] = 0xffffffffu;  // not a leader: emits nothing
-              atomicOr(err, kErrSpin);
-              return;
-            }
-            __nanosleep(32);
+          if (!bounded_wait_eq(&s->ready, epoch, spin_limit)) {
+            lead[i] = 0xffffffffu;  // not a leader: emits nothing
+            atomicOr(err, kErrSpin);
+            return;
           }
           const unsigned ld = ld_relaxed(&s->leader);
           bool same = t.g[ld] == g;

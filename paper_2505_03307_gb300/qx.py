@@ -37,6 +37,7 @@ EXPORTED = (
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
     "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough", "qx_adjoint_dot_pauli",
+    "qx_wait_selftest",
 )
 
 
@@ -179,6 +180,7 @@ def load_library():
         "qx_tape_info": (ctypes.c_int, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ),
                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
         "qx_free_tape": (None, [_P]),
+        "qx_wait_selftest": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int]),
         "qx_merge_qubit_static": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.c_int, _P, _P, _P, _P,
                                                  ctypes.c_int, _DP, _P, _P, _P, _P, _SZ,
                                                  ctypes.POINTER(_SZ), _P]),
@@ -529,6 +531,11 @@ def expval(plan: Plan, paulis, **kw):
     _check(load_library().qx_expval(plan._h, G, x.ctypes.data_as(_U64P), z.ctypes.data_as(_U64P),
                                      ctypes.byref(o), out.ctypes.data_as(_DP)))
     return out[:G]
+
+
+def wait_selftest(timeout_ms=100, publish=False):
+    """qx_wait_selftest: raises QxError (QX_ETIMEOUT) when the wait gave up."""
+    _check(load_library().qx_wait_selftest(int(timeout_ms), 1 if publish else 0))
 
 
 def paulis_to_arrays(paulis, n):
