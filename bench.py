@@ -161,7 +161,7 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
-        r = qx.propagate(plan, kernel_timing=True)
+        r = qx.propagate(plan)
         r.free()
     torch.cuda.synchronize()
 
@@ -177,7 +177,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = qx.propagate(plan, kernel_timing=True)
+            r = qx.propagate(plan)
             e1.record(stream)
             stats.append(r.stats())
             r.free()
@@ -191,6 +191,16 @@ def run_ours(args):
     updates = sum(s["term_updates"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
     clocks = clk.summary()
+    # ---- the same steps again with a CUDA event pair around every launch
+    # (kernel shares and the roofline's per-launch times); the events and
+    # their readout add host work, so these steps are not the timed ones
+    kstats = []
+    for _ in range(args.steps):
+        flush.zero_()
+        r = qx.propagate(plan, kernel_timing=True)
+        kstats.append(r.stats())
+        r.free()
+    torch.cuda.synchronize()
 
     # ---- end to end through the C ABI: host circuit in, host result out
     e2e_ms = []
@@ -231,7 +241,7 @@ def run_ours(args):
     value = updates_all / (total_ms_max / 1e3)
     # ---- roofline of the dominant kernel class
     kc = {}
-    for s in stats:
+    for s in kstats:
         for name, d in s["kernels"].items():
             a = kc.setdefault(name, {"launches": 0, "alg_bytes": 0, "ms": 0.0})
             a["launches"] += d["launches"]
@@ -262,6 +272,10 @@ def run_ours(args):
                      "alg_bytes_per_launch": d["alg_bytes"] / max(1, d["launches"]),
                      "avg_launch_ms": d["ms"] / max(1, d["launches"])},
         "kernel_share": share,
+        # per-step device time of each kernel class (CUDA events around its
+        # launches); the rest of ms_per_step is time between classes
+        "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in kc.items()
+                               if v["launches"]},
         "per_step": {"term_updates": s0["term_updates"], "children": s0["children"],
                      "alg_bytes": s0["alg_bytes"], "kernel_launches": s0["kernel_launches"],
                      "host_syncs": s0["host_syncs"], "K": s0["K"], "Kp": s0["Kp"],

@@ -370,6 +370,22 @@ struct Timer {
 
 thread_local std::vector<cudaEvent_t> t_event_pool;
 
+// Pinned host staging for the small host-to-device copies of a call.  A copy
+// from pageable memory may first wait for the stream to drain, which leaves
+// the GPU idle while the host issues the next launches; from pinned memory it
+// is queued like a launch.  One buffer per host thread (like the event pool);
+// a call's bump offset goes back to 0 whenever it synchronises its stream, at
+// which point its earlier copies are complete.
+constexpr size_t kStageBytes = size_t(256) << 10;
+struct StageBuf {
+  unsigned char* p = nullptr;
+  bool tried = false;
+  ~StageBuf() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local StageBuf t_stage;
+
 struct qx_result {
   int n = 0, W = 1, G = 0;
   int wtb = 8;  // bytes per weight: 8 (FP64) or 4 (FP32)
@@ -410,6 +426,13 @@ struct Ctx {
   Timer tm;
   FastTable* ftab = nullptr;  // pooled merge table of the fast path (held for the call)
   bool inplace = true;        // merge wires may run in place (QX_FLAG_NO_INPLACE clears it)
+  size_t stage_off = 0;       // bytes of t_stage queued since the last stream sync
+  Ctx() = default;
+  Ctx(const Ctx&) = delete;
+  Ctx& operator=(const Ctx&) = delete;
+  ~Ctx() {
+    if (stage_off) cudaStreamSynchronize(al.s);  // the staging buffer is reused next
+  }
   void begin(int k) { tm.begin(k); }
   // after a launch: class, launches it made, algorithmic bytes
   void end(int k, int launches, uint64_t bytes) {
@@ -426,7 +449,30 @@ struct Ctx {
 qx_status sync_read(Ctx& c, void* host, const void* dev, size_t bytes) {
   QX_TRY_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c.al.s));
   QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
+  c.stage_off = 0;
   c.st.host_syncs++;
+  return QX_OK;
+}
+
+// Host-to-device copy of a small host array, through t_stage when it has room.
+qx_status h2d(Ctx& c, void* dev, const void* host, size_t bytes) {
+  if (!bytes) return QX_OK;
+  if (!t_stage.tried) {
+    t_stage.tried = true;
+    if (cudaMallocHost(reinterpret_cast<void**>(&t_stage.p), kStageBytes) != cudaSuccess) {
+      cudaGetLastError();
+      t_stage.p = nullptr;
+    }
+  }
+  const size_t need = (bytes + 63) & ~size_t(63);
+  if (t_stage.p && c.stage_off + need <= kStageBytes) {
+    unsigned char* st = t_stage.p + c.stage_off;
+    std::memcpy(st, host, bytes);
+    c.stage_off += need;
+    QX_TRY_CUDA(cudaMemcpyAsync(dev, st, bytes, cudaMemcpyHostToDevice, c.al.s));
+    return QX_OK;
+  }
+  QX_TRY_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, c.al.s));
   return QX_OK;
 }
 
@@ -753,8 +799,7 @@ qx_status run_merges_inplace(Ctx& c, const std::vector<const FanQubit*>& mq, boo
     QX_TRY_CUDA(cudaMemcpyAsync(view.w, src, N * sizeof(WT), cudaMemcpyDeviceToDevice, c.al.s));
     if (!relabel.empty()) {  // the letters the in-place weights belong to
       auto* d_ops = reinterpret_cast<uint32_t*>(tab);  // the index is no longer needed
-      QX_TRY_CUDA(cudaMemcpyAsync(d_ops, relabel.data(), relabel.size() * 4,
-                                  cudaMemcpyHostToDevice, c.al.s));
+      QX_TRY(h2d(c, d_ops, relabel.data(), relabel.size() * 4));
       c.begin(KC_CLIFF);
       k_clifford_ops<W, WT><<<grid, kThreads, relabel.size() * 4, c.al.s>>>(
           view, c.sc.ncnt + c.cslot, d_ops, int(relabel.size()));
@@ -800,6 +845,23 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
     }
     hb.radix[j] = uint8_t(r);
     if (r < 2) return QX_OK;
+    // packed form: rank by xz code c = x | z << 1 (letters X 1, Z 2, Y 3)
+    const int q = mq[j]->q;
+    const uint64_t qb = 1ull << q;
+    uint32_t inf = uint32_t(q) | (uint32_t(r) << 24) | (15u << 8);  // c = 0: I
+    const int letter_of_code[4] = {-1, 0, 2, 1};  // c -> table letter (0 X, 1 Y, 2 Z)
+    for (int cc = 1; cc < 4; ++cc) {
+      const int a = letter_of_code[cc];
+      inf |= uint32_t(hb.rank[j][a] == 255 ? 15 : hb.rank[j][a]) << (8 + 4 * cc);
+    }
+    hb.inf[j] = inf;
+    if (!mq[j]->iso[0]) hb.niso_x |= qb;
+    if (!mq[j]->iso[1]) hb.niso_y |= qb;
+    if (!mq[j]->iso[2]) hb.niso_z |= qb;
+    if (hb.canon[j] <= 1) hb.canon_x |= qb;  // X or Y
+    if (hb.canon[j] >= 1) hb.canon_z |= qb;  // Y or Z
+    hb.pi[j] = uint8_t(inplace_pi(*mq[j]));
+    if (hb.pi[j] != (0 | (1 << 2) | (2 << 4))) hb.relab |= 1u << j;
   }
   const size_t N = c.N;
   const unsigned long long bcap = std::max<unsigned long long>(1024, 2ull * N);
@@ -812,9 +874,10 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
     return o;
   };
   const size_t o_tab = take(bcap * 16), o_cnt = take(bcap * 4), o_exp = take(bcap * 4),
-               o_off = take((bcap + ntiles + 1) * 8), o_n = take(32), o_slot = take(N * 4),
+               o_off = take((bcap + ntiles + 1) * 8), o_n = take(32),
+               o_list = take((kBlockListMax + 1) * 4), o_slot = take(N * 4),
                o_pib = take(N * 4), o_code = take(N * 8), o_code2 = take(N * 8),
-               o_w = take(N * sizeof(WT)), o_bw = take(sizeof(BlockWires)), o_ops = take(256);
+               o_w = take(N * sizeof(WT)), o_bw = take(sizeof(BlockWires));
   void* mem = c.al.get(off);
   if (!mem) return QX_OK;
   auto* b8 = static_cast<unsigned char*>(mem);
@@ -822,14 +885,15 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
   auto* bcnt = reinterpret_cast<unsigned*>(b8 + o_cnt);
   auto* bexp = reinterpret_cast<unsigned*>(b8 + o_exp);
   auto* boff = reinterpret_cast<unsigned long long*>(b8 + o_off);
-  auto* dn = reinterpret_cast<unsigned long long*>(b8 + o_n);  // [0] bcap, [1] scan total
+  auto* dn = reinterpret_cast<unsigned long long*>(b8 + o_n);  // [0] sweep count, [1] scan total
+  auto* nblk = reinterpret_cast<unsigned*>(b8 + o_list);     // claimed blocks
+  unsigned* blist = nblk + 1;                                // their slots (the first 1024)
   auto* bslot = reinterpret_cast<unsigned*>(b8 + o_slot);
   auto* pib = reinterpret_cast<unsigned*>(b8 + o_pib);
   auto* lcode = reinterpret_cast<unsigned long long*>(b8 + o_code);
   auto* lcode2 = reinterpret_cast<unsigned long long*>(b8 + o_code2);
   auto* wtmp = reinterpret_cast<WT*>(b8 + o_w);
   auto* d_bw = reinterpret_cast<BlockWires*>(b8 + o_bw);
-  auto* d_ops = reinterpret_cast<uint32_t*>(b8 + o_ops);
   TermBuf out;
   auto body = [&]() -> qx_status {
     const unsigned grid = grid_for(N, kThreads, c.sms, 8);
@@ -837,59 +901,47 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
     QX_TRY_CUDA(cudaMemsetAsync(btab, 0xff, bcap * 16, c.al.s));
     QX_TRY_CUDA(cudaMemsetAsync(bcnt, 0, bcap * 4, c.al.s));
     QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
-    QX_TRY_CUDA(cudaMemcpyAsync(d_bw, &hb, sizeof hb, cudaMemcpyHostToDevice, c.al.s));
-    QX_TRY_CUDA(cudaMemcpyAsync(dn, &bcap, 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(nblk, 0, 4, c.al.s));
+    QX_TRY(h2d(c, d_bw, &hb, sizeof hb));
     c.begin(KC_BLOCK_SETUP);
     k_block_claim<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, d_bw, btab, bcap, bcnt, bexp,
-                                                      bslot, pib, lcode, c.sc.err);
-    k_block_sizes<<<grid_for(bcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(btab, bcap, bcnt,
+                                                      bslot, pib, lcode, nblk, blist, c.sc.err);
+    // offsets: from the list of blocks when it is short, else (dn[0] = bcap)
+    // from the sweep of the table and its scan, which otherwise do nothing
+    k_block_list<<<1, kBlockListMax, 0, c.al.s>>>(nblk, blist, bcnt, bexp, bcap, boff, dn,
+                                                  c.sc.err);
+    k_block_sizes<<<grid_for(bcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(btab, dn, bcnt,
                                                                              bexp, boff, c.sc.err);
     k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
     k_scan_sums<<<1, 1024, 0, c.al.s>>>(boff + bcap, ntiles, dn + 1);
     k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
     QX_TRY_CUDA(cudaGetLastError());
-    // complete blocks only: their sizes must add up to the term count
-    unsigned long long chk[2] = {0, 0};
-    unsigned err = 0;
-    QX_TRY_CUDA(cudaMemcpyAsync(&err, c.sc.err, 4, cudaMemcpyDeviceToHost, c.al.s));
-    QX_TRY(sync_read(c, chk, dn, 16));
-    if (err || chk[1] != N) {
-      QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
-      c.tm.end();
-      return QX_OK;
-    }
+    // No host round trip here: every block is complete exactly when the error
+    // word stayed 0 (then the sizes add up to N), and the kernels below do
+    // nothing otherwise.  The word is read once, after the last wire.
     QX_TRY(alloc_terms(c.al, W, c.wtb, N, &out));
     const auto ov = out.view<WT>();
-    k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, bslot, pib, boff, lcode, ov, lcode2,
-                                                        ov.w);
-    c.end(KC_BLOCK_SETUP, 6, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
+    k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, d_bw, bslot, pib, boff, lcode, ov,
+                                                        lcode2, ov.w, c.sc.err);
+    c.end(KC_BLOCK_SETUP, 7, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
     const WT* src = ov.w;
-    std::vector<uint32_t> relabel;  // letter permutations, applied after every wire
     for (int j = 0; j < m; ++j) {
       WT* dst = (j & 1) ? ov.w : wtmp;
-      const int pi = inplace_pi(*mq[j]);
-      if (pi != (0 | (1 << 2) | (2 << 4))) {
-        uint32_t code = 0;
-        for (int p = 0; p < 3; ++p) code |= uint32_t((pi >> (2 * p)) & 3) << (3 * p);
-        relabel.push_back(encode_op(kOpPerm, mq[j]->q, -1, code));
-      }
       c.begin(KC_BLOCK);
-      k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), pi, lcode2, src,
-                                                       dst);
+      k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), hb.pi[j], lcode2,
+                                                       src, dst, c.sc.err);
       c.end(KC_BLOCK, 1, 2ull * N * (16 * W + sizeof(WT)));
       src = dst;
     }
     if (src != ov.w)
       QX_TRY_CUDA(cudaMemcpyAsync(ov.w, src, N * sizeof(WT), cudaMemcpyDeviceToDevice, c.al.s));
-    if (!relabel.empty()) {
-      QX_TRY_CUDA(cudaMemcpyAsync(d_ops, relabel.data(), relabel.size() * 4,
-                                  cudaMemcpyHostToDevice, c.al.s));
-      c.begin(KC_CLIFF);
-      k_clifford_ops<W, WT><<<grid, kThreads, relabel.size() * 4, c.al.s>>>(
-          ov, c.sc.ncnt + c.cslot, d_ops, int(relabel.size()));
-      c.end(KC_CLIFF, 1, 2ull * N * 16 * W);
-    }
     QX_TRY_CUDA(cudaGetLastError());
+    unsigned err = 0;
+    QX_TRY(sync_read(c, &err, c.sc.err, 4));
+    if (err) {  // some block is incomplete: the terms in c.cur are unchanged
+      QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+      return QX_OK;
+    }
     replace_cur(c, out, N, c.cslot);
     out = TermBuf();
     *done = true;
@@ -897,11 +949,10 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
   };
   const qx_status st = body();
   c.al.put(mem);
-  if (st != QX_OK) {
+  if (st != QX_OK || !*done) {
     c.al.put(out.base);
     return st;
   }
-  if (!*done) return QX_OK;
   c.st.merge_passes += mq.size();
   c.st.inplace_steps++;
   c.st.block_steps++;
@@ -1000,7 +1051,7 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
     c.N = N0;
     // the passes above overwrote both count slots: restore the input's count
     const unsigned long long n0 = N0;
-    QX_TRY_CUDA(cudaMemcpyAsync(c.sc.ncnt + slot0, &n0, 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY(h2d(c, c.sc.ncnt + slot0, &n0, 8));
     QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
     QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
     c.st.host_syncs++;
@@ -1062,7 +1113,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
     for (int a = 0; a < 3; ++a)
       if (!f.iso[a]) niso[a][f.q / 64] |= 1ull << (f.q % 64);
   uint64_t* d_niso = reinterpret_cast<uint64_t*>(s.fanq + c.n);  // staging after the FanQ array
-  QX_TRY_CUDA(cudaMemcpyAsync(d_niso, niso, sizeof niso, cudaMemcpyHostToDevice, c.al.s));
+  QX_TRY(h2d(c, d_niso, niso, sizeof niso));
   QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
   c.begin(KC_MASK);
   k_fan_mask<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
@@ -1085,15 +1136,14 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   for (const FanQubit& f : fs.qs)
     ((any[f.q / 64] >> (f.q % 64)) & 1 ? mq : fq).push_back(&f);
   if (!mq.empty())
-    QX_TRY_CUDA(cudaMemcpyAsync(s.mixed, mixed.data(), G * W * 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY(h2d(c, s.mixed, mixed.data(), G * W * 8));
   // 2. one merge pass per qubit that needs it in some generator
   if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm));
   if (fq.empty()) return QX_OK;
   // 3. one-shot expansion over the qubits that need no merge anywhere
   std::vector<FanQ> hq;
   for (const FanQubit* f : fq) hq.push_back(to_dev(*f));
-  QX_TRY_CUDA(cudaMemcpyAsync(s.fanq, hq.data(), hq.size() * sizeof(FanQ), cudaMemcpyHostToDevice,
-                              c.al.s));
+  QX_TRY(h2d(c, s.fanq, hq.data(), hq.size() * sizeof(FanQ)));
   const int nq = int(hq.size());
   const size_t ntiles = (c.N + kScanTile - 1) / kScanTile;
   auto* offs = static_cast<unsigned long long*>(c.al.get((c.N + ntiles + 1) * 8));
@@ -1133,7 +1183,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   const int oslot = 1 - c.cslot;
   c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
   c.st.children += total;
-  QX_TRY_CUDA(cudaMemcpyAsync(s.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
+  QX_TRY(h2d(c, s.ncnt + oslot, &total, 8));
   replace_cur(c, out, total, oslot);
   if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
   return QX_OK;
@@ -1182,7 +1232,7 @@ qx_status run_rot(Ctx& c, const RotStep& rs, uint64_t ops_before) {
     c.end(KC_ROT, 6, (N + total) * (16 * W + sizeof(WT)));
     QX_TRY_CUDA(cudaGetLastError());
     const int oslot = 1 - c.cslot;
-    QX_TRY_CUDA(cudaMemcpyAsync(c.sc.ncnt + oslot, &total, 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
     c.st.alg_bytes += (N + total) * (16 * W + sizeof(WT));
     c.st.children += total;
     replace_cur(c, out, total, oslot);
@@ -1252,9 +1302,9 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     auto* tx = static_cast<uint64_t*>(tmp);
     auto* tz = tx + G * W;
     auto* tw = reinterpret_cast<double*>(tz + G * W);
-    QX_TRY_CUDA(cudaMemcpyAsync(tx, init_x, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
-    QX_TRY_CUDA(cudaMemcpyAsync(tz, init_z, G * W * 8, cudaMemcpyHostToDevice, c.al.s));
-    if (init_w) QX_TRY_CUDA(cudaMemcpyAsync(tw, init_w, G * 8, cudaMemcpyHostToDevice, c.al.s));
+    QX_TRY(h2d(c, tx, init_x, G * W * 8));
+    QX_TRY(h2d(c, tz, init_z, G * W * 8));
+    if (init_w) QX_TRY(h2d(c, tw, init_w, G * 8));
     k_init_rows<W, WT><<<unsigned((G + 127) / 128), 128, 0, c.al.s>>>(c.cur.view<WT>(), tx, tz,
                                                                   init_w ? tw : nullptr, c.G,
                                                                   c.sc.ncnt);
@@ -1293,7 +1343,7 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   QX_TRY_CUDA(cudaMemsetAsync(st, 0, G * 16, c.al.s));
   c.begin(KC_STATS);
   if (c.N)
-    k_gen_stats<W, WT><<<grid_for(c.N, kThreads * 16, c.sms, 2), kThreads, 0, c.al.s>>>(
+    k_gen_stats<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
         c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
   c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));

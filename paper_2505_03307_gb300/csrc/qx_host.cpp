@@ -118,26 +118,22 @@ Table3 gate_image(const qx_instr& g) {
 }
 
 // Algorithm 1 for one wire: each of X, Y, Z is mapped through the gates of
-// U_{k,j} in list order; the weight vector after the last gate is the row.
-Table3 compose(const std::vector<const qx_instr*>& gates) {
-  Table3 out{};
+// U_{k,j} in list order.  Row p of m holds the weights of the image of letter
+// p so far; one step maps them through the next gate's table t.  The rows are
+// settled after the last gate.
+constexpr Table3 kIdentity3{{{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}}};
+
+void compose_step(Table3& m, const Table3& t) {
   for (int p = 0; p < 3; ++p) {
-    double w[3] = {0.0, 0.0, 0.0};
-    w[p] = 1.0;
-    for (const qx_instr* g : gates) {
-      const Table3 t = gate_image(*g);
-      double nw[3];
-      for (int c = 0; c < 3; ++c) {
-        double acc = w[0] * t.r[0][c];
-        acc += w[1] * t.r[1][c];
-        acc += w[2] * t.r[2][c];
-        nw[c] = acc;
-      }
-      std::memcpy(w, nw, sizeof w);
+    double nw[3];
+    for (int c = 0; c < 3; ++c) {
+      double acc = m.r[p][0] * t.r[0][c];
+      acc += m.r[p][1] * t.r[1][c];
+      acc += m.r[p][2] * t.r[2][c];
+      nw[c] = acc;
     }
-    for (int c = 0; c < 3; ++c) out.r[p][c] = settle(w[c]);
+    std::memcpy(m.r[p], nw, sizeof nw);
   }
-  return out;
 }
 
 // d/dtheta of a rotation table (RX, RY, RZ): (c, s) -> (-s, c).
@@ -584,6 +580,9 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   p->luts.resize(runs.size());
   CliffPass cur;
   uint64_t ops_since_fan = 0;
+  std::vector<uint8_t> seen(static_cast<size_t>(n), 0);
+  std::vector<Table3> acc(static_cast<size_t>(n));
+  std::vector<int> touched;
   for (size_t k = 0; k < runs.size(); ++k) {
     const auto [b, e] = runs[k];
     if (p->op_kind[k] == 0) {
@@ -613,14 +612,27 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
       continue;
     }
     ++p->K;
-    std::vector<std::vector<const qx_instr*>> per(n);
-    for (size_t i = b; i < e; ++i) per[c->ins[i].q0].push_back(&c->ins[i]);
+    // Algorithm 1 for the wires this run touches (the others keep the
+    // identity table), gate by gate in list order.
+    touched.clear();
+    for (size_t i = b; i < e; ++i) {
+      const int q = c->ins[i].q0;
+      if (!seen[q]) {
+        seen[q] = 1;
+        touched.push_back(q);
+        acc[q] = kIdentity3;
+      }
+      compose_step(acc[q], gate_image(c->ins[i]));
+    }
+    std::sort(touched.begin(), touched.end());
     std::vector<Table3>& lut = p->luts[k];
-    lut.resize(n);
+    lut.assign(n, kIdentity3);
     FanStep fs;
     fs.op_index = k;
-    for (int j = 0; j < n; ++j) {
-      lut[j] = compose(per[j]);
+    for (const int j : touched) {
+      seen[j] = 0;
+      for (int r = 0; r < 3; ++r)
+        for (int col = 0; col < 3; ++col) lut[j].r[r][col] = settle(acc[j].r[r][col]);
       uint32_t code = 0;
       const TableKind kind = classify(lut[j], &code);
       if (kind == kSignedPerm)

@@ -117,6 +117,15 @@ __device__ __forceinline__ float group_sum(const FanQ& f, int col, const bool* h
   return sum + comp;
 }
 
+// Sign flip by the sign bit (an integer operation: the FP64 unit is the
+// scarce one on this GPU); bit-identical to IEEE negation.
+__device__ __forceinline__ double wneg(double w) {
+  return __longlong_as_double(__double_as_longlong(w) ^ (1ll << 63));
+}
+__device__ __forceinline__ float wneg(float w) {
+  return __uint_as_float(__float_as_uint(w) ^ 0x80000000u);
+}
+
 // Running product of a weight with table entries (the Cartesian expansion).
 template <typename WT>
 struct WProd;
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(256) k_clifford_ops(TermsT<WT> t, const unsign
       t.x[k * t.cap + i] = x[k];
       t.z[k * t.cap + i] = z[k];
     }
-    if (neg) t.w[i] = -t.w[i];
+    if (neg) t.w[i] = wneg(t.w[i]);
   }
 }
 
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
       t.x[k * t.cap + i] = ax[k];
       t.z[k * t.cap + i] = az[k];
     }
-    if (neg) t.w[i] = -t.w[i];
+    if (neg) t.w[i] = wneg(t.w[i]);
   }
 }
 
@@ -432,16 +441,58 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
 // non-isolated letters are all the same in a generator cannot make two of that
 // generator's strings collide, so it is expanded without a merge.
 
+// Lanes of the warp holding the same key as this lane.  Terms of one
+// generator (or one block) usually sit together, so a warp-wide equality vote
+// answers most calls without the match instruction.
+__device__ __forceinline__ unsigned warp_peers(unsigned key) {
+  const unsigned k0 = __shfl_sync(0xffffffffu, key, 0);
+  if (__all_sync(0xffffffffu, key == k0)) return 0xffffffffu;
+  return __match_any_sync(0xffffffffu, key);
+}
+
+// Contiguous range of terms for the calling warp: [*b, *e), a multiple of 32
+// long, so that a warp's terms (usually of one generator) are read once and
+// in order.
+__device__ __forceinline__ void warp_range(size_t N, size_t* b, size_t* e) {
+  const size_t nw = size_t(gridDim.x) * (blockDim.x >> 5);
+  const size_t w = size_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const size_t per = (((N + nw - 1) / nw) + 31) & ~size_t(31);
+  *b = min(N, w * per);
+  *e = min(N, *b + per);
+}
+
 template <int W, typename WT = double>
 __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const uint64_t* nisoX,
                            const uint64_t* nisoY, const uint64_t* nisoZ,
                            unsigned long long* gmask /* [G][3][W] */) {
   const size_t N = *n_in;
   const unsigned lane = threadIdx.x & 31;
-  for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
-       base += size_t(gridDim.x) * blockDim.x) {
-    const size_t i = base + threadIdx.x;
-    const bool valid = i < N;
+  size_t b, e;
+  warp_range(N, &b, &e);
+  // running OR of a warp whose lanes all held generator cg (lane 0 adds it to
+  // gmask when the generator changes and at the end)
+  uint32_t cg = 0xffffffffu;
+  uint64_t acc[3][W];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[a][k] = 0;
+  auto flush = [&]() {
+    if (cg != 0xffffffffu && lane == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          if (acc[a][k]) atomicOr(&gmask[(size_t(cg) * 3 + a) * W + k], acc[a][k]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[a][k] = 0;
+  };
+  for (size_t base = b; base < e; base += 32) {
+    const size_t i = base + lane;
+    const bool valid = i < e;
     uint32_t g = valid ? t.g[i] : 0xffffffffu;
     uint64_t m[3][W];
     if (valid) {
@@ -457,8 +508,7 @@ __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const u
 #pragma unroll
       for (int k = 0; k < W; ++k) m[0][k] = m[1][k] = m[2][k] = 0;
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, g);
-    const unsigned leader = __ffs(peers) - 1;
+    const unsigned peers = warp_peers(g);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -467,18 +517,26 @@ __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const u
         const unsigned hi = __reduce_or_sync(peers, unsigned(m[a][k] >> 32));
         m[a][k] = (uint64_t(hi) << 32) | lo;
       }
-    if (valid && lane == leader) {
+    if (peers == 0xffffffffu) {  // one generator in the whole warp
+      if (g != cg) {
+        flush();
+        cg = g;
+      }
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          unsigned long long* dst = &gmask[(size_t(g) * 3 + a) * W + k];
-          // bits are only ever set: skip the atomic when they are all there
-          // already (a stale read costs at most a redundant atomic)
-          if (m[a][k] && (__ldcg(dst) & m[a][k]) != m[a][k]) atomicOr(dst, m[a][k]);
-        }
+        for (int k = 0; k < W; ++k) acc[a][k] |= m[a][k];
+      continue;
+    }
+    if (valid && lane == __ffs(peers) - 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          if (m[a][k]) atomicOr(&gmask[(size_t(g) * 3 + a) * W + k], m[a][k]);
     }
   }
+  flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -982,68 +1040,65 @@ __global__ void __launch_bounds__(THREADS) k_compact_pruned(TermsT<WT> in, const
 // ---------------------------------------------------------------------------
 // Per-generator statistics: term count and sum of squared weights.
 
-constexpr int kStatsSmemGens = 2048;
-
-// Per-generator term count and sum of squared weights.  Each warp first
-// combines the lanes that hold the same generator id (one atomic per distinct
-// id and warp instead of one per term, which matters when few generators
-// share all terms).  With at most kStatsSmemGens generators the warp leaders
-// add into shared memory and each block adds its totals once per generator;
-// otherwise they add into global memory directly.
+// Per-generator term count and sum of squared weights.  Each warp reads a
+// contiguous range; while all its lanes hold one generator id each lane keeps
+// its own partial sum (one fused multiply-add per term) and the warp combines
+// the lanes and adds into global memory only when the id changes and at the
+// end.  FP64 instructions are the scarce resource on this GPU (a warp-wide one
+// takes about 16 SM cycles), so the butterfly is paid once per run of one id,
+// not once per 32 terms.  Mixed warps combine equal ids first.
 template <int W, typename WT = double>
 __global__ void k_gen_stats(TermsT<WT> t, const unsigned long long* n_in, int G,
                             unsigned long long* count, double* sumsq) {
-  __shared__ unsigned s_cnt[kStatsSmemGens];
-  __shared__ double s_sq[kStatsSmemGens];
+  (void)G;
   const size_t N = *n_in;
-  const bool shared = G <= kStatsSmemGens;
-  if (shared) {
-    for (int k = threadIdx.x; k < G; k += blockDim.x) {
-      s_cnt[k] = 0;
-      s_sq[k] = 0.0;
+  const unsigned lane = threadIdx.x & 31;
+  size_t b, e;
+  warp_range(N, &b, &e);
+  uint32_t cg = 0xffffffffu;
+  unsigned long long acc_n = 0;
+  double acc_sq = 0.0;  // this lane's share of generator cg
+  auto flush = [&]() {
+    if (cg != 0xffffffffu) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) acc_sq += __shfl_xor_sync(0xffffffffu, acc_sq, o);
+      if (lane == 0) {
+        atomicAdd(&count[cg], acc_n);
+        atomicAdd(&sumsq[cg], acc_sq);
+      }
     }
-    __syncthreads();
-  }
-  for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
-       base += size_t(gridDim.x) * blockDim.x) {
-    const size_t i = base + threadIdx.x;
-    const bool valid = i < N;
+    acc_n = 0;
+    acc_sq = 0.0;
+  };
+  for (size_t base = b; base < e; base += 32) {
+    const size_t i = base + lane;
+    const bool valid = i < e;
     const uint32_t g = valid ? t.g[i] : 0xffffffffu;
     const double w = valid ? double(t.w[i]) : 0.0;
-    const unsigned peers = __match_any_sync(0xffffffffu, g);
-    double sq;
-    if (peers == 0xffffffffu) {  // one id in the whole warp: butterfly sum
-      sq = w * w;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    } else {
-      sq = 0.0;
-      unsigned rest = peers;
-      while (rest) {
-        const int src = __ffs(rest) - 1;
-        rest &= rest - 1;
-        const double o = __shfl_sync(peers, w, src);
-        sq += o * o;
+    const unsigned peers = warp_peers(g);
+    if (peers == 0xffffffffu) {  // one id in the whole warp
+      if (g != cg) {
+        flush();
+        cg = g;
       }
+      acc_n += 32;
+      acc_sq = fma(w, w, acc_sq);
+      continue;
     }
-    if (valid && int(threadIdx.x & 31) == __ffs(peers) - 1) {
-      if (shared) {
-        atomicAdd(&s_cnt[g], unsigned(__popc(peers)));
-        atomicAdd(&s_sq[g], sq);
-      } else {
-        atomicAdd(&count[g], (unsigned long long)__popc(peers));
-        atomicAdd(&sumsq[g], sq);
-      }
+    double sq = 0.0;
+    unsigned rest = peers;
+    while (rest) {
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const double o = __shfl_sync(peers, w, src);
+      sq = fma(o, o, sq);
+    }
+    if (valid && int(lane) == __ffs(peers) - 1) {
+      atomicAdd(&count[g], (unsigned long long)__popc(peers));
+      atomicAdd(&sumsq[g], sq);
     }
   }
-  if (!shared) return;
-  __syncthreads();
-  for (int k = threadIdx.x; k < G; k += blockDim.x) {
-    if (s_cnt[k]) {
-      atomicAdd(&count[k], (unsigned long long)s_cnt[k]);
-      atomicAdd(&sumsq[k], s_sq[k]);
-    }
-  }
+  flush();
 }
 
 // ---------------------------------------------------------------------------

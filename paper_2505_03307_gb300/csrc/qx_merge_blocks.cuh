@@ -20,6 +20,9 @@ namespace qx {
 namespace dev {
 
 constexpr int kMaxBlockWires = 32;  // letter code: 2 bits per merge wire in 64 bits
+// Up to this many blocks, their offsets come from the list of claimed slots
+// (one small kernel); beyond it, from a sweep and scan of the whole table.
+constexpr int kBlockListMax = 1024;
 // With at most 16 merge wires the code's upper half holds two masks, the wires
 // where the term's block has radix 2 (bits 32..47) and radix 3 (48..63), so a
 // stride is 2^a 3^b from two population counts.
@@ -31,6 +34,18 @@ struct BlockWires {
   uint8_t canon[kMaxBlockWires];  // the canonical non-isolated letter (0 X, 1 Y, 2 Z)
   uint8_t radix[kMaxBlockWires];  // number of non-isolated letters
   uint8_t rank[kMaxBlockWires][3];  // rank of a non-isolated letter, 255 for isolated
+  // letter permutation pi of the wire (2 bits per source letter X, Y, Z), the
+  // names the merged weights belong to; relab: bit j set when pi_j is not the
+  // identity
+  uint8_t pi[kMaxBlockWires];
+  uint32_t relab;
+  // The same facts packed for the per-term loop of k_block_claim: inf[j] =
+  // q (bits 0-5), the rank of the letter with xz code c = x | z << 1 in bits
+  // 8 + 4c .. 11 + 4c (15: I or an isolated letter), the radix in bits 24-25;
+  // and, per qubit, where X / Y / Z are non-isolated and the canonical
+  // letter's x and z bits.
+  uint32_t inf[kMaxBlockWires];
+  uint64_t niso_x, niso_y, niso_z, canon_x, canon_z;
 };
 
 // Letter index of bits (x, z): 0 I, 1 X, 2 Y, 3 Z  -> table letter = index - 1.
@@ -42,42 +57,55 @@ __device__ __forceinline__ int letter4(uint64_t x, uint64_t z, int q) {
 // Per term: the block key (non-isolated letters of the merge wires replaced
 // by the wire's canonical letter, generator packed in), claimed in the block
 // table; the member count of the block (warp-combined), the block's expected
-// size, the term's place in its block and its letter code.
+// size, the term's place in its block and its letter code.  The key is formed
+// with whole-word masks; only the place and the code need a loop over wires.
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int n,
                                                      const BlockWires* bw_g, ulonglong2* btab,
                                                      unsigned long long bcap, unsigned* bcnt,
                                                      unsigned* bexp, unsigned* bslot,
                                                      unsigned* pib, unsigned long long* lcode,
+                                                     unsigned* nblk, unsigned* blist,
                                                      unsigned* err) {
-  __shared__ BlockWires bw;
-  if (threadIdx.x == 0) bw = *bw_g;
+  __shared__ uint32_t s_inf[kMaxBlockWires];
+  __shared__ uint64_t s_mask[5];
+  const int m = bw_g->m;
+  if (threadIdx.x < unsigned(m)) s_inf[threadIdx.x] = bw_g->inf[threadIdx.x];
+  if (threadIdx.x == 32) {
+    s_mask[0] = bw_g->niso_x;
+    s_mask[1] = bw_g->niso_y;
+    s_mask[2] = bw_g->niso_z;
+    s_mask[3] = bw_g->canon_x;
+    s_mask[4] = bw_g->canon_z;
+  }
   __syncthreads();
+  const bool fast = m <= kFastStrideWires;
   for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
        base += size_t(gridDim.x) * blockDim.x) {
     const size_t i = base + threadIdx.x;
     unsigned slot = 0xffffffffu;
     if (i < N) {
-      uint64_t x = t.x[i], z = t.z[i];
+      const uint64_t x = t.x[i], z = t.z[i];
+      const uint64_t dm = (x & ~z & s_mask[0]) | (x & z & s_mask[1]) | (~x & z & s_mask[2]);
+      const uint64_t kx = (x & ~dm) | (s_mask[3] & dm), kz = (z & ~dm) | (s_mask[4] & dm);
       unsigned long long code = 0;
-      unsigned pos = 0, stride = 1;
-      for (int j = 0; j < bw.m; ++j) {
-        const int q = bw.q[j];
-        const int L = letter4(x, z, q);
-        code |= (unsigned long long)L << (2 * j);
-        if (L && bw.rank[j][L - 1] != 255) {  // non-isolated: a digit of the block
-          pos += unsigned(bw.rank[j][L - 1]) * stride;
-          stride *= bw.radix[j];
-          if (bw.m <= kFastStrideWires)
-            code |= 1ull << ((bw.radix[j] == 2 ? 32 : 48) + j);
-          const int c = bw.canon[j];
-          const uint64_t m = 1ull << q;
-          x = c <= 1 ? (x | m) : (x & ~m);
-          z = c >= 1 ? (z | m) : (z & ~m);
+      unsigned pos = 0, stride = 1, r2 = 0, r3 = 0;
+      for (int j = 0; j < m; ++j) {
+        const uint32_t inf = s_inf[j];
+        const int q = int(inf & 63u);
+        const uint32_t c = (uint32_t(x >> q) & 1u) | ((uint32_t(z >> q) & 1u) << 1);
+        code |= (unsigned long long)(c ^ (c >> 1)) << (2 * j);  // 0 I, 1 X, 2 Y, 3 Z
+        const uint32_t rk = (inf >> (8 + 4 * c)) & 15u;
+        if (rk != 15u) {  // a digit of the block
+          const uint32_t rdx = (inf >> 24) & 3u;
+          pos += rk * stride;
+          stride *= rdx;
+          if (rdx == 2) r2 |= 1u << j; else r3 |= 1u << j;
         }
       }
+      if (fast) code |= ((unsigned long long)r2 << 32) | ((unsigned long long)r3 << 48);
       unsigned long long lo, hi;
-      pack_full_key(x, z, t.g[i], n, &lo, &hi);
+      pack_full_key(kx, kz, t.g[i], n, &lo, &hi);
       unsigned long long p = __umul64hi(slot_hash(lo, hi), bcap);
       for (unsigned long long probe = 0; probe < bcap; ++probe) {
         // a block has many members: read first (a cached read may be stale
@@ -93,6 +121,8 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
           if (olo == ~0ull && ohi == ~0ull) {
             slot = unsigned(p);
             bexp[slot] = stride;  // the claimant records the block's size
+            const unsigned li = atomicAdd(nblk, 1u);  // and lists the slot
+            if (li < kBlockListMax) blist[li] = slot;
             break;
           }
         }
@@ -111,17 +141,77 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       }
     }
     // member counts, one atomic per block and warp
-    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    const unsigned peers = warp_peers(slot);
     if (slot != 0xffffffffu && int(threadIdx.x & 31) == __ffs(peers) - 1)
       atomicAdd(&bcnt[slot], unsigned(__popc(peers)));
   }
 }
 
-// size[s] = expected size of the block in slot s (0 if empty); a block whose
-// count differs from its size is incomplete.
-static __global__ void k_block_sizes(const ulonglong2* btab, unsigned long long bcap,
+// Offsets of at most kBlockListMax blocks, in slot order (the order the table
+// sweep gives), from the list of claimed slots: each block's rank is the
+// number of listed slots below its own, and the offsets are the exclusive scan
+// of the sizes in rank order.  A block whose count differs from its size is
+// incomplete.  dn[0] receives the element count of the table sweep that
+// follows: 0 when the list sufficed, the table size otherwise.
+static __global__ void __launch_bounds__(kBlockListMax) k_block_list(
+    const unsigned* nblk, const unsigned* blist, const unsigned* bcnt, const unsigned* bexp,
+    unsigned long long bcap, unsigned long long* boff, unsigned long long* dn, unsigned* err) {
+  __shared__ unsigned s_slot[kBlockListMax];
+  __shared__ unsigned long long s_size[kBlockListMax];
+  __shared__ unsigned long long s_warp[kBlockListMax / 32];
+  const unsigned nb = *nblk;
+  const unsigned t = threadIdx.x;
+  if (nb > unsigned(kBlockListMax)) {
+    if (t == 0) dn[0] = bcap;
+    return;
+  }
+  if (t == 0) dn[0] = 0;
+  const unsigned my = t < nb ? blist[t] : 0xffffffffu;
+  s_slot[t] = my;
+  s_size[t] = 0;
+  __syncthreads();
+  unsigned rank = 0;
+  unsigned long long sz = 0;
+  if (t < nb) {
+    for (unsigned u = 0; u < nb; ++u) rank += s_slot[u] < my ? 1u : 0u;
+    sz = bexp[my];
+    if (bcnt[my] != sz) atomicOr(err, kErrNotClosed);
+  }
+  __syncthreads();
+  if (t < nb) s_size[rank] = sz;
+  __syncthreads();
+  // exclusive scan of s_size: warps, then the warp totals
+  const unsigned lane = t & 31, wid = t >> 5;
+  const unsigned long long v = s_size[t];
+  unsigned long long inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= unsigned(d)) inc += o;
+  }
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long w = s_warp[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= unsigned(d)) w += o;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  s_size[t] = (wid ? s_warp[wid - 1] : 0) + inc - v;
+  __syncthreads();
+  if (t < nb) boff[my] = s_size[rank];
+}
+
+// size[s] = expected size of the block in slot s (0 if empty) for the first
+// *count slots; a block whose count differs from its size is incomplete.
+static __global__ void k_block_sizes(const ulonglong2* btab, const unsigned long long* count,
                                      const unsigned* bcnt, const unsigned* bexp,
                                      unsigned long long* size, unsigned* err) {
+  const unsigned long long bcap = *count;
   for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < bcap;
        s += (unsigned long long)gridDim.x * blockDim.x) {
     const ulonglong2 k = btab[s];
@@ -132,18 +222,37 @@ static __global__ void k_block_sizes(const ulonglong2* btab, unsigned long long 
 }
 
 // Terms to block order: place = offset of the block + place in the block.
+// The strings are written with the letter permutations pi of the merge wires
+// already applied (the wire passes read only letter codes and weights, so the
+// names can change before them).
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_scatter(TermsT<WT> t, size_t N,
+                                                       const BlockWires* bw_g,
                                                        const unsigned* bslot, const unsigned* pib,
                                                        const unsigned long long* boff,
                                                        const unsigned long long* lcode,
                                                        TermsT<WT> out, unsigned long long* lcode_out,
-                                                       WT* w_out) {
+                                                       WT* w_out, const unsigned* err) {
+  if (*err) return;  // an incomplete block: the places are not a permutation
+  __shared__ BlockWires bw;
+  if (threadIdx.x == 0) bw = *bw_g;
+  __syncthreads();
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
        i += size_t(gridDim.x) * blockDim.x) {
     const unsigned long long d = boff[bslot[i]] + pib[i];
-    out.x[d] = t.x[i];
-    out.z[d] = t.z[i];
+    uint64_t x = t.x[i], z = t.z[i];
+    for (uint32_t r = bw.relab; r; r &= r - 1) {
+      const int j = __ffs(r) - 1;
+      const int q = bw.q[j];
+      const int L = letter4(x, z, q);
+      if (!L) continue;
+      const int c = (bw.pi[j] >> (2 * (L - 1))) & 3;  // 0 X, 1 Y, 2 Z
+      const uint64_t m = 1ull << q;
+      x = c <= 1 ? (x | m) : (x & ~m);
+      z = c >= 1 ? (z | m) : (z & ~m);
+    }
+    out.x[d] = x;
+    out.z[d] = z;
     out.g[d] = t.g[i];
     w_out[d] = t.w[i];
     lcode_out[d] = lcode[i];
@@ -157,7 +266,9 @@ template <typename WT>
 __global__ void __launch_bounds__(256) k_block_wire(size_t N, const BlockWires* bw_g, int j,
                                                     FanQ fq, int pi,
                                                     const unsigned long long* lcode,
-                                                    const WT* w_in, WT* w_out) {
+                                                    const WT* w_in, WT* w_out,
+                                                    const unsigned* err) {
+  if (*err) return;  // no block order: the partner distances do not hold
   __shared__ FanQ f;
   __shared__ BlockWires bw;
   if (threadIdx.x == 0) {

@@ -69,14 +69,14 @@ __device__ __forceinline__ void rot_outputs(const RotQ& r, const uint64_t* x, co
   v[rq] = w;
   if (present) {
     has[rp] = true;
-    v[rp] = rot_sign<W>(r, xp, zp) < 0 ? -wp : wp;
+    v[rp] = rot_sign<W>(r, xp, zp) < 0 ? wneg(wp) : wp;
   }
   bool reached = false;
   *own = group_sum(r.tab, rq, has, v, &reached);
   *own_on = reached;
   *part_on = false;
   if (!present) {  // the partner string: column rp, from this term alone
-    v[rq] = rot_sign<W>(r, x, z) < 0 ? -w : w;
+    v[rq] = rot_sign<W>(r, x, z) < 0 ? wneg(w) : w;
     has[rp] = false;
     *part = group_sum(r.tab, rp, has, v, &reached);
     *part_on = reached;

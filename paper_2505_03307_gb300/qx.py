@@ -313,10 +313,10 @@ class Circuit:
             self.instrs = None
             self.ninstr = len(rec)
         else:
-            arr = (Instr * max(1, len(instrs)))()
-            for i, (g, a, b, th) in enumerate(instrs):
-                arr[i] = Instr(GATE_CODES[g], int(a), int(b), float(th))
-            _check(lib.qx_load_circuit(int(n), arr, len(instrs), ctypes.byref(h)))
+            rec = np.array([(GATE_CODES[g], a, b, th) for g, a, b, th in instrs],
+                           INSTR_DTYPE).reshape(-1)
+            _check(lib.qx_load_circuit(int(n), ctypes.cast(rec.ctypes.data, ctypes.POINTER(Instr)),
+                                       len(rec), ctypes.byref(h)))
             self.instrs = list(instrs)
             self.ninstr = len(instrs)
         self.n = n
