@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -718,6 +719,38 @@ int inplace_pi(const FanQubit& f) {
   return pi[0] | (pi[1] << 2) | (pi[2] << 4);
 }
 
+// Coefficients of a radix-2 merge wire for k_block_wire2; false when the wire
+// has another number of non-isolated letters.
+bool wire2_of(const FanQubit& f, int pi, Wire2* out) {
+  int lt[2], n = 0, iso = -1;
+  for (int a = 0; a < 3; ++a) {
+    if (f.iso[a])
+      iso = a;
+    else if (n < 2)
+      lt[n++] = a;
+    else
+      return false;
+  }
+  if (n != 2) return false;
+  Wire2 w{};
+  // letter code L of table letter a: X 1, Y 2, Z 3
+  w.rk = 0;
+  for (int d = 0; d < 2; ++d) w.rk |= uint32_t(d) << (2 * (lt[d] + 1));
+  if (iso >= 0) {
+    w.rk |= 3u << (2 * (iso + 1));
+    w.iso_t = f.t.r[iso][(pi >> (2 * iso)) & 3];
+  }
+  for (int d = 0; d < 2; ++d) {
+    const int col = (pi >> (2 * lt[d])) & 3;
+    for (int r = 0; r < 2; ++r) {
+      w.c[d][r] = f.t.r[lt[r]][col];
+      if (w.c[d][r] != 0.0) w.nz |= 1u << (2 * d + r);
+    }
+  }
+  *out = w;
+  return true;
+}
+
 // Whether the merge wires of a step may run in place: one-word keys with a
 // free empty pattern and, per generator, letter sets that are closed under
 // each wire's table up to its letter permutation (a necessary condition for
@@ -928,8 +961,15 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
     for (int j = 0; j < m; ++j) {
       WT* dst = (j & 1) ? ov.w : wtmp;
       c.begin(KC_BLOCK);
-      k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), hb.pi[j], lcode2,
-                                                       src, dst, c.sc.err);
+      Wire2 w2;
+      if (std::is_same<WT, double>::value && m <= kFastStrideWires &&
+          wire2_of(*mq[j], hb.pi[j], &w2))
+        k_block_wire2<<<grid, kThreads, 0, c.al.s>>>(N, j, w2, lcode2,
+                                                     reinterpret_cast<const double*>(src),
+                                                     reinterpret_cast<double*>(dst), c.sc.err);
+      else
+        k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), hb.pi[j],
+                                                         lcode2, src, dst, c.sc.err);
       c.end(KC_BLOCK, 1, 2ull * N * (16 * W + sizeof(WT)));
       src = dst;
     }
@@ -1173,7 +1213,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   const unsigned egrid = unsigned(std::max<unsigned long long>(
       1, std::min<unsigned long long>((total + kExpTile - 1) / kExpTile,
                                       (unsigned long long)c.sms * 8)));
-  const size_t esmem = nq * sizeof(FanQ) + size_t(kExpTile) * 8;
+  const size_t esmem = expand_emit_smem<W, WT>(nq);
   c.begin(KC_EXPAND);
   k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, offs, total,
                                                          s.fanq, nq, out.view<WT>());
@@ -1415,7 +1455,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   c.inplace = (opts.flags & QX_FLAG_NO_INPLACE) == 0;
   c.tm.s = c.al.s;
   c.tm.pool = &t_event_pool;
-  if (p->dev->max_smem > 48 * 1024) {
+  {  // kernels whose dynamic shared memory may pass 48 KB
     static thread_local int attr_dev = -1;
     if (attr_dev != dev) {
       const int mx = 200 * 1024;
@@ -1428,6 +1468,10 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
       cudaFuncSetAttribute(k_clifford_table<1, 3, float>, attr, mx);
       cudaFuncSetAttribute(k_clifford_table<2, 4, float>, attr, mx);
       cudaFuncSetAttribute(k_clifford_table<2, 3, float>, attr, mx);
+      cudaFuncSetAttribute(k_expand_emit<1, double>, attr, mx);
+      cudaFuncSetAttribute(k_expand_emit<2, double>, attr, mx);
+      cudaFuncSetAttribute(k_expand_emit<1, float>, attr, mx);
+      cudaFuncSetAttribute(k_expand_emit<2, float>, attr, mx);
       attr_dev = dev;
     }
   }

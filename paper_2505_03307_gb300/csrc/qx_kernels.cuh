@@ -934,11 +934,33 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long 
 constexpr int kExpThreads = 256;
 constexpr int kExpItems = 4;
 constexpr int kExpTile = kExpThreads * kExpItems;
+constexpr int kExpMaxH = 8;  // distinct upper digit values a tree tile may span
+
+// Dynamic shared memory of k_expand_emit: the fan-out tables, the parent
+// offsets of a tile and (FP64) the product tree of a single-parent tile.
+template <int W, typename WT>
+constexpr size_t expand_emit_smem(int nq) {
+  return size_t(nq) * sizeof(FanQ) + size_t(kExpTile) * 8 +
+         (sizeof(WT) == 8 ? size_t(kExpTile) * (8 + 16 * W) : 0);
+}
 
 // Children [c0, c0 + kExpTile) per block iteration.  The parents of the tile
 // are located once (binary search on the offsets), their offsets staged in
 // shared memory, and each child finds its parent there; the child index within
-// the parent is decoded in mixed radix over the parent's fan-out letters.
+// the parent is decoded in mixed radix over the parent's fan-out letters (the
+// first wire is the least significant digit), and its weight is the parent's
+// times one table entry per wire, in wire order.
+//
+// A tile whose children all have one parent (a large fan-out; FP64 weights)
+// shares that product: the parent's wires split into a lower part (the first
+// wires, at most kExpTile digit combinations) and an upper part.  The lower
+// products w t_0 t_1 ... are built once per tile as a tree, one level per wire
+// (each node one multiplication: the same roundings as the product in wire
+// order), the upper products t_k t_k+1 ... once per distinct upper digit value
+// of the tile, and each child takes one more multiplication.  This regroups the
+// product as (w t_0 ... t_k-1)(t_k ... t_m-1), a reordering within rounding,
+// and takes the FP64 work from one multiplication per wire and child to about
+// three per child (an FP64 instruction costs about 16 SM cycles on this GPU).
 template <int W, typename WT = double>
 __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* offs,
@@ -946,7 +968,15 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
   extern __shared__ unsigned char s_raw[];
   FanQ* s_fq = reinterpret_cast<FanQ*>(s_raw);
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_fq + nq);
+  double* s_lw = reinterpret_cast<double*>(s_off + kExpTile);  // tree tiles only
+  uint64_t* s_lx = reinterpret_cast<uint64_t*>(s_lw + kExpTile);
+  uint64_t* s_lz = s_lx + size_t(kExpTile) * W;
   __shared__ size_t s_p0, s_p1;
+  __shared__ uint8_t s_wj[kMaxQubits], s_wa[kMaxQubits], s_wn[kMaxQubits];
+  __shared__ int s_nw, s_klo, s_nh;
+  __shared__ unsigned long long s_rlo, s_h0;
+  __shared__ double s_hw[kExpMaxH];
+  __shared__ uint64_t s_hx[kExpMaxH][W], s_hz[kExpMaxH][W], s_hm[W];
   for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
   const size_t N = *n_in;
   for (unsigned long long c0 = (unsigned long long)blockIdx.x * kExpTile; c0 < total;
@@ -966,9 +996,157 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
         if (offs[mid] <= c1 - 1) lo2 = mid; else hi2 = mid;
       }
       s_p1 = lo2;
+      s_nh = 0;
+      if constexpr (sizeof(WT) == 8) {
+        if (lo2 == lo) {  // one parent: its fan-out wires in order, and the split
+          uint64_t x[W], z[W];
+          load_term<W>(in, lo, x, z);
+          int nw = 0, klo = 0;
+          unsigned long long rlo = 1;
+          bool lower = true;
+          for (int j = 0; j < nq; ++j) {
+            const int L = letter_at<W>(x, z, s_fq[j].q);
+            if (!L) continue;
+            const int nn = s_fq[j].nnz[L - 1];
+            if (lower && rlo * nn <= (unsigned long long)kExpTile) {
+              rlo *= nn;
+              klo = nw + 1;
+            } else {
+              lower = false;
+            }
+            s_wj[nw] = uint8_t(j);
+            s_wa[nw] = uint8_t(L - 1);
+            s_wn[nw] = uint8_t(nn);
+            ++nw;
+          }
+          const unsigned long long r0 = c0 - offs[lo], r1 = c1 - 1 - offs[lo];
+          const unsigned long long h0 = r0 / rlo, nh = r1 / rlo - h0 + 1;
+          if (nh <= (unsigned long long)kExpMaxH) {
+            s_nw = nw;
+            s_klo = klo;
+            s_rlo = rlo;
+            s_h0 = h0;
+            s_nh = int(nh);
+          }
+        }
+      }
     }
     __syncthreads();
     const size_t p0 = s_p0, np = s_p1 - p0 + 1;
+    if constexpr (sizeof(WT) == 8) {
+      if (s_nh > 0) {
+        const size_t p = p0;
+        const int nw = s_nw, klo = s_klo, nh = s_nh;
+        const unsigned long long rlo = s_rlo, h0 = s_h0, off = offs[p];
+        // lower tree: level e multiplies every node by wire e's entries
+        if (threadIdx.x == 0) {
+          s_lw[0] = double(in.w[p]);
+          uint64_t x[W], z[W];
+          load_term<W>(in, p, x, z);
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            s_lx[k] = x[k];
+            s_lz[k] = z[k];
+          }
+        }
+        // upper products, one per distinct upper digit value; the mask of
+        // the upper wires' qubits
+        if (threadIdx.x >= 32 && threadIdx.x < 32 + unsigned(nh)) {
+          const int t = threadIdx.x - 32;
+          unsigned long long h = h0 + t;
+          uint64_t x[W], z[W];
+          load_term<W>(in, p, x, z);
+          double v = 1.0;
+          for (int e = klo; e < nw; ++e) {
+            const FanQ& f = s_fq[s_wj[e]];
+            const int a = s_wa[e], nn = s_wn[e];
+            int d = 0;
+            if (nn == 2) {
+              d = int(h & 1);
+              h >>= 1;
+            } else if (nn == 3) {
+              d = int(h % 3);
+              h /= 3;
+            }
+            const int col = f.col[a][d];
+            v = e == klo ? f.t[a][col] : v * f.t[a][col];
+            set_letter<W>(x, z, f.q, col);
+          }
+          s_hw[t] = v;
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            s_hx[t][k] = x[k];
+            s_hz[t][k] = z[k];
+          }
+        }
+        if (threadIdx.x == 64) {
+          uint64_t hm[W];
+#pragma unroll
+          for (int k = 0; k < W; ++k) hm[k] = 0;
+          for (int e = klo; e < nw; ++e) {
+            const int q = s_fq[s_wj[e]].q;
+            hm[q >> 6] |= 1ull << (q & 63);
+          }
+#pragma unroll
+          for (int k = 0; k < W; ++k) s_hm[k] = hm[k];
+        }
+        __syncthreads();
+        unsigned long long size = 1;
+        for (int e = 0; e < klo; ++e) {
+          const FanQ& f = s_fq[s_wj[e]];
+          const int a = s_wa[e], nn = s_wn[e];
+          for (unsigned long long idx = threadIdx.x; idx < size; idx += blockDim.x) {
+            const double v = s_lw[idx];
+            uint64_t x[W], z[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              x[k] = s_lx[idx * W + k];
+              z[k] = s_lz[idx * W + k];
+            }
+            for (int d = nn - 1; d >= 0; --d) {
+              const int col = f.col[a][d];
+              const unsigned long long o = idx + size * d;
+              s_lw[o] = v * f.t[a][col];
+              uint64_t xo[W], zo[W];
+#pragma unroll
+              for (int k = 0; k < W; ++k) {
+                xo[k] = x[k];
+                zo[k] = z[k];
+              }
+              set_letter<W>(xo, zo, f.q, col);
+#pragma unroll
+              for (int k = 0; k < W; ++k) {
+                s_lx[o * W + k] = xo[k];
+                s_lz[o * W + k] = zo[k];
+              }
+            }
+          }
+          size *= nn;
+          __syncthreads();
+        }
+        const uint32_t g = in.g[p];
+        const bool upper = klo < nw;
+        const bool pow2 = (rlo & (rlo - 1)) == 0;
+        const int sh = __ffsll((long long)rlo) - 1;
+        for (int k = 0; k < kExpItems; ++k) {
+          const unsigned long long c = c0 + (unsigned long long)k * kExpThreads + threadIdx.x;
+          if (c >= c1) break;
+          const unsigned long long r = c - off;
+          const unsigned long long hq = pow2 ? r >> sh : r / rlo, rho = r - hq * rlo;
+          const int t = int(hq - h0);
+          uint64_t x[W], z[W];
+#pragma unroll
+          for (int k2 = 0; k2 < W; ++k2) {
+            x[k2] = (s_lx[rho * W + k2] & ~s_hm[k2]) | (s_hx[t][k2] & s_hm[k2]);
+            z[k2] = (s_lz[rho * W + k2] & ~s_hm[k2]) | (s_hz[t][k2] & s_hm[k2]);
+          }
+          const double v = upper ? s_lw[rho] * s_hw[t] : s_lw[rho];
+          store_term<W>(out, size_t(c), x, z, WT(v), g);
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     for (size_t j = threadIdx.x; j < np; j += blockDim.x) s_off[j] = offs[p0 + j];
     __syncthreads();
     for (int k = 0; k < kExpItems; ++k) {

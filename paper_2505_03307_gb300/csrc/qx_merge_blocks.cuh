@@ -318,5 +318,57 @@ __global__ void __launch_bounds__(256) k_block_wire(size_t N, const BlockWires* 
   }
 }
 
+// A merge wire with exactly two non-isolated letters (radix 2: the common
+// case of a rotation mixing two letters), with at most kFastStrideWires
+// wires.  The member of rank d (0: the first of the two letters in X, Y, Z
+// order) gets c[d][0] v_0 + c[d][1] v_1, v_r the weight of the member of rank
+// r, c[d][r] = t[letter r][pi(letter d)]: the same fused multiply-adds in the
+// same order as group_sum (a zero coefficient is skipped, as there), so the
+// result is bit-identical to k_block_wire; the coefficients come in as kernel
+// parameters instead of shared-memory tables, which leaves the FP64 unit as
+// the only busy one.  I passes through; the isolated letter is scaled by
+// t[p][pi(p)].
+struct Wire2 {
+  double c[2][2];
+  double iso_t;
+  uint32_t rk;  // 2 bits per letter code L = 1 X, 2 Y, 3 Z: rank 0 / 1, 3 isolated
+  uint32_t nz;  // bit 2d + r: c[d][r] != 0
+};
+
+static __global__ void __launch_bounds__(256) k_block_wire2(size_t N, int j, Wire2 wv,
+                                                     const unsigned long long* lcode,
+                                                     const double* w_in, double* w_out,
+                                                     const unsigned* err) {
+  if (*err) return;  // no block order: the partner distances do not hold
+  const unsigned below = (1u << j) - 1;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const unsigned long long code = lcode[i];
+    const double w = w_in[i];
+    const int L = int((code >> (2 * j)) & 3);
+    if (L == 0) {
+      w_out[i] = w;
+      continue;
+    }
+    const int r = int((wv.rk >> (2 * L)) & 3);
+    if (r == 3) {
+      w_out[i] = w * wv.iso_t;
+      continue;
+    }
+    const int a = __popc(unsigned(code >> 32) & 0xffffu & below);
+    const int b = __popc(unsigned(code >> 48) & below);
+    long long stride = 1ll << a;
+    for (int k = 0; k < b; ++k) stride *= 3;
+    const double vp = w_in[(long long)i + (r ? -stride : stride)];
+    const double v0 = r ? vp : w, v1 = r ? w : vp;
+    const double c0 = r ? wv.c[1][0] : wv.c[0][0], c1 = r ? wv.c[1][1] : wv.c[0][1];
+    const uint32_t nz = wv.nz >> (2 * r);
+    double acc = 0.0;
+    if (nz & 1u) acc = fma(c0, v0, acc);
+    if (nz & 2u) acc = fma(c1, v1, acc);
+    w_out[i] = acc;
+  }
+}
+
 }  // namespace dev
 }  // namespace qx
