@@ -136,6 +136,8 @@ struct qx_plan_device {
     int chunks = 0, cb = 0;
     bool use_table = false, identity = true;
     size_t smem = 0;
+    uint64_t live = 0;                 // chunks with a qubit some gate touches
+    uint64_t idle[qx::kMaxWords] = {};  // qubits of the other chunks
   };
   std::vector<Pass> passes;
   size_t max_smem = 0;
@@ -248,6 +250,29 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
     dp.use_table = pc.use_table;
     dp.identity = pc.identity;
     dp.smem = pc.use_table ? pc.tab_xz.size() * 8 + pc.tab_e.size() : pc.ops.size() * 4;
+    if (pc.use_table) {
+      uint64_t touched[kMaxWords] = {};
+      for (const uint32_t op : pc.ops) {
+        const int q0 = int((op >> 2) & 127), q1 = int((op >> 9) & 127);
+        touched[q0 >> 6] |= 1ull << (q0 & 63);
+        if ((op & 3) != kOpPerm) touched[q1 >> 6] |= 1ull << (q1 & 63);
+      }
+      for (int ch = 0; ch < pc.chunks; ++ch) {
+        bool any = false;
+        for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
+          const int q = ch * pc.chunk_bits + b2;
+          if (q < p->n && ((touched[q >> 6] >> (q & 63)) & 1)) any = true;
+        }
+        if (any) {
+          dp.live |= 1ull << ch;
+        } else {
+          for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
+            const int q = ch * pc.chunk_bits + b2;
+            if (q < p->n) dp.idle[q >> 6] |= 1ull << (q & 63);
+          }
+        }
+      }
+    }
     d->max_smem = std::max(d->max_smem, dp.smem);
     d->passes.push_back(dp);
   }
@@ -512,12 +537,23 @@ qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
     // as many blocks per SM as their tables fit in shared memory
     const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (dp.smem + 1024))));
     const unsigned grid = grid_for(c.N, kThreads, c.sms, per_sm);
+    PassMasks pmk{};
+    for (int k = 0; k < kMaxWords; ++k) pmk.idle[k] = dp.idle[k];
+    const int P = clifford_parts<W>();
+    for (int pp = 0; pp < P; ++pp)
+      for (int ch = pp * dp.chunks / P; ch < (pp + 1) * dp.chunks / P; ++ch) {
+        if (!((dp.live >> ch) & 1)) continue;
+        for (int b2 = 0; b2 < dp.cb; ++b2) {
+          const int q = ch * dp.cb + b2;
+          if (q < c.n) pmk.part[pp][q >> 6] |= 1ull << (q & 63);
+        }
+      }
     if (dp.cb == 4)
-      k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.tab_xz,
-                                                                   dp.tab_e, dp.chunks);
+      k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(
+          c.cur.view<WT>(), n_in, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk);
     else
-      k_clifford_table<W, 3, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.tab_xz,
-                                                                   dp.tab_e, dp.chunks);
+      k_clifford_table<W, 3, WT><<<grid, kThreads, dp.smem, c.al.s>>>(
+          c.cur.view<WT>(), n_in, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk);
   } else {
     const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
     k_clifford_ops<W, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.ops, dp.nops);
@@ -1214,11 +1250,22 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
       1, std::min<unsigned long long>((total + kExpTile - 1) / kExpTile,
                                       (unsigned long long)c.sms * 8)));
   const size_t esmem = expand_emit_smem<W, WT>(nq);
+  const unsigned long long ntile = (total + kExpTile - 1) / kExpTile;
+  auto* tiles = static_cast<unsigned long long*>(c.al.get(size_t(2 * ntile + 2) * 8));
+  if (!tiles) {
+    c.al.put(offs);
+    c.al.put(out.base);
+    return fail(QX_ENOMEM, "device allocation of the expansion tile table failed");
+  }
   c.begin(KC_EXPAND);
-  k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, offs, total,
-                                                         s.fanq, nq, out.view<WT>());
-  c.end(KC_EXPAND, 1, (c.N + total) * (16 * W + sizeof(WT)));
+  k_expand_tiles<<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+      offs, s.ncnt + c.cslot, total, tiles, tiles + ntile + 1);
+  k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, offs, total, tiles, tiles + ntile + 1, s.fanq, nq,
+      out.view<WT>());
+  c.end(KC_EXPAND, 2, (c.N + total) * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
+  c.al.put(tiles);
   c.al.put(offs);
   const int oslot = 1 - c.cslot;
   c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));

@@ -126,6 +126,26 @@ __device__ __forceinline__ float wneg(float w) {
   return __uint_as_float(__float_as_uint(w) ^ 0x80000000u);
 }
 
+// Lanes of the warp holding the same key as this lane.  Terms of one
+// generator (or one block) usually sit together, so a warp-wide equality vote
+// answers most calls without the match instruction.
+__device__ __forceinline__ unsigned warp_peers(unsigned key) {
+  const unsigned k0 = __shfl_sync(0xffffffffu, key, 0);
+  if (__all_sync(0xffffffffu, key == k0)) return 0xffffffffu;
+  return __match_any_sync(0xffffffffu, key);
+}
+
+// Contiguous range of terms for the calling warp: [*b, *e), a multiple of 32
+// long, so that a warp's terms (usually of one generator) are read once and
+// in order.
+__device__ __forceinline__ void warp_range(size_t N, size_t* b, size_t* e) {
+  const size_t nw = size_t(gridDim.x) * (blockDim.x >> 5);
+  const size_t w = size_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const size_t per = (((N + nw - 1) / nw) + 31) & ~size_t(31);
+  *b = min(N, w * per);
+  *e = min(N, *b + per);
+}
+
 // Running product of a weight with table entries (the Cartesian expansion).
 template <typename WT>
 struct WProd;
@@ -200,18 +220,23 @@ __device__ __forceinline__ uint64_t key_hash(uint32_t g, const uint64_t* kx, con
 // Pauli letter of qubit q: 0 = I, 1 = X, 2 = Y, 3 = Z (as (x, z) bits).
 template <int W>
 __device__ __forceinline__ int letter_at(const uint64_t* x, const uint64_t* z, int q) {
-  const int k = q >> 6, b = q & 63;
-  const int xb = int((x[k] >> b) & 1), zb = int((z[k] >> b) & 1);
+  // the word by a select: a run-time index would put the string in local memory
+  const bool hi = W > 1 && q >= 64;
+  const int b = q & 63;
+  const int xb = int(((hi ? x[W - 1] : x[0]) >> b) & 1), zb = int(((hi ? z[W - 1] : z[0]) >> b) & 1);
   return xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
 }
 
 // Sets qubit q to table letter c (0 = X, 1 = Y, 2 = Z).
 template <int W>
 __device__ __forceinline__ void set_letter(uint64_t* x, uint64_t* z, int q, int c) {
-  const int k = q >> 6;
   const uint64_t m = 1ull << (q & 63);
-  x[k] = (c <= 1) ? (x[k] | m) : (x[k] & ~m);
-  z[k] = (c >= 1) ? (z[k] | m) : (z[k] & ~m);
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const uint64_t mk = (k == (q >> 6)) ? m : 0ull;
+    x[k] = (c <= 1) ? (x[k] | mk) : (x[k] & ~mk);
+    z[k] = (c >= 1) ? (z[k] | mk) : (z[k] & ~mk);
+  }
 }
 
 template <int W, typename WT = double>
@@ -353,11 +378,41 @@ __global__ void __launch_bounds__(256) k_clifford_ops(TermsT<WT> t, const unsign
   }
 }
 
+// Parts of the chunk range of k_clifford_table: part p is chunks
+// [p * chunks / P, (p + 1) * chunks / P).
+template <int W>
+__host__ __device__ constexpr int clifford_parts() {
+  return W == 1 ? 3 : 2;
+}
+
+// Qubit masks of a Clifford pass for k_clifford_table: the qubits of chunks
+// that the pass leaves alone (every gate of the pass acts elsewhere), and per
+// part the qubits of its other chunks (the letters its product depends on).
+struct PassMasks {
+  uint64_t idle[kMaxWords];
+  uint64_t part[3][kMaxWords];
+};
+
+// The image of a string is the product of its chunks' images, in chunk order
+// (X then Z letters within a chunk).  Three facts cut the table lookups:
+// * a chunk whose qubits no gate of the pass touches maps to itself; its
+//   letters pass through (their images have disjoint support from every other
+//   image, so they add no phase) and it is never looked up (`live`);
+// * the chunks split into P parts; the product of a part, with its phase, is
+//   kept per lane together with the part's letters that produced it, and
+//   reused while the lane's next string has the same letters there (strings of
+//   one generator that differ only on fan-out wires share most parts);
+// * the parts combine in order: the phase gains 2 |z_acc & x_part| (mod 4),
+//   which equals the sum of the per-chunk terms mod 2.
+// Each warp reads a contiguous range, so consecutive strings of a lane are
+// close relatives.
 template <int W, int CB, typename WT = double>
 __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsigned long long* n_in,
                                                         const uint64_t* tab_xz,
-                                                        const uint8_t* tab_e, int chunks) {
+                                                        const uint8_t* tab_e, int chunks,
+                                                        uint64_t live, PassMasks pmk) {
   constexpr int E = 1 << (2 * CB);
+  constexpr int P = clifford_parts<W>();
   extern __shared__ __align__(16) uint64_t s_tab[];
   uint8_t* s_e = reinterpret_cast<uint8_t*>(s_tab + size_t(chunks) * E * 2 * W);
   {
@@ -369,8 +424,12 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
   __syncthreads();
   const size_t N = *n_in;
   constexpr uint32_t M = (1u << CB) - 1;
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
-       i += size_t(gridDim.x) * blockDim.x) {
+  uint64_t kx[P][W], kz[P][W], vx[P][W], vz[P][W];
+  int ve[P];
+  unsigned valid = 0;
+  size_t rb, re;
+  warp_range(N, &rb, &re);
+  for (size_t i = rb + (threadIdx.x & 31); i < re; i += 32) {
     uint64_t x[W], z[W];
     load_term<W>(t, i, x, z);
     int e = 0;
@@ -382,43 +441,87 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
       ax[k] = 0;
       az[k] = 0;
     }
-    for (int c = 0; c < chunks; ++c) {
-      const int lo = c * CB, k = lo >> 6, off = lo & 63;
-      // chunks never straddle a word: 64 is a multiple of CB = 4, and for
-      // CB = 3 the straddling chunk is assembled from both words
-      uint32_t xb, zb;
-      if (CB == 4 || off + CB <= 64) {
-        xb = uint32_t(x[k] >> off) & M;
-        zb = uint32_t(z[k] >> off) & M;
-      } else {
-        xb = uint32_t((x[k] >> off) | (k + 1 < W ? (x[k + 1] << (64 - off)) : 0)) & M;
-        zb = uint32_t((z[k] >> off) | (k + 1 < W ? (z[k + 1] << (64 - off)) : 0)) & M;
-      }
-      const uint32_t idx = xb | (zb << CB);
-      if (!idx) continue;
-      // the entry (x words, then z words) in 16-byte loads
-      const ulonglong2* ent = reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
-      uint64_t ex[W], ez[W];
-      if (W == 1) {
-        const ulonglong2 v = ent[0];
-        ex[0] = v.x;
-        ez[0] = v.y;
-      } else {
-        const ulonglong2 v0 = ent[0], v1 = ent[1];
-        ex[0] = v0.x;
-        ex[W - 1] = v0.y;
-        ez[0] = v1.x;
-        ez[W - 1] = v1.y;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      bool same = (valid >> p) & 1;
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        same = same && kx[p][k] == (x[k] & pmk.part[p][k]) && kz[p][k] == (z[k] & pmk.part[p][k]);
+      if (!same) {  // the product of this part's chunks
+        uint64_t px[W], pz[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          px[k] = 0;
+          pz[k] = 0;
+          kx[p][k] = x[k] & pmk.part[p][k];
+          kz[p][k] = z[k] & pmk.part[p][k];
+        }
+        int pe = 0;
+        for (int c = p * chunks / P; c < (p + 1) * chunks / P; ++c) {
+          if (!((live >> c) & 1)) continue;
+          const int lo = c * CB, k = lo >> 6, off = lo & 63;
+          // for CB = 3 the chunk across the word boundary takes bits of both
+          // words by selects, not by a run-time index (which would put the
+          // string in local memory)
+          const uint64_t xw = (W == 1 || k == 0) ? x[0] : x[W - 1];
+          const uint64_t zw = (W == 1 || k == 0) ? z[0] : z[W - 1];
+          uint32_t xb, zb;
+          if (CB == 4 || off + CB <= 64) {
+            xb = uint32_t(xw >> off) & M;
+            zb = uint32_t(zw >> off) & M;
+          } else {  // k == 0 < W - 1
+            xb = uint32_t((xw >> off) | (W > 1 ? (x[W - 1] << (64 - off)) : 0)) & M;
+            zb = uint32_t((zw >> off) | (W > 1 ? (z[W - 1] << (64 - off)) : 0)) & M;
+          }
+          const uint32_t idx = xb | (zb << CB);
+          if (!idx) continue;
+          // the entry (x words, then z words) in 16-byte loads
+          const ulonglong2* ent =
+              reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
+          uint64_t ex[W], ez[W];
+          if (W == 1) {
+            const ulonglong2 v = ent[0];
+            ex[0] = v.x;
+            ez[0] = v.y;
+          } else {
+            const ulonglong2 v0 = ent[0], v1 = ent[1];
+            ex[0] = v0.x;
+            ex[W - 1] = v0.y;
+            ez[0] = v1.x;
+            ez[W - 1] = v1.y;
+          }
+          int anti = 0;
+#pragma unroll
+          for (int kk = 0; kk < W; ++kk) anti += __popcll(pz[kk] & ex[kk]);
+          pe += int(s_e[c * E + idx]) + 2 * anti;
+#pragma unroll
+          for (int kk = 0; kk < W; ++kk) {
+            px[kk] ^= ex[kk];
+            pz[kk] ^= ez[kk];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          vx[p][k] = px[k];
+          vz[p][k] = pz[k];
+        }
+        ve[p] = pe & 3;
+        valid |= 1u << p;
       }
       int anti = 0;
 #pragma unroll
-      for (int kk = 0; kk < W; ++kk) anti += __popcll(az[kk] & ex[kk]);
-      e += int(s_e[c * E + idx]) + 2 * anti;
+      for (int k = 0; k < W; ++k) anti += __popcll(az[k] & vx[p][k]);
+      e += ve[p] + 2 * anti;
 #pragma unroll
-      for (int kk = 0; kk < W; ++kk) {
-        ax[kk] ^= ex[kk];
-        az[kk] ^= ez[kk];
+      for (int k = 0; k < W; ++k) {
+        ax[k] ^= vx[p][k];
+        az[k] ^= vz[p][k];
       }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {  // the letters the pass leaves alone
+      ax[k] |= x[k] & pmk.idle[k];
+      az[k] |= z[k] & pmk.idle[k];
     }
     int c2 = 0;
 #pragma unroll
@@ -440,26 +543,6 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
 // where that row of the qubit's table is not isolated.  A qubit whose
 // non-isolated letters are all the same in a generator cannot make two of that
 // generator's strings collide, so it is expanded without a merge.
-
-// Lanes of the warp holding the same key as this lane.  Terms of one
-// generator (or one block) usually sit together, so a warp-wide equality vote
-// answers most calls without the match instruction.
-__device__ __forceinline__ unsigned warp_peers(unsigned key) {
-  const unsigned k0 = __shfl_sync(0xffffffffu, key, 0);
-  if (__all_sync(0xffffffffu, key == k0)) return 0xffffffffu;
-  return __match_any_sync(0xffffffffu, key);
-}
-
-// Contiguous range of terms for the calling warp: [*b, *e), a multiple of 32
-// long, so that a warp's terms (usually of one generator) are read once and
-// in order.
-__device__ __forceinline__ void warp_range(size_t N, size_t* b, size_t* e) {
-  const size_t nw = size_t(gridDim.x) * (blockDim.x >> 5);
-  const size_t w = size_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const size_t per = (((N + nw - 1) / nw) + 31) & ~size_t(31);
-  *b = min(N, w * per);
-  *e = min(N, *b + per);
-}
 
 template <int W, typename WT = double>
 __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const uint64_t* nisoX,
@@ -936,6 +1019,28 @@ constexpr int kExpItems = 4;
 constexpr int kExpTile = kExpThreads * kExpItems;
 constexpr int kExpMaxH = 8;  // distinct upper digit values a tree tile may span
 
+// The parents at the ends of every emit tile: tile_first[t] holds the child
+// c = t kExpTile and tile_last[t] the tile's last child; one thread per parent
+// marks the tile ends that fall in its range [offs[p], offs[p + 1]).  (A
+// search of the offsets per tile would be a chain of dependent memory reads
+// at the start of every tile.)
+static __global__ void k_expand_tiles(const unsigned long long* offs, const unsigned long long* n_in,
+                                      unsigned long long total, unsigned long long* tile_first,
+                                      unsigned long long* tile_last) {
+  const size_t N = *n_in;
+  const unsigned long long T = kExpTile;
+  for (size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
+       p += size_t(gridDim.x) * blockDim.x) {
+    const unsigned long long lo = offs[p], hi = p + 1 < N ? offs[p + 1] : total;
+    if (lo >= hi) continue;
+    for (unsigned long long t = lo / T; t <= (hi - 1) / T; ++t) {
+      const unsigned long long first = t * T, last = min(total, first + T) - 1;
+      if (first >= lo && first < hi) tile_first[t] = p;
+      if (last >= lo && last < hi) tile_last[t] = p;
+    }
+  }
+}
+
 // Dynamic shared memory of k_expand_emit: the fan-out tables, the parent
 // offsets of a tile and (FP64) the product tree of a single-parent tile.
 template <int W, typename WT>
@@ -964,7 +1069,8 @@ constexpr size_t expand_emit_smem(int nq) {
 template <int W, typename WT = double>
 __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* offs,
-    unsigned long long total, const FanQ* fq_g, int nq, TermsT<WT> out) {
+    unsigned long long total, const unsigned long long* tile_first,
+    const unsigned long long* tile_last, const FanQ* fq_g, int nq, TermsT<WT> out) {
   extern __shared__ unsigned char s_raw[];
   FanQ* s_fq = reinterpret_cast<FanQ*>(s_raw);
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_fq + nq);
@@ -978,23 +1084,15 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
   __shared__ double s_hw[kExpMaxH];
   __shared__ uint64_t s_hx[kExpMaxH][W], s_hz[kExpMaxH][W], s_hm[W];
   for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
-  const size_t N = *n_in;
+  (void)n_in;
   for (unsigned long long c0 = (unsigned long long)blockIdx.x * kExpTile; c0 < total;
        c0 += (unsigned long long)gridDim.x * kExpTile) {
     const unsigned long long c1 = min(total, c0 + kExpTile);
     if (threadIdx.x == 0) {
-      // last parent with offs[p] <= c0, and last parent with offs[p] <= c1 - 1
-      size_t lo = 0, hi = N;
-      while (hi - lo > 1) {
-        const size_t mid = (lo + hi) / 2;
-        if (offs[mid] <= c0) lo = mid; else hi = mid;
-      }
+      // the parents of the first and the last child of the tile
+      const size_t lo = size_t(tile_first[c0 / kExpTile]);
+      const size_t lo2 = size_t(tile_last[c0 / kExpTile]);
       s_p0 = lo;
-      size_t lo2 = lo, hi2 = N;
-      while (hi2 - lo2 > 1) {
-        const size_t mid = (lo2 + hi2) / 2;
-        if (offs[mid] <= c1 - 1) lo2 = mid; else hi2 = mid;
-      }
       s_p1 = lo2;
       s_nh = 0;
       if constexpr (sizeof(WT) == 8) {
