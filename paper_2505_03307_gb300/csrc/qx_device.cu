@@ -6,7 +6,9 @@
 // or from cudaMallocAsync on the caller's stream; nothing is allocated with a
 // blocking call on the hot path.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <memory>
 #include <cstring>
 #include <type_traits>
 #include <mutex>
@@ -125,9 +127,27 @@ void set_pool_threshold() {
 
 // Device copy of the plan: Clifford passes (gate lists or chunk tables) and
 // the fan-out tables, uploaded once per plan and device.
+// What the last run of a fan-out step of this plan did, as the guess the next
+// run launches on before the per-generator letter masks come back: an
+// expansion over every fan-out qubit (with its output size), or block-ordered
+// merges over a set of wires.  The device results and the masks decide
+// whether the guess held; a wrong guess costs only the discarded launches.
+// Plans may be shared between threads, so the fields are atomics (a torn
+// guess is just a wrong one).
+enum : int { kHintNone = 0, kHintExpand = 1, kHintBlocks = 2 };
+struct FanHint {
+  std::atomic<int> kind{kHintNone};
+  std::atomic<uint64_t> mq[qx::kMaxWords];
+  std::atomic<unsigned long long> total{0};
+  FanHint() {
+    for (auto& w : mq) w.store(0, std::memory_order_relaxed);
+  }
+};
+
 struct qx_plan_device {
   int device = -1;
   void* base = nullptr;
+  std::unique_ptr<FanHint[]> hints;  // one per fan-out step
   struct Pass {
     const uint32_t* ops = nullptr;
     int nops = 0;
@@ -275,6 +295,12 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
     }
     d->max_smem = std::max(d->max_smem, dp.smem);
     d->passes.push_back(dp);
+  }
+  d->hints.reset(new (std::nothrow) FanHint[std::max<size_t>(1, p->fans.size())]);
+  if (!d->hints) {
+    cudaFree(base);
+    delete d;
+    return fail(QX_ENOMEM, "host allocation failed");
   }
   p->dev = d;
   return QX_OK;
@@ -478,6 +504,22 @@ qx_status sync_read(Ctx& c, void* host, const void* dev, size_t bytes) {
   c.stage_off = 0;
   c.st.host_syncs++;
   return QX_OK;
+}
+
+// Two device-to-host reads and one synchronisation.
+qx_status sync_read2(Ctx& c, void* h1, const void* d1, size_t b1, void* h2, const void* d2,
+                     size_t b2) {
+  QX_TRY_CUDA(cudaMemcpyAsync(h1, d1, b1, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(h2, d2, b2, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
+  c.stage_off = 0;
+  c.st.host_syncs++;
+  return QX_OK;
+}
+
+bool limits_ok(const Ctx& c, size_t terms) {
+  return !(c.max_terms && terms > c.max_terms) &&
+         !(c.budget && terms * term_bytes(c.W, c.wtb) > c.budget);
 }
 
 // Host-to-device copy of a small host array, through t_stage when it has room.
@@ -890,14 +932,23 @@ qx_status run_merges_inplace(Ctx& c, const std::vector<const FanQubit*>& mq, boo
 }
 
 // The merge wires of a step in place, with the terms in block order (see
-// qx_merge_blocks.cuh).  *done is false when some block is incomplete (or the
-// step does not fit the block code); the terms are then unchanged.
+// qx_merge_blocks.cuh), in two halves: launch_blocks queues every kernel with
+// no host round trip (kernels after the block table check the error word and
+// do nothing when some block is incomplete); finish_blocks, given the error
+// word read back, keeps the block-ordered terms or releases them (the terms
+// in c.cur are then unchanged).
+struct BlocksPending {
+  void* mem = nullptr;
+  TermBuf out;
+  size_t N = 0, m = 0;
+  bool launched = false;  // false: the step does not fit the block code
+};
+
 template <int W, typename WT>
-qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
-                            bool* done) {
-  *done = false;
+qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPending* bp) {
+  bp->launched = false;
   const int m = int(mq.size());
-  if (m > kMaxBlockWires) return QX_OK;
+  if (m > kMaxBlockWires || m == 0) return QX_OK;
   BlockWires hb{};
   hb.m = m;
   for (int j = 0; j < m; ++j) {
@@ -1012,30 +1063,61 @@ qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool
     if (src != ov.w)
       QX_TRY_CUDA(cudaMemcpyAsync(ov.w, src, N * sizeof(WT), cudaMemcpyDeviceToDevice, c.al.s));
     QX_TRY_CUDA(cudaGetLastError());
-    unsigned err = 0;
-    QX_TRY(sync_read(c, &err, c.sc.err, 4));
-    if (err) {  // some block is incomplete: the terms in c.cur are unchanged
-      QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
-      return QX_OK;
-    }
-    replace_cur(c, out, N, c.cslot);
-    out = TermBuf();
-    *done = true;
     return QX_OK;
   };
   const qx_status st = body();
-  c.al.put(mem);
-  if (st != QX_OK || !*done) {
+  if (st != QX_OK) {
+    c.al.put(mem);
     c.al.put(out.base);
     return st;
   }
-  c.st.merge_passes += mq.size();
+  bp->mem = mem;
+  bp->out = out;
+  bp->N = N;
+  bp->m = size_t(m);
+  bp->launched = true;
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status finish_blocks(Ctx& c, BlocksPending* bp, unsigned err, bool accept, bool more_after,
+                        bool* done) {
+  *done = false;
+  c.al.put(bp->mem);
+  bp->mem = nullptr;
+  if (err) QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+  if (err || !accept) {
+    c.al.put(bp->out.base);
+    bp->out = TermBuf();
+    return QX_OK;
+  }
+  const size_t N = bp->N;
+  replace_cur(c, bp->out, N, c.cslot);
+  bp->out = TermBuf();
+  *done = true;
+  c.st.merge_passes += bp->m;
   c.st.inplace_steps++;
   c.st.block_steps++;
-  c.st.alg_bytes += mq.size() * 2ull * N * (16 * W + sizeof(WT));
-  c.st.children += mq.size() * N;
+  c.st.alg_bytes += bp->m * 2ull * N * (16 * W + sizeof(WT));
+  c.st.children += bp->m * N;
   if (!more_after && c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
   return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
+                            bool* done) {
+  *done = false;
+  BlocksPending bp;
+  QX_TRY((launch_blocks<W, WT>(c, mq, &bp)));
+  if (!bp.launched) return QX_OK;
+  unsigned err = 0;
+  if (const qx_status st = sync_read(c, &err, c.sc.err, 4)) {
+    c.al.put(bp.mem);
+    c.al.put(bp.out.base);
+    return st;
+  }
+  return finish_blocks<W, WT>(c, &bp, err, true, more_after, done);
 }
 
 template <int W, typename WT>
@@ -1176,8 +1258,110 @@ qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_a
   return QX_OK;
 }
 
+// Expansion of a fan-out step over the qubits that need no merge, in parts:
+// exp_count uploads their tables, counts every term's children and scans the
+// counts (the total lands in ncnt[2]); exp_emit allocates the output for cap
+// children and launches the tile table and the emit (which do nothing if the
+// total exceeds cap); exp_accept makes the output current.
+struct ExpPending {
+  unsigned long long* offs = nullptr;
+  unsigned long long* tiles = nullptr;
+  TermBuf out;
+  int nq = 0;
+};
+
+void exp_release(Ctx& c, ExpPending* ep) {
+  c.al.put(ep->tiles);
+  c.al.put(ep->offs);
+  c.al.put(ep->out.base);
+  *ep = ExpPending();
+}
+
 template <int W, typename WT>
-qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
+qx_status exp_count(Ctx& c, const std::vector<const FanQubit*>& fq, ExpPending* ep) {
+  Scratch& s = c.sc;
+  std::vector<FanQ> hq;
+  for (const FanQubit* f : fq) hq.push_back(to_dev(*f));
+  QX_TRY(h2d(c, s.fanq, hq.data(), hq.size() * sizeof(FanQ)));
+  ep->nq = int(hq.size());
+  const size_t ntiles = (c.N + kScanTile - 1) / kScanTile;
+  ep->offs = static_cast<unsigned long long*>(c.al.get((c.N + ntiles + 1) * 8));
+  if (!ep->offs) return fail(QX_ENOMEM, "device allocation of the expansion offsets failed");
+  unsigned long long* tsum = ep->offs + c.N;
+  c.begin(KC_COUNT);
+  k_expand_count<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, ep->nq * sizeof(FanQ),
+                          c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, ep->nq, ep->offs);
+  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + sizeof(WT)));
+  c.begin(KC_SCAN);
+  k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(ep->offs, s.ncnt + c.cslot, tsum);
+  k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, s.ncnt + 2);
+  k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(ep->offs, s.ncnt + c.cslot, tsum);
+  c.end(KC_SCAN, 3, uint64_t(c.N) * 8 * 3);
+  QX_TRY_CUDA(cudaGetLastError());
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status exp_emit(Ctx& c, ExpPending* ep, unsigned long long cap) {
+  Scratch& s = c.sc;
+  QX_TRY(alloc_terms(c.al, W, c.wtb, cap, &ep->out));
+  const unsigned egrid = unsigned(std::max<unsigned long long>(
+      1, std::min<unsigned long long>((cap + kExpTile - 1) / kExpTile,
+                                      (unsigned long long)c.sms * 8)));
+  const size_t esmem = expand_emit_smem<W, WT>(ep->nq);
+  const unsigned long long ntile = (cap + kExpTile - 1) / kExpTile;
+  ep->tiles = static_cast<unsigned long long*>(c.al.get(size_t(2 * ntile + 2) * 8));
+  if (!ep->tiles) return fail(QX_ENOMEM, "device allocation of the expansion tile table failed");
+  c.begin(KC_EXPAND);
+  k_expand_tiles<<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+      ep->offs, s.ncnt + c.cslot, s.ncnt + 2, cap, ep->tiles, ep->tiles + ntile + 1);
+  k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, ep->offs, s.ncnt + 2, cap, ep->tiles,
+      ep->tiles + ntile + 1, s.fanq, ep->nq, ep->out.view<WT>());
+  c.end(KC_EXPAND, 2, (c.N + cap) * (16 * W + sizeof(WT)));
+  QX_TRY_CUDA(cudaGetLastError());
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status exp_accept(Ctx& c, ExpPending* ep, unsigned long long total) {
+  const int oslot = 1 - c.cslot;
+  c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
+  c.st.children += total;
+  QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
+  c.al.put(ep->tiles);
+  c.al.put(ep->offs);
+  replace_cur(c, ep->out, total, oslot);
+  *ep = ExpPending();
+  if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
+  return QX_OK;
+}
+
+// From the per-generator letter masks: the qubits that need a merge in some
+// generator (mq, with the per-generator mixed masks) and the others (fq).
+void split_fan(const Ctx& c, const FanStep& fs, const std::vector<unsigned long long>& gm,
+               std::vector<uint64_t>* mixed, std::vector<const FanQubit*>* mq,
+               std::vector<const FanQubit*>* fq) {
+  const int W = c.W;
+  const size_t G = size_t(c.G);
+  mixed->assign(G * W, 0);
+  uint64_t any[kMaxWords] = {0, 0};
+  for (size_t g = 0; g < G; ++g)
+    for (int k = 0; k < W; ++k) {
+      const uint64_t a = gm[(g * 3 + 0) * W + k], b = gm[(g * 3 + 1) * W + k],
+                     d = gm[(g * 3 + 2) * W + k];
+      const uint64_t m = (a & b) | (a & d) | (b & d);
+      (*mixed)[g * W + k] = m;
+      any[k] |= m;
+    }
+  mq->clear();
+  fq->clear();
+  for (const FanQubit& f : fs.qs)
+    ((any[f.q / 64] >> (f.q % 64)) & 1 ? mq : fq)->push_back(&f);
+}
+
+template <int W, typename WT>
+qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint) {
   c.st.term_updates += (ops_before + 1) * c.N;
   c.st.fan_steps++;
   if (c.N == 0) return QX_OK;
@@ -1197,83 +1381,103 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before) {
   c.end(KC_MASK, 1, uint64_t(c.N) * 16 * W);
   QX_TRY_CUDA(cudaGetLastError());
   std::vector<unsigned long long> gm(G * 3 * W);
-  QX_TRY(sync_read(c, gm.data(), s.gmask, gm.size() * 8));
-  std::vector<uint64_t> mixed(G * W, 0);
-  uint64_t any[kMaxWords] = {0, 0};
-  for (size_t g = 0; g < G; ++g)
-    for (int k = 0; k < W; ++k) {
-      const uint64_t a = gm[(g * 3 + 0) * W + k], b = gm[(g * 3 + 1) * W + k],
-                     d = gm[(g * 3 + 2) * W + k];
-      const uint64_t m = (a & b) | (a & d) | (b & d);
-      mixed[g * W + k] = m;
-      any[k] |= m;
-    }
+  std::vector<uint64_t> mixed;
   std::vector<const FanQubit*> mq, fq;
-  for (const FanQubit& f : fs.qs)
-    ((any[f.q / 64] >> (f.q % 64)) & 1 ? mq : fq).push_back(&f);
-  if (!mq.empty())
-    QX_TRY(h2d(c, s.mixed, mixed.data(), G * W * 8));
-  // 2. one merge pass per qubit that needs it in some generator
+  bool have_gm = false;
+  // 2. the last run's outcome, launched before the masks are read back
+  const int guess = hint ? hint->kind.load(std::memory_order_relaxed) : kHintNone;
+  if (guess == kHintExpand) {
+    const unsigned long long cap = hint->total.load(std::memory_order_relaxed);
+    if (cap && limits_ok(c, cap)) {
+      std::vector<const FanQubit*> all;
+      for (const FanQubit& f : fs.qs) all.push_back(&f);
+      ExpPending ep;
+      qx_status st = exp_count<W, WT>(c, all, &ep);
+      if (st == QX_OK) st = exp_emit<W, WT>(c, &ep, cap);
+      unsigned long long total = 0;
+      if (st == QX_OK) st = sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &total, s.ncnt + 2, 8);
+      if (st != QX_OK) {
+        exp_release(c, &ep);
+        return st;
+      }
+      have_gm = true;
+      split_fan(c, fs, gm, &mixed, &mq, &fq);
+      if (mq.empty() && limits_ok(c, total)) {  // the guess held
+        if (total > cap) {  // more children than last time: emit again at full size
+          c.al.put(ep.tiles);
+          c.al.put(ep.out.base);
+          ep.tiles = nullptr;
+          ep.out = TermBuf();
+          st = exp_emit<W, WT>(c, &ep, total);
+          if (st != QX_OK) {
+            exp_release(c, &ep);
+            return st;
+          }
+        }
+        hint->total.store(total, std::memory_order_relaxed);
+        return exp_accept<W, WT>(c, &ep, total);
+      }
+      exp_release(c, &ep);
+    }
+  } else if (guess == kHintBlocks && c.inplace && W == 1 && c.n < 64) {
+    const uint64_t hm = hint->mq[0].load(std::memory_order_relaxed);
+    std::vector<const FanQubit*> gq;
+    for (const FanQubit& f : fs.qs)
+      if ((hm >> f.q) & 1) gq.push_back(&f);
+    BlocksPending bp;
+    QX_TRY((launch_blocks<W, WT>(c, gq, &bp)));
+    if (bp.launched) {
+      unsigned err = 0;
+      if (const qx_status st =
+              sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &err, c.sc.err, 4)) {
+        c.al.put(bp.mem);
+        c.al.put(bp.out.base);
+        return st;
+      }
+      have_gm = true;
+      split_fan(c, fs, gm, &mixed, &mq, &fq);
+      const bool held = fq.empty() && mq == gq && inplace_candidate(c, mq, gm);
+      bool done = false;
+      QX_TRY((finish_blocks<W, WT>(c, &bp, err, held, false, &done)));
+      if (done) return QX_OK;
+    }
+  }
+  if (!have_gm) {
+    QX_TRY(sync_read(c, gm.data(), s.gmask, gm.size() * 8));
+    split_fan(c, fs, gm, &mixed, &mq, &fq);
+  }
+  if (!mq.empty()) QX_TRY(h2d(c, s.mixed, mixed.data(), G * W * 8));
+  // 3. one merge pass per qubit that needs it in some generator
+  const uint64_t blocks0 = c.st.block_steps;
   if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm));
-  if (fq.empty()) return QX_OK;
-  // 3. one-shot expansion over the qubits that need no merge anywhere
-  std::vector<FanQ> hq;
-  for (const FanQubit* f : fq) hq.push_back(to_dev(*f));
-  QX_TRY(h2d(c, s.fanq, hq.data(), hq.size() * sizeof(FanQ)));
-  const int nq = int(hq.size());
-  const size_t ntiles = (c.N + kScanTile - 1) / kScanTile;
-  auto* offs = static_cast<unsigned long long*>(c.al.get((c.N + ntiles + 1) * 8));
-  if (!offs) return fail(QX_ENOMEM, "device allocation of the expansion offsets failed");
-  unsigned long long* tsum = offs + c.N;
-  c.begin(KC_COUNT);
-  k_expand_count<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, nq * sizeof(FanQ), c.al.s>>>(
-      c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, nq, offs);
-  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + sizeof(WT)));
-  c.begin(KC_SCAN);
-  k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, s.ncnt + c.cslot, tsum);
-  k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, s.ncnt + 2);
-  k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, s.ncnt + c.cslot, tsum);
-  c.end(KC_SCAN, 3, uint64_t(c.N) * 8 * 3);
-  QX_TRY_CUDA(cudaGetLastError());
+  if (fq.empty()) {
+    if (hint) {
+      const bool blocks = c.st.block_steps > blocks0 && W == 1;
+      if (blocks) {
+        uint64_t m = 0;
+        for (const FanQubit* f : mq) m |= 1ull << (f->q & 63);
+        hint->mq[0].store(m, std::memory_order_relaxed);
+      }
+      hint->kind.store(blocks ? kHintBlocks : kHintNone, std::memory_order_relaxed);
+    }
+    return QX_OK;
+  }
+  // 4. one-shot expansion over the qubits that need no merge anywhere
+  ExpPending ep;
+  qx_status st = exp_count<W, WT>(c, fq, &ep);
   unsigned long long total = 0;
-  QX_TRY(sync_read(c, &total, s.ncnt + 2, 8));
-  if (const qx_status e = check_limits(c, total)) {
-    c.al.put(offs);
-    return e;
+  if (st == QX_OK) st = sync_read(c, &total, s.ncnt + 2, 8);
+  if (st == QX_OK) st = check_limits(c, total);
+  if (st == QX_OK) st = exp_emit<W, WT>(c, &ep, total);
+  if (st != QX_OK) {
+    exp_release(c, &ep);
+    return st;
   }
-  TermBuf out;
-  if (const qx_status e = alloc_terms(c.al, W, c.wtb, total, &out)) {
-    c.al.put(offs);
-    return e;
+  if (hint) {
+    hint->total.store(total, std::memory_order_relaxed);
+    hint->kind.store(mq.empty() ? kHintExpand : kHintNone, std::memory_order_relaxed);
   }
-  const unsigned egrid = unsigned(std::max<unsigned long long>(
-      1, std::min<unsigned long long>((total + kExpTile - 1) / kExpTile,
-                                      (unsigned long long)c.sms * 8)));
-  const size_t esmem = expand_emit_smem<W, WT>(nq);
-  const unsigned long long ntile = (total + kExpTile - 1) / kExpTile;
-  auto* tiles = static_cast<unsigned long long*>(c.al.get(size_t(2 * ntile + 2) * 8));
-  if (!tiles) {
-    c.al.put(offs);
-    c.al.put(out.base);
-    return fail(QX_ENOMEM, "device allocation of the expansion tile table failed");
-  }
-  c.begin(KC_EXPAND);
-  k_expand_tiles<<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-      offs, s.ncnt + c.cslot, total, tiles, tiles + ntile + 1);
-  k_expand_emit<W, WT><<<egrid, kExpThreads, esmem, c.al.s>>>(
-      c.cur.view<WT>(), s.ncnt + c.cslot, offs, total, tiles, tiles + ntile + 1, s.fanq, nq,
-      out.view<WT>());
-  c.end(KC_EXPAND, 2, (c.N + total) * (16 * W + sizeof(WT)));
-  QX_TRY_CUDA(cudaGetLastError());
-  c.al.put(tiles);
-  c.al.put(offs);
-  const int oslot = 1 - c.cslot;
-  c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
-  c.st.children += total;
-  QX_TRY(h2d(c, s.ncnt + oslot, &total, 8));
-  replace_cur(c, out, total, oslot);
-  if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
-  return QX_OK;
+  return exp_accept<W, WT>(c, &ep, total);
 }
 
 // One Pauli rotation step (qx_pauli_rot.cuh): index the terms, count each
@@ -1406,7 +1610,8 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     } else if (stp.kind == kStepRot) {
       QX_TRY(run_rot<W, WT>(c, p->rots[stp.index], stp.ops_before));
     } else {
-      QX_TRY(run_fan<W, WT>(c, p->fans[stp.index], stp.ops_before));
+      QX_TRY(run_fan<W, WT>(c, p->fans[stp.index], stp.ops_before,
+                            p->dev ? &p->dev->hints[stp.index] : nullptr));
     }
   }
   c.st.term_updates += p->ops_after_last_fan * c.N;

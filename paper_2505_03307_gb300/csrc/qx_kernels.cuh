@@ -1024,9 +1024,14 @@ constexpr int kExpMaxH = 8;  // distinct upper digit values a tree tile may span
 // marks the tile ends that fall in its range [offs[p], offs[p + 1]).  (A
 // search of the offsets per tile would be a chain of dependent memory reads
 // at the start of every tile.)
+// *total_d is the output size; a launch sized for cap < *total_d (a guess that
+// was too small) does nothing, as does the emit below.
 static __global__ void k_expand_tiles(const unsigned long long* offs, const unsigned long long* n_in,
-                                      unsigned long long total, unsigned long long* tile_first,
+                                      const unsigned long long* total_d, unsigned long long cap,
+                                      unsigned long long* tile_first,
                                       unsigned long long* tile_last) {
+  const unsigned long long total = *total_d;
+  if (total > cap) return;
   const size_t N = *n_in;
   const unsigned long long T = kExpTile;
   for (size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
@@ -1069,8 +1074,11 @@ constexpr size_t expand_emit_smem(int nq) {
 template <int W, typename WT = double>
 __global__ void __launch_bounds__(kExpThreads) k_expand_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* offs,
-    unsigned long long total, const unsigned long long* tile_first,
-    const unsigned long long* tile_last, const FanQ* fq_g, int nq, TermsT<WT> out) {
+    const unsigned long long* total_d, unsigned long long cap,
+    const unsigned long long* tile_first, const unsigned long long* tile_last, const FanQ* fq_g,
+    int nq, TermsT<WT> out) {
+  const unsigned long long total = *total_d;
+  if (total > cap) return;  // sized for a smaller guess: the caller launches again
   extern __shared__ unsigned char s_raw[];
   FanQ* s_fq = reinterpret_cast<FanQ*>(s_raw);
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(s_fq + nq);
