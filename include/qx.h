@@ -135,6 +135,9 @@ typedef struct {
   uint64_t inplace_steps;      /* fan-out steps whose merges ran in place */
   uint64_t inplace_fallbacks;  /* in-place attempts that found an open group */
   uint64_t block_steps;        /* in-place steps that ran in block order */
+  uint64_t guesses_held;       /* fan-out steps launched on the plan's record of its last
+                                  run (before their letter masks were read) that kept it */
+  uint64_t guesses_missed;     /* such launches that the masks or the device rejected */
   /* per kernel class: launches, algorithmic bytes (terms each launch must
    * read and write, 16W+8 bytes per term), and device milliseconds (only with
    * QX_FLAG_KERNEL_TIMING; 0 otherwise) */

@@ -1415,8 +1415,10 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
           }
         }
         hint->total.store(total, std::memory_order_relaxed);
+        c.st.guesses_held++;
         return exp_accept<W, WT>(c, &ep, total);
       }
+      c.st.guesses_missed++;
       exp_release(c, &ep);
     }
   } else if (guess == kHintBlocks && c.inplace && W == 1 && c.n < 64) {
@@ -1439,7 +1441,11 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       const bool held = fq.empty() && mq == gq && inplace_candidate(c, mq, gm);
       bool done = false;
       QX_TRY((finish_blocks<W, WT>(c, &bp, err, held, false, &done)));
-      if (done) return QX_OK;
+      if (done) {
+        c.st.guesses_held++;
+        return QX_OK;
+      }
+      c.st.guesses_missed++;
     }
   }
   if (!have_gm) {

@@ -72,7 +72,8 @@ KC_COUNT = 15
 
 _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches", "host_syncs",
             "final_terms", "peak_terms", "fan_steps", "merge_passes", "clifford_passes",
-            "inplace_steps", "inplace_fallbacks", "block_steps")
+            "inplace_steps", "inplace_fallbacks", "block_steps", "guesses_held",
+            "guesses_missed")
 
 
 class ServerOpts(ctypes.Structure):

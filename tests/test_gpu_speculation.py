@@ -1,0 +1,113 @@
+"""Fan-out steps launched on the plan's record of its last run.
+
+A plan remembers, per fan-out step, whether its last run was a pure expansion
+(with its output size) or block-ordered merges over a set of wires, and the
+next run launches that work before the per-generator letter masks come back.
+These tests run one plan repeatedly with options that change the outcome
+(generator ranges that change the output size or the merge wires, in-place
+merges switched off, FP32), so that each kind of wrong guess happens, and
+compare every result with a fresh plan (which has no record) bit for bit and
+with the oracle.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import compare_result
+from oracle import oracle as O
+from paper_2505_03307_gb300 import qx
+from paper_2505_03307_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+
+
+def _sorted(res):
+    x, z, w, g = (t.cpu().numpy() for t in res.raw_device())
+    keys = [g] + [x[:, k] for k in range(x.shape[1])] + [z[:, k] for k in range(z.shape[1])]
+    order = np.lexsort(tuple(reversed(keys)))
+    return g[order], x[order], z[order], w[order]
+
+
+def _same(a, b):
+    ga, xa, za, wa = _sorted(a)
+    gb, xb, zb, wb = _sorted(b)
+    assert np.array_equal(ga, gb) and np.array_equal(xa, xb) and np.array_equal(za, zb)
+    assert np.array_equal(wa, wb)
+
+
+def _fresh(n, instrs, **kw):
+    return qx.propagate(qx.group_ops(qx.load_circuit(n, instrs)), **kw)
+
+
+def test_second_run_keeps_the_guesses_and_the_result():
+    n, instrs = W.fan_in_heavy(2, n=20, n_s=8, total=500, tail=80)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    first = qx.propagate(plan)
+    second = qx.propagate(plan)
+    s1, s2 = first.stats(), second.stats()
+    assert s1["guesses_held"] == 0 and s1["guesses_missed"] == 0
+    # the T layer (an expansion) and the RZ layer (block-ordered merges)
+    assert s2["guesses_held"] == 2 and s2["guesses_missed"] == 0
+    assert s2["host_syncs"] == s1["host_syncs"] - 2
+    _same(first, second)
+    compare_result(second, O.propagate(n, instrs, mode="plan", threads=8))
+
+
+def test_generator_ranges_change_sizes_and_merge_wires():
+    """Generators inside the fan-out set S have two strings and merge on one
+    wire each; those outside have 2^8 and merge on all eight wires.  Changing
+    the range makes the recorded output size too small or too large and the
+    recorded merge wires wrong."""
+    n, instrs = W.fan_in_heavy(3, n=20, n_s=8, total=500, tail=80)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    held = missed = 0
+    for gens in [(0, 4), (0, 20), (12, 20), (2, 6), (0, 20), (0, 20)]:
+        res = qx.propagate(plan, gens=gens)
+        st = res.stats()
+        held += st["guesses_held"]
+        missed += st["guesses_missed"]
+        _same(res, _fresh(n, instrs, gens=gens))
+        compare_result(res, O.propagate(n, instrs, mode="plan", gens=gens, threads=8))
+    assert held > 0 and missed > 0
+
+
+def test_options_that_disable_the_recorded_path():
+    n, instrs = W.fan_in_heavy(4, n=20, n_s=8, total=500, tail=80)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    base = qx.propagate(plan)
+    # in-place merges off: the block record must not be used
+    off = qx.propagate(plan, inplace=False)
+    assert off.stats()["block_steps"] == 0
+    _same(off, _fresh(n, instrs, inplace=False))
+    # FP32 on the same plan, then FP64 again
+    f32 = qx.propagate(plan, precision=32)
+    _same(f32, _fresh(n, instrs, precision=32))
+    again = qx.propagate(plan)
+    _same(again, base)
+    # pruning: the records hold output sizes before pruning
+    pr = qx.propagate(plan, eps=1e-3)
+    _same(pr, _fresh(n, instrs, eps=1e-3))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_circuits_repeated(seed):
+    """Random small circuits with T / RZ layers on random subsets, one plan
+    propagated over a sequence of generator ranges."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(6, 13))
+    _, instrs = W.random_small_2q(seed, n, 60, p2=0.2)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(4):
+        a = int(rng.integers(0, n))
+        b = int(rng.integers(a + 1, n + 1))
+        res = qx.propagate(plan, gens=(a, b))
+        _same(res, _fresh(n, instrs, gens=(a, b)))
+        compare_result(res, O.propagate(n, instrs, mode="plan", gens=(a, b), threads=4))
