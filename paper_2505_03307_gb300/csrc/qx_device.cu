@@ -980,6 +980,7 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     if (!mq[j]->iso[2]) hb.niso_z |= qb;
     if (hb.canon[j] <= 1) hb.canon_x |= qb;  // X or Y
     if (hb.canon[j] >= 1) hb.canon_z |= qb;  // Y or Z
+    (r == 2 ? hb.rad2 : hb.rad3) |= qb;
     hb.pi[j] = uint8_t(inplace_pi(*mq[j]));
     if (hb.pi[j] != (0 | (1 << 2) | (2 << 4))) hb.relab |= 1u << j;
   }
@@ -996,7 +997,7 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
   const size_t o_tab = take(bcap * 16), o_cnt = take(bcap * 4), o_exp = take(bcap * 4),
                o_off = take((bcap + ntiles + 1) * 8), o_n = take(32),
                o_list = take((kBlockListMax + 1) * 4), o_slot = take(N * 4),
-               o_pib = take(N * 4), o_code = take(N * 8), o_code2 = take(N * 8),
+               o_code2 = take(N * 8),
                o_w = take(N * sizeof(WT)), o_bw = take(sizeof(BlockWires));
   void* mem = c.al.get(off);
   if (!mem) return QX_OK;
@@ -1009,8 +1010,6 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
   auto* nblk = reinterpret_cast<unsigned*>(b8 + o_list);     // claimed blocks
   unsigned* blist = nblk + 1;                                // their slots (the first 1024)
   auto* bslot = reinterpret_cast<unsigned*>(b8 + o_slot);
-  auto* pib = reinterpret_cast<unsigned*>(b8 + o_pib);
-  auto* lcode = reinterpret_cast<unsigned long long*>(b8 + o_code);
   auto* lcode2 = reinterpret_cast<unsigned long long*>(b8 + o_code2);
   auto* wtmp = reinterpret_cast<WT*>(b8 + o_w);
   auto* d_bw = reinterpret_cast<BlockWires*>(b8 + o_bw);
@@ -1025,7 +1024,7 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     QX_TRY(h2d(c, d_bw, &hb, sizeof hb));
     c.begin(KC_BLOCK_SETUP);
     k_block_claim<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, d_bw, btab, bcap, bcnt, bexp,
-                                                      bslot, pib, lcode, nblk, blist, c.sc.err);
+                                                      bslot, nblk, blist, c.sc.err);
     // offsets: from the list of blocks when it is short, else (dn[0] = bcap)
     // from the sweep of the table and its scan, which otherwise do nothing
     k_block_list<<<1, kBlockListMax, 0, c.al.s>>>(nblk, blist, bcnt, bexp, bcap, boff, dn,
@@ -1041,8 +1040,8 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     // nothing otherwise.  The word is read once, after the last wire.
     QX_TRY(alloc_terms(c.al, W, c.wtb, N, &out));
     const auto ov = out.view<WT>();
-    k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, d_bw, bslot, pib, boff, lcode, ov,
-                                                        lcode2, ov.w, c.sc.err);
+    k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, d_bw, bslot, boff, ov, lcode2,
+                                                        ov.w, c.sc.err);
     c.end(KC_BLOCK_SETUP, 7, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
     const WT* src = ov.w;
     for (int j = 0; j < m; ++j) {

@@ -39,13 +39,14 @@ struct BlockWires {
   // identity
   uint8_t pi[kMaxBlockWires];
   uint32_t relab;
-  // The same facts packed for the per-term loop of k_block_claim: inf[j] =
+  // The same facts packed for the per-term loop of k_block_scatter: inf[j] =
   // q (bits 0-5), the rank of the letter with xz code c = x | z << 1 in bits
   // 8 + 4c .. 11 + 4c (15: I or an isolated letter), the radix in bits 24-25;
   // and, per qubit, where X / Y / Z are non-isolated and the canonical
   // letter's x and z bits.
   uint32_t inf[kMaxBlockWires];
   uint64_t niso_x, niso_y, niso_z, canon_x, canon_z;
+  uint64_t rad2, rad3;  // qubits of the wires with two / three non-isolated letters
 };
 
 // Letter index of bits (x, z): 0 I, 1 X, 2 Y, 3 Z  -> table letter = index - 1.
@@ -56,30 +57,29 @@ __device__ __forceinline__ int letter4(uint64_t x, uint64_t z, int q) {
 
 // Per term: the block key (non-isolated letters of the merge wires replaced
 // by the wire's canonical letter, generator packed in), claimed in the block
-// table; the member count of the block (warp-combined), the block's expected
-// size, the term's place in its block and its letter code.  The key is formed
-// with whole-word masks; only the place and the code need a loop over wires.
+// table; the member count of the block (warp-combined) and the block's
+// expected size.  Everything here is whole-word: the key from letter masks,
+// the size 2^a 3^b from two population counts.  The term's place in its
+// block and its letter code are left to k_block_scatter, which reads the
+// strings anyway.
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int n,
                                                      const BlockWires* bw_g, ulonglong2* btab,
                                                      unsigned long long bcap, unsigned* bcnt,
                                                      unsigned* bexp, unsigned* bslot,
-                                                     unsigned* pib, unsigned long long* lcode,
                                                      unsigned* nblk, unsigned* blist,
                                                      unsigned* err) {
-  __shared__ uint32_t s_inf[kMaxBlockWires];
-  __shared__ uint64_t s_mask[5];
-  const int m = bw_g->m;
-  if (threadIdx.x < unsigned(m)) s_inf[threadIdx.x] = bw_g->inf[threadIdx.x];
-  if (threadIdx.x == 32) {
+  __shared__ uint64_t s_mask[7];
+  if (threadIdx.x == 0) {
     s_mask[0] = bw_g->niso_x;
     s_mask[1] = bw_g->niso_y;
     s_mask[2] = bw_g->niso_z;
     s_mask[3] = bw_g->canon_x;
     s_mask[4] = bw_g->canon_z;
+    s_mask[5] = bw_g->rad2;
+    s_mask[6] = bw_g->rad3;
   }
   __syncthreads();
-  const bool fast = m <= kFastStrideWires;
   for (size_t base = size_t(blockIdx.x) * blockDim.x; base < N;
        base += size_t(gridDim.x) * blockDim.x) {
     const size_t i = base + threadIdx.x;
@@ -88,22 +88,8 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       const uint64_t x = t.x[i], z = t.z[i];
       const uint64_t dm = (x & ~z & s_mask[0]) | (x & z & s_mask[1]) | (~x & z & s_mask[2]);
       const uint64_t kx = (x & ~dm) | (s_mask[3] & dm), kz = (z & ~dm) | (s_mask[4] & dm);
-      unsigned long long code = 0;
-      unsigned pos = 0, stride = 1, r2 = 0, r3 = 0;
-      for (int j = 0; j < m; ++j) {
-        const uint32_t inf = s_inf[j];
-        const int q = int(inf & 63u);
-        const uint32_t c = (uint32_t(x >> q) & 1u) | ((uint32_t(z >> q) & 1u) << 1);
-        code |= (unsigned long long)(c ^ (c >> 1)) << (2 * j);  // 0 I, 1 X, 2 Y, 3 Z
-        const uint32_t rk = (inf >> (8 + 4 * c)) & 15u;
-        if (rk != 15u) {  // a digit of the block
-          const uint32_t rdx = (inf >> 24) & 3u;
-          pos += rk * stride;
-          stride *= rdx;
-          if (rdx == 2) r2 |= 1u << j; else r3 |= 1u << j;
-        }
-      }
-      if (fast) code |= ((unsigned long long)r2 << 32) | ((unsigned long long)r3 << 48);
+      unsigned size = 1u << __popcll(dm & s_mask[5]);
+      for (int k = __popcll(dm & s_mask[6]); k > 0; --k) size *= 3u;
       unsigned long long lo, hi;
       pack_full_key(kx, kz, t.g[i], n, &lo, &hi);
       unsigned long long p = __umul64hi(slot_hash(lo, hi), bcap);
@@ -120,7 +106,7 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
           k.y = ohi;
           if (olo == ~0ull && ohi == ~0ull) {
             slot = unsigned(p);
-            bexp[slot] = stride;  // the claimant records the block's size
+            bexp[slot] = size;  // the claimant records the block's size
             const unsigned li = atomicAdd(nblk, 1u);  // and lists the slot
             if (li < kBlockListMax) blist[li] = slot;
             break;
@@ -132,13 +118,10 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
         }
         if (++p == bcap) p = 0;
       }
-      if (slot == 0xffffffffu) {
+      if (slot == 0xffffffffu)
         atomicOr(err, kErrProbe);
-      } else {
+      else
         bslot[i] = slot;
-        pib[i] = pos;
-        lcode[i] = code;
-      }
     }
     // member counts, one atomic per block and warp
     const unsigned peers = warp_peers(slot);
@@ -221,41 +204,68 @@ static __global__ void k_block_sizes(const ulonglong2* btab, const unsigned long
   }
 }
 
-// Terms to block order: place = offset of the block + place in the block.
-// The strings are written with the letter permutations pi of the merge wires
-// already applied (the wire passes read only letter codes and weights, so the
-// names can change before them).
+// Terms to block order: place = offset of the block + place in the block,
+// the place being the mixed-radix number of the term's letters on the
+// block's digit wires (digit = rank among the wire's non-isolated letters).
+// Each term also gets its letter code (2 bits per wire, and with at most
+// kFastStrideWires wires the masks of the radix-2 and radix-3 wires of its
+// block in the upper half), and its string is written with the letter
+// permutations pi of the merge wires applied (the wire passes read only
+// letter codes and weights, so the names can change before them).
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_scatter(TermsT<WT> t, size_t N,
                                                        const BlockWires* bw_g,
-                                                       const unsigned* bslot, const unsigned* pib,
+                                                       const unsigned* bslot,
                                                        const unsigned long long* boff,
-                                                       const unsigned long long* lcode,
                                                        TermsT<WT> out, unsigned long long* lcode_out,
                                                        WT* w_out, const unsigned* err) {
   if (*err) return;  // an incomplete block: the places are not a permutation
-  __shared__ BlockWires bw;
-  if (threadIdx.x == 0) bw = *bw_g;
+  __shared__ uint32_t s_inf[kMaxBlockWires];
+  __shared__ uint8_t s_pi[kMaxBlockWires];
+  __shared__ uint32_t s_relab;
+  const int m = bw_g->m;
+  if (threadIdx.x < unsigned(m)) {
+    s_inf[threadIdx.x] = bw_g->inf[threadIdx.x];
+    s_pi[threadIdx.x] = bw_g->pi[threadIdx.x];
+  }
+  if (threadIdx.x == 32) s_relab = bw_g->relab;
   __syncthreads();
+  const bool fast = m <= kFastStrideWires;
+  const uint32_t relab = s_relab;
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
        i += size_t(gridDim.x) * blockDim.x) {
-    const unsigned long long d = boff[bslot[i]] + pib[i];
-    uint64_t x = t.x[i], z = t.z[i];
-    for (uint32_t r = bw.relab; r; r &= r - 1) {
-      const int j = __ffs(r) - 1;
-      const int q = bw.q[j];
-      const int L = letter4(x, z, q);
-      if (!L) continue;
-      const int c = (bw.pi[j] >> (2 * (L - 1))) & 3;  // 0 X, 1 Y, 2 Z
-      const uint64_t m = 1ull << q;
-      x = c <= 1 ? (x | m) : (x & ~m);
-      z = c >= 1 ? (z | m) : (z & ~m);
+    const unsigned slot = bslot[i];
+    const uint64_t x = t.x[i], z = t.z[i];
+    uint64_t xo = x, zo = z;
+    unsigned long long code = 0;
+    unsigned pos = 0, stride = 1, r2 = 0, r3 = 0;
+    for (int j = 0; j < m; ++j) {
+      const uint32_t inf = s_inf[j];
+      const int q = int(inf & 63u);
+      const uint32_t c = (uint32_t(x >> q) & 1u) | ((uint32_t(z >> q) & 1u) << 1);
+      const uint32_t L = c ^ (c >> 1);  // 0 I, 1 X, 2 Y, 3 Z
+      code |= (unsigned long long)L << (2 * j);
+      const uint32_t rk = (inf >> (8 + 4 * c)) & 15u;
+      if (rk != 15u) {  // a digit of the block
+        const uint32_t rdx = (inf >> 24) & 3u;
+        pos += rk * stride;
+        stride *= rdx;
+        if (rdx == 2) r2 |= 1u << j; else r3 |= 1u << j;
+      }
+      if (L && ((relab >> j) & 1u)) {
+        const uint32_t cl = (uint32_t(s_pi[j]) >> (2 * (L - 1))) & 3u;  // 0 X, 1 Y, 2 Z
+        const uint64_t mq = 1ull << q;
+        xo = cl <= 1 ? (xo | mq) : (xo & ~mq);
+        zo = cl >= 1 ? (zo | mq) : (zo & ~mq);
+      }
     }
-    out.x[d] = x;
-    out.z[d] = z;
+    if (fast) code |= ((unsigned long long)r2 << 32) | ((unsigned long long)r3 << 48);
+    const unsigned long long d = boff[slot] + pos;
+    out.x[d] = xo;
+    out.z[d] = zo;
     out.g[d] = t.g[i];
     w_out[d] = t.w[i];
-    lcode_out[d] = lcode[i];
+    lcode_out[d] = code;
   }
 }
 
@@ -335,38 +345,58 @@ struct Wire2 {
   uint32_t nz;  // bit 2d + r: c[d][r] != 0
 };
 
+// One term of k_block_wire2: its letter code's digit decides whether it
+// passes through (I), scales (isolated letter) or needs its partner, at
+// *partner (-1: none).
+__device__ __forceinline__ int wire2_kind(const Wire2& wv, unsigned long long code, int j,
+                                          unsigned below, size_t i, long long* partner) {
+  const int L = int((code >> (2 * j)) & 3);
+  *partner = -1;
+  if (L == 0) return 3;  // I
+  const int r = int((wv.rk >> (2 * L)) & 3);
+  if (r == 3) return 2;  // isolated
+  const int a = __popc(unsigned(code >> 32) & 0xffffu & below);
+  const int b = __popc(unsigned(code >> 48) & below);
+  long long stride = 1ll << a;
+  for (int k = 0; k < b; ++k) stride *= 3;
+  *partner = (long long)i + (r ? -stride : stride);
+  return r;
+}
+
+__device__ __forceinline__ double wire2_out(const Wire2& wv, int kind, double w, double vp) {
+  if (kind == 3) return w;
+  if (kind == 2) return w * wv.iso_t;
+  const int r = kind;
+  const double v0 = r ? vp : w, v1 = r ? w : vp;
+  const double c0 = r ? wv.c[1][0] : wv.c[0][0], c1 = r ? wv.c[1][1] : wv.c[0][1];
+  const uint32_t nz = wv.nz >> (2 * r);
+  double acc = 0.0;
+  if (nz & 1u) acc = fma(c0, v0, acc);
+  if (nz & 2u) acc = fma(c1, v1, acc);
+  return acc;
+}
+
+// Two terms per thread and iteration (i and i + the grid's thread count), so
+// that each thread has two independent chains of loads in flight in front of
+// the FP64 unit.
 static __global__ void __launch_bounds__(256) k_block_wire2(size_t N, int j, Wire2 wv,
-                                                     const unsigned long long* lcode,
-                                                     const double* w_in, double* w_out,
-                                                     const unsigned* err) {
+                                                            const unsigned long long* lcode,
+                                                            const double* w_in, double* w_out,
+                                                            const unsigned* err) {
   if (*err) return;  // no block order: the partner distances do not hold
   const unsigned below = (1u << j) - 1;
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
-       i += size_t(gridDim.x) * blockDim.x) {
-    const unsigned long long code = lcode[i];
-    const double w = w_in[i];
-    const int L = int((code >> (2 * j)) & 3);
-    if (L == 0) {
-      w_out[i] = w;
-      continue;
-    }
-    const int r = int((wv.rk >> (2 * L)) & 3);
-    if (r == 3) {
-      w_out[i] = w * wv.iso_t;
-      continue;
-    }
-    const int a = __popc(unsigned(code >> 32) & 0xffffu & below);
-    const int b = __popc(unsigned(code >> 48) & below);
-    long long stride = 1ll << a;
-    for (int k = 0; k < b; ++k) stride *= 3;
-    const double vp = w_in[(long long)i + (r ? -stride : stride)];
-    const double v0 = r ? vp : w, v1 = r ? w : vp;
-    const double c0 = r ? wv.c[1][0] : wv.c[0][0], c1 = r ? wv.c[1][1] : wv.c[0][1];
-    const uint32_t nz = wv.nz >> (2 * r);
-    double acc = 0.0;
-    if (nz & 1u) acc = fma(c0, v0, acc);
-    if (nz & 2u) acc = fma(c1, v1, acc);
-    w_out[i] = acc;
+  const size_t S = size_t(gridDim.x) * blockDim.x;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += 2 * S) {
+    const size_t i2 = i + S;
+    const bool two = i2 < N;
+    const unsigned long long code = lcode[i], code2 = two ? lcode[i2] : 0ull;
+    const double w = w_in[i], w2 = two ? w_in[i2] : 0.0;
+    long long p, p2 = -1;
+    const int k = wire2_kind(wv, code, j, below, i, &p);
+    const int k2 = two ? wire2_kind(wv, code2, j, below, i2, &p2) : 3;
+    const double vp = p >= 0 ? w_in[p] : 0.0, vp2 = p2 >= 0 ? w_in[p2] : 0.0;
+    w_out[i] = wire2_out(wv, k, w, vp);
+    if (two) w_out[i2] = wire2_out(wv, k2, w2, vp2);
   }
 }
 
