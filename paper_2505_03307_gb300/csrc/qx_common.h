@@ -104,7 +104,9 @@ struct qx_plan {
   std::vector<size_t> order;                       // order[k]: input index of ins[k] (empty: identity)
   size_t K = 0, Kp = 0;
   std::vector<int> op_kind;                        // chain: 1 = U, 0 = V
-  std::vector<std::vector<qx::Table3>> luts;       // per chain op (empty for V)
+  // per chain op (empty for V): the tables of the wires the operator touches,
+  // in increasing qubit order (every other wire's table is the identity)
+  std::vector<std::vector<std::pair<int, qx::Table3>>> luts;
   std::vector<qx::CliffPass> passes;
   std::vector<qx::FanStep> fans;
   std::vector<qx::RotStep> rots;

@@ -625,20 +625,22 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
       compose_step(acc[q], gate_image(c->ins[i]));
     }
     std::sort(touched.begin(), touched.end());
-    std::vector<Table3>& lut = p->luts[k];
-    lut.assign(n, kIdentity3);
+    auto& lut = p->luts[k];
+    lut.reserve(touched.size());
     FanStep fs;
     fs.op_index = k;
     for (const int j : touched) {
       seen[j] = 0;
+      Table3 t;
       for (int r = 0; r < 3; ++r)
-        for (int col = 0; col < 3; ++col) lut[j].r[r][col] = settle(acc[j].r[r][col]);
+        for (int col = 0; col < 3; ++col) t.r[r][col] = settle(acc[j].r[r][col]);
+      lut.emplace_back(j, t);
       uint32_t code = 0;
-      const TableKind kind = classify(lut[j], &code);
+      const TableKind kind = classify(t, &code);
       if (kind == kSignedPerm)
         cur.ops.push_back(encode_op(kOpPerm, j, -1, code));
       else if (kind == kFanOut)
-        fs.qs.push_back(make_fan_qubit(j, lut[j]));
+        fs.qs.push_back(make_fan_qubit(j, t));
     }
     if (fs.qs.empty()) {
       ++ops_since_fan;
@@ -824,7 +826,10 @@ qx_status qx_plan_lut(const qx_plan* p, size_t op, double* out) {
     return fail(QX_EINVAL, "operator is not a one-qubit operator");
   for (int j = 0; j < p->n; ++j)
     for (int a = 0; a < 3; ++a)
-      for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = p->luts[op][j].r[a][c];
+      for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = kIdentity3.r[a][c];
+  for (const auto& [j, t] : p->luts[op])
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = t.r[a][c];
   return QX_OK;
 }
 
