@@ -814,14 +814,21 @@ bool wire2_of(const FanQubit& f, int pi, Wire2* out) {
   // letter code L of table letter a: X 1, Y 2, Z 3
   w.rk = 0;
   for (int d = 0; d < 2; ++d) w.rk |= uint32_t(d) << (2 * (lt[d] + 1));
+  // the FP32 split exactly as to_dev builds FanQ::th / tl
+  auto split = [](double t, float* h, float* l) {
+    *h = float(t);
+    *l = float(t - double(*h));
+  };
   if (iso >= 0) {
     w.rk |= 3u << (2 * (iso + 1));
     w.iso_t = f.t.r[iso][(pi >> (2 * iso)) & 3];
+    split(w.iso_t, &w.iso_h, &w.iso_l);
   }
   for (int d = 0; d < 2; ++d) {
     const int col = (pi >> (2 * lt[d])) & 3;
     for (int r = 0; r < 2; ++r) {
       w.c[d][r] = f.t.r[lt[r]][col];
+      split(w.c[d][r], &w.ch[d][r], &w.cl[d][r]);
       if (w.c[d][r] != 0.0) w.nz |= 1u << (2 * d + r);
     }
   }
@@ -1048,11 +1055,8 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
       WT* dst = (j & 1) ? ov.w : wtmp;
       c.begin(KC_BLOCK);
       Wire2 w2;
-      if (std::is_same<WT, double>::value && m <= kFastStrideWires &&
-          wire2_of(*mq[j], hb.pi[j], &w2))
-        k_block_wire2<<<grid, kThreads, 0, c.al.s>>>(N, j, w2, lcode2,
-                                                     reinterpret_cast<const double*>(src),
-                                                     reinterpret_cast<double*>(dst), c.sc.err);
+      if (m <= kFastStrideWires && wire2_of(*mq[j], hb.pi[j], &w2))
+        k_block_wire2<WT><<<grid, kThreads, 0, c.al.s>>>(N, j, w2, lcode2, src, dst, c.sc.err);
       else
         k_block_wire<WT><<<grid, kThreads, 0, c.al.s>>>(N, d_bw, j, to_dev(*mq[j]), hb.pi[j],
                                                          lcode2, src, dst, c.sc.err);

@@ -67,10 +67,33 @@ __device__ __forceinline__ double wmul(double w, const FanQ& f, int a, int c) {
   return w * f.t[a][c];
 }
 
-__device__ __forceinline__ float wmul(float w, const FanQ& f, int a, int c) {
-  const float th = f.th[a][c];
+// w t for t = th + tl (hi / lo floats): the leading product and its rounding
+// error (TwoProduct by FMA) plus the low part.
+__device__ __forceinline__ float wmul_split(float w, float th, float tl) {
   const float p = w * th;
-  return p + fmaf(w, f.tl[a][c], fmaf(w, th, -p));
+  return p + fmaf(w, tl, fmaf(w, th, -p));
+}
+
+__device__ __forceinline__ float wmul(float w, const FanQ& f, int a, int c) {
+  return wmul_split(w, f.th[a][c], f.tl[a][c]);
+}
+
+// One member of a compensated group sum (Dot2 of Ogita, Rump and Oishi): adds
+// v t, t = th + tl, to (sum, comp); the first member starts the sum.
+__device__ __forceinline__ void dot2_add(float v, float th, float tl, bool* any, float* sum,
+                                         float* comp) {
+  const float p = v * th;
+  const float pe = fmaf(v, th, -p) + v * tl;
+  if (!*any) {
+    *sum = p;
+    *comp = pe;
+    *any = true;
+  } else {
+    const float t = *sum + p;  // TwoSum
+    const float bp = t - *sum;
+    *comp += ((*sum - (t - bp)) + (p - bp)) + pe;
+    *sum = t;
+  }
 }
 
 // sum over the present letters a (in the order X, Y, Z) of t[a][col] v[a],
@@ -96,23 +119,8 @@ __device__ __forceinline__ float group_sum(const FanQ& f, int col, const bool* h
   bool any = false;
   float sum = 0.f, comp = 0.f;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (has[a] && ((f.nz >> (3 * a + col)) & 1)) {
-      const float th = f.th[a][col];
-      const float p = v[a] * th;
-      const float pe = fmaf(v[a], th, -p) + v[a] * f.tl[a][col];
-      if (!any) {
-        sum = p;
-        comp = pe;
-        any = true;
-      } else {
-        const float t = sum + p;  // TwoSum
-        const float bp = t - sum;
-        comp += ((sum - (t - bp)) + (p - bp)) + pe;
-        sum = t;
-      }
-    }
-  }
+  for (int a = 0; a < 3; ++a)
+    if (has[a] && ((f.nz >> (3 * a + col)) & 1)) dot2_add(v[a], f.th[a][col], f.tl[a][col], &any, &sum, &comp);
   *reached = any;
   return sum + comp;
 }

@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
        base += size_t(gridDim.x) * blockDim.x) {
     const size_t i = base + threadIdx.x;
     unsigned slot = 0xffffffffu;
+    unsigned long long key_lo = 0, key_hi = 0;
+    unsigned blk_size = 0;
     if (i < N) {
       const uint64_t x = t.x[i], z = t.z[i];
       const uint64_t dm = (x & ~z & s_mask[0]) | (x & z & s_mask[1]) | (~x & z & s_mask[2]);
@@ -92,12 +94,36 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       for (int k = __popcll(dm & s_mask[6]); k > 0; --k) size *= 3u;
       unsigned long long lo, hi;
       pack_full_key(kx, kz, t.g[i], n, &lo, &hi);
+      key_lo = lo;
+      key_hi = hi;
+      blk_size = size;
+    }
+    // One probe per distinct key and warp: the lanes of a warp usually hold
+    // members of one block.  (Every probe of a claimed block by a lane whose
+    // L1 still holds the slot as empty would be a compare-and-swap on one
+    // hot address.)
+    const bool valid = i < N;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    unsigned peers;
+    {
+      const unsigned long long l0 = __shfl_sync(0xffffffffu, key_lo, 0);
+      const unsigned long long h0 = __shfl_sync(0xffffffffu, key_hi, 0);
+      if (__all_sync(0xffffffffu, !valid || (key_lo == l0 && key_hi == h0)))
+        peers = act;
+      else
+        peers = __match_any_sync(0xffffffffu, key_lo) & __match_any_sync(0xffffffffu, key_hi) &
+                act;
+    }
+    const int lane = int(threadIdx.x & 31);
+    const int leader = valid ? __ffs(peers) - 1 : lane;
+    if (valid && lane == leader) {
+      const unsigned long long lo = key_lo, hi = key_hi;
+      const unsigned size = blk_size;
       unsigned long long p = __umul64hi(slot_hash(lo, hi), bcap);
       for (unsigned long long probe = 0; probe < bcap; ++probe) {
-        // a block has many members: read first (a cached read may be stale
-        // only as "empty", which the compare-and-swap corrects; keys never
-        // change once written) and compare-and-swap only an empty slot, so
-        // that the members of a claimed block do not contend
+        // read first (a cached read may be stale only as "empty", which the
+        // compare-and-swap corrects; keys never change once written) and
+        // compare-and-swap only an empty slot
         ulonglong2 k = btab[p];
         if (k.x == ~0ull && k.y == ~0ull) {
           unsigned long long olo, ohi;
@@ -121,12 +147,11 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       if (slot == 0xffffffffu)
         atomicOr(err, kErrProbe);
       else
-        bslot[i] = slot;
+        atomicAdd(&bcnt[slot], unsigned(__popc(peers)));  // the members' count
     }
-    // member counts, one atomic per block and warp
-    const unsigned peers = warp_peers(slot);
-    if (slot != 0xffffffffu && int(threadIdx.x & 31) == __ffs(peers) - 1)
-      atomicAdd(&bcnt[slot], unsigned(__popc(peers)));
+    // the leader's slot to its peers
+    slot = __shfl_sync(0xffffffffu, slot, leader);
+    if (valid && slot != 0xffffffffu) bslot[i] = slot;
   }
 }
 
@@ -341,6 +366,8 @@ __global__ void __launch_bounds__(256) k_block_wire(size_t N, const BlockWires* 
 struct Wire2 {
   double c[2][2];
   double iso_t;
+  float ch[2][2], cl[2][2];  // FP32 path: c = ch + cl
+  float iso_h, iso_l;
   uint32_t rk;  // 2 bits per letter code L = 1 X, 2 Y, 3 Z: rank 0 / 1, 3 isolated
   uint32_t nz;  // bit 2d + r: c[d][r] != 0
 };
@@ -376,13 +403,28 @@ __device__ __forceinline__ double wire2_out(const Wire2& wv, int kind, double w,
   return acc;
 }
 
+// FP32 weights: the same compensated sum (and scaling) as group_sum / wmul.
+__device__ __forceinline__ float wire2_out(const Wire2& wv, int kind, float w, float vp) {
+  if (kind == 3) return w;
+  if (kind == 2) return wmul_split(w, wv.iso_h, wv.iso_l);
+  const int r = kind;
+  const float v0 = r ? vp : w, v1 = r ? w : vp;
+  const uint32_t nz = wv.nz >> (2 * r);
+  bool any = false;
+  float sum = 0.f, comp = 0.f;
+  if (nz & 1u) dot2_add(v0, wv.ch[r][0], wv.cl[r][0], &any, &sum, &comp);
+  if (nz & 2u) dot2_add(v1, wv.ch[r][1], wv.cl[r][1], &any, &sum, &comp);
+  return sum + comp;
+}
+
 // Two terms per thread and iteration (i and i + the grid's thread count), so
 // that each thread has two independent chains of loads in flight in front of
 // the FP64 unit.
-static __global__ void __launch_bounds__(256) k_block_wire2(size_t N, int j, Wire2 wv,
-                                                            const unsigned long long* lcode,
-                                                            const double* w_in, double* w_out,
-                                                            const unsigned* err) {
+template <typename WT>
+__global__ void __launch_bounds__(256) k_block_wire2(size_t N, int j, Wire2 wv,
+                                                     const unsigned long long* lcode,
+                                                     const WT* w_in, WT* w_out,
+                                                     const unsigned* err) {
   if (*err) return;  // no block order: the partner distances do not hold
   const unsigned below = (1u << j) - 1;
   const size_t S = size_t(gridDim.x) * blockDim.x;
@@ -390,11 +432,11 @@ static __global__ void __launch_bounds__(256) k_block_wire2(size_t N, int j, Wir
     const size_t i2 = i + S;
     const bool two = i2 < N;
     const unsigned long long code = lcode[i], code2 = two ? lcode[i2] : 0ull;
-    const double w = w_in[i], w2 = two ? w_in[i2] : 0.0;
+    const WT w = w_in[i], w2 = two ? w_in[i2] : WT(0);
     long long p, p2 = -1;
     const int k = wire2_kind(wv, code, j, below, i, &p);
     const int k2 = two ? wire2_kind(wv, code2, j, below, i2, &p2) : 3;
-    const double vp = p >= 0 ? w_in[p] : 0.0, vp2 = p2 >= 0 ? w_in[p2] : 0.0;
+    const WT vp = p >= 0 ? w_in[p] : WT(0), vp2 = p2 >= 0 ? w_in[p2] : WT(0);
     w_out[i] = wire2_out(wv, k, w, vp);
     if (two) w_out[i2] = wire2_out(wv, k2, w2, vp2);
   }
