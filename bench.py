@@ -439,6 +439,8 @@ def fp32_bench(qx, plan, flush, steps, fp64_step_ms, warmup=3):
         if k < warmup + steps - 1:
             r.free()
     st = r.stats()
+    flush()
+    kt = qx.propagate(plan, precision=32, kernel_timing=True).stats()["kernels"]
     ref = qx.propagate(plan)
     worst = 0.0
     for g in (16, 33, 49):
@@ -451,6 +453,7 @@ def fp32_bench(qx, plan, flush, steps, fp64_step_ms, warmup=3):
     return {"precision": 32, "ms_per_step": ms, "term_updates_per_s": st["term_updates"] / (ms / 1e3),
             "speedup_vs_fp64": statistics.median(fp64_step_ms) / ms,
             "max_rel_error_vs_fp64": worst, "error_sample": "generators 16, 33, 49, |w| > 1e-6",
+            "kernel_ms": {k: round(d["ms"], 4) for k, d in kt.items() if d["launches"]},
             "l2": "flushed between timed steps"}
 
 

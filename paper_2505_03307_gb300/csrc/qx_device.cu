@@ -988,8 +988,28 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     if (hb.canon[j] <= 1) hb.canon_x |= qb;  // X or Y
     if (hb.canon[j] >= 1) hb.canon_z |= qb;  // Y or Z
     (r == 2 ? hb.rad2 : hb.rad3) |= qb;
+    hb.qmask |= qb;
+    if (r == 2) {  // the rank-1 letter
+      for (int a = 0; a < 3; ++a)
+        if (hb.rank[j][a] == 1) (a == 0 ? hb.r1x : a == 1 ? hb.r1y : hb.r1z) |= qb;
+    }
     hb.pi[j] = uint8_t(inplace_pi(*mq[j]));
-    if (hb.pi[j] != (0 | (1 << 2) | (2 << 4))) hb.relab |= 1u << j;
+    if (hb.pi[j] != (0 | (1 << 2) | (2 << 4))) {
+      hb.relab |= 1u << j;
+      hb.rq |= qb;
+      for (int a = 0; a < 3; ++a) {  // source letter a -> image letter pi(a)
+        const int im = (hb.pi[j] >> (2 * a)) & 3;
+        if (im <= 1) hb.tx[a] |= qb;
+        if (im >= 1) hb.tz[a] |= qb;
+      }
+    }
+  }
+  {  // whole-word layout when every wire has radix 2 and the qubits increase
+    bool inc = true;
+    for (int j = 1; j < m; ++j) inc = inc && hb.q[j] > hb.q[j - 1];
+    hb.lay_fast = (m <= kFastStrideWires && hb.rad3 == 0 && inc) ? 1 : 0;
+    for (int b = 0; b < 8; ++b)
+      if ((hb.qmask >> (8 * b)) & 0xffull) hb.bytes[hb.nbytes++] = uint8_t(b);
   }
   const size_t N = c.N;
   const unsigned long long bcap = std::max<unsigned long long>(1024, 2ull * N);

@@ -47,6 +47,16 @@ struct BlockWires {
   uint32_t inf[kMaxBlockWires];
   uint64_t niso_x, niso_y, niso_z, canon_x, canon_z;
   uint64_t rad2, rad3;  // qubits of the wires with two / three non-isolated letters
+  // Whole-word form of k_block_scatter's per-term work, when every wire has
+  // radix 2, there are at most kFastStrideWires of them and their qubits
+  // increase with j (lay_fast): the qubits where letter X / Y / Z has rank 1
+  // (r1*), the merge qubits (qmask) and the bytes of the word that hold them;
+  // the relabelled qubits (rq) and, per source letter X / Y / Z, where its
+  // image has an x bit (tx) or a z bit (tz).
+  int lay_fast;
+  int nbytes;
+  uint8_t bytes[8];
+  uint64_t r1x, r1y, r1z, qmask, rq, tx[3], tz[3];
 };
 
 // Letter index of bits (x, z): 0 I, 1 X, 2 Y, 3 Z  -> table letter = index - 1.
@@ -229,6 +239,26 @@ static __global__ void k_block_sizes(const ulonglong2* btab, const unsigned long
   }
 }
 
+// Bits of v at the merge qubits, gathered in wire order through the
+// per-byte tables of k_block_scatter (tab[b][byte]: that byte's merge-qubit
+// bits at their wire positions).
+__device__ __forceinline__ uint32_t gather_wires(uint64_t v, const uint16_t (*tab)[256],
+                                                 const uint8_t* bytes, int nb) {
+  uint32_t r = 0;
+  for (int k = 0; k < nb; ++k) r |= tab[k][(v >> (8 * bytes[k])) & 255u];
+  return r;
+}
+
+// Spreads the low 16 bits of v to the even bits of a 32-bit word.
+__device__ __forceinline__ uint32_t spread16(uint32_t v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
 // Terms to block order: place = offset of the block + place in the block,
 // the place being the mixed-radix number of the term's letters on the
 // block's digit wires (digit = rank among the wire's non-isolated letters).
@@ -236,7 +266,10 @@ static __global__ void k_block_sizes(const ulonglong2* btab, const unsigned long
 // kFastStrideWires wires the masks of the radix-2 and radix-3 wires of its
 // block in the upper half), and its string is written with the letter
 // permutations pi of the merge wires applied (the wire passes read only
-// letter codes and weights, so the names can change before them).
+// letter codes and weights, so the names can change before them).  With
+// lay_fast the letters of all wires are gathered at once (byte tables), the
+// place is the rank bits gathered over the digit wires, and the relabel is
+// whole-word; otherwise one loop step per wire.
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_scatter(TermsT<WT> t, size_t N,
                                                        const BlockWires* bw_g,
@@ -248,43 +281,86 @@ __global__ void __launch_bounds__(256) k_block_scatter(TermsT<WT> t, size_t N,
   __shared__ uint32_t s_inf[kMaxBlockWires];
   __shared__ uint8_t s_pi[kMaxBlockWires];
   __shared__ uint32_t s_relab;
+  __shared__ uint16_t s_tab[8][256];
+  __shared__ uint8_t s_bytes[8];
   const int m = bw_g->m;
+  const bool lay = bw_g->lay_fast != 0;
+  const int nb = bw_g->nbytes;
   if (threadIdx.x < unsigned(m)) {
     s_inf[threadIdx.x] = bw_g->inf[threadIdx.x];
     s_pi[threadIdx.x] = bw_g->pi[threadIdx.x];
   }
   if (threadIdx.x == 32) s_relab = bw_g->relab;
+  if (threadIdx.x < 8) s_bytes[threadIdx.x] = bw_g->bytes[threadIdx.x];
+  const uint64_t qmask = bw_g->qmask;
+  if (lay) {
+    for (int e = threadIdx.x; e < nb * 256; e += blockDim.x) {
+      const int k = e >> 8, v = e & 255, b = bw_g->bytes[k];
+      uint32_t r = 0;
+      for (int bit = 0; bit < 8; ++bit) {
+        const int q = 8 * b + bit;
+        if (((v >> bit) & 1) && ((qmask >> q) & 1))
+          r |= 1u << __popcll(qmask & ((1ull << q) - 1));
+      }
+      s_tab[k][v] = uint16_t(r);
+    }
+  }
   __syncthreads();
   const bool fast = m <= kFastStrideWires;
   const uint32_t relab = s_relab;
+  const uint64_t nx = bw_g->niso_x, ny = bw_g->niso_y, nz = bw_g->niso_z;
+  const uint64_t r1x = bw_g->r1x, r1y = bw_g->r1y, r1z = bw_g->r1z, rq = bw_g->rq;
+  const uint64_t tx0 = bw_g->tx[0], tx1 = bw_g->tx[1], tx2 = bw_g->tx[2];
+  const uint64_t tz0 = bw_g->tz[0], tz1 = bw_g->tz[1], tz2 = bw_g->tz[2];
+  const uint32_t all = m >= 32 ? 0xffffffffu : ((1u << m) - 1);
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
        i += size_t(gridDim.x) * blockDim.x) {
     const unsigned slot = bslot[i];
     const uint64_t x = t.x[i], z = t.z[i];
     uint64_t xo = x, zo = z;
     unsigned long long code = 0;
-    unsigned pos = 0, stride = 1, r2 = 0, r3 = 0;
-    for (int j = 0; j < m; ++j) {
-      const uint32_t inf = s_inf[j];
-      const int q = int(inf & 63u);
-      const uint32_t c = (uint32_t(x >> q) & 1u) | ((uint32_t(z >> q) & 1u) << 1);
-      const uint32_t L = c ^ (c >> 1);  // 0 I, 1 X, 2 Y, 3 Z
-      code |= (unsigned long long)L << (2 * j);
-      const uint32_t rk = (inf >> (8 + 4 * c)) & 15u;
-      if (rk != 15u) {  // a digit of the block
-        const uint32_t rdx = (inf >> 24) & 3u;
-        pos += rk * stride;
-        stride *= rdx;
-        if (rdx == 2) r2 |= 1u << j; else r3 |= 1u << j;
+    unsigned pos = 0;
+    if (lay) {
+      const uint64_t ix = x & ~z, iy = x & z, iz = ~x & z;
+      const uint32_t D = gather_wires((ix & nx) | (iy & ny) | (iz & nz), s_tab, s_bytes, nb);
+      const uint32_t R = gather_wires((ix & r1x) | (iy & r1y) | (iz & r1z), s_tab, s_bytes, nb);
+      const uint32_t cx = gather_wires(x ^ z, s_tab, s_bytes, nb);
+      const uint32_t cz = gather_wires(z, s_tab, s_bytes, nb);
+      code = spread16(cx) | (spread16(cz) << 1) | ((unsigned long long)D << 32);
+      if (D == all) {
+        pos = R;
+      } else {
+        int k = 0;
+        for (uint32_t d = D; d; d &= d - 1, ++k) pos |= ((R >> (__ffs(d) - 1)) & 1u) << k;
       }
-      if (L && ((relab >> j) & 1u)) {
-        const uint32_t cl = (uint32_t(s_pi[j]) >> (2 * (L - 1))) & 3u;  // 0 X, 1 Y, 2 Z
-        const uint64_t mq = 1ull << q;
-        xo = cl <= 1 ? (xo | mq) : (xo & ~mq);
-        zo = cl >= 1 ? (zo | mq) : (zo & ~mq);
+      if (rq) {
+        xo = (x & ~rq) | (ix & tx0) | (iy & tx1) | (iz & tx2);
+        zo = (z & ~rq) | (ix & tz0) | (iy & tz1) | (iz & tz2);
       }
+    } else {
+      unsigned stride = 1, r2 = 0, r3 = 0;
+      for (int j = 0; j < m; ++j) {
+        const uint32_t inf = s_inf[j];
+        const int q = int(inf & 63u);
+        const uint32_t c = (uint32_t(x >> q) & 1u) | ((uint32_t(z >> q) & 1u) << 1);
+        const uint32_t L = c ^ (c >> 1);  // 0 I, 1 X, 2 Y, 3 Z
+        code |= (unsigned long long)L << (2 * j);
+        const uint32_t rk = (inf >> (8 + 4 * c)) & 15u;
+        if (rk != 15u) {  // a digit of the block
+          const uint32_t rdx = (inf >> 24) & 3u;
+          pos += rk * stride;
+          stride *= rdx;
+          if (rdx == 2) r2 |= 1u << j; else r3 |= 1u << j;
+        }
+        if (L && ((relab >> j) & 1u)) {
+          const uint32_t cl = (uint32_t(s_pi[j]) >> (2 * (L - 1))) & 3u;  // 0 X, 1 Y, 2 Z
+          const uint64_t mq = 1ull << q;
+          xo = cl <= 1 ? (xo | mq) : (xo & ~mq);
+          zo = cl >= 1 ? (zo | mq) : (zo & ~mq);
+        }
+      }
+      if (fast) code |= ((unsigned long long)r2 << 32) | ((unsigned long long)r3 << 48);
     }
-    if (fast) code |= ((unsigned long long)r2 << 32) | ((unsigned long long)r3 << 48);
     const unsigned long long d = boff[slot] + pos;
     out.x[d] = xo;
     out.z[d] = zo;
