@@ -249,8 +249,11 @@ qx_status qx_result_stats(const qx_result* r, qx_prop_stats* s);
 qx_status qx_result_export(const qx_result* r, int gen, uint64_t* x, uint64_t* z, double* w,
                            size_t cap, int on_device);
 
-/* All terms of the result in device order (unsorted), into caller device
- * buffers: x, z (cap x W words), w (cap doubles), gen (cap int32). */
+/* All terms of the result in device order (unsorted), into caller buffers:
+ * x, z (cap x W words), w (cap doubles), gen (cap int32).  The buffers are
+ * device memory or page-locked host memory (cudaHostAlloc / cudaMallocHost),
+ * which the export kernel then writes across the host link directly, with no
+ * intermediate device copy.  Returns after the writes are complete. */
 qx_status qx_result_raw(const qx_result* r, uint64_t* x, uint64_t* z, double* w, int32_t* gen,
                         size_t cap);
 

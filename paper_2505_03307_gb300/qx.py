@@ -457,6 +457,21 @@ class Result:
                                              g.data_ptr(), k))
         return x[:k], z[:k], w[:k], g[:k]
 
+    def raw_into(self, x, z, w, g):
+        """All terms in device order into the given torch tensors (CUDA, or
+        pinned CPU tensors, which the export kernel writes directly): x, z
+        int64 (>= nterms, W), w float64, g int32.  Returns nterms."""
+        k = self.nterms
+        for t in (x, z, w, g):
+            if not (t.is_cuda or t.is_pinned()) or not t.is_contiguous():
+                raise ValueError("buffers must be contiguous CUDA or pinned CPU tensors")
+        cap = min(x.shape[0], z.shape[0], w.shape[0], g.shape[0])
+        if cap < k:
+            raise ValueError("buffers are smaller than the result")
+        _check(load_library().qx_result_raw(self._h, x.data_ptr(), z.data_ptr(), w.data_ptr(),
+                                             g.data_ptr(), cap))
+        return k
+
     def coeff(self, g, pauli):
         xw, zw = pauli_to_words(pauli, self.n)
         re, im = ctypes.c_double(), ctypes.c_double()
