@@ -139,6 +139,7 @@ struct FanHint {
   std::atomic<int> kind{kHintNone};
   std::atomic<uint64_t> mq[qx::kMaxWords];
   std::atomic<unsigned long long> total{0};
+  std::atomic<unsigned> nblk{0};  // blocks of the last block-ordered run (table size)
   FanHint() {
     for (auto& w : mq) w.store(0, std::memory_order_relaxed);
   }
@@ -948,11 +949,13 @@ struct BlocksPending {
   void* mem = nullptr;
   TermBuf out;
   size_t N = 0, m = 0;
+  const unsigned* nblk = nullptr;  // device: the number of blocks claimed
   bool launched = false;  // false: the step does not fit the block code
 };
 
 template <int W, typename WT>
-qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPending* bp) {
+qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPending* bp,
+                        unsigned nblk_guess = 0) {
   bp->launched = false;
   const int m = int(mq.size());
   if (m > kMaxBlockWires || m == 0) return QX_OK;
@@ -1012,7 +1015,14 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
       if ((hb.qmask >> (8 * b)) & 0xffull) hb.bytes[hb.nbytes++] = uint8_t(b);
   }
   const size_t N = c.N;
-  const unsigned long long bcap = std::max<unsigned long long>(1024, 2ull * N);
+  // The block table holds every block at load <= 1/2: 2N slots covers N
+  // blocks of one.  With the block count of the plan's last run, 4x that
+  // count; more blocks than that exhaust the probes, which fails the step
+  // like an incomplete block, and the caller repeats it at full size.
+  const unsigned long long bcap =
+      nblk_guess ? std::min<unsigned long long>(std::max<unsigned long long>(1024, 4ull * nblk_guess),
+                                                std::max<unsigned long long>(1024, 2ull * N))
+                 : std::max<unsigned long long>(1024, 2ull * N);
   const size_t ntiles = (bcap + kScanTile - 1) / kScanTile;
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t off = 0;
@@ -1050,8 +1060,9 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     QX_TRY_CUDA(cudaMemsetAsync(nblk, 0, 4, c.al.s));
     QX_TRY(h2d(c, d_bw, &hb, sizeof hb));
     c.begin(KC_BLOCK_SETUP);
-    k_block_claim<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, d_bw, btab, bcap, bcnt, bexp,
-                                                      bslot, nblk, blist, c.sc.err);
+    const unsigned long long plimit = nblk_guess ? std::min<unsigned long long>(bcap, 256) : bcap;
+    k_block_claim<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, c.n, d_bw, btab, bcap, plimit, bcnt,
+                                                      bexp, bslot, nblk, blist, c.sc.err);
     // offsets: from the list of blocks when it is short, else (dn[0] = bcap)
     // from the sweep of the table and its scan, which otherwise do nothing
     k_block_list<<<1, kBlockListMax, 0, c.al.s>>>(nblk, blist, bcnt, bexp, bcap, boff, dn,
@@ -1098,6 +1109,7 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
   bp->out = out;
   bp->N = N;
   bp->m = size_t(m);
+  bp->nblk = nblk;
   bp->launched = true;
   return QX_OK;
 }
@@ -1129,26 +1141,27 @@ qx_status finish_blocks(Ctx& c, BlocksPending* bp, unsigned err, bool accept, bo
 
 template <int W, typename WT>
 qx_status run_merges_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
-                            bool* done) {
+                            bool* done, FanHint* hint) {
   *done = false;
   BlocksPending bp;
   QX_TRY((launch_blocks<W, WT>(c, mq, &bp)));
   if (!bp.launched) return QX_OK;
-  unsigned err = 0;
-  if (const qx_status st = sync_read(c, &err, c.sc.err, 4)) {
+  unsigned err = 0, nb = 0;
+  if (const qx_status st = sync_read2(c, &err, c.sc.err, 4, &nb, bp.nblk, 4)) {
     c.al.put(bp.mem);
     c.al.put(bp.out.base);
     return st;
   }
+  if (hint && !err) hint->nblk.store(nb, std::memory_order_relaxed);
   return finish_blocks<W, WT>(c, &bp, err, true, more_after, done);
 }
 
 template <int W, typename WT>
 qx_status run_merges(Ctx& c, const std::vector<const FanQubit*>& mq, bool more_after,
-                     const std::vector<unsigned long long>& gm) {
+                     const std::vector<unsigned long long>& gm, FanHint* hint) {
   if (c.inplace && inplace_candidate(c, mq, gm)) {
     bool done = false;
-    QX_TRY(run_merges_blocks<W, WT>(c, mq, more_after, &done));
+    QX_TRY(run_merges_blocks<W, WT>(c, mq, more_after, &done, hint));
     if (done) return QX_OK;
     QX_TRY(run_merges_inplace<W, WT>(c, mq, more_after, &done));
     if (done) return QX_OK;
@@ -1450,15 +1463,18 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
     for (const FanQubit& f : fs.qs)
       if ((hm >> f.q) & 1) gq.push_back(&f);
     BlocksPending bp;
-    QX_TRY((launch_blocks<W, WT>(c, gq, &bp)));
+    QX_TRY((launch_blocks<W, WT>(c, gq, &bp, hint->nblk.load(std::memory_order_relaxed))));
     if (bp.launched) {
-      unsigned err = 0;
+      unsigned en[2] = {0, 0};
+      QX_TRY_CUDA(cudaMemcpyAsync(&en[1], bp.nblk, 4, cudaMemcpyDeviceToHost, c.al.s));
       if (const qx_status st =
-              sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &err, c.sc.err, 4)) {
+              sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &en[0], c.sc.err, 4)) {
         c.al.put(bp.mem);
         c.al.put(bp.out.base);
         return st;
       }
+      const unsigned err = en[0];
+      if (!err) hint->nblk.store(en[1], std::memory_order_relaxed);
       have_gm = true;
       split_fan(c, fs, gm, &mixed, &mq, &fq);
       const bool held = fq.empty() && mq == gq && inplace_candidate(c, mq, gm);
@@ -1478,7 +1494,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
   if (!mq.empty()) QX_TRY(h2d(c, s.mixed, mixed.data(), G * W * 8));
   // 3. one merge pass per qubit that needs it in some generator
   const uint64_t blocks0 = c.st.block_steps;
-  if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm));
+  if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm, hint));
   if (fq.empty()) {
     if (hint) {
       const bool blocks = c.st.block_steps > blocks0 && W == 1;

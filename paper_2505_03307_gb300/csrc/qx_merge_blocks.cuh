@@ -67,7 +67,8 @@ __device__ __forceinline__ int letter4(uint64_t x, uint64_t z, int q) {
 
 // Per term: the block key (non-isolated letters of the merge wires replaced
 // by the wire's canonical letter, generator packed in), claimed in the block
-// table; the member count of the block (warp-combined) and the block's
+// table (at most plimit probes: a table sized from a guess gives up early);
+// the member count of the block (warp-combined) and the block's
 // expected size.  Everything here is whole-word: the key from letter masks,
 // the size 2^a 3^b from two population counts.  The term's place in its
 // block and its letter code are left to k_block_scatter, which reads the
@@ -75,7 +76,8 @@ __device__ __forceinline__ int letter4(uint64_t x, uint64_t z, int q) {
 template <typename WT>
 __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int n,
                                                      const BlockWires* bw_g, ulonglong2* btab,
-                                                     unsigned long long bcap, unsigned* bcnt,
+                                                     unsigned long long bcap,
+                                                     unsigned long long plimit, unsigned* bcnt,
                                                      unsigned* bexp, unsigned* bslot,
                                                      unsigned* nblk, unsigned* blist,
                                                      unsigned* err) {
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
       const unsigned long long lo = key_lo, hi = key_hi;
       const unsigned size = blk_size;
       unsigned long long p = __umul64hi(slot_hash(lo, hi), bcap);
-      for (unsigned long long probe = 0; probe < bcap; ++probe) {
+      for (unsigned long long probe = 0; probe < plimit; ++probe) {
         // read first (a cached read may be stale only as "empty", which the
         // compare-and-swap corrects; keys never change once written) and
         // compare-and-swap only an empty slot

@@ -111,3 +111,30 @@ def test_random_circuits_repeated(seed):
         res = qx.propagate(plan, gens=(a, b))
         _same(res, _fresh(n, instrs, gens=(a, b)))
         compare_result(res, O.propagate(n, instrs, mode="plan", gens=(a, b), threads=4))
+
+
+def test_block_count_beyond_the_recorded_table():
+    """Blocks of 16 (RZ on 4 of 12 fan-out wires): a run over one generator
+    records 256 blocks, and the block table of the next run, over 28
+    generators (7,168 blocks), is sized from that record.  The claim gives up
+    early, the step is repeated at full size, and the result is unchanged."""
+    import math
+    n, S = 40, list(range(12))
+    rest = [q for q in range(n) if q not in S]
+    rng = np.random.default_rng(11)
+    instrs = [("H", q, -1, 0.0) for q in range(n)]
+    instrs += [("CX", i, q, 0.0) for i in rest for q in S]
+    instrs += [("T", q, -1, 0.0) for q in S]
+    instrs += [("CX", n - 2, n - 1, 0.0)]  # closes the T operator (as in fan_in_heavy)
+    instrs += [("RZ", q, -1, float(rng.uniform(0, 2 * math.pi))) for q in S[:4]]
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    one = qx.propagate(plan, gens=(20, 21))
+    assert one.stats()["block_steps"] == 1
+    many = qx.propagate(plan, gens=(12, 40))
+    st = many.stats()
+    assert st["block_steps"] == 1 and st["guesses_missed"] >= 1
+    _same(many, _fresh(n, instrs, gens=(12, 40)))
+    compare_result(many, O.propagate(n, instrs, mode="plan", gens=(12, 40), threads=8))
+    again = qx.propagate(plan, gens=(12, 40))  # now recorded at full count
+    assert again.stats()["guesses_missed"] == 0
+    _same(again, many)
