@@ -437,9 +437,20 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
   unsigned valid = 0;
   size_t rb, re;
   warp_range(N, &rb, &re);
+  // the next string is loaded before the current one is mapped
+  uint64_t nx[W], nz[W];
+  {
+    const size_t i0 = rb + (threadIdx.x & 31);
+    if (i0 < re) load_term<W>(t, i0, nx, nz);
+  }
   for (size_t i = rb + (threadIdx.x & 31); i < re; i += 32) {
     uint64_t x[W], z[W];
-    load_term<W>(t, i, x, z);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[k] = nx[k];
+      z[k] = nz[k];
+    }
+    if (i + 32 < re) load_term<W>(t, i + 32, nx, nz);
     int e = 0;
 #pragma unroll
     for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
@@ -581,24 +592,33 @@ __global__ void k_fan_mask(TermsT<WT> t, const unsigned long long* n_in, const u
 #pragma unroll
       for (int k = 0; k < W; ++k) acc[a][k] = 0;
   };
+  // the next 32 terms are loaded before the current ones are combined, so a
+  // warp keeps one load in flight behind its shuffles
+  uint32_t ng = 0xffffffffu;
+  uint64_t nx[W], nz[W];
+  auto fetch = [&](size_t base) {
+    const size_t i = base + lane;
+    const bool valid = base < e && i < e;
+    ng = valid ? t.g[i] : 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      nx[k] = valid ? t.x[k * t.cap + i] : 0ull;
+      nz[k] = valid ? t.z[k * t.cap + i] : 0ull;
+    }
+  };
+  fetch(b);
   for (size_t base = b; base < e; base += 32) {
     const size_t i = base + lane;
     const bool valid = i < e;
-    uint32_t g = valid ? t.g[i] : 0xffffffffu;
+    const uint32_t g = ng;
     uint64_t m[3][W];
-    if (valid) {
-      uint64_t x[W], z[W];
-      load_term<W>(t, i, x, z);
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        m[0][k] = x[k] & ~z[k] & nisoX[k];
-        m[1][k] = x[k] & z[k] & nisoY[k];
-        m[2][k] = ~x[k] & z[k] & nisoZ[k];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < W; ++k) m[0][k] = m[1][k] = m[2][k] = 0;
+    for (int k = 0; k < W; ++k) {  // zero for invalid lanes (their x, z are 0)
+      m[0][k] = nx[k] & ~nz[k] & nisoX[k];
+      m[1][k] = nx[k] & nz[k] & nisoY[k];
+      m[2][k] = ~nx[k] & nz[k] & nisoZ[k];
     }
+    fetch(base + 32);
     const unsigned peers = warp_peers(g);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -1362,11 +1382,22 @@ __global__ void k_gen_stats(TermsT<WT> t, const unsigned long long* n_in, int G,
     acc_n = 0;
     acc_sq = 0.0;
   };
+  // the next 32 terms are loaded before the current ones are combined
+  uint32_t ng = 0xffffffffu;
+  double nw = 0.0;
+  auto fetch = [&](size_t base) {
+    const size_t i = base + lane;
+    const bool valid = base < e && i < e;
+    ng = valid ? t.g[i] : 0xffffffffu;
+    nw = valid ? double(t.w[i]) : 0.0;
+  };
+  fetch(b);
   for (size_t base = b; base < e; base += 32) {
     const size_t i = base + lane;
     const bool valid = i < e;
-    const uint32_t g = valid ? t.g[i] : 0xffffffffu;
-    const double w = valid ? double(t.w[i]) : 0.0;
+    const uint32_t g = ng;
+    const double w = nw;
+    fetch(base + 32);
     const unsigned peers = warp_peers(g);
     if (peers == 0xffffffffu) {  // one id in the whole warp
       if (g != cg) {
