@@ -65,6 +65,25 @@ def peaks():
         return 6800.0, "of fallback"
 
 
+# Nominal FP64 rate of the GPU (FP64 is far below the tensor rates on this
+# part): the ceiling of a merge wire, whose bytes stay in L2 between wires.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_view(kernel, d, s0):
+    """The dominant merge-wire class against the FP64 unit: each term of a
+    two-member group takes two fused multiply-adds per wire (4 flops); on the
+    bench workload that is every term but the 32 of the 16 two-term
+    generators.  None for other classes."""
+    if kernel != "merge_blocks" or d["ms"] <= 0:
+        return None
+    flops = 4.0 * s0["final_terms"]
+    t = d["ms"] / max(1, d["launches"]) / 1e3
+    tf = flops / t / 1e12
+    return {"flops_per_launch": flops, "achieved_tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,
+            "peak_source": "nominal (recipe)", "frac": tf / FP64_PEAK_TFLOPS}
+
+
 def ncu_traffic(kernel):
     """Per-launch DRAM bytes of kernel class `kernel` from the committed ncu
     summary, if the capture was taken on the current source of that kernel
@@ -272,7 +291,8 @@ def run_ours(args):
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "alg_bytes_per_launch": d["alg_bytes"] / max(1, d["launches"]),
-                     "avg_launch_ms": d["ms"] / max(1, d["launches"])},
+                     "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                     "fp64": fp64_view(dom, d, s0)},
         "kernel_share": share,
         # per-step device time of each kernel class (CUDA events around its
         # launches); the rest of ms_per_step is time between classes
