@@ -479,7 +479,7 @@ def fp32_bench(qx, plan, flush, steps, fp64_step_ms, warmup=3):
             "l2": "flushed between timed steps"}
 
 
-def large_bench(qx, W, flush, steps, peak, warmup=2):
+def large_bench(qx, W, flush, steps, peak, warmup=3):
     """The HBM-scale configuration: fan_in_deep_n100 (n = 100, 20 RZ on 20
     fan-out qubits spread over 100,000 gates, 80 x 2^20 + 40 = 83,886,120
     final terms, 3.4 GB of FP64 terms).  Device time per propagation (CUDA

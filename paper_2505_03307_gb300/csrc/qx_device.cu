@@ -140,6 +140,7 @@ struct FanHint {
   std::atomic<uint64_t> mq[qx::kMaxWords];
   std::atomic<unsigned long long> total{0};
   std::atomic<unsigned> nblk{0};  // blocks of the last block-ordered run (table size)
+  std::atomic<unsigned> streak{0};  // runs in a row that kept the guess
   FanHint() {
     for (auto& w : mq) w.store(0, std::memory_order_relaxed);
   }
@@ -438,6 +439,11 @@ struct StageBuf {
   }
 };
 thread_local StageBuf t_stage;
+// Pinned host memory for the read-backs a run checks only at its end (the
+// letter masks, output sizes and error words of steps launched on the plan's
+// record), one per host thread.
+constexpr size_t kReadbackBytes = size_t(1) << 20;
+thread_local StageBuf t_readback;
 
 struct qx_result {
   int n = 0, W = 1, G = 0;
@@ -480,6 +486,24 @@ struct Ctx {
   FastTable* ftab = nullptr;  // pooled merge table of the fast path (held for the call)
   bool inplace = true;        // merge wires may run in place (QX_FLAG_NO_INPLACE clears it)
   size_t stage_off = 0;       // bytes of t_stage queued since the last stream sync
+  // Steps launched on the plan's record whose check waits for the end of the
+  // run (no host round trip of their own); a failed check repeats the run with
+  // every step checked at once (defer = false).
+  struct Deferred {
+    int kind = 0;  // kHintExpand or kHintBlocks
+    FanHint* hint = nullptr;
+    const FanStep* fs = nullptr;
+    std::vector<const FanQubit*> gq;  // the recorded merge wires (blocks)
+    unsigned long long expect = 0;    // the recorded output size (expansion)
+    const unsigned long long* gm = nullptr;  // pinned: the step's letter masks
+    const unsigned long long* total = nullptr;
+    const unsigned* err = nullptr;
+    const unsigned* nblk = nullptr;
+  };
+  bool defer = false;
+  bool retry = false;  // set by a run whose deferred checks failed
+  std::vector<Deferred> deferred;
+  size_t rb_off = 0;
   Ctx() = default;
   Ctx(const Ctx&) = delete;
   Ctx& operator=(const Ctx&) = delete;
@@ -505,6 +529,22 @@ qx_status sync_read(Ctx& c, void* host, const void* dev, size_t bytes) {
   c.stage_off = 0;
   c.st.host_syncs++;
   return QX_OK;
+}
+
+// Pinned space for a read-back checked at the end of the run, or nullptr.
+void* rb_take(Ctx& c, size_t bytes) {
+  if (!t_readback.tried) {
+    t_readback.tried = true;
+    if (cudaMallocHost(reinterpret_cast<void**>(&t_readback.p), kReadbackBytes) != cudaSuccess) {
+      cudaGetLastError();
+      t_readback.p = nullptr;
+    }
+  }
+  const size_t need = (bytes + 63) & ~size_t(63);
+  if (!t_readback.p || c.rb_off + need > kReadbackBytes) return nullptr;
+  void* r = t_readback.p + c.rb_off;
+  c.rb_off += need;
+  return r;
 }
 
 // Two device-to-host reads and one synchronisation.
@@ -1430,6 +1470,28 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       ExpPending ep;
       qx_status st = exp_count<W, WT>(c, all, &ep);
       if (st == QX_OK) st = exp_emit<W, WT>(c, &ep, cap);
+      // a guess that held in the last runs: no read-back now, the check
+      // happens at the end of the run (the output is made harmless first
+      // where its size differs from the guess)
+      if (st == QX_OK && c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
+        auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
+        auto* rt = static_cast<unsigned long long*>(rb_take(c, 8));
+        if (rg && rt) {
+          k_fill_tail<W, WT><<<grid_for(cap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+              ep.out.view<WT>(), s.ncnt + 2, cap);
+          QX_TRY_CUDA(cudaMemcpyAsync(rg, s.gmask, gm.size() * 8, cudaMemcpyDeviceToHost, c.al.s));
+          QX_TRY_CUDA(cudaMemcpyAsync(rt, s.ncnt + 2, 8, cudaMemcpyDeviceToHost, c.al.s));
+          Ctx::Deferred d;
+          d.kind = kHintExpand;
+          d.hint = hint;
+          d.fs = &fs;
+          d.expect = cap;
+          d.gm = rg;
+          d.total = rt;
+          c.deferred.push_back(std::move(d));
+          return exp_accept<W, WT>(c, &ep, cap);
+        }
+      }
       unsigned long long total = 0;
       if (st == QX_OK) st = sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &total, s.ncnt + 2, 8);
       if (st != QX_OK) {
@@ -1451,9 +1513,12 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
           }
         }
         hint->total.store(total, std::memory_order_relaxed);
+        if (total == cap) hint->streak.fetch_add(1, std::memory_order_relaxed);
+        else hint->streak.store(0, std::memory_order_relaxed);
         c.st.guesses_held++;
         return exp_accept<W, WT>(c, &ep, total);
       }
+      hint->streak.store(0, std::memory_order_relaxed);
       c.st.guesses_missed++;
       exp_release(c, &ep);
     }
@@ -1464,6 +1529,30 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       if ((hm >> f.q) & 1) gq.push_back(&f);
     BlocksPending bp;
     QX_TRY((launch_blocks<W, WT>(c, gq, &bp, hint->nblk.load(std::memory_order_relaxed))));
+    if (bp.launched && c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
+      auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
+      auto* re = static_cast<unsigned*>(rb_take(c, 8));
+      if (rg && re) {  // checked at the end of the run (see the expansion above)
+        k_zero_if_err<W, WT><<<grid_for(bp.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+            bp.out.view<WT>(), bp.N, c.sc.err);
+        QX_TRY_CUDA(cudaMemcpyAsync(rg, s.gmask, gm.size() * 8, cudaMemcpyDeviceToHost, c.al.s));
+        QX_TRY_CUDA(cudaMemcpyAsync(re, c.sc.err, 4, cudaMemcpyDeviceToHost, c.al.s));
+        QX_TRY_CUDA(cudaMemcpyAsync(re + 1, bp.nblk, 4, cudaMemcpyDeviceToHost, c.al.s));
+        // a stale error word must not fail a later step: it is in re now
+        QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+        Ctx::Deferred d;
+        d.kind = kHintBlocks;
+        d.hint = hint;
+        d.fs = &fs;
+        d.gq = gq;
+        d.gm = rg;
+        d.err = re;
+        d.nblk = re + 1;
+        c.deferred.push_back(std::move(d));
+        bool done = false;
+        return finish_blocks<W, WT>(c, &bp, 0, true, false, &done);
+      }
+    }
     if (bp.launched) {
       unsigned en[2] = {0, 0};
       QX_TRY_CUDA(cudaMemcpyAsync(&en[1], bp.nblk, 4, cudaMemcpyDeviceToHost, c.al.s));
@@ -1481,9 +1570,11 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       bool done = false;
       QX_TRY((finish_blocks<W, WT>(c, &bp, err, held, false, &done)));
       if (done) {
+        hint->streak.fetch_add(1, std::memory_order_relaxed);
         c.st.guesses_held++;
         return QX_OK;
       }
+      hint->streak.store(0, std::memory_order_relaxed);
       c.st.guesses_missed++;
     }
   }
@@ -1694,6 +1785,31 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     delete r;
     return fail(QX_ECUDA, std::string("propagation failed: ") + cudaGetErrorString(se));
   }
+  // the checks of the steps launched on the plan's record without a read-back
+  bool held = true;
+  for (const Ctx::Deferred& d : c.deferred) {
+    std::vector<unsigned long long> gmv(d.gm, d.gm + G * 3 * W);
+    std::vector<uint64_t> mixed;
+    std::vector<const FanQubit*> mq, fq;
+    split_fan(c, *d.fs, gmv, &mixed, &mq, &fq);
+    const bool ok = d.kind == kHintExpand
+                        ? mq.empty() && *d.total == d.expect
+                        : fq.empty() && mq == d.gq && inplace_candidate(c, mq, gmv) && *d.err == 0;
+    if (ok) {
+      d.hint->streak.fetch_add(1, std::memory_order_relaxed);
+      if (d.kind == kHintBlocks) d.hint->nblk.store(*d.nblk, std::memory_order_relaxed);
+      c.st.guesses_held++;
+    } else {
+      d.hint->streak.store(0, std::memory_order_relaxed);
+      d.hint->kind.store(kHintNone, std::memory_order_relaxed);
+      held = false;
+    }
+  }
+  if (!held) {  // the caller repeats the run, every step checked on the spot
+    delete r;
+    c.retry = true;
+    return QX_OK;
+  }
   c.tm.resolve(&c.st);
   c.st.final_terms = c.N;
   c.st.K = p->K;
@@ -1775,12 +1891,35 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   qx_status s;
   if (from && (from->n != p->n || from->wtb != (opts.precision == 32 ? 4 : 8)))
     return fail(QX_EINVAL, "the initial state must have the plan's qubit count and precision");
-  if (p->W == 1)
-    s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, from, out)
-                             : propagate_impl<1, double>(c, ix, iz, iw, gen_begin, from, out);
-  else
-    s = opts.precision == 32 ? propagate_impl<2, float>(c, ix, iz, iw, gen_begin, from, out)
-                             : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, from, out);
+  // Steps launched on the plan's record may leave their check to the end of
+  // the run (not with pruning, whose compaction reads counts mid-step).  A run
+  // whose deferred checks fail is repeated once with every check on the spot.
+  c.defer = opts.eps == 0.0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (p->W == 1)
+      s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, from, out)
+                               : propagate_impl<1, double>(c, ix, iz, iw, gen_begin, from, out);
+    else
+      s = opts.precision == 32 ? propagate_impl<2, float>(c, ix, iz, iw, gen_begin, from, out)
+                               : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, from, out);
+    if (s != QX_OK || !c.retry) break;
+    // release the first attempt's buffers (its stream work is complete)
+    const uint64_t missed = c.st.guesses_missed + c.deferred.size();
+    c.al.put(c.cur.base);
+    c.cur = TermBuf();
+    free_scratch(c);
+    c.st = qx_prop_stats{};
+    c.st.guesses_missed = missed;
+    c.tm.rec.clear();
+    c.tm.used = 0;
+    c.deferred.clear();
+    c.rb_off = 0;
+    c.stage_off = 0;
+    c.N = 0;
+    c.cslot = 0;
+    c.retry = false;
+    c.defer = false;
+  }
   if (s != QX_OK) {
     const std::string msg = qx_last_error();
     c.al.put(c.cur.base);

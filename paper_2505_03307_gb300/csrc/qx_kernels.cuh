@@ -1074,6 +1074,45 @@ static __global__ void k_expand_tiles(const unsigned long long* offs, const unsi
   }
 }
 
+// Harmless terms (the identity string, generator 0, weight 0) in [from, cap)
+// of an output whose size was guessed: from = *total_d where the expansion
+// wrote fewer children than the guess, 0 where it wrote none (*total_d >
+// cap).  A run whose guess is checked only at its end is then repeated, but
+// until that check every later kernel reads in-bounds generator ids.
+template <int W, typename WT = double>
+__global__ void k_fill_tail(TermsT<WT> t, const unsigned long long* total_d,
+                            unsigned long long cap) {
+  const unsigned long long total = *total_d;
+  const unsigned long long from = total > cap ? 0ull : total;
+  for (unsigned long long i = from + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       i < cap; i += (unsigned long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      t.x[k * t.cap + i] = 0ull;
+      t.z[k * t.cap + i] = 0ull;
+    }
+    t.w[i] = WT(0);
+    t.g[i] = 0u;
+  }
+}
+
+// The same over a whole output of n terms when *err is set (a block-ordered
+// step whose kernels did nothing).
+template <int W, typename WT = double>
+__global__ void k_zero_if_err(TermsT<WT> t, size_t n, const unsigned* err) {
+  if (!*err) return;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      t.x[k * t.cap + i] = 0ull;
+      t.z[k * t.cap + i] = 0ull;
+    }
+    t.w[i] = WT(0);
+    t.g[i] = 0u;
+  }
+}
+
 // Dynamic shared memory of k_expand_emit: the fan-out tables, the parent
 // offsets of a tile and (FP64) the product tree of a single-parent tile.
 template <int W, typename WT>

@@ -138,3 +138,46 @@ def test_block_count_beyond_the_recorded_table():
     again = qx.propagate(plan, gens=(12, 40))  # now recorded at full count
     assert again.stats()["guesses_missed"] == 0
     _same(again, many)
+
+
+def test_checks_at_the_end_of_the_run():
+    """After two runs that kept a step's guess, the next run launches the step
+    without any read-back and checks it at the end of the run (one host
+    round trip in all); a run whose end-of-run check fails is repeated with
+    every check on the spot, and its result equals a fresh plan's."""
+    n, instrs = W.fan_in_heavy(6, n=20, n_s=8, total=500, tail=80)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    runs = [qx.propagate(plan) for _ in range(4)]
+    syncs = [r.stats()["host_syncs"] for r in runs]
+    assert syncs[1] == syncs[0] - 2 and syncs[2] == syncs[1]
+    assert syncs[3] == 1  # both fan-out steps checked at the end
+    assert runs[3].stats()["guesses_held"] == 2
+    for r in runs[1:]:
+        _same(r, runs[0])
+    # other generators: the recorded sizes and merge wires are wrong
+    other = qx.propagate(plan, gens=(0, 6))
+    st = other.stats()
+    assert st["guesses_missed"] >= 1
+    _same(other, _fresh(n, instrs, gens=(0, 6)))
+    compare_result(other, O.propagate(n, instrs, mode="plan", gens=(0, 6), threads=8))
+    # FP32 with the records of FP64 runs, then FP64 again
+    for _ in range(3):
+        f32 = qx.propagate(plan, precision=32)
+    _same(f32, _fresh(n, instrs, precision=32))
+    for _ in range(3):
+        again = qx.propagate(plan)
+    _same(again, runs[0])
+
+
+def test_checks_at_the_end_on_the_large_workload_shape():
+    """A chain of expansions (one fan-out qubit per step, 12 steps) where every
+    step is checked at the end of the run after two runs; then a generator
+    range that changes every output size."""
+    n, instrs = W.fan_in_deep(2, n=40, n_s=12, total=3000)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    a = [qx.propagate(plan) for _ in range(4)][-1]
+    assert a.stats()["host_syncs"] == 1
+    _same(a, _fresh(n, instrs))
+    b = qx.propagate(plan, gens=(12, 20))
+    _same(b, _fresh(n, instrs, gens=(12, 20)))
+    compare_result(b, O.propagate(n, instrs, mode="plan", gens=(12, 20), threads=8))
