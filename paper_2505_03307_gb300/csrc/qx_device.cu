@@ -1105,13 +1105,18 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
                                                       bexp, bslot, nblk, blist, c.sc.err);
     // offsets: from the list of blocks when it is short, else (dn[0] = bcap)
     // from the sweep of the table and its scan, which otherwise do nothing
+    // With a guessed table of at most 4 x 256 blocks the list always
+    // suffices unless the guess was wrong (which fails the step): no sweep.
+    const bool sweep = !(nblk_guess && nblk_guess <= kBlockListMax / 4);
     k_block_list<<<1, kBlockListMax, 0, c.al.s>>>(nblk, blist, bcnt, bexp, bcap, boff, dn,
-                                                  c.sc.err);
-    k_block_sizes<<<grid_for(bcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(btab, dn, bcnt,
-                                                                             bexp, boff, c.sc.err);
-    k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
-    k_scan_sums<<<1, 1024, 0, c.al.s>>>(boff + bcap, ntiles, dn + 1);
-    k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
+                                                  c.sc.err, sweep ? 1 : 0);
+    if (sweep) {
+      k_block_sizes<<<grid_for(bcap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(btab, dn, bcnt,
+                                                                               bexp, boff, c.sc.err);
+      k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
+      k_scan_sums<<<1, 1024, 0, c.al.s>>>(boff + bcap, ntiles, dn + 1);
+      k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(boff, dn, boff + bcap);
+    }
     QX_TRY_CUDA(cudaGetLastError());
     // No host round trip here: every block is complete exactly when the error
     // word stayed 0 (then the sizes add up to N), and the kernels below do
@@ -1120,7 +1125,7 @@ qx_status launch_blocks(Ctx& c, const std::vector<const FanQubit*>& mq, BlocksPe
     const auto ov = out.view<WT>();
     k_block_scatter<WT><<<grid, kThreads, 0, c.al.s>>>(view, N, d_bw, bslot, boff, ov, lcode2,
                                                         ov.w, c.sc.err);
-    c.end(KC_BLOCK_SETUP, 7, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
+    c.end(KC_BLOCK_SETUP, sweep ? 7 : 3, uint64_t(N) * (2 * (16 * W + 4 + sizeof(WT)) + 24));
     const WT* src = ov.w;
     for (int j = 0; j < m; ++j) {
       WT* dst = (j & 1) ? ov.w : wtmp;
@@ -1364,6 +1369,14 @@ qx_status exp_count(Ctx& c, const std::vector<const FanQubit*>& fq, ExpPending* 
   ep->offs = static_cast<unsigned long long*>(c.al.get((c.N + ntiles + 1) * 8));
   if (!ep->offs) return fail(QX_ENOMEM, "device allocation of the expansion offsets failed");
   unsigned long long* tsum = ep->offs + c.N;
+  if (c.N <= size_t(kScanTile)) {  // one block counts and scans
+    c.begin(KC_COUNT);
+    k_expand_count_small<W, WT><<<1, kScanThreads, ep->nq * sizeof(FanQ), c.al.s>>>(
+        c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, ep->nq, ep->offs, s.ncnt + 2);
+    c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * W + sizeof(WT)));
+    QX_TRY_CUDA(cudaGetLastError());
+    return QX_OK;
+  }
   c.begin(KC_COUNT);
   k_expand_count<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, ep->nq * sizeof(FanQ),
                           c.al.s>>>(c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, ep->nq, ep->offs);

@@ -995,6 +995,61 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(unsigned lon
   if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = run;
 }
 
+// Counts and exclusive scan of at most kScanTile parents in one block (small
+// steps, where three scan launches would be mostly launch latency): offs[i]
+// and the total in *total.
+template <int W, typename WT = double>
+__global__ void __launch_bounds__(kScanThreads) k_expand_count_small(
+    TermsT<WT> t, const unsigned long long* n_in, const FanQ* fq_g, int nq,
+    unsigned long long* offs, unsigned long long* total) {
+  extern __shared__ FanQ s_fq[];
+  __shared__ unsigned long long s[kScanThreads / 32 + 1];
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  __syncthreads();
+  const size_t N = *n_in;
+  unsigned long long v[kScanItems];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const size_t i = size_t(threadIdx.x) * kScanItems + k;
+    v[k] = 0;
+    if (i < N) {
+      uint64_t x[W], z[W];
+      load_term<W>(t, i, x, z);
+      v[k] = child_count<W>(x, z, s_fq, nq);
+    }
+    sum += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) s[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    constexpr int NW = kScanThreads / 32;
+    unsigned long long w = lane < NW ? s[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += o;
+    }
+    if (lane < NW) s[lane] = w;
+    if (lane == NW - 1) *total = w;
+  }
+  __syncthreads();
+  unsigned long long run = (wid ? s[wid - 1] : 0) + inc - sum;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const size_t i = size_t(threadIdx.x) * kScanItems + k;
+    if (i < N) offs[i] = run;
+    run += v[k];
+  }
+}
+
 static __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* sums, size_t ntiles,
                                                     unsigned long long* total) {
   __shared__ unsigned long long s[33];

@@ -172,17 +172,23 @@ __global__ void __launch_bounds__(256) k_block_claim(TermsT<WT> t, size_t N, int
 // number of listed slots below its own, and the offsets are the exclusive scan
 // of the sizes in rank order.  A block whose count differs from its size is
 // incomplete.  dn[0] receives the element count of the table sweep that
-// follows: 0 when the list sufficed, the table size otherwise.
+// follows: 0 when the list sufficed, the table size otherwise; when the caller
+// launched no sweep (sweep == 0), more blocks than the list holds fail the
+// step instead.
 static __global__ void __launch_bounds__(kBlockListMax) k_block_list(
     const unsigned* nblk, const unsigned* blist, const unsigned* bcnt, const unsigned* bexp,
-    unsigned long long bcap, unsigned long long* boff, unsigned long long* dn, unsigned* err) {
+    unsigned long long bcap, unsigned long long* boff, unsigned long long* dn, unsigned* err,
+    int sweep) {
   __shared__ unsigned s_slot[kBlockListMax];
   __shared__ unsigned long long s_size[kBlockListMax];
   __shared__ unsigned long long s_warp[kBlockListMax / 32];
   const unsigned nb = *nblk;
   const unsigned t = threadIdx.x;
   if (nb > unsigned(kBlockListMax)) {
-    if (t == 0) dn[0] = bcap;
+    if (t == 0) {
+      dn[0] = bcap;
+      if (!sweep) atomicOr(err, kErrNotClosed);
+    }
     return;
   }
   if (t == 0) dn[0] = 0;
