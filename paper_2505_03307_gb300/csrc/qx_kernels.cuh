@@ -1004,20 +1004,33 @@ __global__ void __launch_bounds__(kScanThreads) k_expand_count_small(
     unsigned long long* offs, unsigned long long* total) {
   extern __shared__ FanQ s_fq[];
   __shared__ unsigned long long s[kScanThreads / 32 + 1];
-  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  __shared__ unsigned long long s_cnt[kScanTile];
+  {  // the tables word by word over all threads
+    static_assert(sizeof(FanQ) % 4 == 0, "FanQ is copied in 4-byte words");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(fq_g);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_fq);
+    const int nw = nq * int(sizeof(FanQ) / 4);
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+  }
   __syncthreads();
   const size_t N = *n_in;
+  // counts with one term per thread and pass (independent loads), then each
+  // thread scans its kScanItems consecutive counts
+  for (size_t i = threadIdx.x; i < size_t(kScanTile); i += blockDim.x) {
+    unsigned long long cnt = 0;
+    if (i < N) {
+      uint64_t x[W], z[W];
+      load_term<W>(t, i, x, z);
+      cnt = child_count<W>(x, z, s_fq, nq);
+    }
+    s_cnt[i] = cnt;
+  }
+  __syncthreads();
   unsigned long long v[kScanItems];
   unsigned long long sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    const size_t i = size_t(threadIdx.x) * kScanItems + k;
-    v[k] = 0;
-    if (i < N) {
-      uint64_t x[W], z[W];
-      load_term<W>(t, i, x, z);
-      v[k] = child_count<W>(x, z, s_fq, nq);
-    }
+    v[k] = s_cnt[threadIdx.x * kScanItems + k];
     sum += v[k];
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
