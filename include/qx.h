@@ -222,7 +222,16 @@ qx_status qx_plan_clifford_apply(const qx_plan* p, size_t pass, uint64_t* x, uin
  * The result owns its device arrays (freed by qx_free_result with the same
  * allocator).  Returns QX_EBUDGET / QX_ECAP before allocating a step whose
  * counted size exceeds the limits; the plan stays valid either way.
- * Result generator g (0 <= g < gen_end - gen_begin) is Z_{gen_begin + g}. */
+ * Result generator g (0 <= g < gen_end - gen_begin) is Z_{gen_begin + g}.
+ *
+ * A plan keeps, per fan-out step, what its last propagation did (a pure
+ * expansion and its size, or block-ordered in-place merges and their block
+ * count) and launches the next propagation's step on that record before
+ * reading anything back; steps whose record held twice in a row are checked
+ * only at the end of the call, which repeats itself once with every check on
+ * the spot if one fails.  Results never depend on the record (a wrong one
+ * costs time only: qx_prop_stats.guesses_missed); plans may be shared between
+ * threads and streams (the record is updated atomically). */
 qx_status qx_propagate(const qx_plan* p, const qx_prop_opts* o, qx_result** out);
 
 /* As qx_propagate, but the initial generators are `ngen` single terms given
