@@ -125,26 +125,23 @@ void set_pool_threshold() {
 
 }  // namespace
 
-// Device copy of the plan: Clifford passes (gate lists or chunk tables) and
-// the fan-out tables, uploaded once per plan and device.
 // What the last run of a fan-out step of this plan did, as the guess the next
 // run launches on before the per-generator letter masks come back: an
 // expansion over every fan-out qubit (with its output size), or block-ordered
-// merges over a set of wires.  The device results and the masks decide
-// whether the guess held; a wrong guess costs only the discarded launches.
-// Plans may be shared between threads, so the fields are atomics (a torn
-// guess is just a wrong one).
+// merges over every fan-out qubit (with the block count).  The masks (for an
+// expansion) and the device results decide whether the guess held; a wrong
+// guess costs only the discarded launches.  Plans may be shared between
+// threads, so the fields are atomics (a torn guess is just a wrong one).
 enum : int { kHintNone = 0, kHintExpand = 1, kHintBlocks = 2 };
 struct FanHint {
   std::atomic<int> kind{kHintNone};
-  std::atomic<uint64_t> mq[qx::kMaxWords];
   std::atomic<unsigned long long> total{0};
   std::atomic<unsigned> nblk{0};  // blocks of the last block-ordered run (table size)
   std::atomic<unsigned> streak{0};  // runs in a row that kept the guess
-  FanHint() {
-    for (auto& w : mq) w.store(0, std::memory_order_relaxed);
-  }
 };
+
+// Device copy of the plan: Clifford passes (gate lists or chunk tables) and
+// the fan-out tables, uploaded once per plan and device.
 
 struct qx_plan_device {
   int device = -1;
@@ -493,7 +490,6 @@ struct Ctx {
     int kind = 0;  // kHintExpand or kHintBlocks
     FanHint* hint = nullptr;
     const FanStep* fs = nullptr;
-    std::vector<const FanQubit*> gq;  // the recorded merge wires (blocks)
     unsigned long long expect = 0;    // the recorded output size (expansion)
     const unsigned long long* gm = nullptr;  // pinned: the step's letter masks
     const unsigned long long* total = nullptr;
@@ -1610,12 +1606,8 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
   if (!mq.empty()) QX_TRY(run_merges<W, WT>(c, mq, !fq.empty(), gm, hint));
   if (fq.empty()) {
     if (hint) {
+      // every fan-out wire merged in block order: the next run tries that
       const bool blocks = c.st.block_steps > blocks0 && W == 1;
-      if (blocks) {
-        uint64_t m = 0;
-        for (const FanQubit* f : mq) m |= 1ull << (f->q & 63);
-        hint->mq[0].store(m, std::memory_order_relaxed);
-      }
       hint->kind.store(blocks ? kHintBlocks : kHintNone, std::memory_order_relaxed);
     }
     return QX_OK;
