@@ -1493,58 +1493,69 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
       for (const FanQubit& f : fs.qs) all.push_back(&f);
       ExpPending ep;
       qx_status st = exp_count<W, WT>(c, all, &ep);
-      if (st == QX_OK) st = exp_emit<W, WT>(c, &ep, cap);
-      // a guess that held in the last runs: no read-back now, the check
-      // happens at the end of the run (the output is made harmless first
-      // where its size differs from the guess)
-      if (st == QX_OK && c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
-        auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
-        auto* rt = static_cast<unsigned long long*>(rb_take(c, 8));
-        if (rg && rt) {
-          k_fill_tail<W, WT><<<grid_for(cap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-              ep.out.view<WT>(), s.ncnt + 2, cap);
-          QX_TRY_CUDA(cudaMemcpyAsync(rg, s.gmask, gm.size() * 8, cudaMemcpyDeviceToHost, c.al.s));
-          QX_TRY_CUDA(cudaMemcpyAsync(rt, s.ncnt + 2, 8, cudaMemcpyDeviceToHost, c.al.s));
-          Ctx::Deferred d;
-          d.kind = kHintExpand;
-          d.hint = hint;
-          d.fs = &fs;
-          d.expect = cap;
-          d.gm = rg;
-          d.total = rt;
-          c.deferred.push_back(std::move(d));
-          return exp_accept<W, WT>(c, &ep, cap);
-        }
-      }
-      unsigned long long total = 0;
-      if (st == QX_OK) st = sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &total, s.ncnt + 2, 8);
       if (st != QX_OK) {
         exp_release(c, &ep);
         return st;
       }
-      have_gm = true;
-      split_fan(c, fs, gm, &mixed, &mq, &fq);
-      if (mq.empty() && limits_ok(c, total)) {  // the guess held
-        if (total > cap) {  // more children than last time: emit again at full size
-          c.al.put(ep.tiles);
-          c.al.put(ep.out.base);
-          ep.tiles = nullptr;
-          ep.out = TermBuf();
-          st = exp_emit<W, WT>(c, &ep, total);
-          if (st != QX_OK) {
-            exp_release(c, &ep);
-            return st;
+      if (exp_emit<W, WT>(c, &ep, cap) != QX_OK) {
+        // the recorded size does not fit now (another generator range, a
+        // tighter device): no guess, the ordinary path counts first
+        exp_release(c, &ep);
+        clear_error();
+        cudaGetLastError();
+      } else {
+        // a guess that held in the last runs: no read-back now, the check
+        // happens at the end of the run (the output is made harmless first
+        // where its size differs from the guess)
+        if (st == QX_OK && c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
+          auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
+          auto* rt = static_cast<unsigned long long*>(rb_take(c, 8));
+          if (rg && rt) {
+            k_fill_tail<W, WT><<<grid_for(cap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+                ep.out.view<WT>(), s.ncnt + 2, cap);
+            QX_TRY_CUDA(cudaMemcpyAsync(rg, s.gmask, gm.size() * 8, cudaMemcpyDeviceToHost, c.al.s));
+            QX_TRY_CUDA(cudaMemcpyAsync(rt, s.ncnt + 2, 8, cudaMemcpyDeviceToHost, c.al.s));
+            Ctx::Deferred d;
+            d.kind = kHintExpand;
+            d.hint = hint;
+            d.fs = &fs;
+            d.expect = cap;
+            d.gm = rg;
+            d.total = rt;
+            c.deferred.push_back(std::move(d));
+            return exp_accept<W, WT>(c, &ep, cap);
           }
         }
-        hint->total.store(total, std::memory_order_relaxed);
-        if (total == cap) hint->streak.fetch_add(1, std::memory_order_relaxed);
-        else hint->streak.store(0, std::memory_order_relaxed);
-        c.st.guesses_held++;
-        return exp_accept<W, WT>(c, &ep, total);
+        unsigned long long total = 0;
+        if (st == QX_OK) st = sync_read2(c, gm.data(), s.gmask, gm.size() * 8, &total, s.ncnt + 2, 8);
+        if (st != QX_OK) {
+          exp_release(c, &ep);
+          return st;
+        }
+        have_gm = true;
+        split_fan(c, fs, gm, &mixed, &mq, &fq);
+        if (mq.empty() && limits_ok(c, total)) {  // the guess held
+          if (total > cap) {  // more children than last time: emit again at full size
+            c.al.put(ep.tiles);
+            c.al.put(ep.out.base);
+            ep.tiles = nullptr;
+            ep.out = TermBuf();
+            st = exp_emit<W, WT>(c, &ep, total);
+            if (st != QX_OK) {
+              exp_release(c, &ep);
+              return st;
+            }
+          }
+          hint->total.store(total, std::memory_order_relaxed);
+          if (total == cap) hint->streak.fetch_add(1, std::memory_order_relaxed);
+          else hint->streak.store(0, std::memory_order_relaxed);
+          c.st.guesses_held++;
+          return exp_accept<W, WT>(c, &ep, total);
+        }
+        hint->streak.store(0, std::memory_order_relaxed);
+        c.st.guesses_missed++;
+        exp_release(c, &ep);
       }
-      hint->streak.store(0, std::memory_order_relaxed);
-      c.st.guesses_missed++;
-      exp_release(c, &ep);
     }
   } else if (guess == kHintBlocks && c.inplace && blocks_fit(c)) {
     // Every fan-out wire merged in block order last time.  The device decides
