@@ -146,3 +146,17 @@ def test_propagate_without_gpu_fails_loudly():
     with pytest.raises(qx.QxError) as e:
         qx.propagate(plan)
     assert e.value.name in ("QX_EUNSUPPORTED", "QX_ECUDA")
+
+
+def test_records_and_tuples_give_the_same_plan():
+    """qx_instr records built from column arrays and the tuple list describe
+    the same circuit: the same operators, tables and Clifford passes."""
+    n, instrs = W.fan_in_heavy(1, n=20, n_s=8, total=500, tail=80)
+    cols = list(zip(*instrs))
+    rec = qx.instr_records(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]))
+    a = qx.group_ops(qx.load_circuit(n, instrs))
+    b = qx.group_ops(qx.load_circuit_records(n, rec))
+    assert a.info() == b.info() and a.ops() == b.ops()
+    for op, kind in enumerate(a.ops()):
+        if kind == "U":
+            assert np.array_equal(a.lut(op), b.lut(op))
