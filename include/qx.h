@@ -426,17 +426,21 @@ void qx_server_destroy(qx_server* s);
  * and outputs are device memory in planar layout: word k of string i is at
  * x[k * n_in + i] (input) and out_x[k * out_cap + i] (output), W = ceil(n/64)
  * words; weights and generator ids one per term.  Input strings must be
- * unique within their generator and generator ids must be < ngen.  Output
- * order is unspecified; *n_out (host) receives the number of output terms.
+ * unique within their generator.  Output order is unspecified; *n_out (host)
+ * receives the number of output terms.
  *
  * Limits: n_in <= 262144 terms, ngen <= 4096, otherwise QX_EINVAL before any
- * device work; QX_ECAP when out_cap is too small (at most 3 * n_in outputs).
+ * device work; a generator id >= ngen is found on the device before any
+ * merge kernel reads it and gives QX_EINVAL with no output written;
+ * QX_ECAP when out_cap is too small (at most 3 * n_in outputs).
  * The first call on a device (with that device current) looks up and clears
  * the scratch and synchronises the device; make that first call before any
  * other work that must not be synchronised.  Every call on a device shares
- * the same scratch and leaves its contents behind (later calls ignore them);
- * calls whose device work overlaps (different streams or threads) race on
- * the scratch and must be serialised by the caller.  The call synchronises
+ * the same scratch array and leaves its contents behind (later calls ignore
+ * them).  Calls from one process are serialised by a lock inside the library
+ * that is held until the call's stream has finished its work; device work of
+ * another process, or work the caller queues on the scratch's device
+ * outside this call, does not touch the array.  The call synchronises
  * `stream` (a cudaStream_t, NULL for the default stream) before returning. */
 qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const uint64_t* x,
                                 const uint64_t* z, const double* w, const uint32_t* gen, int q,

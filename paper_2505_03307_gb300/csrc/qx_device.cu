@@ -1497,12 +1497,17 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
         exp_release(c, &ep);
         return st;
       }
-      if (exp_emit<W, WT>(c, &ep, cap) != QX_OK) {
-        // the recorded size does not fit now (another generator range, a
-        // tighter device): no guess, the ordinary path counts first
+      const qx_status est = exp_emit<W, WT>(c, &ep, cap);
+      if (est != QX_OK) {
         exp_release(c, &ep);
+        // only an allocation at the recorded size that fails now (another
+        // generator range, a fuller device) falls back: no guess, the
+        // ordinary path counts first; any other failure is the caller's
+        if (est != QX_ENOMEM) return est;
         clear_error();
         cudaGetLastError();
+        hint->streak.store(0, std::memory_order_relaxed);
+        c.st.guesses_missed++;
       } else {
         // a guess that held in the last runs: no read-back now, the check
         // happens at the end of the run (the output is made harmless first

@@ -412,6 +412,140 @@ struct PassMasks {
 //   one generator that differ only on fan-out wires share most parts);
 // * the parts combine in order: the phase gains 2 |z_acc & x_part| (mod 4),
 //   which equals the sum of the per-chunk terms mod 2.
+//
+// CliffCache holds a lane's part products; clifford_table_map maps one string
+// in place through the chunk tables in shared memory and returns whether its
+// weight changes sign.  k_clifford_table applies it in place; the fused
+// expansion applies it to each parent before emitting its children.
+template <int W>
+struct CliffCache {
+  static constexpr int P = clifford_parts<W>();
+  uint64_t kx[P][W], kz[P][W], vx[P][W], vz[P][W];
+  int ve[P];
+  unsigned valid = 0;
+};
+
+template <int W, int CB>
+__device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, const uint64_t* s_tab,
+                                                   const uint8_t* s_e, int chunks, uint64_t live,
+                                                   const PassMasks& pmk, CliffCache<W>& cc) {
+  constexpr int E = 1 << (2 * CB);
+  constexpr int P = clifford_parts<W>();
+  constexpr uint32_t M = (1u << CB) - 1;
+  int e = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
+  uint64_t ax[W], az[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    ax[k] = 0;
+    az[k] = 0;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    bool same = (cc.valid >> p) & 1;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      same = same && cc.kx[p][k] == (x[k] & pmk.part[p][k]) && cc.kz[p][k] == (z[k] & pmk.part[p][k]);
+    if (!same) {  // the product of this part's chunks
+      uint64_t px[W], pz[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        px[k] = 0;
+        pz[k] = 0;
+        cc.kx[p][k] = x[k] & pmk.part[p][k];
+        cc.kz[p][k] = z[k] & pmk.part[p][k];
+      }
+      int pe = 0;
+      for (int c = p * chunks / P; c < (p + 1) * chunks / P; ++c) {
+        if (!((live >> c) & 1)) continue;
+        const int lo = c * CB, k = lo >> 6, off = lo & 63;
+        // for CB = 3 the chunk across the word boundary takes bits of both
+        // words by selects, not by a run-time index (which would put the
+        // string in local memory)
+        const uint64_t xw = (W == 1 || k == 0) ? x[0] : x[W - 1];
+        const uint64_t zw = (W == 1 || k == 0) ? z[0] : z[W - 1];
+        uint32_t xb, zb;
+        if (CB == 4 || off + CB <= 64) {
+          xb = uint32_t(xw >> off) & M;
+          zb = uint32_t(zw >> off) & M;
+        } else {  // k == 0 < W - 1
+          xb = uint32_t((xw >> off) | (W > 1 ? (x[W - 1] << (64 - off)) : 0)) & M;
+          zb = uint32_t((zw >> off) | (W > 1 ? (z[W - 1] << (64 - off)) : 0)) & M;
+        }
+        const uint32_t idx = xb | (zb << CB);
+        if (!idx) continue;
+        // the entry (x words, then z words) in 16-byte loads
+        const ulonglong2* ent =
+            reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
+        uint64_t ex[W], ez[W];
+        if (W == 1) {
+          const ulonglong2 v = ent[0];
+          ex[0] = v.x;
+          ez[0] = v.y;
+        } else {
+          const ulonglong2 v0 = ent[0], v1 = ent[1];
+          ex[0] = v0.x;
+          ex[W - 1] = v0.y;
+          ez[0] = v1.x;
+          ez[W - 1] = v1.y;
+        }
+        int anti = 0;
+#pragma unroll
+        for (int kk = 0; kk < W; ++kk) anti += __popcll(pz[kk] & ex[kk]);
+        pe += int(s_e[c * E + idx]) + 2 * anti;
+#pragma unroll
+        for (int kk = 0; kk < W; ++kk) {
+          px[kk] ^= ex[kk];
+          pz[kk] ^= ez[kk];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        cc.vx[p][k] = px[k];
+        cc.vz[p][k] = pz[k];
+      }
+      cc.ve[p] = pe & 3;
+      cc.valid |= 1u << p;
+    }
+    int anti = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) anti += __popcll(az[k] & cc.vx[p][k]);
+    e += cc.ve[p] + 2 * anti;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      ax[k] ^= cc.vx[p][k];
+      az[k] ^= cc.vz[p][k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) {  // the letters the pass leaves alone
+    ax[k] |= x[k] & pmk.idle[k];
+    az[k] |= z[k] & pmk.idle[k];
+  }
+  int c2 = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) c2 += __popcll(ax[k] & az[k]);
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    x[k] = ax[k];
+    z[k] = az[k];
+  }
+  return ((e - c2) & 3) == 2;
+}
+
+// Copies the chunk tables of a pass into shared memory (all threads).
+template <int CB, int W>
+__device__ __forceinline__ void load_clifford_table(uint64_t* s_tab, uint8_t* s_e,
+                                                    const uint64_t* tab_xz, const uint8_t* tab_e,
+                                                    int chunks) {
+  constexpr int E = 1 << (2 * CB);
+  const int nw = chunks * E * 2 * W;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) s_tab[i] = tab_xz[i];
+  const int ne = chunks * E;
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) s_e[i] = tab_e[i];
+}
+
 // Each warp reads a contiguous range, so consecutive strings of a lane are
 // close relatives.
 template <int W, int CB, typename WT = double>
@@ -420,21 +554,12 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
                                                         const uint8_t* tab_e, int chunks,
                                                         uint64_t live, PassMasks pmk) {
   constexpr int E = 1 << (2 * CB);
-  constexpr int P = clifford_parts<W>();
   extern __shared__ __align__(16) uint64_t s_tab[];
   uint8_t* s_e = reinterpret_cast<uint8_t*>(s_tab + size_t(chunks) * E * 2 * W);
-  {
-    const int nw = chunks * E * 2 * W;
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) s_tab[i] = tab_xz[i];
-    const int ne = chunks * E;
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) s_e[i] = tab_e[i];
-  }
+  load_clifford_table<CB, W>(s_tab, s_e, tab_xz, tab_e, chunks);
   __syncthreads();
   const size_t N = *n_in;
-  constexpr uint32_t M = (1u << CB) - 1;
-  uint64_t kx[P][W], kz[P][W], vx[P][W], vz[P][W];
-  int ve[P];
-  unsigned valid = 0;
+  CliffCache<W> cc;
   size_t rb, re;
   warp_range(N, &rb, &re);
   // the next string is loaded before the current one is mapped
@@ -451,105 +576,11 @@ __global__ void __launch_bounds__(256) k_clifford_table(TermsT<WT> t, const unsi
       z[k] = nz[k];
     }
     if (i + 32 < re) load_term<W>(t, i + 32, nx, nz);
-    int e = 0;
-#pragma unroll
-    for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
-    uint64_t ax[W], az[W];
+    const bool neg = clifford_table_map<W, CB>(x, z, s_tab, s_e, chunks, live, pmk, cc);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      ax[k] = 0;
-      az[k] = 0;
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      bool same = (valid >> p) & 1;
-#pragma unroll
-      for (int k = 0; k < W; ++k)
-        same = same && kx[p][k] == (x[k] & pmk.part[p][k]) && kz[p][k] == (z[k] & pmk.part[p][k]);
-      if (!same) {  // the product of this part's chunks
-        uint64_t px[W], pz[W];
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          px[k] = 0;
-          pz[k] = 0;
-          kx[p][k] = x[k] & pmk.part[p][k];
-          kz[p][k] = z[k] & pmk.part[p][k];
-        }
-        int pe = 0;
-        for (int c = p * chunks / P; c < (p + 1) * chunks / P; ++c) {
-          if (!((live >> c) & 1)) continue;
-          const int lo = c * CB, k = lo >> 6, off = lo & 63;
-          // for CB = 3 the chunk across the word boundary takes bits of both
-          // words by selects, not by a run-time index (which would put the
-          // string in local memory)
-          const uint64_t xw = (W == 1 || k == 0) ? x[0] : x[W - 1];
-          const uint64_t zw = (W == 1 || k == 0) ? z[0] : z[W - 1];
-          uint32_t xb, zb;
-          if (CB == 4 || off + CB <= 64) {
-            xb = uint32_t(xw >> off) & M;
-            zb = uint32_t(zw >> off) & M;
-          } else {  // k == 0 < W - 1
-            xb = uint32_t((xw >> off) | (W > 1 ? (x[W - 1] << (64 - off)) : 0)) & M;
-            zb = uint32_t((zw >> off) | (W > 1 ? (z[W - 1] << (64 - off)) : 0)) & M;
-          }
-          const uint32_t idx = xb | (zb << CB);
-          if (!idx) continue;
-          // the entry (x words, then z words) in 16-byte loads
-          const ulonglong2* ent =
-              reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
-          uint64_t ex[W], ez[W];
-          if (W == 1) {
-            const ulonglong2 v = ent[0];
-            ex[0] = v.x;
-            ez[0] = v.y;
-          } else {
-            const ulonglong2 v0 = ent[0], v1 = ent[1];
-            ex[0] = v0.x;
-            ex[W - 1] = v0.y;
-            ez[0] = v1.x;
-            ez[W - 1] = v1.y;
-          }
-          int anti = 0;
-#pragma unroll
-          for (int kk = 0; kk < W; ++kk) anti += __popcll(pz[kk] & ex[kk]);
-          pe += int(s_e[c * E + idx]) + 2 * anti;
-#pragma unroll
-          for (int kk = 0; kk < W; ++kk) {
-            px[kk] ^= ex[kk];
-            pz[kk] ^= ez[kk];
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          vx[p][k] = px[k];
-          vz[p][k] = pz[k];
-        }
-        ve[p] = pe & 3;
-        valid |= 1u << p;
-      }
-      int anti = 0;
-#pragma unroll
-      for (int k = 0; k < W; ++k) anti += __popcll(az[k] & vx[p][k]);
-      e += ve[p] + 2 * anti;
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        ax[k] ^= vx[p][k];
-        az[k] ^= vz[p][k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) {  // the letters the pass leaves alone
-      ax[k] |= x[k] & pmk.idle[k];
-      az[k] |= z[k] & pmk.idle[k];
-    }
-    int c2 = 0;
-#pragma unroll
-    for (int k = 0; k < W; ++k) c2 += __popcll(ax[k] & az[k]);
-    const bool neg = ((e - c2) & 3) == 2;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      t.x[k * t.cap + i] = ax[k];
-      t.z[k * t.cap + i] = az[k];
+      t.x[k * t.cap + i] = x[k];
+      t.z[k * t.cap + i] = z[k];
     }
     if (neg) t.w[i] = wneg(t.w[i]);
   }

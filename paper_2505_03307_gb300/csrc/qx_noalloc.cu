@@ -49,6 +49,19 @@ std::mutex g_mutex;
 
 __global__ void k_na_set_count(unsigned long long* p, unsigned long long v) { *p = v; }
 
+// A generator id at or beyond ngen would index the per-generator arrays of the
+// scratch (mixed masks) past their region.  This pass runs before the merge
+// kernels and flags such ids; the merge kernels return at once when the error
+// word is set, so no term with a bad id is ever read as an index.
+constexpr unsigned kErrGenId = 16u;
+__global__ void k_na_check_gen(const uint32_t* gen, size_t n, uint32_t ngen, unsigned* err) {
+  bool bad = false;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    bad |= gen[i] >= ngen;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrGenId);
+}
+
 // Once per device, with the device current: address lookup and clearing.
 qx_status setup(int dev, DeviceState** out) {
   DeviceState& st = g_state[dev];
@@ -97,7 +110,7 @@ bool fan_qubit_from_table(int q, const double* t9, FanQ* f) {
 }
 
 template <int W>
-void launch(const Terms& in, const Terms& out, int q, const FanQ& f, unsigned char* b,
+void launch(const Terms& in, const Terms& out, int q, int ngen, const FanQ& f, unsigned char* b,
             unsigned epoch, int sms, cudaStream_t s) {
   auto* table = reinterpret_cast<Slot*>(b + kOffTable);
   auto* lead = reinterpret_cast<uint32_t*>(b + kOffLead);
@@ -111,6 +124,7 @@ void launch(const Terms& in, const Terms& out, int q, const FanQ& f, unsigned ch
   const size_t N = in.cap;
   const unsigned grid =
       unsigned(std::max<size_t>(1, std::min<size_t>((N + 255) / 256, size_t(sms) * 8)));
+  k_na_check_gen<<<grid, 256, 0, s>>>(in.g, N, uint32_t(ngen), err);
   k_merge_insert<W><<<grid, 256, 0, s>>>(in, n_in, q, f, mixed, table, kNaSlots, epoch, lead, pv,
                                          pmask, kNaMaxTerms, 1u << 25, err);
   k_merge_emit<W, 256><<<grid, 256, 0, s>>>(in, n_in, q, f, mixed, lead, pv, pmask, kNaMaxTerms,
@@ -169,9 +183,9 @@ extern "C" qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const u
                  const_cast<uint32_t*>(gen), n_in};
   const Terms out{out_x, out_z, out_w, out_gen, out_cap};
   if (W == 1)
-    launch<1>(in, out, q, f, b, st->epoch, sms, s);
+    launch<1>(in, out, q, ngen, f, b, st->epoch, sms, s);
   else
-    launch<2>(in, out, q, f, b, st->epoch, sms, s);
+    launch<2>(in, out, q, ngen, f, b, st->epoch, sms, s);
   cudaError_t e = cudaGetLastError();
   unsigned long long cnt[3] = {0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, counters, 24, cudaMemcpyDeviceToHost, s);
@@ -179,6 +193,7 @@ extern "C" qx_status qx_merge_qubit_static(int n, size_t n_in, int ngen, const u
   if (e != cudaSuccess)
     return fail(QX_ECUDA, std::string("static merge failed: ") + cudaGetErrorString(e));
   const unsigned err = unsigned(cnt[2]);
+  if (err & kErrGenId) return fail(QX_EINVAL, "a generator id is not below ngen");
   if (err & kErrSpin) return fail(QX_ETIMEOUT, "a device-side wait for a group leader gave up");
   if (err & kErrProbe) return fail(QX_ECAP, "the static hash table ran out of probe slots");
   if (err & kErrCap) return fail(QX_ECAP, "out_cap is smaller than the number of output terms");

@@ -260,7 +260,11 @@ _torch_alloc = None
 
 
 def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeout_ms=0,
-              torch_allocator=False, kernel_timing=False, precision=64, inplace=True):
+              torch_allocator=False, kernel_timing=False, precision=64, inplace=True,
+              allocator=None):
+    """qx_prop_opts from keyword arguments.  ``allocator``: an object with
+    ``alloc`` / ``free`` ctypes callbacks (ALLOC_FN / FREE_FN) that the library
+    calls for every device allocation of the call."""
     o = PropOpts()
     load_library().qx_default_opts(ctypes.byref(o))
     o.precision = int(precision)
@@ -278,6 +282,9 @@ def make_opts(eps=0.0, gens=None, hbm_budget=0, max_terms=0, stream=None, timeou
             _torch_alloc = _TorchAllocator()
         o.alloc = _torch_alloc.alloc
         o.free = _torch_alloc.free
+    if allocator is not None:
+        o.alloc = allocator.alloc
+        o.free = allocator.free
     return o
 
 
@@ -401,6 +408,7 @@ class Result:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.qx_free_result(self._h)
             self._h = None
+            self._allocator = None
 
     def free(self):
         self.__del__()
@@ -513,7 +521,10 @@ def propagate(plan: Plan, **kw) -> Result:
     o = make_opts(**kw)
     h = _P()
     _check(load_library().qx_propagate(plan._h, ctypes.byref(o), ctypes.byref(h)))
-    return Result(h, plan.n)
+    r = Result(h, plan.n)
+    # the result frees its arrays through the allocator's callbacks
+    r._allocator = kw.get("allocator")
+    return r
 
 
 def propagate_from(plan: Plan, paulis, weights=None, **kw) -> Result:

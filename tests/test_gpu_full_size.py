@@ -21,7 +21,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_util import compare_gen, compare_result
+from gpu_util import close, compare_gen, compare_result
 from oracle import oracle as O
 from paper_2505_03307_gb300 import qx
 from paper_2505_03307_gb300 import workloads as W
@@ -69,7 +69,7 @@ def test_random_pairs_n100_full_digest():
         for s, hx in d["sample"]:
             want = float.fromhex(hx)
             assert s in got, (g, s)
-            assert abs(got[s] - want) <= 1e-12 * abs(want) + 1e-13, (g, s, got[s], want)
+            assert close(got[s], want), (g, s, got[s], want)
 
 
 def test_fan_in_deep_n100_closed_form():
@@ -104,7 +104,7 @@ def test_fan_in_deep_n100_closed_form():
                                                         for s in strings[:16]]
         got = res.coeff_batch([g] * (len(strings) + len(absent)), strings + absent)
         for s, v, x in zip(strings, want, got):
-            assert abs(x - v) <= 1e-12 * abs(v) + 1e-15, (g, s, x, v)
+            assert close(x, v), (g, s, x, v)
         assert np.all(got[len(strings):] == 0.0)
     for g in (0, 7, 19):
         d = res.export_dict(g)

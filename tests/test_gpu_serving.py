@@ -5,10 +5,16 @@ gates, 0-14 T/RZ) are submitted together; the server's slots propagate them
 concurrently on their own streams.  Every result must equal qx_propagate of
 the same circuit alone: the same strings and, in FP64, bit-identical weights
 (every sum in the kernels has a fixed order, only the term order may differ).
-FP32 serving is compared with FP64 alone at 1e-5 relative.
+Every served result is also compared with the oracle's plan mode: exact
+string sets, FP64 weights within 1e-12 |w| + 1e-15, FP32 weights within
+1e-5 |w| + 1e-7.
 """
+import os
+
 import pytest
 
+from gpu_util import compare_gen
+from oracle import oracle as O
 from paper_2505_03307_gb300 import qx
 from paper_2505_03307_gb300 import workloads as W
 
@@ -38,8 +44,11 @@ def test_mix_equals_alone_fp64():
         res, lat = srv.wait(t)
         assert lat > 0
         want = _alone(n, instrs)
+        ref = O.propagate(n, instrs, mode="plan", threads=os.cpu_count() or 1)
         for g in range(n):
-            assert res.export_dict(g) == want[g], (t, g)
+            got = res.export_dict(g)
+            assert got == want[g], (t, g)
+            compare_gen(got, O.as_dict(ref[g]), f"request {t} generator {g}")
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
@@ -56,8 +65,11 @@ def test_budget_admission_reruns_exclusive():
     for t, (n, instrs) in tickets:
         res, _ = srv.wait(t)
         want = _alone(n, instrs)
+        ref = O.propagate(n, instrs, mode="plan", threads=os.cpu_count() or 1)
         for g in range(n):
-            assert res.export_dict(g) == want[g]
+            got = res.export_dict(g)
+            assert got == want[g]
+            compare_gen(got, O.as_dict(ref[g]), f"generator {g}")
     assert srv.stats()["retried_exclusive"] >= 1
     srv.close()
 
@@ -70,13 +82,17 @@ def test_fp32_serving_matches_fp64_alone():
     for t, n, instrs in tickets:
         res, _ = srv.wait(t)
         want = _alone(n, instrs, precision=64)
+        ref = O.propagate(n, instrs, mode="plan", threads=os.cpu_count() or 1)
         for g in range(n):
             got = res.export_dict(g)
             assert got.keys() == want[g].keys()
             for s, w in want[g].items():
                 d = abs(got[s] - w)
                 assert d <= 1e-5 * abs(w) + 1e-7
+            for s, w in O.as_dict(ref[g]).items():
+                d = abs(got[s] - w)
+                assert d <= 1e-5 * abs(w) + 1e-7, (t, g, s, got[s], w)
                 if abs(w) > 1e-3:
                     worst = max(worst, d / abs(w))
-    print(f"FP32 serving vs FP64 alone: max relative error {worst:.2e}")
+    print(f"FP32 serving vs the FP64 oracle: max relative error {worst:.2e}")
     srv.close()

@@ -183,3 +183,53 @@ def test_checks_at_the_end_on_the_large_workload_shape():
     b = qx.propagate(plan, gens=(12, 20))
     _same(b, _fresh(n, instrs, gens=(12, 20)))
     compare_result(b, O.propagate(n, instrs, mode="plan", gens=(12, 20), threads=8))
+
+
+class _LoggingAllocator:
+    """PyTorch's caching allocator behind the library's allocator callbacks,
+    logging the size of every request; with ``refuse_new`` it refuses, once,
+    the first request whose size is not in that set."""
+
+    def __init__(self, refuse_new=None):
+        import torch
+        self.torch = torch
+        self.sizes = []
+        self.refuse_new = refuse_new
+        self.refused = []
+        self.alloc = qx.ALLOC_FN(self._alloc)
+        self.free = qx.FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx, stream):
+        nbytes = int(nbytes)
+        self.sizes.append(nbytes)
+        if self.refuse_new is not None and not self.refused and nbytes not in self.refuse_new:
+            self.refused.append(nbytes)
+            return None
+        try:
+            return self.torch.cuda.caching_allocator_alloc(nbytes, stream=stream or 0)
+        except Exception:  # noqa: BLE001 - NULL tells the library
+            return None
+
+    def _free(self, ptr, ctx, stream):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+def test_recorded_size_that_cannot_be_allocated_falls_back():
+    """The plan's record of an expansion holds the full run's output size; a
+    run over fewer generators whose allocation at that size fails goes back
+    to counting first, counts the miss and gives the same result."""
+    n, instrs = W.fan_in_heavy(2, n=20, n_s=8, total=500, tail=80)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(3):
+        qx.propagate(plan).free()
+    gens = (12, 20)
+    fresh_log = _LoggingAllocator()
+    fresh = _fresh(n, instrs, gens=gens, allocator=fresh_log)
+    refusing = _LoggingAllocator(refuse_new=set(fresh_log.sizes))
+    res = qx.propagate(plan, gens=gens, allocator=refusing)
+    assert len(refusing.refused) == 1, refusing.refused
+    assert res.stats()["guesses_missed"] >= 1
+    _same(res, fresh)
+    compare_result(res, O.propagate(n, instrs, mode="plan", gens=gens, threads=8))
+    res.free()
+    fresh.free()

@@ -7,14 +7,17 @@ with index-based accumulation keeps its scratch in a fixed array inside the
 library.  This test hands it the terms of a propagated circuit and checks, on
 two calls in a row (the second reuses the scratch the first left behind),
 that it gives the same generators as qx_propagate of the circuit followed by
-the same one-qubit gate.  This file is collected last on purpose.
+the same one-qubit gate, and the same as the oracle's plan mode within the
+FP64 tolerance.  This file is collected last on purpose.
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
 
 from gpu_util import compare_gen
+from oracle import oracle as O
 from paper_2505_03307_gb300 import qx
 from paper_2505_03307_gb300 import workloads as W
 
@@ -70,6 +73,8 @@ def test_static_merge_matches_propagate(n, q):
     table = plan_b.lut(len(plan_b.ops()) - 1)[q]
     res_b = qx.propagate(plan_b)
     want = [res_b.export_dict(j) for j in range(n)]
+    ref = O.propagate(n, base + [extra], mode="plan", threads=os.cpu_count() or 1)
+    oracle_dicts = [O.as_dict(r) for r in ref]
     N = w.numel()
     cap = 3 * N
     for _ in range(2):
@@ -82,6 +87,7 @@ def test_static_merge_matches_propagate(n, q):
         got = _as_dicts(n, ox, oz, ow, og, cnt, n)
         for j in range(n):
             compare_gen(got[j], want[j], f"generator {j}")
+            compare_gen(got[j], oracle_dicts[j], f"generator {j} against the oracle")
 
 
 def test_static_merge_rejects_sizes_beyond_its_limit():
@@ -95,3 +101,31 @@ def test_static_merge_rejects_sizes_beyond_its_limit():
     rc = lib.qx_merge_qubit_static(8, 10, 5000, None, None, None, None, 0, table, None, None, None,
                                    None, 0, ctypes.byref(nout), None)
     assert qx.STATUS[rc] == "QX_EINVAL"
+
+
+def test_static_merge_rejects_generator_ids_beyond_ngen():
+    """An id at or above ngen is caught on the device before any merge
+    kernel uses it as an index (QX_EINVAL, nothing written).  The bad id 7
+    with ngen = 5 stays inside the scratch's per-generator region, so the
+    access would be in bounds even without the check."""
+    import torch
+    n, q = 10, 3
+    N = 6
+    x = torch.zeros((1, N), dtype=torch.int64, device="cuda")
+    z = torch.zeros((1, N), dtype=torch.int64, device="cuda")
+    x[0, :] = torch.tensor([1 << q | 1 << k for k in range(N)], dtype=torch.int64)
+    w = torch.full((N,), 0.5, dtype=torch.float64, device="cuda")
+    g = torch.tensor([0, 1, 2, 3, 4, 7], dtype=torch.int32, device="cuda")
+    table = np.array([[0.6, 0.8, 0.0], [-0.8, 0.6, 0.0], [0.0, 0.0, 1.0]])
+    ox = torch.full((1, 3 * N), -1, dtype=torch.int64, device="cuda")
+    oz = torch.full_like(ox, -1)
+    ow = torch.full((3 * N,), 7.0, dtype=torch.float64, device="cuda")
+    og = torch.full((3 * N,), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(qx.QxError, match="generator id"):
+        qx.merge_qubit_static(n, 5, x, z, w, g, q, table, ox, oz, ow, og)
+    torch.cuda.synchronize()
+    assert torch.all(ow == 7.0) and torch.all(og == -1)
+    # the same call with valid ids works right after
+    g[5] = 4
+    cnt = qx.merge_qubit_static(n, 5, x, z, w, g, q, table, ox, oz, ow, og)
+    assert cnt == 2 * N
