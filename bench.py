@@ -1,19 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the extended-stabilizer propagation hot path (qx_propagate).
 
-Workload (the n=50 Clifford+T configuration at its quoted size): 50 qubits,
-2000 gates, 16 T and 16 RZ gates on 16 fan-out qubits, generators Z_0..Z_49;
-34 generators reach 65,536 terms each (2,228,256 terms in all).  A step is one
-qx_propagate of the whole circuit: initial generators (create_Z_j), fused
-Clifford passes, the 2^16 expansion, 16 index-accumulation passes and the
-Clifford tail, with inputs resident on the device.  L2 is flushed (a 512 MB
-write) between timed steps, outside the per-step CUDA events.
+Headline workload (the n=100 configuration at its quoted size, ~1e8 terms /
+~5 GB): fan_in_deep_n100.  100 qubits (two words per string), 100,000 gates:
+H on every qubit, CX fan-in from the 80 other qubits onto the 20 fan-out
+qubits, then 20 rounds of [a random H/S/CX block of ~4,760 gates on the 80
+other qubits; RZ(theta ~ U[0, 2 pi)) on fan-out qubit r], and a last block.
+Generators Z_0..Z_99, FP64 weights, pruning eps = 1e-14; 80 x 2^20 + 40 =
+83,886,120 final terms (3.7 GB of terms).  A step is one qx_propagate of the
+whole circuit (initial generators, 20 fan-out steps, the Clifford passes) with
+the plan resident on the device.  The terms are larger than L2 and L2 is also
+flushed (a 512 MB write) between timed steps, outside the per-step CUDA events.
 
 Metric: Pauli-term updates per second = sum over the K + K' grouped operators
-of the terms each was applied to, divided by the step time.
+of the terms each was applied to, divided by the step time; beside it,
+children per second and the step's algorithmic bytes per second (the survey's
+accounting: (parents + children) x (16W + 8) per fan-out step, plus 2N x
+(16W + 8) per Clifford pass not fused into an expansion).
+
+Secondary legs: fan_in_heavy_n50 (2.2M terms, L2-resident merge wires, its
+FP64-bound kernel against the measured FP64 FMA rate), FP32 weights on both
+workloads, serving, gradients, grouping variants and the XYZ + chain sweep.
 
 --gpus N under torchrun: every rank propagates its own seeded instance
-(independent problems, no data-path collective): weak scaling.
+(independent problems, no data-path collective): weak scaling.  With
+--split generators the ranks share one circuit instead, each propagating the
+generators of its range (balanced by the term counts of an untimed run):
+strong scaling, with a host gather of per-generator counts and norms.
 --impl reference: the CPU oracle (std::map per generator, gate by gate) on
 the host cores, each step advancing one heavy generator through a bounded
 slice of the same circuit.
@@ -21,9 +34,11 @@ slice of the same circuit.
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -31,16 +46,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "fan_in_heavy_n50"
+WORKLOAD = "fan_in_deep_n100"
+EPS = 1e-14
 CONFIG = {
     "workload": WORKLOAD,
-    "description": "n=50, 2000 gates (H/S/CNOT + 16 T + 16 RZ on 16 fan-out qubits), "
-                   "generators Z_0..Z_49, 34 x 65536 + 16 x 2 = 2,228,256 final terms, "
-                   "FP64 weights, eps=0",
-    "n_qubits": 50,
-    "gates": 2000,
-    "final_terms": 2228256,
-    "l2": "flushed between timed steps (512 MB write)",
+    "description": "n=100 (W=2), 100,000 gates: H on all, CX fan-in onto 20 fan-out qubits, "
+                   "20 x [random H/S/CX block on the other 80 qubits; RZ(theta ~ U[0,2pi)) on one "
+                   "fan-out qubit], last block; generators Z_0..Z_99; 80 x 2^20 + 40 = "
+                   "83,886,120 final terms (3.7 GB of terms), FP64 weights, eps=1e-14",
+    "n_qubits": 100,
+    "gates": 100000,
+    "eps": EPS,
+    "final_terms": 83886120,
+    "l2": "terms larger than L2 (3.7 GB); L2 also flushed between timed steps (512 MB write)",
 }
 METRIC = "Pauli-term updates/sec"
 UNIT = "term-updates/s"
@@ -65,31 +83,48 @@ def peaks():
         return 6800.0, "of fallback"
 
 
-# Nominal FP64 rate of the GPU (FP64 is far below the tensor rates on this
-# part): the ceiling of a merge wire, whose bytes stay in L2 between wires.
-FP64_PEAK_TFLOPS = 1.25
+def measure_fma_peaks():
+    """FP64 and FP32 FMA throughput of this GPU (libqxpeak: independent FMA
+    chains, CUDA events, best of 3 launches after an untimed one)."""
+    import ctypes
+
+    from paper_2505_03307_gb300 import build as B
+    lib = ctypes.CDLL(B.PEAK_LIB)
+    lib.qx_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for bits, iters in ((64, 8192), (32, 131072)):
+        best, ms_best = 0.0, 0.0
+        for _ in range(3):
+            tf, ms = ctypes.c_double(), ctypes.c_double()
+            rc = lib.qx_peak_fma(bits, 8, iters, ctypes.byref(tf), ctypes.byref(ms))
+            if rc == 0 and tf.value > best:
+                best, ms_best = tf.value, ms.value
+        out[f"fp{bits}_tflops"] = best
+        out[f"fp{bits}_launch_ms"] = ms_best
+    out["how"] = ("k_fma_chains: 8 independent FMA chains per thread, 8 blocks of 256 threads "
+                  "per SM, 2 flops per FMA, CUDA events, best of 3 launches (qx_peak.cu)")
+    return out
 
 
-def fp64_view(kernel, d, s0):
-    """The dominant merge-wire class against the FP64 unit: each term of a
-    two-member group takes two fused multiply-adds per wire (4 flops); on the
-    bench workload that is every term but the 32 of the 16 two-term
-    generators.  None for other classes."""
-    if kernel != "merge_blocks" or d["ms"] <= 0:
+def fp64_view(kernel, d, terms_per_launch, fp64_peak):
+    """A merge-wire class against the measured FP64 FMA rate: each member of
+    a two-member group takes two fused multiply-adds per wire (4 flops)."""
+    if kernel != "merge_blocks" or d["ms"] <= 0 or not fp64_peak:
         return None
-    flops = 4.0 * s0["final_terms"]
+    flops = 4.0 * terms_per_launch
     t = d["ms"] / max(1, d["launches"]) / 1e3
     tf = flops / t / 1e12
-    return {"flops_per_launch": flops, "achieved_tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,
-            "peak_source": "nominal (recipe)", "frac": tf / FP64_PEAK_TFLOPS}
+    return {"flops_per_launch": flops, "achieved_tflops": tf, "peak_tflops": fp64_peak,
+            "peak_source": "measured FP64 FMA rate (qx_peak.cu)", "frac": tf / fp64_peak}
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, workload):
     """Per-launch DRAM bytes of kernel class `kernel` from the committed ncu
-    summary, if the capture was taken on the current source of that kernel
-    (the file and its sha256 are recorded on the kernel's line)."""
+    summary of `workload`, if the capture was taken on the current source of
+    that kernel (the file and its sha256 are recorded on the kernel's line)."""
     import hashlib
-    summ = os.path.join(ROOT, "profiles", "ncu_traffic_fan_in_heavy_n50.txt")
+    summ = os.path.join(ROOT, "profiles", f"ncu_traffic_{workload}.txt")
     try:
         for ln in open(summ):
             parts = ln.split()
@@ -100,6 +135,17 @@ def ncu_traffic(kernel):
     except (OSError, ValueError):
         pass
     return None
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -155,6 +201,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def timed_steps(fn, steps, flush, stream=None):
+    """Device time (CUDA events on the launch stream) of `steps` calls of fn,
+    L2 flushed before each outside the events; returns (ms list, results)."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    out, res = [], []
+    for _ in range(steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        r = fn()
+        e1.record(s)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+        res.append(r)
+    return out, res
+
+
+def kernel_classes(stats_list):
+    kc = {}
+    for s in stats_list:
+        for name, d in s["kernels"].items():
+            a = kc.setdefault(name, {"launches": 0, "alg_bytes": 0, "ms": 0.0})
+            a["launches"] += d["launches"]
+            a["alg_bytes"] += d["alg_bytes"]
+            a["ms"] += d["ms"]
+    return kc
+
+
 # --------------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -170,18 +245,28 @@ def run_ours(args):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
+    from paper_2505_03307_gb300 import dist as qdist
     from paper_2505_03307_gb300 import qx
     from paper_2505_03307_gb300 import workloads as W
 
     qx.load_library()
-    n, instrs = W.fan_in_heavy(1 + rank)
+    split = args.split == "generators" and world > 1
+    # weak scaling: every rank its own seeded instance; strong: one circuit
+    n, instrs = W.fan_in_deep(1 if split else 1 + rank)
     plan = qx.group_ops(qx.load_circuit(n, instrs))
+    gens = cost = None
+    if split:  # ranges balanced by the term counts of an untimed run
+        r = qx.propagate(plan, eps=EPS)
+        cost = [r.info(g)["nterms"] for g in range(n)]
+        r.free()
+        gens = qdist.shard_generators(n, rank, world, cost)
+    kw = {"eps": EPS} if gens is None else {"eps": EPS, "gens": gens}
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = flush_buf.zero_
 
     for _ in range(args.warmup):
-        r = qx.propagate(plan)
-        r.free()
+        qx.propagate(plan, **kw).free()
     torch.cuda.synchronize()
 
     # ---- device-resident timed region
@@ -192,11 +277,11 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         for _ in range(args.steps):
-            flush.zero_()
+            flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = qx.propagate(plan)
+            r = qx.propagate(plan, **kw)
             e1.record(stream)
             stats.append(r.stats())
             r.free()
@@ -208,6 +293,7 @@ def run_ours(args):
         dist.barrier()
     total_ms = sum(step_ms)
     updates = sum(s["term_updates"] for s in stats)
+    children = sum(s["children"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
     clocks = clk.summary()
     # ---- the same steps again with a CUDA event pair around every launch
@@ -215,11 +301,21 @@ def run_ours(args):
     # their readout add host work, so these steps are not the timed ones
     kstats = []
     for _ in range(args.steps):
-        flush.zero_()
-        r = qx.propagate(plan, kernel_timing=True)
+        flush()
+        r = qx.propagate(plan, kernel_timing=True, **kw)
         kstats.append(r.stats())
         r.free()
     torch.cuda.synchronize()
+    # ---- a new plan every step: the first run of a plan, with no record of
+    # earlier runs (plan building outside the device events)
+    cold_ms = []
+    for _ in range(max(3, args.steps // 4)):
+        p2 = qx.group_ops(qx.load_circuit(n, instrs))
+        ms, res = timed_steps(lambda: qx.propagate(p2, **kw), 1, flush, stream)
+        cold_ms += ms
+        cold_syncs = res[0].stats()["host_syncs"]
+        res[0].free()
+        del p2
 
     # ---- end to end through the C ABI: host circuit in, host result out.
     # The circuit is held as qx_instr records (24 B per gate, the C ABI's
@@ -235,7 +331,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = qx.group_ops(qx.load_circuit_records(n, recs))
-        r = qx.propagate(p2)
+        r = qx.propagate(p2, **kw)
         k = r.nterms
         if pinned is None or pinned[2].numel() < k:
             pinned = [torch.empty((k, r.W), dtype=torch.int64, pin_memory=True),
@@ -253,10 +349,24 @@ def run_ours(args):
             d2h = k * (2 * 8 * r.W + 8 + 4)
         r.free()
         del p2
+    del pinned
+
+    # ---- strong scaling: the per-generator counts and norms of every rank
+    # gathered on the host (the full term arrays stay on their devices)
+    gathered = None
+    if split:
+        def run_range(b, e):
+            r = qx.propagate(plan, eps=EPS, gens=(b, e))
+            out = [(r.info(g)["nterms"], r.info(g)["sumsq"]) for g in range(e - b)]
+            r.free()
+            return out
+        rows, _ = qdist.run_generator_split(n, rank, world, cost, run_range)
+        gathered = {"generators": len(rows), "terms": int(sum(c for c, _ in rows)),
+                    "max_norm_error": float(max(abs(s2 - 1.0) for _, s2 in rows))}
 
     # ---- max of the time over ranks, sum of the work
-    from paper_2505_03307_gb300 import dist as qdist
     total_ms_max, updates_all = qdist.reduce_step_times(total_ms, updates, device="cuda")
+    _, children_all = qdist.reduce_step_times(total_ms, children, device="cuda")
     e2e_ms_max, e2e_updates_all = qdist.reduce_step_times(sum(e2e_ms), e2e_updates,
                                                           device="cuda")
     if rank != 0:
@@ -265,29 +375,29 @@ def run_ours(args):
         return
 
     value = updates_all / (total_ms_max / 1e3)
-    # ---- roofline of the dominant kernel class
-    kc = {}
-    for s in kstats:
-        for name, d in s["kernels"].items():
-            a = kc.setdefault(name, {"launches": 0, "alg_bytes": 0, "ms": 0.0})
-            a["launches"] += d["launches"]
-            a["alg_bytes"] += d["alg_bytes"]
-            a["ms"] += d["ms"]
+    peak, peak_kind = peaks()
+    kc = kernel_classes(kstats)
     dom = max(kc, key=lambda k: kc[k]["ms"])
     d = kc[dom]
-    peak, peak_kind = peaks()
     achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
-    traffic = ncu_traffic(dom)
     share = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kc.values())), 4)
              for k, v in kc.items() if v["launches"]}
     s0 = stats[0]
+    ms_step = total_ms_max / args.steps
+    step_gbs = s0["alg_bytes"] / (statistics.median(step_ms) / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "strong" if split else "weak",
+        "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded circuits; no dataset)",
-        "config": dict(CONFIG, parallelism=f"independent circuits x{world}" if world > 1 else "single"),
+        "config": dict(CONFIG, parallelism=(f"generator ranges x{world}" if split else
+                                            f"independent circuits x{world}" if world > 1
+                                            else "single")),
+        "children_per_s": children_all / (total_ms_max / 1e3),
+        "step_alg_gbs": step_gbs,
+        "step_alg_frac": step_gbs / peak,
         "e2e": {"value": e2e_updates_all / (e2e_ms_max / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms_max / args.steps,
@@ -296,10 +406,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic,
+                     "traffic": ncu_traffic(dom, WORKLOAD),
                      "alg_bytes_per_launch": d["alg_bytes"] / max(1, d["launches"]),
-                     "avg_launch_ms": d["ms"] / max(1, d["launches"]),
-                     "fp64": fp64_view(dom, d, s0)},
+                     "avg_launch_ms": d["ms"] / max(1, d["launches"])},
         "kernel_share": share,
         # per-step device time of each kernel class (CUDA events around its
         # launches); the rest of ms_per_step is time between classes
@@ -308,53 +417,58 @@ def run_ours(args):
         "per_step": {"term_updates": s0["term_updates"], "children": s0["children"],
                      "alg_bytes": s0["alg_bytes"], "kernel_launches": s0["kernel_launches"],
                      "host_syncs": s0["host_syncs"], "K": s0["K"], "Kp": s0["Kp"],
-                     "final_terms": s0["final_terms"], "merge_passes": s0["merge_passes"],
-                     "alg_gbs": s0["alg_bytes"] / (statistics.median(step_ms) / 1e3) / 1e9},
+                     "final_terms": s0["final_terms"], "fan_steps": s0["fan_steps"],
+                     "clifford_passes": s0["clifford_passes"],
+                     "guesses_held": s0["guesses_held"]},
+        "cold_plan": {"propagate_ms": statistics.median(cold_ms), "host_syncs": cold_syncs,
+                      "note": "a new plan for every step (first run of a plan, no record of "
+                              "earlier runs); plan building outside the device events"},
         "clocks": clocks,
         "wall_s": t_wall,
     }
-    if world == 1 and args.serve_requests > 0:
-        line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
-    if world == 1 and args.adjoint_steps > 0:
-        line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
-    if world == 1 and args.fp32_steps > 0:
-        line["fp32"] = fp32_bench(qx, plan, flush.zero_, args.fp32_steps, step_ms)
-    if world == 1 and args.large_steps > 0:
-        line["large"] = large_bench(qx, W, flush.zero_, args.large_steps, peak)
-    if world == 1 and args.grouping_steps > 0:
-        line["grouping"] = grouping_bench(qx, W, flush.zero_, args.grouping_steps)
-    if world == 1 and args.xyz_repeats:
-        line["xyz_chain"] = xyz_chain_bench(qx, W, [int(r) for r in args.xyz_repeats.split(",")],
-                                            flush.zero_, oracle_sample=not args.no_cpu_baseline)
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(plan_updates_per_gen(qx, plan, n), budget_s=20.0)
+    if gathered is not None:
+        line["gather"] = gathered
+    del plan
+    if world == 1:
+        fma = measure_fma_peaks()
+        line["fma_peaks"] = fma
+        if args.heavy_steps > 0:
+            line["heavy50"] = heavy50_bench(qx, W, flush, args.heavy_steps, peak,
+                                            fma["fp64_tflops"])
+        if args.fp32_steps > 0:
+            line["fp32"] = fp32_bench(qx, W, flush, args.fp32_steps, statistics.median(step_ms))
+        if args.serve_requests > 0:
+            line["serving"] = serving_bench(qx, W, args.serve_requests, args.serve_rate)
+        if args.adjoint_steps > 0:
+            line["adjoint"] = adjoint_bench(qx, W, args.adjoint_steps)
+        if args.grouping_steps > 0:
+            line["grouping"] = grouping_bench(qx, W, flush, args.grouping_steps)
+        if args.xyz_repeats:
+            line["xyz_chain"] = xyz_chain_bench(qx, W, [int(r) for r in args.xyz_repeats.split(",")],
+                                                flush, oracle_sample=not args.no_cpu_baseline)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
-    """Serving stream (n in [10, 60], 200-5000 Clifford gates, 0-14 T/RZ,
-    Poisson arrivals at rate_hz): circuits/s and p50/p99 latency of the
-    request loop (FP32 weights, admission by HBM budget), next to the same
-    circuits propagated one at a time in FP64 on the same GPU."""
-    import threading
-    import torch
-
-    reqs = W.serving_stream(7, count=count, rate_hz=rate_hz)
-    # the client's marshalling is done before the clock starts
-    arrays = [qx.instr_array(instrs) for _, _, instrs in reqs]
-    srv = qx.Server(slots=slots, hbm_budget=64 << 30, precision=32)
-    # warm-up: a few requests through every slot
-    for _, n, instrs in reqs[:2 * slots]:
-        res, _ = srv.wait(srv.submit(n, instrs))
+def _serve_once(qx, reqs, arrays, rate_hz, slots, budget, warm):
+    """One pass of the stream at `rate_hz` (0: every request at once):
+    circuits/s over the wall clock and latency percentiles."""
+    srv = qx.Server(slots=slots, hbm_budget=budget, precision=32)
+    for k in range(warm):  # warm-up: planners, engines, allocator pools
+        res, _ = srv.wait(srv.submit(reqs[k][1], arrays[k]))
         res.free()
     tickets = [None] * len(reqs)
+    scale = 0.0 if rate_hz <= 0 else 1.0
     t0 = time.perf_counter()
+    arrival0 = reqs[0][0]
 
     def submitter():
         for k, (at, n, _) in enumerate(reqs):
-            delay = at - (time.perf_counter() - t0)
+            delay = scale * (at - arrival0) * (2000.0 / rate_hz if rate_hz > 0 else 0.0) \
+                - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
             tickets[k] = srv.submit(n, arrays[k])
@@ -364,7 +478,7 @@ def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
     lat = []
     for k in range(len(reqs)):
         while tickets[k] is None:
-            time.sleep(0.0005)
+            time.sleep(0.0002)
         res, ms = srv.wait(tickets[k])
         lat.append(ms)
         res.free()
@@ -372,6 +486,30 @@ def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+    lat.sort()
+    return {"rate_hz": rate_hz if rate_hz > 0 else "all at once",
+            "circuits_per_s": len(reqs) / wall, "wall_s": wall,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "batches": st["batches"],
+            "mean_batch": st["mean_batch"], "failed": st["failed"], "alone": st["alone"],
+            "peak_reserved_bytes": st["peak_reserved"]}
+
+
+def serving_bench(qx, W, count, rate_hz, slots=2, baseline_count=300):
+    """The serving stream (n in [10, 60], 200-5000 Clifford gates, 0-14 T/RZ,
+    10k seeded requests): circuits/s and p50/p99 latency of the request loop
+    (FP32 weights, batches admitted by the HBM ledger) at Poisson arrival
+    rates up to saturation (every request submitted at once), next to the
+    same circuits propagated one at a time in FP64 on the same GPU (list-order
+    plans, one qx_propagate each)."""
+    import torch
+
+    reqs = W.serving_stream(7, count=count, rate_hz=2000.0)
+    # the client's marshalling is done before the clock starts
+    arrays = [qx.instr_array(instrs) for _, _, instrs in reqs]
+    budget = 64 << 30
+    rates = [rate_hz] if rate_hz > 0 else [2000.0, 8000.0, 32000.0, 0.0]
+    sweep = [_serve_once(qx, reqs, arrays, r, slots, budget, warm=16) for r in rates]
     # one at a time, FP64, no overlap: the first baseline_count circuits
     torch.cuda.synchronize()
     b0 = time.perf_counter()
@@ -381,12 +519,10 @@ def serving_bench(qx, W, count, rate_hz, slots=8, baseline_count=300):
         r.free()
     torch.cuda.synchronize()
     base = baseline_count / (time.perf_counter() - b0)
-    lat.sort()
-    return {"requests": count, "rate_hz": rate_hz, "slots": slots, "precision": 32,
-            "hbm_budget_bytes": 64 << 30,
-            "served_circuits_per_s": count / wall, "wall_s": wall,
-            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "retried_exclusive": st["retried_exclusive"], "failed": st["failed"],
+    sat = max(x["circuits_per_s"] for x in sweep)
+    return {"requests": count, "slots": slots, "precision": 32, "hbm_budget_bytes": budget,
+            "arrivals": "Poisson (seeded), the stream's gaps scaled to each rate",
+            "sweep": sweep, "saturated_circuits_per_s": sat,
             "one_at_a_time_fp64_circuits_per_s": base,
             "one_at_a_time_sample": f"first {baseline_count} requests of the same stream"}
 
@@ -447,101 +583,125 @@ def adjoint_bench(qx, W, steps, warmup=3):
             "timing": "host clock around synchronised calls, median of steps"}
 
 
-def fp32_bench(qx, plan, flush, steps, fp64_step_ms, warmup=3):
-    """The main workload with FP32 weights and compensated arithmetic: time
-    per step (CUDA events, L2 flushed) and the largest relative error against
-    the FP64 result over three heavy generators (|w| > 1e-6)."""
+def fp32_bench(qx, W, flush, steps, fp64_step_ms, warmup=3):
+    """FP32 weights with compensated arithmetic on the headline workload (and
+    fan_in_heavy_n50): device time per step (CUDA events, L2 flushed), speed
+    against FP64, and the largest relative error against the FP64 oracle's
+    closed form (headline: every coefficient is a product of per-qubit cos /
+    sin factors times the sign of a Clifford-only propagation) and against
+    the FP64 path (fan_in_heavy_n50)."""
     import torch
 
-    times = []
-    for k in range(warmup + steps):
-        flush()
-        s = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s)
-        r = qx.propagate(plan, precision=32)
-        e1.record(s)
-        torch.cuda.synchronize()
-        if k >= warmup:
-            times.append(e0.elapsed_time(e1))
-        if k < warmup + steps - 1:
-            r.free()
-    st = r.stats()
+    out = {"precision": 32, "l2": "flushed between timed steps"}
+    n, instrs = W.fan_in_deep(1)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(warmup):
+        qx.propagate(plan, precision=32, eps=EPS).free()
+    ms, res = timed_steps(lambda: qx.propagate(plan, precision=32, eps=EPS), steps, flush)
+    for r in res[:-1]:
+        r.free()
+    r32 = res[-1]
+    st = r32.stats()
+    # error against the exact coefficients on sampled strings of 4 generators
+    thetas = [th for g, _, _, th in instrs if g == "RZ"]
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    ref64 = qx.propagate(plan, eps=EPS)
+    for g in (20, 41, 77, 99):
+        strings, w = ref64.export_strings(g)
+        pick = rng.choice(len(strings), size=256, replace=False)
+        qs = [strings[int(k)] for k in pick]
+        got = r32.coeff_batch([g] * len(qs), qs)
+        for s_, v in zip(qs, got):
+            exact = np.prod([np.cos(thetas[q]) if s_[q] == "X" else np.sin(thetas[q])
+                             for q in range(20)])
+            sign = np.sign(ref64.coeff(g, s_))
+            want = sign * abs(exact)
+            worst = max(worst, abs(v - want) / abs(want))
+    ref64.free()
+    kt = None
     flush()
-    kt = qx.propagate(plan, precision=32, kernel_timing=True).stats()["kernels"]
-    ref = qx.propagate(plan)
+    rk = qx.propagate(plan, precision=32, eps=EPS, kernel_timing=True)
+    kt = {k: round(d["ms"], 4) for k, d in rk.stats()["kernels"].items() if d["launches"]}
+    rk.free()
+    r32.free()
+    m = statistics.median(ms)
+    out["fan_in_deep_n100"] = {
+        "ms_per_step": m, "term_updates_per_s": st["term_updates"] / (m / 1e3),
+        "children_per_s": st["children"] / (m / 1e3),
+        "speedup_vs_fp64": fp64_step_ms / m, "max_rel_error_vs_exact": worst,
+        "error_sample": "256 sampled strings of generators 20, 41, 77, 99 against "
+                        "sign x prod(|cos|, |sin|) in FP64",
+        "kernel_ms": kt}
+    del plan
+    # the merge-heavy secondary workload
+    n, instrs = W.fan_in_heavy(1)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(warmup):
+        qx.propagate(plan, precision=32).free()
+        qx.propagate(plan).free()
+    ms32, res = timed_steps(lambda: qx.propagate(plan, precision=32), steps, flush)
+    for r in res[:-1]:
+        r.free()
+    r32 = res[-1]
+    ms64, res64 = timed_steps(lambda: qx.propagate(plan), steps, flush)
+    for r in res64[:-1]:
+        r.free()
+    ref = res64[-1]
     worst = 0.0
     for g in (16, 33, 49):
-        a, b = r.export_dict(g), ref.export_dict(g)
+        a, b = r32.export_dict(g), ref.export_dict(g)
         assert a.keys() == b.keys()
         for key, w in b.items():
             if abs(w) > 1e-6:
                 worst = max(worst, abs(a[key] - w) / abs(w))
-    ms = statistics.median(times)
-    return {"precision": 32, "ms_per_step": ms, "term_updates_per_s": st["term_updates"] / (ms / 1e3),
-            "speedup_vs_fp64": statistics.median(fp64_step_ms) / ms,
-            "max_rel_error_vs_fp64": worst, "error_sample": "generators 16, 33, 49, |w| > 1e-6",
-            "kernel_ms": {k: round(d["ms"], 4) for k, d in kt.items() if d["launches"]},
-            "l2": "flushed between timed steps"}
+    m32, m64 = statistics.median(ms32), statistics.median(ms64)
+    out["fan_in_heavy_n50"] = {"ms_per_step": m32, "fp64_ms_per_step": m64,
+                               "speedup_vs_fp64": m64 / m32, "max_rel_error_vs_fp64": worst,
+                               "error_sample": "generators 16, 33, 49, |w| > 1e-6"}
+    r32.free()
+    ref.free()
+    return out
 
 
-def large_bench(qx, W, flush, steps, peak, warmup=3):
-    """The HBM-scale configuration: fan_in_deep_n100 (n = 100, 20 RZ on 20
-    fan-out qubits spread over 100,000 gates, 80 x 2^20 + 40 = 83,886,120
-    final terms, 3.4 GB of FP64 terms).  Device time per propagation (CUDA
-    events) and the dominant kernel class's achieved bandwidth (algorithmic
-    bytes over its CUDA-event time, QX_FLAG_KERNEL_TIMING)."""
-    import torch
-
-    n, instrs = W.fan_in_deep(1)
-    circ = qx.load_circuit(n, instrs)
-    plan = qx.group_ops(circ)
-    dag_ms = []
-    dplan = qx.group_ops(circ, dag=True)
-    for k in range(warmup + steps):  # the same circuit with qubit-wise grouping
-        flush()
-        s = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s)
-        r = qx.propagate(dplan)
-        e1.record(s)
-        torch.cuda.synchronize()
-        if k >= warmup:
-            dag_ms.append(e0.elapsed_time(e1))
-        dag_terms = r.nterms
+def heavy50_bench(qx, W, flush, steps, peak, fp64_peak, warmup=3):
+    """fan_in_heavy_n50 (n = 50, 2000 gates, 16 T and 16 RZ on 16 fan-out
+    qubits, 34 x 65,536 + 16 x 2 = 2,228,256 final terms, 62 MB): the
+    merge-heavy case.  Its 16 merge wires run in place over 53 MB of weights
+    that stay in L2 between wires, so their survey bytes are not DRAM bytes;
+    the wire kernel is bound by the FP64 unit and is reported against the
+    measured FP64 FMA rate as well."""
+    n, instrs = W.fan_in_heavy(1)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(warmup):
+        qx.propagate(plan).free()
+    ms, res = timed_steps(lambda: qx.propagate(plan), steps, flush)
+    st = res[0].stats()
+    for r in res:
         r.free()
-    del dplan
-    times, st = [], None
-    for k in range(warmup + steps):
+    kst = []
+    for _ in range(steps):
         flush()
-        s = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s)
         r = qx.propagate(plan, kernel_timing=True)
-        e1.record(s)
-        torch.cuda.synchronize()
-        if k >= warmup:
-            times.append(e0.elapsed_time(e1))
-            st = r.stats()
-        nterms = r.nterms
+        kst.append(r.stats())
         r.free()
-    ms = statistics.median(times)
-    kern = st["kernels"]
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    d = kern[dom]
+    kc = kernel_classes(kst)
+    dom = max(kc, key=lambda k: kc[k]["ms"])
+    d = kc[dom]
     achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
-    return {"workload": "fan_in_deep_n100", "final_terms": nterms,
-            "term_bytes": nterms * 44, "steps": steps, "warmup": warmup,
-            "propagate_ms": ms, "term_updates_per_s": st["term_updates"] / (ms / 1e3),
-            "children_per_s": st["children"] / (ms / 1e3),
-            "dominant_kernel": dom, "dominant_share": d["ms"] / sum(v["ms"] for v in kern.values()),
-            "dominant_achieved_gbs": achieved, "dominant_frac_of_peak": achieved / peak,
-            "kernel_ms": {k: round(v["ms"], 3) for k, v in kern.items() if v["ms"] > 0},
-            "qubit_wise_grouping": {"propagate_ms": statistics.median(dag_ms),
-                                    "final_terms": dag_terms},
+    m = statistics.median(ms)
+    return {"workload": "fan_in_heavy_n50", "final_terms": st["final_terms"],
+            "ms_per_step": m, "term_updates_per_s": st["term_updates"] / (m / 1e3),
+            "children_per_s": st["children"] / (m / 1e3),
+            "step_alg_gbs": st["alg_bytes"] / (m / 1e3) / 1e9,
+            "dominant_kernel": dom, "dominant_share": d["ms"] / sum(v["ms"] for v in kc.values()),
+            "dominant_alg_gbs": achieved, "dominant_alg_frac": achieved / peak,
+            "dominant_note": "L2-resident: the wires' weights stay in L2 between wires, so "
+                             "these survey bytes exceed the DRAM bytes (ncu traffic below)",
+            "traffic": ncu_traffic(dom, "fan_in_heavy_n50"),
+            "fp64": fp64_view(dom, d, st["final_terms"], fp64_peak),
+            "kernel_ms_per_step": {k: round(v["ms"] / steps, 4) for k, v in kc.items()
+                                   if v["launches"]},
             "l2": "flushed between timed steps"}
 
 
@@ -642,14 +802,6 @@ def xyz_chain_bench(qx, W, repeats_list, flush, steps=5, warmup=3, n=12, layers=
     return res
 
 
-def plan_updates_per_gen(qx, plan, n):
-    """Term updates of one heavy generator (Z_16) in the library's own accounting."""
-    r = qx.propagate(plan, gens=(16, 17))
-    u = r.stats()["term_updates"]
-    r.free()
-    return u
-
-
 # --------------------------------------------------------------------------- oracle
 
 def operator_bounds(instrs):
@@ -709,19 +861,46 @@ class OracleStepper:
         return done, time.perf_counter() - t0
 
 
-def cpu_baseline(lib_updates_per_gen, budget_s):
+def _oracle_run(gen, budget_s, out, k):
     from paper_2505_03307_gb300 import workloads as W
-    n, instrs = W.fan_in_heavy(1)
-    st = OracleStepper(n, instrs, 16)
+    n, instrs = W.fan_in_deep(1)
+    st = OracleStepper(n, instrs, gen)
     done, secs = 0, 0.0
     while secs < budget_s:
         u, s = st.step(2_000_000)
         done += u
         secs += s
-    return {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"generator Z_16 (a 65,536-term generator) of the same circuit, gate by gate "
-                      f"through whole operators for {secs:.1f} s ({done} term updates); "
-                      f"single thread"}
+    out[k] = (done, secs)
+
+
+def cpu_baseline(budget_s):
+    """The oracle on the host cores: one thread advancing heavy generator
+    Z_20 of the headline circuit gate by gate (through whole operators, term
+    updates counted per operator like the library), and one thread per core,
+    each on its own heavy generator (generators are independent), for about
+    budget_s seconds each."""
+    cores = os.cpu_count() or 1
+    one = [None]
+    _oracle_run(20, budget_s, one, 0)
+    single = one[0][0] / one[0][1]
+    res = [None] * cores
+    ths = [threading.Thread(target=_oracle_run, args=(20 + (k % 80), budget_s, res, k))
+           for k in range(cores)]
+    t0 = time.perf_counter()
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    wall = time.perf_counter() - t0
+    allc = sum(r[0] for r in res) / wall
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": cores,
+            "single_thread": {"value": single, "cores": 1,
+                              "sample": f"generator Z_20, {one[0][1]:.1f} s ({one[0][0]} term "
+                                        f"updates)"},
+            "sample": f"one thread per core, thread k advancing generator Z_(20 + k mod 80) of "
+                      f"the same circuit gate by gate through whole operators for ~{budget_s:.0f} "
+                      f"s ({wall:.1f} s wall); term updates counted per operator"}
 
 
 def run_reference(args):
@@ -732,8 +911,8 @@ def run_reference(args):
     from paper_2505_03307_gb300 import workloads as W
 
     O.build()
-    n, instrs = W.fan_in_heavy(1)
-    st = OracleStepper(n, instrs, 16)
+    n, instrs = W.fan_in_deep(1)
+    st = OracleStepper(n, instrs, 20)
     budget = 3_000_000
     for _ in range(args.warmup):
         st.step(budget)
@@ -743,15 +922,16 @@ def run_reference(args):
         done += u
         times.append(s)
     value = done / sum(times)
+    sample = ("each step: about 3M term updates of generator Z_20, gate by gate through whole "
+              "operators of the same circuit; single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded circuits; no dataset)", "config": dict(CONFIG),
+        "data": "synthetic (seeded circuits; no dataset)",
+        "config": dict(CONFIG, parallelism="single"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: about 3M term updates of generator Z_16 "
-                                   "(65,536 terms at the heavy end), gate by gate through whole "
-                                   "operators of the same circuit; single thread"},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -763,16 +943,22 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--split", default="circuits", choices=["circuits", "generators"],
+                    help="N > 1: independent circuits per rank (weak) or one circuit split "
+                         "by generator range (strong)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2000,
-                    help="requests of the serving stream (0: skip; the full stream has 10000)")
-    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (Hz)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="seconds of oracle work per CPU-baseline leg")
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests of the serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="Poisson arrival rate (Hz) of the serving leg; 0: a sweep up to saturation")
     ap.add_argument("--adjoint-steps", type=int, default=5,
                     help="timed steps of the gradient leg (0: skip)")
     ap.add_argument("--fp32-steps", type=int, default=5,
-                    help="timed steps of the FP32 leg (0: skip)")
-    ap.add_argument("--large-steps", type=int, default=3,
-                    help="timed steps of the 84M-term fan_in_deep_n100 leg (0: skip)")
+                    help="timed steps of the FP32 legs (0: skip)")
+    ap.add_argument("--heavy-steps", type=int, default=10,
+                    help="timed steps of the fan_in_heavy_n50 leg (0: skip)")
     ap.add_argument("--grouping-steps", type=int, default=5,
                     help="timed steps per case of the grouping comparison (0: skip)")
     ap.add_argument("--xyz-repeats", default="100,1000,10000,100000",

@@ -371,34 +371,51 @@ qx_status qx_tape_info(const qx_tape* t, size_t* nrot, size_t* nops, size_t* hel
                        size_t* held_bytes);
 
 /* ---- Serving: a request loop with continuous batching ---------------------
- * Circuits are submitted as they arrive and propagated by `slots` host
- * workers, each with its own CUDA stream, so the device work of several
- * circuits overlaps; a request starts as soon as a slot is free, in arrival
- * order.  Admission by memory follows the feasibility region of Sec. IV
- * (term storage bounded by M_max): each slot may use hbm_budget / slots bytes
- * of term storage; a request that needs more is run again alone with the
- * whole budget once the other slots have drained (0 = no limit).
- * Results are the same as qx_propagate of the circuit alone. */
+ * Circuits are submitted as they arrive.  Host planner threads turn each into
+ * a push-through plan (as qx_group_ops_pushthrough: its non-Clifford gates as
+ * Pauli rotations, then one Clifford pass) and reserve for it an upper bound
+ * on its term storage (each rotation at most doubles each generator).
+ * `slots` engine threads, each with its own CUDA stream, admit planned
+ * requests in arrival order into a batch while the reservations of all
+ * running batches stay within hbm_budget (the memory side of the feasibility
+ * region of Sec. IV, term storage bounded by M_max; 0 = no limit), and
+ * propagate the batch in one term store: every generator of every request has
+ * its own id, each rotation step is one launch sequence for the whole batch,
+ * and the final passes run in one launch.  Requests that arrive while batches
+ * run join the next batch as soon as an engine and memory are free, and
+ * several batches run on the device at once.  A request whose bound alone
+ * exceeds hbm_budget runs by itself once no batch runs, with hbm_budget
+ * enforced on its exact sizes (QX_EBUDGET if it needs more).
+ * Each result equals qx_propagate of the circuit's push-through plan alone:
+ * the same strings and weights (the batched kernels do the same arithmetic
+ * per term); the order of its terms may differ. */
 typedef struct qx_server qx_server;
 
 typedef struct {
-  int slots;          /* concurrent requests (host workers / CUDA streams), 1..256 */
-  size_t hbm_budget;  /* bytes of term storage for all slots together; 0 = unlimited */
+  int slots;          /* engines (batches on the device at once), 1..256 */
+  size_t hbm_budget;  /* bytes of term storage reserved by all running batches; 0 = unlimited */
   int precision;      /* 64 or 32, as qx_prop_opts.precision */
   double eps;         /* as qx_prop_opts.eps */
   size_t max_queue;   /* waiting requests accepted; 0 = unlimited (else QX_ECAP) */
+  int max_batch;      /* requests per batch, >= 1; 0 = 256 */
 } qx_server_opts;
 
 typedef struct {
-  uint64_t completed, failed, retried_exclusive, queued, running;
+  uint64_t completed, failed;
+  uint64_t alone;     /* requests whose bound exceeded hbm_budget, run by themselves */
+  uint64_t queued, running;       /* waiting requests; batches on the device */
   double p50_ms, p99_ms, max_ms;  /* latency from submission to completion */
+  uint64_t batches;   /* batches run */
+  double mean_batch;  /* requests per batch */
+  uint64_t peak_reserved;  /* largest bytes reserved at once by running batches */
 } qx_serve_stats;
 
-/* Defaults: 4 slots, no budget, precision 64, eps 0, unbounded queue. */
+/* Defaults: 2 engines, no budget, precision 64, eps 0, unbounded queue,
+ * batches of up to 256 requests. */
 void qx_server_default_opts(qx_server_opts* o);
-/* Starts the workers on the current device. */
+/* Starts the planners and engines on the current device. */
 qx_status qx_server_create(const qx_server_opts* o, qx_server** out);
-/* Queues a circuit (copied; validated when it runs); *ticket identifies it. */
+/* Queues a circuit (copied; validated when it is planned); *ticket identifies it. */
 qx_status qx_server_submit(qx_server* s, int n, const qx_instr* ins, size_t m, uint64_t* ticket);
 /* *done = 1 once the request has finished (with or without error). */
 qx_status qx_server_poll(qx_server* s, uint64_t ticket, int* done);
@@ -407,8 +424,8 @@ qx_status qx_server_poll(qx_server* s, uint64_t ticket, int* done);
  * for once. */
 qx_status qx_server_wait(qx_server* s, uint64_t ticket, qx_result** out, double* latency_ms);
 qx_status qx_server_stats(qx_server* s, qx_serve_stats* st);
-/* Finishes running requests, fails queued ones, stops the workers and frees
- * results that were never waited for. */
+/* Finishes running batches, fails waiting requests, stops the threads and
+ * frees results that were never waited for. */
 void qx_server_destroy(qx_server* s);
 
 /* One-qubit expansion with index-based accumulation that allocates nothing.

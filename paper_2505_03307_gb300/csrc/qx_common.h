@@ -48,6 +48,7 @@ struct CliffPass {
   std::vector<uint64_t> tab_xz;  // [chunks][1 << 2cb][2W]: x words then z words
   std::vector<uint8_t> tab_e;    // [chunks][1 << 2cb]
   bool use_table = false;        // device applies tab_* (else the gate list)
+  uint64_t support[kMaxWords] = {0, 0};  // qubits some gate of the pass acts on
 };
 
 // A fan-out qubit of a one-qubit operator: a 3x3 table that is not a signed
@@ -63,7 +64,37 @@ struct FanQubit {
 struct FanStep {
   std::vector<FanQubit> qs;  // increasing qubit order
   size_t op_index;           // position of the U operator in the chain
+  // For the last fan-out step of a plan whose Clifford passes before and
+  // after it both act on other qubits than its wires: index into
+  // qx_plan::aux_passes of the two passes composed (before, then after),
+  // which the step may apply to each parent in one go; -1 otherwise.
+  int pre_tail = -1;
 };
+
+// Whether pass pc acts only on qubits other than the wires of fan step fs (the
+// two then commute: conjugations on disjoint qubits).
+inline bool pass_disjoint(const CliffPass& pc, const FanStep& fs) {
+  for (const FanQubit& f : fs.qs)
+    if ((pc.support[f.q >> 6] >> (f.q & 63)) & 1) return false;
+  return true;
+}
+
+// Fan-out steps that the fused expansion takes: at most kSmallMaxWires wires
+// and at most kSmallMaxChildren children per parent (the product over the
+// wires of their largest row's entry count).
+constexpr int kSmallMaxWires = 8;
+constexpr int kSmallMaxChildren = 16;
+inline bool small_fan_step(const FanStep& fs) {
+  if (fs.qs.empty() || fs.qs.size() > size_t(kSmallMaxWires)) return false;
+  int prod = 1;
+  for (const FanQubit& f : fs.qs) {
+    int m = 1;
+    for (int a = 0; a < 3; ++a) m = f.nnz[a] > m ? f.nnz[a] : m;
+    prod *= m;
+    if (prod > kSmallMaxChildren) return false;
+  }
+  return true;
+}
 
 // A Pauli rotation exp(-i phi P / 2) as a device step: a string Q that
 // anticommutes with P becomes cos phi Q + sin phi (i Q P), and i Q P = +-(Q xor P).
@@ -108,6 +139,8 @@ struct qx_plan {
   // in increasing qubit order (every other wire's table is the identity)
   std::vector<std::vector<std::pair<int, qx::Table3>>> luts;
   std::vector<qx::CliffPass> passes;
+  // composed passes that no program step names (FanStep::pre_tail)
+  std::vector<qx::CliffPass> aux_passes;
   std::vector<qx::FanStep> fans;
   std::vector<qx::RotStep> rots;
   std::vector<qx::Step> program;
@@ -125,4 +158,19 @@ void free_plan_device(qx_plan* p);
 void result_set_stream(qx_result* r, void* stream);
 // Applies pass `pc` to one string on the host with the same tables the device uses.
 void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z, int* sign);
+// Push-through plan of a circuit (qx_group_ops_pushthrough).
+qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out);
+
+// Batched propagation (the serving loop): the plans, all push-through plans
+// of one word count, propagate together in one term store on `stream`
+// (allocations stream-ordered on it), each request's generators with their own
+// ids; result r is request r's, as qx_propagate of its plan alone would give
+// (the same strings and weights; term order may differ).  budget bounds the
+// batch's term storage at every step (0: none).  On error no result is set.
+struct BatchRequest {
+  const qx_plan* plan = nullptr;
+  qx_result* result = nullptr;
+};
+qx_status batch_propagate(std::vector<BatchRequest>& reqs, int precision, double eps,
+                          size_t budget, void* stream);
 }  // namespace qx

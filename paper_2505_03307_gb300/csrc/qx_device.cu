@@ -20,6 +20,8 @@
 
 #include "qx_common.h"
 #include "qx_kernels.cuh"
+#include "qx_expand_fused.cuh"
+#include "qx_batch.cuh"
 
 using namespace qx;
 using namespace qx::dev;
@@ -158,6 +160,7 @@ struct qx_plan_device {
     uint64_t live = 0;                 // chunks with a qubit some gate touches
     uint64_t idle[qx::kMaxWords] = {};  // qubits of the other chunks
   };
+  // the plan's passes, then its aux_passes (index passes.size() + k)
   std::vector<Pass> passes;
   size_t max_smem = 0;
 };
@@ -216,6 +219,25 @@ void free_plan_device(qx_plan* p) {
 
 namespace {
 
+// Chunks of a table-form pass that some gate touches (live) and the qubits
+// no gate touches (idle: their letters pass through).
+void pass_geometry(const CliffPass& pc, int n, uint64_t* live, uint64_t* idle) {
+  *live = 0;
+  for (int k = 0; k < kMaxWords; ++k) idle[k] = 0;
+  for (int ch = 0; ch < pc.chunks; ++ch) {
+    bool any = false;
+    for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
+      const int q = ch * pc.chunk_bits + b2;
+      if (q >= n) continue;
+      if ((pc.support[q >> 6] >> (q & 63)) & 1)
+        any = true;
+      else
+        idle[q >> 6] |= 1ull << (q & 63);
+    }
+    if (any) *live |= 1ull << ch;
+  }
+}
+
 qx_status ensure_plan_device(const qx_plan* cp, int device) {
   auto* p = const_cast<qx_plan*>(cp);
   if (p->dev && p->dev->device == device) return QX_OK;
@@ -224,12 +246,14 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
   if (!d) return fail(QX_ENOMEM, "host allocation failed");
   d->device = device;
   // one contiguous upload: [ops of every pass][tables of every pass]
-  std::vector<size_t> off_ops(p->passes.size()), off_tab(p->passes.size()),
-      off_e(p->passes.size());
+  std::vector<const CliffPass*> all;
+  for (const CliffPass& pc : p->passes) all.push_back(&pc);
+  for (const CliffPass& pc : p->aux_passes) all.push_back(&pc);
+  std::vector<size_t> off_ops(all.size()), off_tab(all.size()), off_e(all.size());
   size_t bytes = 0;
   auto align = [](size_t v) { return (v + 255) & ~size_t(255); };
-  for (size_t i = 0; i < p->passes.size(); ++i) {
-    const CliffPass& pc = p->passes[i];
+  for (size_t i = 0; i < all.size(); ++i) {
+    const CliffPass& pc = *all[i];
     off_ops[i] = bytes;
     bytes = align(bytes + pc.ops.size() * 4);
     off_tab[i] = bytes;
@@ -238,8 +262,8 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
     bytes = align(bytes + pc.tab_e.size());
   }
   std::vector<unsigned char> host(std::max<size_t>(bytes, 1));
-  for (size_t i = 0; i < p->passes.size(); ++i) {
-    const CliffPass& pc = p->passes[i];
+  for (size_t i = 0; i < all.size(); ++i) {
+    const CliffPass& pc = *all[i];
     if (!pc.ops.empty()) std::memcpy(&host[off_ops[i]], pc.ops.data(), pc.ops.size() * 4);
     if (!pc.tab_xz.empty()) std::memcpy(&host[off_tab[i]], pc.tab_xz.data(), pc.tab_xz.size() * 8);
     if (!pc.tab_e.empty()) std::memcpy(&host[off_e[i]], pc.tab_e.data(), pc.tab_e.size());
@@ -257,8 +281,8 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
   }
   d->base = base;
   auto* b = static_cast<unsigned char*>(base);
-  for (size_t i = 0; i < p->passes.size(); ++i) {
-    const CliffPass& pc = p->passes[i];
+  for (size_t i = 0; i < all.size(); ++i) {
+    const CliffPass& pc = *all[i];
     qx_plan_device::Pass dp;
     dp.ops = reinterpret_cast<const uint32_t*>(b + off_ops[i]);
     dp.nops = int(pc.ops.size());
@@ -269,29 +293,7 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
     dp.use_table = pc.use_table;
     dp.identity = pc.identity;
     dp.smem = pc.use_table ? pc.tab_xz.size() * 8 + pc.tab_e.size() : pc.ops.size() * 4;
-    if (pc.use_table) {
-      uint64_t touched[kMaxWords] = {};
-      for (const uint32_t op : pc.ops) {
-        const int q0 = int((op >> 2) & 127), q1 = int((op >> 9) & 127);
-        touched[q0 >> 6] |= 1ull << (q0 & 63);
-        if ((op & 3) != kOpPerm) touched[q1 >> 6] |= 1ull << (q1 & 63);
-      }
-      for (int ch = 0; ch < pc.chunks; ++ch) {
-        bool any = false;
-        for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
-          const int q = ch * pc.chunk_bits + b2;
-          if (q < p->n && ((touched[q >> 6] >> (q & 63)) & 1)) any = true;
-        }
-        if (any) {
-          dp.live |= 1ull << ch;
-        } else {
-          for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
-            const int q = ch * pc.chunk_bits + b2;
-            if (q < p->n) dp.idle[q >> 6] |= 1ull << (q & 63);
-          }
-        }
-      }
-    }
+    if (pc.use_table) pass_geometry(pc, p->n, &dp.live, dp.idle);
     d->max_smem = std::max(d->max_smem, dp.smem);
     d->passes.push_back(dp);
   }
@@ -607,6 +609,24 @@ void replace_cur(Ctx& c, TermBuf nb, size_t n, int slot) {
   c.st.peak_terms = std::max<uint64_t>(c.st.peak_terms, n);
 }
 
+// Qubit masks of a table-form pass for clifford_table_map: the idle qubits
+// and, per part of the chunk range, the qubits of its live chunks.
+template <int W>
+PassMasks pass_masks(const qx_plan_device::Pass& dp, int n) {
+  PassMasks pmk{};
+  for (int k = 0; k < kMaxWords; ++k) pmk.idle[k] = dp.idle[k];
+  const int P = clifford_parts<W>();
+  for (int pp = 0; pp < P; ++pp)
+    for (int ch = pp * dp.chunks / P; ch < (pp + 1) * dp.chunks / P; ++ch) {
+      if (!((dp.live >> ch) & 1)) continue;
+      for (int b2 = 0; b2 < dp.cb; ++b2) {
+        const int q = ch * dp.cb + b2;
+        if (q < n && !((dp.idle[q >> 6] >> (q & 63)) & 1)) pmk.part[pp][q >> 6] |= 1ull << (q & 63);
+      }
+    }
+  return pmk;
+}
+
 template <int W, typename WT>
 qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   if (dp.identity || c.N == 0) return QX_OK;
@@ -616,17 +636,7 @@ qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
     // as many blocks per SM as their tables fit in shared memory
     const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (dp.smem + 1024))));
     const unsigned grid = grid_for(c.N, kThreads, c.sms, per_sm);
-    PassMasks pmk{};
-    for (int k = 0; k < kMaxWords; ++k) pmk.idle[k] = dp.idle[k];
-    const int P = clifford_parts<W>();
-    for (int pp = 0; pp < P; ++pp)
-      for (int ch = pp * dp.chunks / P; ch < (pp + 1) * dp.chunks / P; ++ch) {
-        if (!((dp.live >> ch) & 1)) continue;
-        for (int b2 = 0; b2 < dp.cb; ++b2) {
-          const int q = ch * dp.cb + b2;
-          if (q < c.n) pmk.part[pp][q >> 6] |= 1ull << (q & 63);
-        }
-      }
+    const PassMasks pmk = pass_masks<W>(dp, c.n);
     if (dp.cb == 4)
       k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(
           c.cur.view<WT>(), n_in, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk);
@@ -1451,10 +1461,265 @@ void split_fan(const Ctx& c, const FanStep& fs, const std::vector<unsigned long 
     ((any[f.q / 64] >> (f.q % 64)) & 1 ? mq : fq)->push_back(&f);
 }
 
+// Fused expansion of a small fan-out step (qx_expand_fused.cuh), in parts:
+// xs_count uploads the step's tables, writes the letter masks (gmask) and the
+// children per tile and scans them (the total lands in ncnt[2]); xs_emit
+// allocates the output for cap children and writes them, applying `fused`
+// (a Clifford pass on other qubits, or none) to each parent; xs_accept makes
+// the output current.
+struct XsPending {
+  unsigned long long* tiles = nullptr;  // span sums -> offsets; [nt]: nt; then scan scratch
+  TermBuf out;
+  size_t ntiles = 0;
+};
+
+void xs_release(Ctx& c, XsPending* xp) {
+  c.al.put(xp->tiles);
+  c.al.put(xp->out.base);
+  *xp = XsPending();
+}
+
+XsMasks xs_masks(const FanStep& fs) {
+  XsMasks mk{};
+  for (const FanQubit& f : fs.qs) {
+    mk.words |= 1u << (f.q / 64);
+    for (int a = 0; a < 3; ++a)
+      if (!f.iso[a]) mk.niso[a][f.q / 64] |= 1ull << (f.q % 64);
+  }
+  return mk;
+}
+
 template <int W, typename WT>
-qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint) {
+qx_status xs_count(Ctx& c, const FanStep& fs, XsPending* xp) {
+  Scratch& s = c.sc;
+  std::vector<FanQ> hq;
+  for (const FanQubit& f : fs.qs) hq.push_back(to_dev(f));
+  QX_TRY(h2d(c, s.fanq, hq.data(), hq.size() * sizeof(FanQ)));
+  const XsMasks mk = xs_masks(fs);
+  const size_t nt = (c.N + kXsSpan - 1) / kXsSpan;
+  const size_t n2 = (nt + kScanTile - 1) / kScanTile;
+  xp->ntiles = nt;
+  xp->tiles = static_cast<unsigned long long*>(c.al.get((nt + 2 + n2) * 8));
+  if (!xp->tiles) return fail(QX_ENOMEM, "device allocation of the expansion span sums failed");
+  const size_t G = size_t(c.G);
+  QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
+  unsigned words = 0;
+  for (int k = 0; k < W; ++k) words += (mk.words >> k) & 1;
+  const size_t warps_per_block = kXsThreads / 32;
+  c.begin(KC_COUNT);
+  k_xs_count<W, WT><<<grid_for(nt, int(warps_per_block), c.sms, 8), kXsThreads, 0, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, int(hq.size()), mk, c.eps, s.gmask, xp->tiles);
+  c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * words + 4 + (c.eps > 0.0 ? sizeof(WT) : 0)));
+  c.begin(KC_SCAN);
+  if (nt <= size_t(4) * 1024) {
+    k_scan_sums<<<1, 1024, 0, c.al.s>>>(xp->tiles, nt, s.ncnt + 2);
+    c.end(KC_SCAN, 1, uint64_t(nt) * 16);
+  } else {  // three phases over the span sums; their count sits at tiles[nt]
+    const unsigned long long ntv = nt;
+    QX_TRY(h2d(c, xp->tiles + nt, &ntv, 8));
+    unsigned long long* t2 = xp->tiles + nt + 1;
+    k_scan_tiles<<<unsigned(n2), kScanThreads, 0, c.al.s>>>(xp->tiles, xp->tiles + nt, t2);
+    k_scan_sums<<<1, 1024, 0, c.al.s>>>(t2, n2, s.ncnt + 2);
+    k_scan_add<<<unsigned(n2), kScanThreads, 0, c.al.s>>>(xp->tiles, xp->tiles + nt, t2);
+    c.end(KC_SCAN, 3, uint64_t(nt) * 8 * 3);
+  }
+  QX_TRY_CUDA(cudaGetLastError());
+  return QX_OK;
+}
+
+template <int W, typename WT, int CK>
+void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap, const XsPass& ps,
+               size_t smem) {
+  // as many blocks per SM as the fused pass's tables fit in shared memory
+  const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (smem + 3072))));
+  const unsigned grid = grid_for(xp->ntiles, kXsThreads / 32, c.sms, per_sm);
+  k_xs_emit<W, WT, CK><<<grid, kXsThreads, smem, c.al.s>>>(
+      c.cur.view<WT>(), c.sc.ncnt + c.cslot, xp->tiles, c.sc.ncnt + 2, cap, c.sc.fanq,
+      int(fs.qs.size()), xs_masks(fs), ps, c.eps, c.sc.pruned, xp->out.view<WT>());
+}
+
+template <int W, typename WT>
+qx_status xs_emit(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap,
+                  const qx_plan_device::Pass* fused) {
+  QX_TRY(alloc_terms(c.al, W, c.wtb, cap, &xp->out));
+  XsPass ps{};
+  c.begin(KC_EXPAND);
+  if (!fused || fused->identity) {
+    xs_launch<W, WT, 0>(c, fs, xp, cap, ps, 0);
+  } else if (!fused->use_table) {
+    ps.ops = fused->ops;
+    ps.nops = fused->nops;
+    xs_launch<W, WT, 1>(c, fs, xp, cap, ps, size_t(fused->nops) * 4);
+  } else {
+    ps.tab_xz = fused->tab_xz;
+    ps.tab_e = fused->tab_e;
+    ps.chunks = fused->chunks;
+    ps.live = fused->live;
+    ps.pmk = pass_masks<W>(*fused, c.n);
+    if (fused->cb == 4)
+      xs_launch<W, WT, 4>(c, fs, xp, cap, ps, fused->smem);
+    else
+      xs_launch<W, WT, 3>(c, fs, xp, cap, ps, fused->smem);
+  }
+  c.end(KC_EXPAND, 1, (c.N + cap) * (16 * W + sizeof(WT)));
+  QX_TRY_CUDA(cudaGetLastError());
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status xs_accept(Ctx& c, XsPending* xp, unsigned long long total, int nfused) {
+  const int oslot = 1 - c.cslot;
+  c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
+  c.st.children += total;
+  c.st.clifford_passes += uint64_t(nfused);
+  QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
+  c.al.put(xp->tiles);
+  replace_cur(c, xp->out, total, oslot);
+  *xp = XsPending();  // pruning (eps > 0) happened in the emission
+  return QX_OK;
+}
+
+// A small fan-out step through the fused expansion.  `pre` is the pending
+// Clifford pass before the step and `tail` the program's last pass after it
+// (both act on other qubits than the step's wires, either may be NULL);
+// pre_tail is the two composed.  *done is false when some wire needs a merge:
+// gm then holds the letter masks, `pre` has been applied and the ordinary
+// path continues.  *absorbed: the tail pass ran inside the expansion.
+template <int W, typename WT>
+qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
+                        const qx_plan_device::Pass* pre, const qx_plan_device::Pass* tail,
+                        const qx_plan_device::Pass* pre_tail,
+                        std::vector<unsigned long long>& gm, bool* done, bool* absorbed) {
+  *done = false;
+  *absorbed = false;
+  const qx_plan_device::Pass* fused = pre;
+  int nfused = pre ? 1 : 0;
+  bool uses_tail = false;
+  if (tail && !pre) {
+    fused = tail;
+    nfused = 1;
+    uses_tail = true;
+  } else if (tail && pre_tail) {
+    fused = pre_tail;
+    nfused = 2;
+    uses_tail = true;
+  }
+  XsPending xp;
+  qx_status st = xs_count<W, WT>(c, fs, &xp);
+  if (st != QX_OK) {
+    xs_release(c, &xp);
+    return st;
+  }
+  auto finish = [&](unsigned long long total) -> qx_status {
+    *done = true;
+    *absorbed = uses_tail;
+    return xs_accept<W, WT>(c, &xp, total, nfused);
+  };
+  std::vector<uint64_t> mixed;
+  std::vector<const FanQubit*> mq, fq;
+  unsigned long long total = 0;
+  bool have_gm = false;
+  const int guess = hint ? hint->kind.load(std::memory_order_relaxed) : kHintNone;
+  const unsigned long long cap = hint ? hint->total.load(std::memory_order_relaxed) : 0;
+  if (guess == kHintExpand && cap && limits_ok(c, cap)) {
+    // the last run's size, launched before the masks are read back
+    st = xs_emit<W, WT>(c, fs, &xp, cap, fused);
+    if (st == QX_ENOMEM) {  // that size does not fit now: count first
+      c.al.put(xp.out.base);
+      xp.out = TermBuf();
+      clear_error();
+      cudaGetLastError();
+      hint->streak.store(0, std::memory_order_relaxed);
+      c.st.guesses_missed++;
+    } else if (st != QX_OK) {
+      xs_release(c, &xp);
+      return st;
+    } else {
+      if (c.defer && hint->streak.load(std::memory_order_relaxed) >= 2) {
+        // checked at the end of the run (see run_fan)
+        auto* rg = static_cast<unsigned long long*>(rb_take(c, gm.size() * 8));
+        auto* rt = static_cast<unsigned long long*>(rb_take(c, 8));
+        if (rg && rt) {
+          k_fill_tail<W, WT><<<grid_for(cap, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+              xp.out.view<WT>(), c.sc.ncnt + 2, cap);
+          QX_TRY_CUDA(cudaMemcpyAsync(rg, c.sc.gmask, gm.size() * 8, cudaMemcpyDeviceToHost,
+                                      c.al.s));
+          QX_TRY_CUDA(cudaMemcpyAsync(rt, c.sc.ncnt + 2, 8, cudaMemcpyDeviceToHost, c.al.s));
+          Ctx::Deferred d;
+          d.kind = kHintExpand;
+          d.hint = hint;
+          d.fs = &fs;
+          d.expect = cap;
+          d.gm = rg;
+          d.total = rt;
+          c.deferred.push_back(std::move(d));
+          return finish(cap);
+        }
+      }
+      st = sync_read2(c, gm.data(), c.sc.gmask, gm.size() * 8, &total, c.sc.ncnt + 2, 8);
+      if (st != QX_OK) {
+        xs_release(c, &xp);
+        return st;
+      }
+      have_gm = true;
+      split_fan(c, fs, gm, &mixed, &mq, &fq);
+      if (mq.empty() && limits_ok(c, total)) {  // the guess held
+        if (total > cap) {  // more children than last time: emit again at full size
+          c.al.put(xp.out.base);
+          xp.out = TermBuf();
+          st = xs_emit<W, WT>(c, fs, &xp, total, fused);
+          if (st != QX_OK) {
+            xs_release(c, &xp);
+            return st;
+          }
+        }
+        hint->total.store(total, std::memory_order_relaxed);
+        if (total == cap) hint->streak.fetch_add(1, std::memory_order_relaxed);
+        else hint->streak.store(0, std::memory_order_relaxed);
+        c.st.guesses_held++;
+        return finish(total);
+      }
+      hint->streak.store(0, std::memory_order_relaxed);
+      c.st.guesses_missed++;
+      c.al.put(xp.out.base);
+      xp.out = TermBuf();
+    }
+  }
+  if (!have_gm) {
+    st = sync_read2(c, gm.data(), c.sc.gmask, gm.size() * 8, &total, c.sc.ncnt + 2, 8);
+    if (st != QX_OK) {
+      xs_release(c, &xp);
+      return st;
+    }
+    split_fan(c, fs, gm, &mixed, &mq, &fq);
+  }
+  if (mq.empty()) {
+    st = check_limits(c, total);
+    if (st == QX_OK) st = xs_emit<W, WT>(c, fs, &xp, total, fused);
+    if (st != QX_OK) {
+      xs_release(c, &xp);
+      return st;
+    }
+    if (hint) {
+      hint->total.store(total, std::memory_order_relaxed);
+      hint->kind.store(kHintExpand, std::memory_order_relaxed);
+    }
+    return finish(total);
+  }
+  // some wire needs a merge: the ordinary path continues from the masks (the
+  // pending pass acts on other qubits, so the masks stay valid after it)
+  xs_release(c, &xp);
+  if (pre) QX_TRY((run_pass<W, WT>(c, *pre)));
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint,
+                  const qx_plan_device::Pass* pre, const qx_plan_device::Pass* tail,
+                  const qx_plan_device::Pass* pre_tail, bool* absorbed) {
   c.st.term_updates += (ops_before + 1) * c.N;
   c.st.fan_steps++;
+  *absorbed = false;
   if (c.N == 0) return QX_OK;
   Scratch& s = c.sc;
   const size_t G = size_t(c.G);
@@ -1485,7 +1750,20 @@ qx_status run_fan(Ctx& c, const FanStep& fs, uint64_t ops_before, FanHint* hint)
   bool have_gm = false;
   // 2. the last run's outcome, launched before the masks are read back
   const int guess = hint ? hint->kind.load(std::memory_order_relaxed) : kHintNone;
-  if (guess == kHintExpand) {
+  if (small_fan_step(fs) && guess != kHintBlocks) {
+    // the fused expansion (it computes the masks itself)
+    bool done = false;
+    QX_TRY((run_fan_small<W, WT>(c, fs, hint, pre, tail, pre_tail, gm, &done, absorbed)));
+    if (done) return QX_OK;
+    have_gm = true;
+    masked = true;
+    split_fan(c, fs, gm, &mixed, &mq, &fq);
+  } else if (pre) {
+    QX_TRY((run_pass<W, WT>(c, *pre)));
+  }
+  if (have_gm) {
+    // the small path's masks decide below
+  } else if (guess == kHintExpand) {
     const unsigned long long cap = hint->total.load(std::memory_order_relaxed);
     if (cap && limits_ok(c, cap)) {
       QX_TRY(launch_mask());  // the masks decide whether a merge was needed
@@ -1706,22 +1984,12 @@ qx_status run_rot(Ctx& c, const RotStep& rs, uint64_t ops_before) {
   return QX_OK;
 }
 
-void free_scratch(Ctx& c) {
-  c.al.put(c.sc.table);
-  c.al.put(c.sc.payload);
-  c.al.put(c.sc.base);
-  c.sc = Scratch();
-}
-
-template <int W, typename WT>
-qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
-                         const double* init_w, int gen_begin, const qx_result* from,
-                         qx_result** out) {
-  const qx_plan* p = c.p;
-  // scratch: counters, masks, pruned mass, fan-out tables
-  const size_t G = size_t(c.G);
+// Scratch of a propagation over c.G generators: counters, letter masks,
+// mixed masks, pruned mass, fan-out tables.
+qx_status setup_scratch(Ctx& c) {
+  const size_t G = size_t(c.G), W = size_t(c.W);
   const size_t sz_cnt = 64, sz_gm = G * 3 * W * 8, sz_mx = G * W * 8, sz_pr = G * 8,
-               sz_fq = size_t(c.n) * sizeof(FanQ) + 3 * kMaxWords * 8;
+               sz_fq = size_t(std::max(c.n, kSmallMaxWires)) * sizeof(FanQ) + 3 * kMaxWords * 8;
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t total = al(sz_cnt) + al(sz_gm) + al(sz_mx) + al(sz_pr) + al(sz_fq);
   c.sc.base = c.al.get(total);
@@ -1739,6 +2007,23 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   c.sc.fanq = reinterpret_cast<FanQ*>(b);
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
+  return QX_OK;
+}
+
+void free_scratch(Ctx& c) {
+  c.al.put(c.sc.table);
+  c.al.put(c.sc.payload);
+  c.al.put(c.sc.base);
+  c.sc = Scratch();
+}
+
+template <int W, typename WT>
+qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
+                         const double* init_w, int gen_begin, const qx_result* from,
+                         qx_result** out) {
+  const qx_plan* p = c.p;
+  const size_t G = size_t(c.G);
+  QX_TRY(setup_scratch(c));
   // A3: initial generators (or every term of a given state)
   const size_t N0 = from ? from->N : G;
   QX_TRY(check_limits(c, N0));
@@ -1770,14 +2055,43 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   c.end(KC_INIT, 1, N0 * (16 * W + sizeof(WT) + 4) * (from ? 2 : 1));
   QX_TRY_CUDA(cudaGetLastError());
   // the program: Clifford passes and fan-out steps in circuit order
-  for (const Step& stp : p->program) {
+  // A pass right before a small fan-out step and on other qubits than its
+  // wires is left pending: the step's expansion applies it to each parent
+  // (the two commute).  The program's last pass may likewise run inside the
+  // last step's expansion.
+  const auto& prog = p->program;
+  const qx_plan_device::Pass* pending = nullptr;
+  for (size_t si = 0; si < prog.size(); ++si) {
+    const Step& stp = prog[si];
     if (stp.kind == kStepCliff) {
-      QX_TRY(run_pass<W, WT>(c, p->dev->passes[stp.index]));
+      const qx_plan_device::Pass& dp = p->dev->passes[stp.index];
+      if (!dp.identity && si + 1 < prog.size() && prog[si + 1].kind == kStepFan) {
+        const FanStep& nf = p->fans[prog[si + 1].index];
+        if (small_fan_step(nf) && pass_disjoint(p->passes[stp.index], nf)) {
+          pending = &dp;
+          continue;
+        }
+      }
+      QX_TRY(run_pass<W, WT>(c, dp));
     } else if (stp.kind == kStepRot) {
       QX_TRY(run_rot<W, WT>(c, p->rots[stp.index], stp.ops_before));
     } else {
-      QX_TRY(run_fan<W, WT>(c, p->fans[stp.index], stp.ops_before,
-                            p->dev ? &p->dev->hints[stp.index] : nullptr));
+      const FanStep& fs = p->fans[stp.index];
+      const qx_plan_device::Pass* tail = nullptr;
+      const qx_plan_device::Pass* pre_tail = nullptr;
+      if (si + 2 == prog.size() && prog[si + 1].kind == kStepCliff) {
+        const CliffPass& tp = p->passes[prog[si + 1].index];
+        if (!tp.identity && pass_disjoint(tp, fs)) {
+          tail = &p->dev->passes[prog[si + 1].index];
+          if (pending && fs.pre_tail >= 0)
+            pre_tail = &p->dev->passes[p->passes.size() + size_t(fs.pre_tail)];
+        }
+      }
+      bool absorbed = false;
+      QX_TRY(run_fan<W, WT>(c, fs, stp.ops_before, p->dev ? &p->dev->hints[stp.index] : nullptr,
+                            pending, tail, pre_tail, &absorbed));
+      pending = nullptr;
+      if (absorbed) ++si;  // the last pass ran inside the expansion
     }
   }
   c.st.term_updates += p->ops_after_last_fan * c.N;
@@ -1918,6 +2232,14 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
       cudaFuncSetAttribute(k_expand_emit<2, double>, attr, mx);
       cudaFuncSetAttribute(k_expand_emit<1, float>, attr, mx);
       cudaFuncSetAttribute(k_expand_emit<2, float>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 3>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 4>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 3>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 4>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 3>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 4>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 3>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 4>, attr, mx);
       attr_dev = dev;
     }
   }
@@ -1925,9 +2247,13 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
   if (from && (from->n != p->n || from->wtb != (opts.precision == 32 ? 4 : 8)))
     return fail(QX_EINVAL, "the initial state must have the plan's qubit count and precision");
   // Steps launched on the plan's record may leave their check to the end of
-  // the run (not with pruning, whose compaction reads counts mid-step).  A run
-  // whose deferred checks fail is repeated once with every check on the spot.
-  c.defer = opts.eps == 0.0;
+  // the run: without pruning, or when every fan-out step is small (the fused
+  // expansion prunes as it writes; a separate compaction would read counts
+  // mid-step).  A run whose deferred checks fail is repeated once with every
+  // check on the spot.
+  bool all_small = true;
+  for (const FanStep& f : p->fans) all_small = all_small && small_fan_step(f);
+  c.defer = opts.eps == 0.0 || (all_small && p->rots.empty());
   for (int attempt = 0; attempt < 2; ++attempt) {
     if (p->W == 1)
       s = opts.precision == 32 ? propagate_impl<1, float>(c, ix, iz, iw, gen_begin, from, out)
@@ -2220,7 +2546,333 @@ qx_status adjoint_dot_impl(const qx_result* m, const qx_result* lam, const int32
   return st;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched propagation of push-through plans (qx_batch.cuh): the serving loop.
+
+// One rotation step of a batch: every term applies the step's rotation of its
+// request (or passes unchanged), as run_rot does for one plan.
+template <int W, typename WT>
+qx_status run_brot(Ctx& c, const RotQ* rots, const int32_t* gen_req, const int32_t* rot_off,
+                   const int32_t* nrot, int step) {
+  const size_t N = c.N;
+  if (N == 0) return QX_OK;
+  const unsigned long long cap = std::max<unsigned long long>(64, 2ull * N);
+  const size_t ntiles = (N + kScanTile - 1) / kScanTile;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t tab_bytes = up(cap * sizeof(IndexSlot) + 16);
+  void* mem = c.al.get(tab_bytes + up((N + ntiles + 1) * 8) + up(N * 8));
+  if (!mem) return fail(QX_ENOMEM, "device allocation for a rotation step failed");
+  auto* b8 = static_cast<unsigned char*>(mem);
+  auto* tab = reinterpret_cast<IndexSlot*>(b8);
+  auto* offs = reinterpret_cast<unsigned long long*>(b8 + tab_bytes);
+  unsigned long long* tsum = offs + N;
+  auto* pidx = reinterpret_cast<long long*>(b8 + tab_bytes + up((N + ntiles + 1) * 8));
+  TermBuf out;
+  auto body = [&]() -> qx_status {
+    QX_TRY_CUDA(cudaMemsetAsync(tab, 0, cap * sizeof(IndexSlot), c.al.s));
+    QX_TRY_CUDA(cudaMemsetAsync(c.sc.err, 0, 4, c.al.s));
+    const unsigned grid = grid_for(N, kThreads, c.sms, 8);
+    const auto view = c.cur.view<WT>();
+    c.begin(KC_ROT);
+    k_index_build<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, tab, cap, c.sc.err);
+    k_brot_count<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, rots, gen_req, rot_off, nrot,
+                                                        step, tab, cap, offs, pidx);
+    k_scan_tiles<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, c.sc.ncnt + c.cslot, tsum);
+    k_scan_sums<<<1, 1024, 0, c.al.s>>>(tsum, ntiles, c.sc.ncnt + 2);
+    k_scan_add<<<unsigned(ntiles), kScanThreads, 0, c.al.s>>>(offs, c.sc.ncnt + c.cslot, tsum);
+    QX_TRY_CUDA(cudaGetLastError());
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    QX_TRY(sync_read(c, h, c.sc.ncnt, 40));
+    if (unsigned(h[4]) & kErrProbe) return fail(QX_ECAP, "a hash table ran out of probe slots");
+    const unsigned long long total = h[2];
+    QX_TRY(check_limits(c, total));
+    QX_TRY(alloc_terms(c.al, W, c.wtb, total, &out));
+    k_brot_emit<W, WT><<<grid, kThreads, 0, c.al.s>>>(view, N, rots, gen_req, rot_off, nrot, step,
+                                                       offs, pidx, out.view<WT>());
+    c.end(KC_ROT, 6, (N + total) * (16 * W + sizeof(WT)));
+    QX_TRY_CUDA(cudaGetLastError());
+    const int oslot = 1 - c.cslot;
+    QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
+    c.st.alg_bytes += (N + total) * (16 * W + sizeof(WT));
+    c.st.children += total;
+    replace_cur(c, out, total, oslot);
+    out = TermBuf();
+    return QX_OK;
+  };
+  const qx_status st = body();
+  c.al.put(mem);
+  if (st != QX_OK) {
+    c.al.put(out.base);
+    return st;
+  }
+  if (c.eps > 0.0) QX_TRY(prune_cur<W, WT>(c));
+  return QX_OK;
+}
+
+template <int W, typename WT>
+qx_status batch_impl(Ctx& c, std::vector<qx::BatchRequest>& reqs) {
+  const size_t R = reqs.size();
+  // host tables of the batch
+  std::vector<int32_t> gen_req, rot_off(R), nrot(R);
+  std::vector<uint32_t> gen_base(R);
+  std::vector<RotQ> rots;
+  std::vector<BatchPass> bps(R);
+  std::vector<uint32_t> ops;
+  std::vector<uint64_t> tabs;
+  std::vector<uint8_t> tabe;
+  int tmax = 0;
+  uint32_t G = 0;
+  for (size_t r = 0; r < R; ++r) {
+    const qx_plan* p = reqs[r].plan;
+    gen_base[r] = G;
+    for (int j = 0; j < p->n; ++j) gen_req.push_back(int32_t(r));
+    G += uint32_t(p->n);
+    rot_off[r] = int32_t(rots.size());
+    const CliffPass* last = nullptr;
+    for (const Step& stp : p->program) {
+      if (stp.kind == kStepRot) {
+        if (last) return fail(QX_EINVAL, "a batched plan must end with its only Clifford pass");
+        rots.push_back(to_dev(p->rots[size_t(stp.index)]));
+      } else if (stp.kind == kStepCliff) {
+        if (last) return fail(QX_EINVAL, "a batched plan has one Clifford pass");
+        last = &p->passes[size_t(stp.index)];
+      } else {
+        return fail(QX_EINVAL, "a batched plan has no fan-out steps (push-through plans only)");
+      }
+    }
+    nrot[r] = int32_t(rots.size()) - rot_off[r];
+    tmax = std::max(tmax, int(nrot[r]));
+    BatchPass& bp = bps[r];
+    std::memset(&bp, 0, sizeof bp);
+    if (!last || last->identity) {
+      bp.kind = 0;
+    } else if (!last->use_table) {
+      bp.kind = 1;
+      bp.ops_off = ops.size();
+      bp.nops = int(last->ops.size());
+      ops.insert(ops.end(), last->ops.begin(), last->ops.end());
+    } else {
+      bp.kind = 2;
+      if (tabs.size() & 1) tabs.push_back(0);  // 16-byte entries
+      bp.tab_off = tabs.size();
+      bp.e_off = tabe.size();
+      bp.chunks = last->chunks;
+      tabs.insert(tabs.end(), last->tab_xz.begin(), last->tab_xz.end());
+      tabe.insert(tabe.end(), last->tab_e.begin(), last->tab_e.end());
+      qx_plan_device::Pass dp;
+      dp.chunks = last->chunks;
+      dp.cb = last->chunk_bits;
+      pass_geometry(*last, p->n, &dp.live, dp.idle);
+      bp.live = dp.live;
+      bp.pmk = pass_masks<W>(dp, p->n);
+    }
+  }
+  if (rots.empty()) rots.push_back(RotQ{});
+  if (ops.empty()) ops.push_back(0);
+  if (tabs.empty()) tabs.assign(2, 0);
+  if (tabe.empty()) tabe.push_back(0);
+  c.G = int(G);
+  QX_TRY(setup_scratch(c));
+  // one upload of every table
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t o_req = 0, o_base = up(o_req + G * 4), o_roff = up(o_base + R * 4),
+               o_nrot = up(o_roff + R * 4), o_rots = up(o_nrot + R * 4),
+               o_bps = up(o_rots + rots.size() * sizeof(RotQ)),
+               o_ops = up(o_bps + R * sizeof(BatchPass)), o_tab = up(o_ops + ops.size() * 4),
+               o_e = up(o_tab + tabs.size() * 8), o_cur = up(o_e + tabe.size()),
+               o_outs = up(o_cur + size_t(G) * 8), total = up(o_outs + R * sizeof(BatchOut<WT>));
+  std::vector<unsigned char> host(total, 0);
+  std::memcpy(&host[o_req], gen_req.data(), G * 4);
+  std::memcpy(&host[o_base], gen_base.data(), R * 4);
+  std::memcpy(&host[o_roff], rot_off.data(), R * 4);
+  std::memcpy(&host[o_nrot], nrot.data(), R * 4);
+  std::memcpy(&host[o_rots], rots.data(), rots.size() * sizeof(RotQ));
+  std::memcpy(&host[o_bps], bps.data(), R * sizeof(BatchPass));
+  std::memcpy(&host[o_ops], ops.data(), ops.size() * 4);
+  std::memcpy(&host[o_tab], tabs.data(), tabs.size() * 8);
+  std::memcpy(&host[o_e], tabe.data(), tabe.size());
+  auto* dev = static_cast<unsigned char*>(c.al.get(total));
+  if (!dev) return fail(QX_ENOMEM, "device allocation of the batch tables failed");
+  struct Put {
+    Alloc* al;
+    void* p;
+    ~Put() { al->put(p); }
+  } put_dev{&c.al, dev};
+  QX_TRY_CUDA(cudaMemcpyAsync(dev, host.data(), o_cur, cudaMemcpyHostToDevice, c.al.s));
+  const auto* d_req = reinterpret_cast<const int32_t*>(dev + o_req);
+  const auto* d_base = reinterpret_cast<const uint32_t*>(dev + o_base);
+  const auto* d_roff = reinterpret_cast<const int32_t*>(dev + o_roff);
+  const auto* d_nrot = reinterpret_cast<const int32_t*>(dev + o_nrot);
+  const auto* d_rots = reinterpret_cast<const RotQ*>(dev + o_rots);
+  const auto* d_bps = reinterpret_cast<const BatchPass*>(dev + o_bps);
+  const auto* d_ops = reinterpret_cast<const uint32_t*>(dev + o_ops);
+  const auto* d_tab = reinterpret_cast<const uint64_t*>(dev + o_tab);
+  const auto* d_e = reinterpret_cast<const uint8_t*>(dev + o_e);
+  auto* d_cur = reinterpret_cast<unsigned long long*>(dev + o_cur);
+  auto* d_outs = reinterpret_cast<BatchOut<WT>*>(dev + o_outs);
+  // A3: every request's generators; then the rotation steps and the passes
+  QX_TRY(check_limits(c, G));
+  QX_TRY(alloc_terms(c.al, W, c.wtb, G, &c.cur));
+  c.N = G;
+  c.cslot = 0;
+  c.begin(KC_INIT);
+  k_batch_init<W, WT><<<(G + 127) / 128, 128, 0, c.al.s>>>(c.cur.view<WT>(), d_req, d_base, G,
+                                                           c.sc.ncnt);
+  c.end(KC_INIT, 1, uint64_t(G) * (16 * W + sizeof(WT) + 4));
+  QX_TRY_CUDA(cudaGetLastError());
+  for (int t = 0; t < tmax; ++t) {
+    c.st.fan_steps++;
+    QX_TRY((run_brot<W, WT>(c, d_rots, d_req, d_roff, d_nrot, t)));
+  }
+  if (c.N) {
+    c.begin(KC_CLIFF);
+    constexpr int CB = W == 1 ? 4 : 3;
+    k_batch_clifford<W, CB, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), c.sc.ncnt + c.cslot, d_req, d_bps, d_ops, d_tab, d_e);
+    c.end(KC_CLIFF, 1, 2ull * c.N * (16 * W + sizeof(WT)));
+    c.st.clifford_passes++;
+    QX_TRY_CUDA(cudaGetLastError());
+  }
+  // per-generator counts and norms, then each request's own buffer
+  std::vector<unsigned long long> cnt(G, 0);
+  std::vector<double> sumsq(G, 0.0), pruned(G, 0.0);
+  void* stb = c.al.get(size_t(G) * 16 + 16);
+  if (!stb) return fail(QX_ENOMEM, "device allocation failed");
+  struct Put put_stb{&c.al, stb};
+  auto* d_count = static_cast<unsigned long long*>(stb);
+  auto* d_sumsq = reinterpret_cast<double*>(d_count + G);
+  QX_TRY_CUDA(cudaMemsetAsync(stb, 0, size_t(G) * 16, c.al.s));
+  c.begin(KC_STATS);
+  if (c.N)
+    k_gen_stats<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), c.sc.ncnt + c.cslot, int(G), d_count, d_sumsq);
+  c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
+  QX_TRY_CUDA(cudaMemcpyAsync(cnt.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(pruned.data(), c.sc.pruned, G * 8, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaStreamSynchronize(c.al.s));
+  c.st.host_syncs++;
+  std::vector<TermBuf> bufs(R);
+  std::vector<size_t> nres(R, 0);
+  std::vector<unsigned long long> cursor(G);
+  std::vector<BatchOut<WT>> outs(R);
+  auto release = [&]() {
+    for (TermBuf& b : bufs) c.al.put(b.base);
+  };
+  for (size_t r = 0; r < R; ++r) {
+    const uint32_t b0 = gen_base[r], b1 = b0 + uint32_t(reqs[r].plan->n);
+    size_t run = 0;
+    for (uint32_t g = b0; g < b1; ++g) {
+      cursor[g] = run;
+      run += cnt[g];
+    }
+    nres[r] = run;
+    if (alloc_terms(c.al, W, c.wtb, run, &bufs[r]) != QX_OK) {
+      release();
+      return fail(QX_ENOMEM, "device allocation of a request's result failed");
+    }
+    outs[r].t = bufs[r].view<WT>();
+  }
+  std::memcpy(&host[o_cur], cursor.data(), size_t(G) * 8);
+  std::memcpy(&host[o_outs], outs.data(), R * sizeof(BatchOut<WT>));
+  cudaError_t e = cudaMemcpyAsync(dev + o_cur, &host[o_cur], total - o_cur,
+                                  cudaMemcpyHostToDevice, c.al.s);
+  if (e == cudaSuccess && c.N) {
+    k_batch_split<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+        c.cur.view<WT>(), c.sc.ncnt + c.cslot, d_req, d_base, d_cur, d_outs);
+    c.st.kernel_launches++;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.al.s);  // the host copy of the tables is read
+  if (e != cudaSuccess) {
+    release();
+    return fail(QX_ECUDA, std::string("batched propagation failed: ") + cudaGetErrorString(e));
+  }
+  c.tm.resolve(&c.st);
+  int device = 0;
+  cudaGetDevice(&device);
+  for (size_t r = 0; r < R; ++r) {
+    auto* res = new (std::nothrow) qx_result;
+    if (!res) {
+      for (size_t k = 0; k < r; ++k) {
+        qx_free_result(reqs[k].result);
+        reqs[k].result = nullptr;
+      }
+      for (size_t k = r; k < R; ++k) c.al.put(bufs[k].base);
+      return fail(QX_ENOMEM, "host allocation failed");
+    }
+    const int n = reqs[r].plan->n;
+    const uint32_t b0 = gen_base[r];
+    res->n = n;
+    res->W = W;
+    res->G = n;
+    res->wtb = int(sizeof(WT));
+    res->N = nres[r];
+    res->buf = bufs[r];
+    res->al = c.al;
+    res->device = device;
+    res->count.assign(cnt.begin() + b0, cnt.begin() + b0 + n);
+    res->sumsq.assign(sumsq.begin() + b0, sumsq.begin() + b0 + n);
+    res->pruned.assign(pruned.begin() + b0, pruned.begin() + b0 + n);
+    res->st = c.st;  // the batch's counters
+    res->st.final_terms = nres[r];
+    reqs[r].result = res;
+  }
+  return QX_OK;
+}
+
 }  // namespace
+
+namespace qx {
+qx_status batch_propagate(std::vector<BatchRequest>& reqs, int precision, double eps,
+                          size_t budget, void* stream) {
+  clear_error();
+  cudaGetLastError();
+  if (reqs.empty()) return QX_OK;
+  const int W = reqs[0].plan->W;
+  for (const BatchRequest& b : reqs)
+    if (!b.plan || b.plan->W != W) return fail(QX_EINVAL, "a batch needs plans of one word count");
+  if (precision != 64 && precision != 32) return fail(QX_EINVAL, "precision must be 64 or 32");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(QX_EUNSUPPORTED, "no CUDA device is available");
+  }
+  set_pool_threshold();
+  Ctx c;
+  c.p = reqs[0].plan;
+  c.n = 0;
+  for (const BatchRequest& b : reqs) c.n = std::max(c.n, b.plan->n);
+  c.W = W;
+  c.sms = device_sms();
+  c.wtb = precision == 32 ? 4 : 8;
+  c.eps = eps;
+  c.budget = budget;
+  c.al.s = static_cast<cudaStream_t>(stream);
+  c.tm.s = c.al.s;
+  c.tm.pool = &t_event_pool;
+  qx_status s;
+  if (W == 1)
+    s = precision == 32 ? batch_impl<1, float>(c, reqs) : batch_impl<1, double>(c, reqs);
+  else
+    s = precision == 32 ? batch_impl<2, float>(c, reqs) : batch_impl<2, double>(c, reqs);
+  c.al.put(c.cur.base);
+  c.cur = TermBuf();
+  free_scratch(c);
+  if (s != QX_OK) {
+    const std::string msg = qx_last_error();
+    cudaStreamSynchronize(c.al.s);
+    cudaGetLastError();
+    for (BatchRequest& b : reqs) {
+      qx_free_result(b.result);
+      b.result = nullptr;
+    }
+    return fail(s, msg);
+  }
+  return QX_OK;
+}
+}  // namespace qx
 
 extern "C" {
 

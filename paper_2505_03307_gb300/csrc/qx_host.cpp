@@ -278,6 +278,12 @@ struct ColumnTableau {
 };
 
 void build_pass_tables(CliffPass& pc, int n, int W) {
+  pc.support[0] = pc.support[1] = 0;
+  for (const uint32_t op : pc.ops) {
+    const int q0 = int((op >> 2) & 127), q1 = int((op >> 9) & 127);
+    pc.support[q0 >> 6] |= 1ull << (q0 & 63);
+    if ((op & 3) != kOpPerm) pc.support[q1 >> 6] |= 1ull << (q1 & 63);
+  }
   ColumnTableau tab(n);
   for (uint32_t op : pc.ops) tab.apply(op);
   pc.img_x.assign(size_t(2 * n) * W, 0);
@@ -560,6 +566,28 @@ std::vector<RotTerm> gate_rotation_terms(const qx_instr& g) {
   return out;
 }
 
+// When the program ends [pass a, fan step f, pass b] and both passes act on
+// other qubits than f's wires, the three commute into (b a) then f: the
+// composed pass lets f's expansion apply both to each parent once instead of
+// b to every child afterwards.
+void add_pre_tail_pass(qx_plan* p) {
+  const auto& prog = p->program;
+  const size_t m = prog.size();
+  if (m < 3 || prog[m - 1].kind != kStepCliff || prog[m - 2].kind != kStepFan ||
+      prog[m - 3].kind != kStepCliff)
+    return;
+  const CliffPass& a = p->passes[size_t(prog[m - 3].index)];
+  const CliffPass& b = p->passes[size_t(prog[m - 1].index)];
+  FanStep& f = p->fans[size_t(prog[m - 2].index)];
+  if (a.identity || b.identity || !pass_disjoint(a, f) || !pass_disjoint(b, f)) return;
+  CliffPass ab;
+  ab.ops = a.ops;
+  ab.ops.insert(ab.ops.end(), b.ops.begin(), b.ops.end());
+  build_pass_tables(ab, p->n, p->W);
+  p->aux_passes.push_back(std::move(ab));
+  f.pre_tail = int(p->aux_passes.size() - 1);
+}
+
 qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   auto* p = new (std::nothrow) qx_plan;
   if (!p) return fail(QX_ENOMEM, "host allocation failed");
@@ -659,6 +687,7 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
   p->ops_after_last_fan = ops_since_fan;
   for (auto& pc : p->passes) build_pass_tables(pc, n, p->W);
+  add_pre_tail_pass(p);
   *out = p;
   return QX_OK;
 }

@@ -393,9 +393,9 @@ __host__ __device__ constexpr int clifford_parts() {
   return W == 1 ? 3 : 2;
 }
 
-// Qubit masks of a Clifford pass for k_clifford_table: the qubits of chunks
-// that the pass leaves alone (every gate of the pass acts elsewhere), and per
-// part the qubits of its other chunks (the letters its product depends on).
+// Qubit masks of a Clifford pass for k_clifford_table: the qubits that no
+// gate of the pass acts on (idle: their letters map to themselves), and per
+// part the other qubits of its chunks (the letters its product depends on).
 struct PassMasks {
   uint64_t idle[kMaxWords];
   uint64_t part[3][kMaxWords];
@@ -403,9 +403,10 @@ struct PassMasks {
 
 // The image of a string is the product of its chunks' images, in chunk order
 // (X then Z letters within a chunk).  Three facts cut the table lookups:
-// * a chunk whose qubits no gate of the pass touches maps to itself; its
-//   letters pass through (their images have disjoint support from every other
-//   image, so they add no phase) and it is never looked up (`live`);
+// * a qubit that no gate of the pass touches maps to itself; its letter
+//   passes through (its image has disjoint support from every other image, so
+//   it adds no phase), the chunk index is taken with its bits cleared, and a
+//   chunk with no touched qubit is never looked up (`live`);
 // * the chunks split into P parts; the product of a part, with its phase, is
 //   kept per lane together with the part's letters that produced it, and
 //   reused while the lane's next string has the same letters there (strings of
@@ -435,6 +436,7 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
   int e = 0;
 #pragma unroll
   for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
+
   uint64_t ax[W], az[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) {
@@ -463,15 +465,18 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
         // for CB = 3 the chunk across the word boundary takes bits of both
         // words by selects, not by a run-time index (which would put the
         // string in local memory)
-        const uint64_t xw = (W == 1 || k == 0) ? x[0] : x[W - 1];
-        const uint64_t zw = (W == 1 || k == 0) ? z[0] : z[W - 1];
+        // the letters of touched qubits only (the mask is a kernel parameter)
+        const uint64_t iw = (W == 1 || k == 0) ? pmk.idle[0] : pmk.idle[W - 1];
+        const uint64_t xw = ((W == 1 || k == 0) ? x[0] : x[W - 1]) & ~iw;
+        const uint64_t zw = ((W == 1 || k == 0) ? z[0] : z[W - 1]) & ~iw;
         uint32_t xb, zb;
         if (CB == 4 || off + CB <= 64) {
           xb = uint32_t(xw >> off) & M;
           zb = uint32_t(zw >> off) & M;
         } else {  // k == 0 < W - 1
-          xb = uint32_t((xw >> off) | (W > 1 ? (x[W - 1] << (64 - off)) : 0)) & M;
-          zb = uint32_t((zw >> off) | (W > 1 ? (z[W - 1] << (64 - off)) : 0)) & M;
+          const uint64_t ih = W > 1 ? ~pmk.idle[W - 1] : 0ull;
+          xb = uint32_t((xw >> off) | (W > 1 ? ((x[W - 1] & ih) << (64 - off)) : 0)) & M;
+          zb = uint32_t((zw >> off) | (W > 1 ? ((z[W - 1] & ih) << (64 - off)) : 0)) & M;
         }
         const uint32_t idx = xb | (zb << CB);
         if (!idx) continue;

@@ -83,6 +83,85 @@ __device__ __forceinline__ void rot_outputs(const RotQ& r, const uint64_t* x, co
   }
 }
 
+// Term i's number of outputs (1 if it commutes with P) and its partner's
+// index (-1 when absent or not needed), for rotation r.
+template <int W, typename WT>
+__device__ __forceinline__ void rot_count_term(const RotQ& r, const TermsT<WT>& t, size_t i,
+                                               const IndexSlot* tab, unsigned long long cap,
+                                               unsigned long long* cnt, long long* pidx) {
+  uint64_t x[W], z[W];
+  load_term<W>(t, i, x, z);
+  if (!rot_anticommutes<W>(r, x, z)) {
+    cnt[i] = 1;
+    pidx[i] = -1;
+    return;
+  }
+  uint64_t xp[W], zp[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    xp[k] = x[k] ^ r.px[k];
+    zp[k] = z[k] ^ r.pz[k];
+  }
+  const uint32_t g = t.g[i];
+  long long j = -1;
+  {
+    const uint64_t h = key_hash<W>(g, xp, zp);
+    const unsigned long long tag = h | 1ull;
+    unsigned long long pos = __umul64hi(h, cap);
+    for (unsigned long long probe = 0; probe < cap; ++probe) {
+      const unsigned long long s = tab[pos].tag;
+      if (s == 0ull) break;
+      if (s == tag) {
+        const unsigned m = tab[pos].idx;
+        bool same = t.g[m] == g;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          same = same && t.x[k * t.cap + m] == xp[k] && t.z[k * t.cap + m] == zp[k];
+        if (same) {
+          j = m;
+          break;
+        }
+      }
+      if (++pos == cap) pos = 0;
+    }
+  }
+  WT own, part;
+  bool own_on, part_on;
+  rot_outputs<W, WT>(r, x, z, t.w[i], j >= 0, j >= 0 ? t.w[j] : WT(0), xp, zp, &own, &own_on,
+                     &part, &part_on);
+  cnt[i] = (own_on ? 1 : 0) + (part_on ? 1 : 0);
+  pidx[i] = j;
+}
+
+// Term i's outputs at offs[i]; r == nullptr: the term passes unchanged.
+template <int W, typename WT>
+__device__ __forceinline__ void rot_emit_term(const RotQ* r, const TermsT<WT>& t, size_t i,
+                                              const unsigned long long* offs,
+                                              const long long* pidx, const TermsT<WT>& out) {
+  uint64_t x[W], z[W];
+  load_term<W>(t, i, x, z);
+  const uint32_t g = t.g[i];
+  const WT w = t.w[i];
+  unsigned long long o = offs[i];
+  if (!r || !rot_anticommutes<W>(*r, x, z)) {
+    store_term<W>(out, o, x, z, w, g);
+    return;
+  }
+  uint64_t xp[W], zp[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    xp[k] = x[k] ^ r->px[k];
+    zp[k] = z[k] ^ r->pz[k];
+  }
+  const long long j = pidx[i];
+  WT own, part;
+  bool own_on, part_on;
+  rot_outputs<W, WT>(*r, x, z, w, j >= 0, j >= 0 ? t.w[j] : WT(0), xp, zp, &own, &own_on, &part,
+                     &part_on);
+  if (own_on) store_term<W>(out, o++, x, z, own, g);
+  if (part_on) store_term<W>(out, o, xp, zp, part, g);
+}
+
 // Per term: the number of outputs (1 if it commutes with P), and its
 // partner's index (-1 when absent or not needed).
 template <int W, typename WT>
@@ -93,50 +172,8 @@ __global__ void __launch_bounds__(256) k_rot_count(TermsT<WT> t, size_t N, RotQ 
   if (threadIdx.x == 0) r = rq;
   __syncthreads();
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
-       i += size_t(gridDim.x) * blockDim.x) {
-    uint64_t x[W], z[W];
-    load_term<W>(t, i, x, z);
-    if (!rot_anticommutes<W>(r, x, z)) {
-      cnt[i] = 1;
-      pidx[i] = -1;
-      continue;
-    }
-    uint64_t xp[W], zp[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      xp[k] = x[k] ^ r.px[k];
-      zp[k] = z[k] ^ r.pz[k];
-    }
-    const uint32_t g = t.g[i];
-    long long j = -1;
-    {
-      const uint64_t h = key_hash<W>(g, xp, zp);
-      const unsigned long long tag = h | 1ull;
-      unsigned long long pos = __umul64hi(h, cap);
-      for (unsigned long long probe = 0; probe < cap; ++probe) {
-        const unsigned long long s = tab[pos].tag;
-        if (s == 0ull) break;
-        if (s == tag) {
-          const unsigned m = tab[pos].idx;
-          bool same = t.g[m] == g;
-#pragma unroll
-          for (int k = 0; k < W; ++k)
-            same = same && t.x[k * t.cap + m] == xp[k] && t.z[k * t.cap + m] == zp[k];
-          if (same) {
-            j = m;
-            break;
-          }
-        }
-        if (++pos == cap) pos = 0;
-      }
-    }
-    WT own, part;
-    bool own_on, part_on;
-    rot_outputs<W, WT>(r, x, z, t.w[i], j >= 0, j >= 0 ? t.w[j] : WT(0), xp, zp, &own, &own_on,
-                       &part, &part_on);
-    cnt[i] = (own_on ? 1 : 0) + (part_on ? 1 : 0);
-    pidx[i] = j;
-  }
+       i += size_t(gridDim.x) * blockDim.x)
+    rot_count_term<W, WT>(r, t, i, tab, cap, cnt, pidx);
 }
 
 template <int W, typename WT>
@@ -147,30 +184,50 @@ __global__ void __launch_bounds__(256) k_rot_emit(TermsT<WT> t, size_t N, RotQ r
   if (threadIdx.x == 0) r = rq;
   __syncthreads();
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x)
+    rot_emit_term<W, WT>(&r, t, i, offs, pidx, out);
+}
+
+// Batched form (many circuits in one term store, the serving loop): term i
+// of global generator g belongs to request gen_req[g]; at step `step` it
+// applies that request's rotation rots[rot_off[req] + step] if the request
+// has more than `step` rotations, and passes unchanged otherwise.
+__device__ __forceinline__ const RotQ* batch_rot(const RotQ* rots, const int32_t* gen_req,
+                                                 const int32_t* rot_off, const int32_t* nrot,
+                                                 int step, uint32_t g) {
+  const int q = gen_req[g];
+  return step < nrot[q] ? rots + rot_off[q] + step : nullptr;
+}
+
+template <int W, typename WT>
+__global__ void __launch_bounds__(256) k_brot_count(TermsT<WT> t, size_t N, const RotQ* rots,
+                                                    const int32_t* gen_req,
+                                                    const int32_t* rot_off, const int32_t* nrot,
+                                                    int step, const IndexSlot* tab,
+                                                    unsigned long long cap,
+                                                    unsigned long long* cnt, long long* pidx) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
        i += size_t(gridDim.x) * blockDim.x) {
-    uint64_t x[W], z[W];
-    load_term<W>(t, i, x, z);
-    const uint32_t g = t.g[i];
-    const WT w = t.w[i];
-    unsigned long long o = offs[i];
-    if (!rot_anticommutes<W>(r, x, z)) {
-      store_term<W>(out, o, x, z, w, g);
+    const RotQ* r = batch_rot(rots, gen_req, rot_off, nrot, step, t.g[i]);
+    if (!r) {
+      cnt[i] = 1;
+      pidx[i] = -1;
       continue;
     }
-    uint64_t xp[W], zp[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      xp[k] = x[k] ^ r.px[k];
-      zp[k] = z[k] ^ r.pz[k];
-    }
-    const long long j = pidx[i];
-    WT own, part;
-    bool own_on, part_on;
-    rot_outputs<W, WT>(r, x, z, w, j >= 0, j >= 0 ? t.w[j] : WT(0), xp, zp, &own, &own_on, &part,
-                       &part_on);
-    if (own_on) store_term<W>(out, o++, x, z, own, g);
-    if (part_on) store_term<W>(out, o, xp, zp, part, g);
+    rot_count_term<W, WT>(*r, t, i, tab, cap, cnt, pidx);
   }
+}
+
+template <int W, typename WT>
+__global__ void __launch_bounds__(256) k_brot_emit(TermsT<WT> t, size_t N, const RotQ* rots,
+                                                   const int32_t* gen_req,
+                                                   const int32_t* rot_off, const int32_t* nrot,
+                                                   int step, const unsigned long long* offs,
+                                                   const long long* pidx, TermsT<WT> out) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += size_t(gridDim.x) * blockDim.x)
+    rot_emit_term<W, WT>(batch_rot(rots, gen_req, rot_off, nrot, step, t.g[i]), t, i, offs,
+                         pidx, out);
 }
 
 }  // namespace dev

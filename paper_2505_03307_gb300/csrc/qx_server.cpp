@@ -1,13 +1,20 @@
 // Request loop with continuous batching for many circuits (qx_server_*).
 //
-// Requests (circuits) are queued as they arrive.  `slots` host workers, each
-// with its own non-blocking CUDA stream, take requests in arrival order as
-// soon as a slot and memory are free, so the device work of several circuits
-// overlaps.  Admission follows the memory side of the feasibility region of
-// Sec. IV (n1* <= M_max / (c n)): every slot may hold hbm_budget / slots bytes of
-// term storage; a request that needs more stops with QX_EBUDGET inside its
-// share, goes back to the head of the queue marked exclusive, and runs alone
-// with the whole budget once the other slots have drained.
+// Requests (circuits) are queued as they arrive.  Planner threads turn each
+// into a push-through plan (its non-Clifford gates as Pauli rotations, then
+// one Clifford pass) and a reservation: an upper bound on the bytes of term
+// storage it can need, from its generator count and rotation count (each
+// rotation at most doubles a generator's terms).  Engine threads, each with
+// its own CUDA stream, admit planned requests in arrival order into a batch
+// while the live ledger of reserved bytes stays within hbm_budget (the memory
+// side of the feasibility region of Sec. IV, n1* <= M_max / (c n)), and
+// propagate the whole batch in one term store (qx::batch_propagate: the
+// generator id becomes (request, generator), every rotation step is one
+// launch sequence for all requests).  Requests that arrive while batches run
+// join the next batch as soon as an engine and memory are free; several
+// batches run on the device at once.  A request whose bound alone exceeds the
+// budget runs by itself once nothing else runs, with the budget enforced on
+// its exact counted sizes (QX_EBUDGET if it really needs more).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,7 +42,9 @@ struct Request {
   int n = 0;
   std::vector<qx_instr> ins;
   Clock::time_point submitted;
-  bool exclusive = false;
+  qx_plan* plan = nullptr;
+  size_t reserve = 0;  // bytes the ledger holds for it while it runs
+  int W = 1;
   bool done = false;
   qx_status status = QX_OK;
   std::string error;
@@ -48,102 +57,160 @@ struct Request {
 struct qx_server {
   qx_server_opts opts{};
   std::mutex mu;
-  std::condition_variable cv_work;  // workers: a request or a slot became available
-  std::condition_variable cv_done;  // waiters: a request finished
-  std::deque<std::shared_ptr<Request>> queue;
+  std::condition_variable cv_plan;   // planners: a request arrived
+  std::condition_variable cv_ready;  // engines: a request was planned or memory came free
+  std::condition_variable cv_done;   // waiters: a request finished
+  std::deque<std::shared_ptr<Request>> to_plan;
+  std::map<uint64_t, std::shared_ptr<Request>> ready;  // planned, by arrival
   std::map<uint64_t, std::shared_ptr<Request>> all;
-  std::vector<std::thread> workers;
+  std::vector<std::thread> planners, engines;
   uint64_t next_ticket = 1;
-  int running = 0;
-  bool exclusive_running = false;
+  size_t in_use = 0, peak_in_use = 0;  // the ledger: bytes reserved by running batches
+  int running = 0;                     // batches on the device
+  bool alone_running = false;          // a request over the budget runs by itself
   bool stopping = false;
-  uint64_t completed = 0, failed = 0, retried = 0;
+  uint64_t completed = 0, failed = 0, alone = 0, batches = 0, batched = 0;
   std::vector<double> latencies;
   int device = 0;
 };
 
 namespace {
 
-void run_one(qx_server* s, const std::shared_ptr<Request>& r, cudaStream_t stream, size_t budget) {
-  qx_circuit* c = nullptr;
-  qx_plan* p = nullptr;
-  qx_status st = qx_load_circuit(r->n, r->ins.data(), r->ins.size(), &c);
-  if (st == QX_OK) st = qx_group_ops(c, &p);
-  qx_result* res = nullptr;
-  if (st == QX_OK) {
-    qx_prop_opts o;
-    qx_default_opts(&o);
-    o.precision = s->opts.precision;
-    o.eps = s->opts.eps;
-    o.hbm_budget = budget;
-    o.stream = stream;
-    st = qx_propagate(p, &o, &res);
-  }
-  const std::string msg = st == QX_OK ? std::string() : std::string(qx_last_error());
-  qx_free_plan(p);
-  qx_free_circuit(c);
-  std::lock_guard<std::mutex> lock(s->mu);
-  s->running--;
-  if (r->exclusive) s->exclusive_running = false;
-  if (st == QX_EBUDGET && !r->exclusive && s->opts.slots > 1) {
-    // over its share: run again alone with the whole budget
-    r->exclusive = true;
-    s->queue.push_front(r);
-    s->retried++;
-    s->cv_work.notify_all();
-    return;
-  }
+// Upper bound on the bytes of term storage of a push-through plan: each of
+// its R rotations at most doubles each of its n generators (and no generator
+// holds more than 4^n - 1 strings); a rotation step holds its input, its
+// output of at most twice as many terms, the index (two 16-byte slots per
+// input term) and two 8-byte words per input term, and the results are
+// written beside the last step's output.
+size_t reservation(const qx_plan* p, int precision) {
+  size_t rot = 0;
+  for (const Step& s : p->program) rot += s.kind == kStepRot ? 1 : 0;
+  const int lg = int(std::min<size_t>(rot, 40));
+  unsigned long long per = 1ull << lg;
+  if (p->n < 20) per = std::min<unsigned long long>(per, (1ull << (2 * p->n)) - 1);
+  const size_t tb = size_t(16 * p->W + (precision == 32 ? 4 : 8) + 4);
+  return size_t(per) * size_t(p->n) * (2 * tb + 40) + size_t(p->n) * 64 + 4096;
+}
+
+void finish(qx_server* s, const std::shared_ptr<Request>& r, qx_status st, const std::string& msg,
+            qx_result* res) {
   r->status = st;
   r->error = msg;
   r->result = res;
   r->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->submitted).count();
   r->done = true;
+  qx_free_plan(r->plan);
+  r->plan = nullptr;
   if (st == QX_OK) {
     s->completed++;
     s->latencies.push_back(r->latency_ms);
   } else {
     s->failed++;
   }
-  s->cv_done.notify_all();
-  s->cv_work.notify_all();
 }
 
-void worker_main(qx_server* s) {
-  cudaSetDevice(s->device);
-  cudaStream_t stream = nullptr;
-  const bool have_stream = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
-  if (!have_stream) {
-    cudaGetLastError();
-    stream = nullptr;  // requests then fail with the library's own error (no device)
-  }
-  const size_t share = s->opts.hbm_budget ? s->opts.hbm_budget / size_t(s->opts.slots) : 0;
+void planner_main(qx_server* s) {
   while (true) {
     std::shared_ptr<Request> r;
     {
       std::unique_lock<std::mutex> lock(s->mu);
-      s->cv_work.wait(lock, [&] {
-        if (s->stopping) return true;
-        if (s->queue.empty() || s->exclusive_running) return false;
-        // an exclusive request waits until it is alone
-        return !s->queue.front()->exclusive || s->running == 0;
-      });
-      if (s->stopping && s->queue.empty()) break;
-      if (s->stopping) {  // drain: fail what is still queued
-        r = s->queue.front();
-        s->queue.pop_front();
-        r->status = QX_EINVAL;
-        r->error = "server stopped";
-        r->done = true;
-        s->failed++;
+      s->cv_plan.wait(lock, [&] { return s->stopping || !s->to_plan.empty(); });
+      if (s->to_plan.empty()) break;  // stopping
+      r = s->to_plan.front();
+      s->to_plan.pop_front();
+      if (s->stopping) {
+        finish(s, r, QX_EINVAL, "server stopped", nullptr);
         s->cv_done.notify_all();
         continue;
       }
-      r = s->queue.front();
-      s->queue.pop_front();
-      s->running++;
-      if (r->exclusive) s->exclusive_running = true;
     }
-    run_one(s, r, stream, r->exclusive ? s->opts.hbm_budget : share);
+    qx_circuit* c = nullptr;
+    qx_plan* p = nullptr;
+    qx_status st = qx_load_circuit(r->n, r->ins.data(), r->ins.size(), &c);
+    if (st == QX_OK) st = qx_group_ops_pushthrough(c, &p);
+    const std::string msg = st == QX_OK ? std::string() : std::string(qx_last_error());
+    qx_free_circuit(c);
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (st != QX_OK) {
+      finish(s, r, st, msg, nullptr);
+      s->cv_done.notify_all();
+      continue;
+    }
+    r->plan = p;
+    r->W = p->W;
+    r->reserve = reservation(p, s->opts.precision);
+    s->ready[r->ticket] = r;
+    s->cv_ready.notify_one();
+  }
+}
+
+// Whether an engine can start a batch now (the lock is held).
+bool admissible(const qx_server* s) {
+  if (s->ready.empty() || s->alone_running) return false;
+  const size_t budget = s->opts.hbm_budget;
+  const size_t first = s->ready.begin()->second->reserve;
+  if (budget && first > budget) return s->running == 0;  // runs alone
+  return !budget || s->in_use + first <= budget;
+}
+
+void engine_main(qx_server* s) {
+  cudaSetDevice(s->device);
+  cudaStream_t stream = nullptr;
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    stream = nullptr;  // requests then fail with the library's own error (no device)
+  }
+  const size_t budget = s->opts.hbm_budget;
+  const size_t max_batch = size_t(s->opts.max_batch > 0 ? s->opts.max_batch : 256);
+  while (true) {
+    std::vector<std::shared_ptr<Request>> batch;
+    size_t reserved = 0;
+    bool alone = false;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv_ready.wait(lock, [&] { return s->stopping || admissible(s); });
+      if (s->stopping) {  // fail what waits for admission; running batches finish
+        for (auto& kv : s->ready) finish(s, kv.second, QX_EINVAL, "server stopped", nullptr);
+        s->ready.clear();
+        s->cv_done.notify_all();
+        break;
+      }
+      const auto& first = s->ready.begin()->second;
+      if (budget && first->reserve > budget) {
+        alone = true;
+        batch.push_back(first);
+        s->alone_running = true;
+        s->alone++;
+      } else {
+        const int W = first->W;
+        for (const auto& kv : s->ready) {  // in arrival order, stop at the first that waits
+          const auto& r = kv.second;
+          if (r->W != W || batch.size() >= max_batch) break;
+          if (budget && (r->reserve > budget || s->in_use + reserved + r->reserve > budget)) break;
+          batch.push_back(r);
+          reserved += r->reserve;
+        }
+      }
+      for (const auto& r : batch) s->ready.erase(r->ticket);
+      s->in_use += reserved;
+      s->peak_in_use = std::max(s->peak_in_use, s->in_use);
+      s->running++;
+      s->batches++;
+      s->batched += batch.size();
+    }
+    std::vector<BatchRequest> br(batch.size());
+    for (size_t k = 0; k < batch.size(); ++k) br[k].plan = batch[k]->plan;
+    const qx_status st =
+        batch_propagate(br, s->opts.precision, s->opts.eps, alone ? budget : 0, stream);
+    const std::string msg = st == QX_OK ? std::string() : std::string(qx_last_error());
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->in_use -= reserved;
+    s->running--;
+    if (alone) s->alone_running = false;
+    for (size_t k = 0; k < batch.size(); ++k)
+      finish(s, batch[k], st, msg, st == QX_OK ? br[k].result : nullptr);
+    s->cv_done.notify_all();
+    s->cv_ready.notify_all();
   }
   if (stream) cudaStreamDestroy(stream);
 }
@@ -164,8 +231,9 @@ extern "C" {
 void qx_server_default_opts(qx_server_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
-  o->slots = 4;
+  o->slots = 2;
   o->precision = 64;
+  o->max_batch = 256;
 }
 
 qx_status qx_server_create(const qx_server_opts* o, qx_server** out) {
@@ -178,6 +246,7 @@ qx_status qx_server_create(const qx_server_opts* o, qx_server** out) {
   if (opts.precision != 64 && opts.precision != 32)
     return fail(QX_EINVAL, "precision must be 64 or 32");
   if (!(opts.eps >= 0.0)) return fail(QX_EINVAL, "eps must be >= 0");
+  if (opts.max_batch < 0) return fail(QX_EINVAL, "max_batch must be >= 0");
   auto* s = new (std::nothrow) qx_server;
   if (!s) return fail(QX_ENOMEM, "host allocation failed");
   s->opts = opts;
@@ -185,7 +254,10 @@ qx_status qx_server_create(const qx_server_opts* o, qx_server** out) {
     cudaGetLastError();
     s->device = 0;
   }
-  for (int k = 0; k < opts.slots; ++k) s->workers.emplace_back(worker_main, s);
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int planners = int(std::max(1u, std::min(8u, hw / 2)));
+  for (int k = 0; k < planners; ++k) s->planners.emplace_back(planner_main, s);
+  for (int k = 0; k < opts.slots; ++k) s->engines.emplace_back(engine_main, s);
   *out = s;
   return QX_OK;
 }
@@ -200,13 +272,13 @@ qx_status qx_server_submit(qx_server* s, int n, const qx_instr* ins, size_t m, u
   r->submitted = Clock::now();
   std::lock_guard<std::mutex> lock(s->mu);
   if (s->stopping) return fail(QX_EINVAL, "server is stopping");
-  if (s->opts.max_queue && s->queue.size() >= s->opts.max_queue)
+  if (s->opts.max_queue && s->to_plan.size() + s->ready.size() >= s->opts.max_queue)
     return fail(QX_ECAP, "request queue is full");
   r->ticket = s->next_ticket++;
   s->all[r->ticket] = r;
-  s->queue.push_back(r);
+  s->to_plan.push_back(r);
   *ticket = r->ticket;
-  s->cv_work.notify_one();
+  s->cv_plan.notify_one();
   return QX_OK;
 }
 
@@ -231,10 +303,11 @@ qx_status qx_server_wait(qx_server* s, uint64_t ticket, qx_result** out, double*
   s->all.erase(ticket);
   if (latency_ms) *latency_ms = r->latency_ms;
   if (r->status != QX_OK) return fail(r->status, "request " + std::to_string(ticket) + ": " + r->error);
-  // the worker's stream dies with the server: later work on the result goes
-  // to the default stream (the worker synchronised its stream already)
+  // the engine's stream dies with the server: later work on the result goes
+  // to the default stream (the engine synchronised its stream already)
   result_set_stream(r->result, nullptr);
   *out = r->result;
+  r->result = nullptr;
   return QX_OK;
 }
 
@@ -244,12 +317,15 @@ qx_status qx_server_stats(qx_server* s, qx_serve_stats* st) {
   std::lock_guard<std::mutex> lock(s->mu);
   st->completed = s->completed;
   st->failed = s->failed;
-  st->retried_exclusive = s->retried;
-  st->queued = s->queue.size();
+  st->alone = s->alone;
+  st->queued = s->to_plan.size() + s->ready.size();
   st->running = uint64_t(s->running);
   st->p50_ms = percentile(s->latencies, 0.50);
   st->p99_ms = percentile(s->latencies, 0.99);
   st->max_ms = s->latencies.empty() ? 0.0 : *std::max_element(s->latencies.begin(), s->latencies.end());
+  st->batches = s->batches;
+  st->mean_batch = s->batches ? double(s->batched) / double(s->batches) : 0.0;
+  st->peak_reserved = s->peak_in_use;
   return QX_OK;
 }
 
@@ -259,10 +335,14 @@ void qx_server_destroy(qx_server* s) {
     std::lock_guard<std::mutex> lock(s->mu);
     s->stopping = true;
   }
-  s->cv_work.notify_all();
-  for (auto& t : s->workers) t.join();
-  for (auto& kv : s->all)
-    if (kv.second->result) qx_free_result(kv.second->result);
+  s->cv_plan.notify_all();
+  s->cv_ready.notify_all();
+  for (auto& t : s->planners) t.join();
+  for (auto& t : s->engines) t.join();
+  for (auto& kv : s->all) {
+    qx_free_result(kv.second->result);
+    qx_free_plan(kv.second->plan);
+  }
   delete s;
 }
 

@@ -88,3 +88,16 @@ def gather_generators(local: list, begin: int, n: int):
     if any(x is None for x in out):
         raise ValueError("some generators were not computed")
     return out
+
+
+def run_generator_split(n: int, rank: int, world: int, cost, run_range):
+    """Strong scaling of one circuit: this rank's generator range, balanced by
+    `cost` (e.g. the per-generator term counts of an earlier run), is
+    propagated by ``run_range(begin, end)``, which returns one row per
+    generator of the range; the rows of all ranks are gathered in generator
+    order.  Returns (all rows, (begin, end))."""
+    begin, end = shard_generators(n, rank, world, cost)
+    rows = list(run_range(begin, end))
+    if len(rows) != end - begin:
+        raise ValueError("run_range must return one row per generator of its range")
+    return gather_generators(rows, begin, n), (begin, end)

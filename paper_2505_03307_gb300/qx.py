@@ -79,14 +79,16 @@ _SCALARS = ("K", "Kp", "term_updates", "children", "alg_bytes", "kernel_launches
 class ServerOpts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("precision", ctypes.c_int), ("eps", ctypes.c_double),
-                ("max_queue", ctypes.c_size_t)]
+                ("max_queue", ctypes.c_size_t), ("max_batch", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
-                ("retried_exclusive", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("alone", ctypes.c_uint64), ("queued", ctypes.c_uint64),
                 ("running", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
-                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
+                ("peak_reserved", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -704,14 +706,18 @@ def instr_array(instrs):
 
 class Server:
     """Request loop with continuous batching (qx_server_*): submit circuits as
-    they arrive, wait for their results; slots propagate concurrently."""
+    they arrive, wait for their results; planned requests are admitted by
+    the HBM ledger into batches that share one term store, `slots` batches at
+    a time."""
 
-    def __init__(self, slots=4, hbm_budget=0, precision=64, eps=0.0, max_queue=0):
+    def __init__(self, slots=2, hbm_budget=0, precision=64, eps=0.0, max_queue=0, max_batch=0):
         lib = load_library()
         o = ServerOpts()
         lib.qx_server_default_opts(ctypes.byref(o))
         o.slots, o.hbm_budget, o.precision = int(slots), int(hbm_budget), int(precision)
         o.eps, o.max_queue = float(eps), int(max_queue)
+        if max_batch:
+            o.max_batch = int(max_batch)
         h = _P()
         _check(lib.qx_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -99,3 +99,36 @@ def test_single_process_passthrough():
     assert qdist.gather_generators([1, 2], 0, 2) == [1, 2]
     with pytest.raises(ValueError):
         qdist.gather_generators([1], 0, 2)
+
+
+def _split_like_the_bench(rank, world):
+    """The bench's strong-scaling path (dist.run_generator_split with ranges
+    balanced by an earlier run's term counts), the oracle standing in for
+    each rank's propagation: per-generator (term count, sum of squares)."""
+    from oracle import oracle as O
+    from paper_2505_03307_gb300 import workloads as W
+    n, instrs = W.fan_in_deep(2, n=24, n_s=6, total=900)
+    cost = [len(O.as_dict(g)) for g in O.propagate(n, instrs, mode="plan")]
+
+    def run_range(b, e):
+        res = O.propagate(n, instrs, mode="plan", gens=(b, e))
+        return [(len(O.as_dict(g)), sum(w * w for w in O.as_dict(g).values())) for g in res]
+
+    rows, rng = qdist.run_generator_split(n, rank, world, cost, run_range)
+    return rows, rng, cost
+
+
+def test_generator_split_of_the_bench_gathers_every_generator():
+    from oracle import oracle as O
+    from paper_2505_03307_gb300 import workloads as W
+    n, instrs = W.fan_in_deep(2, n=24, n_s=6, total=900)
+    full = [O.as_dict(g) for g in O.propagate(n, instrs, mode="plan")]
+    results = _run(_split_like_the_bench)
+    (rows0, r0, cost), (rows1, r1, _) = results
+    assert rows0 == rows1
+    assert [c for c, _ in rows0] == [len(d) for d in full]
+    assert all(abs(s2 - 1.0) < 1e-12 for _, s2 in rows0)
+    assert r0[0] == 0 and r0[1] == r1[0] and r1[1] == n
+    # balanced by cost: each half holds about half of the terms
+    c0 = sum(cost[r0[0]:r0[1]])
+    assert abs(c0 - sum(cost) / 2) <= max(cost)
