@@ -68,7 +68,11 @@ typedef enum {
    * controlled rotations with q0 the control: CRX/CRY/CRZ(theta) apply
    * RX/RY/RZ(theta) to q1 when q0 is |1>, CP(theta) = diag(1, 1, 1, e^{i theta}). */
   QX_SWAP = 15, QX_RXX = 16, QX_RYY = 17, QX_RZZ = 18, QX_CRX = 19, QX_CRY = 20,
-  QX_CRZ = 21, QX_CP = 22
+  QX_CRZ = 21, QX_CP = 22,
+  /* Any two-qubit unitary on (q0, q1), given as a 4 x 4 matrix through
+   * qx_load_circuit_u4 (theta = index of the matrix).  Basis index
+   * 2 b(q0) + b(q1): q0 is the left tensor factor. */
+  QX_U4 = 23
 } qx_gate;
 
 /* One instruction {g, w, theta} (Sec. III.A): gate, wire(s), parameter.
@@ -157,6 +161,29 @@ void qx_default_opts(qx_prop_opts* o);
  * 0 <= q0 < n, for CX/CZ 0 <= q1 < n and q1 != q0, theta finite.
  * m may be 0.  *out is owned by the caller (qx_free_circuit). */
 qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out);
+
+/* As qx_load_circuit, for circuits with arbitrary two-qubit unitaries
+ * (QX_U4; the paper leaves gates beyond its set to future work, Sec. II.C and
+ * III.C).  mats holds nmats 4 x 4 complex matrices, 32 doubles each: row-major,
+ * real and imaginary parts interleaved, basis index 2 b(q0) + b(q1); a QX_U4
+ * instruction names its matrix by theta (an integer 0 <= theta < nmats).
+ * Each such gate is replaced in the circuit by 15 gates whose product is its
+ * matrix up to a global phase (which conjugation ignores): RZ RY RZ on each
+ * wire, RXX RYY RZZ (three commuting Pauli rotations), RZ RY RZ on each wire
+ * (the KAK decomposition, computed on the host and accepted only when the
+ * product matches the matrix to 1e-10).  The circuit then holds those gates
+ * (instruction indices of later calls refer to them).  QX_EINVAL for a matrix
+ * that is not unitary to 1e-8 or an index out of range.  Other instructions
+ * as qx_load_circuit. */
+qx_status qx_load_circuit_u4(int n, const qx_instr* ins, size_t m, const double* mats,
+                             size_t nmats, qx_circuit** out);
+
+/* The 15 gates that qx_load_circuit_u4 puts in place of one QX_U4 on
+ * (q0, q1): out receives them (15 entries), *count their number, *residual
+ * (may be NULL) the largest entry of (their product - e^{i phi} u) for the
+ * best phase phi.  u: 32 doubles as in qx_load_circuit_u4.  Host only. */
+qx_status qx_u4_decompose(const double* u, int q0, int q1, qx_instr* out, size_t* count,
+                          double* residual);
 
 /* divide_instruction + create_chain + create_LUT_1q (Algorithm 2 header lines,
  * Algorithm 1): maximal runs of one-qubit gates become U_k, maximal runs of

@@ -26,6 +26,7 @@ GATE_CODES = {
     "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
     "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
     "SWAP": 15, "RXX": 16, "RYY": 17, "RZZ": 18, "CRX": 19, "CRY": 20, "CRZ": 21, "CP": 22,
+    "U4": 23,
 }
 
 _MODES = {"gate": 0, "plan": 1, "dag": 2, "push": 3}
@@ -57,6 +58,8 @@ def _load():
                                        _c_dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _c_dbl_p,
                                        ctypes.c_int]
+            lib.oracle_run_u4.restype = ctypes.c_void_p
+            lib.oracle_run_u4.argtypes = lib.oracle_run.argtypes + [_c_dbl_p, ctypes.c_long]
             lib.oracle_run_sum.restype = ctypes.c_void_p
             lib.oracle_run_sum.argtypes = [ctypes.c_int, ctypes.c_long, _c_int_p, _c_int_p,
                                            _c_int_p, _c_dbl_p, ctypes.c_int, ctypes.c_double,
@@ -89,12 +92,26 @@ def _load():
 
 
 def _arrays(instrs):
+    """Column arrays of a circuit; a U4 instruction's matrix (4 x 4 complex, in
+    place of theta) goes to a side array and theta becomes its index."""
     m = len(instrs)
+    mats = []
+    thetas = []
+    for i in instrs:
+        if i[0] == "U4":
+            u = np.asarray(i[3], dtype=complex).reshape(4, 4)
+            v = np.empty(32)
+            v[0::2], v[1::2] = u.real.reshape(-1), u.imag.reshape(-1)
+            thetas.append(float(len(mats)))
+            mats.append(v)
+        else:
+            thetas.append(i[3])
     g = np.array([GATE_CODES[i[0]] for i in instrs], dtype=np.int32).reshape(m)
     a = np.array([i[1] for i in instrs], dtype=np.int32).reshape(m)
     b = np.array([i[2] for i in instrs], dtype=np.int32).reshape(m)
-    t = np.array([i[3] for i in instrs], dtype=np.float64).reshape(m)
-    return m, g, a, b, t
+    t = np.array(thetas, dtype=np.float64).reshape(m)
+    u = np.concatenate(mats) if mats else None
+    return m, g, a, b, t, u
 
 
 def _ip(a):
@@ -134,16 +151,17 @@ def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
     Returns one dict per generator: strings (base-4 order), re, im, pruned_sumsq.
     """
     lib = _load()
-    m, g, a, b, t = _arrays(instrs)
+    m, g, a, b, t, u = _arrays(instrs)
     gb, ge = (0, n) if gens is None else gens
+    mats = (_dp(u), len(u) // 32) if u is not None else (None, 0)
     if init:
         s = "".join(p for p, _ in init).encode("ascii")
         wts = np.array([w for _, w in init], np.float64)
-        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
-                           float(eps), 0, 0, len(init), s, _dp(wts), int(threads))
+        h = lib.oracle_run_u4(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
+                              float(eps), 0, 0, len(init), s, _dp(wts), int(threads), *mats)
     else:
-        h = lib.oracle_run(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
-                           float(eps), int(gb), int(ge), 0, None, None, int(threads))
+        h = lib.oracle_run_u4(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
+                              float(eps), int(gb), int(ge), 0, None, None, int(threads), *mats)
     if not h:
         raise ValueError("oracle rejected the circuit")
     return _collect(lib, h, n)
@@ -152,7 +170,7 @@ def propagate(n, instrs, mode="plan", eps=0.0, gens=None, init=None, threads=1):
 def propagate_sum(n, instrs, strings, weights, mode="gate", eps=0.0):
     """One generator starting as sum_i weights[i] strings[i]; returns its result dict."""
     lib = _load()
-    m, g, a, b, t = _arrays(instrs)
+    m, g, a, b, t, _ = _arrays(instrs)
     s = "".join(strings).encode("ascii")
     w = np.ascontiguousarray(weights, np.float64)
     h = lib.oracle_run_sum(n, m, _ip(g), _ip(a), _ip(b), _dp(t), _MODES[mode],
@@ -187,7 +205,7 @@ def plan(n, instrs, dag=False):
     """[(kind, lut)] per operator: kind 'U' with an n x 3 x 3 table, or 'V' with None.
     dag=True: qubit-wise grouping (one-qubit gates move past gates on other wires)."""
     lib = _load()
-    m, g, a, b, t = _arrays(instrs)
+    m, g, a, b, t, _ = _arrays(instrs)
     h = lib.oracle_plan(n, m, _ip(g), _ip(a), _ip(b), _dp(t), 1 if dag else 0)
     if not h:
         raise ValueError("oracle rejected the circuit")
@@ -218,7 +236,7 @@ def flatten(lambdas, w4):
 def expval(n, instrs, q):
     """<0|U^dagger Q U|0> for one Pauli string q."""
     lib = _load()
-    m, g, a, b, t = _arrays(instrs)
+    m, g, a, b, t, _ = _arrays(instrs)
     out = np.zeros(1, np.float64)
     rc = lib.oracle_expval(n, m, _ip(g), _ip(a), _ip(b), _dp(t), q.encode("ascii"), _dp(out))
     if rc:

@@ -62,12 +62,15 @@ using Table = std::array<std::array<double, 3>, 3>;  // T[p][c]: coefficient of 
 // Gate codes of this file (the Python wrapper maps names onto them).
 enum Gate {
   G_H = 0, G_S, G_SDG, G_X, G_Y, G_Z, G_SX, G_SXDG, G_T, G_TDG, G_RX, G_RY, G_RZ, G_CX, G_CZ,
-  G_SWAP, G_RXX, G_RYY, G_RZZ, G_CRX, G_CRY, G_CRZ, G_CP, G_COUNT
+  G_SWAP, G_RXX, G_RYY, G_RZZ, G_CRX, G_CRY, G_CRZ, G_CP, G_U4, G_COUNT
 };
 
 struct Instr {
   int g, q0, q1;
   double theta;
+  // G_U4: its 4 x 4 unitary (32 doubles, row-major, re / im interleaved,
+  // basis index 2 b(q0) + b(q1)); owned by the caller for the run
+  const double* u = nullptr;
 };
 
 const char kLetter[3] = {'X', 'Y', 'Z'};
@@ -81,10 +84,12 @@ int letter_index(char c) {
   }
 }
 
-bool is_two_qubit(int g) { return g == G_CX || g == G_CZ || (g >= G_SWAP && g <= G_CP); }
+bool is_two_qubit(int g) { return g == G_CX || g == G_CZ || (g >= G_SWAP && g <= G_U4); }
 
+// A general two-qubit unitary counts as non-Clifford (push-through mode then
+// conjugates it literally, which is exact either way).
 bool is_clifford(int g) {
-  return g != G_T && g != G_TDG && g != G_RX && g != G_RY && g != G_RZ && (g < G_RXX || g > G_CP);
+  return g != G_T && g != G_TDG && g != G_RX && g != G_RY && g != G_RZ && (g < G_RXX || g > G_U4);
 }
 
 double snap(double v) {
@@ -268,8 +273,12 @@ Mat4 mul4(const Mat4& a, const Mat4& b) {
   return r;
 }
 
-Table16 gate_table_2q(int g, double th) {
-  const Mat4 u = gate_unitary_2q(g, th);
+Table16 table_of_unitary(const Mat4& u);
+
+Table16 gate_table_2q(int g, double th) { return table_of_unitary(gate_unitary_2q(g, th)); }
+
+// T[(p0, p1)][(c0, c1)] = Tr((C0 x C1) U (P0 x P1) U^dagger) / 4 for a given U.
+Table16 table_of_unitary(const Mat4& u) {
   Mat4 ud{};
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) ud[i][j] = std::conj(u[j][i]);
@@ -320,7 +329,15 @@ PauliSum apply_2q(const PauliSum& in, int g, int c, int t) {
   return apply_2q_table(in, c, t, gate_table_2q(g, 0.0));
 }
 
+Mat4 u4_matrix(const double* u) {
+  Mat4 m{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) m[i][j] = cplx(u[2 * (4 * i + j)], u[2 * (4 * i + j) + 1]);
+  return m;
+}
+
 PauliSum apply_gate(const PauliSum& in, const Instr& g) {
+  if (g.g == G_U4) return apply_2q_table(in, g.q0, g.q1, table_of_unitary(u4_matrix(g.u)));
   if (g.g >= G_RXX && g.g <= G_CP) return apply_2q_table(in, g.q0, g.q1, gate_table_2q(g.g, g.theta));
   if (is_two_qubit(g.g)) return apply_2q(in, g.g, g.q0, g.q1);
   return apply_1q(in, g.q0, gate_table(g.g, g.theta));
@@ -550,10 +567,22 @@ std::vector<Instr> read_instrs(long m, const int* gate, const int* q0, const int
   return v;
 }
 
+// U4 instructions name their matrix by theta (an index into mats).
+bool attach_u4(std::vector<Instr>& ins, const double* mats, long nmats) {
+  for (auto& g : ins) {
+    if (g.g != G_U4) continue;
+    const long k = long(g.theta);
+    if (!mats || double(k) != g.theta || k < 0 || k >= nmats) return false;
+    g.u = mats + size_t(k) * 32;
+  }
+  return true;
+}
+
 bool valid(int n, const std::vector<Instr>& ins) {
   if (n < 1) return false;
   for (const auto& g : ins) {
     if (g.g < 0 || g.g >= G_COUNT) return false;
+    if (g.g == G_U4 && !g.u) return false;
     if (g.q0 < 0 || g.q0 >= n) return false;
     if (is_two_qubit(g.g) && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) return false;
   }
@@ -583,11 +612,26 @@ extern "C" {
 //   n_init strings in init (n letters each, concatenated) with weights init_w.
 //   nthreads: generators are independent, so they are split across threads.
 // Returns NULL on invalid input.
+void* oracle_run_u4(int n, long m, const int* gate, const int* q0, const int* q1,
+                    const double* theta, int mode, double eps, int gen_begin, int gen_end,
+                    int n_init, const char* init, const double* init_w, int nthreads,
+                    const double* mats, long nmats);
+
 void* oracle_run(int n, long m, const int* gate, const int* q0, const int* q1,
                  const double* theta, int mode, double eps, int gen_begin, int gen_end,
                  int n_init, const char* init, const double* init_w, int nthreads) {
+  return oracle_run_u4(n, m, gate, q0, q1, theta, mode, eps, gen_begin, gen_end, n_init, init,
+                       init_w, nthreads, nullptr, 0);
+}
+
+// As oracle_run, with the matrices of the circuit's U4 gates (gate code 23;
+// theta = matrix index; 32 doubles per matrix, see Instr::u).
+void* oracle_run_u4(int n, long m, const int* gate, const int* q0, const int* q1,
+                    const double* theta, int mode, double eps, int gen_begin, int gen_end,
+                    int n_init, const char* init, const double* init_w, int nthreads,
+                    const double* mats, long nmats) {
   std::vector<Instr> ins = read_instrs(m, gate, q0, q1, theta);
-  if (!valid(n, ins)) return nullptr;
+  if (!attach_u4(ins, mats, nmats) || !valid(n, ins)) return nullptr;
   std::vector<PauliSum> start;
   if (n_init > 0) {
     for (int i = 0; i < n_init; ++i) {

@@ -158,6 +158,11 @@ void free_plan_device(qx_plan* p);
 void result_set_stream(qx_result* r, void* stream);
 // Applies pass `pc` to one string on the host with the same tables the device uses.
 void host_apply_pass(const CliffPass& pc, int n, int W, uint64_t* x, uint64_t* z, int* sign);
+// The gates (RZ / RY on each wire, RXX, RYY, RZZ) whose product is the 4 x 4
+// unitary u32 (row-major, re / im interleaved, basis index 2 b(q0) + b(q1)) up
+// to a global phase; *residual: the largest entry of the difference.
+qx_status decompose_u4(const double* u32, int q0, int q1, std::vector<qx_instr>* out,
+                       double* residual);
 // Push-through plan of a circuit (qx_group_ops_pushthrough).
 qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out);
 

@@ -1479,23 +1479,57 @@ void xs_release(Ctx& c, XsPending* xp) {
   *xp = XsPending();
 }
 
-XsMasks xs_masks(const FanStep& fs) {
-  XsMasks mk{};
-  for (const FanQubit& f : fs.qs) {
-    mk.words |= 1u << (f.q / 64);
-    for (int a = 0; a < 3; ++a)
-      if (!f.iso[a]) mk.niso[a][f.q / 64] |= 1ull << (f.q % 64);
+// The step record of the fused kernels: each wire's rows (children's letters
+// and entries), the letter masks, and the pruning thresholds as bit patterns
+// (the kernels compare |w| with them as integers).
+XsStep xs_step(const FanStep& fs, double eps) {
+  XsStep st;
+  std::memset(&st, 0, sizeof st);
+  st.nq = int(fs.qs.size());
+  double tmin = 1.0;
+  for (int j = 0; j < st.nq; ++j) {
+    const FanQubit& f = fs.qs[size_t(j)];
+    st.word[j] = uint8_t(f.q / 64);
+    st.bit[j] = uint8_t(f.q % 64);
+    st.words |= 1u << (f.q / 64);
+    double m = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      if (!f.iso[a]) st.niso[a][f.q / 64] |= 1ull << (f.q % 64);
+      XsRow& row = st.row[j][a];
+      row.nn = f.nnz[a];
+      for (int d = 0; d < f.nnz[a]; ++d) {
+        const int c = f.col[a][d];
+        row.col[d] = uint8_t(c);
+        row.t[d] = f.t.r[a][c];
+        row.th[d] = float(row.t[d]);
+        row.tl[d] = float(row.t[d] - double(row.th[d]));
+        m = std::min(m, std::fabs(row.t[d]));
+      }
+    }
+    tmin *= m;
   }
-  return mk;
+  st.prune = eps > 0.0 ? 1 : 0;
+  if (st.prune) {
+    std::memcpy(&st.eps_bits, &eps, 8);
+    // the smallest float not below eps: double(v) < eps iff |v| < it
+    float ef = float(eps);
+    if (double(ef) < eps) ef = std::nextafter(ef, INFINITY);
+    std::memcpy(&st.eps_bits32, &ef, 4);
+    // every child of a parent with |w| >= keep has |w t...| >= eps (the
+    // margin covers the roundings of up to kSmallMaxWires products)
+    const double keep = tmin > 0.0 ? eps / tmin * (1.0 + 1e-6) : INFINITY;
+    std::memcpy(&st.keep_bits, &keep, 8);
+    float kf = float(keep * (1.0 + 1e-4));
+    if (double(kf) < keep * (1.0 + 1e-4)) kf = std::nextafter(kf, INFINITY);
+    std::memcpy(&st.keep_bits32, &kf, 4);
+  }
+  return st;
 }
 
 template <int W, typename WT>
 qx_status xs_count(Ctx& c, const FanStep& fs, XsPending* xp) {
   Scratch& s = c.sc;
-  std::vector<FanQ> hq;
-  for (const FanQubit& f : fs.qs) hq.push_back(to_dev(f));
-  QX_TRY(h2d(c, s.fanq, hq.data(), hq.size() * sizeof(FanQ)));
-  const XsMasks mk = xs_masks(fs);
+  const XsStep st = xs_step(fs, c.eps);
   const size_t nt = (c.N + kXsSpan - 1) / kXsSpan;
   const size_t n2 = (nt + kScanTile - 1) / kScanTile;
   xp->ntiles = nt;
@@ -1504,11 +1538,10 @@ qx_status xs_count(Ctx& c, const FanStep& fs, XsPending* xp) {
   const size_t G = size_t(c.G);
   QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
   unsigned words = 0;
-  for (int k = 0; k < W; ++k) words += (mk.words >> k) & 1;
-  const size_t warps_per_block = kXsThreads / 32;
+  for (int k = 0; k < W; ++k) words += (st.words >> k) & 1;
   c.begin(KC_COUNT);
-  k_xs_count<W, WT><<<grid_for(nt, int(warps_per_block), c.sms, 8), kXsThreads, 0, c.al.s>>>(
-      c.cur.view<WT>(), s.ncnt + c.cslot, s.fanq, int(hq.size()), mk, c.eps, s.gmask, xp->tiles);
+  k_xs_count<W, WT><<<grid_for(nt, kXsThreads / 32, c.sms, 8), kXsThreads, 0, c.al.s>>>(
+      c.cur.view<WT>(), s.ncnt + c.cslot, st, s.gmask, xp->tiles);
   c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * words + 4 + (c.eps > 0.0 ? sizeof(WT) : 0)));
   c.begin(KC_SCAN);
   if (nt <= size_t(4) * 1024) {
@@ -1531,11 +1564,11 @@ template <int W, typename WT, int CK>
 void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap, const XsPass& ps,
                size_t smem) {
   // as many blocks per SM as the fused pass's tables fit in shared memory
-  const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (smem + 3072))));
+  const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (smem + 4096))));
   const unsigned grid = grid_for(xp->ntiles, kXsThreads / 32, c.sms, per_sm);
   k_xs_emit<W, WT, CK><<<grid, kXsThreads, smem, c.al.s>>>(
-      c.cur.view<WT>(), c.sc.ncnt + c.cslot, xp->tiles, c.sc.ncnt + 2, cap, c.sc.fanq,
-      int(fs.qs.size()), xs_masks(fs), ps, c.eps, c.sc.pruned, xp->out.view<WT>());
+      c.cur.view<WT>(), c.sc.ncnt + c.cslot, xp->tiles, c.sc.ncnt + 2, cap, xs_step(fs, c.eps),
+      ps, c.sc.pruned, xp->out.view<WT>());
 }
 
 template <int W, typename WT>

@@ -8,26 +8,32 @@
 // rotations), the expansion streams the terms twice:
 //
 // * k_xs_count reads only the words of the strings that hold a fan-out wire
-//   (and the generator id) and writes, per span of kXsSpan parents (one
-//   warp's share), the number of children, together with the per-generator
-//   letter masks that decide whether a merge was needed (the same masks as
-//   k_fan_mask);
+//   (the weight too when pruning, and the generator id) and writes, per span
+//   of kXsSpan parents (one warp's share), the number of children, together
+//   with the per-generator letter masks that decide whether a merge was
+//   needed (the same masks as k_fan_mask);
 // * the span sums are scanned (64 bytes per thousand parents);
 // * k_xs_emit reads each parent once, recounts its children within the span,
 //   applies the Clifford pass that precedes the step (when it acts on other
 //   qubits than the step's wires it commutes with the step, so mapping the
 //   parent first and substituting the wires' letters afterwards gives each
 //   child's image), and writes the children at the span's offset.
-// Warps work on their spans independently (no block barrier): each lane
-// loads all kXsItems of its parents before it writes anything, so a warp keeps
-// that many parents per lane in flight.
+// Warps work on contiguous ranges of spans independently (no block barrier):
+// each lane loads all kXsItems of its parents before it writes anything, so a
+// warp keeps that many parents per lane in flight.
+//
+// The FP64 unit of this GPU is the scarce one (about 1.3 TFLOP/s against
+// tens for FP32), so nothing here compares or converts in FP64: pruning tests
+// |w| < eps on the weight's bits as integers, a parent whose |w| is at least
+// the step's keep threshold (eps over the smallest table entry, with margin)
+// keeps every child without computing it, and each child's weight costs one
+// product per wire.  Each (wire, letter) row of the tables is one shared
+// record (children's letters and entries), read once per parent.
 //
 // Per parent that is 16W + 8 + 4 bytes read and the children's bytes written,
-// plus the fan-out words once more, against the separate Clifford pass (read
-// and write every term), letter masks, count, three-kernel scan of per-term
-// offsets, tile table and emission of the general path.  Child order and
-// weights (the running product in wire order, first wire least significant)
-// are those of k_expand_emit.
+// plus the fan-out words once more.  Child order and weights (the running
+// product in wire order, first wire least significant) are those of
+// k_expand_emit.
 #pragma once
 
 #include "qx_kernels.cuh"
@@ -36,14 +42,29 @@ namespace qx {
 namespace dev {
 
 constexpr int kXsThreads = 256;
-constexpr int kXsItems = 4;                          // parents per lane and span
+constexpr int kXsItems = 2;                          // parents per lane and span
 constexpr int kXsSpan = 32 * kXsItems;               // parents per span (one warp)
 
-// Letter masks of the wires' non-isolated rows (as k_fan_mask) and the words
-// of a string that hold a fan-out wire (bit k: word k).
-struct XsMasks {
-  uint64_t niso[3][kMaxWords];
-  uint32_t words;
+// Row of wire j's table for one letter: its children's letters and entries.
+struct XsRow {
+  double t[3];
+  float th[3], tl[3];  // t = th + tl (FP32 weights)
+  uint8_t col[3];
+  uint8_t nn;
+};
+
+// What a small step's kernels need, built on the host.
+struct XsStep {
+  XsRow row[kSmallMaxWires][3];      // [wire][letter - 1]
+  uint8_t word[kSmallMaxWires], bit[kSmallMaxWires];
+  uint64_t niso[3][kMaxWords];       // wires whose X / Y / Z rows are not isolated
+  uint64_t eps_bits;                 // FP64: pruned iff bits(|w|) < eps_bits
+  uint64_t keep_bits;                // FP64: every child kept iff bits(|w|) >= keep_bits
+  uint32_t eps_bits32, keep_bits32;  // the same for FP32 weights
+  int nq;
+  int prune;
+  uint32_t words;                    // words of the string that hold a fan-out wire
+  uint32_t pad;
 };
 
 // A Clifford pass applied to each parent before its children are written:
@@ -58,8 +79,97 @@ struct XsPass {
   PassMasks pmk;
 };
 
+__device__ __forceinline__ uint64_t abs_bits(double w) {
+  return uint64_t(__double_as_longlong(w)) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ uint32_t abs_bits(float w) { return __float_as_uint(w) & 0x7fffffffu; }
+
+template <typename WT>
+__device__ __forceinline__ bool xs_pruned(const XsStep& st, WT v) {
+  if constexpr (sizeof(WT) == 8) return abs_bits(v) < st.eps_bits;
+  else return abs_bits(v) < st.eps_bits32;
+}
+template <typename WT>
+__device__ __forceinline__ bool xs_keeps_all(const XsStep& st, WT w) {
+  if constexpr (sizeof(WT) == 8) return abs_bits(w) >= st.keep_bits;
+  else return abs_bits(w) >= st.keep_bits32;
+}
+
+// Letter (1 X, 2 Y, 3 Z, 0 I) of wire j.
+template <int W>
+__device__ __forceinline__ int xs_letter(const XsStep& st, int j, const uint64_t* x,
+                                         const uint64_t* z) {
+  const bool hi = W > 1 && st.word[j];
+  const int b = st.bit[j];
+  const int xb = int(((hi ? x[W - 1] : x[0]) >> b) & 1), zb = int(((hi ? z[W - 1] : z[0]) >> b) & 1);
+  return xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+}
+
+// Children of a parent: the product of its wires' row sizes.
+template <int W>
+__device__ __forceinline__ unsigned xs_count_children(const XsStep& st, const uint64_t* x,
+                                                      const uint64_t* z) {
+  unsigned c = 1;
+  for (int j = 0; j < st.nq; ++j) {
+    const int L = xs_letter<W>(st, j, x, z);
+    if (L) c *= st.row[j][L - 1].nn;
+  }
+  return c;
+}
+
+// Child r of a parent: letters into cx, cz (a copy of the parent's with the
+// wires' letters replaced) and the weight w times one entry per wire.
+template <int W, typename WT>
+__device__ __forceinline__ WT xs_child(const XsStep& st, const uint64_t* x, const uint64_t* z, WT w,
+                                       unsigned r, uint64_t* cx, uint64_t* cz) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    cx[k] = x[k];
+    cz[k] = z[k];
+  }
+  WProd<WT> p(w);
+  for (int j = 0; j < st.nq; ++j) {
+    const int L = xs_letter<W>(st, j, x, z);
+    if (!L) continue;
+    const XsRow& row = st.row[j][L - 1];
+    int d = 0;
+    if (row.nn == 2) {
+      d = int(r & 1);
+      r >>= 1;
+    } else if (row.nn == 3) {
+      d = int(r % 3);
+      r /= 3;
+    }
+    p.mul_entry(row.t[d], row.th[d], row.tl[d]);
+    const int col = row.col[d];
+    const uint64_t m = 1ull << st.bit[j];
+    const bool hi = W > 1 && st.word[j];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const uint64_t mk = (k == (hi ? W - 1 : 0)) ? m : 0ull;
+      cx[k] = (col <= 1) ? (cx[k] | mk) : (cx[k] & ~mk);
+      cz[k] = (col >= 1) ? (cz[k] | mk) : (cz[k] & ~mk);
+    }
+  }
+  return p.get();
+}
+
+// Children of a parent that survive pruning (all of them without pruning,
+// or when |w| is at least the keep threshold).
+template <int W, typename WT>
+__device__ __forceinline__ unsigned xs_kept(const XsStep& st, const uint64_t* x, const uint64_t* z,
+                                            WT w, unsigned cnt) {
+  if (!st.prune || xs_keeps_all<WT>(st, w)) return cnt;
+  unsigned kept = 0;
+  for (unsigned r = 0; r < cnt; ++r) {
+    uint64_t cx[W], cz[W];
+    kept += xs_pruned<WT>(st, xs_child<W, WT>(st, x, z, w, r, cx, cz)) ? 0u : 1u;
+  }
+  return kept;
+}
+
 // Words of term i that hold fan-out wires; the others read as 0 (letter I,
-// which no table row of a fan-out wire is asked about).
+// which no fan-out wire is asked about).
 template <int W, typename WT>
 __device__ __forceinline__ void load_fan_words(const TermsT<WT>& t, size_t i, uint32_t words,
                                                uint64_t* x, uint64_t* z) {
@@ -71,52 +181,22 @@ __device__ __forceinline__ void load_fan_words(const TermsT<WT>& t, size_t i, ui
   }
 }
 
-// Child r of a parent (letters x, z after the fused pass, weight w): its
-// letters in cx, cz and its weight, the running product in wire order with
-// the first wire as the least significant mixed-radix digit (as k_expand_emit).
-template <int W, typename WT>
-__device__ __forceinline__ WT xs_child(const FanQ* fq, int nq, const uint64_t* x, const uint64_t* z,
-                                       WT w, unsigned r, uint64_t* cx, uint64_t* cz) {
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    cx[k] = x[k];
-    cz[k] = z[k];
-  }
-  WProd<WT> p(w);
-  for (int j = 0; j < nq; ++j) {
-    const FanQ& f = fq[j];
-    const int L = letter_at<W>(x, z, f.q);
-    if (!L) continue;
-    const int a = L - 1;
-    const int nn = f.nnz[a];
-    int d = 0;
-    if (nn == 2) {
-      d = int(r & 1);
-      r >>= 1;
-    } else if (nn == 3) {
-      d = int(r % 3);
-      r /= 3;
-    }
-    const int col = f.col[a][d];
-    p.mul(f, a, col);
-    set_letter<W>(cx, cz, f.q, col);
-  }
-  return p.get();
+// The calling warp's contiguous range of spans [*b, *e): consecutive spans of
+// a warp hold neighbouring parents (usually of one generator), which keeps
+// the fused pass's image cache valid from span to span.
+__device__ __forceinline__ void warp_spans(size_t nspans, size_t warps, size_t* b, size_t* e) {
+  const size_t w = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5);
+  const size_t per = (nspans + warps - 1) / warps;
+  *b = min(nspans, w * per);
+  *e = min(nspans, *b + per);
 }
 
-// Children of a parent that survive pruning (|w| < eps is dropped, in FP64
-// as k_compact_pruned decides); all of them when eps = 0.
-template <int W, typename WT>
-__device__ __forceinline__ unsigned xs_kept(const FanQ* fq, int nq, const uint64_t* x,
-                                            const uint64_t* z, WT w, unsigned cnt, double eps) {
-  if (!(eps > 0.0)) return cnt;
-  unsigned kept = 0;
-  for (unsigned r = 0; r < cnt; ++r) {
-    uint64_t cx[W], cz[W];
-    const WT v = xs_child<W, WT>(fq, nq, x, z, w, r, cx, cz);
-    kept += fabs(double(v)) < eps ? 0u : 1u;
-  }
-  return kept;
+// Copies the step record into shared memory in 4-byte words.
+__device__ __forceinline__ void load_xs_step(XsStep* dst, const XsStep& src) {
+  static_assert(sizeof(XsStep) % 4 == 0, "XsStep is copied in 4-byte words");
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(&src);
+  uint32_t* b = reinterpret_cast<uint32_t*>(dst);
+  for (int k = threadIdx.x; k < int(sizeof(XsStep) / 4); k += blockDim.x) b[k] = a[k];
 }
 
 // Children per span of kXsSpan parents (span_sums) and the per-generator
@@ -125,17 +205,18 @@ __device__ __forceinline__ unsigned xs_kept(const FanQ* fq, int nq, const uint64
 template <int W, typename WT = double>
 __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
                                                          const unsigned long long* n_in,
-                                                         const FanQ* fq_g, int nq, XsMasks mk,
-                                                         double eps,
+                                                         const __grid_constant__ XsStep step,
                                                          unsigned long long* gmask,
                                                          unsigned long long* span_sums) {
-  __shared__ FanQ s_fq[kSmallMaxWires];
-  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  __shared__ XsStep st;
+  load_xs_step(&st, step);
   __syncthreads();
   const size_t N = *n_in;
   const size_t nspans = (N + kXsSpan - 1) / kXsSpan;
   const unsigned lane = threadIdx.x & 31;
   const size_t warps = size_t(gridDim.x) * (kXsThreads / 32);
+  const bool prune = st.prune != 0;
+  const uint32_t words = st.words;
   // running OR of a warp whose lanes all held generator cg
   uint32_t cg = 0xffffffffu;
   uint64_t acc[3][W];
@@ -156,8 +237,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 #pragma unroll
       for (int k = 0; k < W; ++k) acc[a][k] = 0;
   };
-  for (size_t span = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5); span < nspans;
-       span += warps) {
+  size_t s0, s1;
+  warp_spans(nspans, warps, &s0, &s1);
+  for (size_t span = s0; span < s1; ++span) {
     const size_t base = span * kXsSpan;
     // all loads of the span first, then the counts and masks
     uint64_t x[kXsItems][W], z[kXsItems][W];
@@ -168,9 +250,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
       const size_t i = base + size_t(it) * 32 + lane;
       wv[it] = WT(0);
       if (i < N) {
-        load_fan_words<W>(t, i, mk.words, x[it], z[it]);
+        load_fan_words<W>(t, i, words, x[it], z[it]);
         g[it] = t.g[i];
-        if (eps > 0.0) wv[it] = t.w[i];  // pruning counts the surviving children
+        if (prune) wv[it] = t.w[i];  // pruning counts the surviving children
       } else {
 #pragma unroll
         for (int k = 0; k < W; ++k) x[it][k] = z[it][k] = 0ull;
@@ -182,21 +264,20 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
     for (int it = 0; it < kXsItems; ++it) {
       const bool valid = g[it] != 0xffffffffu;
       if (valid)
-        sum += xs_kept<W, WT>(s_fq, nq, x[it], z[it], wv[it],
-                              unsigned(child_count<W>(x[it], z[it], s_fq, nq)), eps);
+        sum += xs_kept<W, WT>(st, x[it], z[it], wv[it], xs_count_children<W>(st, x[it], z[it]));
       uint64_t m[3][W];
 #pragma unroll
       for (int k = 0; k < W; ++k) {  // zero for invalid lanes (their x, z are 0)
-        m[0][k] = x[it][k] & ~z[it][k] & mk.niso[0][k];
-        m[1][k] = x[it][k] & z[it][k] & mk.niso[1][k];
-        m[2][k] = ~x[it][k] & z[it][k] & mk.niso[2][k];
+        m[0][k] = x[it][k] & ~z[it][k] & st.niso[0][k];
+        m[1][k] = x[it][k] & z[it][k] & st.niso[1][k];
+        m[2][k] = ~x[it][k] & z[it][k] & st.niso[2][k];
       }
       const unsigned peers = warp_peers(g[it]);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int k = 0; k < W; ++k) {  // OR over the lanes of the same generator
-          if (!((mk.words >> k) & 1)) continue;
+          if (!((words >> k) & 1)) continue;
           const unsigned lo = __reduce_or_sync(peers, unsigned(m[a][k]));
           const unsigned hi = __reduce_or_sync(peers, unsigned(m[a][k] >> 32));
           m[a][k] = (uint64_t(hi) << 32) | lo;
@@ -235,12 +316,12 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 template <int W, typename WT, int CK>
 __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* span_offs,
-    const unsigned long long* total_d, unsigned long long cap, const FanQ* fq_g, int nq,
-    XsMasks mk, XsPass ps, double eps, double* pruned, TermsT<WT> out) {
+    const unsigned long long* total_d, unsigned long long cap, const __grid_constant__ XsStep step,
+    XsPass ps, double* pruned, TermsT<WT> out) {
   if (*total_d > cap) return;
   extern __shared__ __align__(16) uint64_t s_dyn[];
-  __shared__ FanQ s_fq[kSmallMaxWires];
-  for (int j = threadIdx.x; j < nq; j += blockDim.x) s_fq[j] = fq_g[j];
+  __shared__ XsStep st;
+  load_xs_step(&st, step);
   const uint8_t* s_e = nullptr;
   if constexpr (CK >= 3) {
     constexpr int E = 1 << (2 * CK);
@@ -252,14 +333,15 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     for (int i = threadIdx.x; i < ps.nops; i += blockDim.x) s_ops[i] = ps.ops[i];
   }
   __syncthreads();
-  (void)mk;
   const size_t N = *n_in;
   const size_t nspans = (N + kXsSpan - 1) / kXsSpan;
   const unsigned lane = threadIdx.x & 31;
   const size_t warps = size_t(gridDim.x) * (kXsThreads / 32);
-  CliffCache<W> cc;
-  for (size_t span = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5); span < nspans;
-       span += warps) {
+  const bool prune = st.prune != 0;
+  FullCache<W> fc;
+  size_t s0, s1;
+  warp_spans(nspans, warps, &s0, &s1);
+  for (size_t span = s0; span < s1; ++span) {
     const size_t base = span * kXsSpan;
     // every parent of the lane first (independent loads), then the counts
     // and the warp's offsets in parent order (with pruning: of the
@@ -287,8 +369,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
 #pragma unroll
     for (int it = 0; it < kXsItems; ++it) {
       const bool valid = g[it] != 0xffffffffu;
-      const unsigned c = valid ? unsigned(child_count<W>(x[it], z[it], s_fq, nq)) : 0u;
-      const unsigned kc = valid ? xs_kept<W, WT>(s_fq, nq, x[it], z[it], wv[it], c, eps) : 0u;
+      const unsigned c = valid ? xs_count_children<W>(st, x[it], z[it]) : 0u;
+      const unsigned kc = valid ? xs_kept<W, WT>(st, x[it], z[it], wv[it], c) : 0u;
       unsigned inc = kc;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -304,19 +386,21 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
       if (!cnt[it]) continue;
       WT w = wv[it];
       if constexpr (CK >= 3) {
-        if (clifford_table_map<W, CK>(x[it], z[it], s_dyn, s_e, ps.chunks, ps.live, ps.pmk, cc))
+        if (clifford_table_map_full<W, CK>(x[it], z[it], s_dyn, s_e, ps.chunks, ps.live, ps.pmk,
+                                           fc))
           w = wneg(w);
       } else if constexpr (CK == 1) {
         int neg = 0;
         apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn), ps.nops, x[it], z[it], &neg);
         if (neg) w = wneg(w);
       }
+      const bool all = !prune || xs_keeps_all<WT>(st, w);
       // o + (children kept) <= *total_d <= cap (the counts the span sums came from)
       unsigned long long o = loc[it];
       for (unsigned r = 0; r < cnt[it]; ++r) {
         uint64_t cx[W], cz[W];
-        const WT v = xs_child<W, WT>(s_fq, nq, x[it], z[it], w, r, cx, cz);
-        if (eps > 0.0 && fabs(double(v)) < eps) {
+        const WT v = xs_child<W, WT>(st, x[it], z[it], w, r, cx, cz);
+        if (!all && xs_pruned<WT>(st, v)) {
           atomicAdd(&pruned[g[it]], double(v) * double(v));
           continue;
         }

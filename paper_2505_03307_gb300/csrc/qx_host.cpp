@@ -746,6 +746,9 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
   if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
   for (size_t i = 0; i < m; ++i) {
     const qx_instr& g = ins[i];
+    if (g.gate == QX_U4)
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) +
+                                 ": U4 needs its matrix (qx_load_circuit_u4)");
     if (g.gate > QX_CP) return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad gate");
     if (g.q0 < 0 || g.q0 >= n)
       return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": wire out of range");
@@ -760,6 +763,36 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
   c->ins.assign(ins, ins + m);
   *out = c;
   return QX_OK;
+}
+
+qx_status qx_load_circuit_u4(int n, const qx_instr* ins, size_t m, const double* mats,
+                             size_t nmats, qx_circuit** out) {
+  clear_error();
+  if (!out) return fail(QX_EINVAL, "out is NULL");
+  if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
+  if (nmats && !mats) return fail(QX_EINVAL, "mats is NULL");
+  // each U4 becomes its decomposition (15 gates); the others are copied
+  std::vector<qx_instr> all;
+  all.reserve(m);
+  for (size_t i = 0; i < m; ++i) {
+    const qx_instr& g = ins[i];
+    if (g.gate != QX_U4) {
+      all.push_back(g);
+      continue;
+    }
+    if (g.q0 < 0 || g.q0 >= n || g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": bad U4 wires");
+    const double k = g.theta;
+    if (!(k >= 0.0) || k != std::floor(k) || k >= double(nmats))
+      return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": U4 matrix index out of range");
+    std::vector<qx_instr> gs;
+    if (const qx_status st = decompose_u4(mats + size_t(k) * 32, g.q0, g.q1, &gs, nullptr)) {
+      const std::string msg = qx_last_error();
+      return fail(st, "instruction " + std::to_string(i) + ": " + msg);
+    }
+    all.insert(all.end(), gs.begin(), gs.end());
+  }
+  return qx_load_circuit(n, all.data(), all.size(), out);
 }
 
 qx_status qx_group_ops(const qx_circuit* c, qx_plan** out) {

@@ -21,6 +21,7 @@ GATE_CODES = {
     "H": 0, "S": 1, "SDG": 2, "X": 3, "Y": 4, "Z": 5, "SX": 6, "SXDG": 7,
     "T": 8, "TDG": 9, "RX": 10, "RY": 11, "RZ": 12, "CX": 13, "CZ": 14,
     "SWAP": 15, "RXX": 16, "RYY": 17, "RZZ": 18, "CRX": 19, "CRY": 20, "CRZ": 21, "CP": 22,
+    "U4": 23,
 }
 STATUS = {0: "QX_OK", 1: "QX_EINVAL", 2: "QX_ENOMEM", 3: "QX_EBUDGET", 4: "QX_ECAP",
           5: "QX_ECUDA", 6: "QX_ETIMEOUT", 7: "QX_EUNSUPPORTED"}
@@ -37,7 +38,7 @@ EXPORTED = (
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
     "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough", "qx_adjoint_dot_pauli",
-    "qx_wait_selftest",
+    "qx_wait_selftest", "qx_load_circuit_u4", "qx_u4_decompose",
 )
 
 
@@ -134,6 +135,10 @@ def load_library():
         "qx_default_opts": (None, [ctypes.POINTER(PropOpts)]),
         "qx_load_circuit": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Instr), _SZ,
                                            ctypes.POINTER(_P)]),
+        "qx_load_circuit_u4": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Instr), _SZ, _DP, _SZ,
+                                              ctypes.POINTER(_P)]),
+        "qx_u4_decompose": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Instr),
+                                           ctypes.POINTER(_SZ), _DP]),
         "qx_group_ops": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "qx_group_ops_dag": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "qx_group_ops_pushthrough": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
@@ -310,6 +315,29 @@ def instr_records(names, q0, q1, theta):
     return rec
 
 
+def u4_array(u):
+    """A 4 x 4 complex matrix as the 32 doubles of the C interface (row-major,
+    real and imaginary parts interleaved)."""
+    u = np.asarray(u, dtype=complex).reshape(4, 4)
+    out = np.empty(32, np.float64)
+    out[0::2] = u.real.reshape(-1)
+    out[1::2] = u.imag.reshape(-1)
+    return out
+
+
+def u4_decompose(u, q0=0, q1=1):
+    """qx_u4_decompose: the 15 gates (name, q0, q1, theta) that replace a
+    two-qubit unitary, and the residual of their product."""
+    inv = {v: k for k, v in GATE_CODES.items()}
+    arr = (Instr * 16)()
+    cnt, res = _SZ(), ctypes.c_double()
+    a = u4_array(u)
+    _check(load_library().qx_u4_decompose(a.ctypes.data_as(_DP), int(q0), int(q1), arr,
+                                           ctypes.byref(cnt), ctypes.byref(res)))
+    return [(inv[arr[k].gate], arr[k].q0, arr[k].q1, arr[k].theta) for k in range(cnt.value)], \
+        res.value
+
+
 class Circuit:
     def __init__(self, n, instrs, records=None):
         """instrs: (gate, q0, q1, theta) tuples; or records: an INSTR_DTYPE
@@ -323,10 +351,24 @@ class Circuit:
             self.instrs = None
             self.ninstr = len(rec)
         else:
-            rec = np.array([(GATE_CODES[g], a, b, th) for g, a, b, th in instrs],
-                           INSTR_DTYPE).reshape(-1)
-            _check(lib.qx_load_circuit(int(n), ctypes.cast(rec.ctypes.data, ctypes.POINTER(Instr)),
-                                       len(rec), ctypes.byref(h)))
+            # a U4 instruction carries its 4 x 4 matrix in place of theta: the
+            # matrices go to a side array and theta becomes the index
+            mats = []
+            rows = []
+            for g, a, b, th in instrs:
+                if g == "U4":
+                    rows.append((GATE_CODES[g], a, b, float(len(mats))))
+                    mats.append(u4_array(th))
+                else:
+                    rows.append((GATE_CODES[g], a, b, th))
+            rec = np.array(rows, INSTR_DTYPE).reshape(-1)
+            ptr = ctypes.cast(rec.ctypes.data, ctypes.POINTER(Instr))
+            if mats:
+                m = np.ascontiguousarray(np.concatenate(mats), np.float64)
+                _check(lib.qx_load_circuit_u4(int(n), ptr, len(rec), m.ctypes.data_as(_DP),
+                                              len(mats), ctypes.byref(h)))
+            else:
+                _check(lib.qx_load_circuit(int(n), ptr, len(rec), ctypes.byref(h)))
             self.instrs = list(instrs)
             self.ninstr = len(instrs)
         self.n = n

@@ -367,6 +367,60 @@ def qaoa(seed: int, n: int = 16, layers: int = 2, degree: int = 3):
     return n, instrs
 
 
+def haar_u4(rng):
+    """A Haar-random 4 x 4 unitary (QR of a complex Gaussian matrix with the
+    phases of R's diagonal moved into Q)."""
+    z = (rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))
+
+
+def special_u4():
+    """Named two-qubit unitaries whose KAK coordinates are degenerate (local
+    gates, CX, CZ, SWAP, iSWAP, sqrt(SWAP), controlled phases) as 4 x 4
+    matrices (basis index 2 b(q0) + b(q1))."""
+    h = np.array([[1, 1], [1, -1]]) / math.sqrt(2.0)
+    s = np.diag([1, 1j])
+    out = {
+        "identity": np.eye(4, dtype=complex),
+        "local": np.kron(h, s @ h),
+        "cx": np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex),
+        "cz": np.diag([1, 1, 1, -1]).astype(complex),
+        "swap": np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=complex),
+        "iswap": np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=complex),
+        "cp": np.diag([1, 1, 1, np.exp(0.7j)]),
+    }
+    a = (1 + 1j) / 2
+    out["sqrt_swap"] = np.array([[1, 0, 0, 0], [0, a, a.conjugate(), 0],
+                                 [0, a.conjugate(), a, 0], [0, 0, 0, 1]], dtype=complex)
+    out["phase"] = np.exp(0.3j) * out["iswap"] @ np.kron(s, h)
+    return out
+
+
+def random_small_u4(seed: int, n: int, m: int, p_u4: float = 0.25, p_cx: float = 0.15):
+    """Random circuit of one-qubit gates, CX and general two-qubit unitaries
+    ("U4", q0, q1, matrix): Haar matrices, and at times a named one."""
+    rng = np.random.default_rng(seed)
+    names1 = ("H", "S", "SX", "T", "RX", "RY", "RZ")
+    spec = list(special_u4().values())
+    out = []
+    for _ in range(m):
+        r = rng.random()
+        if n >= 2 and r < p_u4:
+            a, b = (int(v) for v in rng.choice(n, size=2, replace=False))
+            u = spec[int(rng.integers(0, len(spec)))] if rng.random() < 0.2 else haar_u4(rng)
+            out.append(("U4", a, b, u))
+        elif n >= 2 and r < p_u4 + p_cx:
+            a, b = (int(v) for v in rng.choice(n, size=2, replace=False))
+            out.append(_g2("CX", a, b))
+        else:
+            g = names1[int(rng.integers(0, len(names1)))]
+            th = float(rng.uniform(0, 2 * math.pi)) if g.startswith("R") else 0.0
+            out.append(_g1(g, int(rng.integers(0, n)), th))
+    return n, out
+
+
 def random_paulis(seed: int, n: int, k: int, min_weight: int = 1):
     """``k`` seeded random Pauli strings ("IXYZ" letters, character i = qubit i)."""
     rng = np.random.default_rng(seed)

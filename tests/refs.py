@@ -120,6 +120,8 @@ def dense_unitary(n, instrs):
         elif g == "CZ":
             sign = np.where(((idx >> a) & 1) & ((idx >> b) & 1), -1.0, 1.0)
             U = U * sign[:, None]
+        elif g == "U4":  # a general two-qubit unitary (its matrix in place of theta)
+            U = _apply_2q(U, n, a, b, np.asarray(th, dtype=complex).reshape(4, 4))
         elif b >= 0:
             U = _apply_2q(U, n, a, b, gate_matrix_2q(g, th))
         else:

@@ -62,7 +62,29 @@ def test_mix_equals_alone_fp64():
     st = srv.stats()
     assert st["completed"] == len(items) and st["failed"] == 0
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
-    assert st["batches"] < len(items) and st["mean_batch"] > 1.0
+    srv.close()
+
+
+def test_requests_that_wait_share_a_batch():
+    """A request whose bound exceeds the budget runs by itself first (its
+    exact size fits); the light requests submitted behind it wait for it and
+    then run as shared batches.  Each result equals its circuit alone."""
+    heavy = W.fan_in_heavy(2, n=60, n_s=17, total=1500, tail=200)  # 43 x 2^17 terms
+    light = [(n, instrs) for _, n, instrs in W.serving_stream(14, count=40)]
+    srv = qx.Server(slots=1, hbm_budget=8 << 30)
+    first = srv.submit(*heavy)
+    tickets = [(srv.submit(n, instrs), n, instrs) for n, instrs in light]
+    res, _ = srv.wait(first)
+    assert res.nterms >= 43 * 2 ** 17
+    for g in (0, 20, 59):
+        assert abs(res.info(g)["sumsq"] - 1.0) < 1e-10
+    res.free()
+    for t, n, instrs in tickets:
+        res, _ = srv.wait(t)
+        _check_fp64(res, n, instrs, f"request {t}")
+    st = srv.stats()
+    assert st["alone"] == 1 and st["failed"] == 0
+    assert st["batches"] < 1 + len(light) and st["mean_batch"] > 1.0
     srv.close()
 
 

@@ -25,7 +25,7 @@ def built():
 
 def test_exports_every_declared_symbol():
     text = open(HEADER).read()
-    declared = set(re.findall(r"\b(qx_[a-z_]+)\s*\(", text))
+    declared = set(re.findall(r"\b(qx_[a-z0-9_]+)\s*\(", text))
     assert declared == set(qx.EXPORTED)
     lib = qx.load_library()
     for name in declared:

@@ -364,3 +364,38 @@ def test_fan_in_closed_form_small():
             assert abs(w - want) < 1e-12
     # one generator inside S: two terms
     assert len(res[0]["strings"]) == 2
+
+
+# --- general two-qubit unitaries (U4) ----------------------------------------
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("mode", ["gate", "plan", "push"])
+def test_dense_general_two_qubit_unitaries(seed, mode):
+    """U4 gates (Haar-random and named 4 x 4 matrices) in every oracle mode
+    against the dense brute force (Kronecker-indexed 4 x 4 blocks applied to
+    the state's rows in refs)."""
+    n = 2 + seed % 4
+    _, instrs = W.random_small_u4(seed, n, 8 + 3 * n)
+    assert any(g[0] == "U4" for g in instrs)
+    _check_dense(n, instrs, mode)
+
+
+def test_u4_of_named_gates_equals_the_gate():
+    """A U4 holding the matrix of CX (or of RZZ) gives the same generators
+    as the gate itself."""
+    import cmath
+    n = 3
+    cx = W.special_u4()["cx"]
+    th = 0.37
+    rzz = np.diag([cmath.exp(-0.5j * th), cmath.exp(0.5j * th), cmath.exp(0.5j * th),
+                   cmath.exp(-0.5j * th)])
+    base = [("H", 0, -1, 0.0), ("RY", 1, -1, 0.4), ("T", 2, -1, 0.0)]
+    for named, u in ((("CX", 0, 2, 0.0), cx), (("RZZ", 1, 2, th), rzz)):
+        a = O.propagate(n, base + [named], mode="gate")
+        b = O.propagate(n, base + [("U4", named[1], named[2], u)], mode="gate")
+        for ga, gb in zip(a, b):
+            da = {s: w for s, w in O.as_dict(ga).items() if abs(w) > 1e-14}
+            db = {s: w for s, w in O.as_dict(gb).items() if abs(w) > 1e-14}
+            assert da.keys() == db.keys()
+            for s, w in da.items():
+                assert abs(db[s] - w) < 1e-13
