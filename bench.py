@@ -937,6 +937,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """--warmup then --profile-steps propagations of the headline workload on
+    cuda:0 with nothing else on the device: the command the committed ncu
+    summaries name.  The profiled propagations sit in the NVTX range
+    "qx_profile"."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_03307_gb300 import qx
+    from paper_2505_03307_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    # --profile-nfan < 20: the same construction with fewer fan-out qubits
+    # (80 generators of 2^k terms), a small case for multi-pass captures
+    n, instrs = W.fan_in_deep(1, n_s=args.profile_nfan)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    launches = 0
+    for k in range(args.warmup + args.profile_steps):
+        if k == args.warmup:  # ncu --nvtx --nvtx-include "qx_profile/" captures from here
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("qx_profile")
+        r = qx.propagate(plan, eps=EPS)
+        launches = r.stats()["kernel_launches"]
+        r.free()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_steps": args.profile_steps, "warmup": args.warmup,
+                      "kernel_launches_per_propagation": launches}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -963,9 +992,16 @@ def main():
                     help="timed steps per case of the grouping comparison (0: skip)")
     ap.add_argument("--xyz-repeats", default="100,1000,10000,100000",
                     help="#Repeats of the XYZ + chain sweep, comma-separated ('' skips it)")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only --warmup then this many propagations of the headline workload, "
+                         "no timing and no other legs (for ncu launch lists)")
+    ap.add_argument("--profile-nfan", type=int, default=20,
+                    help="fan-out qubits of the --profile-steps workload (20: the headline)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_steps > 0:
+        run_profile(args)
     else:
         run_ours(args)
 

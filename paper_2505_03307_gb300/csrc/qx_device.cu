@@ -1468,9 +1468,11 @@ void split_fan(const Ctx& c, const FanStep& fs, const std::vector<unsigned long 
 // (a Clifford pass on other qubits, or none) to each parent; xs_accept makes
 // the output current.
 struct XsPending {
-  unsigned long long* tiles = nullptr;  // span sums -> offsets; [nt]: nt; then scan scratch
+  unsigned long long* tiles = nullptr;  // range sums -> offsets
   TermBuf out;
-  size_t ntiles = 0;
+  size_t nranges = 0;  // ranges of spans: one warp of the emission each
+  size_t per = 0;      // spans per range
+  unsigned grid = 0;   // blocks of the emission (nranges / 8)
 };
 
 void xs_release(Ctx& c, XsPending* xp) {
@@ -1526,49 +1528,113 @@ XsStep xs_step(const FanStep& fs, double eps) {
   return st;
 }
 
+// The partition of a small step's spans into ranges: one warp of the
+// emission per range, and exactly one wave of emission blocks (as many as
+// stay resident on every SM with the kernel's registers and parent stages:
+// a second, partial wave would leave most SMs idle behind its last ranges).
+template <int W, typename WT, int CK, int NQ>
+int xs_emit_per_sm(size_t smem) {
+  static thread_local int cached[2] = {0, 0};  // [smem has a gate list]
+  int& slot = cached[smem > xs_emit_stage_bytes<W, WT>() ? 1 : 0];
+  if (slot) return slot;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xs_emit<W, WT, CK, NQ>, kXsThreads,
+                                                    smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  slot = n;
+  return n;
+}
+
 template <int W, typename WT>
-qx_status xs_count(Ctx& c, const FanStep& fs, XsPending* xp) {
+int xs_emit_blocks_per_sm(const FanStep& fs, const qx_plan_device::Pass* fused) {
+  const int nq = int(fs.qs.size());
+  const size_t smem = xs_emit_stage_bytes<W, WT>() +
+                      (fused && !fused->identity && !fused->use_table ? size_t(fused->nops) * 4 : 0);
+  auto pick = [&](auto ck) {
+    constexpr int CK = decltype(ck)::value;
+    return nq == 1   ? xs_emit_per_sm<W, WT, CK, 1>(smem)
+           : nq == 2 ? xs_emit_per_sm<W, WT, CK, 2>(smem)
+                     : xs_emit_per_sm<W, WT, CK, 0>(smem);
+  };
+  if (!fused || fused->identity) return pick(std::integral_constant<int, 0>());
+  if (!fused->use_table) return pick(std::integral_constant<int, 1>());
+  return fused->cb == 4 ? pick(std::integral_constant<int, 4>())
+                        : pick(std::integral_constant<int, 3>());
+}
+
+template <int W, typename WT>
+void xs_partition(const Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused,
+                  XsPending* xp) {
+  const size_t nspans = (c.N + kXsSpan - 1) / kXsSpan;
+  const int per_sm = xs_emit_blocks_per_sm<W, WT>(fs, fused);
+  xp->grid = grid_for(nspans, kXsThreads / 32, c.sms, per_sm);
+  xp->nranges = size_t(xp->grid) * (kXsThreads / 32);
+  xp->per = std::max<size_t>(1, (nspans + xp->nranges - 1) / xp->nranges);
+}
+
+template <int W, typename WT>
+qx_status xs_count(Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused, XsPending* xp) {
   Scratch& s = c.sc;
   const XsStep st = xs_step(fs, c.eps);
-  const size_t nt = (c.N + kXsSpan - 1) / kXsSpan;
-  const size_t n2 = (nt + kScanTile - 1) / kScanTile;
-  xp->ntiles = nt;
-  xp->tiles = static_cast<unsigned long long*>(c.al.get((nt + 2 + n2) * 8));
-  if (!xp->tiles) return fail(QX_ENOMEM, "device allocation of the expansion span sums failed");
+  xs_partition<W, WT>(c, fs, fused, xp);
+  const size_t R = xp->nranges;
+  xp->tiles = static_cast<unsigned long long*>(c.al.get((R + 1) * 8));
+  if (!xp->tiles) return fail(QX_ENOMEM, "device allocation of the expansion range sums failed");
   const size_t G = size_t(c.G);
   QX_TRY_CUDA(cudaMemsetAsync(s.gmask, 0, G * 3 * W * 8, c.al.s));
   unsigned words = 0;
   for (int k = 0; k < W; ++k) words += (st.words >> k) & 1;
   c.begin(KC_COUNT);
-  k_xs_count<W, WT><<<grid_for(nt, kXsThreads / 32, c.sms, 8), kXsThreads, 0, c.al.s>>>(
-      c.cur.view<WT>(), s.ncnt + c.cslot, st, s.gmask, xp->tiles);
+  // one wave of count blocks, each warp striding over the ranges
+  static thread_local int count_per_sm = 0;
+  if (!count_per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&count_per_sm, k_xs_count<W, WT, 1>,
+                                                      kXsThreads, 0) != cudaSuccess ||
+        count_per_sm < 1) {
+      cudaGetLastError();
+      count_per_sm = 2;
+    }
+  }
+  const unsigned cgrid = grid_for(R, kXsThreads / 32, c.sms, count_per_sm);
+  const auto view = c.cur.view<WT>();
+  if (st.nq == 1)
+    k_xs_count<W, WT, 1><<<cgrid, kXsThreads, 0, c.al.s>>>(view, s.ncnt + c.cslot, st, R, xp->per,
+                                                           s.gmask, xp->tiles);
+  else if (st.nq == 2)
+    k_xs_count<W, WT, 2><<<cgrid, kXsThreads, 0, c.al.s>>>(view, s.ncnt + c.cslot, st, R, xp->per,
+                                                           s.gmask, xp->tiles);
+  else
+    k_xs_count<W, WT, 0><<<cgrid, kXsThreads, 0, c.al.s>>>(view, s.ncnt + c.cslot, st, R, xp->per,
+                                                           s.gmask, xp->tiles);
   c.end(KC_COUNT, 1, uint64_t(c.N) * (16 * words + 4 + (c.eps > 0.0 ? sizeof(WT) : 0)));
   c.begin(KC_SCAN);
-  if (nt <= size_t(4) * 1024) {
-    k_scan_sums<<<1, 1024, 0, c.al.s>>>(xp->tiles, nt, s.ncnt + 2);
-    c.end(KC_SCAN, 1, uint64_t(nt) * 16);
-  } else {  // three phases over the span sums; their count sits at tiles[nt]
-    const unsigned long long ntv = nt;
-    QX_TRY(h2d(c, xp->tiles + nt, &ntv, 8));
-    unsigned long long* t2 = xp->tiles + nt + 1;
-    k_scan_tiles<<<unsigned(n2), kScanThreads, 0, c.al.s>>>(xp->tiles, xp->tiles + nt, t2);
-    k_scan_sums<<<1, 1024, 0, c.al.s>>>(t2, n2, s.ncnt + 2);
-    k_scan_add<<<unsigned(n2), kScanThreads, 0, c.al.s>>>(xp->tiles, xp->tiles + nt, t2);
-    c.end(KC_SCAN, 3, uint64_t(nt) * 8 * 3);
-  }
+  k_scan_sums<<<1, 1024, 0, c.al.s>>>(xp->tiles, R, s.ncnt + 2);
+  c.end(KC_SCAN, 1, uint64_t(R) * 16);
   QX_TRY_CUDA(cudaGetLastError());
   return QX_OK;
 }
 
 template <int W, typename WT, int CK>
 void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap, const XsPass& ps,
-               size_t smem) {
-  // as many blocks per SM as the fused pass's tables fit in shared memory
-  const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (smem + 4096))));
-  const unsigned grid = grid_for(xp->ntiles, kXsThreads / 32, c.sms, per_sm);
-  k_xs_emit<W, WT, CK><<<grid, kXsThreads, smem, c.al.s>>>(
-      c.cur.view<WT>(), c.sc.ncnt + c.cslot, xp->tiles, c.sc.ncnt + 2, cap, xs_step(fs, c.eps),
-      ps, c.sc.pruned, xp->out.view<WT>());
+               size_t extra) {
+  // dynamic shared memory: every warp's parent stages, then a gate list
+  const size_t smem = xs_emit_stage_bytes<W, WT>() + extra;
+  const unsigned grid = xp->grid;  // one warp per range of the count's partition
+  const XsStep st = xs_step(fs, c.eps);
+  const auto in = c.cur.view<WT>();
+  const auto out = xp->out.view<WT>();
+  const unsigned long long* n_in = c.sc.ncnt + c.cslot;
+  if (st.nq == 1)
+    k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
+        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
+  else if (st.nq == 2)
+    k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
+        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
+  else
+    k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
+        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
 }
 
 template <int W, typename WT>
@@ -1589,10 +1655,11 @@ qx_status xs_emit(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long c
     ps.chunks = fused->chunks;
     ps.live = fused->live;
     ps.pmk = pass_masks<W>(*fused, c.n);
+    // the tables stay in global memory (k_xs_emit reads them on image-cache misses)
     if (fused->cb == 4)
-      xs_launch<W, WT, 4>(c, fs, xp, cap, ps, fused->smem);
+      xs_launch<W, WT, 4>(c, fs, xp, cap, ps, 0);
     else
-      xs_launch<W, WT, 3>(c, fs, xp, cap, ps, fused->smem);
+      xs_launch<W, WT, 3>(c, fs, xp, cap, ps, 0);
   }
   c.end(KC_EXPAND, 1, (c.N + cap) * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
@@ -1638,7 +1705,7 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
     uses_tail = true;
   }
   XsPending xp;
-  qx_status st = xs_count<W, WT>(c, fs, &xp);
+  qx_status st = xs_count<W, WT>(c, fs, fused, &xp);
   if (st != QX_OK) {
     xs_release(c, &xp);
     return st;
@@ -2265,14 +2332,54 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
       cudaFuncSetAttribute(k_expand_emit<2, double>, attr, mx);
       cudaFuncSetAttribute(k_expand_emit<1, float>, attr, mx);
       cudaFuncSetAttribute(k_expand_emit<2, float>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<1, double, 3>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<1, double, 4>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<2, double, 3>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<2, double, 4>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<1, float, 3>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<1, float, 4>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<2, float, 3>, attr, mx);
-      cudaFuncSetAttribute(k_xs_emit<2, float, 4>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 0, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 0, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 0, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 1, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 1, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 1, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 3, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 3, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 3, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 4, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 4, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, double, 4, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 0, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 0, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 0, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 1, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 1, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 1, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 3, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 3, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 3, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 4, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 4, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<1, float, 4, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 0, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 0, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 0, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 1, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 1, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 1, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 3, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 3, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 3, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 4, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 4, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, double, 4, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 0, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 0, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 0, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 1, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 1, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 1, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 3, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 3, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 3, 2>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 4, 0>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 4, 1>, attr, mx);
+      cudaFuncSetAttribute(k_xs_emit<2, float, 4, 2>, attr, mx);
       attr_dev = dev;
     }
   }

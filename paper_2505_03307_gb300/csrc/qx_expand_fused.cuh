@@ -8,11 +8,12 @@
 // rotations), the expansion streams the terms twice:
 //
 // * k_xs_count reads only the words of the strings that hold a fan-out wire
-//   (the weight too when pruning, and the generator id) and writes, per span
-//   of kXsSpan parents (one warp's share), the number of children, together
+//   (the weight too when pruning, and the generator id) and writes, per range
+//   of spans of kXsSpan parents (one emission warp's share), the number of
+//   children, together
 //   with the per-generator letter masks that decide whether a merge was
 //   needed (the same masks as k_fan_mask);
-// * the span sums are scanned (64 bytes per thousand parents);
+// * the range sums are scanned (one per warp of the emission);
 // * k_xs_emit reads each parent once, recounts its children within the span,
 //   applies the Clifford pass that precedes the step (when it acts on other
 //   qubits than the step's wires it commutes with the step, so mapping the
@@ -168,6 +169,120 @@ __device__ __forceinline__ unsigned xs_kept(const XsStep& st, const uint64_t* x,
   return kept;
 }
 
+// Steps of one or two wires (NQ = 1, 2; every rotation and T step, and
+// two-wire operators) resolve each parent once: the wires' bit positions sit
+// in registers for the whole kernel, and the rows that the parent's letters
+// select are copied from shared memory into registers, so its children cost
+// no further shared-memory reads.  NQ = 0 keeps the run-time loops above.
+template <int NQ>
+struct XsWires {
+  int word[NQ], bit[NQ];
+};
+
+template <int NQ>
+__device__ __forceinline__ XsWires<NQ> xs_wires(const XsStep& st) {
+  XsWires<NQ> wr;
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    wr.word[j] = st.word[j];
+    wr.bit[j] = st.bit[j];
+  }
+  return wr;
+}
+
+template <int NQ>
+struct XsParentRows {
+  double t[NQ][3];
+  float th[NQ][3], tl[NQ][3];
+  int col[NQ][3];
+  int nn[NQ];  // 1 for a wire with letter I (the parent's letter passes)
+  int on[NQ];
+};
+
+template <int W, int NQ>
+__device__ __forceinline__ unsigned xs_resolve(const XsStep& st, const XsWires<NQ>& wr,
+                                               const uint64_t* x, const uint64_t* z,
+                                               XsParentRows<NQ>* pr) {
+  unsigned c = 1;
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const bool hi = W > 1 && wr.word[j];
+    const int b = wr.bit[j];
+    const int xb = int(((hi ? x[W - 1] : x[0]) >> b) & 1);
+    const int zb = int(((hi ? z[W - 1] : z[0]) >> b) & 1);
+    const int L = xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+    pr->on[j] = L != 0;
+    if (L) {
+      const XsRow& row = st.row[j][L - 1];
+      pr->nn[j] = row.nn;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        pr->t[j][d] = row.t[d];
+        pr->th[j][d] = row.th[d];
+        pr->tl[j][d] = row.tl[d];
+        pr->col[j][d] = row.col[d];
+      }
+      c *= unsigned(row.nn);
+    } else {
+      pr->nn[j] = 1;
+    }
+  }
+  return c;
+}
+
+// Child r of a resolved parent (as xs_child).
+template <int W, typename WT, int NQ>
+__device__ __forceinline__ WT xs_child_r(const XsWires<NQ>& wr, const XsParentRows<NQ>& pr,
+                                         const uint64_t* x, const uint64_t* z, WT w, unsigned r,
+                                         uint64_t* cx, uint64_t* cz) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    cx[k] = x[k];
+    cz[k] = z[k];
+  }
+  WProd<WT> p(w);
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    if (!pr.on[j]) continue;
+    int d = 0;
+    if (pr.nn[j] == 2) {
+      d = int(r & 1);
+      r >>= 1;
+    } else if (pr.nn[j] == 3) {
+      d = int(r % 3);
+      r /= 3;
+    }
+    const double t = d == 0 ? pr.t[j][0] : d == 1 ? pr.t[j][1] : pr.t[j][2];
+    const float th = d == 0 ? pr.th[j][0] : d == 1 ? pr.th[j][1] : pr.th[j][2];
+    const float tl = d == 0 ? pr.tl[j][0] : d == 1 ? pr.tl[j][1] : pr.tl[j][2];
+    const int col = d == 0 ? pr.col[j][0] : d == 1 ? pr.col[j][1] : pr.col[j][2];
+    p.mul_entry(t, th, tl);
+    const uint64_t m = 1ull << wr.bit[j];
+    // the word is the same for every lane: a uniform branch, no selects
+    if (W == 1 || !wr.word[j]) {
+      cx[0] = (col <= 1) ? (cx[0] | m) : (cx[0] & ~m);
+      cz[0] = (col >= 1) ? (cz[0] | m) : (cz[0] & ~m);
+    } else {
+      cx[W - 1] = (col <= 1) ? (cx[W - 1] | m) : (cx[W - 1] & ~m);
+      cz[W - 1] = (col >= 1) ? (cz[W - 1] | m) : (cz[W - 1] & ~m);
+    }
+  }
+  return p.get();
+}
+
+template <int W, typename WT, int NQ>
+__device__ __forceinline__ unsigned xs_kept_r(const XsStep& st, const XsWires<NQ>& wr,
+                                              const XsParentRows<NQ>& pr, const uint64_t* x,
+                                              const uint64_t* z, WT w, unsigned cnt) {
+  if (!st.prune || xs_keeps_all<WT>(st, w)) return cnt;
+  unsigned kept = 0;
+  for (unsigned r = 0; r < cnt; ++r) {
+    uint64_t cx[W], cz[W];
+    kept += xs_pruned<WT>(st, xs_child_r<W, WT, NQ>(wr, pr, x, z, w, r, cx, cz)) ? 0u : 1u;
+  }
+  return kept;
+}
+
 // Words of term i that hold fan-out wires; the others read as 0 (letter I,
 // which no fan-out wire is asked about).
 template <int W, typename WT>
@@ -181,13 +296,15 @@ __device__ __forceinline__ void load_fan_words(const TermsT<WT>& t, size_t i, ui
   }
 }
 
-// The calling warp's contiguous range of spans [*b, *e): consecutive spans of
-// a warp hold neighbouring parents (usually of one generator), which keeps
-// the fused pass's image cache valid from span to span.
-__device__ __forceinline__ void warp_spans(size_t nspans, size_t warps, size_t* b, size_t* e) {
-  const size_t w = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5);
-  const size_t per = (nspans + warps - 1) / warps;
-  *b = min(nspans, w * per);
+// Range r of the step's partition: spans [r per, (r + 1) per) (the last
+// ranges may be short or empty).  The emission runs one warp per range, so
+// consecutive spans of a warp hold neighbouring parents (usually of one
+// generator), which keeps the fused pass's image cache valid from span to
+// span, and the count gives one child total per range: the scan is over the
+// ranges, and a warp reads its range's offset once.
+__device__ __forceinline__ void range_spans(size_t r, size_t per, size_t nspans, size_t* b,
+                                            size_t* e) {
+  *b = min(nspans, r * per);
   *e = min(nspans, *b + per);
 }
 
@@ -199,15 +316,16 @@ __device__ __forceinline__ void load_xs_step(XsStep* dst, const XsStep& src) {
   for (int k = threadIdx.x; k < int(sizeof(XsStep) / 4); k += blockDim.x) b[k] = a[k];
 }
 
-// Children per span of kXsSpan parents (span_sums) and the per-generator
+// Children per range of spans (range_sums) and the per-generator
 // letter masks gmask [G][3][W] (OR over the generator's terms of the fan-out
 // wires carrying X, Y or Z on a non-isolated row).
-template <int W, typename WT = double>
+template <int W, typename WT, int NQ>
 __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
                                                          const unsigned long long* n_in,
                                                          const __grid_constant__ XsStep step,
+                                                         size_t nranges, size_t per,
                                                          unsigned long long* gmask,
-                                                         unsigned long long* span_sums) {
+                                                         unsigned long long* range_sums) {
   __shared__ XsStep st;
   load_xs_step(&st, step);
   __syncthreads();
@@ -217,6 +335,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
   const size_t warps = size_t(gridDim.x) * (kXsThreads / 32);
   const bool prune = st.prune != 0;
   const uint32_t words = st.words;
+  XsWires<NQ ? NQ : 1> wr;
+  if constexpr (NQ > 0) wr = xs_wires<NQ>(st);
   // running OR of a warp whose lanes all held generator cg
   uint32_t cg = 0xffffffffu;
   uint64_t acc[3][W];
@@ -237,8 +357,11 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 #pragma unroll
       for (int k = 0; k < W; ++k) acc[a][k] = 0;
   };
+  for (size_t rg = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5); rg < nranges;
+       rg += warps) {
   size_t s0, s1;
-  warp_spans(nspans, warps, &s0, &s1);
+  range_spans(rg, per, nspans, &s0, &s1);
+  unsigned long long rsum = 0;
   for (size_t span = s0; span < s1; ++span) {
     const size_t base = span * kXsSpan;
     // all loads of the span first, then the counts and masks
@@ -263,8 +386,15 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 #pragma unroll
     for (int it = 0; it < kXsItems; ++it) {
       const bool valid = g[it] != 0xffffffffu;
-      if (valid)
-        sum += xs_kept<W, WT>(st, x[it], z[it], wv[it], xs_count_children<W>(st, x[it], z[it]));
+      if (valid) {
+        if constexpr (NQ > 0) {
+          XsParentRows<NQ> pr;
+          const unsigned c = xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
+          sum += xs_kept_r<W, WT, NQ>(st, wr, pr, x[it], z[it], wv[it], c);
+        } else {
+          sum += xs_kept<W, WT>(st, x[it], z[it], wv[it], xs_count_children<W>(st, x[it], z[it]));
+        }
+      }
       uint64_t m[3][W];
 #pragma unroll
       for (int k = 0; k < W; ++k) {  // zero for invalid lanes (their x, z are 0)
@@ -303,33 +433,67 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-    if (lane == 0) span_sums[span] = sum;
+    rsum += sum;
+  }
+  if (lane == 0) range_sums[rg] = rsum;
   }
   flush();
 }
 
-// Children of each parent at span_offs[span] (exclusive scan of the span
-// sums) plus the parent's offset within the span, in parent order.  A launch
+// Asynchronous global-to-shared copies (cp.async, completed by the copy unit:
+// the thread's later wait_group returns once its own copies have landed).
+__device__ __forceinline__ void cp_async_bytes8(void* smem, const void* gmem) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes4(void* smem, const void* gmem) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One span's parents in shared memory (structure of arrays, slot = item x 32 + lane).
+template <int W, typename WT>
+struct XsStage {
+  uint64_t x[W][kXsSpan], z[W][kXsSpan];
+  WT w[kXsSpan];
+  uint32_t g[kXsSpan];
+};
+constexpr int kXsStages = 3;  // spans per warp in flight: the current one and two ahead
+
+template <int W, typename WT>
+__host__ __device__ constexpr size_t xs_emit_stage_bytes() {
+  return size_t(kXsThreads / 32) * kXsStages * sizeof(XsStage<W, WT>);
+}
+
+// Children of each parent at its range's offset (exclusive scan of the range
+// sums) plus the children of the range's earlier parents, in parent order.  A launch
 // sized for cap < *total_d (an output size guessed too small) does nothing.
-// CK selects the fused Clifford pass: 0 none, 1 gate list, 3 or 4 chunk
-// tables (dynamic shared memory holds the pass).
-template <int W, typename WT, int CK>
+// CK selects the fused Clifford pass: 0 none, 1 gate list (in shared memory
+// after the stages), 3 or 4 chunk tables (read from global memory: the image
+// cache of clifford_table_map_full hits for all but the first parent of a run
+// of parents with the same touched letters, so the tables are rarely read).
+// Each lane copies its parents of the next two spans into its warp's stages
+// with cp.async while it writes the children of the current span, so every
+// warp keeps two spans of loads in flight without holding them in registers.
+template <int W, typename WT, int CK, int NQ>
 __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
-    TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* span_offs,
-    const unsigned long long* total_d, unsigned long long cap, const __grid_constant__ XsStep step,
-    XsPass ps, double* pruned, TermsT<WT> out) {
+    TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
+    size_t per, const unsigned long long* total_d, unsigned long long cap,
+    const __grid_constant__ XsStep step, XsPass ps, double* pruned, TermsT<WT> out) {
   if (*total_d > cap) return;
   extern __shared__ __align__(16) uint64_t s_dyn[];
   __shared__ XsStep st;
   load_xs_step(&st, step);
-  const uint8_t* s_e = nullptr;
-  if constexpr (CK >= 3) {
-    constexpr int E = 1 << (2 * CK);
-    uint8_t* e8 = reinterpret_cast<uint8_t*>(s_dyn + size_t(ps.chunks) * E * 2 * W);
-    load_clifford_table<CK, W>(s_dyn, e8, ps.tab_xz, ps.tab_e, ps.chunks);
-    s_e = e8;
-  } else if constexpr (CK == 1) {
-    uint32_t* s_ops = reinterpret_cast<uint32_t*>(s_dyn);
+  auto* stages = reinterpret_cast<XsStage<W, WT>*>(s_dyn);
+  if constexpr (CK == 1) {
+    uint32_t* s_ops = reinterpret_cast<uint32_t*>(s_dyn + xs_emit_stage_bytes<W, WT>() / 8);
     for (int i = threadIdx.x; i < ps.nops; i += blockDim.x) s_ops[i] = ps.ops[i];
   }
   __syncthreads();
@@ -338,24 +502,68 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   const unsigned lane = threadIdx.x & 31;
   const size_t warps = size_t(gridDim.x) * (kXsThreads / 32);
   const bool prune = st.prune != 0;
+  XsWires<NQ ? NQ : 1> wr;
+  if constexpr (NQ > 0) wr = xs_wires<NQ>(st);
   FullCache<W> fc;
+  XsStage<W, WT>* my = stages + (threadIdx.x >> 5) * kXsStages;
+  uint64_t* ox[W];
+  uint64_t* oz[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    ox[k] = out.x + size_t(k) * out.cap;
+    oz[k] = out.z + size_t(k) * out.cap;
+  }
+  const size_t rg = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5);
   size_t s0, s1;
-  warp_spans(nspans, warps, &s0, &s1);
+  range_spans(rg, per, nspans, &s0, &s1);
+  (void)warps;
+  // the children of this warp's range start at its range's offset
+  unsigned long long run = s0 < s1 ? range_offs[rg] : 0ull;
+  // this lane's parents of `span` into stage `b` (none beyond the range or N;
+  // a group is committed either way, so the wait counts stay uniform)
+  auto issue = [&](size_t span, int b) {
+    if (span < s1) {
+      const size_t base = span * kXsSpan;
+#pragma unroll
+      for (int it = 0; it < kXsItems; ++it) {
+        const size_t i = base + size_t(it) * 32 + lane;
+        const int slot = it * 32 + int(lane);
+        if (i < N) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            cp_async_bytes8(&my[b].x[k][slot], in.x + k * in.cap + i);
+            cp_async_bytes8(&my[b].z[k][slot], in.z + k * in.cap + i);
+          }
+          if constexpr (sizeof(WT) == 8) cp_async_bytes8(&my[b].w[slot], in.w + i);
+          else cp_async_bytes4(&my[b].w[slot], in.w + i);
+          cp_async_bytes4(&my[b].g[slot], in.g + i);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  issue(s0, 0);
+  issue(s0 + 1, 1);
+  int b = 0;
   for (size_t span = s0; span < s1; ++span) {
+    issue(span + 2, (b + 2) % kXsStages);
+    cp_async_wait<2>();  // this span's group has landed (two newer may be in flight)
+    const XsStage<W, WT>& sg = my[b];
     const size_t base = span * kXsSpan;
-    // every parent of the lane first (independent loads), then the counts
-    // and the warp's offsets in parent order (with pruning: of the
-    // surviving children)
     uint64_t x[kXsItems][W], z[kXsItems][W];
     WT wv[kXsItems];
     uint32_t g[kXsItems];
 #pragma unroll
     for (int it = 0; it < kXsItems; ++it) {
-      const size_t i = base + size_t(it) * 32 + lane;
-      if (i < N) {
-        load_term<W>(in, i, x[it], z[it]);
-        wv[it] = in.w[i];
-        g[it] = in.g[i];
+      const int slot = it * 32 + int(lane);
+      if (base + size_t(slot) < N) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          x[it][k] = sg.x[k][slot];
+          z[it][k] = sg.z[k][slot];
+        }
+        wv[it] = sg.w[slot];
+        g[it] = sg.g[slot];
       } else {
 #pragma unroll
         for (int k = 0; k < W; ++k) x[it][k] = z[it][k] = 0ull;
@@ -365,12 +573,20 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     }
     unsigned cnt[kXsItems];
     unsigned long long loc[kXsItems];
-    unsigned long long run = span_offs[span];
 #pragma unroll
     for (int it = 0; it < kXsItems; ++it) {
       const bool valid = g[it] != 0xffffffffu;
-      const unsigned c = valid ? xs_count_children<W>(st, x[it], z[it]) : 0u;
-      const unsigned kc = valid ? xs_kept<W, WT>(st, x[it], z[it], wv[it], c) : 0u;
+      unsigned c = 0, kc = 0;
+      if (valid) {
+        if constexpr (NQ > 0) {
+          XsParentRows<NQ> pr;
+          c = xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
+          kc = xs_kept_r<W, WT, NQ>(st, wr, pr, x[it], z[it], wv[it], c);
+        } else {
+          c = xs_count_children<W>(st, x[it], z[it]);
+          kc = xs_kept<W, WT>(st, x[it], z[it], wv[it], c);
+        }
+      }
       unsigned inc = kc;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -386,29 +602,46 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
       if (!cnt[it]) continue;
       WT w = wv[it];
       if constexpr (CK >= 3) {
-        if (clifford_table_map_full<W, CK>(x[it], z[it], s_dyn, s_e, ps.chunks, ps.live, ps.pmk,
-                                           fc))
+        if (clifford_table_map_full<W, CK>(x[it], z[it], ps.tab_xz, ps.tab_e, ps.chunks, ps.live,
+                                           ps.pmk, fc))
           w = wneg(w);
       } else if constexpr (CK == 1) {
         int neg = 0;
-        apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn), ps.nops, x[it], z[it], &neg);
+        apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn + xs_emit_stage_bytes<W, WT>() / 8),
+                     ps.nops, x[it], z[it], &neg);
         if (neg) w = wneg(w);
       }
       const bool all = !prune || xs_keeps_all<WT>(st, w);
+      // the parent's rows again (shared-memory reads once per parent; kept
+      // in registers for one parent at a time)
+      XsParentRows<NQ ? NQ : 1> pr;
+      if constexpr (NQ > 0) xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
       // o + (children kept) <= *total_d <= cap (the counts the span sums came from)
-      unsigned long long o = loc[it];
+      size_t o = size_t(loc[it]);
       for (unsigned r = 0; r < cnt[it]; ++r) {
         uint64_t cx[W], cz[W];
-        const WT v = xs_child<W, WT>(st, x[it], z[it], w, r, cx, cz);
+        WT v;
+        if constexpr (NQ > 0) v = xs_child_r<W, WT, NQ>(wr, pr, x[it], z[it], w, r, cx, cz);
+        else v = xs_child<W, WT>(st, x[it], z[it], w, r, cx, cz);
         if (!all && xs_pruned<WT>(st, v)) {
           atomicAdd(&pruned[g[it]], double(v) * double(v));
           continue;
         }
-        if (o < cap) store_term<W>(out, size_t(o), cx, cz, v, g[it]);
+        if (o < cap) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            ox[k][o] = cx[k];
+            oz[k][o] = cz[k];
+          }
+          out.w[o] = v;
+          out.g[o] = g[it];
+        }
         ++o;
       }
     }
+    b = (b + 1) % kXsStages;
   }
+  cp_async_wait<0>();
 }
 
 }  // namespace dev

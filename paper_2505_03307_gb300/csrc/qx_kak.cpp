@@ -15,12 +15,12 @@
 // entangling part, whose phases solve a 4 x 4 linear system for (g, a, b, c).
 // Each SU(2) factor becomes RZ(alpha) RY(beta) RZ(gamma) (Euler angles).
 //
-// The real symmetric matrices Re M and Im M commute; a fixed-seed random
-// combination of the two is diagonalised by Jacobi rotations (its eigenvectors
-// then diagonalise M unless eigenvalues collide by accident, which the
-// residual check catches; the next combination is tried).  The decomposition
-// is accepted only when the product of its gates equals U up to a global phase
-// to 1e-10 (max entry), else QX_EINVAL.
+// The real symmetric matrices Re M and Im M commute; a combination of the two
+// with a fixed irrational coefficient is diagonalised by Jacobi rotations (its
+// eigenvectors then diagonalise M unless eigenvalues nearly collide by
+// accident).  Six coefficients are tried and the decomposition whose gate
+// product is closest to U (up to a global phase, max entry) is kept; it is
+// accepted when that distance is at most 1e-10, else QX_EINVAL.
 #include <array>
 #include <cmath>
 #include <complex>
@@ -283,6 +283,7 @@ bool decompose(const M4& u_in, int q0, int q1, std::vector<qx_instr>* out, doubl
     for (int k = 0; k < 4; ++k) lam[p][k] = d[k][k].real();
   }
   const double mix[6] = {0.61803398875, 1.41421356237, -0.7320508, 2.2360679775, -1.9, 0.3};
+  double best = INFINITY;
   for (int attempt = 0; attempt < 6; ++attempt) {
     R4 a{}, o{};
     for (int i = 0; i < 4; ++i)
@@ -350,13 +351,13 @@ bool decompose(const M4& u_in, int q0, int q1, std::vector<qx_instr>* out, doubl
     euler(a0, q0);
     euler(a1, q1);
     const double res = phase_residual(product(gs, q0), u_in);
-    if (res <= 1e-10) {
+    if (res < best) {  // keep the most accurate of the combinations
+      best = res;
       *out = gs;
       *residual = res;
-      return true;
     }
   }
-  return false;
+  return best <= 1e-10;
 }
 
 }  // namespace

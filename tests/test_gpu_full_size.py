@@ -135,3 +135,75 @@ def test_hea_n16_four_layers_stops_at_budget():
     n2, two = W.hea(1, n=16, layers=2)
     res = qx.propagate(qx.group_ops(qx.load_circuit(n2, two)), gens=(0, 1))
     assert res.info(0)["nterms"] == 349920
+
+
+def _deep_samples(n, instrs, S, gens, count=256):
+    """Sampled strings of fan_in_deep generators and their exact coefficients
+    (sign and rest of the string from the oracle's Clifford-only run)."""
+    cliff = [ins for ins in instrs if ins[0] != "RZ"]
+    base = [O.as_dict(gen) for gen in O.propagate(n, cliff, mode="gate", gens=None, threads=8)]
+    thetas = {ins[1]: ins[3] for ins in instrs if ins[0] == "RZ"}
+    rng = np.random.default_rng(7)
+    out = []
+    for g in gens:
+        (bs, bw), = base[g].items()
+        for pat in rng.integers(0, 2, size=(count, S)):
+            s = "".join("XY"[b] for b in pat) + bs[S:]
+            v = bw
+            for q in range(S):
+                v *= math.cos(thetas[q]) if pat[q] == 0 else math.sin(thetas[q])
+            out.append((g, s, v))
+    return out
+
+
+def test_fan_in_deep_n100_fp32_and_pruning_as_benchmarked():
+    """The benchmark's configuration (eps = 1e-14) in FP64 and FP32: no
+    coefficient of this circuit falls below 1e-14 (the smallest is ~5e-12), so
+    the counts are the closed form's and nothing is pruned; FP32 weights
+    within 1e-5 relative of the exact coefficients."""
+    n, instrs = W.fan_in_deep(1)
+    S = 20
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    samples = _deep_samples(n, instrs, S, (20, 61, 99))
+    worst = {}
+    for precision in (64, 32):
+        res = qx.propagate(plan, eps=1e-14, precision=precision)
+        assert res.nterms == 80 * 2 ** 20 + 2 * S
+        for g in (0, 20, 61, 99):
+            info = res.info(g)
+            assert info["nterms"] == (2 ** 20 if g >= S else 2)
+            assert info["pruned_sumsq"] == 0.0
+        got = res.coeff_batch([g for g, _, _ in samples], [s for _, s, _ in samples])
+        rel = max(abs(x - v) / abs(v) for (_, _, v), x in zip(samples, got))
+        worst[precision] = rel
+        if precision == 64:
+            for (g, s, v), x in zip(samples, got):
+                assert close(x, v), (g, s, x, v)
+        else:
+            assert rel <= 1e-5, rel
+        res.free()
+    print(f"fan_in_deep_n100 eps=1e-14: max relative error FP64 {worst[64]:.2e}, "
+          f"FP32 {worst[32]:.2e}")
+
+
+def test_random_pairs_n100_fp32_against_the_digest():
+    """FP32 weights on the n = 100, 100,000-gate circuit (eps = 1e-14): term
+    counts and norms as the oracle's digest, sampled weights within 1e-5
+    relative of the oracle's."""
+    dg = json.load(open(os.path.join(GOLDEN, "random_pairs_n100_digest.json")))
+    n, instrs = W.random_pairs(1)
+    res = qx.propagate(qx.group_ops(qx.load_circuit(n, instrs)), eps=dg["eps"], precision=32)
+    worst = 0.0
+    for g, d in enumerate(dg["generators"]):
+        info = res.info(g)
+        assert info["nterms"] == d["nterms"], g
+        assert abs(info["sumsq"] - d["sumsq"]) < 1e-5
+        strings, w = res.export_strings(g)
+        got = dict(zip(strings, w.tolist()))
+        for s, hx in d["sample"]:
+            want = float.fromhex(hx)
+            assert s in got, (g, s)
+            rel = abs(got[s] - want) / abs(want)
+            assert rel <= 1e-5, (g, s, got[s], want)
+            worst = max(worst, rel)
+    print(f"random_pairs_n100 FP32: max relative error {worst:.2e}")
