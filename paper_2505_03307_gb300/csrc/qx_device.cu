@@ -134,12 +134,27 @@ void set_pool_threshold() {
 // expansion) and the device results decide whether the guess held; a wrong
 // guess costs only the discarded launches.  Plans may be shared between
 // threads, so the fields are atomics (a torn guess is just a wrong one).
-enum : int { kHintNone = 0, kHintExpand = 1, kHintBlocks = 2 };
+enum : int { kHintNone = 0, kHintExpand = 1, kHintBlocks = 2, kHintReplay = 3 };
 struct FanHint {
   std::atomic<int> kind{kHintNone};
   std::atomic<unsigned long long> total{0};
   std::atomic<unsigned> nblk{0};  // blocks of the last block-ordered run (table size)
   std::atomic<unsigned> streak{0};  // runs in a row that kept the guess
+  // A small step's range offsets from a run whose guess held (device memory
+  // of the plan, written once and published at the end of that run), one
+  // record per precision: a later run with the same input count, partition
+  // and threshold launches the emission on them without counting, and the
+  // emission checks every range against them.  One failed check retires the
+  // record.
+  struct Record {
+    std::atomic<unsigned long long*> offs{nullptr};
+    std::atomic<int> claim{0};  // a run is recording
+    std::atomic<int> bad{0};
+    size_t n = 0, ranges = 0, per = 0;
+    unsigned long long total = 0;
+    double eps = 0.0;
+  };
+  Record rec[2];  // [FP32]
 };
 
 // Device copy of the plan: Clifford passes (gate lists or chunk tables) and
@@ -210,6 +225,10 @@ namespace qx {
 
 void free_plan_device(qx_plan* p) {
   if (!p || !p->dev) return;
+  if (p->dev->hints)
+    for (size_t i = 0; i < std::max<size_t>(1, p->fans.size()); ++i)
+      for (FanHint::Record& rc : p->dev->hints[i].rec)
+        if (unsigned long long* r = rc.offs.load()) cudaFree(r);
   if (p->dev->base) cudaFree(p->dev->base);
   delete p->dev;
   p->dev = nullptr;
@@ -489,7 +508,7 @@ struct Ctx {
   // run (no host round trip of their own); a failed check repeats the run with
   // every step checked at once (defer = false).
   struct Deferred {
-    int kind = 0;  // kHintExpand or kHintBlocks
+    int kind = 0;  // kHintExpand, kHintBlocks or kHintReplay
     FanHint* hint = nullptr;
     const FanStep* fs = nullptr;
     unsigned long long expect = 0;    // the recorded output size (expansion)
@@ -497,10 +516,20 @@ struct Ctx {
     const unsigned long long* total = nullptr;
     const unsigned* err = nullptr;
     const unsigned* nblk = nullptr;
+    const uint32_t* gwire = nullptr;  // pinned: letter codes (replayed offsets)
+    FanHint::Record* rec = nullptr;   // the record it replayed
   };
   bool defer = false;
   bool retry = false;  // set by a run whose deferred checks failed
   std::vector<Deferred> deferred;
+  // range offsets recorded by this run, published when it completes
+  struct Record {
+    FanHint::Record* rec = nullptr;
+    unsigned long long* offs = nullptr;
+    size_t n = 0, ranges = 0, per = 0;
+    unsigned long long total = 0;
+  };
+  std::vector<Record> records;
   size_t rb_off = 0;
   Ctx() = default;
   Ctx(const Ctx&) = delete;
@@ -1462,13 +1491,16 @@ void split_fan(const Ctx& c, const FanStep& fs, const std::vector<unsigned long 
 }
 
 // Fused expansion of a small fan-out step (qx_expand_fused.cuh), in parts:
-// xs_count uploads the step's tables, writes the letter masks (gmask) and the
-// children per tile and scans them (the total lands in ncnt[2]); xs_emit
-// allocates the output for cap children and writes them, applying `fused`
-// (a Clifford pass on other qubits, or none) to each parent; xs_accept makes
-// the output current.
+// xs_count writes the letter masks (gmask) and the children per range and
+// scans them (the total lands in ncnt[2]); xs_emit allocates the output for
+// cap children and writes them, applying `fused` (a Clifford pass on other
+// qubits, or none) to each parent; xs_accept makes the output current.  A
+// run on the step's recorded offsets (xs_replay) skips the count.
 struct XsPending {
-  unsigned long long* tiles = nullptr;  // range sums -> offsets
+  unsigned long long* tiles = nullptr;  // range sums -> offsets (owned)
+  const unsigned long long* offs = nullptr;     // the range offsets the emission uses
+  const unsigned long long* total_d = nullptr;  // their total (device)
+  XsCheck chk{nullptr, nullptr};
   TermBuf out;
   size_t nranges = 0;  // ranges of spans: one warp of the emission each
   size_t per = 0;      // spans per range
@@ -1530,12 +1562,12 @@ XsStep xs_step(const FanStep& fs, double eps) {
 
 // The partition of a small step's spans into ranges: one warp of the
 // emission per range, and exactly one wave of emission blocks (as many as
-// stay resident on every SM with the kernel's registers and parent stages:
-// a second, partial wave would leave most SMs idle behind its last ranges).
+// stay resident on every SM with the kernel's registers and gate list: a
+// second, partial wave would leave most SMs idle behind its last ranges).
 template <int W, typename WT, int CK, int NQ>
 int xs_emit_per_sm(size_t smem) {
   static thread_local int cached[2] = {0, 0};  // [smem has a gate list]
-  int& slot = cached[smem > xs_emit_stage_bytes<W, WT>() ? 1 : 0];
+  int& slot = cached[smem ? 1 : 0];
   if (slot) return slot;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xs_emit<W, WT, CK, NQ>, kXsThreads,
@@ -1550,8 +1582,8 @@ int xs_emit_per_sm(size_t smem) {
 template <int W, typename WT>
 int xs_emit_blocks_per_sm(const FanStep& fs, const qx_plan_device::Pass* fused) {
   const int nq = int(fs.qs.size());
-  const size_t smem = xs_emit_stage_bytes<W, WT>() +
-                      (fused && !fused->identity && !fused->use_table ? size_t(fused->nops) * 4 : 0);
+  const size_t smem =
+      fused && !fused->identity && !fused->use_table ? size_t(fused->nops) * 4 : 0;
   auto pick = [&](auto ck) {
     constexpr int CK = decltype(ck)::value;
     return nq == 1   ? xs_emit_per_sm<W, WT, CK, 1>(smem)
@@ -1613,14 +1645,15 @@ qx_status xs_count(Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused,
   k_scan_sums<<<1, 1024, 0, c.al.s>>>(xp->tiles, R, s.ncnt + 2);
   c.end(KC_SCAN, 1, uint64_t(R) * 16);
   QX_TRY_CUDA(cudaGetLastError());
+  xp->offs = xp->tiles;
+  xp->total_d = s.ncnt + 2;
   return QX_OK;
 }
 
 template <int W, typename WT, int CK>
 void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap, const XsPass& ps,
                size_t extra) {
-  // dynamic shared memory: every warp's parent stages, then a gate list
-  const size_t smem = xs_emit_stage_bytes<W, WT>() + extra;
+  const size_t smem = extra;  // dynamic shared memory: the gate list
   const unsigned grid = xp->grid;  // one warp per range of the count's partition
   const XsStep st = xs_step(fs, c.eps);
   const auto in = c.cur.view<WT>();
@@ -1628,13 +1661,13 @@ void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap,
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   if (st.nq == 1)
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
   else if (st.nq == 2)
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
   else
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->tiles, xp->per, c.sc.ncnt + 2, cap, st, ps, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
 }
 
 template <int W, typename WT>
@@ -1679,6 +1712,104 @@ qx_status xs_accept(Ctx& c, XsPending* xp, unsigned long long total, int nfused)
   return QX_OK;
 }
 
+// Keeps the range offsets of a step launched on its guessed size (the scan
+// of this run's count): the plan's copy, published only when the run
+// completes with every check held (then every step's input was exact).  One
+// run per step and precision records.
+template <int W, typename WT>
+void xs_record(Ctx& c, FanHint* hint, const XsPending& xp, unsigned long long total) {
+  FanHint::Record& h = hint->rec[sizeof(WT) == 4];
+  if (!c.defer || !xp.tiles || h.bad.load() || h.offs.load(std::memory_order_acquire)) return;
+  int free_slot = 0;
+  if (!h.claim.compare_exchange_strong(free_slot, 1)) return;
+  unsigned long long* r = nullptr;
+  const size_t R = xp.nranges;
+  if (cudaMalloc(&r, (R + 1) * 8) != cudaSuccess ||
+      cudaMemcpyAsync(r, xp.tiles, R * 8, cudaMemcpyDeviceToDevice, c.al.s) != cudaSuccess ||
+      cudaMemcpyAsync(r + R, c.sc.ncnt + 2, 8, cudaMemcpyDeviceToDevice, c.al.s) != cudaSuccess) {
+    cudaGetLastError();
+    if (r) {
+      cudaStreamSynchronize(c.al.s);
+      cudaFree(r);
+    }
+    h.claim.store(0);
+    return;
+  }
+  Ctx::Record rc;
+  rc.rec = &h;
+  rc.offs = r;
+  rc.n = c.N;
+  rc.ranges = R;
+  rc.per = xp.per;
+  rc.total = total;
+  c.records.push_back(rc);
+}
+
+// The run's records into their hints (the run completed; its stream work is done).
+void publish_records(Ctx& c) {
+  for (const Ctx::Record& rc : c.records) {
+    FanHint::Record* h = rc.rec;
+    h->n = rc.n;
+    h->ranges = rc.ranges;
+    h->per = rc.per;
+    h->total = rc.total;
+    h->eps = c.eps;
+    h->offs.store(rc.offs, std::memory_order_release);
+  }
+  c.records.clear();
+}
+
+// A step launched on its recorded range offsets: the emission alone, with
+// the checks of XsCheck read back at the end of the run.  *ran is false
+// (nothing launched) when the record does not apply to this run.
+template <int W, typename WT>
+qx_status xs_replay(Ctx& c, const FanStep& fs, FanHint* hint, const qx_plan_device::Pass* fused,
+                    XsPending* xp, bool* ran, unsigned long long* total) {
+  *ran = false;
+  if (!hint || !c.defer) return QX_OK;
+  FanHint::Record& h = hint->rec[sizeof(WT) == 4];
+  if (h.bad.load(std::memory_order_relaxed)) return QX_OK;
+  const unsigned long long* rec = h.offs.load(std::memory_order_acquire);
+  if (!rec || h.n != c.N || h.eps != c.eps) return QX_OK;
+  xs_partition<W, WT>(c, fs, fused, xp);
+  if (xp->nranges != h.ranges || xp->per != h.per || !limits_ok(c, h.total)) return QX_OK;
+  const size_t G = size_t(c.G);
+  const size_t bytes = 16 + G * 4;  // err word, then the letter codes
+  auto* rb = static_cast<unsigned char*>(rb_take(c, bytes));
+  if (!rb) return QX_OK;
+  void* chk = c.al.get(bytes);
+  if (!chk) return QX_OK;
+  QX_TRY_CUDA(cudaMemsetAsync(chk, 0, bytes, c.al.s));
+  xp->offs = rec;
+  xp->total_d = rec + xp->nranges;
+  xp->chk.err = static_cast<unsigned*>(chk);
+  xp->chk.gwire = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(chk) + 16);
+  const qx_status st = xs_emit<W, WT>(c, fs, xp, h.total, fused);
+  if (st != QX_OK) {
+    c.al.put(chk);
+    if (st != QX_ENOMEM) return st;
+    c.al.put(xp->out.base);  // the recorded size does not fit now: count first
+    *xp = XsPending();
+    clear_error();
+    cudaGetLastError();
+    return QX_OK;
+  }
+  QX_TRY_CUDA(cudaMemcpyAsync(rb, chk, bytes, cudaMemcpyDeviceToHost, c.al.s));
+  c.al.put(chk);
+  Ctx::Deferred d;
+  d.kind = kHintReplay;
+  d.hint = hint;
+  d.rec = &h;
+  d.fs = &fs;
+  d.expect = h.total;
+  d.err = reinterpret_cast<const unsigned*>(rb);
+  d.gwire = reinterpret_cast<const uint32_t*>(rb + 16);
+  c.deferred.push_back(std::move(d));
+  *ran = true;
+  *total = h.total;
+  return QX_OK;
+}
+
 // A small fan-out step through the fused expansion.  `pre` is the pending
 // Clifford pass before the step and `tail` the program's last pass after it
 // (both act on other qubits than the step's wires, either may be NULL);
@@ -1705,6 +1836,15 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
     uses_tail = true;
   }
   XsPending xp;
+  bool replayed = false;
+  unsigned long long rtotal = 0;
+  QX_TRY((xs_replay<W, WT>(c, fs, hint, fused, &xp, &replayed, &rtotal)));
+  if (replayed) {
+    *done = true;
+    *absorbed = uses_tail;
+    return xs_accept<W, WT>(c, &xp, rtotal, nfused);
+  }
+  xp = XsPending();
   qx_status st = xs_count<W, WT>(c, fs, fused, &xp);
   if (st != QX_OK) {
     xs_release(c, &xp);
@@ -1753,6 +1893,7 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
           d.gm = rg;
           d.total = rt;
           c.deferred.push_back(std::move(d));
+          xs_record<W, WT>(c, hint, xp, cap);
           return finish(cap);
         }
       }
@@ -1777,6 +1918,7 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
         if (total == cap) hint->streak.fetch_add(1, std::memory_order_relaxed);
         else hint->streak.store(0, std::memory_order_relaxed);
         c.st.guesses_held++;
+        if (total == cap) xs_record<W, WT>(c, hint, xp, total);
         return finish(total);
       }
       hint->streak.store(0, std::memory_order_relaxed);
@@ -2239,6 +2381,18 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
       std::vector<const FanQubit*> mq, fq;
       split_fan(c, *d.fs, gmv, &mixed, &mq, &fq);
       ok = mq.empty() && *d.total == d.expect;
+    } else if (d.kind == kHintReplay) {  // every range as recorded, no merge wire
+      ok = *d.err == 0;
+      const size_t nq = d.fs->qs.size();
+      for (size_t g = 0; ok && g < G; ++g)
+        for (size_t j = 0; j < nq; ++j) {
+          const uint32_t a = (d.gwire[g] >> (3 * j)) & 7u;
+          if (a & (a - 1)) {  // two letters on a non-isolated row
+            ok = false;
+            break;
+          }
+        }
+      if (!ok) d.rec->bad.store(1);
     } else {  // every block complete
       ok = *d.err == 0;
     }
@@ -2257,6 +2411,7 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     c.retry = true;
     return QX_OK;
   }
+  publish_records(c);
   c.tm.resolve(&c.st);
   c.st.final_terms = c.N;
   c.st.K = p->K;
@@ -2269,6 +2424,15 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   r->st = c.st;
   *out = r;
   return QX_OK;
+}
+
+// Records of a run that did not complete (its stream work is done).
+void drop_records(Ctx& c) {
+  for (const Ctx::Record& rc : c.records) {
+    cudaFree(rc.offs);
+    rc.rec->claim.store(0);
+  }
+  c.records.clear();
 }
 
 qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, int gen_begin,
@@ -2403,6 +2567,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
                                : propagate_impl<2, double>(c, ix, iz, iw, gen_begin, from, out);
     if (s != QX_OK || !c.retry) break;
     // release the first attempt's buffers (its stream work is complete)
+    drop_records(c);
     const uint64_t missed = c.st.guesses_missed + c.deferred.size();
     c.al.put(c.cur.base);
     c.cur = TermBuf();
@@ -2425,6 +2590,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
     free_scratch(c);
     cudaStreamSynchronize(c.al.s);
     cudaGetLastError();
+    drop_records(c);
     release_table(c.ftab);
     fail(s, msg);
     return s;

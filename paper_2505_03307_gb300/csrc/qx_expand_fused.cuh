@@ -23,6 +23,12 @@
 // each lane loads all kXsItems of its parents before it writes anything, so a
 // warp keeps that many parents per lane in flight.
 //
+// A plan whose step has kept the same range sums records them (the device
+// driver keeps the scan's offsets): later runs launch only k_xs_emit on the
+// recorded offsets, with an XsCheck that flags any range whose children
+// differ from its share and collects the letter codes of the merge test, so
+// the whole step is one pass over the parents, checked at the end of the run.
+//
 // The FP64 unit of this GPU is the scarce one (about 1.3 TFLOP/s against
 // tens for FP32), so nothing here compares or converts in FP64: pruning tests
 // |w| < eps on the weight's bits as integers, a parent whose |w| is at least
@@ -308,6 +314,38 @@ __device__ __forceinline__ void range_spans(size_t r, size_t per, size_t nspans,
   *e = min(nspans, *b + per);
 }
 
+// The checks of an emission launched on a step's recorded range offsets
+// instead of a fresh count (both null after a count): err is set when some
+// range's children differ from its recorded share (its writes stay inside
+// that share), and gwire[g] collects the letter codes of generator g's
+// parents on the fan-out wires (bit 3j + a: wire j carries letter a + 1 on a
+// non-isolated row), which decide, as the count's letter masks do, whether
+// some wire needed a merge.
+struct XsCheck {
+  unsigned* err;
+  uint32_t* gwire;
+};
+
+// The letter code of one parent (see XsCheck).
+template <int W, int NQ>
+__device__ __forceinline__ uint32_t xs_wire_code(const XsStep& st, const XsWires<NQ ? NQ : 1>& wr,
+                                                 const uint64_t* x, const uint64_t* z) {
+  uint32_t code = 0;
+  const int nq = NQ > 0 ? NQ : st.nq;
+#pragma unroll
+  for (int j = 0; j < (NQ > 0 ? NQ : kSmallMaxWires); ++j) {
+    if (j >= nq) break;
+    const int wd = NQ > 0 ? wr.word[j] : st.word[j];
+    const int b = NQ > 0 ? wr.bit[j] : st.bit[j];
+    const bool hi = W > 1 && wd;
+    const uint64_t xw = hi ? x[W - 1] : x[0], zw = hi ? z[W - 1] : z[0];
+    const int xb = int((xw >> b) & 1), zb = int((zw >> b) & 1);
+    const int L = xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+    if (L && ((st.niso[L - 1][hi ? W - 1 : 0] >> b) & 1)) code |= 1u << (3 * j + L - 1);
+  }
+  return code;
+}
+
 // Copies the step record into shared memory in 4-byte words.
 __device__ __forceinline__ void load_xs_step(XsStep* dst, const XsStep& src) {
   static_assert(sizeof(XsStep) % 4 == 0, "XsStep is copied in 4-byte words");
@@ -440,60 +478,33 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
   flush();
 }
 
-// Asynchronous global-to-shared copies (cp.async, completed by the copy unit:
-// the thread's later wait_group returns once its own copies have landed).
-__device__ __forceinline__ void cp_async_bytes8(void* smem, const void* gmem) {
-  const unsigned d = unsigned(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_bytes4(void* smem, const void* gmem) {
-  const unsigned d = unsigned(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// One span's parents in shared memory (structure of arrays, slot = item x 32 + lane).
-template <int W, typename WT>
-struct XsStage {
-  uint64_t x[W][kXsSpan], z[W][kXsSpan];
-  WT w[kXsSpan];
-  uint32_t g[kXsSpan];
-};
-constexpr int kXsStages = 3;  // spans per warp in flight: the current one and two ahead
-
-template <int W, typename WT>
-__host__ __device__ constexpr size_t xs_emit_stage_bytes() {
-  return size_t(kXsThreads / 32) * kXsStages * sizeof(XsStage<W, WT>);
-}
-
 // Children of each parent at its range's offset (exclusive scan of the range
-// sums) plus the children of the range's earlier parents, in parent order.  A launch
-// sized for cap < *total_d (an output size guessed too small) does nothing.
-// CK selects the fused Clifford pass: 0 none, 1 gate list (in shared memory
-// after the stages), 3 or 4 chunk tables (read from global memory: the image
-// cache of clifford_table_map_full hits for all but the first parent of a run
-// of parents with the same touched letters, so the tables are rarely read).
-// Each lane copies its parents of the next two spans into its warp's stages
-// with cp.async while it writes the children of the current span, so every
-// warp keeps two spans of loads in flight without holding them in registers.
+// sums, or the offsets recorded by an earlier run of the step) plus the
+// children of the range's earlier parents, in parent order; no write leaves
+// the range's share [range_offs[r], range_offs[r + 1]) (the last range ends
+// at *total_d).  A launch sized for cap < *total_d (an output size guessed
+// too small) does nothing.
+// CK selects the fused Clifford pass: 0 none, 1 gate list (in shared
+// memory), 3 or 4 chunk tables (read from global memory: the image cache of
+// clifford_table_map_full hits for all but the first parent of a run of
+// parents with the same touched letters, so the tables are rarely read).
+// Each lane loads both of its parents of a span into registers before it
+// counts or writes anything.  (Staging the next two spans in shared memory
+// with cp.async, or one parent at a time at three blocks per SM, measured
+// 9 % and 13 % slower on the 84M-term chain.)
 template <int W, typename WT, int CK, int NQ>
 __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
-    const __grid_constant__ XsStep step, XsPass ps, double* pruned, TermsT<WT> out) {
-  if (*total_d > cap) return;
+    const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, double* pruned,
+    TermsT<WT> out) {
+  const unsigned long long total = *total_d;
+  if (total > cap) return;
   extern __shared__ __align__(16) uint64_t s_dyn[];
   __shared__ XsStep st;
   load_xs_step(&st, step);
-  auto* stages = reinterpret_cast<XsStage<W, WT>*>(s_dyn);
   if constexpr (CK == 1) {
-    uint32_t* s_ops = reinterpret_cast<uint32_t*>(s_dyn + xs_emit_stage_bytes<W, WT>() / 8);
+    uint32_t* s_ops = reinterpret_cast<uint32_t*>(s_dyn);
     for (int i = threadIdx.x; i < ps.nops; i += blockDim.x) s_ops[i] = ps.ops[i];
   }
   __syncthreads();
@@ -505,7 +516,6 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   XsWires<NQ ? NQ : 1> wr;
   if constexpr (NQ > 0) wr = xs_wires<NQ>(st);
   FullCache<W> fc;
-  XsStage<W, WT>* my = stages + (threadIdx.x >> 5) * kXsStages;
   uint64_t* ox[W];
   uint64_t* oz[W];
 #pragma unroll
@@ -516,54 +526,27 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   const size_t rg = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5);
   size_t s0, s1;
   range_spans(rg, per, nspans, &s0, &s1);
-  (void)warps;
   // the children of this warp's range start at its range's offset
-  unsigned long long run = s0 < s1 ? range_offs[rg] : 0ull;
-  // this lane's parents of `span` into stage `b` (none beyond the range or N;
-  // a group is committed either way, so the wait counts stay uniform)
-  auto issue = [&](size_t span, int b) {
-    if (span < s1) {
-      const size_t base = span * kXsSpan;
-#pragma unroll
-      for (int it = 0; it < kXsItems; ++it) {
-        const size_t i = base + size_t(it) * 32 + lane;
-        const int slot = it * 32 + int(lane);
-        if (i < N) {
-#pragma unroll
-          for (int k = 0; k < W; ++k) {
-            cp_async_bytes8(&my[b].x[k][slot], in.x + k * in.cap + i);
-            cp_async_bytes8(&my[b].z[k][slot], in.z + k * in.cap + i);
-          }
-          if constexpr (sizeof(WT) == 8) cp_async_bytes8(&my[b].w[slot], in.w + i);
-          else cp_async_bytes4(&my[b].w[slot], in.w + i);
-          cp_async_bytes4(&my[b].g[slot], in.g + i);
-        }
-      }
-    }
-    cp_async_commit();
-  };
-  issue(s0, 0);
-  issue(s0 + 1, 1);
-  int b = 0;
+  unsigned long long run = range_offs[rg];
+  const unsigned long long end = rg + 1 < warps ? range_offs[rg + 1] : total;
+  const size_t lim = size_t(end < cap ? end : cap);
+  // this lane's running letter code and its generator (checked launches)
+  uint32_t code_g = 0xffffffffu, code = 0;
   for (size_t span = s0; span < s1; ++span) {
-    issue(span + 2, (b + 2) % kXsStages);
-    cp_async_wait<2>();  // this span's group has landed (two newer may be in flight)
-    const XsStage<W, WT>& sg = my[b];
     const size_t base = span * kXsSpan;
+    // every parent of the lane first (independent loads), then the counts
+    // and the warp's places in parent order (with pruning: of the surviving
+    // children), then the children
     uint64_t x[kXsItems][W], z[kXsItems][W];
     WT wv[kXsItems];
     uint32_t g[kXsItems];
 #pragma unroll
     for (int it = 0; it < kXsItems; ++it) {
-      const int slot = it * 32 + int(lane);
-      if (base + size_t(slot) < N) {
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          x[it][k] = sg.x[k][slot];
-          z[it][k] = sg.z[k][slot];
-        }
-        wv[it] = sg.w[slot];
-        g[it] = sg.g[slot];
+      const size_t i = base + size_t(it) * 32 + lane;
+      if (i < N) {
+        load_term<W>(in, i, x[it], z[it]);
+        wv[it] = in.w[i];
+        g[it] = in.g[i];
       } else {
 #pragma unroll
         for (int k = 0; k < W; ++k) x[it][k] = z[it][k] = 0ull;
@@ -586,6 +569,14 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
           c = xs_count_children<W>(st, x[it], z[it]);
           kc = xs_kept<W, WT>(st, x[it], z[it], wv[it], c);
         }
+        if (chk.gwire) {
+          if (g[it] != code_g) {
+            if (code) atomicOr(&chk.gwire[code_g], code);
+            code_g = g[it];
+            code = 0;
+          }
+          code |= xs_wire_code<W, NQ>(st, wr, x[it], z[it]);
+        }
       }
       unsigned inc = kc;
 #pragma unroll
@@ -607,8 +598,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
           w = wneg(w);
       } else if constexpr (CK == 1) {
         int neg = 0;
-        apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn + xs_emit_stage_bytes<W, WT>() / 8),
-                     ps.nops, x[it], z[it], &neg);
+        apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn), ps.nops, x[it], z[it], &neg);
         if (neg) w = wneg(w);
       }
       const bool all = !prune || xs_keeps_all<WT>(st, w);
@@ -616,7 +606,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
       // in registers for one parent at a time)
       XsParentRows<NQ ? NQ : 1> pr;
       if constexpr (NQ > 0) xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
-      // o + (children kept) <= *total_d <= cap (the counts the span sums came from)
+      // o + (children kept) <= lim when the range offsets hold
       size_t o = size_t(loc[it]);
       for (unsigned r = 0; r < cnt[it]; ++r) {
         uint64_t cx[W], cz[W];
@@ -627,7 +617,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
           atomicAdd(&pruned[g[it]], double(v) * double(v));
           continue;
         }
-        if (o < cap) {
+        if (o < lim) {
 #pragma unroll
           for (int k = 0; k < W; ++k) {
             ox[k][o] = cx[k];
@@ -639,9 +629,23 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
         ++o;
       }
     }
-    b = (b + 1) % kXsStages;
   }
-  cp_async_wait<0>();
+  if (chk.gwire && code) atomicOr(&chk.gwire[code_g], code);
+  if (chk.err && run != end) {
+    // a range that wrote fewer children than its recorded share fills the
+    // rest with zero-weight identity terms of generator 0, so that the run
+    // (repeated once its checks are read) sees only valid generator ids
+    if (lane == 0) atomicOr(chk.err, 1u);
+    for (unsigned long long i = run + lane; i < lim; i += 32) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        ox[k][i] = 0ull;
+        oz[k][i] = 0ull;
+      }
+      out.w[i] = WT(0);
+      out.g[i] = 0u;
+    }
+  }
 }
 
 }  // namespace dev

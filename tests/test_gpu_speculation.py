@@ -233,3 +233,48 @@ def test_recorded_size_that_cannot_be_allocated_falls_back():
     compare_result(res, O.propagate(n, instrs, mode="plan", gens=gens, threads=8))
     res.free()
     fresh.free()
+
+
+def test_recorded_range_offsets_skip_the_count():
+    """A chain of small expansions: the second run, whose guesses held on the
+    spot, records each step's range offsets, and from the third run on every
+    step is one emission on them (no count, no scan) with its checks at the
+    end of the run.  The same plan started from the generators in reverse
+    order has the same step sizes but other range shares: the emission flags
+    the ranges, the run is repeated with every check on the spot, the result
+    equals a fresh plan's, and the records that failed are retired."""
+    n, instrs = W.fan_in_deep(3, n=40, n_s=12, total=3000)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    runs = [qx.propagate(plan) for _ in range(4)]
+    counts = [r.stats()["kernels"]["expand_count"]["launches"] for r in runs]
+    assert counts[0] == counts[1] == 12 and counts[2] == counts[3] == 0, counts
+    for r in runs[2:]:
+        st = r.stats()
+        assert st["host_syncs"] == 1 and st["guesses_held"] == 12 and st["guesses_missed"] == 0
+        assert st["kernels"]["expand_scan"]["launches"] == 0
+        _same(r, runs[0])
+    compare_result(runs[3], O.propagate(n, instrs, mode="plan", threads=8))
+    # generators in reverse order: same totals per step, other shares per range
+    rev = ["".join("Z" if q == j else "I" for q in range(n)) for j in reversed(range(n))]
+    res = qx.propagate_from(plan, rev)
+    st = res.stats()
+    assert st["guesses_missed"] >= 1
+    assert st["kernels"]["expand_count"]["launches"] == 12
+    _same(res, qx.propagate_from(qx.group_ops(qx.load_circuit(n, instrs)), rev))
+    # the records whose check failed are retired: later runs count those
+    # steps again (their guesses still hold)
+    later = [qx.propagate(plan) for _ in range(3)][-1]
+    assert 0 < later.stats()["kernels"]["expand_count"]["launches"] <= 12
+    assert later.stats()["guesses_missed"] == 0
+    _same(later, runs[0])
+
+
+def test_recorded_offsets_with_pruning_and_fp32():
+    """Records are per precision and threshold: an FP64 record is not used by
+    FP32 or pruned runs (their sizes differ), and each configuration's own
+    runs give the fresh plan's result."""
+    n, instrs = W.fan_in_deep(4, n=40, n_s=10, total=2500)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for kw in ({}, {"precision": 32}, {"eps": 1e-3}, {"eps": 1e-3, "precision": 32}, {}):
+        rs = [qx.propagate(plan, **kw) for _ in range(3)]
+        _same(rs[-1], _fresh(n, instrs, **kw))
