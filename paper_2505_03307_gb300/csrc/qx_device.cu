@@ -377,6 +377,8 @@ struct Scratch {
   unsigned long long* gmask = nullptr;  // [G][3][W]
   uint64_t* mixed = nullptr;            // [G][W]
   double* pruned = nullptr;             // [G]
+  unsigned long long* gcount = nullptr;  // [G] final terms per generator
+  double* gsumsq = nullptr;              // [G] their sum of squared weights
   FanQ* fanq = nullptr;                 // [n]
   void* base = nullptr;
   // hash table and leader payload (grow on demand)
@@ -521,6 +523,10 @@ struct Ctx {
   };
   bool defer = false;
   bool retry = false;  // set by a run whose deferred checks failed
+  // the current step is the program's last expansion or merge: a fused
+  // expansion then writes the per-generator statistics (stats_done)
+  bool stats_last = false;
+  bool stats_done = false;
   std::vector<Deferred> deferred;
   // range offsets recorded by this run, published when it completes
   struct Record {
@@ -1659,15 +1665,16 @@ void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap,
   const auto in = c.cur.view<WT>();
   const auto out = xp->out.view<WT>();
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
+  const XsStats sts{c.stats_last ? c.sc.gcount : nullptr, c.stats_last ? c.sc.gsumsq : nullptr};
   if (st.nq == 1)
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
   else if (st.nq == 2)
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
   else
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
 }
 
 template <int W, typename WT>
@@ -1675,6 +1682,7 @@ qx_status xs_emit(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long c
                   const qx_plan_device::Pass* fused) {
   QX_TRY(alloc_terms(c.al, W, c.wtb, cap, &xp->out));
   XsPass ps{};
+  if (c.stats_last) QX_TRY_CUDA(cudaMemsetAsync(c.sc.gcount, 0, size_t(c.G) * 16, c.al.s));
   c.begin(KC_EXPAND);
   if (!fused || fused->identity) {
     xs_launch<W, WT, 0>(c, fs, xp, cap, ps, 0);
@@ -1842,6 +1850,7 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
   if (replayed) {
     *done = true;
     *absorbed = uses_tail;
+    c.stats_done = c.stats_last;
     return xs_accept<W, WT>(c, &xp, rtotal, nfused);
   }
   xp = XsPending();
@@ -1853,6 +1862,7 @@ qx_status run_fan_small(Ctx& c, const FanStep& fs, FanHint* hint,
   auto finish = [&](unsigned long long total) -> qx_status {
     *done = true;
     *absorbed = uses_tail;
+    c.stats_done = c.stats_last;
     return xs_accept<W, WT>(c, &xp, total, nfused);
   };
   std::vector<uint64_t> mixed;
@@ -2231,9 +2241,10 @@ qx_status run_rot(Ctx& c, const RotStep& rs, uint64_t ops_before) {
 qx_status setup_scratch(Ctx& c) {
   const size_t G = size_t(c.G), W = size_t(c.W);
   const size_t sz_cnt = 64, sz_gm = G * 3 * W * 8, sz_mx = G * W * 8, sz_pr = G * 8,
+               sz_st = G * 16,
                sz_fq = size_t(std::max(c.n, kSmallMaxWires)) * sizeof(FanQ) + 3 * kMaxWords * 8;
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const size_t total = al(sz_cnt) + al(sz_gm) + al(sz_mx) + al(sz_pr) + al(sz_fq);
+  const size_t total = al(sz_cnt) + al(sz_gm) + al(sz_mx) + al(sz_pr) + al(sz_st) + al(sz_fq);
   c.sc.base = c.al.get(total);
   if (!c.sc.base) return fail(QX_ENOMEM, "device allocation of scratch failed");
   auto* b = static_cast<unsigned char*>(c.sc.base);
@@ -2246,6 +2257,9 @@ qx_status setup_scratch(Ctx& c) {
   b += al(sz_mx);
   c.sc.pruned = reinterpret_cast<double*>(b);
   b += al(sz_pr);
+  c.sc.gcount = reinterpret_cast<unsigned long long*>(b);
+  c.sc.gsumsq = reinterpret_cast<double*>(b + G * 8);
+  b += al(sz_st);
   c.sc.fanq = reinterpret_cast<FanQ*>(b);
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
   QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
@@ -2303,6 +2317,9 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   // last step's expansion.
   const auto& prog = p->program;
   const qx_plan_device::Pass* pending = nullptr;
+  size_t last_work = prog.size();  // the last fan-out or rotation step
+  for (size_t si = 0; si < prog.size(); ++si)
+    if (prog[si].kind != kStepCliff) last_work = si;
   for (size_t si = 0; si < prog.size(); ++si) {
     const Step& stp = prog[si];
     if (stp.kind == kStepCliff) {
@@ -2330,8 +2347,10 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
         }
       }
       bool absorbed = false;
+      c.stats_last = si == last_work;
       QX_TRY(run_fan<W, WT>(c, fs, stp.ops_before, p->dev ? &p->dev->hints[stp.index] : nullptr,
                             pending, tail, pre_tail, &absorbed));
+      c.stats_last = false;
       pending = nullptr;
       if (absorbed) ++si;  // the last pass ran inside the expansion
     }
@@ -2347,26 +2366,22 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
   r->count.assign(G, 0);
   r->sumsq.assign(G, 0.0);
   r->pruned.assign(G, 0.0);
-  void* st = c.al.get(G * 16 + 16);
-  if (!st) {
-    delete r;
-    return fail(QX_ENOMEM, "device allocation failed");
+  auto* d_count = c.sc.gcount;
+  auto* d_sumsq = c.sc.gsumsq;
+  if (!c.stats_done) {  // else the last expansion counted its children
+    QX_TRY_CUDA(cudaMemsetAsync(d_count, 0, G * 16, c.al.s));
+    c.begin(KC_STATS);
+    if (c.N)
+      k_gen_stats<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
+          c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
+    c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   }
-  auto* d_count = static_cast<unsigned long long*>(st);
-  auto* d_sumsq = reinterpret_cast<double*>(d_count + G);
-  QX_TRY_CUDA(cudaMemsetAsync(st, 0, G * 16, c.al.s));
-  c.begin(KC_STATS);
-  if (c.N)
-    k_gen_stats<W, WT><<<grid_for(c.N, kThreads, c.sms, 8), kThreads, 0, c.al.s>>>(
-        c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
-  c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
   QX_TRY_CUDA(cudaMemcpyAsync(r->sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));
   QX_TRY_CUDA(cudaMemcpyAsync(r->pruned.data(), c.sc.pruned, G * 8, cudaMemcpyDeviceToHost,
                               c.al.s));
   const cudaError_t se = cudaStreamSynchronize(c.al.s);
   c.st.host_syncs++;
-  c.al.put(st);
   if (se != cudaSuccess) {
     delete r;
     return fail(QX_ECUDA, std::string("propagation failed: ") + cudaGetErrorString(se));
@@ -2583,6 +2598,7 @@ qx_status propagate_common(const qx_plan* p, const qx_prop_opts* o, int ngen, in
     c.cslot = 0;
     c.retry = false;
     c.defer = false;
+    c.stats_done = false;
   }
   if (s != QX_OK) {
     const std::string msg = qx_last_error();

@@ -326,6 +326,14 @@ struct XsCheck {
   uint32_t* gwire;
 };
 
+// Per-generator term counts and sums of squared weights of the children an
+// emission writes (both null unless it is the program's last expansion:
+// later Clifford passes change neither).
+struct XsStats {
+  unsigned long long* count;
+  double* sumsq;
+};
+
 // The letter code of one parent (see XsCheck).
 template <int W, int NQ>
 __device__ __forceinline__ uint32_t xs_wire_code(const XsStep& st, const XsWires<NQ ? NQ : 1>& wr,
@@ -496,7 +504,7 @@ template <int W, typename WT, int CK, int NQ>
 __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
-    const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, double* pruned,
+    const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, XsStats sts, double* pruned,
     TermsT<WT> out) {
   const unsigned long long total = *total_d;
   if (total > cap) return;
@@ -532,6 +540,18 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   const size_t lim = size_t(end < cap ? end : cap);
   // this lane's running letter code and its generator (checked launches)
   uint32_t code_g = 0xffffffffu, code = 0;
+  // this lane's running statistics and their generator (last expansion)
+  uint32_t sg = 0xffffffffu;
+  unsigned long long sn = 0;
+  double ssq = 0.0;
+  auto stats_flush = [&]() {
+    if (sn) {
+      atomicAdd(&sts.count[sg], sn);
+      atomicAdd(&sts.sumsq[sg], ssq);
+    }
+    sn = 0;
+    ssq = 0.0;
+  };
   for (size_t span = s0; span < s1; ++span) {
     const size_t base = span * kXsSpan;
     // every parent of the lane first (independent loads), then the counts
@@ -625,11 +645,20 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
           }
           out.w[o] = v;
           out.g[o] = g[it];
+          if (sts.count) {
+            if (g[it] != sg) {
+              stats_flush();
+              sg = g[it];
+            }
+            ++sn;
+            ssq += double(v) * double(v);
+          }
         }
         ++o;
       }
     }
   }
+  if (sts.count) stats_flush();
   if (chk.gwire && code) atomicOr(&chk.gwire[code_g], code);
   if (chk.err && run != end) {
     // a range that wrote fewer children than its recorded share fills the

@@ -57,6 +57,15 @@ def test_deep_chain_of_single_wire_steps(n, n_s, total):
     assert st["kernels"]["clifford_pass"]["launches"] <= 1
     again = qx.propagate(plan)  # on the plan's records
     compare_result(again, O.propagate(n, instrs, mode="plan", threads=CORES))
+    # the last expansion counted its children per generator (no statistics
+    # pass over the final terms): counts and norms equal the exported terms'
+    for r in (res, again, qx.propagate(plan), qx.propagate(plan, precision=32)):
+        assert r.stats()["kernels"]["gen_stats"]["launches"] == 0
+        for g in range(n):
+            info = r.info(g)
+            w = np.array(list(r.export_dict(g).values()))
+            assert info["nterms"] == len(w)
+            assert abs(info["sumsq"] - float(np.sum(w * w))) <= 1e-12 * max(1.0, info["sumsq"])
 
 
 def _short_pass_circuit(seed, n, rounds, tail_on_wire):
