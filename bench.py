@@ -203,10 +203,13 @@ class ClockSampler:
 
 def timed_steps(fn, steps, flush, stream=None):
     """Device time (CUDA events on the launch stream) of `steps` calls of fn,
-    L2 flushed before each outside the events; returns (ms list, results)."""
+    L2 flushed before each outside the events; returns (ms list, [the last
+    result]).  Earlier results are freed after their step, as a caller that
+    propagates in a loop would (holding them all would make every step grow
+    the memory pool instead of reusing it)."""
     import torch
     s = stream or torch.cuda.current_stream()
-    out, res = [], []
+    out, last = [], None
     for _ in range(steps):
         flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -215,8 +218,10 @@ def timed_steps(fn, steps, flush, stream=None):
         e1.record(s)
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
-        res.append(r)
-    return out, res
+        if last is not None:
+            last.free()
+        last = r
+    return out, [last]
 
 
 def kernel_classes(stats_list):
@@ -598,8 +603,6 @@ def fp32_bench(qx, W, flush, steps, fp64_step_ms, warmup=3):
     for _ in range(warmup):
         qx.propagate(plan, precision=32, eps=EPS).free()
     ms, res = timed_steps(lambda: qx.propagate(plan, precision=32, eps=EPS), steps, flush)
-    for r in res[:-1]:
-        r.free()
     r32 = res[-1]
     st = r32.stats()
     # error against the exact coefficients on sampled strings of 4 generators
@@ -641,12 +644,8 @@ def fp32_bench(qx, W, flush, steps, fp64_step_ms, warmup=3):
         qx.propagate(plan, precision=32).free()
         qx.propagate(plan).free()
     ms32, res = timed_steps(lambda: qx.propagate(plan, precision=32), steps, flush)
-    for r in res[:-1]:
-        r.free()
     r32 = res[-1]
     ms64, res64 = timed_steps(lambda: qx.propagate(plan), steps, flush)
-    for r in res64[:-1]:
-        r.free()
     ref = res64[-1]
     worst = 0.0
     for g in (16, 33, 49):

@@ -518,8 +518,9 @@ struct Ctx {
     const unsigned long long* total = nullptr;
     const unsigned* err = nullptr;
     const unsigned* nblk = nullptr;
-    const uint32_t* gwire = nullptr;  // pinned: letter codes (replayed offsets)
+    const uint32_t* gwire = nullptr;  // letter codes (replayed offsets)
     FanHint::Record* rec = nullptr;   // the record it replayed
+    int slot = -1;                    // its check slot (err, gwire: set once read back)
   };
   bool defer = false;
   bool retry = false;  // set by a run whose deferred checks failed
@@ -528,6 +529,11 @@ struct Ctx {
   bool stats_last = false;
   bool stats_done = false;
   std::vector<Deferred> deferred;
+  // check slots of steps launched on recorded offsets (XsCheck), in the
+  // scratch right after the per-generator statistics
+  unsigned char* chk_dev = nullptr;
+  size_t chk_stride = 0;
+  int chk_slots = 0, chk_used = 0;
   // range offsets recorded by this run, published when it completes
   struct Record {
     FanHint::Record* rec = nullptr;
@@ -1511,6 +1517,7 @@ struct XsPending {
   size_t nranges = 0;  // ranges of spans: one warp of the emission each
   size_t per = 0;      // spans per range
   unsigned grid = 0;   // blocks of the emission (nranges / 8)
+  unsigned long long written = ~0ull;  // the count the last emission stored in the output slot
 };
 
 void xs_release(Ctx& c, XsPending* xp) {
@@ -1666,15 +1673,20 @@ void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap,
   const auto out = xp->out.view<WT>();
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   const XsStats sts{c.stats_last ? c.sc.gcount : nullptr, c.stats_last ? c.sc.gsumsq : nullptr};
+  unsigned long long* n_out = c.sc.ncnt + (1 - c.cslot);  // the slot xs_accept makes current
+  xp->written = cap;
   if (st.nq == 1)
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
+        n_out);
   else if (st.nq == 2)
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
+        n_out);
   else
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
-        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out);
+        in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
+        n_out);
 }
 
 template <int W, typename WT>
@@ -1713,7 +1725,9 @@ qx_status xs_accept(Ctx& c, XsPending* xp, unsigned long long total, int nfused)
   c.st.alg_bytes += (c.N + total) * (16 * W + sizeof(WT));
   c.st.children += total;
   c.st.clifford_passes += uint64_t(nfused);
-  QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
+  // the emission stored its output size in the slot; another total (a guess
+  // that was larger than the count) is copied
+  if (xp->written != total) QX_TRY(h2d(c, c.sc.ncnt + oslot, &total, 8));
   c.al.put(xp->tiles);
   replace_cur(c, xp->out, total, oslot);
   *xp = XsPending();  // pruning (eps > 0) happened in the emission
@@ -1781,20 +1795,15 @@ qx_status xs_replay(Ctx& c, const FanStep& fs, FanHint* hint, const qx_plan_devi
   if (!rec || h.n != c.N || h.eps != c.eps) return QX_OK;
   xs_partition<W, WT>(c, fs, fused, xp);
   if (xp->nranges != h.ranges || xp->per != h.per || !limits_ok(c, h.total)) return QX_OK;
-  const size_t G = size_t(c.G);
-  const size_t bytes = 16 + G * 4;  // err word, then the letter codes
-  auto* rb = static_cast<unsigned char*>(rb_take(c, bytes));
-  if (!rb) return QX_OK;
-  void* chk = c.al.get(bytes);
-  if (!chk) return QX_OK;
-  QX_TRY_CUDA(cudaMemsetAsync(chk, 0, bytes, c.al.s));
+  if (c.chk_used >= c.chk_slots) return QX_OK;
+  const int slot = c.chk_used;
+  unsigned char* chk = c.chk_dev + size_t(slot) * c.chk_stride;  // zeroed with the scratch
   xp->offs = rec;
   xp->total_d = rec + xp->nranges;
-  xp->chk.err = static_cast<unsigned*>(chk);
-  xp->chk.gwire = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(chk) + 16);
+  xp->chk.err = reinterpret_cast<unsigned*>(chk);
+  xp->chk.gwire = reinterpret_cast<uint32_t*>(chk + 16);
   const qx_status st = xs_emit<W, WT>(c, fs, xp, h.total, fused);
   if (st != QX_OK) {
-    c.al.put(chk);
     if (st != QX_ENOMEM) return st;
     c.al.put(xp->out.base);  // the recorded size does not fit now: count first
     *xp = XsPending();
@@ -1802,16 +1811,14 @@ qx_status xs_replay(Ctx& c, const FanStep& fs, FanHint* hint, const qx_plan_devi
     cudaGetLastError();
     return QX_OK;
   }
-  QX_TRY_CUDA(cudaMemcpyAsync(rb, chk, bytes, cudaMemcpyDeviceToHost, c.al.s));
-  c.al.put(chk);
+  c.chk_used++;
   Ctx::Deferred d;
   d.kind = kHintReplay;
   d.hint = hint;
   d.rec = &h;
   d.fs = &fs;
   d.expect = h.total;
-  d.err = reinterpret_cast<const unsigned*>(rb);
-  d.gwire = reinterpret_cast<const uint32_t*>(rb + 16);
+  d.slot = slot;
   c.deferred.push_back(std::move(d));
   *ran = true;
   *total = h.total;
@@ -2236,33 +2243,41 @@ qx_status run_rot(Ctx& c, const RotStep& rs, uint64_t ops_before) {
   return QX_OK;
 }
 
-// Scratch of a propagation over c.G generators: counters, letter masks,
-// mixed masks, pruned mass, fan-out tables.
+// Scratch of a propagation over c.G generators: counters; the per-generator
+// term counts, squared-weight sums and pruned mass, followed by the check
+// slots of steps launched on recorded offsets (one device-to-host copy reads
+// all of them at the end of the run); letter masks, mixed masks, fan-out
+// tables.
 qx_status setup_scratch(Ctx& c) {
   const size_t G = size_t(c.G), W = size_t(c.W);
-  const size_t sz_cnt = 64, sz_gm = G * 3 * W * 8, sz_mx = G * W * 8, sz_pr = G * 8,
-               sz_st = G * 16,
-               sz_fq = size_t(std::max(c.n, kSmallMaxWires)) * sizeof(FanQ) + 3 * kMaxWords * 8;
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const size_t total = al(sz_cnt) + al(sz_gm) + al(sz_mx) + al(sz_pr) + al(sz_st) + al(sz_fq);
+  // check slots: as many as the plan has fan-out steps, while they and the
+  // statistics fit a quarter of the pinned read-back space
+  c.chk_stride = al(16 + G * 4);
+  const size_t nfan = c.p ? c.p->fans.size() : 0;
+  c.chk_slots = G * 24 + nfan * c.chk_stride <= kReadbackBytes / 4 ? int(nfan) : 0;
+  c.chk_used = 0;
+  const size_t sz_cnt = 64, sz_tail = G * 24 + size_t(c.chk_slots) * c.chk_stride,
+               sz_gm = G * 3 * W * 8, sz_mx = G * W * 8,
+               sz_fq = size_t(std::max(c.n, kSmallMaxWires)) * sizeof(FanQ) + 3 * kMaxWords * 8;
+  const size_t total = al(sz_cnt) + al(sz_tail) + al(sz_gm) + al(sz_mx) + al(sz_fq);
   c.sc.base = c.al.get(total);
   if (!c.sc.base) return fail(QX_ENOMEM, "device allocation of scratch failed");
   auto* b = static_cast<unsigned char*>(c.sc.base);
   c.sc.ncnt = reinterpret_cast<unsigned long long*>(b);
   c.sc.err = reinterpret_cast<unsigned*>(b + 32);
   b += al(sz_cnt);
+  c.sc.gcount = reinterpret_cast<unsigned long long*>(b);
+  c.sc.gsumsq = reinterpret_cast<double*>(b + G * 8);
+  c.sc.pruned = reinterpret_cast<double*>(b + G * 16);
+  c.chk_dev = b + al(G * 24);
+  b += al(sz_tail);
   c.sc.gmask = reinterpret_cast<unsigned long long*>(b);
   b += al(sz_gm);
   c.sc.mixed = reinterpret_cast<uint64_t*>(b);
   b += al(sz_mx);
-  c.sc.pruned = reinterpret_cast<double*>(b);
-  b += al(sz_pr);
-  c.sc.gcount = reinterpret_cast<unsigned long long*>(b);
-  c.sc.gsumsq = reinterpret_cast<double*>(b + G * 8);
-  b += al(sz_st);
   c.sc.fanq = reinterpret_cast<FanQ*>(b);
-  QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt), c.al.s));
-  QX_TRY_CUDA(cudaMemsetAsync(c.sc.pruned, 0, sz_pr, c.al.s));
+  QX_TRY_CUDA(cudaMemsetAsync(c.sc.base, 0, al(sz_cnt) + al(sz_tail), c.al.s));
   return QX_OK;
 }
 
@@ -2376,16 +2391,30 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
           c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
     c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   }
-  QX_TRY_CUDA(cudaMemcpyAsync(r->count.data(), d_count, G * 8, cudaMemcpyDeviceToHost, c.al.s));
-  QX_TRY_CUDA(cudaMemcpyAsync(r->sumsq.data(), d_sumsq, G * 8, cudaMemcpyDeviceToHost, c.al.s));
-  QX_TRY_CUDA(cudaMemcpyAsync(r->pruned.data(), c.sc.pruned, G * 8, cudaMemcpyDeviceToHost,
-                              c.al.s));
+  // counts, sums of squares, pruned mass and the used check slots: one copy
+  const size_t tail = ((G * 24 + 255) & ~size_t(255)) + size_t(c.chk_used) * c.chk_stride;
+  std::vector<unsigned char> tail_host;
+  auto* th = static_cast<unsigned char*>(rb_take(c, tail));
+  if (!th) {
+    tail_host.resize(tail);
+    th = tail_host.data();
+  }
+  QX_TRY_CUDA(cudaMemcpyAsync(th, d_count, tail, cudaMemcpyDeviceToHost, c.al.s));
   const cudaError_t se = cudaStreamSynchronize(c.al.s);
   c.st.host_syncs++;
   if (se != cudaSuccess) {
     delete r;
     return fail(QX_ECUDA, std::string("propagation failed: ") + cudaGetErrorString(se));
   }
+  std::memcpy(r->count.data(), th, G * 8);
+  std::memcpy(r->sumsq.data(), th + G * 8, G * 8);
+  std::memcpy(r->pruned.data(), th + G * 16, G * 8);
+  for (Ctx::Deferred& d : c.deferred)
+    if (d.kind == kHintReplay) {
+      const unsigned char* slot = th + ((G * 24 + 255) & ~size_t(255)) + size_t(d.slot) * c.chk_stride;
+      d.err = reinterpret_cast<const unsigned*>(slot);
+      d.gwire = reinterpret_cast<const uint32_t*>(slot + 16);
+    }
   // the checks of the steps launched on the plan's record without a read-back
   bool held = true;
   for (const Ctx::Deferred& d : c.deferred) {

@@ -490,8 +490,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 // sums, or the offsets recorded by an earlier run of the step) plus the
 // children of the range's earlier parents, in parent order; no write leaves
 // the range's share [range_offs[r], range_offs[r + 1]) (the last range ends
-// at *total_d).  A launch sized for cap < *total_d (an output size guessed
-// too small) does nothing.
+// at *total_d).  *n_out = cap (the output's count slot) in every case; a
+// launch sized for cap < *total_d (an output size guessed too small) writes
+// nothing else.
 // CK selects the fused Clifford pass: 0 none, 1 gate list (in shared
 // memory), 3 or 4 chunk tables (read from global memory: the image cache of
 // clifford_table_map_full hits for all but the first parent of a run of
@@ -505,7 +506,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
     const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, XsStats sts, double* pruned,
-    TermsT<WT> out) {
+    TermsT<WT> out, unsigned long long* n_out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = cap;  // the output's term count
   const unsigned long long total = *total_d;
   if (total > cap) return;
   extern __shared__ __align__(16) uint64_t s_dyn[];
