@@ -85,7 +85,9 @@ struct TermBuf {
 size_t term_bytes(int W, int wtb) { return size_t(16 * W + wtb + 4); }
 
 qx_status alloc_terms(Alloc& al, int W, int wtb, size_t cap, TermBuf* out) {
-  cap = std::max<size_t>(cap, 1);
+  // a multiple of 4: every plane then starts on a 16-byte boundary, and bulk
+  // copies rounded up to 16 bytes stay inside their plane
+  cap = (std::max<size_t>(cap, 1) + 3) & ~size_t(3);
   const size_t bytes = cap * term_bytes(W, wtb) + 64;
   void* base = al.get(bytes);
   if (!base) return fail(QX_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
@@ -374,6 +376,7 @@ RotQ to_dev(const RotStep& r) {
 struct Scratch {
   unsigned long long* ncnt = nullptr;  // [0], [1]: term counts; [2]: scan total
   unsigned* err = nullptr;
+  unsigned* serr = nullptr;  // kErrSpin of a bulk copy that never completed (read at the end)
   unsigned long long* gmask = nullptr;  // [G][3][W]
   uint64_t* mixed = nullptr;            // [G][W]
   double* pruned = nullptr;             // [G]
@@ -1577,26 +1580,65 @@ XsStep xs_step(const FanStep& fs, double eps) {
 // emission per range, and exactly one wave of emission blocks (as many as
 // stay resident on every SM with the kernel's registers and gate list: a
 // second, partial wave would leave most SMs idle behind its last ranges).
+//
+// The dynamic shared memory an emission may use is a process-wide attribute
+// of the kernel (per device), so it is only ever raised, under a lock: a
+// thread that needs less never lowers it under another thread's launch.
+template <int W, typename WT, int CK, int NQ>
+void xs_emit_allow_smem(size_t smem) {
+  static std::atomic<size_t> allowed[64];
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<size_t>& a = allowed[dev & 63];
+  if (smem <= a.load(std::memory_order_acquire)) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= a.load(std::memory_order_relaxed)) return;
+  if (cudaFuncSetAttribute(k_xs_emit<W, WT, CK, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem)) == cudaSuccess)
+    a.store(smem, std::memory_order_release);
+  else
+    cudaGetLastError();  // the launch reports it
+}
+
 template <int W, typename WT, int CK, int NQ>
 int xs_emit_per_sm(size_t smem) {
-  static thread_local int cached[2] = {0, 0};  // [smem has a gate list]
-  int& slot = cached[smem ? 1 : 0];
-  if (slot) return slot;
+  xs_emit_allow_smem<W, WT, CK, NQ>(smem);
+  // the last shared-memory size asked about and its answer
+  static thread_local size_t last_smem = ~size_t(0);
+  static thread_local int last_n = 0;
+  if (smem == last_smem && last_n) return last_n;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xs_emit<W, WT, CK, NQ>, kXsThreads,
                                                     smem) != cudaSuccess || n < 1) {
     cudaGetLastError();
     n = 1;
   }
-  slot = n;
+  last_smem = smem;
+  last_n = n;
   return n;
+}
+
+// The most children a parent of the step can have (the product of its
+// wires' largest row sizes; at most kSmallMaxChildren).
+int xs_max_children(const FanStep& fs) {
+  int prod = 1;
+  for (const FanQubit& f : fs.qs) {
+    int m = 1;
+    for (int a = 0; a < 3; ++a) m = std::max(m, int(f.nnz[a]));
+    prod *= m;
+  }
+  return std::min(prod, kSmallMaxChildren);
+}
+
+int xs_gate_list(const qx_plan_device::Pass* fused) {
+  return fused && !fused->identity && !fused->use_table ? fused->nops : 0;
 }
 
 template <int W, typename WT>
 int xs_emit_blocks_per_sm(const FanStep& fs, const qx_plan_device::Pass* fused) {
   const int nq = int(fs.qs.size());
-  const size_t smem =
-      fused && !fused->identity && !fused->use_table ? size_t(fused->nops) * 4 : 0;
+  const size_t smem = xt_smem_bytes<W, WT>(xs_max_children(fs), xs_gate_list(fused));
   auto pick = [&](auto ck) {
     constexpr int CK = decltype(ck)::value;
     return nq == 1   ? xs_emit_per_sm<W, WT, CK, 1>(smem)
@@ -1663,30 +1705,67 @@ qx_status xs_count(Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused,
   return QX_OK;
 }
 
+// Whether the emission may stage tiles of t with bulk copies: every plane
+// starts on a 16-byte boundary and t.cap is a multiple of 4 (a copy rounded
+// up to 16 bytes then stays inside its plane).
+template <typename WT>
+bool xs_bulk_ok(const TermsT<WT>& t, int W) {
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (t.cap % 4) return false;
+  for (int k = 0; k < W; ++k)
+    if (!a16(t.x + size_t(k) * t.cap) || !a16(t.z + size_t(k) * t.cap)) return false;
+  return a16(t.w) && a16(t.g);
+}
+
+// The launch error of an emission, with its configuration.
+template <int W, typename WT, int CK, int NQ>
+qx_status xs_launch_error(cudaError_t e, size_t smem, unsigned grid) {
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k_xs_emit<W, WT, CK, NQ>);
+  cudaGetLastError();
+  return fail(QX_ECUDA, std::string("fused expansion launch failed: ") + cudaGetErrorString(e) +
+                            " (dynamic shared memory " + std::to_string(smem) + " of at most " +
+                            std::to_string(fa.maxDynamicSharedSizeBytes) + ", static " +
+                            std::to_string(fa.sharedSizeBytes) + ", grid " + std::to_string(grid) +
+                            ")");
+}
+
 template <int W, typename WT, int CK>
-void xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap, const XsPass& ps,
-               size_t extra) {
-  const size_t smem = extra;  // dynamic shared memory: the gate list
-  const unsigned grid = xp->grid;  // one warp per range of the count's partition
+qx_status xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long cap,
+                    const XsPass& ps, int nops) {
+  const int maxc = xs_max_children(fs);
+  const size_t smem = xt_smem_bytes<W, WT>(maxc, nops);
+  const unsigned grid = xp->grid;  // 8 ranges of the count's partition per block
   const XsStep st = xs_step(fs, c.eps);
   const auto in = c.cur.view<WT>();
   const auto out = xp->out.view<WT>();
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   const XsStats sts{c.stats_last ? c.sc.gcount : nullptr, c.stats_last ? c.sc.gsumsq : nullptr};
   unsigned long long* n_out = c.sc.ncnt + (1 - c.cslot);  // the slot xs_accept makes current
+  const int bulk = xs_bulk_ok(in, W) ? 1 : 0;
   xp->written = cap;
-  if (st.nq == 1)
+  QX_TRY_CUDA(cudaGetLastError());  // nothing pending before the launch
+  cudaError_t e;
+  if (st.nq == 1) {
+    xs_emit_allow_smem<W, WT, CK, 1>(smem);
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out);
-  else if (st.nq == 2)
+        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 1>(e, smem, grid);
+  } else if (st.nq == 2) {
+    xs_emit_allow_smem<W, WT, CK, 2>(smem);
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out);
-  else
+        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 2>(e, smem, grid);
+  } else {
+    xs_emit_allow_smem<W, WT, CK, 0>(smem);
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out);
+        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 0>(e, smem, grid);
+  }
+  return QX_OK;
 }
 
 template <int W, typename WT>
@@ -1697,11 +1776,11 @@ qx_status xs_emit(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long c
   if (c.stats_last) QX_TRY_CUDA(cudaMemsetAsync(c.sc.gcount, 0, size_t(c.G) * 16, c.al.s));
   c.begin(KC_EXPAND);
   if (!fused || fused->identity) {
-    xs_launch<W, WT, 0>(c, fs, xp, cap, ps, 0);
+    QX_TRY((xs_launch<W, WT, 0>(c, fs, xp, cap, ps, 0)));
   } else if (!fused->use_table) {
     ps.ops = fused->ops;
     ps.nops = fused->nops;
-    xs_launch<W, WT, 1>(c, fs, xp, cap, ps, size_t(fused->nops) * 4);
+    QX_TRY((xs_launch<W, WT, 1>(c, fs, xp, cap, ps, fused->nops)));
   } else {
     ps.tab_xz = fused->tab_xz;
     ps.tab_e = fused->tab_e;
@@ -1710,9 +1789,9 @@ qx_status xs_emit(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long c
     ps.pmk = pass_masks<W>(*fused, c.n);
     // the tables stay in global memory (k_xs_emit reads them on image-cache misses)
     if (fused->cb == 4)
-      xs_launch<W, WT, 4>(c, fs, xp, cap, ps, 0);
+      QX_TRY((xs_launch<W, WT, 4>(c, fs, xp, cap, ps, 0)));
     else
-      xs_launch<W, WT, 3>(c, fs, xp, cap, ps, 0);
+      QX_TRY((xs_launch<W, WT, 3>(c, fs, xp, cap, ps, 0)));
   }
   c.end(KC_EXPAND, 1, (c.N + cap) * (16 * W + sizeof(WT)));
   QX_TRY_CUDA(cudaGetLastError());
@@ -2266,6 +2345,7 @@ qx_status setup_scratch(Ctx& c) {
   auto* b = static_cast<unsigned char*>(c.sc.base);
   c.sc.ncnt = reinterpret_cast<unsigned long long*>(b);
   c.sc.err = reinterpret_cast<unsigned*>(b + 32);
+  c.sc.serr = reinterpret_cast<unsigned*>(b + 48);
   b += al(sz_cnt);
   c.sc.gcount = reinterpret_cast<unsigned long long*>(b);
   c.sc.gsumsq = reinterpret_cast<double*>(b + G * 8);
@@ -2391,27 +2471,38 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
           c.cur.view<WT>(), c.sc.ncnt + c.cslot, c.G, d_count, d_sumsq);
     c.end(KC_STATS, c.N ? 1 : 0, uint64_t(c.N) * 12);
   }
-  // counts, sums of squares, pruned mass and the used check slots: one copy
-  const size_t tail = ((G * 24 + 255) & ~size_t(255)) + size_t(c.chk_used) * c.chk_stride;
+  // the counters (with the sticky error word), counts, sums of squares,
+  // pruned mass and the used check slots: one copy
+  constexpr size_t head = 256;  // the counters' block ahead of the statistics
+  const size_t tail = head + ((G * 24 + 255) & ~size_t(255)) + size_t(c.chk_used) * c.chk_stride;
   std::vector<unsigned char> tail_host;
   auto* th = static_cast<unsigned char*>(rb_take(c, tail));
   if (!th) {
     tail_host.resize(tail);
     th = tail_host.data();
   }
-  QX_TRY_CUDA(cudaMemcpyAsync(th, d_count, tail, cudaMemcpyDeviceToHost, c.al.s));
+  QX_TRY_CUDA(cudaMemcpyAsync(th, c.sc.base, tail, cudaMemcpyDeviceToHost, c.al.s));
   const cudaError_t se = cudaStreamSynchronize(c.al.s);
   c.st.host_syncs++;
   if (se != cudaSuccess) {
     delete r;
     return fail(QX_ECUDA, std::string("propagation failed: ") + cudaGetErrorString(se));
   }
-  std::memcpy(r->count.data(), th, G * 8);
-  std::memcpy(r->sumsq.data(), th + G * 8, G * 8);
-  std::memcpy(r->pruned.data(), th + G * 16, G * 8);
+  unsigned serr = 0;
+  std::memcpy(&serr, th + (reinterpret_cast<unsigned char*>(c.sc.serr) -
+                           static_cast<unsigned char*>(c.sc.base)),
+              4);
+  if (serr & kErrSpin) {
+    delete r;
+    return fail(QX_ETIMEOUT, "a bulk copy of the fused expansion did not complete");
+  }
+  std::memcpy(r->count.data(), th + head, G * 8);
+  std::memcpy(r->sumsq.data(), th + head + G * 8, G * 8);
+  std::memcpy(r->pruned.data(), th + head + G * 16, G * 8);
   for (Ctx::Deferred& d : c.deferred)
     if (d.kind == kHintReplay) {
-      const unsigned char* slot = th + ((G * 24 + 255) & ~size_t(255)) + size_t(d.slot) * c.chk_stride;
+      const unsigned char* slot =
+          th + head + ((G * 24 + 255) & ~size_t(255)) + size_t(d.slot) * c.chk_stride;
       d.err = reinterpret_cast<const unsigned*>(slot);
       d.gwire = reinterpret_cast<const uint32_t*>(slot + 16);
     }

@@ -486,192 +486,431 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
   flush();
 }
 
-// Children of each parent at its range's offset (exclusive scan of the range
-// sums, or the offsets recorded by an earlier run of the step) plus the
-// children of the range's earlier parents, in parent order; no write leaves
-// the range's share [range_offs[r], range_offs[r + 1]) (the last range ends
-// at *total_d).  *n_out = cap (the output's count slot) in every case; a
-// launch sized for cap < *total_d (an output size guessed too small) writes
-// nothing else.
+// ---------------------------------------------------------------------------
+// The emission works on tiles of kXtTile parents.  A block takes the 8
+// consecutive ranges of the count's partition that its warps would have
+// taken (one contiguous run of parents, whose children are contiguous from
+// the first range's offset) and walks them tile by tile:
+//  * one thread stages the next tiles' term planes in shared memory with
+//    bulk asynchronous copies (cp.async.bulk, completion on an mbarrier), two
+//    stages deep, so the copies of tile k + 1 run while tile k is worked on;
+//  * parent pass, two adjacent parents per thread: the fused Clifford pass,
+//    the rows of the fan-out wires, the children that survive pruning, and a
+//    block scan of their counts; each kept child is entered in a child map
+//    (parent index, child rank);
+//  * child pass, one child per thread and round: consecutive threads write
+//    consecutive children, so every store of a warp covers one contiguous
+//    run of each plane.
+// Compared with one warp per range writing each parent's children from
+// registers, the instructions per parent drop by about half and the writes
+// are whole sectors; the copies keep the loads in flight without registers.
+constexpr int kXtTile = 2 * kXsThreads;  // parents per tile
+
+template <int W, typename WT>
+__host__ __device__ constexpr size_t xt_stage_bytes() {
+  return size_t(kXtTile) * (16 * W + sizeof(WT) + 4);
+}
+
+// Dynamic shared memory of the emission: two stages, the child map
+// (kXtTile x maxc entries of 4 bytes) and the gate list of a CK = 1 pass.
+template <int W, typename WT>
+__host__ __device__ constexpr size_t xt_smem_bytes(int maxc, int nops) {
+  return 2 * xt_stage_bytes<W, WT>() + size_t(kXtTile) * size_t(maxc) * 4 + size_t(nops) * 4;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier, at most `limit` polls (spinning
+// first, then with short sleeps); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it >= 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// its later bulk copies into the same memory (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One stage of kXtTile parents: x planes, z planes, weights, generator ids.
+template <int W, typename WT>
+struct XtStage {
+  unsigned char* base;
+  __device__ __forceinline__ uint64_t* x(int k) const {
+    return reinterpret_cast<uint64_t*>(base) + size_t(k) * kXtTile;
+  }
+  __device__ __forceinline__ uint64_t* z(int k) const {
+    return reinterpret_cast<uint64_t*>(base) + size_t(W + k) * kXtTile;
+  }
+  __device__ __forceinline__ WT* w() const {
+    return reinterpret_cast<WT*>(base + size_t(2 * W) * kXtTile * 8);
+  }
+  __device__ __forceinline__ uint32_t* g() const {
+    return reinterpret_cast<uint32_t*>(base + size_t(2 * W) * kXtTile * 8 +
+                                       size_t(kXtTile) * sizeof(WT));
+  }
+};
+
+// Child r of a parent (letters x, z after the fused pass; the fan-out wires
+// keep their letters under it), reading only the table entries it uses: the
+// same digits (first wire least significant) and the same product in wire
+// order as xs_child / xs_child_r.
+template <int W, typename WT, int NQ>
+__device__ __forceinline__ WT xs_child_at(const XsStep& st, const XsWires<NQ ? NQ : 1>& wr,
+                                          const uint64_t* x, const uint64_t* z, WT w, unsigned r,
+                                          uint64_t* cx, uint64_t* cz) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    cx[k] = x[k];
+    cz[k] = z[k];
+  }
+  WProd<WT> p(w);
+  const int nq = NQ > 0 ? NQ : st.nq;
+#pragma unroll
+  for (int j = 0; j < (NQ > 0 ? NQ : kSmallMaxWires); ++j) {
+    if (j >= nq) break;
+    const int wd = NQ > 0 ? wr.word[j] : st.word[j];
+    const int b = NQ > 0 ? wr.bit[j] : st.bit[j];
+    const bool hi = W > 1 && wd;
+    const uint64_t xw = hi ? x[W - 1] : x[0], zw = hi ? z[W - 1] : z[0];
+    const int xb = int((xw >> b) & 1), zb = int((zw >> b) & 1);
+    const int L = xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+    if (!L) continue;
+    const XsRow& row = st.row[j][L - 1];
+    const int nn = row.nn;
+    int d = 0;
+    if (nn == 2) {
+      d = int(r & 1);
+      r >>= 1;
+    } else if (nn == 3) {
+      d = int(r % 3);
+      r /= 3;
+    }
+    p.mul_entry(row.t[d], row.th[d], row.tl[d]);
+    const int col = row.col[d];
+    const uint64_t m = 1ull << b;
+    if (!hi) {
+      cx[0] = (col <= 1) ? (cx[0] | m) : (cx[0] & ~m);
+      cz[0] = (col >= 1) ? (cz[0] | m) : (cz[0] & ~m);
+    } else {
+      cx[W - 1] = (col <= 1) ? (cx[W - 1] | m) : (cx[W - 1] & ~m);
+      cz[W - 1] = (col >= 1) ? (cz[W - 1] | m) : (cz[W - 1] & ~m);
+    }
+  }
+  return p.get();
+}
+
+// Children of each parent at its block's offset (the offset of the block's
+// first range: the exclusive scan of the range sums, or the offsets recorded
+// by an earlier run of the step) plus the children of the block's earlier
+// parents, in parent order; no write leaves the block's share, the offsets
+// of its first range and of the next block's (the last block ends at
+// *total_d).  *n_out = cap (the output's count slot) in every case; a launch
+// sized for cap < *total_d (an output size guessed too small) writes nothing
+// else.  `bulk` (set by the host when every plane of `in` starts on a 16-byte
+// boundary and in.cap is a multiple of 4, so that copies rounded up to 16
+// bytes stay inside the planes) stages tiles with bulk copies; otherwise the
+// threads copy them.  A copy that does not complete within `spin_limit`
+// polls sets kErrSpin in *serr and the block returns once its copies in
+// flight are done (or given up on as well).
 // CK selects the fused Clifford pass: 0 none, 1 gate list (in shared
 // memory), 3 or 4 chunk tables (read from global memory: the image cache of
 // clifford_table_map_full hits for all but the first parent of a run of
 // parents with the same touched letters, so the tables are rarely read).
-// Each lane loads both of its parents of a span into registers before it
-// counts or writes anything.  (Staging the next two spans in shared memory
-// with cp.async, or one parent at a time at three blocks per SM, measured
-// 9 % and 13 % slower on the 84M-term chain.)
 template <int W, typename WT, int CK, int NQ>
 __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
     const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, XsStats sts, double* pruned,
-    TermsT<WT> out, unsigned long long* n_out) {
+    TermsT<WT> out, unsigned long long* n_out, int maxc, int bulk, unsigned spin_limit,
+    unsigned* serr) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = cap;  // the output's term count
   const unsigned long long total = *total_d;
   if (total > cap) return;
-  extern __shared__ __align__(16) uint64_t s_dyn[];
+  extern __shared__ __align__(16) unsigned char s_raw[];
   __shared__ XsStep st;
+  __shared__ __align__(8) uint64_t s_full[2];
+  __shared__ unsigned s_wsum[kXsThreads / 32];
+  const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto stage = [&](size_t k) {
+    return XtStage<W, WT>{s_raw + (k & 1) * xt_stage_bytes<W, WT>()};
+  };
+  uint32_t* cmap = reinterpret_cast<uint32_t*>(s_raw + 2 * xt_stage_bytes<W, WT>());
+  const uint32_t* s_ops = cmap + size_t(kXtTile) * size_t(maxc);
   load_xs_step(&st, step);
   if constexpr (CK == 1) {
-    uint32_t* s_ops = reinterpret_cast<uint32_t*>(s_dyn);
-    for (int i = threadIdx.x; i < ps.nops; i += blockDim.x) s_ops[i] = ps.ops[i];
+    uint32_t* o = const_cast<uint32_t*>(s_ops);
+    for (int i = tid; i < ps.nops; i += blockDim.x) o[i] = ps.ops[i];
+  }
+  if (tid == 0) {
+    mbar_init(&s_full[0], 1);
+    mbar_init(&s_full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const size_t N = *n_in;
   const size_t nspans = (N + kXsSpan - 1) / kXsSpan;
-  const unsigned lane = threadIdx.x & 31;
-  const size_t warps = size_t(gridDim.x) * (kXsThreads / 32);
+  const size_t nranges = size_t(gridDim.x) * (kXsThreads / 32);
+  const size_t rg0 = size_t(blockIdx.x) * (kXsThreads / 32);
+  const size_t s0 = min(nspans, rg0 * per), s1 = min(nspans, s0 + per * (kXsThreads / 32));
+  const size_t P0 = min(N, s0 * kXsSpan), P1 = min(N, s1 * kXsSpan);
+  const size_t ntiles = (P1 - P0 + kXtTile - 1) / kXtTile;
   const bool prune = st.prune != 0;
   XsWires<NQ ? NQ : 1> wr;
   if constexpr (NQ > 0) wr = xs_wires<NQ>(st);
   FullCache<W> fc;
-  uint64_t* ox[W];
-  uint64_t* oz[W];
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    ox[k] = out.x + size_t(k) * out.cap;
-    oz[k] = out.z + size_t(k) * out.cap;
-  }
-  const size_t rg = size_t(blockIdx.x) * (kXsThreads / 32) + (threadIdx.x >> 5);
-  size_t s0, s1;
-  range_spans(rg, per, nspans, &s0, &s1);
-  // the children of this warp's range start at its range's offset
-  unsigned long long run = range_offs[rg];
-  const unsigned long long end = rg + 1 < warps ? range_offs[rg + 1] : total;
+  unsigned long long run = range_offs[rg0];
+  const unsigned long long end = rg0 + (kXsThreads / 32) < nranges
+                                     ? range_offs[rg0 + (kXsThreads / 32)]
+                                     : total;
   const size_t lim = size_t(end < cap ? end : cap);
-  // this lane's running letter code and its generator (checked launches)
+  // tile k of the block: parents [P0 + k T, min(P1, P0 + (k + 1) T))
+  auto tile_n = [&](size_t k) { return unsigned(min(size_t(kXtTile), P1 - P0 - k * kXtTile)); };
+  auto issue = [&](size_t k) {  // one thread: bulk copies of tile k into stage k & 1
+    const XtStage<W, WT> sg = stage(k);
+    const size_t p0 = P0 + k * kXtTile;
+    const unsigned m = tile_n(k);
+    const unsigned b8 = (m * 8 + 15) & ~15u, bw = (m * unsigned(sizeof(WT)) + 15) & ~15u,
+                   b4 = (m * 4 + 15) & ~15u;
+    mbar_expect_tx(&s_full[k & 1], 2 * W * b8 + bw + b4);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      bulk_g2s(sg.x(q), in.x + size_t(q) * in.cap + p0, b8, &s_full[k & 1]);
+      bulk_g2s(sg.z(q), in.z + size_t(q) * in.cap + p0, b8, &s_full[k & 1]);
+    }
+    bulk_g2s(sg.w(), in.w + p0, bw, &s_full[k & 1]);
+    bulk_g2s(sg.g(), in.g + p0, b4, &s_full[k & 1]);
+  };
+  if (bulk && tid == 0) {
+    if (ntiles > 0) issue(0);
+    if (ntiles > 1) issue(1);
+  }
+  // this thread's running letter code and its generator (checked launches)
   uint32_t code_g = 0xffffffffu, code = 0;
-  // this lane's running statistics and their generator (last expansion)
-  uint32_t sg = 0xffffffffu;
+  // this thread's running statistics and their generator (last expansion)
+  uint32_t sgen = 0xffffffffu;
   unsigned long long sn = 0;
   double ssq = 0.0;
   auto stats_flush = [&]() {
     if (sn) {
-      atomicAdd(&sts.count[sg], sn);
-      atomicAdd(&sts.sumsq[sg], ssq);
+      atomicAdd(&sts.count[sgen], sn);
+      atomicAdd(&sts.sumsq[sgen], ssq);
     }
     sn = 0;
     ssq = 0.0;
   };
-  for (size_t span = s0; span < s1; ++span) {
-    const size_t base = span * kXsSpan;
-    // every parent of the lane first (independent loads), then the counts
-    // and the warp's places in parent order (with pruning: of the surviving
-    // children), then the children
-    uint64_t x[kXsItems][W], z[kXsItems][W];
-    WT wv[kXsItems];
-    uint32_t g[kXsItems];
+  for (size_t k = 0; k < ntiles; ++k) {
+    const XtStage<W, WT> sg = stage(k);
+    const unsigned m = tile_n(k);
+    bool ok = true;
+    if (bulk) {
+      ok = mbar_wait_bounded(&s_full[k & 1], unsigned(k >> 1) & 1u, spin_limit);
+    } else {
+      const size_t p0 = P0 + k * kXtTile;
+      for (unsigned i = tid; i < m; i += kXsThreads) {
 #pragma unroll
-    for (int it = 0; it < kXsItems; ++it) {
-      const size_t i = base + size_t(it) * 32 + lane;
-      if (i < N) {
-        load_term<W>(in, i, x[it], z[it]);
-        wv[it] = in.w[i];
-        g[it] = in.g[i];
-      } else {
-#pragma unroll
-        for (int k = 0; k < W; ++k) x[it][k] = z[it][k] = 0ull;
-        wv[it] = WT(0);
-        g[it] = 0xffffffffu;
+        for (int q = 0; q < W; ++q) {
+          sg.x(q)[i] = in.x[size_t(q) * in.cap + p0 + i];
+          sg.z(q)[i] = in.z[size_t(q) * in.cap + p0 + i];
+        }
+        sg.w()[i] = in.w[p0 + i];
+        sg.g()[i] = in.g[p0 + i];
       }
     }
-    unsigned cnt[kXsItems];
-    unsigned long long loc[kXsItems];
-#pragma unroll
-    for (int it = 0; it < kXsItems; ++it) {
-      const bool valid = g[it] != 0xffffffffu;
-      unsigned c = 0, kc = 0;
-      if (valid) {
-        if constexpr (NQ > 0) {
-          XsParentRows<NQ> pr;
-          c = xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
-          kc = xs_kept_r<W, WT, NQ>(st, wr, pr, x[it], z[it], wv[it], c);
-        } else {
-          c = xs_count_children<W>(st, x[it], z[it]);
-          kc = xs_kept<W, WT>(st, x[it], z[it], wv[it], c);
-        }
-        if (chk.gwire) {
-          if (g[it] != code_g) {
-            if (code) atomicOr(&chk.gwire[code_g], code);
-            code_g = g[it];
-            code = 0;
-          }
-          code |= xs_wire_code<W, NQ>(st, wr, x[it], z[it]);
-        }
+    if (__syncthreads_or(!ok)) {
+      // a copy did not complete: flag it, and let no copy outlive the block
+      if (tid == 0) {
+        atomicOr(serr, kErrSpin);
+        mbar_wait_bounded(&s_full[k & 1], unsigned(k >> 1) & 1u, spin_limit);
+        if (k + 1 < ntiles)
+          mbar_wait_bounded(&s_full[(k + 1) & 1], unsigned((k + 1) >> 1) & 1u, spin_limit);
       }
-      unsigned inc = kc;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= unsigned(d)) inc += o;
-      }
-      cnt[it] = c;
-      loc[it] = run + inc - kc;
-      run += __shfl_sync(0xffffffffu, inc, 31);
+      return;
     }
+    // parent pass: parents 2 tid and 2 tid + 1 of the tile
+    unsigned kc[2];
+    uint32_t keep[2];
 #pragma unroll
-    for (int it = 0; it < kXsItems; ++it) {
-      if (!cnt[it]) continue;
-      WT w = wv[it];
+    for (int it = 0; it < 2; ++it) {
+      const unsigned i = 2 * tid + unsigned(it);
+      kc[it] = 0;
+      keep[it] = 0;
+      if (i >= m) continue;
+      uint64_t x[W], z[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        x[q] = sg.x(q)[i];
+        z[q] = sg.z(q)[i];
+      }
+      WT w = sg.w()[i];
+      const uint32_t g = sg.g()[i];
+      if (chk.gwire) {
+        if (g != code_g) {
+          if (code) atomicOr(&chk.gwire[code_g], code);
+          code_g = g;
+          code = 0;
+        }
+        code |= xs_wire_code<W, NQ>(st, wr, x, z);
+      }
       if constexpr (CK >= 3) {
-        if (clifford_table_map_full<W, CK>(x[it], z[it], ps.tab_xz, ps.tab_e, ps.chunks, ps.live,
-                                           ps.pmk, fc))
+        if (clifford_table_map_full<W, CK>(x, z, ps.tab_xz, ps.tab_e, ps.chunks, ps.live, ps.pmk,
+                                           fc))
           w = wneg(w);
       } else if constexpr (CK == 1) {
         int neg = 0;
-        apply_ops<W>(reinterpret_cast<const uint32_t*>(s_dyn), ps.nops, x[it], z[it], &neg);
+        apply_ops<W>(s_ops, ps.nops, x, z, &neg);
         if (neg) w = wneg(w);
       }
-      const bool all = !prune || xs_keeps_all<WT>(st, w);
-      // the parent's rows again (shared-memory reads once per parent; kept
-      // in registers for one parent at a time)
-      XsParentRows<NQ ? NQ : 1> pr;
-      if constexpr (NQ > 0) xs_resolve<W, NQ>(st, wr, x[it], z[it], &pr);
-      // o + (children kept) <= lim when the range offsets hold
-      size_t o = size_t(loc[it]);
-      for (unsigned r = 0; r < cnt[it]; ++r) {
-        uint64_t cx[W], cz[W];
-        WT v;
-        if constexpr (NQ > 0) v = xs_child_r<W, WT, NQ>(wr, pr, x[it], z[it], w, r, cx, cz);
-        else v = xs_child<W, WT>(st, x[it], z[it], w, r, cx, cz);
-        if (!all && xs_pruned<WT>(st, v)) {
-          atomicAdd(&pruned[g[it]], double(v) * double(v));
-          continue;
-        }
-        if (o < lim) {
+      if constexpr (CK != 0) {  // the mapped parent, for the child pass
 #pragma unroll
-          for (int k = 0; k < W; ++k) {
-            ox[k][o] = cx[k];
-            oz[k][o] = cz[k];
-          }
-          out.w[o] = v;
-          out.g[o] = g[it];
-          if (sts.count) {
-            if (g[it] != sg) {
-              stats_flush();
-              sg = g[it];
-            }
-            ++sn;
-            ssq += double(v) * double(v);
+        for (int q = 0; q < W; ++q) {
+          sg.x(q)[i] = x[q];
+          sg.z(q)[i] = z[q];
+        }
+        sg.w()[i] = w;
+      }
+      unsigned c;
+      if constexpr (NQ > 0) {
+        XsParentRows<NQ> pr;
+        c = xs_resolve<W, NQ>(st, wr, x, z, &pr);
+      } else {
+        c = xs_count_children<W>(st, x, z);
+      }
+      if (!prune || xs_keeps_all<WT>(st, w)) {
+        kc[it] = c;
+        keep[it] = (1u << c) - 1u;
+      } else {
+        for (unsigned r = 0; r < c; ++r) {
+          uint64_t cx[W], cz[W];
+          const WT v = xs_child_at<W, WT, NQ>(st, wr, x, z, w, r, cx, cz);
+          if (xs_pruned<WT>(st, v)) {
+            atomicAdd(&pruned[g], double(v) * double(v));
+          } else {
+            keep[it] |= 1u << r;
+            ++kc[it];
           }
         }
-        ++o;
       }
+    }
+    // block scan of the kept children, in parent order
+    const unsigned v = kc[0] + kc[1];
+    unsigned inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= unsigned(d)) inc += o;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned t = lane < kXsThreads / 32 ? s_wsum[lane] : 0u;
+#pragma unroll
+      for (int d = 1; d < kXsThreads / 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, t, d);
+        if (lane >= unsigned(d)) t += o;
+      }
+      if (lane < kXsThreads / 32) s_wsum[lane] = t;
+    }
+    __syncthreads();
+    unsigned pos = inc - v + (warp ? s_wsum[warp - 1] : 0u);
+    const unsigned tile_children = s_wsum[kXsThreads / 32 - 1];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const uint32_t i = 2 * tid + uint32_t(it);
+      for (uint32_t b = keep[it]; b; b &= b - 1) cmap[pos++] = i | (uint32_t(__ffs(b) - 1) << 16);
+    }
+    __syncthreads();
+    // child pass: child e of the tile goes to run + e
+    for (unsigned e = tid; e < tile_children; e += kXsThreads) {
+      const uint32_t cm = cmap[e];
+      const unsigned i = cm & 0xffffu, r = cm >> 16;
+      uint64_t x[W], z[W], cx[W], cz[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        x[q] = sg.x(q)[i];
+        z[q] = sg.z(q)[i];
+      }
+      const uint32_t g = sg.g()[i];
+      const WT cv = xs_child_at<W, WT, NQ>(st, wr, x, z, sg.w()[i], r, cx, cz);
+      const size_t o = size_t(run) + e;
+      if (o < lim) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          out.x[size_t(q) * out.cap + o] = cx[q];
+          out.z[size_t(q) * out.cap + o] = cz[q];
+        }
+        out.w[o] = cv;
+        out.g[o] = g;
+        if (sts.count) {
+          if (g != sgen) {
+            stats_flush();
+            sgen = g;
+          }
+          ++sn;
+          ssq += double(cv) * double(cv);
+        }
+      }
+    }
+    run += tile_children;
+    __syncthreads();  // the stage and the child map are free again
+    if (bulk && tid == 0 && k + 2 < ntiles) {
+      fence_proxy_async_smem();
+      issue(k + 2);
     }
   }
   if (sts.count) stats_flush();
   if (chk.gwire && code) atomicOr(&chk.gwire[code_g], code);
   if (chk.err && run != end) {
-    // a range that wrote fewer children than its recorded share fills the
+    // a block that wrote fewer children than its recorded share fills the
     // rest with zero-weight identity terms of generator 0, so that the run
     // (repeated once its checks are read) sees only valid generator ids
-    if (lane == 0) atomicOr(chk.err, 1u);
-    for (unsigned long long i = run + lane; i < lim; i += 32) {
+    if (tid == 0) atomicOr(chk.err, 1u);
+    for (unsigned long long i = run + tid; i < lim; i += kXsThreads) {
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        ox[k][i] = 0ull;
-        oz[k][i] = 0ull;
+      for (int q = 0; q < W; ++q) {
+        out.x[size_t(q) * out.cap + i] = 0ull;
+        out.z[size_t(q) * out.cap + i] = 0ull;
       }
       out.w[i] = WT(0);
       out.g[i] = 0u;
