@@ -1750,19 +1750,19 @@ qx_status xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long
     xs_emit_allow_smem<W, WT, CK, 1>(smem);
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 1>(e, smem, grid);
   } else if (st.nq == 2) {
     xs_emit_allow_smem<W, WT, CK, 2>(smem);
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 2>(e, smem, grid);
   } else {
     xs_emit_allow_smem<W, WT, CK, 0>(smem);
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, c.spin_limit, c.sc.serr);
+        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 0>(e, smem, grid);
   }
   return QX_OK;

@@ -486,14 +486,158 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
   flush();
 }
 
+// The fused pass's image of each lane's string through its chunk tables:
+// the chunk-ordered product of the live chunks' images of the string's
+// letters, with the sign from the phase exponents in XZ form.  Each lane
+// keeps its last image (FullCache); the misses are resolved by the whole
+// warp: for each distinct missing key (the letters on the qubits the pass
+// touches), lane j reads the table entries of chunks j and j + 32 at once,
+// and the chunks combine by shuffles: the image is the XOR of the entries,
+// and the phase adds, per chunk c, its entry's exponent and twice the
+// anticommutation count of its X part with the Z part of the chunks before
+// it (a prefix XOR across the lanes).  That is the chunk-ordered product of
+// the serial loop, with one table read's latency per round instead of one
+// per chunk.  Every lane of the warp calls it; `active` lanes get their
+// image (x, z replaced) and return its sign.
+template <int W, int CB>
+__device__ __forceinline__ bool clifford_map_warp(uint64_t* x, uint64_t* z, bool active,
+                                                  const uint64_t* tab_xz, const uint8_t* tab_e,
+                                                  int chunks, uint64_t live, const PassMasks& pmk,
+                                                  FullCache<W>& fc, unsigned lane) {
+  constexpr int E = 1 << (2 * CB);
+  constexpr uint32_t M = (1u << CB) - 1;
+  uint64_t tx[W], tz[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    tx[k] = x[k] & ~pmk.idle[k];
+    tz[k] = z[k] & ~pmk.idle[k];
+  }
+  bool hit = fc.valid;
+#pragma unroll
+  for (int k = 0; k < W; ++k) hit = hit && fc.kx[k] == tx[k] && fc.kz[k] == tz[k];
+  unsigned need = __ballot_sync(0xffffffffu, active && !hit);
+  while (need) {
+    const int src = __ffs(need) - 1;
+    uint64_t kx[W], kz[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      kx[k] = __shfl_sync(0xffffffffu, tx[k], src);
+      kz[k] = __shfl_sync(0xffffffffu, tz[k], src);
+    }
+    int e = 0;  // the phase exponent mod 4 (every lane adds its share; summed below)
+    uint64_t ax[W], az[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) ax[k] = az[k] = 0;
+    for (int c0 = 0; c0 < chunks; c0 += 32) {
+      const int c = c0 + int(lane);
+      uint64_t ex[W], ez[W];
+      int ev = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) ex[k] = ez[k] = 0;
+      if (c < chunks && ((live >> c) & 1)) {
+        const int lo = c * CB, k = lo >> 6, off = lo & 63;
+        const uint64_t xw = (W == 1 || k == 0) ? kx[0] : kx[W - 1];
+        const uint64_t zw = (W == 1 || k == 0) ? kz[0] : kz[W - 1];
+        uint32_t xb, zb;
+        if (CB == 4 || off + CB <= 64) {
+          xb = uint32_t(xw >> off) & M;
+          zb = uint32_t(zw >> off) & M;
+        } else {  // k == 0 < W - 1
+          xb = uint32_t((xw >> off) | (W > 1 ? (kx[W - 1] << (64 - off)) : 0)) & M;
+          zb = uint32_t((zw >> off) | (W > 1 ? (kz[W - 1] << (64 - off)) : 0)) & M;
+        }
+        const uint32_t idx = xb | (zb << CB);
+        if (idx) {
+          const ulonglong2* ent =
+              reinterpret_cast<const ulonglong2*>(tab_xz + (size_t(c) * E + idx) * 2 * W);
+          if (W == 1) {
+            const ulonglong2 v = __ldg(ent);
+            ex[0] = v.x;
+            ez[0] = v.y;
+          } else {
+            const ulonglong2 v0 = __ldg(ent), v1 = __ldg(ent + 1);
+            ex[0] = v0.x;
+            ex[W - 1] = v0.y;
+            ez[0] = v1.x;
+            ez[W - 1] = v1.y;
+          }
+          ev = int(__ldg(tab_e + c * E + idx));
+        }
+      }
+      // Z part of the chunks before this lane's: the earlier rounds' (az)
+      // and an exclusive prefix XOR over the lanes below
+      uint64_t pz[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) pz[k] = ez[k];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const uint64_t o = __shfl_up_sync(0xffffffffu, pz[k], d);
+          if (lane >= unsigned(d)) pz[k] ^= o;
+        }
+      }
+      int anti = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) anti += __popcll((az[k] ^ pz[k] ^ ez[k]) & ex[k]);
+      e += ev + 2 * anti;
+      // the round's XOR of the entries, in every lane
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          ex[k] ^= __shfl_xor_sync(0xffffffffu, ex[k], d);
+          ez[k] ^= __shfl_xor_sync(0xffffffffu, ez[k], d);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        ax[k] ^= ex[k];
+        az[k] ^= ez[k];
+      }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+    int y = 0, c2 = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      y += __popcll(kx[k] & kz[k]);
+      c2 += __popcll(ax[k] & az[k]);
+    }
+    bool same = active;
+#pragma unroll
+    for (int k = 0; k < W; ++k) same = same && tx[k] == kx[k] && tz[k] == kz[k];
+    if (same) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        fc.kx[k] = kx[k];
+        fc.kz[k] = kz[k];
+        fc.rx[k] = ax[k];
+        fc.rz[k] = az[k];
+      }
+      fc.neg = ((y + e - c2) & 3) == 2;
+      fc.valid = true;
+    }
+    need &= ~__ballot_sync(0xffffffffu, same);
+  }
+  if (!active) return false;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    x[k] = (x[k] & pmk.idle[k]) | fc.rx[k];
+    z[k] = (z[k] & pmk.idle[k]) | fc.rz[k];
+  }
+  return fc.neg;
+}
+
 // ---------------------------------------------------------------------------
 // The emission works on tiles of kXtTile parents.  A block takes the 8
 // consecutive ranges of the count's partition that its warps would have
 // taken (one contiguous run of parents, whose children are contiguous from
 // the first range's offset) and walks them tile by tile:
 //  * one thread stages the next tiles' term planes in shared memory with
-//    bulk asynchronous copies (cp.async.bulk, completion on an mbarrier), two
-//    stages deep, so the copies of tile k + 1 run while tile k is worked on;
+//    bulk asynchronous copies (cp.async.bulk, completion on an mbarrier),
+//    kXtStages deep, so the copies of the next tiles run while tile k is
+//    worked on;
 //  * parent pass, two adjacent parents per thread: the fused Clifford pass,
 //    the rows of the fan-out wires, the children that survive pruning, and a
 //    block scan of their counts; each kept child is entered in a child map
@@ -502,20 +646,25 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_count(TermsT<WT> t,
 //    consecutive children, so every store of a warp covers one contiguous
 //    run of each plane.
 // Compared with one warp per range writing each parent's children from
-// registers, the instructions per parent drop by about half and the writes
-// are whole sectors; the copies keep the loads in flight without registers.
-constexpr int kXtTile = 2 * kXsThreads;  // parents per tile
+// registers (127 registers, two blocks per SM), this runs three blocks per
+// SM, the writes are whole sectors, and the copies keep the loads in flight
+// without registers (84M-term chain: 3.64 -> 2.59 ms with the warp-resolved
+// image misses).
+constexpr int kXtPer = 2;                   // parents per thread and tile
+constexpr int kXtTile = kXtPer * kXsThreads;  // parents per tile
+constexpr int kXtStages = 3;                // tiles staged at once
 
 template <int W, typename WT>
 __host__ __device__ constexpr size_t xt_stage_bytes() {
   return size_t(kXtTile) * (16 * W + sizeof(WT) + 4);
 }
 
-// Dynamic shared memory of the emission: two stages, the child map
+// Dynamic shared memory of the emission: the stages, the child map
 // (kXtTile x maxc entries of 4 bytes) and the gate list of a CK = 1 pass.
 template <int W, typename WT>
 __host__ __device__ constexpr size_t xt_smem_bytes(int maxc, int nops) {
-  return 2 * xt_stage_bytes<W, WT>() + size_t(kXtTile) * size_t(maxc) * 4 + size_t(nops) * 4;
+  return kXtStages * xt_stage_bytes<W, WT>() + size_t(kXtTile) * size_t(maxc) * 4 +
+         size_t(nops) * 4;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -533,26 +682,26 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+// One bounded wait for phase `parity`: the thread is suspended (it issues
+// nothing) until the phase completes or about `hint_ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity, unsigned hint_ns) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
 
-// Waits for phase `parity` of the barrier, at most `limit` polls (spinning
-// first, then with short sleeps); false if it gave up.
+// Waits for phase `parity` of the barrier, at most `limit` suspended tries of
+// about a microsecond each; false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
                                                   unsigned limit) {
-  for (unsigned it = 0; it < limit; ++it) {
-    if (mbar_test(bar, parity)) return true;
-    if (it >= 64) __nanosleep(64);
-  }
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity, 1000u)) return true;
   return false;
 }
 
@@ -652,14 +801,14 @@ __device__ __forceinline__ WT xs_child_at(const XsStep& st, const XsWires<NQ ? N
 // boundary and in.cap is a multiple of 4, so that copies rounded up to 16
 // bytes stay inside the planes) stages tiles with bulk copies; otherwise the
 // threads copy them.  A copy that does not complete within `spin_limit`
-// polls sets kErrSpin in *serr and the block returns once its copies in
-// flight are done (or given up on as well).
+// tries (about a microsecond each) sets kErrSpin in *serr and the block
+// returns once its copies in flight are done (or given up on as well).
 // CK selects the fused Clifford pass: 0 none, 1 gate list (in shared
 // memory), 3 or 4 chunk tables (read from global memory: the image cache of
-// clifford_table_map_full hits for all but the first parent of a run of
-// parents with the same touched letters, so the tables are rarely read).
+// clifford_map_warp hits for all but the first parent of a run of parents
+// with the same touched letters, so the tables are rarely read).
 template <int W, typename WT, int CK, int NQ>
-__global__ void __launch_bounds__(kXsThreads) k_xs_emit(
+__global__ void __launch_bounds__(kXsThreads, 3) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
     const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, XsStats sts, double* pruned,
@@ -670,13 +819,13 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   if (total > cap) return;
   extern __shared__ __align__(16) unsigned char s_raw[];
   __shared__ XsStep st;
-  __shared__ __align__(8) uint64_t s_full[2];
+  __shared__ __align__(8) uint64_t s_full[kXtStages];
   __shared__ unsigned s_wsum[kXsThreads / 32];
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   auto stage = [&](size_t k) {
-    return XtStage<W, WT>{s_raw + (k & 1) * xt_stage_bytes<W, WT>()};
+    return XtStage<W, WT>{s_raw + (k % kXtStages) * xt_stage_bytes<W, WT>()};
   };
-  uint32_t* cmap = reinterpret_cast<uint32_t*>(s_raw + 2 * xt_stage_bytes<W, WT>());
+  uint32_t* cmap = reinterpret_cast<uint32_t*>(s_raw + kXtStages * xt_stage_bytes<W, WT>());
   const uint32_t* s_ops = cmap + size_t(kXtTile) * size_t(maxc);
   load_xs_step(&st, step);
   if constexpr (CK == 1) {
@@ -684,8 +833,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     for (int i = tid; i < ps.nops; i += blockDim.x) o[i] = ps.ops[i];
   }
   if (tid == 0) {
-    mbar_init(&s_full[0], 1);
-    mbar_init(&s_full[1], 1);
+    for (int q = 0; q < kXtStages; ++q) mbar_init(&s_full[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -707,25 +855,26 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
   const size_t lim = size_t(end < cap ? end : cap);
   // tile k of the block: parents [P0 + k T, min(P1, P0 + (k + 1) T))
   auto tile_n = [&](size_t k) { return unsigned(min(size_t(kXtTile), P1 - P0 - k * kXtTile)); };
-  auto issue = [&](size_t k) {  // one thread: bulk copies of tile k into stage k & 1
+  auto issue = [&](size_t k) {  // one thread: bulk copies of tile k into its stage
     const XtStage<W, WT> sg = stage(k);
+    uint64_t* bar = &s_full[k % kXtStages];
     const size_t p0 = P0 + k * kXtTile;
     const unsigned m = tile_n(k);
     const unsigned b8 = (m * 8 + 15) & ~15u, bw = (m * unsigned(sizeof(WT)) + 15) & ~15u,
                    b4 = (m * 4 + 15) & ~15u;
-    mbar_expect_tx(&s_full[k & 1], 2 * W * b8 + bw + b4);
+    mbar_expect_tx(bar, 2 * W * b8 + bw + b4);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-      bulk_g2s(sg.x(q), in.x + size_t(q) * in.cap + p0, b8, &s_full[k & 1]);
-      bulk_g2s(sg.z(q), in.z + size_t(q) * in.cap + p0, b8, &s_full[k & 1]);
+      bulk_g2s(sg.x(q), in.x + size_t(q) * in.cap + p0, b8, bar);
+      bulk_g2s(sg.z(q), in.z + size_t(q) * in.cap + p0, b8, bar);
     }
-    bulk_g2s(sg.w(), in.w + p0, bw, &s_full[k & 1]);
-    bulk_g2s(sg.g(), in.g + p0, b4, &s_full[k & 1]);
+    bulk_g2s(sg.w(), in.w + p0, bw, bar);
+    bulk_g2s(sg.g(), in.g + p0, b4, bar);
   };
-  if (bulk && tid == 0) {
-    if (ntiles > 0) issue(0);
-    if (ntiles > 1) issue(1);
-  }
+  // tile k waits for phase (k / kXtStages) mod 2 of its stage's barrier
+  auto parity = [](size_t k) { return unsigned(k / kXtStages) & 1u; };
+  if (bulk && tid == 0)
+    for (size_t k = 0; k < size_t(kXtStages) && k < ntiles; ++k) issue(k);
   // this thread's running letter code and its generator (checked launches)
   uint32_t code_g = 0xffffffffu, code = 0;
   // this thread's running statistics and their generator (last expansion)
@@ -745,7 +894,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     const unsigned m = tile_n(k);
     bool ok = true;
     if (bulk) {
-      ok = mbar_wait_bounded(&s_full[k & 1], unsigned(k >> 1) & 1u, spin_limit);
+      ok = mbar_wait_bounded(&s_full[k % kXtStages], parity(k), spin_limit);
     } else {
       const size_t p0 = P0 + k * kXtTile;
       for (unsigned i = tid; i < m; i += kXsThreads) {
@@ -762,29 +911,40 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
       // a copy did not complete: flag it, and let no copy outlive the block
       if (tid == 0) {
         atomicOr(serr, kErrSpin);
-        mbar_wait_bounded(&s_full[k & 1], unsigned(k >> 1) & 1u, spin_limit);
-        if (k + 1 < ntiles)
-          mbar_wait_bounded(&s_full[(k + 1) & 1], unsigned((k + 1) >> 1) & 1u, spin_limit);
+        for (size_t j = k; j < k + kXtStages && j < ntiles; ++j)
+          mbar_wait_bounded(&s_full[j % kXtStages], parity(j), spin_limit);
       }
       return;
     }
-    // parent pass: parents 2 tid and 2 tid + 1 of the tile
-    unsigned kc[2];
-    uint32_t keep[2];
+    // parent pass: parents kXtPer tid ... kXtPer tid + kXtPer - 1 of the tile
+    unsigned kc[kXtPer];
+    uint32_t keep[kXtPer];
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const unsigned i = 2 * tid + unsigned(it);
+    for (int it = 0; it < kXtPer; ++it) {
+      const unsigned i = kXtPer * tid + unsigned(it);
+      const bool valid = i < m;
       kc[it] = 0;
       keep[it] = 0;
-      if (i >= m) continue;
       uint64_t x[W], z[W];
+      WT w = WT(0);
+      uint32_t g = 0;
 #pragma unroll
-      for (int q = 0; q < W; ++q) {
-        x[q] = sg.x(q)[i];
-        z[q] = sg.z(q)[i];
+      for (int q = 0; q < W; ++q) x[q] = z[q] = 0;
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          x[q] = sg.x(q)[i];
+          z[q] = sg.z(q)[i];
+        }
+        w = sg.w()[i];
+        g = sg.g()[i];
       }
-      WT w = sg.w()[i];
-      const uint32_t g = sg.g()[i];
+      if constexpr (CK >= 3) {  // every lane takes part (misses are resolved by the warp)
+        if (clifford_map_warp<W, CK>(x, z, valid, ps.tab_xz, ps.tab_e, ps.chunks, ps.live, ps.pmk,
+                                     fc, lane))
+          w = wneg(w);
+      }
+      if (!valid) continue;
       if (chk.gwire) {
         if (g != code_g) {
           if (code) atomicOr(&chk.gwire[code_g], code);
@@ -793,11 +953,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
         }
         code |= xs_wire_code<W, NQ>(st, wr, x, z);
       }
-      if constexpr (CK >= 3) {
-        if (clifford_table_map_full<W, CK>(x, z, ps.tab_xz, ps.tab_e, ps.chunks, ps.live, ps.pmk,
-                                           fc))
-          w = wneg(w);
-      } else if constexpr (CK == 1) {
+      if constexpr (CK == 1) {
         int neg = 0;
         apply_ops<W>(s_ops, ps.nops, x, z, &neg);
         if (neg) w = wneg(w);
@@ -834,7 +990,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
       }
     }
     // block scan of the kept children, in parent order
-    const unsigned v = kc[0] + kc[1];
+    unsigned v = 0;
+#pragma unroll
+    for (int it = 0; it < kXtPer; ++it) v += kc[it];
     unsigned inc = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -856,8 +1014,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     unsigned pos = inc - v + (warp ? s_wsum[warp - 1] : 0u);
     const unsigned tile_children = s_wsum[kXsThreads / 32 - 1];
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const uint32_t i = 2 * tid + uint32_t(it);
+    for (int it = 0; it < kXtPer; ++it) {
+      const uint32_t i = kXtPer * tid + uint32_t(it);
       for (uint32_t b = keep[it]; b; b &= b - 1) cmap[pos++] = i | (uint32_t(__ffs(b) - 1) << 16);
     }
     __syncthreads();
@@ -894,9 +1052,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xs_emit(
     }
     run += tile_children;
     __syncthreads();  // the stage and the child map are free again
-    if (bulk && tid == 0 && k + 2 < ntiles) {
+    if (bulk && tid == 0 && k + kXtStages < ntiles) {
       fence_proxy_async_smem();
-      issue(k + 2);
+      issue(k + kXtStages);
     }
   }
   if (sts.count) stats_flush();

@@ -543,103 +543,17 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
   return ((e - c2) & 3) == 2;
 }
 
-// Whole-string form with a one-entry cache: the image of a string depends
+// One-entry cache of a whole-string image: the image of a string depends
 // only on its letters on the touched qubits (the others pass through and add
 // nothing to the sign: their Y's count once in the string's exponent and once
 // in the image's), so a lane whose next string has the same touched letters
-// reuses the last image and sign.  On a miss every live chunk is read.
+// reuses the last image and sign (clifford_map_warp in the fused expansion).
 template <int W>
 struct FullCache {
   uint64_t kx[W], kz[W], rx[W], rz[W];
   bool neg;
   bool valid = false;
 };
-
-template <int W, int CB>
-__device__ __forceinline__ bool clifford_table_map_full(uint64_t* x, uint64_t* z,
-                                                        const uint64_t* s_tab, const uint8_t* s_e,
-                                                        int chunks, uint64_t live,
-                                                        const PassMasks& pmk, FullCache<W>& fc) {
-  constexpr int E = 1 << (2 * CB);
-  constexpr uint32_t M = (1u << CB) - 1;
-  uint64_t tx[W], tz[W];
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    tx[k] = x[k] & ~pmk.idle[k];
-    tz[k] = z[k] & ~pmk.idle[k];
-  }
-  bool hit = fc.valid;
-#pragma unroll
-  for (int k = 0; k < W; ++k) hit = hit && fc.kx[k] == tx[k] && fc.kz[k] == tz[k];
-  if (!hit) {
-    int e = 0;
-#pragma unroll
-    for (int k = 0; k < W; ++k) e += __popcll(tx[k] & tz[k]);
-    uint64_t ax[W], az[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      ax[k] = 0;
-      az[k] = 0;
-    }
-    for (int c = 0; c < chunks; ++c) {
-      if (!((live >> c) & 1)) continue;
-      const int lo = c * CB, k = lo >> 6, off = lo & 63;
-      const uint64_t xw = (W == 1 || k == 0) ? tx[0] : tx[W - 1];
-      const uint64_t zw = (W == 1 || k == 0) ? tz[0] : tz[W - 1];
-      uint32_t xb, zb;
-      if (CB == 4 || off + CB <= 64) {
-        xb = uint32_t(xw >> off) & M;
-        zb = uint32_t(zw >> off) & M;
-      } else {  // k == 0 < W - 1
-        xb = uint32_t((xw >> off) | (W > 1 ? (tx[W - 1] << (64 - off)) : 0)) & M;
-        zb = uint32_t((zw >> off) | (W > 1 ? (tz[W - 1] << (64 - off)) : 0)) & M;
-      }
-      const uint32_t idx = xb | (zb << CB);
-      if (!idx) continue;
-      const ulonglong2* ent =
-          reinterpret_cast<const ulonglong2*>(s_tab + (size_t(c) * E + idx) * 2 * W);
-      uint64_t ex[W], ez[W];
-      if (W == 1) {
-        const ulonglong2 v = ent[0];
-        ex[0] = v.x;
-        ez[0] = v.y;
-      } else {
-        const ulonglong2 v0 = ent[0], v1 = ent[1];
-        ex[0] = v0.x;
-        ex[W - 1] = v0.y;
-        ez[0] = v1.x;
-        ez[W - 1] = v1.y;
-      }
-      int anti = 0;
-#pragma unroll
-      for (int kk = 0; kk < W; ++kk) anti += __popcll(az[kk] & ex[kk]);
-      e += int(s_e[c * E + idx]) + 2 * anti;
-#pragma unroll
-      for (int kk = 0; kk < W; ++kk) {
-        ax[kk] ^= ex[kk];
-        az[kk] ^= ez[kk];
-      }
-    }
-    int c2 = 0;
-#pragma unroll
-    for (int k = 0; k < W; ++k) c2 += __popcll(ax[k] & az[k]);
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      fc.kx[k] = tx[k];
-      fc.kz[k] = tz[k];
-      fc.rx[k] = ax[k];
-      fc.rz[k] = az[k];
-    }
-    fc.neg = ((e - c2) & 3) == 2;
-    fc.valid = true;
-  }
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    x[k] = (x[k] & pmk.idle[k]) | fc.rx[k];
-    z[k] = (z[k] & pmk.idle[k]) | fc.rz[k];
-  }
-  return fc.neg;
-}
 
 // Copies the chunk tables of a pass into shared memory (all threads).
 template <int CB, int W>
