@@ -36,6 +36,7 @@ import json
 import os
 import platform
 import statistics
+import select
 import subprocess
 import sys
 import threading
@@ -63,6 +64,7 @@ CONFIG = {
 METRIC = "Pauli-term updates/sec"
 UNIT = "term-updates/s"
 FLUSH_BYTES = 512 << 20
+RESERVE_BYTES = 12 << 30  # 83,886,120 + 41,943,080 terms x 44 B = 5.5 GB at the last step, x 2
 NON_CLIFFORD = ("T", "TDG", "RX", "RY", "RZ")
 
 
@@ -151,15 +153,23 @@ def cpu_model():
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
+        self.window = None  # host times of the timed region
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __enter__(self):
+        # the sampler's start-up (driver and NVML initialisation) stalls kernel
+        # launches for several milliseconds: wait for its first sample, so
+        # that the start-up happens before the timed region, not inside it
+        self.first = ""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
@@ -167,38 +177,53 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc:
+            ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+            if ready:
+                self.first = self.proc.stdout.readline()
+            time.sleep(0.1)
         return self
 
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
             try:
+                # the first sample predates the timed region: not counted
                 self.out = self.proc.communicate(timeout=5)[0]
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 self.out = ""
 
     def summary(self):
+        """Median SM clock and the throttle reasons of the samples taken in
+        the timed region (widened by one sampling interval on each side when
+        the region is shorter than the interval)."""
         if not self.proc:
             return None
-        sm, mx, reasons = [], 0.0, set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in getattr(self, "out", "").splitlines():
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if self.window:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if not inside:
+                inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+            rows = inside
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = {nm for r in rows for nm, v in zip(names, r[3]) if v.lower() == "active"}
+        return {"sm_mhz": statistics.median(r[1] for r in rows),
+                "sm_max_mhz": max(r[2] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows), "window": "timed region"}
 
 
 def timed_steps(fn, steps, flush, stream=None):
@@ -267,20 +292,30 @@ def run_ours(args):
         gens = qdist.shard_generators(n, rank, world, cost)
     kw = {"eps": EPS} if gens is None else {"eps": EPS, "gens": gens}
     stream = torch.cuda.current_stream()
+    # the memory pool reserves the run's peak up front (the last step holds
+    # its 42M parents and 84M children, 44 B each, plus scratch), as a server
+    # reserves its budget at start-up; growing it inside the first runs maps
+    # memory in the middle of them
+    qx.reserve_device_memory(RESERVE_BYTES, stream.cuda_stream)
     flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     flush = flush_buf.zero_
 
-    for _ in range(args.warmup):
-        qx.propagate(plan, **kw).free()
-    torch.cuda.synchronize()
-
-    # ---- device-resident timed region
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # the clock sampler starts before the warm-up steps, so that neither its
+    # start-up nor an idle GPU's clock ramp falls into the timed region; only
+    # its samples inside the timed region are summarised
     step_ms, stats = [], []
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            flush()
+            qx.propagate(plan, **kw).free()
+        torch.cuda.synchronize()
+
+        # ---- device-resident timed region
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         t_wall = time.perf_counter()
+        t_host0 = time.time()
         for _ in range(args.steps):
             flush()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -294,6 +329,7 @@ def run_ours(args):
             step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        clk.mark(t_host0, time.time())
     if world > 1:
         dist.barrier()
     total_ms = sum(step_ms)
@@ -394,6 +430,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step,
+        "step_ms": [round(t, 4) for t in step_ms],
+        "step_host_syncs": [s["host_syncs"] for s in stats],
         "higher_is_better": True, "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded circuits; no dataset)",

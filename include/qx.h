@@ -90,7 +90,10 @@ typedef struct qx_plan qx_plan;
 typedef struct qx_result qx_result;
 
 /* Optional device allocator: returns device memory of at least `bytes` bytes
- * usable on `stream` (NULL on failure); free releases it, stream-ordered. */
+ * usable on `stream` (NULL on failure); free releases it, stream-ordered.
+ * Any alignment will do: the library asks for 256 bytes more than it uses
+ * and starts its buffer at the next 256-byte boundary inside the block (free
+ * gets the pointer the allocator returned). */
 typedef void* (*qx_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*qx_free_fn)(void* ptr, void* ctx, void* stream);
 
@@ -260,6 +263,20 @@ qx_status qx_plan_clifford_apply(const qx_plan* p, size_t pass, uint64_t* x, uin
  * costs time only: qx_prop_stats.guesses_missed); plans may be shared between
  * threads and streams (the record is updated atomically). */
 qx_status qx_propagate(const qx_plan* p, const qx_prop_opts* o, qx_result** out);
+
+/* Grows the current device's default memory pool (the one cudaMallocAsync
+ * serves qx_propagate from when no allocator is given) to hold at least
+ * `bytes`, stream-ordered on `stream` (NULL: the default stream), and raises
+ * the pool's release threshold so that the memory stays reserved until the
+ * process exits (or cudaMemPoolTrimTo).  A propagation's buffers grow step by
+ * step, and a pool that has to grow with them maps new memory in the middle
+ * of a run: the first runs of a large circuit are up to 2x slower until the
+ * pool holds their peak (two runs after a reservation of the peak, five
+ * without, on the 84M-term workload).  Not a counterpart of anything in the
+ * paper (Sec. IV's M_max is the budget this reserves up front).  Blocks until
+ * the pool has grown.  QX_ENOMEM if the device cannot provide `bytes`
+ * (nothing stays reserved then); QX_EUNSUPPORTED without a device. */
+qx_status qx_reserve_device_memory(size_t bytes, void* stream);
 
 /* As qx_propagate, but the initial generators are `ngen` single terms given
  * in host memory: x, z (ngen x W words) and weights w (ngen doubles, or NULL

@@ -11,6 +11,7 @@
 #include <memory>
 #include <cstring>
 #include <type_traits>
+#include <unordered_map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -43,14 +44,31 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Blocks from a caller's allocator that did not start on a 256-byte
+// boundary: the aligned address handed out -> the caller's pointer.
+std::mutex g_realign_mu;
+std::unordered_map<void*, void*> g_realigned;
+
 struct Alloc {
   qx_alloc_fn a = nullptr;
   qx_free_fn f = nullptr;
   void* ctx = nullptr;
   cudaStream_t s = nullptr;
+  // Every block starts on a 256-byte boundary (the kernels' bulk copies and
+  // 128-bit atomics need 16): cudaMallocAsync guarantees it; a caller's
+  // allocator, which promises only the size, is asked for 256 bytes more and
+  // the block is moved up to the next boundary.
   void* get(size_t bytes) {
     if (bytes == 0) bytes = 256;
-    if (a) return a(bytes, ctx, s);
+    if (a) {
+      void* raw = a(bytes + 256, ctx, s);
+      if (!raw || (reinterpret_cast<uintptr_t>(raw) & 255u) == 0) return raw;
+      void* p = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(raw) + 255u) &
+                                        ~uintptr_t(255));
+      std::lock_guard<std::mutex> lock(g_realign_mu);
+      g_realigned[p] = raw;
+      return p;
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
       cudaGetLastError();
@@ -60,10 +78,19 @@ struct Alloc {
   }
   void put(void* p) {
     if (!p) return;
-    if (f)
+    if (f) {
+      {
+        std::lock_guard<std::mutex> lock(g_realign_mu);
+        auto it = g_realigned.find(p);
+        if (it != g_realigned.end()) {
+          p = it->second;
+          g_realigned.erase(it);
+        }
+      }
       f(p, ctx, s);
-    else
+    } else {
       cudaFreeAsync(p, s);
+    }
   }
 };
 
@@ -1707,7 +1734,8 @@ qx_status xs_count(Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused,
 
 // Whether the emission may stage tiles of t with bulk copies: every plane
 // starts on a 16-byte boundary and t.cap is a multiple of 4 (a copy rounded
-// up to 16 bytes then stays inside its plane).
+// up to 16 bytes then stays inside its plane).  alloc_terms and Alloc make
+// both true of every term buffer.
 template <typename WT>
 bool xs_bulk_ok(const TermsT<WT>& t, int W) {
   auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -1742,7 +1770,8 @@ qx_status xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   const XsStats sts{c.stats_last ? c.sc.gcount : nullptr, c.stats_last ? c.sc.gsumsq : nullptr};
   unsigned long long* n_out = c.sc.ncnt + (1 - c.cslot);  // the slot xs_accept makes current
-  const int bulk = xs_bulk_ok(in, W) ? 1 : 0;
+  if (!xs_bulk_ok(in, W))
+    return fail(QX_ECUDA, "internal error: a term buffer is not on a 16-byte boundary");
   xp->written = cap;
   QX_TRY_CUDA(cudaGetLastError());  // nothing pending before the launch
   cudaError_t e;
@@ -1750,19 +1779,19 @@ qx_status xs_launch(Ctx& c, const FanStep& fs, XsPending* xp, unsigned long long
     xs_emit_allow_smem<W, WT, CK, 1>(smem);
     k_xs_emit<W, WT, CK, 1><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
+        n_out, maxc, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 1>(e, smem, grid);
   } else if (st.nq == 2) {
     xs_emit_allow_smem<W, WT, CK, 2>(smem);
     k_xs_emit<W, WT, CK, 2><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
+        n_out, maxc, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 2>(e, smem, grid);
   } else {
     xs_emit_allow_smem<W, WT, CK, 0>(smem);
     k_xs_emit<W, WT, CK, 0><<<grid, kXsThreads, smem, c.al.s>>>(
         in, n_in, xp->offs, xp->per, xp->total_d, cap, st, ps, xp->chk, sts, c.sc.pruned, out,
-        n_out, maxc, bulk, std::max(64u, c.spin_limit / 32), c.sc.serr);
+        n_out, maxc, std::max(64u, c.spin_limit / 32), c.sc.serr);
     if ((e = cudaGetLastError()) != cudaSuccess) return xs_launch_error<W, WT, CK, 0>(e, smem, grid);
   }
   return QX_OK;
@@ -3647,6 +3676,27 @@ qx_status qx_expval(const qx_plan* p, size_t nobs, const uint64_t* x, const uint
   }
   qx_free_plan(ip);
   return s;
+}
+
+qx_status qx_reserve_device_memory(size_t bytes, void* stream) {
+  clear_error();
+  cudaGetLastError();
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(QX_EUNSUPPORTED, "no CUDA device is available");
+  }
+  set_pool_threshold();
+  if (bytes == 0) return QX_OK;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QX_ENOMEM, "the device cannot reserve " + std::to_string(bytes) + " bytes");
+  }
+  QX_TRY_CUDA(cudaFreeAsync(p, s));  // back to the pool, which keeps it
+  QX_TRY_CUDA(cudaStreamSynchronize(s));
+  return QX_OK;
 }
 
 qx_status qx_wait_selftest(uint32_t timeout_ms, int publish) {

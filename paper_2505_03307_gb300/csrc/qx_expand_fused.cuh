@@ -14,14 +14,14 @@
 //   with the per-generator letter masks that decide whether a merge was
 //   needed (the same masks as k_fan_mask);
 // * the range sums are scanned (one per warp of the emission);
-// * k_xs_emit reads each parent once, recounts its children within the span,
-//   applies the Clifford pass that precedes the step (when it acts on other
-//   qubits than the step's wires it commutes with the step, so mapping the
-//   parent first and substituting the wires' letters afterwards gives each
-//   child's image), and writes the children at the span's offset.
-// Warps work on contiguous ranges of spans independently (no block barrier):
-// each lane loads all kXsItems of its parents before it writes anything, so a
-// warp keeps that many parents per lane in flight.
+// * k_xs_emit reads each parent once (tiles staged in shared memory by bulk
+//   copies), recounts its children, applies the Clifford pass that precedes
+//   the step (when it acts on other qubits than the step's wires it commutes
+//   with the step, so mapping the parent first and substituting the wires'
+//   letters afterwards gives each child's image), and writes the children at
+//   its block's offset, consecutive children from consecutive threads.
+// The count works per range of spans (one warp each); the emission gives each
+// block 8 consecutive ranges, one contiguous run of parents.
 //
 // A plan whose step has kept the same range sums records them (the device
 // driver keeps the scan's offsets): later runs launch only k_xs_emit on the
@@ -797,12 +797,12 @@ __device__ __forceinline__ WT xs_child_at(const XsStep& st, const XsWires<NQ ? N
 // of its first range and of the next block's (the last block ends at
 // *total_d).  *n_out = cap (the output's count slot) in every case; a launch
 // sized for cap < *total_d (an output size guessed too small) writes nothing
-// else.  `bulk` (set by the host when every plane of `in` starts on a 16-byte
-// boundary and in.cap is a multiple of 4, so that copies rounded up to 16
-// bytes stay inside the planes) stages tiles with bulk copies; otherwise the
-// threads copy them.  A copy that does not complete within `spin_limit`
-// tries (about a microsecond each) sets kErrSpin in *serr and the block
-// returns once its copies in flight are done (or given up on as well).
+// else.  Every plane of `in` starts on a 16-byte boundary and in.cap is a
+// multiple of 4 (the host checks both), so a tile's copies, rounded up to 16
+// bytes, stay inside the planes.  A copy that does not complete within
+// `spin_limit` tries (about a microsecond each) sets kErrSpin in *serr and
+// the block returns once its copies in flight are done (or given up on as
+// well).
 // CK selects the fused Clifford pass: 0 none, 1 gate list (in shared
 // memory), 3 or 4 chunk tables (read from global memory: the image cache of
 // clifford_map_warp hits for all but the first parent of a run of parents
@@ -812,8 +812,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xs_emit(
     TermsT<WT> in, const unsigned long long* n_in, const unsigned long long* range_offs,
     size_t per, const unsigned long long* total_d, unsigned long long cap,
     const __grid_constant__ XsStep step, XsPass ps, XsCheck chk, XsStats sts, double* pruned,
-    TermsT<WT> out, unsigned long long* n_out, int maxc, int bulk, unsigned spin_limit,
-    unsigned* serr) {
+    TermsT<WT> out, unsigned long long* n_out, int maxc, unsigned spin_limit, unsigned* serr) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = cap;  // the output's term count
   const unsigned long long total = *total_d;
   if (total > cap) return;
@@ -873,7 +872,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xs_emit(
   };
   // tile k waits for phase (k / kXtStages) mod 2 of its stage's barrier
   auto parity = [](size_t k) { return unsigned(k / kXtStages) & 1u; };
-  if (bulk && tid == 0)
+  if (tid == 0)
     for (size_t k = 0; k < size_t(kXtStages) && k < ntiles; ++k) issue(k);
   // this thread's running letter code and its generator (checked launches)
   uint32_t code_g = 0xffffffffu, code = 0;
@@ -892,21 +891,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xs_emit(
   for (size_t k = 0; k < ntiles; ++k) {
     const XtStage<W, WT> sg = stage(k);
     const unsigned m = tile_n(k);
-    bool ok = true;
-    if (bulk) {
-      ok = mbar_wait_bounded(&s_full[k % kXtStages], parity(k), spin_limit);
-    } else {
-      const size_t p0 = P0 + k * kXtTile;
-      for (unsigned i = tid; i < m; i += kXsThreads) {
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          sg.x(q)[i] = in.x[size_t(q) * in.cap + p0 + i];
-          sg.z(q)[i] = in.z[size_t(q) * in.cap + p0 + i];
-        }
-        sg.w()[i] = in.w[p0 + i];
-        sg.g()[i] = in.g[p0 + i];
-      }
-    }
+    const bool ok = mbar_wait_bounded(&s_full[k % kXtStages], parity(k), spin_limit);
     if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag it, and let no copy outlive the block
       if (tid == 0) {
@@ -1052,7 +1037,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xs_emit(
     }
     run += tile_children;
     __syncthreads();  // the stage and the child map are free again
-    if (bulk && tid == 0 && k + kXtStages < ntiles) {
+    if (tid == 0 && k + kXtStages < ntiles) {
       fence_proxy_async_smem();
       issue(k + kXtStages);
     }

@@ -38,7 +38,7 @@ EXPORTED = (
     "qx_result_from_terms", "qx_propagate_result", "qx_plan_derivative", "qx_adjoint_dot",
     "qx_tape_forward", "qx_tape_backward", "qx_tape_info", "qx_free_tape",
     "qx_group_ops_dag", "qx_plan_order", "qx_group_ops_pushthrough", "qx_adjoint_dot_pauli",
-    "qx_wait_selftest", "qx_load_circuit_u4", "qx_u4_decompose",
+    "qx_wait_selftest", "qx_load_circuit_u4", "qx_u4_decompose", "qx_reserve_device_memory",
 )
 
 
@@ -189,6 +189,7 @@ def load_library():
                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
         "qx_free_tape": (None, [_P]),
         "qx_wait_selftest": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int]),
+        "qx_reserve_device_memory": (ctypes.c_int, [_SZ, _P]),
         "qx_merge_qubit_static": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.c_int, _P, _P, _P, _P,
                                                  ctypes.c_int, _DP, _P, _P, _P, _P, _SZ,
                                                  ctypes.POINTER(_SZ), _P]),
@@ -607,6 +608,13 @@ def expval(plan: Plan, paulis, **kw):
 def wait_selftest(timeout_ms=100, publish=False):
     """qx_wait_selftest: raises QxError (QX_ETIMEOUT) when the wait gave up."""
     _check(load_library().qx_wait_selftest(int(timeout_ms), 1 if publish else 0))
+
+
+def reserve_device_memory(nbytes, stream=None):
+    """qx_reserve_device_memory: grow the current device's default memory pool
+    to hold at least ``nbytes`` (kept until exit), on ``stream`` (default:
+    PyTorch's current stream).  Raises QxError (QX_ENOMEM) if it cannot."""
+    _check(load_library().qx_reserve_device_memory(int(nbytes), _stream_ptr(stream) or None))
 
 
 def paulis_to_arrays(paulis, n):

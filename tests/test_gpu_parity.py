@@ -226,6 +226,22 @@ def test_budget_and_cap_errors():
     assert res.info(12)["nterms"] == 256
 
 
+def test_reserve_device_memory():
+    """Growing the memory pool up front: a size the device holds succeeds, one
+    it cannot hold fails with QX_ENOMEM and reserves nothing, and results do
+    not change either way."""
+    import torch
+    qx.reserve_device_memory(1 << 30)
+    free0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(qx.QxError) as e:
+        qx.reserve_device_memory(1 << 50)
+    assert e.value.name == "QX_ENOMEM"
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    n, instrs = W.random_layers(4)
+    compare_result(qx.propagate(qx.group_ops(qx.load_circuit(n, instrs))),
+                   O.propagate(n, instrs, mode="plan"))
+
+
 def test_fan_in_heavy_full_size_sampled():
     """The n=50 heavy workload at full size (2,228,256 terms), in the bench's
     launch configuration: counts and norms of every generator, and the full
