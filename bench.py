@@ -475,6 +475,8 @@ def run_ours(args):
     if world == 1:
         fma = measure_fma_peaks()
         line["fma_peaks"] = fma
+        if args.mix_steps > 0:
+            line["final_mix"] = final_mix_bench(qx, W, flush, args.mix_steps, peak)
         if args.heavy_steps > 0:
             line["heavy50"] = heavy50_bench(qx, W, flush, args.heavy_steps, peak,
                                             fma["fp64_tflops"])
@@ -740,6 +742,42 @@ def heavy50_bench(qx, W, flush, steps, peak, fp64_peak, warmup=3):
             "kernel_ms_per_step": {k: round(v["ms"] / steps, 4) for k, v in kc.items()
                                    if v["launches"]},
             "l2": "flushed between timed steps"}
+
+
+def final_mix_bench(qx, W, flush, steps, peak, warmup=3):
+    """The headline circuit with 1000 random H/S/CX gates on all 100 qubits
+    appended: the Clifford pass (A4) at HBM scale.  Those gates touch the
+    fan-out qubits, so no expansion can absorb them: they run as one in-place
+    table-form pass over all 83,886,120 terms (2N x 40 B of the survey's bytes,
+    6.7 GB), timed by CUDA events around the launch."""
+    n, instrs = W.fan_in_deep(1, final_mix=1000)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    for _ in range(warmup):
+        qx.propagate(plan, eps=EPS).free()
+    ms, res = timed_steps(lambda: qx.propagate(plan, eps=EPS), steps, flush)
+    st = res[0].stats()
+    res[0].free()
+    kst = []
+    for _ in range(steps):
+        flush()
+        r = qx.propagate(plan, eps=EPS, kernel_timing=True)
+        kst.append(r.stats())
+        r.free()
+    kc = kernel_classes(kst)
+    cp = kc.get("clifford_pass", {"ms": 0.0, "launches": 0, "alg_bytes": 0})
+    last_ms = cp["ms"] / steps
+    # the class also holds the first pass, over the 100 initial terms (tiny)
+    achieved = cp["alg_bytes"] / (cp["ms"] / 1e3) / 1e9 if cp["ms"] > 0 else 0.0
+    m = statistics.median(ms)
+    return {"workload": "fan_in_deep_n100 + 1000 random Clifford gates on all qubits",
+            "final_terms": st["final_terms"], "ms_per_step": m,
+            "term_updates_per_s": st["term_updates"] / (m / 1e3),
+            "clifford_pass_ms_per_step": last_ms,
+            "clifford_pass_launches_per_step": cp["launches"] / steps,
+            "clifford_pass_alg_gbs": achieved, "clifford_pass_frac": achieved / peak,
+            "kernel_ms_per_step": {k: round(v["ms"] / steps, 4) for k, v in kc.items()
+                                   if v["launches"]},
+            "l2": "terms larger than L2; L2 also flushed between timed steps"}
 
 
 def grouping_bench(qx, W, flush, steps, warmup=3):
@@ -1023,6 +1061,9 @@ def main():
                     help="timed steps of the gradient leg (0: skip)")
     ap.add_argument("--fp32-steps", type=int, default=5,
                     help="timed steps of the FP32 legs (0: skip)")
+    ap.add_argument("--mix-steps", type=int, default=5,
+                    help="steps of the headline circuit with an all-qubit Clifford block appended "
+                         "(0: skip)")
     ap.add_argument("--heavy-steps", type=int, default=10,
                     help="timed steps of the fan_in_heavy_n50 leg (0: skip)")
     ap.add_argument("--grouping-steps", type=int, default=5,

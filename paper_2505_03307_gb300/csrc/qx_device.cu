@@ -6,6 +6,7 @@
 // or from cudaMallocAsync on the caller's stream; nothing is allocated with a
 // blocking call on the hot path.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <memory>
@@ -203,6 +204,7 @@ struct qx_plan_device {
     size_t smem = 0;
     uint64_t live = 0;                 // chunks with a qubit some gate touches
     uint64_t idle[qx::kMaxWords] = {};  // qubits of the other chunks
+    uint64_t hot = 0;  // chunks with a qubit where one generator's terms can differ
   };
   // the plan's passes, then its aux_passes (index passes.size() + k)
   std::vector<Pass> passes;
@@ -286,6 +288,38 @@ void pass_geometry(const CliffPass& pc, int n, uint64_t* live, uint64_t* idle) {
   }
 }
 
+// Per Clifford pass of the program, the qubits where two terms of one
+// generator can carry different letters when the pass runs: the wires of
+// every fan-out step and the support of every rotation before it, carried
+// through the passes between (a pass maps a qubit's letters into the supports
+// of the images of X_q and Z_q).  Generators start as single terms.
+std::vector<std::array<uint64_t, kMaxWords>> variation_masks(const qx_plan* p) {
+  std::vector<std::array<uint64_t, kMaxWords>> hot(p->passes.size());
+  std::array<uint64_t, kMaxWords> v{};
+  const int n = p->n, W = p->W;
+  for (const Step& st : p->program) {
+    if (st.kind == kStepFan) {
+      for (const FanQubit& f : p->fans[size_t(st.index)].qs) v[f.q >> 6] |= 1ull << (f.q & 63);
+    } else if (st.kind == kStepRot) {
+      const RotStep& r = p->rots[size_t(st.index)];
+      for (int k = 0; k < W; ++k) v[k] |= r.px[k] | r.pz[k];
+    } else if (st.kind == kStepCliff) {
+      const CliffPass& pc = p->passes[size_t(st.index)];
+      hot[size_t(st.index)] = v;
+      if (pc.identity || pc.img_x.empty()) continue;
+      std::array<uint64_t, kMaxWords> nv{};
+      for (int q = 0; q < n; ++q) {
+        if (!((v[q >> 6] >> (q & 63)) & 1)) continue;
+        for (const int row : {q, n + q})
+          for (int k = 0; k < W; ++k)
+            nv[k] |= pc.img_x[size_t(row) * W + k] | pc.img_z[size_t(row) * W + k];
+      }
+      v = nv;
+    }
+  }
+  return hot;
+}
+
 qx_status ensure_plan_device(const qx_plan* cp, int device) {
   auto* p = const_cast<qx_plan*>(cp);
   if (p->dev && p->dev->device == device) return QX_OK;
@@ -329,6 +363,7 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
   }
   d->base = base;
   auto* b = static_cast<unsigned char*>(base);
+  const auto varq = variation_masks(p);
   for (size_t i = 0; i < all.size(); ++i) {
     const CliffPass& pc = *all[i];
     qx_plan_device::Pass dp;
@@ -341,7 +376,15 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
     dp.use_table = pc.use_table;
     dp.identity = pc.identity;
     dp.smem = pc.use_table ? pc.tab_xz.size() * 8 + pc.tab_e.size() : pc.ops.size() * 4;
-    if (pc.use_table) pass_geometry(pc, p->n, &dp.live, dp.idle);
+    if (pc.use_table) {
+      pass_geometry(pc, p->n, &dp.live, dp.idle);
+      if (i < varq.size())
+        for (int ch = 0; ch < pc.chunks; ++ch)
+          for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
+            const int q = ch * pc.chunk_bits + b2;
+            if (q < p->n && ((varq[i][q >> 6] >> (q & 63)) & 1)) dp.hot |= 1ull << ch;
+          }
+    }
     d->max_smem = std::max(d->max_smem, dp.smem);
     d->passes.push_back(dp);
   }
@@ -687,9 +730,22 @@ PassMasks pass_masks(const qx_plan_device::Pass& dp, int n) {
   PassMasks pmk{};
   for (int k = 0; k < kMaxWords; ++k) pmk.idle[k] = dp.idle[k];
   const int P = clifford_parts<W>();
+  // part 0: the live chunks where one generator's terms can differ, when
+  // that is some but not all of them; the other live chunks in order over
+  // the remaining parts (or all live chunks in order over all parts)
+  const uint64_t hot = dp.live & dp.hot, cold = dp.live & ~dp.hot;
+  const bool split = hot && cold;
+  std::vector<int> rest;
+  for (int ch = 0; ch < dp.chunks; ++ch)
+    if (((split ? cold : dp.live) >> ch) & 1) rest.push_back(ch);
+  const int first = split ? 1 : 0, np = P - first;
+  if (split) pmk.pchunks[0] = hot;
+  for (int pp = 0; pp < np; ++pp)
+    for (size_t r = size_t(pp) * rest.size() / np; r < size_t(pp + 1) * rest.size() / np; ++r)
+      pmk.pchunks[first + pp] |= 1ull << rest[r];
   for (int pp = 0; pp < P; ++pp)
-    for (int ch = pp * dp.chunks / P; ch < (pp + 1) * dp.chunks / P; ++ch) {
-      if (!((dp.live >> ch) & 1)) continue;
+    for (int ch = 0; ch < dp.chunks; ++ch) {
+      if (!((pmk.pchunks[pp] >> ch) & 1)) continue;
       for (int b2 = 0; b2 < dp.cb; ++b2) {
         const int q = ch * dp.cb + b2;
         if (q < n && !((dp.idle[q >> 6] >> (q & 63)) & 1)) pmk.part[pp][q >> 6] |= 1ull << (q & 63);

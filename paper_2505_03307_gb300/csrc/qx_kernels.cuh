@@ -398,11 +398,15 @@ __host__ __device__ constexpr int clifford_parts() {
 }
 
 // Qubit masks of a Clifford pass for k_clifford_table: the qubits that no
-// gate of the pass acts on (idle: their letters map to themselves), and per
-// part the other qubits of its chunks (the letters its product depends on).
+// gate of the pass acts on (idle: their letters map to themselves), per part
+// the live chunks it takes (pchunks) and their other qubits (the letters its
+// product depends on).  Parts need not be contiguous: the images of
+// different chunks are images of Paulis on disjoint qubits, so they commute
+// and their product does not depend on the order they are taken in.
 struct PassMasks {
   uint64_t idle[kMaxWords];
   uint64_t part[3][kMaxWords];
+  uint64_t pchunks[3];
 };
 
 // The image of a string is the product of its chunks' images, in chunk order
@@ -414,7 +418,11 @@ struct PassMasks {
 // * the chunks split into P parts; the product of a part, with its phase, is
 //   kept per lane together with the part's letters that produced it, and
 //   reused while the lane's next string has the same letters there (strings of
-//   one generator that differ only on fan-out wires share most parts);
+//   one generator that differ only on fan-out wires share most parts).  When
+//   the planner knows on which qubits one generator's terms can differ (the
+//   fan-out wires before the pass, carried through the passes between), part
+//   0 holds exactly the chunks of those qubits and the other parts stay
+//   cached along a generator's terms;
 // * the parts combine in order: the phase gains 2 |z_acc & x_part| (mod 4),
 //   which equals the sum of the per-chunk terms mod 2.
 //
@@ -463,8 +471,8 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
         cc.kz[p][k] = z[k] & pmk.part[p][k];
       }
       int pe = 0;
-      for (int c = p * chunks / P; c < (p + 1) * chunks / P; ++c) {
-        if (!((live >> c) & 1)) continue;
+      for (uint64_t cm = pmk.pchunks[p]; cm; cm &= cm - 1) {
+        const int c = __ffsll((long long)cm) - 1;
         const int lo = c * CB, k = lo >> 6, off = lo & 63;
         // for CB = 3 the chunk across the word boundary takes bits of both
         // words by selects, not by a run-time index (which would put the

@@ -235,13 +235,17 @@ def random_pairs(seed: int, n: int = 100, n_cliff: int = 100_000, n_rz: int = 20
     return n, _insert_at_random(rng, instrs, rz)
 
 
-def fan_in_deep(seed: int, n: int = 100, n_s: int = 20, total: int = 100_000):
+def fan_in_deep(seed: int, n: int = 100, n_s: int = 20, total: int = 100_000,
+                final_mix: int = 0):
     """Heavy n=100 workload: 80 generators of 2^20 terms (about 84M terms in all).
 
     H on every qubit, CX(i -> q) for i outside S = {0..n_s-1} and q in S, then
     n_s rounds of [random Clifford block on the qubits outside S; RZ(theta_r)
     on qubit r], and a last Clifford block outside S.  The blocks never touch
     S, so every coefficient is a product of per-qubit cos/sin factors.
+    ``final_mix`` > 0 appends that many random H/S/CX gates on all n qubits
+    (drawn after everything else, so the circuit before them is unchanged):
+    a last Clifford pass over every term that no expansion can absorb.
     """
     rng = np.random.default_rng(seed)
     S = list(range(n_s))
@@ -257,6 +261,8 @@ def fan_in_deep(seed: int, n: int = 100, n_s: int = 20, total: int = 100_000):
         instrs += _random_pair_gates(rng, rest, sizes[r])
         instrs.append(_g1("RZ", r, thetas[r]))
     instrs += _random_pair_gates(rng, rest, sizes[-1])
+    if final_mix:
+        instrs += _random_pair_gates(rng, range(n), final_mix)
     return n, instrs
 
 

@@ -191,3 +191,25 @@ def test_caller_memory_off_16_byte_boundaries(precision):
     if precision == 64:
         compare_result(ref, O.propagate(n, instrs, mode="plan", threads=CORES))
     ref.free()
+
+
+def test_final_clifford_block_on_all_qubits():
+    """A Clifford block on every qubit after the last rotation (it touches the
+    fan-out wires, so the last expansion cannot absorb it): the table-form
+    pass runs over all terms on its own, against the oracle, in both
+    precisions."""
+    n = 100
+    _, instrs = W.fan_in_deep(4, n=n, n_s=9, total=12000, final_mix=400)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    ref = O.propagate(n, instrs, mode="plan", threads=CORES)
+    for _ in range(2):  # the count path, then the plan's record
+        res = qx.propagate(plan)
+        assert res.stats()["kernels"]["clifford_pass"]["launches"] >= 1
+        compare_result(res, ref)
+        res.free()
+    r32 = qx.propagate(plan, precision=32)
+    for g in (0, 9, 50, 99):
+        got, want = r32.export_dict(g), O.as_dict(ref[g])
+        assert got.keys() == want.keys()
+        for s, w in want.items():
+            assert abs(got[s] - w) <= 1e-5 * abs(w) + 1e-7
