@@ -204,7 +204,8 @@ struct qx_plan_device {
     size_t smem = 0;
     uint64_t live = 0;                 // chunks with a qubit some gate touches
     uint64_t idle[qx::kMaxWords] = {};  // qubits of the other chunks
-    uint64_t hot = 0;  // chunks with a qubit where one generator's terms can differ
+    uint64_t hot = 0;     // chunks with a qubit where one generator's terms can differ
+    uint64_t recent = 0;  // those of the last fan-out step or rotation (they differ most often)
   };
   // the plan's passes, then its aux_passes (index passes.size() + k)
   std::vector<Pass> passes;
@@ -289,35 +290,52 @@ void pass_geometry(const CliffPass& pc, int n, uint64_t* live, uint64_t* idle) {
 }
 
 // Per Clifford pass of the program, the qubits where two terms of one
-// generator can carry different letters when the pass runs: the wires of
-// every fan-out step and the support of every rotation before it, carried
-// through the passes between (a pass maps a qubit's letters into the supports
-// of the images of X_q and Z_q).  Generators start as single terms.
-std::vector<std::array<uint64_t, kMaxWords>> variation_masks(const qx_plan* p) {
-  std::vector<std::array<uint64_t, kMaxWords>> hot(p->passes.size());
-  std::array<uint64_t, kMaxWords> v{};
+// generator can carry different letters when the pass runs (all), and among
+// them those of the last fan-out step or rotation before it (recent: the
+// children of one parent sit next to each other, so these letters change
+// from one term to the next, the older ones less often): the wires of the
+// fan-out steps and the supports of the rotations, carried through the
+// passes between (a pass maps a qubit's letters into the supports of the
+// images of X_q and Z_q).  Generators start as single terms.
+struct Variation {
+  std::array<uint64_t, kMaxWords> all{}, recent{};
+};
+
+std::vector<Variation> variation_masks(const qx_plan* p) {
+  std::vector<Variation> out(p->passes.size());
+  Variation v;
   const int n = p->n, W = p->W;
+  auto carry = [&](const CliffPass& pc, const std::array<uint64_t, kMaxWords>& m) {
+    std::array<uint64_t, kMaxWords> nm{};
+    for (int q = 0; q < n; ++q) {
+      if (!((m[q >> 6] >> (q & 63)) & 1)) continue;
+      for (const int row : {q, n + q})
+        for (int k = 0; k < W; ++k)
+          nm[k] |= pc.img_x[size_t(row) * W + k] | pc.img_z[size_t(row) * W + k];
+    }
+    return nm;
+  };
   for (const Step& st : p->program) {
     if (st.kind == kStepFan) {
-      for (const FanQubit& f : p->fans[size_t(st.index)].qs) v[f.q >> 6] |= 1ull << (f.q & 63);
+      v.recent = {};
+      for (const FanQubit& f : p->fans[size_t(st.index)].qs)
+        v.recent[f.q >> 6] |= 1ull << (f.q & 63);
+      for (int k = 0; k < W; ++k) v.all[k] |= v.recent[k];
     } else if (st.kind == kStepRot) {
       const RotStep& r = p->rots[size_t(st.index)];
-      for (int k = 0; k < W; ++k) v[k] |= r.px[k] | r.pz[k];
+      for (int k = 0; k < W; ++k) {
+        v.recent[k] = r.px[k] | r.pz[k];
+        v.all[k] |= v.recent[k];
+      }
     } else if (st.kind == kStepCliff) {
       const CliffPass& pc = p->passes[size_t(st.index)];
-      hot[size_t(st.index)] = v;
+      out[size_t(st.index)] = v;
       if (pc.identity || pc.img_x.empty()) continue;
-      std::array<uint64_t, kMaxWords> nv{};
-      for (int q = 0; q < n; ++q) {
-        if (!((v[q >> 6] >> (q & 63)) & 1)) continue;
-        for (const int row : {q, n + q})
-          for (int k = 0; k < W; ++k)
-            nv[k] |= pc.img_x[size_t(row) * W + k] | pc.img_z[size_t(row) * W + k];
-      }
-      v = nv;
+      v.all = carry(pc, v.all);
+      v.recent = carry(pc, v.recent);
     }
   }
-  return hot;
+  return out;
 }
 
 qx_status ensure_plan_device(const qx_plan* cp, int device) {
@@ -382,7 +400,9 @@ qx_status ensure_plan_device(const qx_plan* cp, int device) {
         for (int ch = 0; ch < pc.chunks; ++ch)
           for (int b2 = 0; b2 < pc.chunk_bits; ++b2) {
             const int q = ch * pc.chunk_bits + b2;
-            if (q < p->n && ((varq[i][q >> 6] >> (q & 63)) & 1)) dp.hot |= 1ull << ch;
+            if (q >= p->n) continue;
+            if ((varq[i].all[q >> 6] >> (q & 63)) & 1) dp.hot |= 1ull << ch;
+            if ((varq[i].recent[q >> 6] >> (q & 63)) & 1) dp.recent |= 1ull << ch;
           }
     }
     d->max_smem = std::max(d->max_smem, dp.smem);
@@ -730,16 +750,29 @@ PassMasks pass_masks(const qx_plan_device::Pass& dp, int n) {
   PassMasks pmk{};
   for (int k = 0; k < kMaxWords; ++k) pmk.idle[k] = dp.idle[k];
   const int P = clifford_parts<W>();
-  // part 0: the live chunks where one generator's terms can differ, when
-  // that is some but not all of them; the other live chunks in order over
-  // the remaining parts (or all live chunks in order over all parts)
-  const uint64_t hot = dp.live & dp.hot, cold = dp.live & ~dp.hot;
-  const bool split = hot && cold;
+  // own parts, first to last: the live chunks of the last fan-out step's
+  // wires (they change between neighbouring terms), the other chunks where
+  // one generator's terms can differ, then the rest (cached along a
+  // generator), split in order over the parts left; without that knowledge
+  // (everything can differ, or nothing) the live chunks in order over all
+  // parts
+  const uint64_t recent = dp.live & dp.recent & dp.hot;
+  const uint64_t old = dp.live & dp.hot & ~recent, cold = dp.live & ~dp.hot;
+  int first = 0;
+  uint64_t rest_mask = dp.live;
+  if (dp.hot & dp.live && cold) {
+    if (recent && old && P > 2) {
+      pmk.pchunks[first++] = recent;
+      pmk.pchunks[first++] = old;
+    } else {
+      pmk.pchunks[first++] = recent | old;
+    }
+    rest_mask = cold;
+  }
   std::vector<int> rest;
   for (int ch = 0; ch < dp.chunks; ++ch)
-    if (((split ? cold : dp.live) >> ch) & 1) rest.push_back(ch);
-  const int first = split ? 1 : 0, np = P - first;
-  if (split) pmk.pchunks[0] = hot;
+    if ((rest_mask >> ch) & 1) rest.push_back(ch);
+  const int np = P - first;
   for (int pp = 0; pp < np; ++pp)
     for (size_t r = size_t(pp) * rest.size() / np; r < size_t(pp + 1) * rest.size() / np; ++r)
       pmk.pchunks[first + pp] |= 1ull << rest[r];

@@ -390,11 +390,11 @@ __global__ void __launch_bounds__(256) k_clifford_ops(TermsT<WT> t, const unsign
   }
 }
 
-// Parts of the chunk range of k_clifford_table: part p is chunks
-// [p * chunks / P, (p + 1) * chunks / P).
+// Parts of the chunks of a table-form pass (each part's product is cached
+// per lane); the host assigns the chunks to them (pass_masks).
 template <int W>
 __host__ __device__ constexpr int clifford_parts() {
-  return W == 1 ? 3 : 2;
+  return 3;
 }
 
 // Qubit masks of a Clifford pass for k_clifford_table: the qubits that no
