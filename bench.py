@@ -1025,7 +1025,7 @@ def run_profile(args):
     torch.cuda.set_device(0)
     # --profile-nfan < 20: the same construction with fewer fan-out qubits
     # (80 generators of 2^k terms), a small case for multi-pass captures
-    n, instrs = W.fan_in_deep(1, n_s=args.profile_nfan)
+    n, instrs = W.fan_in_deep(1, n_s=args.profile_nfan, final_mix=args.profile_mix)
     plan = qx.group_ops(qx.load_circuit(n, instrs))
     launches = 0
     for k in range(args.warmup + args.profile_steps):
@@ -1073,6 +1073,9 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only --warmup then this many propagations of the headline workload, "
                          "no timing and no other legs (for ncu launch lists)")
+    ap.add_argument("--profile-mix", type=int, default=0,
+                    help="random Clifford gates on all qubits appended to the --profile-steps "
+                         "workload (an all-qubit table-form pass over every term)")
     ap.add_argument("--profile-nfan", type=int, default=20,
                     help="fan-out qubits of the --profile-steps workload (20: the headline)")
     args = ap.parse_args()

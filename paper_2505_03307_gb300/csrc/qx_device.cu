@@ -787,22 +787,43 @@ PassMasks pass_masks(const qx_plan_device::Pass& dp, int n) {
   return pmk;
 }
 
+// Blocks of k_clifford_table<W, CB, WT> resident per SM with `smem` bytes
+// of tables (registers and shared memory both count): the pass runs as one
+// wave of them, each warp on one contiguous range.
+template <int W, int CB, typename WT>
+int clifford_table_per_sm(size_t smem) {
+  static thread_local size_t last_smem = ~size_t(0);
+  static thread_local int last_n = 0;
+  if (smem == last_smem && last_n) return last_n;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_clifford_table<W, CB, WT>, kThreads,
+                                                    smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  last_smem = smem;
+  last_n = n;
+  return n;
+}
+
 template <int W, typename WT>
 qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   if (dp.identity || c.N == 0) return QX_OK;
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   c.begin(KC_CLIFF);
   if (dp.use_table) {
-    // as many blocks per SM as their tables fit in shared memory
-    const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, (227u << 10) / (dp.smem + 1024))));
-    const unsigned grid = grid_for(c.N, kThreads, c.sms, per_sm);
     const PassMasks pmk = pass_masks<W>(dp, c.n);
-    if (dp.cb == 4)
+    if (dp.cb == 4) {
+      const unsigned grid =
+          grid_for(c.N, kThreads, c.sms, clifford_table_per_sm<W, 4, WT>(dp.smem));
       k_clifford_table<W, 4, WT><<<grid, kThreads, dp.smem, c.al.s>>>(
           c.cur.view<WT>(), n_in, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk);
-    else
+    } else {
+      const unsigned grid =
+          grid_for(c.N, kThreads, c.sms, clifford_table_per_sm<W, 3, WT>(dp.smem));
       k_clifford_table<W, 3, WT><<<grid, kThreads, dp.smem, c.al.s>>>(
           c.cur.view<WT>(), n_in, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk);
+    }
   } else {
     const unsigned grid = grid_for(c.N, kThreads, c.sms, 8);
     k_clifford_ops<W, WT><<<grid, kThreads, dp.smem, c.al.s>>>(c.cur.view<WT>(), n_in, dp.ops, dp.nops);
