@@ -2558,7 +2558,11 @@ qx_status propagate_impl(Ctx& c, const uint64_t* init_x, const uint64_t* init_z,
     const Step& stp = prog[si];
     if (stp.kind == kStepCliff) {
       const qx_plan_device::Pass& dp = p->dev->passes[stp.index];
-      if (!dp.identity && si + 1 < prog.size() && prog[si + 1].kind == kStepFan) {
+      // a table-form pass over fewer than 64 terms per generator runs on its
+      // own: inside the expansion, a warp whose parents belong to many
+      // generators would resolve its image-cache misses one key at a time
+      const bool few = dp.use_table && c.N < size_t(64) * size_t(c.G);
+      if (!dp.identity && !few && si + 1 < prog.size() && prog[si + 1].kind == kStepFan) {
         const FanStep& nf = p->fans[prog[si + 1].index];
         if (small_fan_step(nf) && pass_disjoint(p->passes[stp.index], nf)) {
           pending = &dp;

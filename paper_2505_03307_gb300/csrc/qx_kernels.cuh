@@ -563,16 +563,32 @@ struct FullCache {
   bool valid = false;
 };
 
-// Copies the chunk tables of a pass into shared memory (all threads).
+// Copies the chunk tables of a pass into shared memory (all threads), in
+// 16-byte words with four loads of each thread in flight before their
+// stores: both tables start on 256-byte boundaries of the plan's device copy
+// and hold multiples of 16 bytes (E >= 64 entries per chunk), and s_tab, s_e
+// are 16-byte aligned.  (One 8-byte word per thread and iteration waited on
+// each load in turn: 25 us for the 70 KB of a 100-qubit pass.)
 template <int CB, int W>
 __device__ __forceinline__ void load_clifford_table(uint64_t* s_tab, uint8_t* s_e,
                                                     const uint64_t* tab_xz, const uint8_t* tab_e,
                                                     int chunks) {
   constexpr int E = 1 << (2 * CB);
-  const int nw = chunks * E * 2 * W;
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) s_tab[i] = tab_xz[i];
-  const int ne = chunks * E;
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) s_e[i] = tab_e[i];
+  auto copy16 = [](uint4* dst, const uint4* src, int n) {
+    const int B = int(blockDim.x);
+    for (int i = threadIdx.x; i < n; i += 4 * B) {
+      uint4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u * B < n) v[u] = __ldg(src + i + u * B);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u * B < n) dst[i + u * B] = v[u];
+    }
+  };
+  copy16(reinterpret_cast<uint4*>(s_tab), reinterpret_cast<const uint4*>(tab_xz),
+         chunks * E * 2 * W * 8 / 16);
+  copy16(reinterpret_cast<uint4*>(s_e), reinterpret_cast<const uint4*>(tab_e), chunks * E / 16);
 }
 
 // Each warp reads a contiguous range, so consecutive strings of a lane are
