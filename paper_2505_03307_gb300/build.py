@@ -16,7 +16,7 @@ PEAK_SRC = "qx_peak.cu"
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["qx_host.cpp", "qx_device.cu", "qx_noalloc.cu", "qx_server.cpp", "qx_adjoint.cpp",
            "qx_kak.cpp"]
-HEADERS = ["qx_common.h", "qx_kernels.cuh", "qx_expand_fused.cuh", "qx_merge_fast.cuh",
+HEADERS = ["qx_common.h", "qx_kernels.cuh", "qx_expand_fused.cuh", "qx_clifford_tiles.cuh", "qx_merge_fast.cuh",
            "qx_merge_inplace.cuh", "qx_merge_blocks.cuh", "qx_pauli_rot.cuh", "qx_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

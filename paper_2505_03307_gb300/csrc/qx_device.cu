@@ -23,6 +23,7 @@
 #include "qx_common.h"
 #include "qx_kernels.cuh"
 #include "qx_expand_fused.cuh"
+#include "qx_clifford_tiles.cuh"
 #include "qx_batch.cuh"
 
 using namespace qx;
@@ -806,12 +807,84 @@ int clifford_table_per_sm(size_t smem) {
   return n;
 }
 
+// Whether a kernel may stage tiles of t with bulk copies: every plane
+// starts on a 16-byte boundary and t.cap is a multiple of 4 (a copy rounded
+// up to 16 bytes then stays inside its plane).  alloc_terms and Alloc make
+// both true of every term buffer.
+template <typename WT>
+bool xs_bulk_ok(const TermsT<WT>& t, int W) {
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (t.cap % 4) return false;
+  for (int k = 0; k < W; ++k)
+    if (!a16(t.x + size_t(k) * t.cap) || !a16(t.z + size_t(k) * t.cap)) return false;
+  return a16(t.w) && a16(t.g);
+}
+
+// The launch error of an emission, with its configuration.
+// The dynamic shared memory limit of a kernel is process-wide (per device),
+// so it is only ever raised, under one lock for all kernels.
+void allow_dyn_smem(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> allowed[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& a = allowed[dev & 63][kernel];
+  if (smem <= a) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) ==
+      cudaSuccess)
+    a = smem;
+  else
+    cudaGetLastError();  // the launch reports it
+}
+
+// A large table-form pass in tiles staged by bulk copies (k_clifford_tiles),
+// one wave of blocks each on a contiguous run of tiles.
+template <int W, int CB, typename WT>
+qx_status run_pass_tiles(Ctx& c, const qx_plan_device::Pass& dp, const PassMasks& pmk) {
+  const size_t smem = ct_smem_bytes<W, WT>(dp.smem);
+  const void* kern = reinterpret_cast<const void*>(k_clifford_tiles<W, CB, WT>);
+  allow_dyn_smem(kern, smem);
+  static thread_local size_t last_smem = ~size_t(0);
+  static thread_local int per_sm = 0;
+  if (smem != last_smem || !per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clifford_tiles<W, CB, WT>,
+                                                      kXsThreads, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    last_smem = smem;
+  }
+  const size_t ntiles = (c.N + kCtTile - 1) / kCtTile;
+  const size_t blocks = std::min<size_t>(ntiles, size_t(c.sms) * size_t(per_sm));
+  const size_t per = (ntiles + blocks - 1) / blocks;
+  k_clifford_tiles<W, CB, WT><<<unsigned(blocks), kXsThreads, smem, c.al.s>>>(
+      c.cur.view<WT>(), c.sc.ncnt + c.cslot, dp.tab_xz, dp.tab_e, dp.chunks, dp.live, pmk, per,
+      std::max(64u, c.spin_limit / 32), c.sc.serr);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(QX_ECUDA, std::string("tiled Clifford pass launch failed: ") +
+                              cudaGetErrorString(e) + " (dynamic shared memory " +
+                              std::to_string(smem) + ")");
+  return QX_OK;
+}
+
+// Passes over at least this many terms run in tiles staged by bulk copies.
+constexpr size_t kTiledPassMin = size_t(1) << 16;
+
 template <int W, typename WT>
 qx_status run_pass(Ctx& c, const qx_plan_device::Pass& dp) {
   if (dp.identity || c.N == 0) return QX_OK;
   const unsigned long long* n_in = c.sc.ncnt + c.cslot;
   c.begin(KC_CLIFF);
-  if (dp.use_table) {
+  if (dp.use_table && c.N >= kTiledPassMin && xs_bulk_ok(c.cur.view<WT>(), W)) {
+    const PassMasks pmk = pass_masks<W>(dp, c.n);
+    if (dp.cb == 4)
+      QX_TRY((run_pass_tiles<W, 4, WT>(c, dp, pmk)));
+    else
+      QX_TRY((run_pass_tiles<W, 3, WT>(c, dp, pmk)));
+  } else if (dp.use_table) {
     const PassMasks pmk = pass_masks<W>(dp, c.n);
     if (dp.cb == 4) {
       const unsigned grid =
@@ -1842,20 +1915,6 @@ qx_status xs_count(Ctx& c, const FanStep& fs, const qx_plan_device::Pass* fused,
   return QX_OK;
 }
 
-// Whether the emission may stage tiles of t with bulk copies: every plane
-// starts on a 16-byte boundary and t.cap is a multiple of 4 (a copy rounded
-// up to 16 bytes then stays inside its plane).  alloc_terms and Alloc make
-// both true of every term buffer.
-template <typename WT>
-bool xs_bulk_ok(const TermsT<WT>& t, int W) {
-  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  if (t.cap % 4) return false;
-  for (int k = 0; k < W; ++k)
-    if (!a16(t.x + size_t(k) * t.cap) || !a16(t.z + size_t(k) * t.cap)) return false;
-  return a16(t.w) && a16(t.g);
-}
-
-// The launch error of an emission, with its configuration.
 template <int W, typename WT, int CK, int NQ>
 qx_status xs_launch_error(cudaError_t e, size_t smem, unsigned grid) {
   cudaFuncAttributes fa{};

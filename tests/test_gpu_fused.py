@@ -217,3 +217,25 @@ def test_final_clifford_block_on_all_qubits():
         assert got.keys() == want.keys()
         for s, w in want.items():
             assert abs(got[s] - w) <= 1e-5 * abs(w) + 1e-7
+
+
+@pytest.mark.parametrize("n,n_s,total,mix", [(40, 12, 600, 60), (70, 11, 800, 80)])
+def test_large_table_pass_in_tiles(n, n_s, total, mix):
+    """A table-form pass over more than 65,536 terms runs in tiles staged by
+    bulk copies (k_clifford_tiles): an all-qubit Clifford block after the
+    last rotation of a chain with 2^n_s terms per heavy generator, one- and
+    two-word strings, against the oracle in both precisions."""
+    _, instrs = W.fan_in_deep(6, n=n, n_s=n_s, total=total, final_mix=mix)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    ref = O.propagate(n, instrs, mode="plan", threads=CORES)
+    res = qx.propagate(plan)
+    assert res.nterms >= (1 << 16)
+    assert res.stats()["kernels"]["clifford_pass"]["launches"] >= 1
+    compare_result(res, ref)
+    res.free()
+    r32 = qx.propagate(plan, precision=32)
+    for g in (0, n_s, n - 1):
+        got, want = r32.export_dict(g), O.as_dict(ref[g])
+        assert got.keys() == want.keys()
+        for s, w in want.items():
+            assert abs(got[s] - w) <= 1e-5 * abs(w) + 1e-7
