@@ -785,6 +785,8 @@ PassMasks pass_masks(const qx_plan_device::Pass& dp, int n) {
         if (q < n && !((dp.idle[q >> 6] >> (q & 63)) & 1)) pmk.part[pp][q >> 6] |= 1ull << (q & 63);
       }
     }
+  for (int k = 0; k < kMaxWords; ++k)
+    for (int pp = 1; pp < P; ++pp) pmk.rest[k] |= pmk.part[pp][k];
   return pmk;
 }
 

@@ -407,6 +407,7 @@ struct PassMasks {
   uint64_t idle[kMaxWords];
   uint64_t part[3][kMaxWords];
   uint64_t pchunks[3];
+  uint64_t rest[kMaxWords];  // part[1] | part[2]
 };
 
 // The image of a string is the product of its chunks' images, in chunk order
@@ -436,6 +437,11 @@ struct CliffCache {
   uint64_t kx[P][W], kz[P][W], vx[P][W], vz[P][W];
   int ve[P];
   unsigned valid = 0;
+  // the product of parts 1 .. P-1 and the letters it came from, so that a
+  // string whose letters changed in part 0 only takes one check for them
+  uint64_t ukx[W], ukz[W], ux[W], uz[W];
+  int ue = 0;
+  bool uvalid = false;
 };
 
 template <int W, int CB>
@@ -449,14 +455,8 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
 #pragma unroll
   for (int k = 0; k < W; ++k) e += __popcll(x[k] & z[k]);
 
-  uint64_t ax[W], az[W];
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    ax[k] = 0;
-    az[k] = 0;
-  }
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
+  // the product of part p (from the lane's cache, or its chunks)
+  auto part_product = [&](int p) {
     bool same = (cc.valid >> p) & 1;
 #pragma unroll
     for (int k = 0; k < W; ++k)
@@ -525,16 +525,52 @@ __device__ __forceinline__ bool clifford_table_map(uint64_t* x, uint64_t* z, con
       cc.ve[p] = pe & 3;
       cc.valid |= 1u << p;
     }
-    int anti = 0;
+  };
+  // parts 1 .. P-1: kept as one product while their letters stay the same
+  bool up = cc.uvalid;
 #pragma unroll
-    for (int k = 0; k < W; ++k) anti += __popcll(az[k] & cc.vx[p][k]);
-    e += cc.ve[p] + 2 * anti;
+  for (int k = 0; k < W; ++k)
+    up = up && cc.ukx[k] == (x[k] & pmk.rest[k]) && cc.ukz[k] == (z[k] & pmk.rest[k]);
+  if (!up) {
+    uint64_t ux[W], uz[W];
+    int ue = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) ux[k] = uz[k] = 0;
+#pragma unroll
+    for (int p = 1; p < P; ++p) {
+      part_product(p);
+      int anti = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) anti += __popcll(uz[k] & cc.vx[p][k]);
+      ue += cc.ve[p] + 2 * anti;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        ux[k] ^= cc.vx[p][k];
+        uz[k] ^= cc.vz[p][k];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      ax[k] ^= cc.vx[p][k];
-      az[k] ^= cc.vz[p][k];
+      cc.ukx[k] = x[k] & pmk.rest[k];
+      cc.ukz[k] = z[k] & pmk.rest[k];
+      cc.ux[k] = ux[k];
+      cc.uz[k] = uz[k];
     }
+    cc.ue = ue & 3;
+    cc.uvalid = true;
   }
+  // part 0, then the rest (the chunks' images commute: any order gives the
+  // same product)
+  part_product(0);
+  uint64_t ax[W], az[W];
+  int anti = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    anti += __popcll(cc.vz[0][k] & cc.ux[k]);
+    ax[k] = cc.vx[0][k] ^ cc.ux[k];
+    az[k] = cc.vz[0][k] ^ cc.uz[k];
+  }
+  e += cc.ve[0] + cc.ue + 2 * anti;
 #pragma unroll
   for (int k = 0; k < W; ++k) {  // the letters the pass leaves alone
     ax[k] |= x[k] & pmk.idle[k];
