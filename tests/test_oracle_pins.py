@@ -399,3 +399,23 @@ def test_u4_of_named_gates_equals_the_gate():
             assert da.keys() == db.keys()
             for s, w in da.items():
                 assert abs(db[s] - w) < 1e-13
+
+
+def test_fan_in_deep_final_mix_is_a_clifford_suffix():
+    """fan_in_deep(final_mix=k) is the plain circuit followed by k H/S/CX
+    gates on all qubits, so each generator keeps its number of terms and the
+    multiset of |weights| (a Clifford block maps strings one to one and can
+    only flip signs), and every fan-out wire is touched by the suffix."""
+    base_n, base = W.fan_in_deep(5, n=12, n_s=4, total=200)
+    n, mixed = W.fan_in_deep(5, n=12, n_s=4, total=200, final_mix=60)
+    assert n == base_n and mixed[:len(base)] == base and len(mixed) == len(base) + 60
+    tail = mixed[len(base):]
+    assert all(g[0] in ("H", "S", "CX") for g in tail)
+    assert any(g[1] < 4 or (g[0] == "CX" and g[2] < 4) for g in tail)
+    a = O.propagate(n, base, mode="plan")
+    b = O.propagate(n, mixed, mode="plan")
+    for ga, gb in zip(a, b):
+        wa = sorted(abs(w) for w in O.as_dict(ga).values())
+        wb = sorted(abs(w) for w in O.as_dict(gb).values())
+        assert len(wa) == len(wb)
+        assert np.allclose(wa, wb, rtol=0, atol=1e-13)
