@@ -14,7 +14,7 @@ flushed (a 512 MB write) between timed steps, outside the per-step CUDA events.
 
 Metric: Pauli-term updates per second = sum over the K + K' grouped operators
 of the terms each was applied to, divided by the step time; beside it,
-children per second and the step's algorithmic bytes per second (the survey's
+children per second and the step's algorithmic bytes per second (the
 accounting: (parents + children) x (16W + 8) per fan-out step, plus 2N x
 (16W + 8) per Clifford pass not fused into an expansion).
 
@@ -709,7 +709,7 @@ def heavy50_bench(qx, W, flush, steps, peak, fp64_peak, warmup=3):
     """fan_in_heavy_n50 (n = 50, 2000 gates, 16 T and 16 RZ on 16 fan-out
     qubits, 34 x 65,536 + 16 x 2 = 2,228,256 final terms, 62 MB): the
     merge-heavy case.  Its 16 merge wires run in place over 53 MB of weights
-    that stay in L2 between wires, so their survey bytes are not DRAM bytes;
+    that stay in L2 between wires, so their algorithmic bytes are not DRAM bytes;
     the wire kernel is bound by the FP64 unit and is reported against the
     measured FP64 FMA rate as well."""
     n, instrs = W.fan_in_heavy(1)
@@ -738,7 +738,7 @@ def heavy50_bench(qx, W, flush, steps, peak, fp64_peak, warmup=3):
             "dominant_kernel": dom, "dominant_share": d["ms"] / sum(v["ms"] for v in kc.values()),
             "dominant_alg_gbs": achieved, "dominant_alg_frac": achieved / peak,
             "dominant_note": "L2-resident: the wires' weights stay in L2 between wires, so "
-                             "these survey bytes exceed the DRAM bytes (ncu traffic below)",
+                             "these algorithmic bytes exceed the DRAM bytes (ncu traffic below)",
             "traffic": ncu_traffic(dom, "fan_in_heavy_n50"),
             "fp64": fp64_view(dom, d, st["final_terms"], fp64_peak),
             "kernel_ms_per_step": {k: round(v["ms"] / steps, 4) for k, v in kc.items()
@@ -750,7 +750,7 @@ def final_mix_bench(qx, W, flush, steps, peak, base_cliff_ms, warmup=3):
     """The headline circuit with 1000 random H/S/CX gates on all 100 qubits
     appended: the Clifford pass (A4) at HBM scale.  Those gates touch the
     fan-out qubits, so no expansion can absorb them: they run as one in-place
-    table-form pass over all 83,886,120 terms (2N x 40 B of the survey's bytes,
+    table-form pass over all 83,886,120 terms (2N x 40 B of algorithmic bytes,
     6.7 GB), timed by CUDA events around the launch.  The class time of the
     headline circuit's own passes (base_cliff_ms: the small steps' passes) is
     taken off to give the all-qubit pass alone."""
