@@ -237,7 +237,10 @@ qx_status qx_plan_op(const qx_plan* p, size_t op, int* kind);
 
 /* LUT_1q of operator `op` (which must be a U): n x 3 x 3 doubles, row-major,
  * entry [j][a][c] = coefficient of Pauli c in the image of Pauli a under
- * U_{k,j}, with a, c in (X, Y, Z) order.  out holds n*9 doubles. */
+ * U_{k,j}, with a, c in (X, Y, Z) order.  out holds n*9 doubles.  The plan
+ * keeps each operator's instruction range, not its tables: every call
+ * composes the operator's gates again (the same arithmetic as the plan's own
+ * tables, so the values are those the plan used). */
 qx_status qx_plan_lut(const qx_plan* p, size_t op, double* out);
 
 /* Host-side inspection of the fused Clifford passes built from the plan:

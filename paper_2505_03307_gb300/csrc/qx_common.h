@@ -137,7 +137,9 @@ struct qx_plan {
   std::vector<int> op_kind;                        // chain: 1 = U, 0 = V
   // per chain op (empty for V): the tables of the wires the operator touches,
   // in increasing qubit order (every other wire's table is the identity)
-  std::vector<std::vector<std::pair<int, qx::Table3>>> luts;
+  // operator k of the chain is ins[op_begin[k] .. op_begin[k + 1]) (its
+  // per-wire tables are recomputed from these gates when asked for)
+  std::vector<size_t> op_begin;
   std::vector<qx::CliffPass> passes;
   // composed passes that no program step names (FanStep::pre_tail)
   std::vector<qx::CliffPass> aux_passes;

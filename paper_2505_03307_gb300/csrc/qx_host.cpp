@@ -5,9 +5,13 @@
 // Built with -ffp-contract=off: the composed tables must be bit-reproducible,
 // because their zero pattern decides which strings exist.
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <system_error>
+#include <thread>
 
 #include "qx_common.h"
 
@@ -136,6 +140,51 @@ void compose_step(Table3& m, const Table3& t) {
   }
 }
 
+// compose_step with the table of a signed permutation (a Clifford gate):
+// letter c goes to letter to[c] with sign sign[c].  The non-zero weights are
+// those of compose_step bit for bit (a sum with one non-zero product and
+// zeros); only the sign of a zero weight can differ, and settle() maps every
+// zero to +0 before a table is used.
+void compose_perm(Table3& m, const SignedPerm& sp) {
+  for (int p = 0; p < 3; ++p) {
+    double nw[3];
+    for (int c = 0; c < 3; ++c) nw[sp.to[c]] = sp.sign[c] > 0 ? m.r[p][c] : -m.r[p][c];
+    std::memcpy(m.r[p], nw, sizeof nw);
+  }
+}
+
+// Algorithm 1 for the wires that the one-qubit operator ins[b .. e) touches
+// (the others keep the identity table), gate by gate in list order: acc[q]
+// is wire q's composed table, not yet settled, and touched lists the wires in
+// increasing order.  seen is all zero on entry and on return.
+void compose_run(const qx_instr* ins, size_t b, size_t e, std::vector<uint8_t>& seen,
+                 std::vector<Table3>& acc, std::vector<int>& touched) {
+  touched.clear();
+  for (size_t i = b; i < e; ++i) {
+    const int q = ins[i].q0;
+    if (!seen[q]) {
+      seen[q] = 1;
+      touched.push_back(q);
+      acc[q] = kIdentity3;
+    }
+    SignedPerm sp;
+    if (clifford_image(ins[i].gate, &sp))
+      compose_perm(acc[q], sp);
+    else
+      compose_step(acc[q], gate_image(ins[i]));
+  }
+  std::sort(touched.begin(), touched.end());
+  for (const int q : touched) seen[q] = 0;
+}
+
+// The table of a wire as the plan holds it: every entry settled.
+Table3 settled(const Table3& a) {
+  Table3 t;
+  for (int r = 0; r < 3; ++r)
+    for (int col = 0; col < 3; ++col) t.r[r][col] = settle(a.r[r][col]);
+  return t;
+}
+
 // d/dtheta of a rotation table (RX, RY, RZ): (c, s) -> (-s, c).
 bool rotation_derivative(const qx_instr& g, Table3* out) {
   int a;
@@ -243,61 +292,108 @@ struct ColumnTableau {
   uint64_t* xc(int q) { return &X[size_t(q) * RW]; }
   uint64_t* zc(int q) { return &Z[size_t(q) * RW]; }
 
-  void apply(uint32_t op) {
-    const uint32_t kind = op & 3, a = (op >> 2) & 127, b = (op >> 9) & 127, perm = op >> 16;
-    if (kind == kOpCX) {
-      uint64_t *xa = xc(a), *za = zc(a), *xb = xc(b), *zb = zc(b);
-      for (int k = 0; k < RW; ++k) {
-        S[k] ^= xa[k] & zb[k] & ~(xb[k] ^ za[k]);
-        xb[k] ^= xa[k];
-        za[k] ^= zb[k];
-      }
-    } else if (kind == kOpCZ) {
-      uint64_t *xa = xc(a), *za = zc(a), *xb = xc(b), *zb = zc(b);
-      for (int k = 0; k < RW; ++k) {
-        S[k] ^= xa[k] & xb[k] & (za[k] ^ zb[k]);
-        zb[k] ^= xa[k];
-        za[k] ^= xb[k];
-      }
-    } else {
-      uint64_t *xq = xc(a), *zq = zc(a);
-      for (int k = 0; k < RW; ++k) {
-        const uint64_t m[3] = {xq[k] & ~zq[k], xq[k] & zq[k], ~xq[k] & zq[k]};
-        uint64_t nx = 0, nz = 0;
+  // Applies the pass's ops in order.  RW <= 4 (n <= 128), so the word loops
+  // unroll, and the sign row stays in registers for the whole pass.
+  void apply_all(const std::vector<uint32_t>& ops) {
+    switch (RW) {
+      case 1: run<1>(ops); break;
+      case 2: run<2>(ops); break;
+      case 3: run<3>(ops); break;
+      default: run<4>(ops); break;
+    }
+  }
+
+  template <int R>
+  void run(const std::vector<uint32_t>& ops) {
+    uint64_t s[R];
+    for (int k = 0; k < R; ++k) s[k] = S[k];
+    uint64_t *xs = X.data(), *zs = Z.data();
+    for (const uint32_t op : ops) {
+      const uint32_t kind = op & 3, a = (op >> 2) & 127, b = (op >> 9) & 127, perm = op >> 16;
+      uint64_t *xa = xs + size_t(a) * R, *za = zs + size_t(a) * R;
+      if (kind == kOpCX) {
+        uint64_t *xb = xs + size_t(b) * R, *zb = zs + size_t(b) * R;
+        for (int k = 0; k < R; ++k) {
+          s[k] ^= xa[k] & zb[k] & ~(xb[k] ^ za[k]);
+          xb[k] ^= xa[k];
+          za[k] ^= zb[k];
+        }
+      } else if (kind == kOpCZ) {
+        uint64_t *xb = xs + size_t(b) * R, *zb = zs + size_t(b) * R;
+        for (int k = 0; k < R; ++k) {
+          s[k] ^= xa[k] & xb[k] & (za[k] ^ zb[k]);
+          zb[k] ^= xa[k];
+          za[k] ^= xb[k];
+        }
+      } else {
+        // per source letter p (X, Y, Z): all-ones masks for the image's x
+        // bit, z bit and sign, decoded once for the whole column
+        uint64_t tx[3], tz[3], ts[3];
         for (int p = 0; p < 3; ++p) {
           const uint32_t f = (perm >> (3 * p)) & 7, to = f & 3;
-          if (to <= 1) nx |= m[p];
-          if (to >= 1) nz |= m[p];
-          if (f & 4) S[k] ^= m[p];
+          tx[p] = to <= 1 ? ~0ull : 0;
+          tz[p] = to >= 1 ? ~0ull : 0;
+          ts[p] = (f & 4) ? ~0ull : 0;
         }
-        xq[k] = nx;
-        zq[k] = nz;
+        for (int k = 0; k < R; ++k) {
+          const uint64_t m0 = xa[k] & ~za[k], m1 = xa[k] & za[k], m2 = ~xa[k] & za[k];
+          xa[k] = (m0 & tx[0]) | (m1 & tx[1]) | (m2 & tx[2]);
+          za[k] = (m0 & tz[0]) | (m1 & tz[1]) | (m2 & tz[2]);
+          s[k] ^= (m0 & ts[0]) | (m1 & ts[1]) | (m2 & ts[2]);
+        }
       }
     }
+    for (int k = 0; k < R; ++k) S[k] = s[k];
   }
 };
 
+// In-place transpose of a 64 x 64 bit matrix held as 64 rows (bit j of a[i]
+// is entry (i, j)): swap the off-diagonal blocks of 32, then of 16, ... 1.
+void transpose64(uint64_t* a) {
+  uint64_t m = 0x00000000FFFFFFFFull;
+  for (int j = 32; j != 0; j >>= 1, m ^= (m << j)) {
+    for (int k = 0; k < 64; k = ((k | j) + 1) & ~j) {
+      const uint64_t t = ((a[k] >> j) ^ a[k | j]) & m;
+      a[k] ^= t << j;
+      a[k | j] ^= t;
+    }
+  }
+}
+
 void build_pass_tables(CliffPass& pc, int n, int W) {
-  pc.support[0] = pc.support[1] = 0;
+  uint64_t sup[2] = {0, 0};
   for (const uint32_t op : pc.ops) {
     const int q0 = int((op >> 2) & 127), q1 = int((op >> 9) & 127);
-    pc.support[q0 >> 6] |= 1ull << (q0 & 63);
-    if ((op & 3) != kOpPerm) pc.support[q1 >> 6] |= 1ull << (q1 & 63);
+    sup[q0 >> 6] |= 1ull << (q0 & 63);
+    if ((op & 3) != kOpPerm) sup[q1 >> 6] |= 1ull << (q1 & 63);
   }
+  pc.support[0] = sup[0];
+  pc.support[1] = sup[1];
   ColumnTableau tab(n);
-  for (uint32_t op : pc.ops) tab.apply(op);
+  tab.apply_all(pc.ops);
   pc.img_x.assign(size_t(2 * n) * W, 0);
   pc.img_z.assign(size_t(2 * n) * W, 0);
   pc.img_e.assign(2 * n, 0);
+  // rows of the image from the tableau's columns, 64 x 64 bit blocks at a
+  // time (row bits of the columns past 2n and columns past n are zero)
+  uint64_t blk[64];
+  for (int side = 0; side < 2; ++side) {
+    const std::vector<uint64_t>& col = side ? tab.Z : tab.X;
+    std::vector<uint64_t>& img = side ? pc.img_z : pc.img_x;
+    for (int k = 0; k < tab.RW; ++k)
+      for (int w = 0; w < W; ++w) {
+        for (int i = 0; i < 64; ++i) {
+          const int q = 64 * w + i;
+          blk[i] = q < n ? col[size_t(q) * tab.RW + k] : 0;
+        }
+        transpose64(blk);
+        for (int i = 0; i < 64 && 64 * k + i < 2 * n; ++i) img[size_t(64 * k + i) * W + w] = blk[i];
+      }
+  }
   bool ident = true;
   for (int r = 0; r < 2 * n; ++r) {
-    uint64_t* xr = &pc.img_x[size_t(r) * W];
-    uint64_t* zr = &pc.img_z[size_t(r) * W];
-    for (int q = 0; q < n; ++q) {
-      const uint64_t bit = 1ull << (r % 64);
-      if (tab.X[size_t(q) * tab.RW + r / 64] & bit) xr[q / 64] |= 1ull << (q % 64);
-      if (tab.Z[size_t(q) * tab.RW + r / 64] & bit) zr[q / 64] |= 1ull << (q % 64);
-    }
+    const uint64_t* xr = &pc.img_x[size_t(r) * W];
+    const uint64_t* zr = &pc.img_z[size_t(r) * W];
     // Hermitian image (-1)^s H(x, z) = (-1)^s i^{|x & z|} X^x Z^z in XZ form
     const int s = int((tab.S[r / 64] >> (r % 64)) & 1);
     int xz = 0;
@@ -342,6 +438,32 @@ void build_pass_tables(CliffPass& pc, int n, int W) {
       pc.tab_e[size_t(c) * E + idx] = e;
     }
   }
+}
+
+// The tables of every pass of a plan.  Passes are independent, so a plan
+// with many Clifford gates builds them on several threads (one pass per task;
+// the tables do not depend on the split).  Plans under 2 x kOpsPerThread ops
+// stay on the calling thread.
+constexpr size_t kOpsPerThread = 10000;
+
+void build_all_pass_tables(std::vector<CliffPass>& passes, int n, int W) {
+  size_t ops = 0;
+  for (const CliffPass& pc : passes) ops += pc.ops.size();
+  const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min({passes.size(), hw, size_t(8), ops / kOpsPerThread});
+  std::atomic<size_t> next{0};
+  auto work = [&] {
+    for (size_t i = next.fetch_add(1); i < passes.size(); i = next.fetch_add(1))
+      build_pass_tables(passes[i], n, W);
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+  } catch (const std::system_error&) {
+    // no more threads: the ones started and this one share the passes
+  }
+  work();
+  for (std::thread& t : pool) t.join();
 }
 
 }  // namespace
@@ -439,6 +561,50 @@ PauliXZ xz_product(int W, const PauliXZ& a, const PauliXZ& b) {
   return r;
 }
 
+// b <- a b (the product with a on the left, in place)
+void xz_mul_left(int W, const PauliXZ& a, PauliXZ& b) {
+  int anti = 0;
+  for (int k = 0; k < W; ++k) anti += __builtin_popcountll(a.z[k] & b.x[k]);
+  b.e = uint8_t((a.e + b.e + 2 * anti) & 3);
+  for (int k = 0; k < W; ++k) {
+    b.x[k] ^= a.x[k];
+    b.z[k] ^= a.z[k];
+  }
+}
+
+// One-qubit Clifford gate g for the push-through plan: its pass op code and
+// the images of X and Z under g^dagger s g (letter 1 X, 2 Y, 3 Z, and sign).
+struct PushPerm {
+  bool clifford = false;
+  uint32_t code = 0;
+  int lx = 1, lz = 3;
+  bool negx = false, negz = false;
+};
+
+const PushPerm& push_perm(uint32_t gate) {
+  static const std::array<PushPerm, 32> table = [] {
+    std::array<PushPerm, 32> t{};
+    for (uint32_t g = 0; g < t.size(); ++g) {
+      SignedPerm sp, inv;
+      if (!clifford_image(g, &sp)) continue;
+      PushPerm& pp = t[g];
+      pp.clifford = true;
+      for (int a = 0; a < 3; ++a)
+        pp.code |= (uint32_t(sp.to[a]) | (sp.sign[a] < 0 ? 4u : 0u)) << (3 * a);
+      const uint32_t ig = g == QX_S ? QX_SDG : g == QX_SDG ? QX_S
+                        : g == QX_SX ? QX_SXDG : g == QX_SXDG ? QX_SX : g;
+      clifford_image(ig, &inv);
+      pp.lx = inv.to[0] + 1;
+      pp.lz = inv.to[2] + 1;
+      pp.negx = inv.sign[0] < 0;
+      pp.negz = inv.sign[2] < 0;
+    }
+    return t;
+  }();
+  static const PushPerm none{};
+  return gate < table.size() ? table[gate] : none;
+}
+
 // Rotation step for exp(-i phi P / 2) with P given in XZ form: the Hermitian
 // string with P's bits and the sign i^(e - |x & z|) (folded into phi).
 RotStep rot_from_xz(int W, const PauliXZ& P, double phi) {
@@ -483,7 +649,6 @@ qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
   };
   CliffPass all;  // every Clifford gate, in circuit order
   for (const qx_instr& g : c->ins) {
-    SignedPerm sp;
     switch (g.gate) {
       case QX_RX:
       case QX_RY:
@@ -494,17 +659,19 @@ qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
       case QX_TDG:
         add_rot(image(g.q0, 3), g.gate == QX_T ? std::atan(1.0) : -std::atan(1.0));
         continue;
-      case QX_CX: {
+      case QX_CX: {  // M'(X_a) = M(X_a) M(X_b), M'(Z_b) = M(Z_a) M(Z_b)
         all.ops.push_back(encode_op(kOpCX, g.q0, g.q1, 0));
-        MX[g.q0] = xz_product(W, MX[g.q0], MX[g.q1]);
-        MZ[g.q1] = xz_product(W, MZ[g.q0], MZ[g.q1]);
+        PauliXZ &xa = MX[g.q0], &xb = MX[g.q1];
+        xz_mul(W, &xa.e, xa.x, xa.z, xb.e, xb.x, xb.z);
+        xz_mul_left(W, MZ[g.q0], MZ[g.q1]);
         continue;
       }
-      case QX_CZ: {
+      case QX_CZ: {  // M'(X_a) = M(X_a) M(Z_b), M'(X_b) = M(Z_a) M(X_b)
         all.ops.push_back(encode_op(kOpCZ, g.q0, g.q1, 0));
-        const PauliXZ xa = MX[g.q0], xb = MX[g.q1];
-        MX[g.q0] = xz_product(W, xa, MZ[g.q1]);
-        MX[g.q1] = xz_product(W, MZ[g.q0], xb);
+        PauliXZ& xa = MX[g.q0];
+        const PauliXZ& zb = MZ[g.q1];
+        xz_mul(W, &xa.e, xa.x, xa.z, zb.e, zb.x, zb.z);
+        xz_mul_left(W, MZ[g.q0], MX[g.q1]);
         continue;
       }
       case QX_SWAP:
@@ -526,20 +693,17 @@ qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
       }
       continue;
     }
-    if (!clifford_image(g.gate, &sp)) return fail(QX_EINVAL, "internal error: unknown gate");
-    uint32_t code = 0;
-    for (int a = 0; a < 3; ++a) code |= (uint32_t(sp.to[a]) | (sp.sign[a] < 0 ? 4u : 0u)) << (3 * a);
-    all.ops.push_back(encode_op(kOpPerm, g.q0, -1, code));
+    const PushPerm& pp = push_perm(g.gate);
+    if (!pp.clifford) return fail(QX_EINVAL, "internal error: unknown gate");
+    all.ops.push_back(encode_op(kOpPerm, g.q0, -1, pp.code));
     // images under the inverse gate (g^dagger s g)
-    SignedPerm inv;
-    const uint32_t ig = g.gate == QX_S ? QX_SDG : g.gate == QX_SDG ? QX_S
-                      : g.gate == QX_SX ? QX_SXDG : g.gate == QX_SXDG ? QX_SX : g.gate;
-    clifford_image(ig, &inv);
-    const PauliXZ nx = image(g.q0, inv.to[0] + 1), nz = image(g.q0, inv.to[2] + 1);
-    MX[g.q0] = nx;
-    MZ[g.q0] = nz;
-    if (inv.sign[0] < 0) MX[g.q0].e = uint8_t((MX[g.q0].e + 2) & 3);
-    if (inv.sign[2] < 0) MZ[g.q0].e = uint8_t((MZ[g.q0].e + 2) & 3);
+    if (pp.lx != 1 || pp.lz != 3) {
+      const PauliXZ nx = image(g.q0, pp.lx), nz = image(g.q0, pp.lz);
+      MX[g.q0] = nx;
+      MZ[g.q0] = nz;
+    }
+    if (pp.negx) MX[g.q0].e = uint8_t((MX[g.q0].e + 2) & 3);
+    if (pp.negz) MZ[g.q0].e = uint8_t((MZ[g.q0].e + 2) & 3);
   }
   p->passes.push_back(std::move(all));
   p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
@@ -595,24 +759,23 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   p->n = n;
   p->W = (n + 63) / 64;
   p->ins = c->ins;
-  // divide_instruction: maximal runs of one-qubit / two-qubit instructions.
-  std::vector<std::pair<size_t, size_t>> runs;  // [begin, end) per operator
+  // divide_instruction: maximal runs of one-qubit / two-qubit instructions;
+  // operator k is ins[op_begin[k] .. op_begin[k + 1]).
   for (size_t i = 0; i < c->ins.size(); ++i) {
     const bool one = !two_qubit(c->ins[i].gate);
-    if (runs.empty() || (p->op_kind.back() == 1) != one) {
-      runs.push_back({i, i});
+    if (p->op_kind.empty() || (p->op_kind.back() == 1) != one) {
+      p->op_begin.push_back(i);
       p->op_kind.push_back(one ? 1 : 0);
     }
-    runs.back().second = i + 1;
   }
-  p->luts.resize(runs.size());
+  p->op_begin.push_back(c->ins.size());
   CliffPass cur;
   uint64_t ops_since_fan = 0;
   std::vector<uint8_t> seen(static_cast<size_t>(n), 0);
   std::vector<Table3> acc(static_cast<size_t>(n));
   std::vector<int> touched;
-  for (size_t k = 0; k < runs.size(); ++k) {
-    const auto [b, e] = runs[k];
+  for (size_t k = 0; k < p->op_kind.size(); ++k) {
+    const size_t b = p->op_begin[k], e = p->op_begin[k + 1];
     if (p->op_kind[k] == 0) {
       ++p->Kp;
       for (size_t i = b; i < e; ++i) {
@@ -640,29 +803,11 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
       continue;
     }
     ++p->K;
-    // Algorithm 1 for the wires this run touches (the others keep the
-    // identity table), gate by gate in list order.
-    touched.clear();
-    for (size_t i = b; i < e; ++i) {
-      const int q = c->ins[i].q0;
-      if (!seen[q]) {
-        seen[q] = 1;
-        touched.push_back(q);
-        acc[q] = kIdentity3;
-      }
-      compose_step(acc[q], gate_image(c->ins[i]));
-    }
-    std::sort(touched.begin(), touched.end());
-    auto& lut = p->luts[k];
-    lut.reserve(touched.size());
+    compose_run(c->ins.data(), b, e, seen, acc, touched);
     FanStep fs;
     fs.op_index = k;
     for (const int j : touched) {
-      seen[j] = 0;
-      Table3 t;
-      for (int r = 0; r < 3; ++r)
-        for (int col = 0; col < 3; ++col) t.r[r][col] = settle(acc[j].r[r][col]);
-      lut.emplace_back(j, t);
+      const Table3 t = settled(acc[j]);
       uint32_t code = 0;
       const TableKind kind = classify(t, &code);
       if (kind == kSignedPerm)
@@ -686,7 +831,7 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   p->passes.push_back(std::move(cur));
   p->program.push_back({kStepCliff, int(p->passes.size() - 1), 0});
   p->ops_after_last_fan = ops_since_fan;
-  for (auto& pc : p->passes) build_pass_tables(pc, n, p->W);
+  build_all_pass_tables(p->passes, n, p->W);
   add_pre_tail_pass(p);
   *out = p;
   return QX_OK;
@@ -889,9 +1034,15 @@ qx_status qx_plan_lut(const qx_plan* p, size_t op, double* out) {
   for (int j = 0; j < p->n; ++j)
     for (int a = 0; a < 3; ++a)
       for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = kIdentity3.r[a][c];
-  for (const auto& [j, t] : p->luts[op])
+  std::vector<uint8_t> seen(size_t(p->n), 0);
+  std::vector<Table3> acc(size_t(p->n));
+  std::vector<int> touched;
+  compose_run(p->ins.data(), p->op_begin[op], p->op_begin[op + 1], seen, acc, touched);
+  for (const int j : touched) {
+    const Table3 t = settled(acc[j]);
     for (int a = 0; a < 3; ++a)
       for (int c = 0; c < 3; ++c) out[9 * j + 3 * a + c] = t.r[a][c];
+  }
   return QX_OK;
 }
 
