@@ -160,3 +160,32 @@ def test_records_and_tuples_give_the_same_plan():
     for op, kind in enumerate(a.ops()):
         if kind == "U":
             assert np.array_equal(a.lut(op), b.lut(op))
+
+
+def test_pass_tables_of_a_many_pass_plan():
+    """A plan with tens of thousands of Clifford operations over several
+    passes (its pass tables are built on several threads): every pass maps
+    strings as the oracle does through that pass's gates.  In list-order
+    grouping, pass k holds the Clifford gates up to the end of the one-qubit
+    run that holds the k-th RZ (the run's other wires commute with it)."""
+    n, instrs = W.fan_in_deep(4, n=70, n_s=6, total=50_000)
+    plan = qx.group_ops(qx.load_circuit(n, instrs))
+    two = {"CX", "CZ", "SWAP", "RXX", "RYY", "RZZ", "CRX", "CRY", "CRZ", "CP"}
+    bounds, i = [0], 0
+    while i < len(instrs):  # maximal runs of one-qubit / two-qubit gates
+        e = i
+        while e < len(instrs) and (instrs[e][0] in two) == (instrs[i][0] in two):
+            e += 1
+        if any(g[0] == "RZ" for g in instrs[i:e]):
+            bounds.append(e)
+        i = e
+    bounds.append(len(instrs))
+    passes = [[g for g in instrs[b:e] if g[0] != "RZ"] for b, e in zip(bounds, bounds[1:])]
+    assert plan.clifford_passes() == len(passes) == 7
+    assert sum(len(p) for p in passes) > 40_000
+    for k, gates in enumerate(passes):
+        starts = W.random_paulis(100 + k, n, 3)
+        ref = O.propagate(n, gates, mode="gate", init=[(s, 1.0) for s in starts])
+        for s, r in zip(starts, ref):
+            (want_s, want_w), = O.as_dict(r).items()
+            assert plan.clifford_apply(k, s) == (want_s, int(want_w))
