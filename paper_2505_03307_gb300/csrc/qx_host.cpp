@@ -177,6 +177,44 @@ void compose_run(const qx_instr* ins, size_t b, size_t e, std::vector<uint8_t>& 
   for (const int q : touched) seen[q] = 0;
 }
 
+// A wire's composed table while every gate on it so far is a Clifford gate:
+// letter p goes to letter to[p] with sign (-1)^neg[p].
+struct WirePerm {
+  uint8_t to[3], neg[3];
+};
+
+// The signed permutation of each one-qubit Clifford gate (clifford_image),
+// from a table built once; ok is false for the other gates.
+struct GatePerm {
+  bool ok;
+  uint8_t to[3], neg[3];
+};
+
+const GatePerm& gate_perm(uint32_t gate) {
+  static const std::array<GatePerm, 32> table = [] {
+    std::array<GatePerm, 32> t{};
+    for (uint32_t g = 0; g < t.size(); ++g) {
+      SignedPerm sp;
+      if (!clifford_image(g, &sp)) continue;
+      t[g].ok = true;
+      for (int a = 0; a < 3; ++a) {
+        t[g].to[a] = uint8_t(sp.to[a]);
+        t[g].neg[a] = uint8_t(sp.sign[a] < 0);
+      }
+    }
+    return t;
+  }();
+  static const GatePerm none{};
+  return gate < table.size() ? table[gate] : none;
+}
+
+// The 3 x 3 table of a signed permutation (entries +-1 and +0).
+Table3 perm_table(const WirePerm& w) {
+  Table3 t{};
+  for (int p = 0; p < 3; ++p) t.r[p][w.to[p]] = w.neg[p] ? -1.0 : 1.0;
+  return t;
+}
+
 // The table of a wire as the plan holds it: every entry settled.
 Table3 settled(const Table3& a) {
   Table3 t;
@@ -771,7 +809,10 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
   p->op_begin.push_back(c->ins.size());
   CliffPass cur;
   uint64_t ops_since_fan = 0;
-  std::vector<uint8_t> seen(static_cast<size_t>(n), 0);
+  // per wire of the current U_k: 0 untouched, 1 a signed permutation so far
+  // (wp), 2 a 3 x 3 table (acc)
+  std::vector<uint8_t> state(static_cast<size_t>(n), 0);
+  std::vector<WirePerm> wp(static_cast<size_t>(n));
   std::vector<Table3> acc(static_cast<size_t>(n));
   std::vector<int> touched;
   for (size_t k = 0; k < p->op_kind.size(); ++k) {
@@ -803,10 +844,57 @@ qx_status build_plan(const qx_circuit* c, qx_plan** out) {
       continue;
     }
     ++p->K;
-    compose_run(c->ins.data(), b, e, seen, acc, touched);
+    // Algorithm 1 for the wires this run touches, gate by gate in list
+    // order.  A wire stays a signed permutation (integers) while its gates
+    // are Clifford gates, and becomes a 3 x 3 table at its first other gate.
+    // The settled tables are those of compose_run: the permutation's entries
+    // are exact, and only signs of zeros can differ, which settle() clears.
+    touched.clear();
+    for (size_t i = b; i < e; ++i) {
+      const qx_instr& g = c->ins[i];
+      const int q = g.q0;
+      if (!state[q]) {
+        state[q] = 1;
+        touched.push_back(q);
+        wp[q] = WirePerm{{0, 1, 2}, {0, 0, 0}};
+      }
+      const GatePerm& gp = gate_perm(g.gate);
+      if (state[q] == 1 && gp.ok) {
+        WirePerm& w = wp[q];
+        for (int a = 0; a < 3; ++a) {
+          const int from = w.to[a];
+          w.to[a] = gp.to[from];
+          w.neg[a] ^= gp.neg[from];
+        }
+        continue;
+      }
+      if (state[q] == 1) {
+        acc[q] = perm_table(wp[q]);
+        state[q] = 2;
+      }
+      SignedPerm sp;
+      if (clifford_image(g.gate, &sp))
+        compose_perm(acc[q], sp);
+      else
+        compose_step(acc[q], gate_image(g));
+    }
+    std::sort(touched.begin(), touched.end());
     FanStep fs;
     fs.op_index = k;
     for (const int j : touched) {
+      if (state[j] == 1) {  // a signed permutation: the pass before the step
+        state[j] = 0;
+        const WirePerm& w = wp[j];
+        uint32_t code = 0;
+        bool ident = true;
+        for (int a = 0; a < 3; ++a) {
+          code |= (uint32_t(w.to[a]) | (w.neg[a] ? 4u : 0u)) << (3 * a);
+          ident = ident && w.to[a] == a && !w.neg[a];
+        }
+        if (!ident) cur.ops.push_back(encode_op(kOpPerm, j, -1, code));
+        continue;
+      }
+      state[j] = 0;
       const Table3 t = settled(acc[j]);
       uint32_t code = 0;
       const TableKind kind = classify(t, &code);
