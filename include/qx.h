@@ -188,8 +188,8 @@ qx_status qx_load_circuit_u4(int n, const qx_instr* ins, size_t m, const double*
 qx_status qx_u4_decompose(const double* u, int q0, int q1, qx_instr* out, size_t* count,
                           double* residual);
 
-/* divide_instruction + create_chain + create_LUT_1q (Algorithm 2 header lines,
- * Algorithm 1): maximal runs of one-qubit gates become U_k, maximal runs of
+/* divide_instruction + create_chain + create_LUT_1q (the set-up steps of
+ * Algorithm 2, and Algorithm 1): maximal runs of one-qubit gates become U_k, maximal runs of
  * two-qubit gates V_k; for each U_k and wire j the gates of U_{k,j} are
  * composed in list order into a 3x3 table.  Host only; deterministic.
  * *out is owned by the caller (qx_free_plan); it does not refer to `c`. */
