@@ -363,6 +363,7 @@ def run_ours(args):
     # host input); turning Python tuples into them is binding convenience
     # outside the ABI and happens once, here.
     e2e_ms = []
+    e2e_plan_ms = []  # host time of qx_load_circuit + qx_group_ops within each step
     h2d = d2h = 0
     e2e_updates = 0
     pinned = None
@@ -372,6 +373,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = qx.group_ops(qx.load_circuit_records(n, recs))
+        t_plan = time.perf_counter()
         r = qx.propagate(p2, **kw)
         k = r.nterms
         if pinned is None or pinned[2].numel() < k:
@@ -385,6 +387,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
+            e2e_plan_ms.append((t_plan - t0) * 1e3)
             e2e_updates += r.stats()["term_updates"]
             h2d = len(instrs) * 24
             d2h = k * (2 * 8 * r.W + 8 + 4)
@@ -444,6 +447,7 @@ def run_ours(args):
         "e2e": {"value": e2e_updates_all / (e2e_ms_max / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms_max / args.steps,
+                "plan_ms_median": statistics.median(e2e_plan_ms),
                 "path": "qx_load_circuit (host qx_instr records) -> qx_group_ops (new plan) -> "
                         "qx_propagate -> qx_result_raw into pinned host memory"},
         "gpu_launches": launches,
