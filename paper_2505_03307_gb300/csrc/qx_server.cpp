@@ -254,8 +254,13 @@ qx_status qx_server_create(const qx_server_opts* o, qx_server** out) {
     cudaGetLastError();
     s->device = 0;
   }
+  // Planning is host work that bounds the loop's throughput once requests
+  // queue up; idle planners sleep on a condition variable.  They get the
+  // cores left after the engines and two more (the caller and the rest of
+  // the process), at least one and at most 16.
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int planners = int(std::max(1u, std::min(8u, hw / 2)));
+  const unsigned spare = unsigned(opts.slots) + 2u;
+  const int planners = int(std::min(16u, hw > spare ? hw - spare : 1u));
   for (int k = 0; k < planners; ++k) s->planners.emplace_back(planner_main, s);
   for (int k = 0; k < opts.slots; ++k) s->engines.emplace_back(engine_main, s);
   *out = s;
