@@ -327,9 +327,6 @@ struct ColumnTableau {
       Z[size_t(q) * RW + (n + q) / 64] |= 1ull << ((n + q) % 64);
     }
   }
-  uint64_t* xc(int q) { return &X[size_t(q) * RW]; }
-  uint64_t* zc(int q) { return &Z[size_t(q) * RW]; }
-
   // Applies the pass's ops in order.  RW <= 4 (n <= 128), so the word loops
   // unroll, and the sign row stays in registers for the whole pass.
   void apply_all(const std::vector<uint32_t>& ops) {
