@@ -30,7 +30,9 @@ void clear_error() { g_last_error.clear(); }
 
 namespace {
 
-bool two_qubit(uint32_t g) { return g == QX_CX || g == QX_CZ || (g >= QX_SWAP && g <= QX_CP); }
+constexpr bool two_qubit(uint32_t g) {
+  return g == QX_CX || g == QX_CZ || (g >= QX_SWAP && g <= QX_CP);
+}
 
 bool rotation_2q(uint32_t g) { return g >= QX_RXX && g <= QX_CP; }
 
@@ -974,7 +976,24 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
   if (n < 1) return fail(QX_EINVAL, "n must be >= 1");
   if (n > kMaxQubits) return fail(QX_EUNSUPPORTED, "n > 128 is not supported");
   if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
+  // One pass without branches finds whether anything is wrong; only then
+  // does the loop below look for the first bad instruction and its message.
+  constexpr uint32_t kTwo = [] {
+    uint32_t mask = 0;
+    for (uint32_t g = 0; g < 32; ++g)
+      if (two_qubit(g)) mask |= 1u << g;
+    return mask;
+  }();
+  bool bad = false;
   for (size_t i = 0; i < m; ++i) {
+    const qx_instr& g = ins[i];
+    const bool two = g.gate < 32 && ((kTwo >> g.gate) & 1u);
+    bad |= g.gate > QX_CP;
+    bad |= uint32_t(g.q0) >= uint32_t(n);
+    bad |= two & ((uint32_t(g.q1) >= uint32_t(n)) | (g.q1 == g.q0));
+    bad |= !std::isfinite(g.theta);
+  }
+  for (size_t i = 0; bad && i < m; ++i) {
     const qx_instr& g = ins[i];
     if (g.gate == QX_U4)
       return fail(QX_EINVAL, "instruction " + std::to_string(i) +
