@@ -48,6 +48,22 @@ def test_validation():
     qx.load_circuit(3, [])  # empty circuit is valid
 
 
+@pytest.mark.parametrize("bad,msg", [(("H", 40, -1, 0.0), "wire out of range"),
+                                     (("CX", 7, 7, 0.0), "bad second wire"),
+                                     (("CZ", 3, -2, 0.0), "bad second wire"),
+                                     (("RZ", 1, -1, float("inf")), "theta not finite")])
+def test_validation_names_the_first_bad_instruction(bad, msg):
+    """In a long valid circuit with two faults, the error names the first."""
+    n, instrs = W.random_clifford(5, 20, 3000)
+    instrs = list(instrs)
+    instrs[1234] = bad
+    instrs[2500] = ("H", 99, -1, 0.0)
+    with pytest.raises(qx.QxError) as e:
+        qx.load_circuit(n, instrs)
+    assert e.value.name == "QX_EINVAL"
+    assert f"instruction 1234: {msg}" in str(e.value)
+
+
 def _circuits():
     yield W.random_layers(1)
     yield W.hea(2, n=8, layers=2)
