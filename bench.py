@@ -570,11 +570,21 @@ def serving_bench(qx, W, count, rate_hz, slots=2, baseline_count=300):
         r.free()
     torch.cuda.synchronize()
     base = baseline_count / (time.perf_counter() - b0)
+    # host planning alone, as one planner thread does it (load + push-through
+    # plan); the records are marshalled before the clock starts
+    recs = [(n, qx.instr_records([g for g, _, _, _ in ins], [a for _, a, _, _ in ins],
+                                 [b for _, _, b, _ in ins], [th for _, _, _, th in ins]))
+            for _, n, ins in reqs[:baseline_count]]
+    p0 = time.perf_counter()
+    for n, rec in recs:
+        qx.group_ops(qx.load_circuit_records(n, rec), pushthrough=True)
+    plan_rate = len(recs) / (time.perf_counter() - p0)
     sat = max(x["circuits_per_s"] for x in sweep)
     return {"requests": count, "slots": slots, "precision": 32, "hbm_budget_bytes": budget,
             "arrivals": "Poisson (seeded), the stream's gaps scaled to each rate",
             "sweep": sweep, "saturated_circuits_per_s": sat,
             "one_at_a_time_fp64_circuits_per_s": base,
+            "planning_circuits_per_s_per_thread": plan_rate, "host_cores": os.cpu_count(),
             "one_at_a_time_sample": f"first {baseline_count} requests of the same stream"}
 
 
