@@ -189,9 +189,9 @@ qx_status qx_u4_decompose(const double* u, int q0, int q1, qx_instr* out, size_t
                           double* residual);
 
 /* divide_instruction + create_chain + create_LUT_1q (the set-up steps of
- * Algorithm 2, and Algorithm 1): maximal runs of one-qubit gates become U_k, maximal runs of
- * two-qubit gates V_k; for each U_k and wire j the gates of U_{k,j} are
- * composed in list order into a 3x3 table.  Host only; deterministic.  A plan
+ * Algorithm 2, and Algorithm 1): maximal runs of one-qubit gates become U_k,
+ * maximal runs of two-qubit gates V_k; for each U_k and wire j the gates of
+ * U_{k,j} are composed in list order into a 3x3 table.  Host only; deterministic.  A plan
  * with 20,000 or more Clifford operations builds its passes' tables on up to
  * 8 short-lived threads, joined before the call returns (the tables do not
  * depend on the number of threads).
