@@ -167,6 +167,10 @@ qx_status decompose_u4(const double* u32, int q0, int q1, std::vector<qx_instr>*
                        double* residual);
 // Push-through plan of a circuit (qx_group_ops_pushthrough).
 qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out);
+// The same from instructions the plan takes over (already validated).
+qx_status build_plan_pushthrough(int n, std::vector<qx_instr>&& ins, qx_plan** out);
+// The checks of qx_load_circuit: n in 1..128, gate codes, wires, finite angles.
+qx_status validate_instrs(int n, const qx_instr* ins, size_t m);
 
 // Batched propagation (the serving loop): the plans, all push-through plans
 // of one word count, propagate together in one term store on `stream`

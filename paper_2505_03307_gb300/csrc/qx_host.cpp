@@ -660,12 +660,17 @@ RotStep rot_from_xz(int W, const PauliXZ& P, double phi) {
 }
 
 qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
+  return build_plan_pushthrough(c->n, std::vector<qx_instr>(c->ins), out);
+}
+
+qx_status build_plan_pushthrough(int n, std::vector<qx_instr>&& ins, qx_plan** out) {
   auto* p = new (std::nothrow) qx_plan;
   if (!p) return fail(QX_ENOMEM, "host allocation failed");
-  const int n = c->n, W = (n + 63) / 64;
+  const int W = (n + 63) / 64;
   p->n = n;
   p->W = W;
-  p->ins = c->ins;
+  p->ins = std::move(ins);
+  const std::vector<qx_instr>& cins = p->ins;
   // M(s) = D^dagger s D for the Clifford prefix D, kept as the images of X_q
   // and Z_q; after a Clifford gate g, M'(s) = M(g^dagger s g).
   std::vector<PauliXZ> MX(n), MZ(n);
@@ -685,7 +690,7 @@ qx_status build_plan_pushthrough(const qx_circuit* c, qx_plan** out) {
     p->program.push_back({kStepRot, int(p->rots.size() - 1), 0});
   };
   CliffPass all;  // every Clifford gate, in circuit order
-  for (const qx_instr& g : c->ins) {
+  for (const qx_instr& g : cins) {
     switch (g.gate) {
       case QX_RX:
       case QX_RY:
@@ -954,25 +959,7 @@ qx_status inverse_circuit(const qx_circuit* c, qx_circuit** out) {
   return QX_OK;
 }
 
-}  // namespace qx
-
-using namespace qx;
-
-extern "C" {
-
-void qx_default_opts(qx_prop_opts* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof *o);
-  o->precision = 64;
-  o->eps = 0.0;
-  o->gen_begin = 0;
-  o->gen_end = 0;
-  o->timeout_ms = 2000;
-}
-
-qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out) {
-  clear_error();
-  if (!out) return fail(QX_EINVAL, "out is NULL");
+qx_status validate_instrs(int n, const qx_instr* ins, size_t m) {
   if (n < 1) return fail(QX_EINVAL, "n must be >= 1");
   if (n > kMaxQubits) return fail(QX_EUNSUPPORTED, "n > 128 is not supported");
   if (m && !ins) return fail(QX_EINVAL, "ins is NULL");
@@ -1006,6 +993,29 @@ qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out
     if (!std::isfinite(g.theta))
       return fail(QX_EINVAL, "instruction " + std::to_string(i) + ": theta not finite");
   }
+  return QX_OK;
+}
+
+}  // namespace qx
+
+using namespace qx;
+
+extern "C" {
+
+void qx_default_opts(qx_prop_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = 64;
+  o->eps = 0.0;
+  o->gen_begin = 0;
+  o->gen_end = 0;
+  o->timeout_ms = 2000;
+}
+
+qx_status qx_load_circuit(int n, const qx_instr* ins, size_t m, qx_circuit** out) {
+  clear_error();
+  if (!out) return fail(QX_EINVAL, "out is NULL");
+  if (const qx_status st = validate_instrs(n, ins, m)) return st;
   auto* c = new (std::nothrow) qx_circuit;
   if (!c) return fail(QX_ENOMEM, "host allocation failed");
   c->n = n;

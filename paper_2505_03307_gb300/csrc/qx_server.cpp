@@ -124,12 +124,13 @@ void planner_main(qx_server* s) {
         continue;
       }
     }
-    qx_circuit* c = nullptr;
+    // the checks of qx_load_circuit, then the plan takes the request's
+    // instructions over (nothing else reads them)
     qx_plan* p = nullptr;
-    qx_status st = qx_load_circuit(r->n, r->ins.data(), r->ins.size(), &c);
-    if (st == QX_OK) st = qx_group_ops_pushthrough(c, &p);
+    qx::clear_error();
+    qx_status st = qx::validate_instrs(r->n, r->ins.data(), r->ins.size());
+    if (st == QX_OK) st = qx::build_plan_pushthrough(r->n, std::move(r->ins), &p);
     const std::string msg = st == QX_OK ? std::string() : std::string(qx_last_error());
-    qx_free_circuit(c);
     std::lock_guard<std::mutex> lock(s->mu);
     if (st != QX_OK) {
       finish(s, r, st, msg, nullptr);
