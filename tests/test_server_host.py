@@ -53,3 +53,26 @@ def test_server_queue_limit():
             rejected += 1
     assert accepted >= 2
     srv.close()
+
+
+def test_server_rejects_an_invalid_circuit_in_the_planner():
+    """A request with a bad instruction fails in its planner with the error
+    of qx_load_circuit (QX_EINVAL, naming the first bad instruction); the
+    valid requests around it are planned as usual."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    n, instrs = W.random_layers(3)
+    bad = list(instrs)
+    bad[17] = ("CX", 2, 2, 0.0)
+    bad[40] = ("H", 99, -1, 0.0)
+    srv = qx.Server(slots=1, max_queue=10)
+    t_ok = srv.submit(n, instrs)
+    t_bad = srv.submit(n, bad)
+    with pytest.raises(qx.QxError) as e:
+        srv.wait(t_bad)
+    assert e.value.name == "QX_EINVAL" and "instruction 17: bad second wire" in str(e.value)
+    with pytest.raises(qx.QxError) as e:
+        srv.wait(t_ok)
+    assert e.value.name in ("QX_EUNSUPPORTED", "QX_ECUDA")  # planned, then no GPU
+    srv.close()
