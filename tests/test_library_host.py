@@ -205,3 +205,20 @@ def test_pass_tables_of_a_many_pass_plan():
         for s, r in zip(starts, ref):
             (want_s, want_w), = O.as_dict(r).items()
             assert plan.clifford_apply(k, s) == (want_s, int(want_w))
+
+
+@pytest.mark.parametrize("dag", [False, True])
+def test_plan_tables_outlive_the_circuit(dag):
+    """A plan keeps its own instructions: after the circuit is freed, its
+    operator tables (recomputed on request) still equal the oracle's."""
+    import gc
+    n, instrs = W.random_small(21, 6, 120, angles="uniform")
+    c = qx.load_circuit(n, instrs)
+    plan = qx.group_ops(c, dag=dag)
+    del c
+    gc.collect()
+    ref = O.plan(n, instrs, dag=dag)
+    assert plan.ops() == [k for k, _ in ref]
+    for op, (kind, lut) in enumerate(ref):
+        if kind == "U":
+            assert np.array_equal(plan.lut(op), lut), op
